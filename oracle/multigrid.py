@@ -1,0 +1,204 @@
+"""Block Gauss-Seidel V-cycle for the LDG Stokes system (oracle).
+
+Section 3 (Multigrid design):
+  * Block Gauss-Seidel: blocks are all velocity and pressure unknowns of one
+    element; x_i <- A_ii^{-1} (b_i - sum_{j != i} A_ij x_j).  The sweep is
+    multi-coloured (colour sum_k (i_k mod 2) 2^k, colours in ascending order,
+    every element of one colour updated from the same x); a lexicographic
+    (element-order) sweep is kept as the second reference.
+  * Algorithm 1: V(E_h, x_h, b_h) with nu1 pre- and nu2 post-smoothing sweeps,
+    r_2h = (I_2h^h)^T (b_h - A_h x_h), coarse guess 0, x_h += I_2h^h x_2h.
+  * Bottom solver (Section 3 footnote on the trivial kernel): symmetric
+    eigendecomposition of the coarsest operator with near-zero eigenvalues
+    snapped to zero (least-squares solution).
+  * V-cycle-preconditioned GMRES (left preconditioning, not restarted) and the
+    convergence rate rho of eq. (rho).
+
+Readings: post-smoothing visits the colours in the same ascending order; the
+snap threshold is |lambda| <= 1e-10 max|lambda|; the A_ii^{-1} applied by the
+smoother is the explicit inverse (numpy.linalg.inv); the outer iteration is
+x <- x + V(0, b - A x) until ||b - A x||_2 <= rtol ||b||_2.
+"""
+import numpy as np
+import scipy.sparse as sp
+
+from .hierarchy import build_hierarchy, diag_blocks
+
+SNAP_THETA = 1e-10
+
+
+def round_fp32(a):
+    return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def round_bf16(a):
+    """Round to bfloat16 (round to nearest even from the fp32 value)."""
+    f = np.asarray(a, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+class SmootherLevel:
+    """Smoother data of one level: A_ii, A_ii^{-1}, and the off-block-diagonal
+    part of A restricted to the rows of each colour."""
+
+    def __init__(self, lev, storage=None):
+        self.lev = lev
+        self.nb = lev.nb
+        self.ne = lev.ne
+        A = lev.A
+        self.diag = diag_blocks(A, self.ne, self.nb)
+        self.inv = np.linalg.inv(self.diag)
+        coo = A.tocoo()
+        off = (coo.row // self.nb) != (coo.col // self.nb)
+        self.Aoff = sp.csr_matrix((coo.data[off], (coo.row[off], coo.col[off])), shape=A.shape)
+        if storage == "fp32":
+            self.inv = round_fp32(self.inv)
+            self.Aoff.data = round_fp32(self.Aoff.data)
+            self.diag = round_fp32(self.diag)
+        elif storage == "bf16":
+            self.inv = round_bf16(self.inv)
+            self.Aoff.data = round_bf16(self.Aoff.data)
+            self.diag = round_bf16(self.diag)
+        self.colour = lev.mesh.colour()
+        self.ncol = 2 ** lev.mesh.d
+        self.elems = [np.nonzero(self.colour == c)[0] for c in range(self.ncol)]
+        self.rows = [(e[:, None] * self.nb + np.arange(self.nb)[None, :]).ravel() for e in self.elems]
+        self.Aoff_rows = [self.Aoff[r, :].tocsr() for r in self.rows]
+
+    def colour_step(self, x, b, c):
+        """Update every element of colour c from the current x (one data-parallel step)."""
+        r = self.rows[c]
+        g = (b[r] - self.Aoff_rows[c] @ x).reshape(-1, self.nb)
+        x[r] = np.einsum("eij,ej->ei", self.inv[self.elems[c]], g).ravel()
+
+    def sweep(self, x, b):
+        for c in range(self.ncol):
+            self.colour_step(x, b, c)
+
+    def sweep_lexicographic(self, x, b):
+        """Element-order block Gauss-Seidel (no colours)."""
+        nb = self.nb
+        A = self.Aoff
+        for i in range(self.ne):
+            sl = slice(i * nb, (i + 1) * nb)
+            g = b[sl] - A[sl, :] @ x
+            x[sl] = self.inv[i] @ g
+
+
+def bottom_pseudo_inverse(A, theta=SNAP_THETA):
+    """Least-squares inverse of the coarsest operator: eigendecomposition with
+    |lambda| <= theta max|lambda| snapped to zero.  Returns (pinv, n_snapped)."""
+    Ad = A.toarray()
+    Ad = 0.5 * (Ad + Ad.T)
+    lam, V = np.linalg.eigh(Ad)
+    keep = np.abs(lam) > theta * np.abs(lam).max()
+    inv = np.where(keep, 1.0 / np.where(keep, lam, 1.0), 0.0)
+    return (V * inv[None, :]) @ V.T, int((~keep).sum())
+
+
+class Multigrid:
+    """The V-cycle hierarchy of a problem (oracle)."""
+
+    def __init__(self, prob, storage=None, levels=None, injections=None, max_levels=None):
+        self.prob = prob
+        if levels is None:
+            levels, injections = build_hierarchy(prob, max_levels=max_levels)
+        self.levels = levels
+        self.I = injections
+        self.storage = storage
+        self.sm = [SmootherLevel(l, storage) for l in levels[:-1]]
+        self.bottom, self.kernel_dim_bottom = bottom_pseudo_inverse(levels[-1].A)
+        self.nu1, self.nu2 = prob.nu1, prob.nu2
+
+    @property
+    def A(self):
+        return self.levels[0].A
+
+    def residual(self, l, x, b):
+        return b - self.levels[l].A @ x
+
+    def restrict(self, l, r):
+        """r_2h = (I_2h^h)^T r_h (Algorithm 1, line 5)."""
+        return self.I[l].T @ r
+
+    def prolong(self, l, xc):
+        """I_2h^h x_2h (injection)."""
+        return self.I[l] @ xc
+
+    def vcycle(self, x, b, l=0, nu1=None, nu2=None, lexicographic=False):
+        """Algorithm 1: returns x after one V-cycle (x is updated in place)."""
+        nu1 = self.nu1 if nu1 is None else nu1
+        nu2 = self.nu2 if nu2 is None else nu2
+        if l == len(self.levels) - 1:
+            x[:] = self.bottom @ b
+            return x
+        sm = self.sm[l]
+        for _ in range(nu1):
+            (sm.sweep_lexicographic if lexicographic else sm.sweep)(x, b)
+        r2 = self.restrict(l, self.residual(l, x, b))
+        x2 = np.zeros_like(r2)
+        self.vcycle(x2, r2, l + 1, nu1, nu2, lexicographic)
+        x += self.prolong(l, x2)
+        for _ in range(nu2):
+            (sm.sweep_lexicographic if lexicographic else sm.sweep)(x, b)
+        return x
+
+    def precondition(self, r, **kw):
+        """The linear operator V: one V-cycle from a zero initial guess."""
+        c = np.zeros_like(r)
+        return self.vcycle(c, r, **kw)
+
+    def solve(self, b, x0=None, rtol=1e-10, maxit=100, **kw):
+        """Outer iteration x <- x + V(0, b - A x) (iterative refinement)."""
+        x = np.zeros_like(b) if x0 is None else x0.copy()
+        nb_ = np.linalg.norm(b)
+        hist = []
+        for it in range(maxit + 1):
+            r = b - self.A @ x
+            rel = np.linalg.norm(r) / nb_
+            hist.append(rel)
+            if rel <= rtol or it == maxit:
+                break
+            x += self.precondition(r, **kw)
+        return x, hist
+
+    def gmres_rho(self, x0, reduction=1e-8, maxit=200, **kw):
+        """eq. (rho): average reduction per iteration of left-preconditioned
+        GMRES on V A x = V b with b = 0 from x0; returns (rho, iterations)."""
+        A = self.A
+
+        def op(v):
+            return self.precondition(A @ v, **kw)
+
+        r0 = -op(x0)
+        beta = np.linalg.norm(r0)
+        Q = [r0 / beta]
+        H = np.zeros((maxit + 1, maxit))
+        cs, sn = np.zeros(maxit), np.zeros(maxit)
+        g = np.zeros(maxit + 1)
+        g[0] = beta
+        n = 0
+        for j in range(maxit):
+            w = op(Q[j])
+            for i in range(j + 1):
+                H[i, j] = np.dot(Q[i], w)
+                w = w - H[i, j] * Q[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            Q.append(w / H[j + 1, j] if H[j + 1, j] > 0 else w)
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            n = j + 1
+            if abs(g[j + 1]) <= reduction * beta:
+                break
+        return float(np.exp(np.log(abs(g[n]) / beta) / n)), n

@@ -1,0 +1,375 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, invariants (symmetry, kernel dimension), convergence orders quoted in
+the text, the equivalence of operator coarsening with direct assembly, a dense
+direct solve, and the tau / rho statements of Tables 1-2 and Sections 4-5.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_1911_05888_gb300 import problems as P
+from oracle import basis, hierarchy, ldg, multigrid
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ----------------------------------------------------------------- basis ----
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_legendre_orthonormal(p):
+    np.testing.assert_allclose(basis.mass_1d(p), 2 * np.eye(p + 1), atol=1e-13)
+
+
+def test_closed_forms_p1():
+    # psi_0 = 1, psi_1 = sqrt(3) xi:  int psi_0 psi_1' = 2 sqrt(3), int psi_1 psi_1' = 0.
+    K = basis.deriv_1d(1)
+    np.testing.assert_allclose(K, [[0, 2 * np.sqrt(3)], [0, 0]], atol=1e-14)
+    # psi_1((xi - 1)/2) = psi_1(xi)/2 - sqrt(3)/2 psi_0 on the lower child.
+    P0 = basis.child_1d(1, 0)
+    np.testing.assert_allclose(P0, [[1, -np.sqrt(3) / 2], [0, 0.5]], atol=1e-14)
+    np.testing.assert_allclose(basis.trace_1d(1, -1), [1, -np.sqrt(3)], atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_injection_reproduces_coarse_polynomial(p):
+    rng = np.random.default_rng(0)
+    c = rng.standard_normal(p + 1)
+    xi = np.linspace(-1, 1, 7)
+    for child in (0, 1):
+        fine = basis.child_1d(p, child) @ c
+        coarse_at = basis.psi(p, (xi + 2 * child - 1) / 2) @ c
+        np.testing.assert_allclose(basis.psi(p, xi) @ fine, coarse_at, atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_derivative_matrix_integrates_by_parts(p):
+    K = basis.deriv_1d(p)
+    tp, tm = basis.trace_1d(p, 1), basis.trace_1d(p, -1)
+    np.testing.assert_allclose(K + K.T, np.outer(tp, tp) - np.outer(tm, tm), atol=1e-12)
+
+
+# --------------------------------------------------------- operator pins ----
+
+def _problems_small():
+    return [
+        P.periodic_standard_2d(n=4, p=2),
+        P.generic(2, 4, 2, 0, [P.DIRICHLET] * 4),
+        P.generic(2, 4, 1, 1, [P.STRESS] * 4),
+        P.stress_variable_mu_2d(n=4, p=2),
+        P.generic(3, 4, 1, 0, [P.PERIODIC] * 6),
+        P.generic(3, 4, 1, 1, [P.DIRICHLET, P.STRESS] * 3),
+        P.unsteady_periodic_3d(n=4, p=1, re=10.0),
+    ]
+
+
+@pytest.mark.parametrize("prob", _problems_small(), ids=lambda q: q.name or str(q.bc))
+def test_symmetry(prob):
+    levels, _ = hierarchy.build_hierarchy(prob)
+    for lev in levels:
+        A = lev.A
+        assert abs(A - A.T).max() <= 1e-13 * abs(A).max()
+
+
+@pytest.mark.parametrize("prob,dim", [
+    (P.periodic_standard_2d(n=4, p=2), 3),                          # constant u, constant p
+    (P.generic(2, 4, 2, 0, [P.DIRICHLET] * 4), 1),                  # constant p
+    (P.generic(2, 4, 2, 1, [P.STRESS] * 4), 3),                     # 2 translations + rotation
+    (P.generic(2, 4, 1, 0, [P.DIRICHLET] * 3 + [P.STRESS]), 0),
+    (P.generic(3, 2, 1, 0, [P.PERIODIC] * 6), 4),
+    (P.unsteady_periodic_3d(n=2, p=1, re=10.0), 1),                 # mass term removes constant u
+])
+def test_kernel_dimension(prob, dim):
+    lev = hierarchy.build_hierarchy(prob, max_levels=1)[0][0]
+    lam = np.linalg.eigvalsh(lev.A.toarray())
+    assert int((np.abs(lam) <= 1e-10 * np.abs(lam).max()).sum()) == dim
+
+
+def test_rotation_in_stress_kernel():
+    """gamma = 1 with stress conditions: u = (-y, x), p = 0 is a null vector
+    (Section 3 footnote on the trivial kernel)."""
+    prob = P.generic(2, 4, 1, 1, [P.STRESS] * 4)
+    lev = hierarchy.build_hierarchy(prob, max_levels=1)[0][0]
+    mesh, s, nb = lev.mesh, lev.s, lev.nb
+    x = np.zeros((mesh.ne, nb))
+    # L2 projection of (-y, x) on Q_1: mode 0 = value at centre, x-linear mode
+    # psi_1(xi_x) = sqrt(3) xi_x with x = c + h xi / 2.
+    for e in range(mesh.ne):
+        cx, cy = mesh.centre[e]
+        hx, hy = mesh.h
+        x[e, 0] = -cy
+        x[e, 2] = -hy / 2 / np.sqrt(3)           # u_1 mode (0, 1): y-linear
+        x[e, s + 0] = cx
+        x[e, s + 1] = hx / 2 / np.sqrt(3)        # u_2 mode (1, 0): x-linear
+    r = lev.A @ x.ravel()
+    assert np.linalg.norm(r) <= 1e-12 * abs(lev.A).max() * np.linalg.norm(x)
+
+
+def _block_counts(lev):
+    """Number of nonzero s x s coupling sub-blocks per interior element."""
+    A = lev.A.tocsr()
+    s, nb = lev.s, lev.nb
+    d = lev.mesh.d
+    e = int(np.ravel_multi_index(tuple([2] * d), lev.mesh.n[::-1]))  # an interior element
+    rows = A[e * nb:(e + 1) * nb, :].tocoo()
+    keys = set()
+    for r, c, v in zip(rows.row, rows.col, rows.data):
+        if abs(v) > 1e-14 * abs(A).max() and c // nb != e:
+            keys.add((c // nb, r // s, (c % nb) // s))
+    return len(keys)
+
+
+@pytest.mark.parametrize("d,gamma,expect", [(2, 0, 16), (2, 1, 22), (3, 0, 30), (3, 1, 48)])
+def test_coupling_sub_block_count(d, gamma, expect):
+    """Sparsity of the element coupling implied by the one-sided fluxes:
+    2d(d+2) sub-blocks (standard) or 2d(2d+1) + d(d-1) (viscous stress)."""
+    prob = P.generic(d, 6 if d == 2 else 5, 1, gamma, [P.PERIODIC] * (2 * d))
+    lev = hierarchy.build_hierarchy(prob, max_levels=1)[0][0]
+    assert _block_counts(lev) == expect
+
+
+@pytest.mark.parametrize("gamma,d", [(0, 2), (1, 2), (1, 3)])
+def test_parity_colouring_separates_couplings(gamma, d):
+    prob = P.generic(d, 4, 1, gamma, [P.PERIODIC] * (2 * d))
+    lev = hierarchy.build_hierarchy(prob, max_levels=1)[0][0]
+    col = lev.mesh.colour()
+    coo = lev.A.tocoo()
+    ei, ej = coo.row // lev.nb, coo.col // lev.nb
+    off = ei != ej
+    assert not np.any(col[ei[off]] == col[ej[off]])
+
+
+@pytest.mark.parametrize("prob", [
+    P.generic(2, 8, 2, 0, [P.DIRICHLET, P.DIRICHLET, P.STRESS, P.DIRICHLET]),
+    P.generic(2, 8, 3, 1, [P.DIRICHLET] * 3 + [P.STRESS]),
+    P.generic(2, 8, 2, 1, [P.PERIODIC] * 4),
+    P.generic(3, 4, 1, 1, [P.PERIODIC, P.PERIODIC, P.DIRICHLET, P.DIRICHLET, P.STRESS, P.DIRICHLET]),
+])
+def test_coarsening_equals_direct_assembly(prob):
+    """T8 (Appendix B): Algorithm 2 on the n mesh equals assembling the LDG
+    operator directly on the n/2 mesh (constant mu, Cartesian)."""
+    levels, _ = hierarchy.build_hierarchy(prob, max_levels=2)
+    coarse = prob.with_(n=tuple(v // 2 for v in prob.n))
+    direct = hierarchy.build_hierarchy(coarse, max_levels=1)[0][0]
+    diff = abs(levels[1].A - direct.A).max()
+    assert diff <= 1e-12 * abs(direct.A).max()
+
+
+def test_unsteady_penalties_coarsen_geometrically():
+    """Algorithm 3: E_mu (x2) and E_rho (x1/2) coarsen to their direct
+    assembly on the coarse mesh; M_rho by Galerkin."""
+    prob = P.unsteady_periodic_3d(n=4, p=1, re=3.0)
+    fine = ldg.fine_operators(prob)
+    mesh_c = ldg.Mesh(3, (2, 2, 2), prob.lo, prob.hi, prob.bc)
+    I = hierarchy.injection(fine["mesh"], mesh_c, prob.p)
+    co = hierarchy.coarsen(fine, I, mesh_c, True)
+    direct = ldg.fine_operators(prob.with_(n=(2, 2, 2)))
+    for key in ("Emu", "Erho", "Mrho", "Mmu"):
+        assert abs(co[key] - direct[key]).max() <= 1e-12 * abs(direct[key]).max(), key
+
+
+def test_mass_coarsening_and_injection():
+    """T9: M_2h = I^T M_h I equals the coarse mass matrix |E_c| I."""
+    prob = P.generic(2, 8, 3, 0, [P.PERIODIC] * 4)
+    ops = ldg.fine_operators(prob)
+    mesh_c = ldg.Mesh(2, (4, 4), prob.lo, prob.hi, prob.bc)
+    I = hierarchy.injection(ops["mesh"], mesh_c, prob.p)
+    M2 = (I.T @ ops["M"] @ I).toarray()
+    np.testing.assert_allclose(M2, mesh_c.vol * np.eye(M2.shape[0]), atol=1e-14)
+
+
+def test_etimedep_reduces_to_harmonic_mean():
+    """eq. (Etimedep): for proportional blocks x B and y B the combination is
+    the harmonic combination xy/(x+y) B (the identity behind eq. Etimedep)."""
+    s = 4
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((s, s))
+    B = B @ B.T
+    x, y = 0.7, 5.0
+    Emu = sp.csr_matrix(x * B)
+    Erho = sp.csr_matrix(y * B)
+    E = hierarchy.combine_pressure_penalty(Emu, Erho, 1, s).toarray()
+    np.testing.assert_allclose(E, x * y / (x + y) * B, rtol=1e-13)
+
+
+def test_taugeneral_limits():
+    """T11: eq. (taupgeneral) gives tau h / mu when rho = 0 and tau0 delta / (h rho)
+    when mu = 0.  Checked on assembled E of a one-face problem."""
+    base = P.unsteady_periodic_3d(n=2, p=1, re=1.0)
+    tiny = 1e-300
+    steady_like = base.with_(rho=lambda x: np.full(x.shape[:-1], tiny))
+    inviscid = base.with_(mu=lambda x: np.full(x.shape[:-1], tiny))
+    ref_mu = ldg.fine_operators(steady_like)
+    ref_rho = ldg.fine_operators(inviscid)
+    np.testing.assert_allclose(ref_mu["E"].toarray(), ref_mu["Emu"].toarray(), rtol=1e-12, atol=0)
+    np.testing.assert_allclose(ref_rho["E"].toarray(), ref_rho["Erho"].toarray(), rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------- accuracy and solvers ----
+
+def _l2_errors(prob, mg, x):
+    lev = mg.levels[0]
+    mesh, d, p, s = lev.mesh, prob.d, prob.p, lev.s
+    q = p + 3
+    xv, wv = mesh.volume_points(q)
+    Phi = basis.tensor_basis(d, p, q)
+    jac = mesh.vol / 2 ** d
+    vals = np.einsum("qa,eva->eqv", Phi, x.reshape(mesh.ne, d + 1, s))
+    ue, pe = prob.exact.u(xv), prob.exact.p(xv)
+    out = []
+    for v in range(d + 1):
+        err = vals[..., v] - (ue[..., v] if v < d else pe)
+        if all(b == P.PERIODIC for b in prob.bc) or (v == d and P.STRESS not in prob.bc):
+            err = err - (err * wv).sum() / (wv.sum() * mesh.ne)   # kernel mode (constant)
+        out.append(np.sqrt(jac * (err ** 2 * wv).sum()))
+    return np.array(out)
+
+
+def _solve_manufactured(prob):
+    mg = multigrid.Multigrid(prob)
+    b = mg.levels[0].P @ ldg.rhs(prob, mg.levels[0].ops)
+    x, hist = mg.solve(b, rtol=1e-12, maxit=300)
+    assert hist[-1] <= 1e-12
+    return _l2_errors(prob, mg, x)
+
+
+def test_order_periodic_standard():
+    """Section 5.1: u and p converge at order p+1 (p = 2) with periodic conditions."""
+    e8 = _solve_manufactured(P.periodic_standard_2d(n=8, p=2))
+    e16 = _solve_manufactured(P.periodic_standard_2d(n=16, p=2))
+    rate = np.log2(e8 / e16)
+    assert np.all(np.abs(rate - 3.0) < 0.3), rate
+
+
+def test_order_stress_variable_viscosity():
+    """Sections 5.3-5.4: viscous-stress form, variable mu, Dirichlet + stress
+    sides: u order p+1, p order about p+1/2 in L2 (p = 2)."""
+    e8 = _solve_manufactured(P.stress_variable_mu_2d(n=8, p=2))
+    e16 = _solve_manufactured(P.stress_variable_mu_2d(n=16, p=2))
+    rate = np.log2(e8 / e16)
+    assert np.all(np.abs(rate[:2] - 3.0) < 0.3), rate
+    assert 2.0 < rate[2] < 3.2, rate
+
+
+@pytest.mark.parametrize("prob", [
+    P.periodic_standard_2d(n=4, p=1),
+    P.generic(2, 4, 2, 0, [P.DIRICHLET] * 4),
+    P.generic(2, 4, 3, 1, [P.DIRICHLET] * 3 + [P.STRESS]),
+    P.generic(2, 4, 2, 1, [P.STRESS] * 4),
+])
+def test_vcycle_solve_matches_dense_pseudo_inverse(prob):
+    """The converged V-cycle iteration equals the least-squares solution of a
+    dense eigendecomposition, modulo the kernel."""
+    mg = multigrid.Multigrid(prob)
+    A = mg.A.toarray()
+    lam, V = np.linalg.eigh(A)
+    keep = np.abs(lam) > 1e-10 * np.abs(lam).max()
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal(A.shape[0])
+    b -= V[:, ~keep] @ (V[:, ~keep].T @ b)
+    pinv = lambda v: V[:, keep] @ ((V[:, keep].T @ v) / lam[keep])
+    x_ref = pinv(b)
+    for _ in range(3):                      # refine the dense solution in FP64
+        x_ref += pinv(b - A @ x_ref)
+    x, hist = mg.solve(b, rtol=1e-13, maxit=400)
+    x -= V[:, ~keep] @ (V[:, ~keep].T @ x)
+    # Both are least-squares solutions up to their residuals:
+    # ||x - x_ref|| <= (||b - A x|| + ||b - A x_ref||) / min |lambda|.
+    bound = (np.linalg.norm(b - A @ x) + np.linalg.norm(b - A @ x_ref)) / np.abs(lam[keep]).min()
+    assert np.linalg.norm(x - x_ref) <= 1.5 * bound + 1e-14 * np.linalg.norm(x_ref)
+    assert np.linalg.norm(x - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+
+
+def test_colour_step_matches_block_definition():
+    """One colour step equals x_i = A_ii^{-1}(b_i - sum_{j != i} A_ij x_j) from
+    the dense operator, for every element of that colour."""
+    prob = P.generic(2, 4, 2, 1, [P.DIRICHLET] * 3 + [P.STRESS])
+    mg = multigrid.Multigrid(prob)
+    sm = mg.sm[0]
+    A = mg.A.toarray()
+    nb = sm.nb
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(A.shape[0])
+    b = rng.standard_normal(A.shape[0])
+    for c in range(sm.ncol):
+        ref = x.copy()
+        for i in sm.elems[c]:
+            sl = slice(i * nb, (i + 1) * nb)
+            g = b[sl] - A[sl, :] @ x + A[sl, sl] @ x[sl]
+            ref[sl] = np.linalg.solve(A[sl, sl], g)
+        sm.colour_step(x, b, c)
+        np.testing.assert_allclose(x, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def test_lexicographic_reference_converges():
+    prob = P.periodic_standard_2d(n=8, p=2)
+    mg = multigrid.Multigrid(prob)
+    b = mg.levels[0].P @ ldg.rhs(prob, mg.levels[0].ops)
+    x, hist = mg.solve(b, rtol=1e-10, maxit=60, lexicographic=True)
+    assert hist[-1] <= 1e-10
+
+
+def test_bottom_snaps_kernel():
+    """The bottom solver snaps exactly the trivial kernel (T2 on the coarsest level)."""
+    mg = multigrid.Multigrid(P.periodic_standard_2d(n=8, p=2))
+    assert mg.kernel_dim_bottom == 3
+    mg = multigrid.Multigrid(P.generic(2, 8, 2, 1, [P.DIRICHLET] * 3 + [P.STRESS]))
+    assert mg.kernel_dim_bottom == 0
+
+
+# ------------------------------------------------------- tau and rho pins ----
+
+def test_golden_tables_match_problem_defaults():
+    for form, d, p, tau in read_golden("table1_optimal_tau.txt"):
+        assert P.TABLE1_TAU[(int(form), int(d), int(p))] == float(tau)
+    for form, d, p, lo, hi in read_golden("table2_tau_window.txt"):
+        assert P.TABLE2_WINDOW[(int(form), int(d), int(p))] == (float(lo), float(hi))
+
+
+def _rho(prob, seed=1):
+    mg = multigrid.Multigrid(prob)
+    x0 = P.random_vector(prob.n_elements, prob.nb, seed=seed).ravel()
+    return mg.gmres_rho(x0)
+
+
+def test_rho_at_optimal_tau_and_breakdown():
+    """Sections 4-5: with tau from Table 1 and V(3,3)-preconditioned GMRES,
+    rho is within the typical 0.05-0.1 range; for tau = 1e-3 (below the 1e-2
+    threshold) the V-cycle breaks down and rho approaches one."""
+    golden = {r[0]: float(r[1]) for r in read_golden("convergence_statements.txt")}
+    rho, it = _rho(P.periodic_standard_2d(n=16, p=2, nu=(3, 3)))
+    assert rho <= golden["rho_typical_hi"], rho
+    rho_bad, _ = _rho(P.periodic_standard_2d(n=16, p=2, nu=(3, 3), tau=1e-3))
+    assert rho_bad >= 0.8, rho_bad
+
+
+@pytest.mark.slow
+def test_table1_tau_within_table2_window_of_oracle_minimum():
+    """Table 1 / Table 2: the paper's optimal tau lies inside the 12.5 percent
+    window of the oracle's own rho(tau) curve (viscous-stress form, p = 2)."""
+    taus = [0.02, 0.03, 0.04, 0.05, 0.07, 0.1, 0.15]
+    rhos = [_rho(P.generic(2, 32, 2, 1, [P.PERIODIC] * 4, tau=t, nu=(3, 3)))[0] for t in taus]
+    rmin = min(rhos)
+    rho_tab, _ = _rho(P.generic(2, 32, 2, 1, [P.PERIODIC] * 4, tau=P.TABLE1_TAU[(1, 2, 2)], nu=(3, 3)))
+    assert rho_tab <= rmin ** (1 - 1 / 9), (rho_tab, rmin)
+    lo, hi = P.TABLE2_WINDOW[(1, 2, 2)]
+    best = taus[int(np.argmin(rhos))]
+    assert lo * 0.8 <= best <= hi * 1.25, best
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    v = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -9, -3.140625])
+    np.testing.assert_array_equal(multigrid.round_bf16(v), [1.0, 1.0 + 2 * 2.0 ** -7, 1.0, -3.140625])
