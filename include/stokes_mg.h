@@ -1,0 +1,204 @@
+/*
+ * stokes_mg.h -- C ABI of the GB300 multigrid library for LDG-discretised
+ * Stokes systems (Saye, "Fast multigrid solution of high-order accurate
+ * multi-phase Stokes problems", arXiv:1911.05888).
+ *
+ * The library builds, for a Cartesian mesh, the LDG operator of the paper's
+ * eq. (blockform) / (timedep2) on every level of a geometric hierarchy
+ * (operator coarsening, Appendix B, Algorithms 2 and 3), factorises the
+ * element blocks, and runs on one GPU the V-cycle of Algorithm 1: coloured
+ * element block Gauss-Seidel, residual, restriction by (I_2h^h)^T,
+ * prolongation by injection and a pseudo-inverse bottom solve.
+ *
+ * Conventions
+ *  - Every call returns an int status: STK_OK (0) or a negative STK_ERR_*.
+ *    stk_last_error(ctx) gives a message owned by ctx, valid until the next
+ *    call on ctx.  No C++ exception crosses this interface.
+ *  - Host arrays passed in are owned by the caller and only read during the
+ *    call.  Device pointers (suffix _dev) are caller-owned device memory on
+ *    the context's device; the library never frees them.  Streams are
+ *    cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - The library owns its hierarchy, work vectors and CUDA graphs until
+ *    stk_destroy.
+ *  - Vectors are element-blocked: [element][nb] with nb = (d+1) (p+1)^d,
+ *    the per-element order [u_1 modes, ..., u_d modes, p modes], modes
+ *    lexicographic with the x index fastest, elements lexicographic with x
+ *    fastest.  The basis is the tensor product of sqrt(2l+1) P_l (Legendre) on
+ *    each element's reference cube, so the element mass matrix is |E| times
+ *    the identity.
+ *  - Values are double unless stated.  With nrhs > 1 a vector is
+ *    [nrhs][element][nb] (right-hand sides outermost).
+ */
+#ifndef STOKES_MG_H
+#define STOKES_MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  STK_OK = 0,
+  STK_ERR_INVALID_ARG = -1,
+  STK_ERR_OOM = -2,
+  STK_ERR_SINGULAR_BLOCK = -3,
+  STK_ERR_TIMEOUT = -4,
+  STK_ERR_DIVERGED = -5,
+  STK_ERR_NOT_SETUP = -6,
+  STK_ERR_CUDA = -7
+};
+
+/* Boundary types of a box side (governing eq. (govern3) of the paper). */
+enum { STK_BC_PERIODIC = 0, STK_BC_DIRICHLET = 1, STK_BC_STRESS = 2 };
+
+/* Storage precision of the element blocks inside the V-cycle. */
+enum { STK_FP64 = 0, STK_FP32 = 1, STK_BF16 = 2 };
+
+/* Point sets at which the caller samples coefficients and data. */
+enum { STK_PTS_VOLUME = 0, STK_PTS_INTERIOR_FACE = 1, STK_PTS_BOUNDARY_FACE = 2 };
+
+typedef struct stk_ctx stk_ctx;
+
+/* Create a context on CUDA device `device`.  *out is set on success. */
+int stk_create(stk_ctx** out, int device);
+/* Release everything the context owns.  NULL is accepted. */
+int stk_destroy(stk_ctx* ctx);
+/* Message describing the last error on ctx (never NULL). */
+const char* stk_last_error(stk_ctx* ctx);
+
+/*
+ * Mesh: the box [lo, hi] in d = 2 or 3 dimensions split into n[0] x ... x
+ * n[d-1] equal elements (Section 2: Cartesian grids).  bc[2k] is the type of
+ * the low side of axis k, bc[2k+1] of the high side; STK_BC_PERIODIC must be
+ * set on both sides of an axis.
+ */
+int stk_set_mesh(stk_ctx* ctx, int d, const int* n, const double* lo, const double* hi,
+                 const int* bc);
+
+/*
+ * Discretisation (Section 2): degree p >= 1 of the tensor-product space Q_p
+ * for velocity and pressure; gamma = 0 standard form, 1 viscous-stress form
+ * (eq. govern1).  Quadrature: Gauss with 2p+2 points per axis for the
+ * mu/rho-weighted mass matrices, face means and data integrals.
+ */
+int stk_set_discretisation(stk_ctx* ctx, int p, int gamma);
+
+/*
+ * Penalty parameters (Section 4 and Appendix A.1): tau is the pressure
+ * penalty prefactor of eq. (taueqn), tau_p = tau h / mu; tau0 the prefactor
+ * of the vanishing-viscosity limit in eq. (taupgeneral).  The velocity
+ * penalties are tau_u,bdry = c_bdry p mu / h on Dirichlet faces and
+ * tau_u,0 = c_intra p mu / h on interior faces (Cartesian default 10 and 0).
+ */
+int stk_set_penalty(stk_ctx* ctx, double tau, double tau0, double c_bdry, double c_intra);
+
+/* Number of sample points of a point set (after stk_set_mesh and
+ * stk_set_discretisation): volume Gauss points [element][q^d], interior-face
+ * points [face][q^(d-1)], boundary-face points [face][q^(d-1)] with q = 2p+2.
+ * Faces are enumerated axis by axis; interior faces by their right element
+ * in element order (periodic wrap faces included), boundary faces by
+ * (axis, low side then high side, element order). */
+int stk_num_points(stk_ctx* ctx, int kind, int64_t* count);
+/* Coordinates [count][d] of a point set, and for boundary faces the outward
+ * unit normals [count][d] (normals may be NULL). */
+int stk_get_points(stk_ctx* ctx, int kind, double* xyz, double* normals);
+
+/*
+ * Viscosity mu > 0 sampled at the volume, interior-face and boundary-face
+ * points (eq. sigmaresult: M_mu; face values enter the penalties as face
+ * means).  Checked: every value finite and positive.
+ */
+int stk_set_viscosity(stk_ctx* ctx, const double* mu_vol, const double* mu_iface,
+                      const double* mu_bface);
+
+/*
+ * Unsteady problem (eq. timedep1/timedep2): density rho > 0 at the volume and
+ * interior-face points and the parameter delta > 0 (proportional to the time
+ * step).  The pressure penalty follows eq. (taupgeneral) and is coarsened by
+ * Algorithm 3.  delta = 0 returns to the steady problem.
+ */
+int stk_set_density(stk_ctx* ctx, const double* rho_vol, const double* rho_iface, double delta);
+
+/*
+ * V-cycle options (Algorithm 1): nu1 pre- and nu2 post-smoothing sweeps of
+ * the coloured block Gauss-Seidel method; precision = STK_FP64 (plain) or
+ * STK_FP32 / STK_BF16 (element blocks stored in that type and accumulated
+ * in FP32 inside the cycle; the outer residual and the bottom solve stay
+ * FP64).
+ */
+int stk_set_cycle(stk_ctx* ctx, int nu1, int nu2, int precision);
+
+/*
+ * Setup: fine-level LDG assembly (Appendix A), operator coarsening
+ * (Algorithm 2, or 3 when unsteady) down to the bottom level (some n_k odd or
+ * equal to 2), the Stokes blocks of every level, element-block inverses (FP64
+ * Gauss-Jordan with partial pivoting; STK_ERR_SINGULAR_BLOCK if a pivot
+ * vanishes), the parity colouring, and the bottom pseudo-inverse (symmetric
+ * eigendecomposition with |lambda| <= 1e-10 max|lambda| snapped to zero).
+ * Allocates all device memory the cycle needs.
+ */
+int stk_setup(stk_ctx* ctx, void* stream);
+
+/*
+ * Hierarchy sizes: number of levels, elements per level (array of
+ * nlevels entries, may be NULL), block size nb, number of snapped bottom
+ * eigenvalues (may be NULL).
+ */
+int stk_get_sizes(stk_ctx* ctx, int* nlevels, int64_t* n_elements, int* nb, int* n_snapped);
+
+/* Dense nb x nb block A_ij (row element i, column element j, natural
+ * element indices) of the level-`level` operator, row-major, into a host
+ * array; zero when the elements do not couple. */
+int stk_get_block(stk_ctx* ctx, int level, int64_t i, int64_t j, double* out);
+
+/* Right-hand side b (Appendix A, eq. appstokes1/appstokes2 multiplied by M)
+ * from samples: f_vol [volume point][d+1] = (f_1..f_d, fdiv) with
+ * -div u = fdiv; bdata [boundary-face point][d] = Dirichlet velocity g on
+ * Dirichlet faces, stress sigma.n = h on stress faces (ignored on periodic
+ * sides).  Writes the host array b [element][nb]. */
+int stk_assemble_rhs(stk_ctx* ctx, const double* f_vol, const double* bdata, double* b);
+
+/* ---- hot path ------------------------------------------------------------ */
+
+/* r = b - A x on level 0 in FP64 (eq. blockform); optional ||r||_2 into
+ * *norm_out (host; synchronises the stream when non-NULL). */
+int stk_residual(stk_ctx* ctx, const double* x_dev, const double* b_dev, double* r_dev,
+                 double* norm_out, void* stream);
+
+/* One colour step of the block Gauss-Seidel smoother on level `level` in
+ * FP64: every element i of colour c (parity colouring sum_k (i_k mod 2) 2^k)
+ * gets x_i = A_ii^{-1} (b_i - sum_{j != i} A_ij x_j) (Section 3). */
+int stk_gs_colour(stk_ctx* ctx, int level, int colour, double* x_dev, const double* b_dev,
+                  void* stream);
+
+/* One V-cycle of Algorithm 1 in place on level 0 in FP64: x <- V(x, b). */
+int stk_vcycle(stk_ctx* ctx, double* x_dev, const double* b_dev, void* stream);
+
+/* Restriction r_c = (I_2h^h)^T r (level -> level+1) and prolongation
+ * x += I_2h^h x_c (level+1 -> level), FP64 (Algorithm 1 lines 5 and 7). */
+int stk_restrict(stk_ctx* ctx, int level, const double* r_dev, double* rc_dev, void* stream);
+int stk_prolong(stk_ctx* ctx, int level, const double* xc_dev, double* x_dev, void* stream);
+/* Bottom solve x = A_c^+ b on the last level (FP64). */
+int stk_bottom_solve(stk_ctx* ctx, const double* b_dev, double* x_dev, void* stream);
+
+/*
+ * Solve A x = b to ||b - A x||_2 <= rtol ||b||_2 by the outer iteration
+ * x <- x + V(0, b - A x) (iterative refinement with the V-cycle of
+ * stk_set_cycle's precision as preconditioner; residual in FP64).  x_dev
+ * holds the initial guess.  *iters_out gets the iteration count, hist (may
+ * be NULL, maxit+1 entries) the relative residual history.  Returns
+ * STK_ERR_DIVERGED if the residual becomes non-finite or grows 1e6-fold.
+ */
+int stk_solve(stk_ctx* ctx, double* x_dev, const double* b_dev, double rtol, int maxit,
+              int* iters_out, double* hist, void* stream);
+
+/* Number of kernel launches the library enqueued since the context was
+ * created (all of them are this library's own kernels). */
+int stk_launch_count(stk_ctx* ctx, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOKES_MG_H */

@@ -1,0 +1,702 @@
+// C ABI of the Stokes multigrid library (declarations and contracts in
+// include/stokes_mg.h): context management, device packing of the hierarchy
+// built by setup.cpp, and the host drivers of the V-cycle (Algorithm 1 of
+// arXiv:1911.05888) and of the outer iteration.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "stk_internal.h"
+#include "../../include/stokes_mg.h"
+
+namespace stk {
+cudaError_t launch_element(const Pattern& pat, int storage, int mode, int pos0, int npos,
+                           const int* perm, const int* nbr, const void* cpl, const void* mat,
+                           const void* b, void* x, void* r, cudaStream_t st);
+cudaError_t launch_restrict(int vec64, int d, int s, int nb, const int* nc, const int* nf, int64_t nec,
+                            const double* P, const void* r, void* rc, cudaStream_t st);
+cudaError_t launch_prolong(int vec64, int d, int s, int nb, const int* nf, const int* nc, int64_t nef,
+                           const double* P, const void* xc, void* x, cudaStream_t st);
+cudaError_t launch_bottom(int vec64, int64_t n, const double* pinv, const void* b, void* x,
+                          cudaStream_t st);
+cudaError_t launch_axpy(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st);
+cudaError_t launch_convert(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st);
+cudaError_t launch_to_bf16(int64_t n, void* y, const double* x, cudaStream_t st);
+cudaError_t launch_sumsq(int64_t n, const double* x, double* part, double* out, cudaStream_t st);
+}  // namespace stk
+
+using namespace stk;
+
+struct stk_ctx : public Ctx {};
+
+namespace {
+
+constexpr int MODE_GS = 0, MODE_RESID = 1;
+
+struct CudaFail {
+  cudaError_t e;
+  const char* what;
+};
+
+inline void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw CudaFail{e, what};
+}
+
+template <typename F>
+int guard(stk_ctx* c, F&& fn) {
+  if (!c) return STK_ERR_INVALID_ARG;
+  try {
+    c->err.clear();
+    return fn();
+  } catch (const CudaFail& f) {
+    c->err = std::string(f.what) + ": " + cudaGetErrorString(f.e);
+    return STK_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return STK_ERR_OOM;
+  } catch (...) {
+    c->err = "unexpected internal error";
+    return STK_ERR_INVALID_ARG;
+  }
+}
+
+int fail(stk_ctx* c, int code, const std::string& msg) {
+  c->err = msg;
+  return code;
+}
+
+void* dalloc(Ctx& c, size_t bytes) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e != cudaSuccess) throw CudaFail{e, "cudaMalloc"};
+  c.allocations.push_back(p);
+  return p;
+}
+
+void free_device(Ctx& c) {
+  for (void* p : c.allocations) cudaFree(p);
+  c.allocations.clear();
+  if (c.norm_host) cudaFreeHost(c.norm_host);
+  c.norm_host = nullptr;
+  if (c.graph) cudaGraphExecDestroy(c.graph);
+  c.graph = nullptr;
+  c.graph_x = c.graph_b = nullptr;
+  c.dev.clear();
+  c.ready = false;
+}
+
+int64_t level_ne(const Ctx& c, int l) { return c.host[l].ne; }
+int nlevels(const Ctx& c) { return (int)c.host.size(); }
+
+int colour_of(const Ctx& c, const int* n, int64_t e) {
+  int idx[3];
+  element_index(n, c.d, e, idx);
+  int col = 0;
+  for (int k = 0; k < c.d; ++k) col |= (idx[k] & 1) << k;
+  return col;
+}
+
+// Pack the Stokes blocks of smoothing level l into the colour-major device
+// records of kernels.cu.
+void pack_level(Ctx& c, int l, cudaStream_t st) {
+  const HostLevel& H = c.host[l];
+  DevLevel& D = c.dev[l];
+  const Pattern& P = c.pat;
+  int s = c.s, nb = c.nb, ss = s * s;
+  int64_t ne = H.ne;
+  D.ne = (int)ne;
+  for (int k = 0; k < 3; ++k) D.n[k] = H.n[k];
+  int ncol = 1 << c.d;
+  D.ncolour = ncol;
+  std::vector<int> perm;
+  perm.reserve(ne);
+  D.cstart[0] = 0;
+  for (int col = 0; col < ncol; ++col) {
+    for (int64_t e = 0; e < ne; ++e)
+      if (colour_of(c, H.n, e) == col) perm.push_back((int)e);
+    D.cstart[col + 1] = (int)perm.size();
+  }
+  std::vector<int> nbr((size_t)ne * P.NO);
+  for (int64_t pos = 0; pos < ne; ++pos)
+    for (int o = 0; o < P.NO; ++o) nbr[(size_t)pos * P.NO + o] = H.nbr[(size_t)perm[pos] * P.NO + o];
+  D.perm = (int*)dalloc(c, ne * sizeof(int));
+  D.nbr = (int*)dalloc(c, nbr.size() * sizeof(int));
+  ck(cudaMemcpy(D.perm, perm.data(), ne * sizeof(int), cudaMemcpyHostToDevice), "copy perm");
+  ck(cudaMemcpy(D.nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice), "copy nbr");
+
+  // Inverses of the diagonal blocks (FP64, host).
+  std::vector<double> Dinv((size_t)ne * nb * nb);
+  std::string err;
+  int rc = invert_blocks(nb, (int)ne, H.D.data(), Dinv.data(), err);
+  if (rc != STK_OK) throw std::runtime_error(err);
+
+  size_t cpl_n = (size_t)ne * s * P.TRP, mat_n = (size_t)ne * nb * P.NBP;
+  std::vector<double> buf(std::max(cpl_n, mat_n));
+  // couplings: rec[c][tr], tr = t*s + i holds C[t][i][c]
+  std::fill(buf.begin(), buf.begin() + cpl_n, 0.0);
+  for (int64_t pos = 0; pos < ne; ++pos) {
+    int64_t e = perm[pos];
+    double* rec = &buf[(size_t)pos * s * P.TRP];
+    for (int t = 0; t < P.T; ++t)
+      for (int i = 0; i < s; ++i)
+        for (int j = 0; j < s; ++j)
+          rec[(size_t)j * P.TRP + t * s + i] = H.C[((size_t)e * P.T + t) * ss + i * s + j];
+  }
+  D.cpl[0] = dalloc(c, cpl_n * sizeof(double));
+  ck(cudaMemcpy(D.cpl[0], buf.data(), cpl_n * sizeof(double), cudaMemcpyHostToDevice), "copy cpl");
+  auto pack_mat = [&](const std::vector<double>& M, void*& out) {
+    std::fill(buf.begin(), buf.begin() + mat_n, 0.0);
+    for (int64_t pos = 0; pos < ne; ++pos) {
+      int64_t e = perm[pos];
+      double* rec = &buf[(size_t)pos * nb * P.NBP];
+      const double* m = &M[(size_t)e * nb * nb];
+      for (int r = 0; r < nb; ++r)
+        for (int cc = 0; cc < nb; ++cc) rec[(size_t)cc * P.NBP + r] = m[(size_t)r * nb + cc];
+    }
+    out = dalloc(c, mat_n * sizeof(double));
+    ck(cudaMemcpy(out, buf.data(), mat_n * sizeof(double), cudaMemcpyHostToDevice), "copy mat");
+  };
+  pack_mat(Dinv, D.inv[0]);
+  pack_mat(H.D, D.dia[0]);
+  // Low-precision copies (rounded once from FP64: round to nearest even).
+  if (c.precision != STK_FP64) {
+    int pr = c.precision;
+    size_t es = (pr == STK_FP32) ? 4 : 2;
+    void* src[3] = {D.cpl[0], D.inv[0], D.dia[0]};
+    size_t cnt[3] = {cpl_n, mat_n, mat_n};
+    void** dst[3] = {&D.cpl[pr], &D.inv[pr], &D.dia[pr]};
+    for (int i = 0; i < 3; ++i) {
+      *dst[i] = dalloc(c, cnt[i] * es);
+      if (pr == STK_FP32)
+        ck(launch_convert(0, 1, (int64_t)cnt[i], *dst[i], src[i], st), "convert fp32");
+      else
+        ck(launch_to_bf16((int64_t)cnt[i], *dst[i], (const double*)src[i], st), "convert bf16");
+    }
+  }
+  (void)st;
+}
+
+void alloc_vectors(Ctx& c) {
+  int L = nlevels(c);
+  for (int l = 0; l < L; ++l) {
+    DevLevel& D = c.dev[l];
+    int64_t n = level_ne(c, l) * c.nb;
+    D.ne = (int)level_ne(c, l);
+    for (int k = 0; k < 3; ++k) D.n[k] = c.host[l].n[k];
+    for (int v = 0; v < 2; ++v) {
+      if (v == 1 && c.precision == STK_FP64) continue;
+      size_t es = v == 0 ? 8 : 4;
+      D.vx[v] = dalloc(c, n * es);
+      D.vb[v] = dalloc(c, n * es);
+      D.vr[v] = dalloc(c, n * es);
+    }
+  }
+  int64_t n0 = level_ne(c, 0) * c.nb;
+  c.r64 = (double*)dalloc(c, n0 * 8);
+  c.c64 = (double*)dalloc(c, n0 * 8);
+  c.norm_buf = (double*)dalloc(c, 1040 * 8);
+  ck(cudaMallocHost(&c.norm_host, 8 * sizeof(double)), "cudaMallocHost");
+}
+
+// Bottom level: dense operator, eigen pseudo-inverse (host), to device.
+void setup_bottom(Ctx& c) {
+  const HostLevel& H = c.host.back();
+  const Pattern& P = c.pat;
+  int nb = c.nb, s = c.s, ss = s * s;
+  int64_t ne = H.ne, n = ne * nb;
+  std::vector<double> A((size_t)n * n, 0.0);
+  for (int64_t a = 0; a < ne; ++a) {
+    for (int r = 0; r < nb; ++r)
+      for (int cc = 0; cc < nb; ++cc)
+        A[(size_t)(a * nb + r) * n + a * nb + cc] += H.D[(size_t)a * nb * nb + r * nb + cc];
+    for (int t = 0; t < P.T; ++t) {
+      int64_t bb = H.nbr[(size_t)a * P.NO + P.task_o[t]];
+      if (bb < 0) continue;
+      int rv = P.task_rv[t], cv = P.task_cv[t];
+      for (int i = 0; i < s; ++i)
+        for (int j = 0; j < s; ++j)
+          A[(size_t)(a * nb + rv * s + i) * n + bb * nb + cv * s + j] +=
+              H.C[((size_t)a * P.T + t) * ss + i * s + j];
+    }
+  }
+  std::vector<double> pinv;
+  pseudo_inverse_jacobi((int)n, A, pinv, c.n_snapped, 1e-10);
+  c.nbot = n;
+  c.bottom_pinv = (double*)dalloc(c, (size_t)n * n * sizeof(double));
+  ck(cudaMemcpy(c.bottom_pinv, pinv.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice),
+     "copy bottom");
+}
+
+// ---- the V-cycle (Algorithm 1) ------------------------------------------------
+// prec: storage precision of the blocks; vectors FP64 when prec == 0, else FP32.
+void enqueue_smooth(Ctx& c, int prec, int l, int sweeps, void* x, const void* b, cudaStream_t st) {
+  DevLevel& D = c.dev[l];
+  for (int it = 0; it < sweeps; ++it)
+    for (int col = 0; col < D.ncolour; ++col) {
+      int n = D.cstart[col + 1] - D.cstart[col];
+      if (n <= 0) continue;
+      ck(launch_element(c.pat, prec, MODE_GS, D.cstart[col], n, D.perm, D.nbr, D.cpl[prec], D.inv[prec],
+                        b, x, nullptr, st),
+         "gs colour launch");
+      c.launches++;
+    }
+}
+
+void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t st) {
+  int vi = prec == STK_FP64 ? 0 : 1;
+  int L = nlevels(c);
+  if (l == L - 1) {
+    ck(launch_bottom(vi == 0, c.nbot, c.bottom_pinv, b, x, st), "bottom launch");
+    c.launches++;
+    return;
+  }
+  DevLevel& D = c.dev[l];
+  DevLevel& Dc = c.dev[l + 1];
+  enqueue_smooth(c, prec, l, c.nu1, x, b, st);
+  ck(launch_element(c.pat, prec, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[prec], D.dia[prec], b, x,
+                    D.vr[vi], st),
+     "residual launch");
+  ck(launch_restrict(vi == 0, c.d, c.s, c.nb, Dc.n, D.n, Dc.ne, c.child_mats, D.vr[vi], Dc.vb[vi], st),
+     "restrict launch");
+  ck(cudaMemsetAsync(Dc.vx[vi], 0, (size_t)Dc.ne * c.nb * (vi == 0 ? 8 : 4), st), "memset");
+  c.launches += 2;  // residual + restriction
+  enqueue_cycle(c, prec, l + 1, Dc.vx[vi], Dc.vb[vi], st);
+  ck(launch_prolong(vi == 0, c.d, c.s, c.nb, D.n, Dc.n, D.ne, c.child_mats, Dc.vx[vi], x, st),
+     "prolong launch");
+  c.launches++;
+  enqueue_smooth(c, prec, l, c.nu2, x, b, st);
+}
+
+void enqueue_residual64(Ctx& c, const double* x, const double* b, double* r, cudaStream_t st) {
+  DevLevel& D = c.dev[0];
+  ck(launch_element(c.pat, STK_FP64, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[0], D.dia[0], b,
+                    (void*)x, r, st),
+     "residual64 launch");
+  c.launches++;
+}
+
+void enqueue_norm(Ctx& c, const double* v, cudaStream_t st) {
+  ck(launch_sumsq(level_ne(c, 0) * c.nb, v, c.norm_buf + 16, c.norm_buf, st), "norm launch");
+  c.launches += 2;
+  ck(cudaMemcpyAsync(c.norm_host, c.norm_buf, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
+}
+
+// One outer iteration after the residual r64 of the current x is known:
+// c = V(0, r), x += c, r64 = b - A x, ||r64||^2 -> host.
+void enqueue_iteration(Ctx& c, double* x, const double* b, cudaStream_t st) {
+  int prec = c.precision;
+  int64_t n0 = level_ne(c, 0) * c.nb;
+  DevLevel& D0 = c.dev[0];
+  if (prec == STK_FP64) {
+    ck(cudaMemsetAsync(c.c64, 0, n0 * 8, st), "memset");
+    enqueue_cycle(c, prec, 0, c.c64, c.r64, st);
+    ck(launch_axpy(1, 1, n0, x, c.c64, st), "axpy");
+  } else {
+    ck(launch_convert(0, 1, n0, D0.vb[1], c.r64, st), "convert");
+    ck(cudaMemsetAsync(D0.vx[1], 0, n0 * 4, st), "memset");
+    enqueue_cycle(c, prec, 0, D0.vx[1], D0.vb[1], st);
+    ck(launch_axpy(1, 0, n0, x, D0.vx[1], st), "axpy");
+    c.launches++;
+  }
+  c.launches++;
+  enqueue_residual64(c, x, b, c.r64, st);
+  enqueue_norm(c, c.r64, st);
+}
+
+bool valid_bc(const int* bc, int d) {
+  for (int k = 0; k < d; ++k) {
+    for (int sd = 0; sd < 2; ++sd)
+      if (bc[2 * k + sd] < 0 || bc[2 * k + sd] > 2) return false;
+    if ((bc[2 * k] == STK_BC_PERIODIC) != (bc[2 * k + 1] == STK_BC_PERIODIC)) return false;
+  }
+  return true;
+}
+
+int64_t count_points(const Ctx& c, int kind) {
+  std::vector<double> xyz;
+  face_points(c, kind, xyz, nullptr);
+  return (int64_t)(xyz.size() / c.d);
+}
+
+}  // namespace
+
+extern "C" {
+
+int stk_create(stk_ctx** out, int device) {
+  if (!out) return STK_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return STK_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return STK_ERR_CUDA;
+  stk_ctx* c = new (std::nothrow) stk_ctx();
+  if (!c) return STK_ERR_OOM;
+  c->device = device;
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return STK_ERR_CUDA;
+  }
+  *out = c;
+  return STK_OK;
+}
+
+int stk_destroy(stk_ctx* c) {
+  if (!c) return STK_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  free_device(*c);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return STK_OK;
+}
+
+const char* stk_last_error(stk_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int stk_set_mesh(stk_ctx* c, int d, const int* n, const double* lo, const double* hi, const int* bc) {
+  return guard(c, [&]() -> int {
+    if (d < 2 || d > 3 || !n || !lo || !hi || !bc) return fail(c, STK_ERR_INVALID_ARG, "bad mesh arguments");
+    for (int k = 0; k < d; ++k) {
+      if (n[k] < 1 || !(hi[k] > lo[k])) return fail(c, STK_ERR_INVALID_ARG, "bad mesh extent");
+    }
+    if (!valid_bc(bc, d)) return fail(c, STK_ERR_INVALID_ARG, "bad boundary types");
+    free_device(*c);
+    c->host.clear();
+    c->d = d;
+    for (int k = 0; k < 3; ++k) {
+      c->n[k] = k < d ? n[k] : 1;
+      c->lo[k] = k < d ? lo[k] : 0.0;
+      c->hi[k] = k < d ? hi[k] : 1.0;
+    }
+    for (int i = 0; i < 6; ++i) c->bc[i] = i < 2 * d ? bc[i] : 0;
+    c->mu_vol.clear();
+    return STK_OK;
+  });
+}
+
+int stk_set_discretisation(stk_ctx* c, int p, int gamma) {
+  return guard(c, [&]() -> int {
+    if (c->d == 0) return fail(c, STK_ERR_INVALID_ARG, "set the mesh first");
+    if (p < 1 || (gamma != 0 && gamma != 1)) return fail(c, STK_ERR_INVALID_ARG, "bad degree or form");
+    int s = 1;
+    for (int k = 0; k < c->d; ++k) s *= (p + 1);
+    if (!(s == 4 || s == 8 || s == 9 || s == 16 || s == 25 || s == 27))
+      return fail(c, STK_ERR_INVALID_ARG, "unsupported (d, p): supported 2D p=1..4, 3D p=1..2");
+    free_device(*c);
+    c->p = p;
+    c->gamma = gamma;
+    c->s = s;
+    c->nb = (c->d + 1) * s;
+    c->q = 2 * p + 2;
+    if (c->tau0 < 0) c->tau0 = 0.5 * p;
+    build_pattern(c->d, p, gamma, c->pat);
+    c->mu_vol.clear();
+    return STK_OK;
+  });
+}
+
+int stk_set_penalty(stk_ctx* c, double tau, double tau0, double c_bdry, double c_intra) {
+  return guard(c, [&]() -> int {
+    if (!(tau > 0) || !(tau0 > 0) || !(c_bdry >= 0) || !(c_intra >= 0))
+      return fail(c, STK_ERR_INVALID_ARG, "penalties must be positive");
+    c->tau = tau;
+    c->tau0 = tau0;
+    c->c_bdry = c_bdry;
+    c->c_intra = c_intra;
+    return STK_OK;
+  });
+}
+
+int stk_num_points(stk_ctx* c, int kind, int64_t* count) {
+  return guard(c, [&]() -> int {
+    if (c->p < 0 || !count || kind < 0 || kind > 2) return fail(c, STK_ERR_INVALID_ARG, "bad call");
+    *count = count_points(*c, kind);
+    return STK_OK;
+  });
+}
+
+int stk_get_points(stk_ctx* c, int kind, double* xyz, double* normals) {
+  return guard(c, [&]() -> int {
+    if (c->p < 0 || !xyz || kind < 0 || kind > 2) return fail(c, STK_ERR_INVALID_ARG, "bad call");
+    std::vector<double> pts, nrm;
+    face_points(*c, kind, pts, normals ? &nrm : nullptr);
+    std::copy(pts.begin(), pts.end(), xyz);
+    if (normals) std::copy(nrm.begin(), nrm.end(), normals);
+    return STK_OK;
+  });
+}
+
+static bool positive_finite(const double* v, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!(v[i] > 0) || !std::isfinite(v[i])) return false;
+  return true;
+}
+
+int stk_set_viscosity(stk_ctx* c, const double* mu_vol, const double* mu_iface, const double* mu_bface) {
+  return guard(c, [&]() -> int {
+    if (c->p < 0) return fail(c, STK_ERR_INVALID_ARG, "set the discretisation first");
+    int64_t nv = count_points(*c, 0), ni = count_points(*c, 1), nbf = count_points(*c, 2);
+    if (!mu_vol || (ni && !mu_iface) || (nbf && !mu_bface)) return fail(c, STK_ERR_INVALID_ARG, "null mu");
+    if (!positive_finite(mu_vol, nv) || (ni && !positive_finite(mu_iface, ni)) ||
+        (nbf && !positive_finite(mu_bface, nbf)))
+      return fail(c, STK_ERR_INVALID_ARG, "mu must be finite and positive");
+    free_device(*c);
+    c->mu_vol.assign(mu_vol, mu_vol + nv);
+    c->mu_if.assign(mu_iface, mu_iface + ni);
+    c->mu_bf.assign(mu_bface, mu_bface + nbf);
+    return STK_OK;
+  });
+}
+
+int stk_set_density(stk_ctx* c, const double* rho_vol, const double* rho_iface, double delta) {
+  return guard(c, [&]() -> int {
+    if (c->p < 0) return fail(c, STK_ERR_INVALID_ARG, "set the discretisation first");
+    free_device(*c);
+    if (delta == 0.0) {
+      c->delta = 0.0;
+      c->rho_vol.clear();
+      c->rho_if.clear();
+      return STK_OK;
+    }
+    if (!(delta > 0) || !rho_vol) return fail(c, STK_ERR_INVALID_ARG, "bad density arguments");
+    int64_t nv = count_points(*c, 0), ni = count_points(*c, 1);
+    if (ni && !rho_iface) return fail(c, STK_ERR_INVALID_ARG, "null rho_iface");
+    if (!positive_finite(rho_vol, nv) || (ni && !positive_finite(rho_iface, ni)))
+      return fail(c, STK_ERR_INVALID_ARG, "rho must be finite and positive");
+    c->delta = delta;
+    c->rho_vol.assign(rho_vol, rho_vol + nv);
+    c->rho_if.assign(rho_iface, rho_iface + ni);
+    return STK_OK;
+  });
+}
+
+int stk_set_cycle(stk_ctx* c, int nu1, int nu2, int precision) {
+  return guard(c, [&]() -> int {
+    if (nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0 || precision < 0 || precision > 2)
+      return fail(c, STK_ERR_INVALID_ARG, "bad cycle options");
+    if (c->ready && precision != c->precision) free_device(*c);
+    c->nu1 = nu1;
+    c->nu2 = nu2;
+    c->precision = precision;
+    return STK_OK;
+  });
+}
+
+int stk_setup(stk_ctx* c, void* stream) {
+  return guard(c, [&]() -> int {
+    if (c->p < 0) return fail(c, STK_ERR_INVALID_ARG, "set mesh and discretisation first");
+    if (c->mu_vol.empty()) return fail(c, STK_ERR_INVALID_ARG, "set the viscosity first");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    free_device(*c);
+    int rc = setup_host(*c);
+    if (rc != STK_OK) return rc;
+    int L = nlevels(*c);
+    if (L < 2) return fail(c, STK_ERR_INVALID_ARG, "mesh too small for a hierarchy (need n >= 4 even)");
+    c->dev.assign(L, DevLevel());
+    cudaStream_t st = (cudaStream_t)stream;
+    try {
+      for (int l = 0; l < L - 1; ++l) pack_level(*c, l, st);
+    } catch (const std::runtime_error& e) {
+      free_device(*c);
+      return fail(c, STK_ERR_SINGULAR_BLOCK, e.what());
+    }
+    alloc_vectors(*c);
+    setup_bottom(*c);
+    std::vector<double> P;
+    child_matrices(c->d, c->p, P);
+    c->child_mats = (double*)dalloc(*c, P.size() * sizeof(double));
+    ck(cudaMemcpy(c->child_mats, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice), "copy P");
+    ck(cudaStreamSynchronize(st), "setup sync");
+    ck(cudaDeviceSynchronize(), "setup sync");
+    c->ready = true;
+    return STK_OK;
+  });
+}
+
+int stk_get_sizes(stk_ctx* c, int* nl, int64_t* ne, int* nb, int* snapped) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (nl) *nl = nlevels(*c);
+    if (ne)
+      for (int l = 0; l < nlevels(*c); ++l) ne[l] = level_ne(*c, l);
+    if (nb) *nb = c->nb;
+    if (snapped) *snapped = c->n_snapped;
+    return STK_OK;
+  });
+}
+
+int stk_get_block(stk_ctx* c, int level, int64_t i, int64_t j, double* out) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (level < 0 || level >= nlevels(*c) || !out) return fail(c, STK_ERR_INVALID_ARG, "bad level");
+    const HostLevel& H = c->host[level];
+    if (i < 0 || j < 0 || i >= H.ne || j >= H.ne) return fail(c, STK_ERR_INVALID_ARG, "bad element");
+    int nb = c->nb, s = c->s, ss = s * s;
+    std::fill(out, out + (size_t)nb * nb, 0.0);
+    if (i == j) std::copy(&H.D[(size_t)i * nb * nb], &H.D[(size_t)(i + 1) * nb * nb], out);
+    for (int t = 0; t < c->pat.T; ++t) {
+      if (H.nbr[(size_t)i * c->pat.NO + c->pat.task_o[t]] != j) continue;
+      int rv = c->pat.task_rv[t], cv = c->pat.task_cv[t];
+      for (int a = 0; a < s; ++a)
+        for (int b = 0; b < s; ++b)
+          out[(size_t)(rv * s + a) * nb + cv * s + b] += H.C[((size_t)i * c->pat.T + t) * ss + a * s + b];
+    }
+    return STK_OK;
+  });
+}
+
+int stk_assemble_rhs(stk_ctx* c, const double* f_vol, const double* bdata, double* b) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (!f_vol || !b) return fail(c, STK_ERR_INVALID_ARG, "null argument");
+    if (count_points(*c, 2) > 0 && !bdata) return fail(c, STK_ERR_INVALID_ARG, "null boundary data");
+    return assemble_rhs_host(*c, f_vol, bdata, b);
+  });
+}
+
+int stk_residual(stk_ctx* c, const double* x, const double* b, double* r, double* norm_out, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (!x || !b || !r) return fail(c, STK_ERR_INVALID_ARG, "null vector");
+    cudaStream_t st = (cudaStream_t)stream;
+    enqueue_residual64(*c, x, b, r, st);
+    if (norm_out) {
+      enqueue_norm(*c, r, st);
+      ck(cudaStreamSynchronize(st), "sync");
+      *norm_out = std::sqrt(c->norm_host[0]);
+    }
+    return STK_OK;
+  });
+}
+
+int stk_gs_colour(stk_ctx* c, int level, int colour, double* x, const double* b, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (level < 0 || level >= nlevels(*c) - 1) return fail(c, STK_ERR_INVALID_ARG, "bad level");
+    if (colour < 0 || colour >= (1 << c->d) || !x || !b) return fail(c, STK_ERR_INVALID_ARG, "bad colour");
+    DevLevel& D = c->dev[level];
+    int n = D.cstart[colour + 1] - D.cstart[colour];
+    ck(launch_element(c->pat, STK_FP64, MODE_GS, D.cstart[colour], n, D.perm, D.nbr, D.cpl[0], D.inv[0], b,
+                      x, nullptr, (cudaStream_t)stream),
+       "gs colour launch");
+    c->launches++;
+    return STK_OK;
+  });
+}
+
+int stk_vcycle(stk_ctx* c, double* x, const double* b, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (!x || !b) return fail(c, STK_ERR_INVALID_ARG, "null vector");
+    enqueue_cycle(*c, STK_FP64, 0, x, b, (cudaStream_t)stream);
+    return STK_OK;
+  });
+}
+
+int stk_restrict(stk_ctx* c, int level, const double* r, double* rc, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (level < 0 || level >= nlevels(*c) - 1 || !r || !rc) return fail(c, STK_ERR_INVALID_ARG, "bad args");
+    DevLevel& D = c->dev[level];
+    DevLevel& Dc = c->dev[level + 1];
+    ck(launch_restrict(1, c->d, c->s, c->nb, Dc.n, D.n, Dc.ne, c->child_mats, r, rc, (cudaStream_t)stream),
+       "restrict");
+    c->launches++;
+    return STK_OK;
+  });
+}
+
+int stk_prolong(stk_ctx* c, int level, const double* xc, double* x, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (level < 0 || level >= nlevels(*c) - 1 || !xc || !x) return fail(c, STK_ERR_INVALID_ARG, "bad args");
+    DevLevel& D = c->dev[level];
+    DevLevel& Dc = c->dev[level + 1];
+    ck(launch_prolong(1, c->d, c->s, c->nb, D.n, Dc.n, D.ne, c->child_mats, xc, x, (cudaStream_t)stream),
+       "prolong");
+    c->launches++;
+    return STK_OK;
+  });
+}
+
+int stk_bottom_solve(stk_ctx* c, const double* b, double* x, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (!b || !x) return fail(c, STK_ERR_INVALID_ARG, "null vector");
+    ck(launch_bottom(1, c->nbot, c->bottom_pinv, b, x, (cudaStream_t)stream), "bottom");
+    c->launches++;
+    return STK_OK;
+  });
+}
+
+int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, int* iters_out, double* hist,
+              void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (!x || !b || maxit < 0 || !(rtol > 0)) return fail(c, STK_ERR_INVALID_ARG, "bad solve arguments");
+    cudaStream_t user = (cudaStream_t)stream;
+    ck(cudaStreamSynchronize(user), "sync caller stream");
+    cudaStream_t st = c->stream;
+    // ||b||
+    enqueue_norm(*c, b, st);
+    ck(cudaStreamSynchronize(st), "sync");
+    double bnorm = std::sqrt(c->norm_host[0]);
+    if (bnorm == 0.0) bnorm = 1.0;
+    enqueue_residual64(*c, x, b, c->r64, st);
+    enqueue_norm(*c, c->r64, st);
+    ck(cudaStreamSynchronize(st), "sync");
+    double rel = std::sqrt(c->norm_host[0]) / bnorm, rel0 = rel;
+    if (hist) hist[0] = rel;
+    int it = 0;
+    // Capture one outer iteration as a CUDA graph (re-captured when the
+    // caller's vectors or the precision change).
+    if (!c->graph || c->graph_x != x || c->graph_b != b || c->graph_prec != c->precision) {
+      if (c->graph) cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+      cudaGraph_t g;
+      int64_t before = c->launches;
+      ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+      try {
+        enqueue_iteration(*c, x, b, st);
+      } catch (...) {
+        cudaStreamEndCapture(st, &g);
+        throw;
+      }
+      ck(cudaStreamEndCapture(st, &g), "end capture");
+      ck(cudaGraphInstantiate(&c->graph, g, 0), "graph instantiate");
+      cudaGraphDestroy(g);
+      c->graph_kernels = c->launches - before;
+      c->launches = before;
+      c->graph_x = x;
+      c->graph_b = b;
+      c->graph_prec = c->precision;
+    }
+    while (rel > rtol && it < maxit) {
+      ck(cudaGraphLaunch(c->graph, st), "graph launch");
+      c->launches += c->graph_kernels;
+      ck(cudaStreamSynchronize(st), "sync");
+      rel = std::sqrt(c->norm_host[0]) / bnorm;
+      ++it;
+      if (hist) hist[it] = rel;
+      if (!std::isfinite(rel) || rel > 1e6 * rel0) {
+        if (iters_out) *iters_out = it;
+        return fail(c, STK_ERR_DIVERGED, "outer iteration diverged");
+      }
+    }
+    if (iters_out) *iters_out = it;
+    return STK_OK;
+  });
+}
+
+int stk_launch_count(stk_ctx* c, int64_t* count) {
+  if (!c || !count) return STK_ERR_INVALID_ARG;
+  *count = c->launches;
+  return STK_OK;
+}
+
+}  // extern "C"

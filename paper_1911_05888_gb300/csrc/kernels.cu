@@ -1,0 +1,409 @@
+// Hot-path CUDA kernels of the Stokes multigrid V-cycle for sm_103a.
+//
+// element_kernel: one colour step of the block Gauss-Seidel smoother
+//   x_i = A_ii^{-1} (b_i - sum_{j != i} A_ij x_j)            (Section 3)
+// or the residual r_i = b_i - sum_{j != i} A_ij x_j - A_ii x_i (Algorithm 1,
+// line 5), over a contiguous range of element "positions" (elements stored
+// colour-major so that one colour is one contiguous stream of records).
+//
+// Per element the kernel streams two records from HBM with 16-byte
+// coalesced, read-once (evict-first) loads:
+//   cpl: the nonzero s x s coupling sub-blocks ("tasks"), stored column-
+//        interleaved [column c][task-row], so that consecutive threads read
+//        consecutive task-rows of one column;
+//   mat: A_ii^{-1} (smoother) or A_ii (residual), column-major [c][row].
+// Neighbour values are gathered once per element into shared memory; the
+// per-task partial sums are reduced per row in shared memory.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "stk_internal.h"
+
+namespace stk {
+
+constexpr int kNT = 128;   // threads per CTA of element_kernel
+
+template <typename TS> struct StorageTraits;
+template <> struct StorageTraits<double> {
+  using Acc = double;
+  static constexpr int V = 2;
+  __device__ static inline void load(const double* p, double* w) {
+    double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+    w[0] = v.x;
+    w[1] = v.y;
+  }
+};
+template <> struct StorageTraits<float> {
+  using Acc = float;
+  static constexpr int V = 4;
+  __device__ static inline void load(const float* p, float* w) {
+    float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = v.z;
+    w[3] = v.w;
+  }
+};
+template <> struct StorageTraits<__nv_bfloat16> {
+  using Acc = float;
+  static constexpr int V = 8;
+  __device__ static inline void load(const __nv_bfloat16* p, float* w) {
+    uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+    uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      w[2 * i] = __uint_as_float(u[i] << 16);
+      w[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+    }
+  }
+};
+
+enum { MODE_GS = 0, MODE_RESID = 1 };
+
+template <typename TS, typename TX, int S>
+__global__ void __launch_bounds__(kNT) element_kernel(const __grid_constant__ Pattern pat, int mode,
+                                                      int pos0, int npos,
+                                                      const int* __restrict__ perm,
+                                                      const int* __restrict__ nbr,
+                                                      const TS* __restrict__ cpl,
+                                                      const TS* __restrict__ mat,
+                                                      const TX* __restrict__ b, TX* x, TX* rout) {
+  using Tr = StorageTraits<TS>;
+  using TA = typename Tr::Acc;
+  constexpr int V = Tr::V;
+  const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
+  const int NRV = NBP / V;
+  const int NCG = (kNT / NRV) > 0 ? (kNT / NRV) : 1;
+  const int CW = (nb + NCG - 1) / NCG;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TA* Xs = reinterpret_cast<TA*>(smem_raw);
+  TA* part = Xs + pat.NG * S;
+  TA* g = part + TRP;
+  TA* xi = g + NBP;
+  TA* part2 = xi + NBP;
+
+  const int tid = threadIdx.x;
+  for (int pos = pos0 + blockIdx.x; pos < pos0 + npos; pos += gridDim.x) {
+    const int e = perm[pos];
+    const int* nbe = nbr + (size_t)pos * pat.NO;
+    // Gather the neighbour values each task multiplies.
+    for (int i = tid; i < pat.NG * S; i += kNT) {
+      const int gi = i / S, ci = i - gi * S;
+      const int j = nbe[pat.g_o[gi]];
+      Xs[i] = (j >= 0) ? (TA)x[(size_t)j * nb + pat.g_cv[gi] * S + ci] : (TA)0;
+    }
+    if (mode == MODE_RESID)
+      for (int i = tid; i < nb; i += kNT) xi[i] = (TA)x[(size_t)e * nb + i];
+    __syncthreads();
+    // Coupling sub-blocks: V consecutive task-rows per thread.
+    const TS* rec = cpl + (size_t)pos * S * TRP;
+    for (int tv = tid; tv < TRP / V; tv += kNT) {
+      const int tr0 = tv * V;
+      const TA* xp[V];
+      TA acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int tr = tr0 + j;
+        xp[j] = (tr < TR) ? Xs + pat.task_g[tr / S] * S : Xs;
+        acc[j] = 0;
+      }
+#pragma unroll 4
+      for (int ci = 0; ci < S; ++ci) {
+        TA w[V];
+        Tr::load(rec + (size_t)ci * TRP + tr0, w);
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = fma(w[j], xp[j][ci], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) part[tr0 + j] = acc[j];
+    }
+    __syncthreads();
+    // g = b - sum_{j != i} A_ij x_j, row by row over the row variable's tasks.
+    for (int r = tid; r < nb; r += kNT) {
+      const int rv = r / S, rr = r - rv * S;
+      TA sum = 0;
+      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[t * S + rr];
+      g[r] = (TA)b[(size_t)e * nb + r] - sum;
+    }
+    __syncthreads();
+    // Dense nb x nb block: A_ii^{-1} g (smoother) or A_ii x_i (residual).
+    const TS* mrec = mat + (size_t)pos * nb * NBP;
+    const TA* vin = (mode == MODE_GS) ? g : xi;
+    for (int u = tid; u < NRV * NCG; u += kNT) {
+      const int rvv = u % NRV, cg = u / NRV;
+      const int c0 = cg * CW, c1 = min(nb, c0 + CW);
+      TA acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) acc[j] = 0;
+      for (int ci = c0; ci < c1; ++ci) {
+        TA w[V];
+        Tr::load(mrec + (size_t)ci * NBP + rvv * V, w);
+        const TA v = vin[ci];
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = fma(w[j], v, acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) part2[cg * NBP + rvv * V + j] = acc[j];
+    }
+    __syncthreads();
+    for (int r = tid; r < nb; r += kNT) {
+      TA sum = 0;
+      for (int cg = 0; cg < NCG; ++cg) sum += part2[cg * NBP + r];
+      if (mode == MODE_GS)
+        x[(size_t)e * nb + r] = (TX)sum;
+      else
+        rout[(size_t)e * nb + r] = (TX)(g[r] - sum);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TS>
+static size_t element_smem(const Pattern& pat) {
+  using TA = typename StorageTraits<TS>::Acc;
+  constexpr int V = StorageTraits<TS>::V;
+  int NRV = pat.NBP / V;
+  int NCG = (kNT / NRV) > 0 ? (kNT / NRV) : 1;
+  size_t n = (size_t)pat.NG * pat.s + pat.TRP + 2 * pat.NBP + (size_t)NCG * pat.NBP;
+  return n * sizeof(TA);
+}
+
+// ---- restriction / prolongation (injection and its transpose) ---------------
+// child_mats[ch][a][b]: fine coefficient a of coarse mode b for child ch.
+template <typename TX>
+__global__ void restrict_kernel(int d, int s, int nb, int nc0, int nc1, int nc2, int nf0, int nf1,
+                                int64_t nec, const double* __restrict__ P,
+                                const TX* __restrict__ r, TX* __restrict__ rc) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nec * nb) return;
+  const int64_t C = idx / nb;
+  const int vb = (int)(idx - C * nb);
+  const int v = vb / s, bm = vb - v * s;
+  int I[3] = {(int)(C % nc0), (int)((C / nc0) % nc1), (int)(C / ((int64_t)nc0 * nc1))};
+  double acc = 0.0;
+  for (int ch = 0; ch < (1 << d); ++ch) {
+    int f0 = 2 * I[0] + (ch & 1), f1 = 2 * I[1] + ((ch >> 1) & 1), f2 = 2 * I[2] + ((ch >> 2) & 1);
+    int64_t f = f0 + (int64_t)nf0 * (f1 + (int64_t)nf1 * f2);
+    if (d == 2) f = f0 + (int64_t)nf0 * f1;
+    const double* Pc = P + (size_t)ch * s * s;
+    const TX* rf = r + (size_t)f * nb + v * s;
+    for (int a = 0; a < s; ++a) acc += Pc[a * s + bm] * (double)rf[a];
+  }
+  rc[(size_t)C * nb + vb] = (TX)acc;
+  (void)nc2;
+}
+
+template <typename TX>
+__global__ void prolong_kernel(int d, int s, int nb, int nf0, int nf1, int nc0, int nc1,
+                               int64_t nef, const double* __restrict__ P,
+                               const TX* __restrict__ xc, TX* __restrict__ x) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nef * nb) return;
+  const int64_t f = idx / nb;
+  const int va = (int)(idx - f * nb);
+  const int v = va / s, am = va - v * s;
+  int fi0 = (int)(f % nf0), fi1 = (int)((f / nf0) % nf1), fi2 = (int)(f / ((int64_t)nf0 * nf1));
+  int ch = (fi0 & 1) | ((fi1 & 1) << 1) | ((d == 3 ? (fi2 & 1) : 0) << 2);
+  int64_t C = (fi0 >> 1) + (int64_t)nc0 * ((fi1 >> 1) + (int64_t)nc1 * (d == 3 ? (fi2 >> 1) : 0));
+  const double* Pc = P + (size_t)ch * s * s + (size_t)am * s;
+  const TX* xcc = xc + (size_t)C * nb + v * s;
+  double acc = 0.0;
+  for (int bm = 0; bm < s; ++bm) acc += Pc[bm] * (double)xcc[bm];
+  x[(size_t)f * nb + va] = (TX)((double)x[(size_t)f * nb + va] + acc);
+}
+
+// ---- bottom solve: x = A_c^+ b (FP64, one warp per row) ---------------------
+template <typename TX>
+__global__ void bottom_kernel(int64_t n, const double* __restrict__ pinv, const TX* __restrict__ b,
+                              TX* __restrict__ x) {
+  int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double acc = 0.0;
+  for (int64_t j = lane; j < n; j += 32) acc += pinv[row * n + j] * (double)b[j];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[row] = (TX)acc;
+}
+
+// ---- vector kernels ------------------------------------------------------------
+template <typename TA, typename TB>
+__global__ void axpy_kernel(int64_t n, TA* __restrict__ y, const TB* __restrict__ x) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (TA)((double)y[i] + (double)x[i]);
+}
+
+template <typename TA, typename TB>
+__global__ void convert_kernel(int64_t n, TA* __restrict__ y, const TB* __restrict__ x) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (TA)x[i];
+}
+
+__global__ void to_bf16_kernel(int64_t n, __nv_bfloat16* __restrict__ y, const double* __restrict__ x) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __float2bfloat16_rn((float)x[i]);
+}
+
+__global__ void sumsq_partial_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += x[i] * x[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void sum_final_kernel(int n, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static int g_num_sms = 0;
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  return g_num_sms;
+}
+
+template <typename TS, typename TX, int S>
+static cudaError_t launch_element_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
+                                    const int* nbr, const void* cpl, const void* mat, const void* b,
+                                    void* x, void* r, cudaStream_t st) {
+  if (npos <= 0) return cudaSuccess;
+  size_t smem = element_smem<TS>(pat);
+  if (smem > 48 * 1024) return cudaErrorInvalidValue;
+  auto kern = element_kernel<TS, TX, S>;
+  int per_sm = 16;
+  int grid = std::min(npos, num_sms() * per_sm);
+  kern<<<grid, kNT, smem, st>>>(pat, mode, pos0, npos, perm, nbr, (const TS*)cpl, (const TS*)mat,
+                                (const TX*)b, (TX*)x, (TX*)r);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TX>
+static cudaError_t launch_element_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
+                                    const int* nbr, const void* cpl, const void* mat, const void* b,
+                                    void* x, void* r, cudaStream_t st) {
+  switch (pat.s) {
+    case 4: return launch_element_s<TS, TX, 4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 8: return launch_element_s<TS, TX, 8>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 9: return launch_element_s<TS, TX, 9>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 16: return launch_element_s<TS, TX, 16>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 25: return launch_element_s<TS, TX, 25>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 27: return launch_element_s<TS, TX, 27>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// storage: 0 fp64, 1 fp32, 2 bf16; vectors are double for storage 0 and
+// float otherwise unless x64 is set (FP64 vectors with FP64 storage only).
+cudaError_t launch_element(const Pattern& pat, int storage, int mode, int pos0, int npos,
+                           const int* perm, const int* nbr, const void* cpl, const void* mat,
+                           const void* b, void* x, void* r, cudaStream_t st) {
+  switch (storage) {
+    case 0: return launch_element_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 1: return launch_element_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 2: return launch_element_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_restrict(int vec64, int d, int s, int nb, const int* nc, const int* nf, int64_t nec,
+                            const double* P, const void* r, void* rc, cudaStream_t st) {
+  int64_t n = nec * nb;
+  int bs = 256;
+  int64_t grid = (n + bs - 1) / bs;
+  if (vec64)
+    restrict_kernel<double><<<grid, bs, 0, st>>>(d, s, nb, nc[0], nc[1], nc[2], nf[0], nf[1], nec, P,
+                                                 (const double*)r, (double*)rc);
+  else
+    restrict_kernel<float><<<grid, bs, 0, st>>>(d, s, nb, nc[0], nc[1], nc[2], nf[0], nf[1], nec, P,
+                                                (const float*)r, (float*)rc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(int vec64, int d, int s, int nb, const int* nf, const int* nc, int64_t nef,
+                           const double* P, const void* xc, void* x, cudaStream_t st) {
+  int64_t n = nef * nb;
+  int bs = 256;
+  int64_t grid = (n + bs - 1) / bs;
+  if (vec64)
+    prolong_kernel<double><<<grid, bs, 0, st>>>(d, s, nb, nf[0], nf[1], nc[0], nc[1], nef, P,
+                                                (const double*)xc, (double*)x);
+  else
+    prolong_kernel<float><<<grid, bs, 0, st>>>(d, s, nb, nf[0], nf[1], nc[0], nc[1], nef, P,
+                                               (const float*)xc, (float*)x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bottom(int vec64, int64_t n, const double* pinv, const void* b, void* x,
+                          cudaStream_t st) {
+  int bs = 256;
+  int64_t grid = (n * 32 + bs - 1) / bs;
+  if (vec64)
+    bottom_kernel<double><<<grid, bs, 0, st>>>(n, pinv, (const double*)b, (double*)x);
+  else
+    bottom_kernel<float><<<grid, bs, 0, st>>>(n, pinv, (const float*)b, (float*)x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st) {
+  int bs = 256;
+  int64_t grid = (n + bs - 1) / bs;
+  if (y64 && x64) axpy_kernel<double, double><<<grid, bs, 0, st>>>(n, (double*)y, (const double*)x);
+  else if (y64) axpy_kernel<double, float><<<grid, bs, 0, st>>>(n, (double*)y, (const float*)x);
+  else if (x64) axpy_kernel<float, double><<<grid, bs, 0, st>>>(n, (float*)y, (const double*)x);
+  else axpy_kernel<float, float><<<grid, bs, 0, st>>>(n, (float*)y, (const float*)x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st) {
+  int bs = 256;
+  int64_t grid = (n + bs - 1) / bs;
+  if (y64 && x64) convert_kernel<double, double><<<grid, bs, 0, st>>>(n, (double*)y, (const double*)x);
+  else if (y64) convert_kernel<double, float><<<grid, bs, 0, st>>>(n, (double*)y, (const float*)x);
+  else if (x64) convert_kernel<float, double><<<grid, bs, 0, st>>>(n, (float*)y, (const double*)x);
+  else convert_kernel<float, float><<<grid, bs, 0, st>>>(n, (float*)y, (const float*)x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(int64_t n, void* y, const double* x, cudaStream_t st) {
+  int bs = 256;
+  int64_t grid = (n + bs - 1) / bs;
+  to_bf16_kernel<<<grid, bs, 0, st>>>(n, (__nv_bfloat16*)y, x);
+  return cudaGetLastError();
+}
+
+// ||x||_2^2 into out[0] (device); part holds 1024 partials.
+cudaError_t launch_sumsq(int64_t n, const double* x, double* part, double* out, cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  int grid = (int)std::min<int64_t>(blocks, 1024);
+  if (grid < 1) grid = 1;
+  sumsq_partial_kernel<<<grid, 256, 0, st>>>(n, x, part);
+  sum_final_kernel<<<1, 256, 0, st>>>(grid, part, out);
+  return cudaGetLastError();
+}
+
+}  // namespace stk

@@ -1,0 +1,120 @@
+// Internal data structures of the Stokes multigrid library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace stk {
+
+constexpr int kMaxTasks = 64;
+constexpr int kMaxGather = 64;
+constexpr int kMaxOffsets = 32;
+
+// Coupling pattern of one element with its neighbours (identical on every
+// level for given d and gamma).  A "task" is one s x s sub-block of the
+// operator: row variable rv, column variable cv, neighbour offset slot.
+struct Pattern {
+  int d, s, nb;
+  int T;       // number of coupling tasks (offset != 0)
+  int TR;      // T * s task-rows
+  int TRP;     // TR padded to a multiple of 8
+  int NBP;     // nb padded to a multiple of 8
+  int NO;      // number of distinct neighbour offsets
+  int NG;      // number of distinct (offset, column variable) gathers
+  int task_rv[kMaxTasks], task_cv[kMaxTasks], task_o[kMaxTasks], task_g[kMaxTasks];
+  int rv_t0[5], rv_t1[5];           // tasks of row variable rv: [rv_t0, rv_t1)
+  int g_o[kMaxGather], g_cv[kMaxGather];
+  int off[kMaxOffsets][3];          // offset vectors
+};
+
+// Host-side operators of one level, stored per element with offset slots.
+//   slot 0: the element itself; slot 1+2k: offset -e_k; slot 2+2k: offset +e_k.
+struct HostLevel {
+  int n[3] = {1, 1, 1};
+  int ne = 0;
+  double h[3] = {0, 0, 0};
+  double vol = 0;
+  std::vector<double> M, Mmu, Mrho;     // [ne][s*s]
+  std::vector<double> G;                // [d][ne][2][s*s]: G_k(e,e), G_k(e,e-e_k)
+  std::vector<double> Et, E, Emu, Erho; // [ne][1+2d][s*s]
+  // Stokes operator blocks
+  std::vector<double> D;                // [ne][nb*nb] diagonal blocks (row-major)
+  std::vector<double> C;                // [ne][T][s*s] coupling task blocks (row-major)
+  std::vector<int> nbr;                 // [ne][NO] neighbour element (-1 absent)
+};
+
+// Device data of one level.
+struct DevLevel {
+  int ne = 0;
+  int cstart[9] = {0};                  // colour ranges in colour-major positions
+  int ncolour = 0;
+  int* perm = nullptr;                  // [ne] position -> element
+  int* nbr = nullptr;                   // [ne][NO] per position
+  void* cpl[3] = {nullptr, nullptr, nullptr};   // per precision: [pos][s][TRP]
+  void* inv[3] = {nullptr, nullptr, nullptr};   // [pos][nb][NBP] column-major A_ii^{-1}
+  void* dia[3] = {nullptr, nullptr, nullptr};   // [pos][nb][NBP] column-major A_ii
+  // cycle vectors: index 0 FP64, index 1 FP32
+  void* vx[2] = {nullptr, nullptr};
+  void* vb[2] = {nullptr, nullptr};
+  void* vr[2] = {nullptr, nullptr};
+  int n[3] = {1, 1, 1};
+};
+
+struct Ctx {
+  int device = 0;
+  std::string err;
+  // problem
+  int d = 0, n[3] = {1, 1, 1}, bc[6] = {0};
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  int p = -1, gamma = 0;
+  double tau = 0.1, tau0 = -1, c_bdry = 10.0, c_intra = 0.0;
+  std::vector<double> mu_vol, mu_if, mu_bf, rho_vol, rho_if;
+  double delta = 0.0;
+  int nu1 = 1, nu2 = 1, precision = 0;
+  // derived
+  int s = 0, nb = 0, q = 0;
+  Pattern pat{};
+  std::vector<HostLevel> host;
+  std::vector<DevLevel> dev;
+  bool ready = false;
+  // bottom
+  int n_snapped = 0;
+  int64_t nbot = 0;
+  double* bottom_pinv = nullptr;  // [nbot][nbot]
+  double* bot_b64 = nullptr;      // FP64 staging for mixed cycles
+  double* bot_x64 = nullptr;
+  // transfer matrices P_f (2^d children), [child][s][s] row-major: fine = P coarse
+  double* child_mats = nullptr;
+  float* child_mats32 = nullptr;
+  // outer-iteration work
+  double* r64 = nullptr;
+  double* c64 = nullptr;
+  double* norm_buf = nullptr;     // device scalars
+  double* norm_host = nullptr;    // pinned
+  int64_t launches = 0;
+  // graph of one outer iteration, keyed by the caller's x and b pointers
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_x = nullptr;
+  const void* graph_b = nullptr;
+  int graph_prec = -1;
+  int64_t graph_kernels = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocations;
+};
+
+// ---- setup.cpp --------------------------------------------------------------
+void build_pattern(int d, int p, int gamma, Pattern& pat);
+int setup_host(Ctx& c);                    // fine assembly, coarsening, Stokes blocks
+void child_matrices(int d, int p, std::vector<double>& out);   // [2^d][s][s]
+void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w);
+int invert_blocks(int n, int count, const double* A, double* Ainv, std::string& err);
+int pseudo_inverse_jacobi(int n, std::vector<double>& A, std::vector<double>& pinv, int& snapped,
+                          double theta);
+void element_index(const int* n, int d, int64_t e, int* idx);
+void face_points(const Ctx& c, int kind, std::vector<double>& xyz, std::vector<double>* nrm);
+int assemble_rhs_host(const Ctx& c, const double* f_vol, const double* bdata, double* b);
+
+}  // namespace stk

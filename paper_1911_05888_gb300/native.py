@@ -1,0 +1,234 @@
+"""ctypes binding of the C ABI in include/stokes_mg.h (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in the
+in-tree shared library libstokes_mg.so and raises StkError on a negative
+status.  Device vectors are torch CUDA tensors (float64, contiguous); the
+library computes everything in its own CUDA kernels.  There is no fallback:
+if the library is missing or no GPU is present, loading fails loudly.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstokes_mg.so")
+
+STK_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "TIMEOUT", -5: "DIVERGED",
+          -6: "NOT_SETUP", -7: "CUDA"}
+BC_PERIODIC, BC_DIRICHLET, BC_STRESS = 0, 1, 2
+FP64, FP32, BF16 = 0, 1, 2
+PTS_VOLUME, PTS_INTERIOR_FACE, PTS_BOUNDARY_FACE = 0, 1, 2
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+_c_i64_p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+
+# name -> argtypes (restype int unless listed in _RESTYPE)
+SIGNATURES = {
+    "stk_create": [ctypes.POINTER(_vp), ctypes.c_int],
+    "stk_destroy": [_vp],
+    "stk_last_error": [_vp],
+    "stk_set_mesh": [_vp, ctypes.c_int, _c_int_p, _c_dbl_p, _c_dbl_p, _c_int_p],
+    "stk_set_discretisation": [_vp, ctypes.c_int, ctypes.c_int],
+    "stk_set_penalty": [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+    "stk_num_points": [_vp, ctypes.c_int, _c_i64_p],
+    "stk_get_points": [_vp, ctypes.c_int, _c_dbl_p, _c_dbl_p],
+    "stk_set_viscosity": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
+    "stk_set_density": [_vp, _c_dbl_p, _c_dbl_p, ctypes.c_double],
+    "stk_set_cycle": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "stk_setup": [_vp, _vp],
+    "stk_get_sizes": [_vp, _c_int_p, _c_i64_p, _c_int_p, _c_int_p],
+    "stk_get_block": [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _c_dbl_p],
+    "stk_assemble_rhs": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
+    "stk_residual": [_vp, _vp, _vp, _vp, _c_dbl_p, _vp],
+    "stk_gs_colour": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
+    "stk_vcycle": [_vp, _vp, _vp, _vp],
+    "stk_restrict": [_vp, ctypes.c_int, _vp, _vp, _vp],
+    "stk_prolong": [_vp, ctypes.c_int, _vp, _vp, _vp],
+    "stk_bottom_solve": [_vp, _vp, _vp, _vp],
+    "stk_solve": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _c_int_p, _c_dbl_p, _vp],
+    "stk_launch_count": [_vp, _c_i64_p],
+}
+_RESTYPE = {"stk_last_error": ctypes.c_char_p}
+
+
+class StkError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libstokes_mg.so (no fallback: raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise StkError("libstokes_mg.so not built: run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, args in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = _RESTYPE.get(name, ctypes.c_int)
+        _lib = lib
+    return _lib
+
+
+def exported_symbols(path=LIB_PATH):
+    lib = ctypes.CDLL(path)
+    return {name for name in SIGNATURES if hasattr(lib, name)}
+
+
+def _dbl(a):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.ctypes.data_as(_c_dbl_p), a
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise StkError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Context:
+    """Owner of one stk_ctx; methods mirror the C entry points."""
+
+    def __init__(self, device=0):
+        self.lib = load()
+        h = _vp()
+        rc = self.lib.stk_create(ctypes.byref(h), device)
+        if rc != STK_OK:
+            raise StkError("stk_create failed (%s)" % ERRORS.get(rc, rc))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, name):
+        if rc != STK_OK:
+            msg = self.lib.stk_last_error(self.h)
+            raise StkError("%s: %s (%s)" % (name, msg.decode() if msg else "", ERRORS.get(rc, rc)))
+
+    def set_mesh(self, d, n, lo, hi, bc):
+        n_ = (ctypes.c_int * d)(*n)
+        lo_ = (ctypes.c_double * d)(*lo)
+        hi_ = (ctypes.c_double * d)(*hi)
+        bc_ = (ctypes.c_int * (2 * d))(*bc)
+        self._check(self.lib.stk_set_mesh(self.h, d, n_, lo_, hi_, bc_), "stk_set_mesh")
+
+    def set_discretisation(self, p, gamma):
+        self._check(self.lib.stk_set_discretisation(self.h, p, gamma), "stk_set_discretisation")
+
+    def set_penalty(self, tau, tau0, c_bdry=10.0, c_intra=0.0):
+        self._check(self.lib.stk_set_penalty(self.h, tau, tau0, c_bdry, c_intra), "stk_set_penalty")
+
+    def num_points(self, kind):
+        n = ctypes.c_int64()
+        self._check(self.lib.stk_num_points(self.h, kind, ctypes.byref(n)), "stk_num_points")
+        return n.value
+
+    def get_points(self, kind, d):
+        n = self.num_points(kind)
+        xyz = np.zeros((n, d))
+        nrm = np.zeros((n, d))
+        self._check(self.lib.stk_get_points(self.h, kind, xyz.ctypes.data_as(_c_dbl_p),
+                                            nrm.ctypes.data_as(_c_dbl_p)), "stk_get_points")
+        return xyz, nrm
+
+    def set_viscosity(self, mu_vol, mu_if, mu_bf):
+        a, b, c = _dbl(mu_vol), _dbl(mu_if), _dbl(mu_bf)
+        self._check(self.lib.stk_set_viscosity(self.h, a[0], b[0], c[0]), "stk_set_viscosity")
+
+    def set_density(self, rho_vol, rho_if, delta):
+        a = _dbl(rho_vol) if rho_vol is not None else (None, None)
+        b = _dbl(rho_if) if rho_if is not None else (None, None)
+        self._check(self.lib.stk_set_density(self.h, a[0], b[0], float(delta)), "stk_set_density")
+
+    def set_cycle(self, nu1, nu2, precision=FP64):
+        self._check(self.lib.stk_set_cycle(self.h, nu1, nu2, precision), "stk_set_cycle")
+
+    def setup(self, stream=None):
+        self._check(self.lib.stk_setup(self.h, _stream(stream)), "stk_setup")
+
+    def sizes(self):
+        nl = ctypes.c_int()
+        nb = ctypes.c_int()
+        sn = ctypes.c_int()
+        self._check(self.lib.stk_get_sizes(self.h, ctypes.byref(nl), None, ctypes.byref(nb),
+                                           ctypes.byref(sn)), "stk_get_sizes")
+        ne = np.zeros(nl.value, dtype=np.int64)
+        self._check(self.lib.stk_get_sizes(self.h, None, ne.ctypes.data_as(_c_i64_p), None, None),
+                    "stk_get_sizes")
+        return nl.value, ne, nb.value, sn.value
+
+    def get_block(self, level, i, j, nb):
+        out = np.zeros((nb, nb))
+        self._check(self.lib.stk_get_block(self.h, level, i, j, out.ctypes.data_as(_c_dbl_p)),
+                    "stk_get_block")
+        return out
+
+    def assemble_rhs(self, f_vol, bdata, ne, nb):
+        b = np.zeros((ne, nb))
+        f = _dbl(f_vol)
+        bd = _dbl(bdata) if bdata is not None else (None, None)
+        self._check(self.lib.stk_assemble_rhs(self.h, f[0], bd[0], b.ctypes.data_as(_c_dbl_p)),
+                    "stk_assemble_rhs")
+        return b
+
+    def residual(self, x, b, r, want_norm=False, stream=None):
+        nrm = ctypes.c_double()
+        self._check(self.lib.stk_residual(self.h, _ptr(x), _ptr(b), _ptr(r),
+                                          ctypes.byref(nrm) if want_norm else None, _stream(stream)),
+                    "stk_residual")
+        return nrm.value if want_norm else None
+
+    def gs_colour(self, level, colour, x, b, stream=None):
+        self._check(self.lib.stk_gs_colour(self.h, level, colour, _ptr(x), _ptr(b), _stream(stream)),
+                    "stk_gs_colour")
+
+    def vcycle(self, x, b, stream=None):
+        self._check(self.lib.stk_vcycle(self.h, _ptr(x), _ptr(b), _stream(stream)), "stk_vcycle")
+
+    def restrict(self, level, r, rc, stream=None):
+        self._check(self.lib.stk_restrict(self.h, level, _ptr(r), _ptr(rc), _stream(stream)), "stk_restrict")
+
+    def prolong(self, level, xc, x, stream=None):
+        self._check(self.lib.stk_prolong(self.h, level, _ptr(xc), _ptr(x), _stream(stream)), "stk_prolong")
+
+    def bottom_solve(self, b, x, stream=None):
+        self._check(self.lib.stk_bottom_solve(self.h, _ptr(b), _ptr(x), _stream(stream)), "stk_bottom_solve")
+
+    def solve(self, x, b, rtol=1e-10, maxit=100, stream=None):
+        it = ctypes.c_int()
+        hist = np.zeros(maxit + 1)
+        rc = self.lib.stk_solve(self.h, _ptr(x), _ptr(b), rtol, maxit, ctypes.byref(it),
+                                hist.ctypes.data_as(_c_dbl_p), _stream(stream))
+        self._check(rc, "stk_solve")
+        return it.value, hist[: it.value + 1]
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        self._check(self.lib.stk_launch_count(self.h, ctypes.byref(n)), "stk_launch_count")
+        return n.value

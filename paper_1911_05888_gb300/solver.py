@@ -1,0 +1,58 @@
+"""Problem-level wrapper over the C ABI: sample the coefficients and data of a
+``problems.Problem`` at the library's own quadrature points and drive setup,
+right-hand-side assembly, V-cycles and solves.  All arithmetic of the method
+runs inside libstokes_mg.so; this module only moves arrays across the ABI."""
+import numpy as np
+
+from . import native
+from .problems import PERIODIC, DIRICHLET, STRESS
+
+
+class StokesMG:
+    def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True):
+        self.prob = prob
+        self.ctx = native.Context(device)
+        d = prob.d
+        self.ctx.set_mesh(d, prob.n, prob.lo, prob.hi, prob.bc)
+        self.ctx.set_discretisation(prob.p, prob.gamma)
+        self.ctx.set_penalty(prob.tau, prob.tau0)
+        xv, _ = self.ctx.get_points(native.PTS_VOLUME, d)
+        xi, _ = self.ctx.get_points(native.PTS_INTERIOR_FACE, d)
+        xb, nb_ = self.ctx.get_points(native.PTS_BOUNDARY_FACE, d)
+        self.points = (xv, xi, xb, nb_)
+        self.ctx.set_viscosity(prob.mu(xv), prob.mu(xi) if len(xi) else np.zeros(0),
+                               prob.mu(xb) if len(xb) else np.zeros(0))
+        if prob.delta is not None:
+            self.ctx.set_density(prob.rho(xv), prob.rho(xi) if len(xi) else np.zeros(0), prob.delta)
+        nu1, nu2 = (prob.nu1, prob.nu2) if nu is None else nu
+        self.ctx.set_cycle(nu1, nu2, precision)
+        if setup:
+            self.ctx.setup()
+            self.nlevels, self.ne_levels, self.nb, self.n_snapped = self.ctx.sizes()
+
+    def rhs(self):
+        """b from the manufactured solution of the problem (host array [ne][nb])."""
+        prob, ex = self.prob, self.prob.exact
+        d = prob.d
+        xv, xi, xb, nrm = self.points
+        f_vol = np.concatenate([ex.f(xv), ex.fdiv(xv)[:, None]], axis=1)
+        bdata = np.zeros((len(xb), d))
+        if len(xb):
+            axis = np.argmax(np.abs(nrm), axis=1)
+            side = np.sign(nrm[np.arange(len(xb)), axis]).astype(int)
+            kind = np.array([prob.bc[2 * k + (0 if s < 0 else 1)] for k, s in zip(axis, side)])
+            dmask = kind == DIRICHLET
+            smask = kind == STRESS
+            if dmask.any():
+                bdata[dmask] = ex.u(xb[dmask])
+            for k in range(d):
+                for s in (-1, 1):
+                    m = smask & (axis == k) & (side == s)
+                    if m.any():
+                        nvec = np.zeros(d)
+                        nvec[k] = s
+                        bdata[m] = ex.stress(xb[m], nvec)
+        return self.ctx.assemble_rhs(f_vol, bdata, prob.n_elements, prob.nb)
+
+    def close(self):
+        self.ctx.close()

@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+FP64 tolerances: operator blocks 1e-13 (relative to the level's largest
+entry), single kernels 1e-13, V-cycle iterates 1e-12 relative (the stated
+target).  Low-precision cycles are judged by the FP64 outer iteration
+reaching 1e-10 and by their distance to the oracle's emulation of the same
+rounding.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1911_05888_gb300 import native, problems as P  # noqa: E402
+from paper_1911_05888_gb300.solver import StokesMG  # noqa: E402
+from oracle import multigrid  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "periodic16p2": lambda: P.periodic_standard_2d(n=16, p=2),
+    "stress16p3": lambda: P.stress_variable_mu_2d(n=16, p=3),
+    "dirichlet-rect": lambda: P.generic(2, (12, 8), 2, 0, [P.DIRICHLET, P.STRESS, P.DIRICHLET, P.DIRICHLET],
+                                        exact=P.paper_solution(2, 0)),
+    "vs-periodic-p1": lambda: P.generic(2, 8, 1, 1, [P.PERIODIC] * 4),
+    "3d-mixed-p1": lambda: P.generic(3, 4, 1, 1, [P.DIRICHLET, P.STRESS, P.PERIODIC, P.PERIODIC,
+                                                  P.DIRICHLET, P.DIRICHLET]),
+    "3d-unsteady-p2": lambda: P.unsteady_periodic_3d(n=8, p=2, re=10.0),
+}
+
+_cache = {}
+
+
+def get(name, precision=native.FP64):
+    key = (name, precision)
+    if key not in _cache:
+        prob = CASES[name]()
+        gpu = StokesMG(prob, precision=precision)
+        orc = multigrid.Multigrid(prob) if (name, native.FP64) not in _cache else _cache[(name, native.FP64)][2]
+        _cache[key] = (prob, gpu, orc)
+    return _cache[key]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hierarchy_and_blocks(name):
+    prob, gpu, orc = get(name)
+    assert gpu.nlevels == len(orc.levels)
+    assert gpu.n_snapped == orc.kernel_dim_bottom
+    rng = np.random.default_rng(5)
+    for l, lev in enumerate(orc.levels):
+        nb, ne = lev.nb, lev.ne
+        scale = abs(lev.A).max()
+        els = range(ne) if ne <= 32 else rng.choice(ne, 24, replace=False)
+        for i in els:
+            row = lev.A[i * nb:(i + 1) * nb, :].toarray()
+            cols = set(np.nonzero(np.abs(row).sum(0))[0] // nb) | {i}
+            for j in cols:
+                blk = gpu.ctx.get_block(l, int(i), int(j), nb)
+                assert np.abs(blk - row[:, j * nb:(j + 1) * nb]).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_colour_step_and_residual(name):
+    prob, gpu, orc = get(name)
+    rng = np.random.default_rng(11)
+    n = prob.n_dofs
+    x0 = rng.uniform(-1, 1, n)
+    b = rng.uniform(-1, 1, n)
+    sm = orc.sm[0]
+    xd, bd = dev(x0), dev(b)
+    xo = x0.copy()
+    for c in range(sm.ncol):
+        gpu.ctx.gs_colour(0, c, xd, bd)
+        sm.colour_step(xo, b, c)
+        assert rel(xd.cpu().numpy(), xo) <= 1e-13
+    r = torch.empty_like(xd)
+    nrm = gpu.ctx.residual(xd, bd, r, want_norm=True)
+    ro = orc.residual(0, xo, b)
+    assert rel(r.cpu().numpy(), ro) <= 1e-12
+    assert abs(nrm - np.linalg.norm(ro)) <= 1e-12 * np.linalg.norm(ro)
+
+
+@pytest.mark.parametrize("name", ["periodic16p2", "stress16p3", "3d-mixed-p1"])
+def test_transfers_and_bottom(name):
+    prob, gpu, orc = get(name)
+    rng = np.random.default_rng(3)
+    for l in range(len(orc.levels) - 1):
+        nf, nc = orc.levels[l].ne * orc.levels[l].nb, orc.levels[l + 1].ne * orc.levels[l + 1].nb
+        r = rng.standard_normal(nf)
+        rc = torch.zeros(nc, dtype=torch.float64, device="cuda")
+        gpu.ctx.restrict(l, dev(r), rc)
+        assert rel(rc.cpu().numpy(), orc.restrict(l, r)) <= 1e-14
+        xc = rng.standard_normal(nc)
+        x = rng.standard_normal(nf)
+        xd = dev(x)
+        gpu.ctx.prolong(l, dev(xc), xd)
+        assert rel(xd.cpu().numpy(), x + orc.prolong(l, xc)) <= 1e-14
+    nbot = orc.levels[-1].ne * orc.levels[-1].nb
+    bb = rng.standard_normal(nbot)
+    xb = torch.zeros(nbot, dtype=torch.float64, device="cuda")
+    gpu.ctx.bottom_solve(dev(bb), xb)
+    assert rel(xb.cpu().numpy(), orc.bottom @ bb) <= 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_vcycle_iterates(name):
+    """Algorithm 1 iterates x_k = V(x_{k-1}, b), k = 1..10, from x_0 = 0."""
+    prob, gpu, orc = get(name)
+    rng = np.random.default_rng(21)
+    b = rng.uniform(-1, 1, prob.n_dofs)
+    bd = dev(b)
+    xd = torch.zeros_like(bd)
+    xo = np.zeros(prob.n_dofs)
+    worst = 0.0
+    for k in range(10):
+        gpu.ctx.vcycle(xd, bd)
+        orc.vcycle(xo, b)
+        worst = max(worst, rel(xd.cpu().numpy(), xo))
+    assert worst <= 1e-12, worst
+
+
+@pytest.mark.parametrize("name", ["periodic16p2", "stress16p3", "dirichlet-rect", "3d-unsteady-p2"])
+def test_solve_fp64_matches_oracle(name):
+    prob, gpu, orc = get(name)
+    b = gpu.rhs().ravel()
+    bd = dev(b)
+    xd = torch.zeros_like(bd)
+    it, hist = gpu.ctx.solve(xd, bd, rtol=1e-10, maxit=100)
+    xo, ho = orc.solve(b, rtol=1e-10, maxit=100)
+    assert hist[-1] <= 1e-10
+    assert abs(it - (len(ho) - 1)) <= 1
+    assert rel(xd.cpu().numpy(), xo) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", [native.FP32, native.BF16])
+@pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-unsteady-p2"])
+def test_mixed_precision_refinement(name, precision):
+    """Low-precision V-cycles inside FP64 refinement reach 1e-10 and the same
+    solution as the FP64 path."""
+    prob, gpu64, orc = get(name)
+    _, gpu, _ = get(name, precision)
+    b = gpu64.rhs().ravel()
+    bd = dev(b)
+    x64 = torch.zeros_like(bd)
+    gpu64.ctx.solve(x64, bd, rtol=1e-10, maxit=100)
+    x = torch.zeros_like(bd)
+    it, hist = gpu.ctx.solve(x, bd, rtol=1e-10, maxit=200)
+    assert hist[-1] <= 1e-10, hist
+    assert rel(x.cpu().numpy(), x64.cpu().numpy()) <= 1e-8
+
+
+def test_fp32_cycle_close_to_oracle_emulation():
+    """One FP32 cycle against the oracle with blocks rounded to FP32 (the
+    accumulation order differs, so the bar is FP32-level agreement)."""
+    name = "stress16p3"
+    prob, gpu64, _ = get(name)
+    _, gpu, _ = get(name, native.FP32)
+    orc32 = multigrid.Multigrid(prob, storage="fp32")
+    b = gpu64.rhs().ravel()
+    bd = dev(b)
+    x = torch.zeros_like(bd)
+    it, hist = gpu.ctx.solve(x, bd, rtol=1e-30, maxit=1)
+    xo = orc32.precondition(b)
+    assert rel(x.cpu().numpy(), xo) <= 1e-4
+
+
+def test_invalid_arguments_are_rejected():
+    ctx = native.Context(0)
+    with pytest.raises(native.StkError):
+        ctx.set_mesh(2, (4, 4), (0, 0), (1, 1), (0, 1, 0, 0))      # periodic on one side only
+    with pytest.raises(native.StkError):
+        ctx.set_mesh(4, (4, 4, 4, 4), (0,) * 4, (1,) * 4, (0,) * 8)
+    ctx.set_mesh(2, (4, 4), (0, 0), (1, 1), (0, 0, 0, 0))
+    with pytest.raises(native.StkError):
+        ctx.set_discretisation(0, 0)
+    ctx.set_discretisation(2, 0)
+    nv = ctx.num_points(native.PTS_VOLUME)
+    ni = ctx.num_points(native.PTS_INTERIOR_FACE)
+    with pytest.raises(native.StkError):
+        ctx.set_viscosity(-np.ones(nv), np.ones(ni), np.zeros(0))  # mu must be positive
+    with pytest.raises(native.StkError):
+        x = torch.zeros(10, dtype=torch.float64, device="cuda")
+        ctx.vcycle(x, x)                                             # not set up
+    ctx.close()
