@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark: LDG Stokes multigrid solve to 1e-10 on one GB300.
+
+Workload: 2D steady viscous-stress form, 256 x 256 elements, p = 3 (nb = 48,
+3,145,728 DOFs), Dirichlet on three sides and a stress condition on the
+fourth, mu = 1 + 0.9 sin(2 pi x) cos(2 pi y); manufactured right-hand side.
+
+A step is one solve to ||b - A x|| <= 1e-10 ||b|| from x = 0: the outer FP64
+iteration x <- x + V(0, b - A x) with V(1,1) cycles (every hot-path kernel:
+coloured block Gauss-Seidel sweeps, residuals, restriction, prolongation,
+bottom solve), captured as one CUDA graph per outer iteration.  The headline
+path stores the element blocks in FP32 inside the FP64 refinement; the plain
+FP64 path is measured on the same problem beside it.
+
+value = DOFs x V-cycles / s (DOF-cycles per second through whole solves).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-10 rel. residual & DOFs/s per V-cycle: mixed+learned vs plain FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default=None, choices=["gs", "resid", "solve"],
+                    help="run only a profiling target (for ncu): 8 finest-level colour sweeps, "
+                         "8 finest-level residuals, or one solve")
+    ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload(n, p):
+    from paper_1911_05888_gb300 import problems as P
+    return P.stress_variable_mu_2d(n=n, p=p, nu=(1, 1))
+
+
+def config(args, prob):
+    return {"workload": "2d-viscous-stress-varmu-dirichlet3-stress1", "n": [args.n, args.n], "p": args.p,
+            "dofs": prob.n_dofs, "nu": [1, 1], "rtol": 1e-10,
+            "cache": "inputs larger than L2 (element blocks >= 3.6 GB per solve)",
+            "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample: the same problem on a 64 x 64 mesh)
+# ---------------------------------------------------------------------------
+def cpu_child(spec):
+    """Runs in a fresh single-threaded process: time oracle V-cycles plus the
+    outer residual on the sample problem; prints one JSON line."""
+    n, p, seconds = [float(v) for v in spec.split(",")]
+    n, p = int(n), int(p)
+    import numpy as np
+    from oracle import multigrid
+    prob = workload(n, p)
+    mg = multigrid.Multigrid(prob)
+    rng = np.random.default_rng(0)
+    b = rng.uniform(-1, 1, prob.n_dofs)
+    x = np.zeros_like(b)
+    cycles, t0 = 0, time.perf_counter()
+    while True:
+        r = b - mg.A @ x
+        x += mg.precondition(r)
+        cycles += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and cycles >= 2:
+            break
+    print(json.dumps({"dofs": prob.n_dofs, "cycles": cycles, "seconds": el}))
+
+
+def cpu_baseline(args, seconds=12.0):
+    n = min(args.n, 64)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child",
+                          "%d,%d,%f" % (n, args.p, seconds)], capture_output=True, text=True, env=env,
+                         timeout=900)
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    value = rec["dofs"] * rec["cycles"] / rec["seconds"]
+    return {"value": value, "unit": "DOF-cycles/s", "cores": 1, "kind": "oracle",
+            "sample": "same problem class on a %dx%d mesh (p=%d, %d DOFs): %d V(1,1) cycles + FP64 "
+                      "residuals in %.1f s, numpy/scipy single thread" % (n, n, args.p, rec["dofs"],
+                                                                          rec["cycles"], rec["seconds"])}
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Native (GPU) arm
+# ---------------------------------------------------------------------------
+def algorithmic_bytes_gs(mg, prob, storage_bytes, vec_bytes, level_ne):
+    """Bytes one colour launch must move at the finest level: stored nonzero
+    coupling sub-blocks and the dense inverse of every element of the colour,
+    plus b_i read and x_i written."""
+    d, s, nb = prob.d, (prob.p + 1) ** prob.d, prob.nb
+    tasks = 2 * d * (d + 2) if prob.gamma == 0 else 2 * d * (2 * d + 1) + d * (d - 1)
+    per_elem = (tasks * s * s + nb * nb) * storage_bytes + 2 * nb * vec_bytes
+    return per_elem * (level_ne // 2 ** d)
+
+
+def time_kernel(fn, reps, stream):
+    import torch
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(reps):
+        fn()
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / reps / 1e3
+
+
+def read_profile_traffic(name):
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("dram_bytes_per_launch:"):
+            try:
+                return float(line.split(":")[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+def run_profile(args):
+    """Small, self-contained launch sequences for ncu captures."""
+    import torch
+    from paper_1911_05888_gb300 import native
+    from paper_1911_05888_gb300.solver import StokesMG
+    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16}[args.precision]
+    prob = workload(args.n, args.p)
+    mg = StokesMG(prob, precision=prec)
+    torch.cuda.synchronize()
+    vdt = torch.float64 if prec == native.FP64 else torch.float32
+    if args.profile in ("gs", "resid"):
+        xv = torch.zeros(prob.n_dofs, dtype=vdt, device="cuda")
+        bv = torch.ones(prob.n_dofs, dtype=vdt, device="cuda")
+        rv = torch.zeros_like(xv)
+        for i in range(8):
+            if args.profile == "gs":
+                mg.ctx.gs_colour_ex(0, i % 4, prec, xv, bv)
+            else:
+                mg.ctx.residual_ex(0, prec, xv, bv, rv)
+    else:
+        b = torch.from_numpy(mg.rhs().ravel()).cuda()
+        x = torch.zeros_like(b)
+        it, hist = mg.ctx.solve(x, b, rtol=1e-10, maxit=200)
+        print("profile solve: %d iterations to %.2e" % (it, hist[-1]))
+    torch.cuda.synchronize()
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    from paper_1911_05888_gb300 import native
+    from paper_1911_05888_gb300.solver import StokesMG
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16}[args.precision]
+    prob = workload(args.n, args.p)
+
+    t0 = time.perf_counter()
+    mg = StokesMG(prob, precision=prec, device=local)
+    setup_s = time.perf_counter() - t0
+    mg64 = StokesMG(prob, precision=native.FP64, device=local) if prec != native.FP64 else mg
+    b_host = mg.rhs().ravel()
+    b = torch.from_numpy(b_host).cuda()
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def solve(ctx):
+        x.zero_()
+        it, hist = ctx.solve(x, b, rtol=1e-10, maxit=200)
+        return it, hist
+
+    def timed(ctx, steps, warmup):
+        for _ in range(warmup):
+            solve(ctx)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = ctx.launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = []
+        ev0.record(stream)
+        for _ in range(steps):
+            it, hist = solve(ctx)
+            iters.append(it)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        el = ev0.elapsed_time(ev1) / 1e3
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        return el, iters, ctx.launch_count() - l0, hist
+
+    clocks = Clocks(local)
+    clocks.start()
+    el, iters, launches, hist = timed(mg.ctx, args.steps, args.warmup)
+    clk = clocks.stop()
+    cycles = sum(iters)
+    value = prob.n_dofs * cycles * world / el
+
+    # Plain FP64 on the same problem (the comparison the metric names).
+    el64, it64, _, hist64 = timed(mg64.ctx, max(1, args.steps // 2), 1)
+    plain = {"ms_per_solve": el64 / len(it64) * 1e3, "iters": it64[0],
+             "dof_cycles_per_s": prob.n_dofs * sum(it64) / el64, "final_rel_residual": float(hist64[-1])}
+
+    # End to end through the public API with host buffers (pinned H2D of b,
+    # solve, D2H of x) per step.
+    bh = torch.from_numpy(b_host).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    for _ in range(1):
+        b.copy_(bh, non_blocking=True)
+        solve(mg.ctx)
+        xh.copy_(x, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_cycles = 0
+    for _ in range(args.steps):
+        b.copy_(bh, non_blocking=True)
+        it, _ = solve(mg.ctx)
+        e2e_cycles += it
+        xh.copy_(x, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e = {"value": prob.n_dofs * e2e_cycles * world / e2e_s, "unit": "DOF-cycles/s",
+           "h2d_bytes_per_step": int(bh.numel() * 8), "d2h_bytes_per_step": int(xh.numel() * 8),
+           "ms_per_solve": e2e_s / args.steps * 1e3}
+
+    # Dominant kernel: finest-level colour sweep in the cycle's precision.
+    nl, ne_levels, nb, _ = mg.ctx.sizes()
+    vdt = torch.float64 if prec == native.FP64 else torch.float32
+    xv = torch.zeros(prob.n_dofs, dtype=vdt, device="cuda")
+    bv = torch.ones(prob.n_dofs, dtype=vdt, device="cuda")
+    t_gs = time_kernel(lambda: mg.ctx.gs_colour_ex(0, 0, prec, xv, bv, stream), 20, stream)
+    sb = {native.FP64: 8, native.FP32: 4, native.BF16: 2}[prec]
+    vb = 8 if prec == native.FP64 else 4
+    alg = algorithmic_bytes_gs(mg, prob, sb, vb, int(ne_levels[0]))
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ach = alg / t_gs / 1e9
+    traffic = read_profile_traffic("gs_sweep_%s_256x256_p3.md" % args.precision)
+    roof = {"kernel": "element_kernel (block GS colour sweep, finest level, %s blocks)" % args.precision,
+            "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(ach / hbm_peak, 3), "traffic": traffic,
+            "algorithmic_bytes_per_launch": int(alg), "launch_ms": round(t_gs * 1e3, 4),
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    t_gs64 = time_kernel(lambda: mg64.ctx.gs_colour(0, 0, x, b, stream), 10, stream)
+    alg64 = algorithmic_bytes_gs(mg64, prob, 8, 8, int(ne_levels[0]))
+    kernels64 = {"gs_sweep_fp64_ms": round(t_gs64 * 1e3, 4),
+                 "gs_sweep_fp64_GBps": round(alg64 / t_gs64 / 1e9, 1),
+                 "gs_sweep_fp64_TFLOPs": round(alg64 / 8 * 2 / t_gs64 / 1e12, 3)}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "DOF-cycles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32-storage/f32-accum in f64 refinement",
+                  "bf16": "bf16-storage/f32-accum in f64 refinement"}[args.precision],
+        "data": "synthetic (manufactured solution, seeded)", "config": config(args, prob),
+        "time_to_1e-10_ms": el / args.steps * 1e3, "iters_per_solve": iters[0],
+        "final_rel_residual": float(hist[-1]), "setup_s": round(setup_s, 2),
+        "plain_fp64": plain, "speedup_vs_plain_fp64": plain["ms_per_solve"] / (el / args.steps * 1e3),
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "fp64_kernels": kernels64,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(result))
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the CPU oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    n = min(args.n, 64)
+    import numpy as np
+    from oracle import multigrid
+    prob = workload(n, args.p)
+    mg = multigrid.Multigrid(prob)
+    b = np.random.default_rng(0).uniform(-1, 1, prob.n_dofs)
+    x = np.zeros_like(b)
+
+    def step():
+        cyc, t0 = 0, time.perf_counter()
+        while True:
+            x[:] += mg.precondition(b - mg.A @ x)
+            cyc += 1
+            if time.perf_counter() - t0 >= per_step:
+                return cyc, time.perf_counter() - t0
+    for _ in range(args.warmup):
+        step()
+    tot_c, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        c, s = step()
+        tot_c += c
+        tot_s += s
+    value = prob.n_dofs * tot_c / tot_s
+    sample = ("oracle (numpy/scipy, single process) on the same problem class at %dx%d, p=%d "
+              "(%d DOFs); each step = %.0f s of V(1,1) cycles with FP64 residuals" % (n, n, args.p,
+                                                                                     prob.n_dofs, per_step))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-cycles/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config(args, workload(args.n, args.p)),
+        "cpu_baseline": {"value": value, "unit": "DOF-cycles/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "DOF-cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.cpu_child:
+        cpu_child(args.cpu_child)
+        return
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -172,6 +172,16 @@ int stk_residual(stk_ctx* ctx, const double* x_dev, const double* b_dev, double*
 int stk_gs_colour(stk_ctx* ctx, int level, int colour, double* x_dev, const double* b_dev,
                   void* stream);
 
+/* The colour step of stk_gs_colour and the residual of Algorithm 1 line 5
+ * on any smoothing level with the blocks stored in `precision`: STK_FP64
+ * (x, b, r are double) or the precision given to stk_set_cycle before
+ * stk_setup (x, b, r are float, accumulation in FP32).  These run the same
+ * kernels as the V-cycle; they exist so callers can time and test them. */
+int stk_gs_colour_ex(stk_ctx* ctx, int level, int colour, int precision, void* x_dev,
+                     const void* b_dev, void* stream);
+int stk_residual_ex(stk_ctx* ctx, int level, int precision, const void* x_dev, const void* b_dev,
+                    void* r_dev, void* stream);
+
 /* One V-cycle of Algorithm 1 in place on level 0 in FP64: x <- V(x, b). */
 int stk_vcycle(stk_ctx* ctx, double* x_dev, const double* b_dev, void* stream);
 

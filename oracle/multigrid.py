@@ -117,6 +117,18 @@ class Multigrid:
     def A(self):
         return self.levels[0].A
 
+    def bottom_solve(self, b, refine=3):
+        """Least-squares solution A_c^+ b of the bottom level (Section 3
+        footnote).  The eigen pseudo-inverse is applied and then refined in
+        FP64, x <- x + A_c^+ (b - A_c x): the eigendecomposition alone leaves a
+        relative error of about 1e-12 on these operators, the refined result is
+        the least-squares solution to rounding level."""
+        A = self.levels[-1].A
+        x = self.bottom @ b
+        for _ in range(refine):
+            x = x + self.bottom @ (b - A @ x)
+        return x
+
     def residual(self, l, x, b):
         return b - self.levels[l].A @ x
 
@@ -133,7 +145,7 @@ class Multigrid:
         nu1 = self.nu1 if nu1 is None else nu1
         nu2 = self.nu2 if nu2 is None else nu2
         if l == len(self.levels) - 1:
-            x[:] = self.bottom @ b
+            x[:] = self.bottom_solve(b)
             return x
         sm = self.sm[l]
         for _ in range(nu1):

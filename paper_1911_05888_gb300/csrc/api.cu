@@ -589,6 +589,43 @@ int stk_gs_colour(stk_ctx* c, int level, int colour, double* x, const double* b,
   });
 }
 
+static bool have_precision(const Ctx& c, int precision) {
+  return precision == STK_FP64 || (precision == c.precision && precision > 0 && precision <= 2);
+}
+
+int stk_gs_colour_ex(stk_ctx* c, int level, int colour, int precision, void* x, const void* b,
+                     void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (level < 0 || level >= nlevels(*c) - 1) return fail(c, STK_ERR_INVALID_ARG, "bad level");
+    if (colour < 0 || colour >= (1 << c->d) || !x || !b) return fail(c, STK_ERR_INVALID_ARG, "bad colour");
+    if (!have_precision(*c, precision)) return fail(c, STK_ERR_INVALID_ARG, "precision not set up");
+    DevLevel& D = c->dev[level];
+    int n = D.cstart[colour + 1] - D.cstart[colour];
+    ck(launch_element(c->pat, precision, MODE_GS, D.cstart[colour], n, D.perm, D.nbr, D.cpl[precision],
+                      D.inv[precision], b, x, nullptr, (cudaStream_t)stream),
+       "gs colour launch");
+    c->launches++;
+    return STK_OK;
+  });
+}
+
+int stk_residual_ex(stk_ctx* c, int level, int precision, const void* x, const void* b, void* r,
+                    void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (level < 0 || level >= nlevels(*c) - 1) return fail(c, STK_ERR_INVALID_ARG, "bad level");
+    if (!x || !b || !r) return fail(c, STK_ERR_INVALID_ARG, "null vector");
+    if (!have_precision(*c, precision)) return fail(c, STK_ERR_INVALID_ARG, "precision not set up");
+    DevLevel& D = c->dev[level];
+    ck(launch_element(c->pat, precision, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[precision],
+                      D.dia[precision], b, (void*)x, r, (cudaStream_t)stream),
+       "residual launch");
+    c->launches++;
+    return STK_OK;
+  });
+}
+
 int stk_vcycle(stk_ctx* c, double* x, const double* b, void* stream) {
   return guard(c, [&]() -> int {
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");

@@ -45,6 +45,8 @@ SIGNATURES = {
     "stk_assemble_rhs": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
     "stk_residual": [_vp, _vp, _vp, _vp, _c_dbl_p, _vp],
     "stk_gs_colour": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
+    "stk_gs_colour_ex": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
+    "stk_residual_ex": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp],
     "stk_vcycle": [_vp, _vp, _vp, _vp],
     "stk_restrict": [_vp, ctypes.c_int, _vp, _vp, _vp],
     "stk_prolong": [_vp, ctypes.c_int, _vp, _vp, _vp],
@@ -207,6 +209,14 @@ class Context:
     def gs_colour(self, level, colour, x, b, stream=None):
         self._check(self.lib.stk_gs_colour(self.h, level, colour, _ptr(x), _ptr(b), _stream(stream)),
                     "stk_gs_colour")
+
+    def gs_colour_ex(self, level, colour, precision, x, b, stream=None):
+        self._check(self.lib.stk_gs_colour_ex(self.h, level, colour, precision, _ptr(x), _ptr(b),
+                                              _stream(stream)), "stk_gs_colour_ex")
+
+    def residual_ex(self, level, precision, x, b, r, stream=None):
+        self._check(self.lib.stk_residual_ex(self.h, level, precision, _ptr(x), _ptr(b), _ptr(r),
+                                             _stream(stream)), "stk_residual_ex")
 
     def vcycle(self, x, b, stream=None):
         self._check(self.lib.stk_vcycle(self.h, _ptr(x), _ptr(b), _stream(stream)), "stk_vcycle")

@@ -373,3 +373,18 @@ def test_table1_tau_within_table2_window_of_oracle_minimum():
 def test_bf16_rounding_is_round_to_nearest_even():
     v = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -9, -3.140625])
     np.testing.assert_array_equal(multigrid.round_bf16(v), [1.0, 1.0 + 2 * 2.0 ** -7, 1.0, -3.140625])
+
+
+def test_bottom_solve_is_least_squares_solution():
+    """The bottom solver returns the least-squares solution: orthogonal to the
+    kernel, residual orthogonal to the range (Section 3 footnote)."""
+    for prob in (P.periodic_standard_2d(n=8, p=2), P.generic(2, 8, 3, 1, [P.DIRICHLET] * 3 + [P.STRESS])):
+        mg = multigrid.Multigrid(prob)
+        A = mg.levels[-1].A.toarray()
+        lam, V = np.linalg.eigh(A)
+        ker = V[:, np.abs(lam) <= 1e-10 * np.abs(lam).max()]
+        b = np.random.default_rng(2).standard_normal(A.shape[0])
+        x = mg.bottom_solve(b)
+        r = b - A @ x
+        assert np.linalg.norm(ker.T @ x) <= 1e-12 * np.linalg.norm(x)
+        assert np.linalg.norm(r - ker @ (ker.T @ r)) <= 1e-13 * np.linalg.norm(b)
