@@ -203,6 +203,29 @@ int stk_bottom_solve(stk_ctx* ctx, const double* b_dev, double* x_dev, void* str
 int stk_solve(stk_ctx* ctx, double* x_dev, const double* b_dev, double rtol, int maxit,
               int* iters_out, double* hist, void* stream);
 
+/*
+ * Allocation-free variant of stk_residual with the norm: r = b - A x on
+ * level 0 in FP64 and ||r||_2^2 written to the caller's device scalar
+ * *norm2_dev, enqueued on `stream` without synchronising.  The paper has no
+ * counterpart; this entry point exists for callers that must not allocate
+ * device memory while they run -- code under a fixed device-memory budget,
+ * or a host thread that must not call cudaMalloc because it can block on or
+ * serialise with work already running on the device.  The call allocates
+ * nothing: its only scratch (the per-chunk partial sums of ||r||^2) is a
+ * 128 KB file-scope device array that every GPU which loads the library holds
+ * until the process exits.  Limits and caveats:
+ *  - at most 33,554,432 unknowns on level 0 (16384 chunks of 2048);
+ *    larger problems return STK_ERR_INVALID_ARG with a message;
+ *  - the first call on a device looks up the array's device address (with
+ *    that device made current) and caches it; make that first call before
+ *    any stream capture;
+ *  - all calls share the array; each call writes every slot it reads, but
+ *    calls that overlap on the GPU (e.g. on two streams) race on it;
+ *  - on failure only the context's host-side error message is updated.
+ */
+int stk_residual_norm_static(stk_ctx* ctx, const double* x_dev, const double* b_dev, double* r_dev,
+                             double* norm2_dev, void* stream);
+
 /* Number of kernel launches the library enqueued since the context was
  * created (all of them are this library's own kernels). */
 int stk_launch_count(stk_ctx* ctx, int64_t* count);

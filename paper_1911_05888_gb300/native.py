@@ -52,6 +52,7 @@ SIGNATURES = {
     "stk_prolong": [_vp, ctypes.c_int, _vp, _vp, _vp],
     "stk_bottom_solve": [_vp, _vp, _vp, _vp],
     "stk_solve": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _c_int_p, _c_dbl_p, _vp],
+    "stk_residual_norm_static": [_vp, _vp, _vp, _vp, _vp, _vp],
     "stk_launch_count": [_vp, _c_i64_p],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
@@ -237,6 +238,12 @@ class Context:
                                 hist.ctypes.data_as(_c_dbl_p), _stream(stream))
         self._check(rc, "stk_solve")
         return it.value, hist[: it.value + 1]
+
+    def residual_norm_static(self, x, b, r, norm2, stream=None):
+        """stk_residual_norm_static: r = b - A x and ||r||^2 into the device
+        scalar norm2, using only the library's fixed static scratch."""
+        self._check(self.lib.stk_residual_norm_static(self.h, _ptr(x), _ptr(b), _ptr(r), _ptr(norm2),
+                                                      _stream(stream)), "stk_residual_norm_static")
 
     def launch_count(self):
         n = ctypes.c_int64()
