@@ -6,11 +6,15 @@ Workload: 2D steady viscous-stress form, 256 x 256 elements, p = 3 (nb = 48,
 fourth, mu = 1 + 0.9 sin(2 pi x) cos(2 pi y); manufactured right-hand side.
 
 A step is one solve to ||b - A x|| <= 1e-10 ||b|| from x = 0: the outer FP64
-iteration x <- x + V(0, b - A x) with V(1,1) cycles (every hot-path kernel:
+iteration preconditioned by V-cycles (every hot-path kernel:
 coloured block Gauss-Seidel sweeps, residuals, restriction, prolongation,
 bottom solve), captured as one CUDA graph per outer iteration.  The headline
 path stores the element blocks in FP32 inside the FP64 refinement; the plain
 FP64 path is measured on the same problem beside it.
+
+The outer iteration is flexible GMRES(30) in FP64 with one V(2,2) cycle as the
+right preconditioner (--solver richardson --nu 1 gives the plain iterative
+refinement with V(1,1)).
 
 value = DOFs x V-cycles / s (DOF-cycles per second through whole solves).
 """
@@ -38,6 +42,9 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--solver", default="fgmres", choices=["fgmres", "richardson"])
+    ap.add_argument("--nu", type=int, default=2, help="pre- and post-smoothing sweeps")
+    ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", default=None, choices=["gs", "resid", "solve"],
                     help="run only a profiling target (for ncu): 8 finest-level colour sweeps, "
@@ -53,7 +60,8 @@ def workload(n, p):
 
 def config(args, prob):
     return {"workload": "2d-viscous-stress-varmu-dirichlet3-stress1", "n": [args.n, args.n], "p": args.p,
-            "dofs": prob.n_dofs, "nu": [1, 1], "rtol": 1e-10,
+            "dofs": prob.n_dofs, "nu": [args.nu, args.nu], "rtol": 1e-10,
+            "outer": "%s(%d) in FP64" % (args.solver, args.restart) if args.solver == "fgmres" else "richardson",
             "cache": "inputs larger than L2 (element blocks >= 3.6 GB per solve)",
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -197,7 +205,8 @@ def run_profile(args):
     from paper_1911_05888_gb300.solver import StokesMG
     prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16}[args.precision]
     prob = workload(args.n, args.p)
-    mg = StokesMG(prob, precision=prec)
+    mg = StokesMG(prob, precision=prec, nu=(args.nu, args.nu))
+    mg.ctx.set_solver(native.FGMRES if args.solver == "fgmres" else native.RICHARDSON, args.restart)
     torch.cuda.synchronize()
     vdt = torch.float64 if prec == native.FP64 else torch.float32
     if args.profile in ("gs", "resid"):
@@ -235,9 +244,13 @@ def run_native(args):
     prob = workload(args.n, args.p)
 
     t0 = time.perf_counter()
-    mg = StokesMG(prob, precision=prec, device=local)
+    mg = StokesMG(prob, precision=prec, device=local, nu=(args.nu, args.nu))
     setup_s = time.perf_counter() - t0
-    mg64 = StokesMG(prob, precision=native.FP64, device=local) if prec != native.FP64 else mg
+    mg64 = StokesMG(prob, precision=native.FP64, device=local, nu=(args.nu, args.nu)) \
+        if prec != native.FP64 else mg
+    method = native.FGMRES if args.solver == "fgmres" else native.RICHARDSON
+    for m_ in (mg, mg64):
+        m_.ctx.set_solver(method, args.restart)
     b_host = mg.rhs().ravel()
     b = torch.from_numpy(b_host).cuda()
     x = torch.zeros_like(b)

@@ -226,6 +226,16 @@ int stk_solve(stk_ctx* ctx, double* x_dev, const double* b_dev, double rtol, int
 int stk_residual_norm_static(stk_ctx* ctx, const double* x_dev, const double* b_dev, double* r_dev,
                              double* norm2_dev, void* stream);
 
+/*
+ * Outer iteration of stk_solve: method 0 = iterative refinement
+ * x <- x + V(0, b - A x) (default); method 1 = flexible GMRES(restart) in
+ * FP64 with one V-cycle (of the stk_set_cycle precision, from a zero guess)
+ * as the right preconditioner -- Section 3 uses the V-cycle as a GMRES
+ * preconditioner; the flexible form keeps the FP64 residual exact when the
+ * cycle runs in FP32/BF16.  restart in 1..100.
+ */
+int stk_set_solver(stk_ctx* ctx, int method, int restart);
+
 /* Number of kernel launches the library enqueued since the context was
  * created (all of them are this library's own kernels). */
 int stk_launch_count(stk_ctx* ctx, int64_t* count);

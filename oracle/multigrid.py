@@ -177,6 +177,56 @@ class Multigrid:
             x += self.precondition(r, **kw)
         return x, hist
 
+    def fgmres(self, b, x0=None, rtol=1e-10, maxit=200, restart=30, **kw):
+        """Flexible right-preconditioned GMRES with the V-cycle as the
+        preconditioner (Section 3 uses V as a GMRES preconditioner; the flexible
+        form also admits a preconditioner that changes between iterations).
+        Returns (x, history of ||b - A x|| / ||b|| per iteration)."""
+        A = self.A
+        x = np.zeros_like(b) if x0 is None else x0.copy()
+        bn = np.linalg.norm(b)
+        r = b - A @ x
+        hist = [np.linalg.norm(r) / bn]
+        it = 0
+        while hist[-1] > rtol and it < maxit:
+            beta = np.linalg.norm(r)
+            V = [r / beta]
+            Z = []
+            H = np.zeros((restart + 1, restart))
+            g = np.zeros(restart + 1)
+            g[0] = beta
+            cs, sn = np.zeros(restart), np.zeros(restart)
+            k = 0
+            for j in range(restart):
+                z = self.precondition(V[j], **kw)
+                Z.append(z)
+                w = A @ z
+                for i in range(j + 1):
+                    H[i, j] = np.dot(V[i], w)
+                    w = w - H[i, j] * V[i]
+                H[j + 1, j] = np.linalg.norm(w)
+                V.append(w / H[j + 1, j] if H[j + 1, j] > 0 else w)
+                for i in range(j):
+                    t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                    H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                    H[i, j] = t
+                den = np.hypot(H[j, j], H[j + 1, j])
+                cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+                H[j, j] = den
+                H[j + 1, j] = 0.0
+                g[j + 1] = -sn[j] * g[j]
+                g[j] = cs[j] * g[j]
+                k = j + 1
+                it += 1
+                hist.append(abs(g[j + 1]) / bn)
+                if hist[-1] <= rtol or it >= maxit:
+                    break
+            y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+            x = x + np.array(Z[:k]).T @ y
+            r = b - A @ x
+            hist[-1] = np.linalg.norm(r) / bn
+        return x, hist
+
     def gmres_rho(self, x0, reduction=1e-8, maxit=200, **kw):
         """eq. (rho): average reduction per iteration of left-preconditioned
         GMRES on V A x = V b with b = 0 from x0; returns (rho, iterations)."""

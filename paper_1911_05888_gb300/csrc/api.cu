@@ -21,15 +21,20 @@ cudaError_t launch_element(const Pattern& pat, int storage, int mode, int pos0, 
                            const int* perm, const int* nbr, const void* cpl, const void* mat,
                            const void* b, void* x, void* r, cudaStream_t st);
 cudaError_t launch_restrict(int vec64, int d, int s, int nb, const int* nc, const int* nf, int64_t nec,
-                            const double* P, const void* r, void* rc, cudaStream_t st);
-cudaError_t launch_prolong(int vec64, int d, int s, int nb, const int* nf, const int* nc, int64_t nef,
-                           const double* P, const void* xc, void* x, cudaStream_t st);
+                            const void* P, const void* r, void* rc, cudaStream_t st);
+cudaError_t launch_prolong(int vec64, int d, int s, int nb, const int* nf, const int* nc, int64_t nec,
+                           const void* PT, const void* xc, void* x, cudaStream_t st);
 cudaError_t launch_bottom(int vec64, int64_t n, const double* pinv, const void* b, void* x,
                           cudaStream_t st);
 cudaError_t launch_axpy(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st);
 cudaError_t launch_convert(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st);
 cudaError_t launch_to_bf16(int64_t n, void* y, const double* x, cudaStream_t st);
 cudaError_t launch_sumsq(int64_t n, const double* x, double* part, double* out, cudaStream_t st);
+cudaError_t launch_multidot(int64_t n, int k, const double* V, int64_t ldv, const double* w, double* part,
+                            double* out, cudaStream_t st);
+cudaError_t launch_multiaxpy(int64_t n, int k, double alpha, const double* coef, const double* V, int64_t ldv,
+                             double* w, cudaStream_t st);
+cudaError_t launch_scale(int64_t n, double s, const double* x, double* y, cudaStream_t st);
 }  // namespace stk
 
 using namespace stk;
@@ -85,6 +90,13 @@ void free_device(Ctx& c) {
   c.allocations.clear();
   if (c.norm_host) cudaFreeHost(c.norm_host);
   c.norm_host = nullptr;
+  if (c.khost) cudaFreeHost(c.khost);
+  c.khost = nullptr;
+  c.kV = c.kZ = c.kw = c.kzero = c.kpart = c.kdots = nullptr;
+  c.kcap = 0;
+  if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
+  c.cycle_graph = nullptr;
+  c.cycle_graph_prec = -1;
   if (c.graph) cudaGraphExecDestroy(c.graph);
   c.graph = nullptr;
   c.graph_x = c.graph_b = nullptr;
@@ -263,12 +275,12 @@ void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t
   ck(launch_element(c.pat, prec, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[prec], D.dia[prec], b, x,
                     D.vr[vi], st),
      "residual launch");
-  ck(launch_restrict(vi == 0, c.d, c.s, c.nb, Dc.n, D.n, Dc.ne, c.child_mats, D.vr[vi], Dc.vb[vi], st),
+  ck(launch_restrict(vi == 0, c.d, c.s, c.nb, Dc.n, D.n, Dc.ne, c.child_P[vi], D.vr[vi], Dc.vb[vi], st),
      "restrict launch");
   ck(cudaMemsetAsync(Dc.vx[vi], 0, (size_t)Dc.ne * c.nb * (vi == 0 ? 8 : 4), st), "memset");
   c.launches += 2;  // residual + restriction
   enqueue_cycle(c, prec, l + 1, Dc.vx[vi], Dc.vb[vi], st);
-  ck(launch_prolong(vi == 0, c.d, c.s, c.nb, D.n, Dc.n, D.ne, c.child_mats, Dc.vx[vi], x, st),
+  ck(launch_prolong(vi == 0, c.d, c.s, c.nb, D.n, Dc.n, Dc.ne, c.child_PT[vi], Dc.vx[vi], x, st),
      "prolong launch");
   c.launches++;
   enqueue_smooth(c, prec, l, c.nu2, x, b, st);
@@ -323,6 +335,180 @@ int64_t count_points(const Ctx& c, int kind) {
   std::vector<double> xyz;
   face_points(c, kind, xyz, nullptr);
   return (int64_t)(xyz.size() / c.d);
+}
+
+// ---- flexible GMRES with the V-cycle as right preconditioner ----------------
+void ensure_krylov(Ctx& c) {
+  if (c.kcap >= c.restart && c.kV) return;
+  int64_t n0 = level_ne(c, 0) * c.nb;
+  int m = c.restart;
+  c.kV = (double*)dalloc(c, (size_t)(m + 1) * n0 * 8);
+  c.kZ = (double*)dalloc(c, (size_t)m * n0 * 8);
+  c.kw = (double*)dalloc(c, (size_t)n0 * 8);
+  c.kzero = (double*)dalloc(c, (size_t)n0 * 8);
+  ck(cudaMemset(c.kzero, 0, (size_t)n0 * 8), "memset");
+  c.kpart = (double*)dalloc(c, (size_t)1024 * 136 * 8);
+  c.kdots = (double*)dalloc(c, 272 * 8);
+  if (!c.khost) ck(cudaMallocHost(&c.khost, 272 * sizeof(double)), "cudaMallocHost");
+  c.kcap = m;
+}
+
+// The V-cycle on the level-0 work vectors (b0 -> x0, x0 zeroed first) as a graph.
+void ensure_cycle_graph(Ctx& c, cudaStream_t st) {
+  if (c.cycle_graph && c.cycle_graph_prec == c.precision) return;
+  if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
+  c.cycle_graph = nullptr;
+  int vi = c.precision == STK_FP64 ? 0 : 1;
+  DevLevel& D0 = c.dev[0];
+  int64_t n0 = level_ne(c, 0) * c.nb;
+  cudaGraph_t g;
+  int64_t before = c.launches;
+  ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    ck(cudaMemsetAsync(D0.vx[vi], 0, (size_t)n0 * (vi == 0 ? 8 : 4), st), "memset");
+    enqueue_cycle(c, c.precision, 0, D0.vx[vi], D0.vb[vi], st);
+  } catch (...) {
+    cudaStreamEndCapture(st, &g);
+    c.launches = before;
+    throw;
+  }
+  ck(cudaStreamEndCapture(st, &g), "end capture");
+  ck(cudaGraphInstantiate(&c.cycle_graph, g, 0), "graph instantiate");
+  cudaGraphDestroy(g);
+  c.cycle_graph_kernels = c.launches - before;
+  c.launches = before;
+  c.cycle_graph_prec = c.precision;
+}
+
+// z = V(0, v): one V-cycle of the configured precision from a zero guess.
+void precondition(Ctx& c, const double* v, double* z, cudaStream_t st) {
+  int64_t n0 = level_ne(c, 0) * c.nb;
+  DevLevel& D0 = c.dev[0];
+  if (c.precision == STK_FP64) {
+    ck(cudaMemcpyAsync(D0.vb[0], v, (size_t)n0 * 8, cudaMemcpyDeviceToDevice, st), "copy");
+  } else {
+    ck(launch_convert(0, 1, n0, D0.vb[1], v, st), "convert");
+    c.launches++;
+  }
+  ck(cudaGraphLaunch(c.cycle_graph, st), "cycle graph");
+  c.launches += c.cycle_graph_kernels;
+  if (c.precision == STK_FP64) {
+    ck(cudaMemcpyAsync(z, D0.vx[0], (size_t)n0 * 8, cudaMemcpyDeviceToDevice, st), "copy");
+  } else {
+    ck(launch_convert(1, 0, n0, z, D0.vx[1], st), "convert");
+    c.launches++;
+  }
+}
+
+// h[0..k) = V[0..k)^T w on the host.
+void host_dots(Ctx& c, int k, const double* V, const double* w, double* h, cudaStream_t st) {
+  int64_t n0 = level_ne(c, 0) * c.nb;
+  ck(launch_multidot(n0, k, V, n0, w, c.kpart, c.kdots, st), "multidot");
+  c.launches += 2;
+  ck(cudaMemcpyAsync(c.khost, c.kdots, (size_t)k * 8, cudaMemcpyDeviceToHost, st), "copy dots");
+  ck(cudaStreamSynchronize(st), "sync");
+  std::copy(c.khost, c.khost + k, h);
+}
+
+// w = alpha w + sum_i coef[i] V[i] (coef from the host).
+void host_axpy(Ctx& c, int k, double alpha, const double* coef, const double* V, double* w, cudaStream_t st) {
+  int64_t n0 = level_ne(c, 0) * c.nb;
+  double* hc = c.khost + 136;
+  std::copy(coef, coef + k, hc);
+  ck(cudaMemcpyAsync(c.kdots + 136, hc, (size_t)std::max(k, 1) * 8, cudaMemcpyHostToDevice, st), "copy coef");
+  ck(launch_multiaxpy(n0, k, alpha, c.kdots + 136, V, n0, w, st), "multiaxpy");
+  c.launches++;
+  ck(cudaStreamSynchronize(st), "sync");   // hc is reused by the next call
+}
+
+double host_norm(Ctx& c, const double* v, cudaStream_t st) {
+  enqueue_norm(c, v, st);
+  ck(cudaStreamSynchronize(st), "sync");
+  return std::sqrt(c.norm_host[0]);
+}
+
+// Returns the iteration count; rel holds the final true relative residual.
+int fgmres(Ctx& c, double* x, const double* b, double rtol, int maxit, double* hist, double bnorm,
+           double& rel, cudaStream_t st) {
+  ensure_krylov(c);
+  ensure_cycle_graph(c, st);
+  int64_t n0 = level_ne(c, 0) * c.nb;
+  const int m = c.restart;
+  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), h(m + 1), h2(m + 1), y(m);
+  enqueue_residual64(c, x, b, c.r64, st);
+  double beta = host_norm(c, c.r64, st);
+  rel = beta / bnorm;
+  double rel0 = rel;
+  int it = 0;
+  while (rel > rtol && it < maxit) {
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    ck(launch_scale(n0, 1.0 / beta, c.r64, c.kV, st), "scale");
+    c.launches++;
+    int k = 0;
+    for (int j = 0; j < m && it < maxit; ++j) {
+      double* vj = c.kV + (size_t)j * n0;
+      double* zj = c.kZ + (size_t)j * n0;
+      precondition(c, vj, zj, st);
+      // w = A z_j, computed as -(0 - A z_j) by the residual kernel.
+      enqueue_residual64(c, zj, c.kzero, c.kw, st);
+      // Classical Gram-Schmidt, twice.
+      host_dots(c, j + 1, c.kV, c.kw, h.data(), st);
+      for (int i = 0; i <= j; ++i) h[i] = -h[i];
+      std::vector<double> negh(j + 1);
+      for (int i = 0; i <= j; ++i) negh[i] = -h[i];
+      host_axpy(c, j + 1, -1.0, negh.data(), c.kV, c.kw, st);
+      host_dots(c, j + 1, c.kV, c.kw, h2.data(), st);
+      for (int i = 0; i <= j; ++i) {
+        negh[i] = -h2[i];
+        h[i] += h2[i];
+      }
+      host_axpy(c, j + 1, 1.0, negh.data(), c.kV, c.kw, st);
+      double hn = host_norm(c, c.kw, st);
+      if (!std::isfinite(hn)) {
+        rel = hn;
+        return it + 1;
+      }
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i];
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0) {
+        ck(launch_scale(n0, 1.0 / hn, c.kw, c.kV + (size_t)(j + 1) * n0, st), "scale");
+        c.launches++;
+      }
+      for (int i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+      double den = std::hypot(a, bb);
+      cs[j] = a / den;
+      sn[j] = bb / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      k = j + 1;
+      ++it;
+      rel = std::fabs(g[j + 1]) / bnorm;
+      if (hist) hist[it] = rel;
+      if (rel <= rtol || !std::isfinite(rel) || rel > 1e6 * rel0) break;
+    }
+    // x += Z y with H[:k,:k] y = g[:k]
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int jj = i + 1; jj < k; ++jj) acc -= H[(size_t)i * m + jj] * y[jj];
+      y[i] = acc / H[(size_t)i * m + i];
+    }
+    host_axpy(c, k, 1.0, y.data(), c.kZ, x, st);
+    enqueue_residual64(c, x, b, c.r64, st);
+    beta = host_norm(c, c.r64, st);
+    rel = beta / bnorm;
+    if (hist) hist[it] = rel;
+    if (!std::isfinite(rel) || rel > 1e6 * rel0) break;
+  }
+  return it;
 }
 
 }  // namespace
@@ -509,8 +695,20 @@ int stk_setup(stk_ctx* c, void* stream) {
     setup_bottom(*c);
     std::vector<double> P;
     child_matrices(c->d, c->p, P);
-    c->child_mats = (double*)dalloc(*c, P.size() * sizeof(double));
-    ck(cudaMemcpy(c->child_mats, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice), "copy P");
+    int s = c->s, nch = 1 << c->d;
+    std::vector<double> PT(P.size());
+    for (int ch = 0; ch < nch; ++ch)
+      for (int a = 0; a < s; ++a)
+        for (int b2 = 0; b2 < s; ++b2) PT[((size_t)ch * s + b2) * s + a] = P[((size_t)ch * s + a) * s + b2];
+    std::vector<float> P32(P.begin(), P.end()), PT32(PT.begin(), PT.end());
+    c->child_P[0] = dalloc(*c, P.size() * 8);
+    c->child_PT[0] = dalloc(*c, P.size() * 8);
+    c->child_P[1] = dalloc(*c, P.size() * 4);
+    c->child_PT[1] = dalloc(*c, P.size() * 4);
+    ck(cudaMemcpy(c->child_P[0], P.data(), P.size() * 8, cudaMemcpyHostToDevice), "copy P");
+    ck(cudaMemcpy(c->child_PT[0], PT.data(), P.size() * 8, cudaMemcpyHostToDevice), "copy P");
+    ck(cudaMemcpy(c->child_P[1], P32.data(), P.size() * 4, cudaMemcpyHostToDevice), "copy P");
+    ck(cudaMemcpy(c->child_PT[1], PT32.data(), P.size() * 4, cudaMemcpyHostToDevice), "copy P");
     ck(cudaStreamSynchronize(st), "setup sync");
     ck(cudaDeviceSynchronize(), "setup sync");
     c->ready = true;
@@ -641,7 +839,7 @@ int stk_restrict(stk_ctx* c, int level, const double* r, double* rc, void* strea
     if (level < 0 || level >= nlevels(*c) - 1 || !r || !rc) return fail(c, STK_ERR_INVALID_ARG, "bad args");
     DevLevel& D = c->dev[level];
     DevLevel& Dc = c->dev[level + 1];
-    ck(launch_restrict(1, c->d, c->s, c->nb, Dc.n, D.n, Dc.ne, c->child_mats, r, rc, (cudaStream_t)stream),
+    ck(launch_restrict(1, c->d, c->s, c->nb, Dc.n, D.n, Dc.ne, c->child_P[0], r, rc, (cudaStream_t)stream),
        "restrict");
     c->launches++;
     return STK_OK;
@@ -654,7 +852,7 @@ int stk_prolong(stk_ctx* c, int level, const double* xc, double* x, void* stream
     if (level < 0 || level >= nlevels(*c) - 1 || !xc || !x) return fail(c, STK_ERR_INVALID_ARG, "bad args");
     DevLevel& D = c->dev[level];
     DevLevel& Dc = c->dev[level + 1];
-    ck(launch_prolong(1, c->d, c->s, c->nb, D.n, Dc.n, D.ne, c->child_mats, xc, x, (cudaStream_t)stream),
+    ck(launch_prolong(1, c->d, c->s, c->nb, D.n, Dc.n, Dc.ne, c->child_PT[0], xc, x, (cudaStream_t)stream),
        "prolong");
     c->launches++;
     return STK_OK;
@@ -690,6 +888,12 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
     double rel = std::sqrt(c->norm_host[0]) / bnorm, rel0 = rel;
     if (hist) hist[0] = rel;
     int it = 0;
+    if (c->solver == 1) {
+      it = fgmres(*c, x, b, rtol, maxit, hist, bnorm, rel, st);
+      if (iters_out) *iters_out = it;
+      if (!std::isfinite(rel) || rel > 1e6 * rel0) return fail(c, STK_ERR_DIVERGED, "outer iteration diverged");
+      return STK_OK;
+    }
     // Capture one outer iteration as a CUDA graph (re-captured when the
     // caller's vectors or the precision change).
     if (!c->graph || c->graph_x != x || c->graph_b != b || c->graph_prec != c->precision) {
@@ -726,6 +930,20 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
       }
     }
     if (iters_out) *iters_out = it;
+    return STK_OK;
+  });
+}
+
+int stk_set_solver(stk_ctx* c, int method, int restart) {
+  return guard(c, [&]() -> int {
+    if (method < 0 || method > 1 || restart < 1 || restart > 100)
+      return fail(c, STK_ERR_INVALID_ARG, "bad solver options (method 0/1, restart 1..100)");
+    c->solver = method;
+    if (restart != c->restart) {
+      c->restart = restart;
+      c->kV = nullptr;   // re-sized on the next solve (old buffers stay owned until destroy)
+      c->kcap = 0;
+    }
     return STK_OK;
   });
 }

@@ -171,47 +171,66 @@ static size_t element_smem(const Pattern& pat) {
 }
 
 // ---- restriction / prolongation (injection and its transpose) ---------------
-// child_mats[ch][a][b]: fine coefficient a of coarse mode b for child ch.
+// P[ch][a][b]: fine coefficient a of coarse mode b for child ch (P_f of the
+// scalar injection; the (d+1) variables share it).  One CTA per coarse
+// element at a time: the children's residual blocks (restriction) or the
+// coarse block (prolongation) are staged in shared memory with coalesced
+// loads; arithmetic is in the vector precision TX.
 template <typename TX>
-__global__ void restrict_kernel(int d, int s, int nb, int nc0, int nc1, int nc2, int nf0, int nf1,
-                                int64_t nec, const double* __restrict__ P,
-                                const TX* __restrict__ r, TX* __restrict__ rc) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nec * nb) return;
-  const int64_t C = idx / nb;
-  const int vb = (int)(idx - C * nb);
-  const int v = vb / s, bm = vb - v * s;
-  int I[3] = {(int)(C % nc0), (int)((C / nc0) % nc1), (int)(C / ((int64_t)nc0 * nc1))};
-  double acc = 0.0;
-  for (int ch = 0; ch < (1 << d); ++ch) {
-    int f0 = 2 * I[0] + (ch & 1), f1 = 2 * I[1] + ((ch >> 1) & 1), f2 = 2 * I[2] + ((ch >> 2) & 1);
-    int64_t f = f0 + (int64_t)nf0 * (f1 + (int64_t)nf1 * f2);
-    if (d == 2) f = f0 + (int64_t)nf0 * f1;
-    const double* Pc = P + (size_t)ch * s * s;
-    const TX* rf = r + (size_t)f * nb + v * s;
-    for (int a = 0; a < s; ++a) acc += Pc[a * s + bm] * (double)rf[a];
+__global__ void restrict_kernel(int d, int s, int nb, int nc0, int nc1, int nf0, int nf1, int64_t nec,
+                                const TX* __restrict__ P, const TX* __restrict__ r, TX* __restrict__ rc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nch = 1 << d;
+  TX* rs = reinterpret_cast<TX*>(smem_raw);
+  const TX* Ps = P;   // small, read through the read-only cache
+  for (int64_t C = blockIdx.x; C < nec; C += gridDim.x) {
+    const int I0 = (int)(C % nc0), I1 = (int)((C / nc0) % nc1), I2 = (int)(C / ((int64_t)nc0 * nc1));
+    __syncthreads();
+    for (int i = threadIdx.x; i < nch * nb; i += blockDim.x) {
+      const int ch = i / nb, k = i - ch * nb;
+      const int f0 = 2 * I0 + (ch & 1), f1 = 2 * I1 + ((ch >> 1) & 1), f2 = 2 * I2 + ((ch >> 2) & 1);
+      const int64_t f = (d == 2) ? f0 + (int64_t)nf0 * f1 : f0 + (int64_t)nf0 * (f1 + (int64_t)nf1 * f2);
+      rs[i] = r[f * nb + k];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nb; o += blockDim.x) {
+      const int v = o / s, bm = o - v * s;
+      TX acc = 0;
+      for (int ch = 0; ch < nch; ++ch) {
+        const TX* pc = Ps + ch * s * s + bm;
+        const TX* rr = rs + ch * nb + v * s;
+        for (int a = 0; a < s; ++a) acc += pc[a * s] * rr[a];
+      }
+      rc[C * nb + o] = acc;
+    }
   }
-  rc[(size_t)C * nb + vb] = (TX)acc;
-  (void)nc2;
 }
 
+// PT[ch][b][a] = P[ch][a][b] (transposed for conflict-free shared reads).
 template <typename TX>
-__global__ void prolong_kernel(int d, int s, int nb, int nf0, int nf1, int nc0, int nc1,
-                               int64_t nef, const double* __restrict__ P,
-                               const TX* __restrict__ xc, TX* __restrict__ x) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nef * nb) return;
-  const int64_t f = idx / nb;
-  const int va = (int)(idx - f * nb);
-  const int v = va / s, am = va - v * s;
-  int fi0 = (int)(f % nf0), fi1 = (int)((f / nf0) % nf1), fi2 = (int)(f / ((int64_t)nf0 * nf1));
-  int ch = (fi0 & 1) | ((fi1 & 1) << 1) | ((d == 3 ? (fi2 & 1) : 0) << 2);
-  int64_t C = (fi0 >> 1) + (int64_t)nc0 * ((fi1 >> 1) + (int64_t)nc1 * (d == 3 ? (fi2 >> 1) : 0));
-  const double* Pc = P + (size_t)ch * s * s + (size_t)am * s;
-  const TX* xcc = xc + (size_t)C * nb + v * s;
-  double acc = 0.0;
-  for (int bm = 0; bm < s; ++bm) acc += Pc[bm] * (double)xcc[bm];
-  x[(size_t)f * nb + va] = (TX)((double)x[(size_t)f * nb + va] + acc);
+__global__ void prolong_kernel(int d, int s, int nb, int nf0, int nf1, int nc0, int nc1, int64_t nec,
+                               const TX* __restrict__ PT, const TX* __restrict__ xc, TX* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nch = 1 << d;
+  TX* xs = reinterpret_cast<TX*>(smem_raw);
+  const TX* Ps = PT;  // small, read through the read-only cache
+  for (int64_t C = blockIdx.x; C < nec; C += gridDim.x) {
+    const int I0 = (int)(C % nc0), I1 = (int)((C / nc0) % nc1), I2 = (int)(C / ((int64_t)nc0 * nc1));
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) xs[i] = xc[C * nb + i];
+    __syncthreads();
+    for (int o = threadIdx.x; o < nch * nb; o += blockDim.x) {
+      const int ch = o / nb, va = o - ch * nb;
+      const int v = va / s, am = va - v * s;
+      const int f0 = 2 * I0 + (ch & 1), f1 = 2 * I1 + ((ch >> 1) & 1), f2 = 2 * I2 + ((ch >> 2) & 1);
+      const int64_t f = (d == 2) ? f0 + (int64_t)nf0 * f1 : f0 + (int64_t)nf0 * (f1 + (int64_t)nf1 * f2);
+      const TX* pc = Ps + ch * s * s + am;
+      const TX* xv = xs + v * s;
+      TX acc = 0;
+      for (int bm = 0; bm < s; ++bm) acc += pc[bm * s] * xv[bm];
+      x[f * nb + va] += acc;
+    }
+  }
 }
 
 // ---- bottom solve: x = A_c^+ b (FP64, one warp per row) ---------------------
@@ -330,31 +349,32 @@ cudaError_t launch_element(const Pattern& pat, int storage, int mode, int pos0, 
   }
 }
 
+// P: [child][s][s] in the vector precision; PT its per-child transpose.
 cudaError_t launch_restrict(int vec64, int d, int s, int nb, const int* nc, const int* nf, int64_t nec,
-                            const double* P, const void* r, void* rc, cudaStream_t st) {
-  int64_t n = nec * nb;
-  int bs = 256;
-  int64_t grid = (n + bs - 1) / bs;
+                            const void* P, const void* r, void* rc, cudaStream_t st) {
+  int grid = (int)std::min<int64_t>(nec, (int64_t)num_sms() * 8);
+  size_t es = vec64 ? 8 : 4;
+  size_t smem = (size_t)(1 << d) * nb * es;
   if (vec64)
-    restrict_kernel<double><<<grid, bs, 0, st>>>(d, s, nb, nc[0], nc[1], nc[2], nf[0], nf[1], nec, P,
-                                                 (const double*)r, (double*)rc);
+    restrict_kernel<double><<<grid, 128, smem, st>>>(d, s, nb, nc[0], nc[1], nf[0], nf[1], nec,
+                                                     (const double*)P, (const double*)r, (double*)rc);
   else
-    restrict_kernel<float><<<grid, bs, 0, st>>>(d, s, nb, nc[0], nc[1], nc[2], nf[0], nf[1], nec, P,
-                                                (const float*)r, (float*)rc);
+    restrict_kernel<float><<<grid, 128, smem, st>>>(d, s, nb, nc[0], nc[1], nf[0], nf[1], nec,
+                                                    (const float*)P, (const float*)r, (float*)rc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong(int vec64, int d, int s, int nb, const int* nf, const int* nc, int64_t nef,
-                           const double* P, const void* xc, void* x, cudaStream_t st) {
-  int64_t n = nef * nb;
-  int bs = 256;
-  int64_t grid = (n + bs - 1) / bs;
+cudaError_t launch_prolong(int vec64, int d, int s, int nb, const int* nf, const int* nc, int64_t nec,
+                           const void* PT, const void* xc, void* x, cudaStream_t st) {
+  int grid = (int)std::min<int64_t>(nec, (int64_t)num_sms() * 8);
+  size_t es = vec64 ? 8 : 4;
+  size_t smem = (size_t)nb * es;
   if (vec64)
-    prolong_kernel<double><<<grid, bs, 0, st>>>(d, s, nb, nf[0], nf[1], nc[0], nc[1], nef, P,
-                                                (const double*)xc, (double*)x);
+    prolong_kernel<double><<<grid, 128, smem, st>>>(d, s, nb, nf[0], nf[1], nc[0], nc[1], nec,
+                                                    (const double*)PT, (const double*)xc, (double*)x);
   else
-    prolong_kernel<float><<<grid, bs, 0, st>>>(d, s, nb, nf[0], nf[1], nc[0], nc[1], nef, P,
-                                               (const float*)xc, (float*)x);
+    prolong_kernel<float><<<grid, 128, smem, st>>>(d, s, nb, nf[0], nf[1], nc[0], nc[1], nec,
+                                                   (const float*)PT, (const float*)xc, (float*)x);
   return cudaGetLastError();
 }
 
@@ -403,6 +423,91 @@ cudaError_t launch_sumsq(int64_t n, const double* x, double* part, double* out, 
   if (grid < 1) grid = 1;
   sumsq_partial_kernel<<<grid, 256, 0, st>>>(n, x, part);
   sum_final_kernel<<<1, 256, 0, st>>>(grid, part, out);
+  return cudaGetLastError();
+}
+
+}  // namespace stk
+
+namespace stk {
+
+// ---- Krylov helpers (FP64) ---------------------------------------------------
+constexpr int kDotBlocks = 1024;   // fixed grid: deterministic reduction order
+
+// part[blk][i] = partial of sum_e V[i][e] w[e] over the entries of block blk.
+__global__ void multidot_kernel(int64_t n, int k, const double* __restrict__ V, int64_t ldv,
+                                const double* __restrict__ w, double* __restrict__ part) {
+  __shared__ double sh[8][256];
+  for (int i0 = 0; i0 < k; i0 += 8) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int ni = min(8, k - i0);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const double we = w[e];
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t < ni) acc[t] += V[(int64_t)(i0 + t) * ldv + e] * we;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) sh[t][threadIdx.x] = acc[t];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) sh[t][threadIdx.x] += sh[t][threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x < ni) part[(int64_t)blockIdx.x * k + i0 + threadIdx.x] = sh[threadIdx.x][0];
+    __syncthreads();
+  }
+}
+
+__global__ void multidot_final_kernel(int k, int nblk, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += part[(int64_t)b * k + i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = sh[0];
+}
+
+// w = alpha w + sum_i coef[i] V[i]
+__global__ void multiaxpy_kernel(int64_t n, int k, double alpha, const double* __restrict__ coef,
+                                 const double* __restrict__ V, int64_t ldv, double* __restrict__ w) {
+  __shared__ double c[128];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) c[i] = coef[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = alpha * w[e];
+    for (int i = 0; i < k; ++i) acc += c[i] * V[(int64_t)i * ldv + e];
+    w[e] = acc;
+  }
+}
+
+__global__ void scale_kernel(int64_t n, double s, const double* __restrict__ x, double* __restrict__ y) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = s * x[i];
+}
+
+cudaError_t launch_multidot(int64_t n, int k, const double* V, int64_t ldv, const double* w, double* part,
+                            double* out, cudaStream_t st) {
+  multidot_kernel<<<kDotBlocks, 256, 0, st>>>(n, k, V, ldv, w, part);
+  multidot_final_kernel<<<k, 256, 0, st>>>(k, kDotBlocks, part, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multiaxpy(int64_t n, int k, double alpha, const double* coef, const double* V, int64_t ldv,
+                             double* w, cudaStream_t st) {
+  multiaxpy_kernel<<<num_sms() * 8, 256, 0, st>>>(n, k, alpha, coef, V, ldv, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(int64_t n, double s, const double* x, double* y, cudaStream_t st) {
+  scale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s, x, y);
   return cudaGetLastError();
 }
 

@@ -87,8 +87,9 @@ struct Ctx {
   double* bot_b64 = nullptr;      // FP64 staging for mixed cycles
   double* bot_x64 = nullptr;
   // transfer matrices P_f (2^d children), [child][s][s] row-major: fine = P coarse
-  double* child_mats = nullptr;
-  float* child_mats32 = nullptr;
+  // index 0: double, 1: float; PT[child][b][a] is the per-child transpose
+  void* child_P[2] = {nullptr, nullptr};
+  void* child_PT[2] = {nullptr, nullptr};
   // outer-iteration work
   double* r64 = nullptr;
   double* c64 = nullptr;
@@ -102,6 +103,20 @@ struct Ctx {
   int graph_prec = -1;
   int64_t graph_kernels = 0;
   cudaStream_t stream = nullptr;
+  // outer iteration: 0 Richardson, 1 flexible GMRES(restart)
+  int solver = 0, restart = 30;
+  double* kV = nullptr;       // (restart+1) Krylov basis vectors, FP64
+  double* kZ = nullptr;       // restart preconditioned vectors, FP64
+  double* kw = nullptr;       // work vector
+  double* kzero = nullptr;    // zero vector (b of the matvec)
+  double* kpart = nullptr;    // multi-dot partials
+  double* kdots = nullptr;    // multi-dot results / coefficients (device)
+  double* khost = nullptr;    // pinned host staging (dots, coefficients)
+  int kcap = 0;               // restart the buffers were sized for
+  // V-cycle alone on the level-0 work vectors, as a CUDA graph
+  cudaGraphExec_t cycle_graph = nullptr;
+  int cycle_graph_prec = -1;
+  int64_t cycle_graph_kernels = 0;
   std::vector<void*> allocations;
 };
 

@@ -19,6 +19,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "TIMEOUT", -5:
           -6: "NOT_SETUP", -7: "CUDA"}
 BC_PERIODIC, BC_DIRICHLET, BC_STRESS = 0, 1, 2
 FP64, FP32, BF16 = 0, 1, 2
+RICHARDSON, FGMRES = 0, 1
 PTS_VOLUME, PTS_INTERIOR_FACE, PTS_BOUNDARY_FACE = 0, 1, 2
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
@@ -53,6 +54,7 @@ SIGNATURES = {
     "stk_bottom_solve": [_vp, _vp, _vp, _vp],
     "stk_solve": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _c_int_p, _c_dbl_p, _vp],
     "stk_residual_norm_static": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "stk_set_solver": [_vp, ctypes.c_int, ctypes.c_int],
     "stk_launch_count": [_vp, _c_i64_p],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
@@ -244,6 +246,9 @@ class Context:
         scalar norm2, using only the library's fixed static scratch."""
         self._check(self.lib.stk_residual_norm_static(self.h, _ptr(x), _ptr(b), _ptr(r), _ptr(norm2),
                                                       _stream(stream)), "stk_residual_norm_static")
+
+    def set_solver(self, method, restart=30):
+        self._check(self.lib.stk_set_solver(self.h, method, restart), "stk_set_solver")
 
     def launch_count(self):
         n = ctypes.c_int64()

@@ -190,3 +190,27 @@ def test_invalid_arguments_are_rejected():
         x = torch.zeros(10, dtype=torch.float64, device="cuda")
         ctx.vcycle(x, x)                                             # not set up
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [native.FP64, native.FP32, native.BF16])
+@pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-unsteady-p2"])
+def test_fgmres_solve(name, precision):
+    """Flexible GMRES with the V-cycle as right preconditioner (Section 3):
+    reaches 1e-10 in FP64; in FP64 it follows the oracle's FGMRES."""
+    prob, gpu64, orc = get(name)
+    _, gpu, _ = get(name, precision)
+    b = gpu64.rhs().ravel()
+    bd = dev(b)
+    x = torch.zeros_like(bd)
+    gpu.ctx.set_solver(native.FGMRES, 30)
+    try:
+        it, hist = gpu.ctx.solve(x, bd, rtol=1e-10, maxit=200)
+    finally:
+        gpu.ctx.set_solver(native.RICHARDSON, 30)
+    assert hist[-1] <= 1e-10, hist
+    xo, ho = orc.fgmres(b, rtol=1e-10, maxit=200, restart=30)
+    if precision == native.FP64:
+        assert abs(it - (len(ho) - 1)) <= 1
+        assert rel(x.cpu().numpy(), xo) <= 1e-9
+    else:
+        assert it <= (len(ho) - 1) + 3

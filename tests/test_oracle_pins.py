@@ -388,3 +388,20 @@ def test_bottom_solve_is_least_squares_solution():
         r = b - A @ x
         assert np.linalg.norm(ker.T @ x) <= 1e-12 * np.linalg.norm(x)
         assert np.linalg.norm(r - ker @ (ker.T @ r)) <= 1e-13 * np.linalg.norm(b)
+
+
+def test_fgmres_matches_dense_solution_and_is_monotone():
+    """Flexible GMRES with the V-cycle preconditioner: the residual never
+    grows within a restart cycle, and the converged solution is the dense
+    least-squares solution (bounded by both residuals)."""
+    prob = P.generic(2, 8, 2, 1, [P.DIRICHLET] * 3 + [P.STRESS])
+    mg = multigrid.Multigrid(prob)
+    A = mg.A.toarray()
+    b = np.random.default_rng(4).standard_normal(A.shape[0])
+    x, hist = mg.fgmres(b, rtol=1e-12, maxit=100, restart=50)
+    assert hist[-1] <= 1e-12
+    assert all(h1 <= h0 * (1 + 1e-12) for h0, h1 in zip(hist[:-1], hist[1:]))
+    lam = np.linalg.eigvalsh(A)
+    x_ref = np.linalg.solve(A, b)
+    bound = (np.linalg.norm(b - A @ x) + np.linalg.norm(b - A @ x_ref)) / np.abs(lam).min()
+    assert np.linalg.norm(x - x_ref) <= 1.5 * bound + 1e-14 * np.linalg.norm(x_ref)
