@@ -12,8 +12,8 @@ bottom solve), captured as one CUDA graph per outer iteration.  The headline
 path stores the element blocks in FP32 inside the FP64 refinement; the plain
 FP64 path is measured on the same problem beside it.
 
-The outer iteration is flexible GMRES(30) in FP64 with one V(2,2) cycle as the
-right preconditioner (--solver richardson --nu 1 gives the plain iterative
+The outer iteration is flexible GMRES(30) in FP64 with one V(3,3) cycle as the
+right preconditioner (the paper's V(3,3); --solver richardson --nu 1 gives plain iterative
 refinement with V(1,1)).
 
 value = DOFs x V-cycles / s (DOF-cycles per second through whole solves).
@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--solver", default="fgmres", choices=["fgmres", "richardson"])
-    ap.add_argument("--nu", type=int, default=2, help="pre- and post-smoothing sweeps")
+    ap.add_argument("--nu", type=int, default=3, help="pre- and post-smoothing sweeps")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", default=None, choices=["gs", "resid", "solve"],
