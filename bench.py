@@ -341,6 +341,13 @@ def run_native(args):
             "frac": round(ach / hbm_peak, 3), "traffic": traffic,
             "algorithmic_bytes_per_launch": int(alg), "launch_ms": round(t_gs * 1e3, 4),
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    variants = {}
+    for var in (0, 1):
+        mg.ctx.set_tuning(var, prec)
+        tv = time_kernel(lambda: mg.ctx.gs_colour_ex(0, 0, prec, xv, bv, stream), 20, stream)
+        variants["direct" if var == 0 else "bulk_pipeline"] = {"launch_ms": round(tv * 1e3, 4),
+                                                               "GBps": round(alg / tv / 1e9, 1)}
+    mg.ctx.set_tuning(1, prec)
     t_gs64 = time_kernel(lambda: mg64.ctx.gs_colour(0, 0, x, b, stream), 10, stream)
     alg64 = algorithmic_bytes_gs(mg64, prob, 8, 8, int(ne_levels[0]))
     kernels64 = {"gs_sweep_fp64_ms": round(t_gs64 * 1e3, 4),
@@ -358,6 +365,7 @@ def run_native(args):
         "final_rel_residual": float(hist[-1]), "setup_s": round(setup_s, 2),
         "plain_fp64": plain, "speedup_vs_plain_fp64": plain["ms_per_solve"] / (el / args.steps * 1e3),
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "fp64_kernels": kernels64,
+        "gs_variants": variants,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:

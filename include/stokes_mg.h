@@ -236,6 +236,19 @@ int stk_residual_norm_static(stk_ctx* ctx, const double* x_dev, const double* b_
  */
 int stk_set_solver(stk_ctx* ctx, int method, int restart);
 
+/*
+ * Kernel tuning for the element kernel (colour steps and residuals):
+ * variant 0 = direct 16-byte loads of the element records; variant 1
+ * (default) = the records streamed into a shared-memory ring of `stages`
+ * buffers by 1-D bulk copies (cp.async.bulk, mbarrier completion), with
+ * `ctas_per_sm` CTAs per SM, for blocks stored in `precision`.  Zero for
+ * ctas_per_sm and stages selects the built-in shape for the record size.
+ * Shapes whose ring does not fit in shared memory fall back to variant 0.
+ * If a bulk copy never completes, the kernel's bounded wait (about one
+ * second) expires and stk_solve returns STK_ERR_TIMEOUT.
+ */
+int stk_set_tuning(stk_ctx* ctx, int variant, int precision, int ctas_per_sm, int stages);
+
 /* Number of kernel launches the library enqueued since the context was
  * created (all of them are this library's own kernels). */
 int stk_launch_count(stk_ctx* ctx, int64_t* count);

@@ -35,6 +35,11 @@ cudaError_t launch_multidot(int64_t n, int k, const double* V, int64_t ldv, cons
 cudaError_t launch_multiaxpy(int64_t n, int k, double alpha, const double* coef, const double* V, int64_t ldv,
                              double* w, cudaStream_t st);
 cudaError_t launch_scale(int64_t n, double s, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_element_pipe(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
+                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                int* err, int ctas, int stages, cudaStream_t st);
+void prepare_pipe_kernels();
+void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages);
 }  // namespace stk
 
 using namespace stk;
@@ -113,6 +118,20 @@ int colour_of(const Ctx& c, const int* n, int64_t e) {
   int col = 0;
   for (int k = 0; k < c.d; ++k) col |= (idx[k] & 1) << k;
   return col;
+}
+
+// One element-kernel launch (colour step or residual) on level l with the
+// configured variant; the pipelined variant falls back to direct loads when
+// its records do not fit in shared memory.
+cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, const void* mat, const void* b,
+                        void* x, void* r, cudaStream_t st) {
+  DevLevel& D = c.dev[l];
+  if (c.variant == 1) {
+    cudaError_t e = launch_element_pipe(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
+                                        c.dev_err, c.pipe_ctas[prec], c.pipe_stages[prec], st);
+    if (e != cudaErrorInvalidValue) return e;
+  }
+  return launch_element(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r, st);
 }
 
 // Pack the Stokes blocks of smoothing level l into the colour-major device
@@ -254,9 +273,7 @@ void enqueue_smooth(Ctx& c, int prec, int l, int sweeps, void* x, const void* b,
     for (int col = 0; col < D.ncolour; ++col) {
       int n = D.cstart[col + 1] - D.cstart[col];
       if (n <= 0) continue;
-      ck(launch_element(c.pat, prec, MODE_GS, D.cstart[col], n, D.perm, D.nbr, D.cpl[prec], D.inv[prec],
-                        b, x, nullptr, st),
-         "gs colour launch");
+      ck(run_element(c, l, prec, MODE_GS, D.cstart[col], n, D.inv[prec], b, x, nullptr, st), "gs colour launch");
       c.launches++;
     }
 }
@@ -272,9 +289,7 @@ void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t
   DevLevel& D = c.dev[l];
   DevLevel& Dc = c.dev[l + 1];
   enqueue_smooth(c, prec, l, c.nu1, x, b, st);
-  ck(launch_element(c.pat, prec, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[prec], D.dia[prec], b, x,
-                    D.vr[vi], st),
-     "residual launch");
+  ck(run_element(c, l, prec, MODE_RESID, 0, D.ne, D.dia[prec], b, x, D.vr[vi], st), "residual launch");
   ck(launch_restrict(vi == 0, c.d, c.s, c.nb, Dc.n, D.n, Dc.ne, c.child_P[vi], D.vr[vi], Dc.vb[vi], st),
      "restrict launch");
   ck(cudaMemsetAsync(Dc.vx[vi], 0, (size_t)Dc.ne * c.nb * (vi == 0 ? 8 : 4), st), "memset");
@@ -288,9 +303,7 @@ void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t
 
 void enqueue_residual64(Ctx& c, const double* x, const double* b, double* r, cudaStream_t st) {
   DevLevel& D = c.dev[0];
-  ck(launch_element(c.pat, STK_FP64, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[0], D.dia[0], b,
-                    (void*)x, r, st),
-     "residual64 launch");
+  ck(run_element(c, 0, STK_FP64, MODE_RESID, 0, D.ne, D.dia[0], b, (void*)x, r, st), "residual64 launch");
   c.launches++;
 }
 
@@ -298,6 +311,7 @@ void enqueue_norm(Ctx& c, const double* v, cudaStream_t st) {
   ck(launch_sumsq(level_ne(c, 0) * c.nb, v, c.norm_buf + 16, c.norm_buf, st), "norm launch");
   c.launches += 2;
   ck(cudaMemcpyAsync(c.norm_host, c.norm_buf, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
+  ck(cudaMemcpyAsync(c.norm_host + 1, c.dev_err, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
 }
 
 // One outer iteration after the residual r64 of the current x is known:
@@ -421,9 +435,12 @@ void host_axpy(Ctx& c, int k, double alpha, const double* coef, const double* V,
   ck(cudaStreamSynchronize(st), "sync");   // hc is reused by the next call
 }
 
+struct Timeout {};
+
 double host_norm(Ctx& c, const double* v, cudaStream_t st) {
   enqueue_norm(c, v, st);
   ck(cudaStreamSynchronize(st), "sync");
+  if (reinterpret_cast<int*>(c.norm_host + 1)[0] != 0) throw Timeout{};
   return std::sqrt(c.norm_host[0]);
 }
 
@@ -693,6 +710,16 @@ int stk_setup(stk_ctx* c, void* stream) {
     }
     alloc_vectors(*c);
     setup_bottom(*c);
+    c->dev_err = (int*)dalloc(*c, 16);
+    ck(cudaMemset(c->dev_err, 0, 16), "memset");
+    static bool prepared[64] = {false};
+    if (c->device >= 0 && c->device < 64 && !prepared[c->device]) {
+      prepare_pipe_kernels();
+      prepared[c->device] = true;
+    }
+    for (int pr = 0; pr < 3; ++pr)
+      if (c->pipe_ctas[pr] <= 0 || c->pipe_stages[pr] <= 0)
+        pipe_default_shape(c->pat, pr, &c->pipe_ctas[pr], &c->pipe_stages[pr]);
     std::vector<double> P;
     child_matrices(c->d, c->p, P);
     int s = c->s, nch = 1 << c->d;
@@ -779,8 +806,8 @@ int stk_gs_colour(stk_ctx* c, int level, int colour, double* x, const double* b,
     if (colour < 0 || colour >= (1 << c->d) || !x || !b) return fail(c, STK_ERR_INVALID_ARG, "bad colour");
     DevLevel& D = c->dev[level];
     int n = D.cstart[colour + 1] - D.cstart[colour];
-    ck(launch_element(c->pat, STK_FP64, MODE_GS, D.cstart[colour], n, D.perm, D.nbr, D.cpl[0], D.inv[0], b,
-                      x, nullptr, (cudaStream_t)stream),
+    ck(run_element(*c, level, STK_FP64, MODE_GS, D.cstart[colour], n, D.inv[0], b, x, nullptr,
+                   (cudaStream_t)stream),
        "gs colour launch");
     c->launches++;
     return STK_OK;
@@ -800,8 +827,8 @@ int stk_gs_colour_ex(stk_ctx* c, int level, int colour, int precision, void* x, 
     if (!have_precision(*c, precision)) return fail(c, STK_ERR_INVALID_ARG, "precision not set up");
     DevLevel& D = c->dev[level];
     int n = D.cstart[colour + 1] - D.cstart[colour];
-    ck(launch_element(c->pat, precision, MODE_GS, D.cstart[colour], n, D.perm, D.nbr, D.cpl[precision],
-                      D.inv[precision], b, x, nullptr, (cudaStream_t)stream),
+    ck(run_element(*c, level, precision, MODE_GS, D.cstart[colour], n, D.inv[precision], b, x, nullptr,
+                   (cudaStream_t)stream),
        "gs colour launch");
     c->launches++;
     return STK_OK;
@@ -816,8 +843,8 @@ int stk_residual_ex(stk_ctx* c, int level, int precision, const void* x, const v
     if (!x || !b || !r) return fail(c, STK_ERR_INVALID_ARG, "null vector");
     if (!have_precision(*c, precision)) return fail(c, STK_ERR_INVALID_ARG, "precision not set up");
     DevLevel& D = c->dev[level];
-    ck(launch_element(c->pat, precision, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[precision],
-                      D.dia[precision], b, (void*)x, r, (cudaStream_t)stream),
+    ck(run_element(*c, level, precision, MODE_RESID, 0, D.ne, D.dia[precision], b, (void*)x, r,
+                   (cudaStream_t)stream),
        "residual launch");
     c->launches++;
     return STK_OK;
@@ -889,7 +916,11 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
     if (hist) hist[0] = rel;
     int it = 0;
     if (c->solver == 1) {
-      it = fgmres(*c, x, b, rtol, maxit, hist, bnorm, rel, st);
+      try {
+        it = fgmres(*c, x, b, rtol, maxit, hist, bnorm, rel, st);
+      } catch (const Timeout&) {
+        return fail(c, STK_ERR_TIMEOUT, "a kernel's bounded wait for its records expired");
+      }
       if (iters_out) *iters_out = it;
       if (!std::isfinite(rel) || rel > 1e6 * rel0) return fail(c, STK_ERR_DIVERGED, "outer iteration diverged");
       return STK_OK;
@@ -921,6 +952,8 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
       ck(cudaGraphLaunch(c->graph, st), "graph launch");
       c->launches += c->graph_kernels;
       ck(cudaStreamSynchronize(st), "sync");
+      if (reinterpret_cast<int*>(c->norm_host + 1)[0] != 0)
+        return fail(c, STK_ERR_TIMEOUT, "a kernel's bounded wait for its records expired");
       rel = std::sqrt(c->norm_host[0]) / bnorm;
       ++it;
       if (hist) hist[it] = rel;
@@ -930,6 +963,28 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
       }
     }
     if (iters_out) *iters_out = it;
+    return STK_OK;
+  });
+}
+
+int stk_set_tuning(stk_ctx* c, int variant, int precision, int ctas_per_sm, int stages) {
+  return guard(c, [&]() -> int {
+    if (variant < 0 || variant > 1 || precision < 0 || precision > 2 || ctas_per_sm < 0 || ctas_per_sm > 32 ||
+        stages < 0 || stages > 16)
+      return fail(c, STK_ERR_INVALID_ARG, "bad tuning options");
+    c->variant = variant;
+    if (ctas_per_sm > 0 && stages > 0) {
+      c->pipe_ctas[precision] = ctas_per_sm;
+      c->pipe_stages[precision] = stages;
+    } else if (c->ready) {
+      pipe_default_shape(c->pat, precision, &c->pipe_ctas[precision], &c->pipe_stages[precision]);
+    }
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_x = c->graph_b = nullptr;
+    if (c->cycle_graph) cudaGraphExecDestroy(c->cycle_graph);
+    c->cycle_graph = nullptr;
+    c->cycle_graph_prec = -1;
     return STK_OK;
   });
 }

@@ -33,6 +33,11 @@ template <> struct StorageTraits<double> {
     w[0] = v.x;
     w[1] = v.y;
   }
+  __device__ static inline void load_shared(const double* p, double* w) {
+    double2 v = *reinterpret_cast<const double2*>(p);
+    w[0] = v.x;
+    w[1] = v.y;
+  }
 };
 template <> struct StorageTraits<float> {
   using Acc = float;
@@ -44,12 +49,28 @@ template <> struct StorageTraits<float> {
     w[2] = v.z;
     w[3] = v.w;
   }
+  __device__ static inline void load_shared(const float* p, float* w) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = v.z;
+    w[3] = v.w;
+  }
 };
 template <> struct StorageTraits<__nv_bfloat16> {
   using Acc = float;
   static constexpr int V = 8;
   __device__ static inline void load(const __nv_bfloat16* p, float* w) {
     uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+    uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      w[2 * i] = __uint_as_float(u[i] << 16);
+      w[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+    }
+  }
+  __device__ static inline void load_shared(const __nv_bfloat16* p, float* w) {
+    uint4 v = *reinterpret_cast<const uint4*>(p);
     uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -157,6 +178,237 @@ __global__ void __launch_bounds__(kNT) element_kernel(const __grid_constant__ Pa
         rout[(size_t)e * nb + r] = (TX)(g[r] - sum);
     }
     __syncthreads();
+  }
+}
+
+// ---- pipelined variant: element records staged by 1-D bulk copies ------------
+// Same arithmetic and output as element_kernel.  Thread 0 streams each
+// element's coupling and dense records into a ring of STAGES shared-memory
+// buffers with cp.async.bulk (completion tracked by an mbarrier per stage),
+// so the next elements' records are in flight while the current one is
+// computed from shared memory.  Position -> element and neighbour indices of
+// all elements of the CTA are preloaded once.  Every mbarrier wait is bounded
+// (about one second of clock ticks); on expiry the kernel raises *err_flag,
+// waits (bounded again) for the copies it issued, and returns.
+__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ inline void proxy_fence_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: true when the phase completed, false after ~2e9 clock ticks.
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > 2000000000LL) return false;
+  }
+  return true;
+}
+
+struct PipeGeom {
+  int stages;
+  int kmax;            // most elements one CTA processes
+  uint32_t cpl_bytes;  // bytes of one coupling record
+  uint32_t mat_bytes;  // bytes of one dense record
+  size_t off_stage;    // byte offset of stage 0
+  size_t stage_stride; // bytes per stage (cpl + mat, 128-aligned)
+  size_t off_work;     // byte offset of the work arrays
+  size_t off_idx;      // byte offset of perm / nbr copies
+  size_t total;
+};
+
+template <typename TS>
+static PipeGeom pipe_geometry(const Pattern& pat, int stages, int kmax) {
+  using TA = typename StorageTraits<TS>::Acc;
+  constexpr int V = StorageTraits<TS>::V;
+  auto up = [](size_t v) { return (v + 127) / 128 * 128; };
+  PipeGeom g;
+  g.stages = stages;
+  g.kmax = kmax;
+  g.cpl_bytes = (uint32_t)((size_t)pat.s * pat.TRP * sizeof(TS));
+  g.mat_bytes = (uint32_t)((size_t)pat.nb * pat.NBP * sizeof(TS));
+  g.off_stage = 128;  // mbarriers (up to 16) first
+  g.stage_stride = up(g.cpl_bytes) + up(g.mat_bytes);
+  g.off_work = g.off_stage + (size_t)stages * g.stage_stride;
+  int NRV = pat.NBP / V;
+  int NCG = (kNT / NRV) > 0 ? (kNT / NRV) : 1;
+  size_t work = ((size_t)pat.NG * pat.s + pat.TRP + 2 * pat.NBP + (size_t)NCG * pat.NBP) * sizeof(TA);
+  g.off_idx = up(g.off_work + work);
+  g.total = g.off_idx + (size_t)kmax * (1 + pat.NO) * sizeof(int);
+  return g;
+}
+
+template <typename TS, typename TX, int S>
+__global__ void __launch_bounds__(kNT) element_pipe_kernel(const __grid_constant__ Pattern pat,
+                                                           const __grid_constant__ PipeGeom geo, int mode,
+                                                           int pos0, int npos, const int* __restrict__ perm,
+                                                           const int* __restrict__ nbr,
+                                                           const TS* __restrict__ cpl,
+                                                           const TS* __restrict__ mat,
+                                                           const TX* __restrict__ b, TX* x, TX* rout,
+                                                           int* err_flag) {
+  using Tr = StorageTraits<TS>;
+  using TA = typename Tr::Acc;
+  constexpr int V = Tr::V;
+  const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
+  const int NRV = NBP / V;
+  const int NCG = (kNT / NRV) > 0 ? (kNT / NRV) : 1;
+  const int CW = (nb + NCG - 1) / NCG;
+  const int ST = geo.stages;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  TA* Xs = reinterpret_cast<TA*>(smem + geo.off_work);
+  TA* part = Xs + pat.NG * S;
+  TA* g = part + TRP;
+  TA* xi = g + NBP;
+  TA* part2 = xi + NBP;
+  int* perm_s = reinterpret_cast<int*>(smem + geo.off_idx);
+  int* nbr_s = perm_s + geo.kmax;
+  __shared__ int timed_out;
+
+  const int tid = threadIdx.x;
+  const int first = pos0 + blockIdx.x;
+  if (first >= pos0 + npos) return;
+  const int K = (pos0 + npos - first + gridDim.x - 1) / gridDim.x;
+
+  for (int i = tid; i < K; i += kNT) perm_s[i] = perm[first + i * gridDim.x];
+  for (int i = tid; i < K * pat.NO; i += kNT) {
+    const int kk = i / pat.NO, o = i - kk * pat.NO;
+    nbr_s[i] = nbr[(size_t)(first + kk * gridDim.x) * pat.NO + o];
+  }
+  if (tid == 0) {
+    timed_out = 0;
+    for (int st = 0; st < ST; ++st) mbar_init(&bar[st], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  auto stage_cpl = [&](int st) { return reinterpret_cast<const TS*>(smem + geo.off_stage + st * geo.stage_stride); };
+  auto stage_mat = [&](int st) {
+    return reinterpret_cast<const TS*>(smem + geo.off_stage + st * geo.stage_stride + (geo.cpl_bytes + 127) / 128 * 128);
+  };
+  auto issue = [&](int kk) {
+    if (kk >= K) return;
+    const int st = kk % ST;
+    const size_t pos = (size_t)first + (size_t)kk * gridDim.x;
+    mbar_expect_tx(&bar[st], geo.cpl_bytes + geo.mat_bytes);
+    bulk_g2s((void*)stage_cpl(st), cpl + pos * (geo.cpl_bytes / sizeof(TS)), geo.cpl_bytes, &bar[st]);
+    bulk_g2s((void*)stage_mat(st), mat + pos * (geo.mat_bytes / sizeof(TS)), geo.mat_bytes, &bar[st]);
+  };
+  if (tid == 0)
+    for (int kk = 0; kk < ST; ++kk) issue(kk);
+
+  int issued = min(K, ST);
+  int kfail = K;
+  for (int k = 0; k < K; ++k) {
+    const int st = k % ST;
+    const int e = perm_s[k];
+    const int* nbe = nbr_s + k * pat.NO;
+    // Neighbour values and the element's own vectors (plain loads, L2-resident).
+    for (int i = tid; i < pat.NG * S; i += kNT) {
+      const int gi = i / S, ci = i - gi * S;
+      const int j = nbe[pat.g_o[gi]];
+      Xs[i] = (j >= 0) ? (TA)x[(size_t)j * nb + pat.g_cv[gi] * S + ci] : (TA)0;
+    }
+    for (int i = tid; i < nb; i += kNT) {
+      g[i] = (TA)b[(size_t)e * nb + i];
+      if (mode == MODE_RESID) xi[i] = (TA)x[(size_t)e * nb + i];
+    }
+    if (!mbar_wait_bounded(&bar[st], (uint32_t)((k / ST) & 1))) timed_out = 1;
+    __syncthreads();
+    if (timed_out) {
+      kfail = k;
+      break;
+    }
+    const TS* rec = stage_cpl(st);
+    for (int tv = tid; tv < TRP / V; tv += kNT) {
+      const int tr0 = tv * V;
+      const TA* xp[V];
+      TA acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int tr = tr0 + j;
+        xp[j] = (tr < TR) ? Xs + pat.task_g[tr / S] * S : Xs;
+        acc[j] = 0;
+      }
+#pragma unroll 4
+      for (int ci = 0; ci < S; ++ci) {
+        TA w[V];
+        Tr::load_shared(rec + (size_t)ci * TRP + tr0, w);
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = fma(w[j], xp[j][ci], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) part[tr0 + j] = acc[j];
+    }
+    __syncthreads();
+    for (int r = tid; r < nb; r += kNT) {
+      const int rv = r / S, rr = r - rv * S;
+      TA sum = 0;
+      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[t * S + rr];
+      g[r] = g[r] - sum;
+    }
+    __syncthreads();
+    const TS* mrec = stage_mat(st);
+    const TA* vin = (mode == MODE_GS) ? g : xi;
+    for (int u = tid; u < NRV * NCG; u += kNT) {
+      const int rvv = u % NRV, cg = u / NRV;
+      const int c0 = cg * CW, c1 = min(nb, c0 + CW);
+      TA acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) acc[j] = 0;
+      for (int ci = c0; ci < c1; ++ci) {
+        TA w[V];
+        Tr::load_shared(mrec + (size_t)ci * NBP + rvv * V, w);
+        const TA v = vin[ci];
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = fma(w[j], v, acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) part2[cg * NBP + rvv * V + j] = acc[j];
+    }
+    __syncthreads();
+    for (int r = tid; r < nb; r += kNT) {
+      TA sum = 0;
+      for (int cg = 0; cg < NCG; ++cg) sum += part2[cg * NBP + r];
+      if (mode == MODE_GS)
+        x[(size_t)e * nb + r] = (TX)sum;
+      else
+        rout[(size_t)e * nb + r] = (TX)(g[r] - sum);
+    }
+    __syncthreads();
+    if (tid == 0 && k + ST < K) {
+      proxy_fence_async();
+      issue(k + ST);
+      issued = k + ST + 1;
+    }
+  }
+  if (timed_out && tid == 0) {
+    atomicExch(err_flag, 1);
+    // Let the copies this CTA issued and not yet consumed land before its
+    // shared memory is released.
+    for (int kk = kfail; kk < issued; ++kk) mbar_wait_bounded(&bar[kk % ST], (uint32_t)((kk / ST) & 1));
   }
 }
 
@@ -332,6 +584,87 @@ static cudaError_t launch_element_t(const Pattern& pat, int mode, int pos0, int 
     case 16: return launch_element_s<TS, TX, 16>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
     case 25: return launch_element_s<TS, TX, 25>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
     case 27: return launch_element_s<TS, TX, 27>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Pipelined launch: returns cudaErrorInvalidValue when the geometry does not
+// fit in shared memory (the caller then uses element_kernel).
+template <typename TS, typename TX, int S>
+static cudaError_t launch_pipe_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
+                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x,
+                                 void* r, int* err, int ctas, int stages, cudaStream_t st) {
+  if (npos <= 0) return cudaSuccess;
+  int grid = std::min(npos, num_sms() * ctas);
+  int kmax = (npos + grid - 1) / grid;
+  PipeGeom geo = pipe_geometry<TS>(pat, stages, kmax);
+  if (geo.total > 226 * 1024 || stages > 16) return cudaErrorInvalidValue;
+  element_pipe_kernel<TS, TX, S><<<grid, kNT, geo.total, st>>>(pat, geo, mode, pos0, npos, perm, nbr,
+                                                               (const TS*)cpl, (const TS*)mat, (const TX*)b,
+                                                               (TX*)x, (TX*)r, err);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TX, int S>
+static void prepare_pipe_s() {
+  cudaFuncSetAttribute(element_pipe_kernel<TS, TX, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+}
+
+template <typename TS, typename TX>
+static cudaError_t launch_pipe_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
+                                 const void* cpl, const void* mat, const void* b, void* x, void* r, int* err,
+                                 int ctas, int stages, cudaStream_t st) {
+#define STK_PIPE_CASE(SV) \
+  case SV: return launch_pipe_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, err, ctas, stages, st);
+  switch (pat.s) {
+    STK_PIPE_CASE(4)
+    STK_PIPE_CASE(8)
+    STK_PIPE_CASE(9)
+    STK_PIPE_CASE(16)
+    STK_PIPE_CASE(25)
+    STK_PIPE_CASE(27)
+    default: return cudaErrorInvalidValue;
+  }
+#undef STK_PIPE_CASE
+}
+
+template <typename TS, typename TX>
+static void prepare_pipe_t() {
+  prepare_pipe_s<TS, TX, 4>();
+  prepare_pipe_s<TS, TX, 8>();
+  prepare_pipe_s<TS, TX, 9>();
+  prepare_pipe_s<TS, TX, 16>();
+  prepare_pipe_s<TS, TX, 25>();
+  prepare_pipe_s<TS, TX, 27>();
+}
+
+// Raise the shared-memory limit of the pipelined kernels (call outside any
+// stream capture, once per process and device).
+void prepare_pipe_kernels() {
+  prepare_pipe_t<double, double>();
+  prepare_pipe_t<float, float>();
+  prepare_pipe_t<__nv_bfloat16, float>();
+}
+
+// Default pipeline shape for a record size: CTAs per SM and ring depth.
+void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages) {
+  size_t es = storage == 0 ? 8 : (storage == 1 ? 4 : 2);
+  size_t rec = (size_t)pat.s * pat.TRP * es + (size_t)pat.nb * pat.NBP * es;
+  size_t budget = 220 * 1024, work = 8 * 1024;
+  int c = (int)std::max<size_t>(1, std::min<size_t>(4, budget / (2 * rec + work)));
+  int sdep = (int)std::max<size_t>(2, std::min<size_t>(4, (budget / c - work) / rec));
+  *ctas = c;
+  *stages = sdep;
+}
+
+cudaError_t launch_element_pipe(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
+                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                int* err, int ctas, int stages, cudaStream_t st) {
+  switch (storage) {
+    case 0: return launch_pipe_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, err, ctas, stages, st);
+    case 1: return launch_pipe_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, err, ctas, stages, st);
+    case 2:
+      return launch_pipe_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, err, ctas, stages, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -117,6 +117,11 @@ struct Ctx {
   cudaGraphExec_t cycle_graph = nullptr;
   int cycle_graph_prec = -1;
   int64_t cycle_graph_kernels = 0;
+  // element-kernel variant: 0 direct loads, 1 bulk-copy pipeline (default),
+  // with the pipeline shape per storage precision (CTAs per SM, ring depth)
+  int variant = 1;
+  int pipe_ctas[3] = {0, 0, 0}, pipe_stages[3] = {0, 0, 0};
+  int* dev_err = nullptr;     // raised by a kernel whose bounded wait expired
   std::vector<void*> allocations;
 };
 

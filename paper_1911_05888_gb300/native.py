@@ -55,6 +55,7 @@ SIGNATURES = {
     "stk_solve": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _c_int_p, _c_dbl_p, _vp],
     "stk_residual_norm_static": [_vp, _vp, _vp, _vp, _vp, _vp],
     "stk_set_solver": [_vp, ctypes.c_int, ctypes.c_int],
+    "stk_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "stk_launch_count": [_vp, _c_i64_p],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
@@ -246,6 +247,9 @@ class Context:
         scalar norm2, using only the library's fixed static scratch."""
         self._check(self.lib.stk_residual_norm_static(self.h, _ptr(x), _ptr(b), _ptr(r), _ptr(norm2),
                                                       _stream(stream)), "stk_residual_norm_static")
+
+    def set_tuning(self, variant, precision, ctas_per_sm=0, stages=0):
+        self._check(self.lib.stk_set_tuning(self.h, variant, precision, ctas_per_sm, stages), "stk_set_tuning")
 
     def set_solver(self, method, restart=30):
         self._check(self.lib.stk_set_solver(self.h, method, restart), "stk_set_solver")
