@@ -30,6 +30,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+DEFAULT_VARIANT = 2
 METRIC = "time to 1e-10 rel. residual & DOFs/s per V-cycle: mixed+learned vs plain FP64"
 
 
@@ -342,12 +343,17 @@ def run_native(args):
             "algorithmic_bytes_per_launch": int(alg), "launch_ms": round(t_gs * 1e3, 4),
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     variants = {}
-    for var in (0, 1):
+    names = {0: "direct", 1: "bulk_pipeline", 2: "warp_per_element"}
+    for var in (0, 1, 2):
         mg.ctx.set_tuning(var, prec)
         tv = time_kernel(lambda: mg.ctx.gs_colour_ex(0, 0, prec, xv, bv, stream), 20, stream)
-        variants["direct" if var == 0 else "bulk_pipeline"] = {"launch_ms": round(tv * 1e3, 4),
-                                                               "GBps": round(alg / tv / 1e9, 1)}
-    mg.ctx.set_tuning(1, prec)
+        variants[names[var]] = {"launch_ms": round(tv * 1e3, 4), "GBps": round(alg / tv / 1e9, 1)}
+        if var == 2:
+            for c_ in (2, 3, 4, 6, 8):
+                mg.ctx.set_tuning(2, prec, c_)
+                tv = time_kernel(lambda: mg.ctx.gs_colour_ex(0, 0, prec, xv, bv, stream), 20, stream)
+                variants["warp_ctas%d" % c_] = {"launch_ms": round(tv * 1e3, 4), "GBps": round(alg / tv / 1e9, 1)}
+    mg.ctx.set_tuning(DEFAULT_VARIANT, prec)
     t_gs64 = time_kernel(lambda: mg64.ctx.gs_colour(0, 0, x, b, stream), 10, stream)
     alg64 = algorithmic_bytes_gs(mg64, prob, 8, 8, int(ne_levels[0]))
     kernels64 = {"gs_sweep_fp64_ms": round(t_gs64 * 1e3, 4),

@@ -238,11 +238,13 @@ int stk_set_solver(stk_ctx* ctx, int method, int restart);
 
 /*
  * Kernel tuning for the element kernel (colour steps and residuals):
- * variant 0 = direct 16-byte loads of the element records; variant 1
- * (default) = the records streamed into a shared-memory ring of `stages`
- * buffers by 1-D bulk copies (cp.async.bulk, mbarrier completion), with
- * `ctas_per_sm` CTAs per SM, for blocks stored in `precision`.  Zero for
- * ctas_per_sm and stages selects the built-in shape for the record size.
+ * variant 0 = one CTA per element with direct 16-byte loads of the element
+ * records; variant 1 = the records streamed into a shared-memory ring of
+ * `stages` buffers by 1-D bulk copies (cp.async.bulk, mbarrier completion);
+ * variant 2 (default) = one warp per element, no block-wide barriers.
+ * `ctas_per_sm` sets the grid (CTAs per SM) of variants 1 and 2, for blocks
+ * stored in `precision`.  Zero for ctas_per_sm and stages selects the
+ * built-in shape for the record size.
  * Shapes whose ring does not fit in shared memory fall back to variant 0.
  * If a bulk copy never completes, the kernel's bounded wait (about one
  * second) expires and stk_solve returns STK_ERR_TIMEOUT.

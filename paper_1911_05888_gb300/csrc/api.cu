@@ -39,6 +39,9 @@ cudaError_t launch_element_pipe(const Pattern& pat, int storage, int mode, int p
                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
                                 int* err, int ctas, int stages, cudaStream_t st);
 void prepare_pipe_kernels();
+cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
+                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                int ctas, cudaStream_t st);
 void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages);
 }  // namespace stk
 
@@ -126,6 +129,11 @@ int colour_of(const Ctx& c, const int* n, int64_t e) {
 cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, const void* mat, const void* b,
                         void* x, void* r, cudaStream_t st) {
   DevLevel& D = c.dev[l];
+  if (c.variant == 2) {
+    cudaError_t e = launch_element_warp(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
+                                        c.warp_ctas[prec], st);
+    if (e != cudaErrorInvalidValue) return e;
+  }
   if (c.variant == 1) {
     cudaError_t e = launch_element_pipe(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
                                         c.dev_err, c.pipe_ctas[prec], c.pipe_stages[prec], st);
@@ -969,11 +977,12 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
 
 int stk_set_tuning(stk_ctx* c, int variant, int precision, int ctas_per_sm, int stages) {
   return guard(c, [&]() -> int {
-    if (variant < 0 || variant > 1 || precision < 0 || precision > 2 || ctas_per_sm < 0 || ctas_per_sm > 32 ||
+    if (variant < 0 || variant > 2 || precision < 0 || precision > 2 || ctas_per_sm < 0 || ctas_per_sm > 32 ||
         stages < 0 || stages > 16)
       return fail(c, STK_ERR_INVALID_ARG, "bad tuning options");
     c->variant = variant;
-    if (ctas_per_sm > 0 && stages > 0) {
+    if (variant == 2 && ctas_per_sm > 0) c->warp_ctas[precision] = ctas_per_sm;
+    if (variant == 1 && ctas_per_sm > 0 && stages > 0) {
       c->pipe_ctas[precision] = ctas_per_sm;
       c->pipe_stages[precision] = stages;
     } else if (c->ready) {

@@ -412,6 +412,132 @@ __global__ void __launch_bounds__(kNT) element_pipe_kernel(const __grid_constant
   }
 }
 
+// ---- warp-per-element variant ------------------------------------------------
+// Each warp owns one element at a time and synchronises only with itself
+// (__syncwarp), so a CTA of kWarps warps keeps kWarps independent elements --
+// and their 16-byte record loads -- in flight; there is no block-wide barrier.
+// Per-warp shared memory holds the gathered neighbour values (slot stride
+// S+1 to spread banks), the task-row partial sums, g and the column-group
+// partials of the dense block.
+constexpr int kWarps = 8;   // warps per CTA of element_warp_kernel
+
+template <typename TS>
+struct WarpGeom {
+  int NCG, CW, XS, words;  // column groups, columns per group, X slot stride, TA words per warp
+};
+
+template <typename TS>
+__host__ __device__ inline WarpGeom<TS> warp_geometry(const Pattern& pat) {
+  constexpr int V = StorageTraits<TS>::V;
+  WarpGeom<TS> g;
+  const int NRV = pat.NBP / V;
+  g.NCG = (32 / NRV) > 0 ? (32 / NRV) : 1;
+  g.CW = (pat.nb + g.NCG - 1) / g.NCG;
+  g.XS = pat.s + 1;
+  int w = pat.NG * g.XS + pat.TRP + 2 * pat.NBP + g.NCG * pat.NBP;
+  g.words = (w + 3) / 4 * 4;
+  return g;
+}
+
+template <typename TS, typename TX, int S>
+__global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_constant__ Pattern pat, int mode,
+                                                                   int pos0, int npos,
+                                                                   const int* __restrict__ perm,
+                                                                   const int* __restrict__ nbr,
+                                                                   const TS* __restrict__ cpl,
+                                                                   const TS* __restrict__ mat,
+                                                                   const TX* __restrict__ b, TX* x, TX* rout) {
+  using Tr = StorageTraits<TS>;
+  using TA = typename Tr::Acc;
+  constexpr int V = Tr::V;
+  const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
+  const int NRV = NBP / V;
+  const WarpGeom<TS> wg = warp_geometry<TS>(pat);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TA* base = reinterpret_cast<TA*>(smem_raw) + (size_t)wid * wg.words;
+  TA* Xs = base;
+  TA* part = Xs + pat.NG * wg.XS;
+  TA* g = part + TRP;
+  TA* xi = g + NBP;
+  TA* part2 = xi + NBP;
+
+  const int nwarps = gridDim.x * kWarps;
+  for (int pos = pos0 + blockIdx.x * kWarps + wid; pos < pos0 + npos; pos += nwarps) {
+    const int e = perm[pos];
+    const int* nbe = nbr + (size_t)pos * pat.NO;
+    for (int i = lane; i < pat.NG * S; i += 32) {
+      const int gi = i / S, ci = i - gi * S;
+      const int j = nbe[pat.g_o[gi]];
+      Xs[gi * wg.XS + ci] = (j >= 0) ? (TA)x[(size_t)j * nb + pat.g_cv[gi] * S + ci] : (TA)0;
+    }
+    for (int i = lane; i < nb; i += 32) {
+      g[i] = (TA)b[(size_t)e * nb + i];
+      if (mode == MODE_RESID) xi[i] = (TA)x[(size_t)e * nb + i];
+    }
+    __syncwarp();
+    const TS* rec = cpl + (size_t)pos * S * TRP;
+    for (int tv = lane; tv < TRP / V; tv += 32) {
+      const int tr0 = tv * V;
+      const TA* xp[V];
+      TA acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int tr = tr0 + j;
+        xp[j] = (tr < TR) ? Xs + pat.task_g[tr / S] * wg.XS : Xs;
+        acc[j] = 0;
+      }
+#pragma unroll
+      for (int ci = 0; ci < S; ++ci) {
+        TA w[V];
+        Tr::load(rec + (size_t)ci * TRP + tr0, w);
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = fma(w[j], xp[j][ci], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) part[tr0 + j] = acc[j];
+    }
+    __syncwarp();
+    for (int r = lane; r < nb; r += 32) {
+      const int rv = r / S, rr = r - rv * S;
+      TA sum = 0;
+      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[t * S + rr];
+      g[r] = g[r] - sum;
+    }
+    __syncwarp();
+    const TS* mrec = mat + (size_t)pos * nb * NBP;
+    const TA* vin = (mode == MODE_GS) ? g : xi;
+    for (int u = lane; u < NRV * wg.NCG; u += 32) {
+      const int rvv = u % NRV, cg = u / NRV;
+      const int c0 = cg * wg.CW, c1 = min(nb, c0 + wg.CW);
+      TA acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) acc[j] = 0;
+#pragma unroll 4
+      for (int ci = c0; ci < c1; ++ci) {
+        TA w[V];
+        Tr::load(mrec + (size_t)ci * NBP + rvv * V, w);
+        const TA v = vin[ci];
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = fma(w[j], v, acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) part2[cg * NBP + rvv * V + j] = acc[j];
+    }
+    __syncwarp();
+    for (int r = lane; r < nb; r += 32) {
+      TA sum = 0;
+      for (int cg = 0; cg < wg.NCG; ++cg) sum += part2[cg * NBP + r];
+      if (mode == MODE_GS)
+        x[(size_t)e * nb + r] = (TX)sum;
+      else
+        rout[(size_t)e * nb + r] = (TX)(g[r] - sum);
+    }
+    __syncwarp();
+  }
+}
+
 template <typename TS>
 static size_t element_smem(const Pattern& pat) {
   using TA = typename StorageTraits<TS>::Acc;
@@ -638,12 +764,74 @@ static void prepare_pipe_t() {
   prepare_pipe_s<TS, TX, 27>();
 }
 
+template <typename TS, typename TX, int S>
+static cudaError_t launch_warp_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
+                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x,
+                                 void* r, int ctas, cudaStream_t st) {
+  if (npos <= 0) return cudaSuccess;
+  WarpGeom<TS> wg = warp_geometry<TS>(pat);
+  size_t smem = (size_t)kWarps * wg.words * sizeof(typename StorageTraits<TS>::Acc);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  int grid = std::min((npos + kWarps - 1) / kWarps, num_sms() * std::max(1, ctas));
+  element_warp_kernel<TS, TX, S><<<grid, 32 * kWarps, smem, st>>>(pat, mode, pos0, npos, perm, nbr,
+                                                                   (const TS*)cpl, (const TS*)mat,
+                                                                   (const TX*)b, (TX*)x, (TX*)r);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TX, int S>
+static void prepare_warp_s() {
+  cudaFuncSetAttribute(element_warp_kernel<TS, TX, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+}
+
+template <typename TS, typename TX>
+static cudaError_t launch_warp_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
+                                 const void* cpl, const void* mat, const void* b, void* x, void* r, int ctas,
+                                 cudaStream_t st) {
+#define STK_WARP_CASE(SV) \
+  case SV: return launch_warp_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, ctas, st);
+  switch (pat.s) {
+    STK_WARP_CASE(4)
+    STK_WARP_CASE(8)
+    STK_WARP_CASE(9)
+    STK_WARP_CASE(16)
+    STK_WARP_CASE(25)
+    STK_WARP_CASE(27)
+    default: return cudaErrorInvalidValue;
+  }
+#undef STK_WARP_CASE
+}
+
+template <typename TS, typename TX>
+static void prepare_warp_t() {
+  prepare_warp_s<TS, TX, 4>();
+  prepare_warp_s<TS, TX, 8>();
+  prepare_warp_s<TS, TX, 9>();
+  prepare_warp_s<TS, TX, 16>();
+  prepare_warp_s<TS, TX, 25>();
+  prepare_warp_s<TS, TX, 27>();
+}
+
+cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
+                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                int ctas, cudaStream_t st) {
+  switch (storage) {
+    case 0: return launch_warp_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, ctas, st);
+    case 1: return launch_warp_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, ctas, st);
+    case 2: return launch_warp_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, ctas, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Raise the shared-memory limit of the pipelined kernels (call outside any
 // stream capture, once per process and device).
 void prepare_pipe_kernels() {
   prepare_pipe_t<double, double>();
   prepare_pipe_t<float, float>();
   prepare_pipe_t<__nv_bfloat16, float>();
+  prepare_warp_t<double, double>();
+  prepare_warp_t<float, float>();
+  prepare_warp_t<__nv_bfloat16, float>();
 }
 
 // Default pipeline shape for a record size: CTAs per SM and ring depth.

@@ -117,10 +117,11 @@ struct Ctx {
   cudaGraphExec_t cycle_graph = nullptr;
   int cycle_graph_prec = -1;
   int64_t cycle_graph_kernels = 0;
-  // element-kernel variant: 0 direct loads, 1 bulk-copy pipeline (default),
+  // element-kernel variant: 0 direct loads, 1 bulk-copy pipeline, 2 warp per element (default),
   // with the pipeline shape per storage precision (CTAs per SM, ring depth)
-  int variant = 1;
+  int variant = 2;
   int pipe_ctas[3] = {0, 0, 0}, pipe_stages[3] = {0, 0, 0};
+  int warp_ctas[3] = {4, 4, 4};   // CTAs (of 8 warps) per SM for the warp-per-element kernel
   int* dev_err = nullptr;     // raised by a kernel whose bounded wait expired
   std::vector<void*> allocations;
 };

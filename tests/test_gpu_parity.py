@@ -214,3 +214,28 @@ def test_fgmres_solve(name, precision):
         assert rel(x.cpu().numpy(), xo) <= 1e-9
     else:
         assert it <= (len(ho) - 1) + 3
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-mixed-p1"])
+def test_kernel_variants_agree(name, variant):
+    """All element-kernel variants (direct loads, bulk-copy ring, warp per
+    element) give the oracle's colour step and residual in FP64."""
+    prob, gpu, orc = get(name)
+    gpu.ctx.set_tuning(variant, native.FP64)
+    try:
+        rng = np.random.default_rng(13)
+        x0 = rng.uniform(-1, 1, prob.n_dofs)
+        b = rng.uniform(-1, 1, prob.n_dofs)
+        xd, bd = dev(x0), dev(b)
+        xo = x0.copy()
+        sm = orc.sm[0]
+        for c in range(sm.ncol):
+            gpu.ctx.gs_colour(0, c, xd, bd)
+            sm.colour_step(xo, b, c)
+        assert rel(xd.cpu().numpy(), xo) <= 1e-13
+        r = torch.empty_like(xd)
+        gpu.ctx.residual(xd, bd, r)
+        assert rel(r.cpu().numpy(), orc.residual(0, xo, b)) <= 1e-12
+    finally:
+        gpu.ctx.set_tuning(2, native.FP64)
