@@ -52,7 +52,7 @@ def build(verbose=False, force=False):
             failed.append(src)
     if failed:
         raise RuntimeError("compilation failed: " + ", ".join(failed))
-    link = ["nvcc", ARCH, "-shared", "-o", LIB] + objs + ["-lcudart", "-lpthread"]
+    link = ["nvcc", ARCH, "-shared", "-o", LIB] + objs + ["-lcudart", "-lpthread", "-ldl"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         sys.stderr.write(r.stdout.decode(errors="replace"))

@@ -4,6 +4,7 @@
 // arXiv:1911.05888) and of the outer iteration.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <dlfcn.h>
 
 #include <algorithm>
 #include <cmath>
@@ -244,7 +245,88 @@ void alloc_vectors(Ctx& c) {
   ck(cudaMallocHost(&c.norm_host, 8 * sizeof(double)), "cudaMallocHost");
 }
 
-// Bottom level: dense operator, eigen pseudo-inverse (host), to device.
+// ---- large bottom levels: eigendecomposition by cuSOLVER (loaded at run time)
+// pinv(i, j) = sum_k V(i, k) w_k V(j, k), V column-major (n x n), w = 1/lambda or 0.
+__global__ void pinv_gemm_kernel(int n, const double* __restrict__ V, const double* __restrict__ w,
+                                 double* __restrict__ P) {
+  __shared__ double As[16][17], Bs[16][17];
+  const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    const int ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
+    const int ib = blockIdx.x * 16 + threadIdx.x;
+    As[threadIdx.y][threadIdx.x] = (i < n && ka < n) ? V[(size_t)ka * n + i] * w[ka] : 0.0;
+    Bs[threadIdx.y][threadIdx.x] = (ib < n && kb < n) ? V[(size_t)kb * n + ib] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc += As[threadIdx.y][k] * Bs[k][threadIdx.x];
+    __syncthreads();
+  }
+  if (i < n && j < n) P[(size_t)i * n + j] = acc;
+}
+
+typedef int (*syevd_buf_fn)(void*, int, int, int, const double*, int, const double*, int*);
+typedef int (*syevd_fn)(void*, int, int, int, double*, int, double*, double*, int, int*);
+typedef int (*create_fn)(void**);
+typedef int (*destroy_fn)(void*);
+
+// Returns false when cuSOLVER cannot be loaded (the caller then uses Jacobi).
+bool pseudo_inverse_cusolver(Ctx& c, int n, const std::vector<double>& A, double* d_pinv, int& snapped,
+                             double theta) {
+  void* so = nullptr;
+  for (const char* name : {"libcusolver.so", "libcusolver.so.12", "libcusolver.so.11"})
+    if ((so = dlopen(name, RTLD_NOW | RTLD_LOCAL))) break;
+  if (!so) return false;
+  auto create = (create_fn)dlsym(so, "cusolverDnCreate");
+  auto destroy = (destroy_fn)dlsym(so, "cusolverDnDestroy");
+  auto bufsz = (syevd_buf_fn)dlsym(so, "cusolverDnDsyevd_bufferSize");
+  auto syevd = (syevd_fn)dlsym(so, "cusolverDnDsyevd");
+  if (!create || !destroy || !bufsz || !syevd) return false;
+  void* h = nullptr;
+  if (create(&h) != 0) return false;
+  const int JOBZ_VECTOR = 1, FILL_LOWER = 0;   // CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER
+  double *dA = nullptr, *dW = nullptr, *dWork = nullptr, *dInv = nullptr;
+  int* dInfo = nullptr;
+  bool ok = false;
+  int lwork = 0, info = 1;
+  std::vector<double> lam(n), inv(n, 0.0);
+  if (cudaMalloc(&dA, (size_t)n * n * 8) != cudaSuccess || cudaMalloc(&dW, (size_t)n * 8) != cudaSuccess ||
+      cudaMalloc(&dInv, (size_t)n * 8) != cudaSuccess || cudaMalloc(&dInfo, sizeof(int)) != cudaSuccess)
+    goto done;
+  // A is symmetric: row-major and column-major storage coincide.
+  if (cudaMemcpy(dA, A.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice) != cudaSuccess) goto done;
+  if (bufsz(h, JOBZ_VECTOR, FILL_LOWER, n, dA, n, dW, &lwork) != 0) goto done;
+  if (cudaMalloc(&dWork, (size_t)std::max(lwork, 1) * 8) != cudaSuccess) goto done;
+  if (syevd(h, JOBZ_VECTOR, FILL_LOWER, n, dA, n, dW, dWork, lwork, dInfo) != 0) goto done;
+  if (cudaMemcpy(&info, dInfo, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || info != 0) goto done;
+  if (cudaMemcpy(lam.data(), dW, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) goto done;
+  {
+    double lmax = 0.0;
+    for (double l : lam) lmax = std::max(lmax, std::fabs(l));
+    snapped = 0;
+    for (int k = 0; k < n; ++k) {
+      if (std::fabs(lam[k]) <= theta * lmax) ++snapped;
+      else inv[k] = 1.0 / lam[k];
+    }
+  }
+  if (cudaMemcpy(dInv, inv.data(), (size_t)n * 8, cudaMemcpyHostToDevice) != cudaSuccess) goto done;
+  {
+    dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
+    pinv_gemm_kernel<<<grd, blk>>>(n, dA, dInv, d_pinv);
+    c.launches++;
+    ok = cudaDeviceSynchronize() == cudaSuccess;
+  }
+done:
+  if (dA) cudaFree(dA);
+  if (dW) cudaFree(dW);
+  if (dWork) cudaFree(dWork);
+  if (dInv) cudaFree(dInv);
+  if (dInfo) cudaFree(dInfo);
+  destroy(h);
+  return ok;
+}
+
+// Bottom level: dense operator, eigen pseudo-inverse, to device.
 void setup_bottom(Ctx& c) {
   const HostLevel& H = c.host.back();
   const Pattern& P = c.pat;
@@ -265,10 +347,13 @@ void setup_bottom(Ctx& c) {
               H.C[((size_t)a * P.T + t) * ss + i * s + j];
     }
   }
-  std::vector<double> pinv;
-  pseudo_inverse_jacobi((int)n, A, pinv, c.n_snapped, 1e-10);
   c.nbot = n;
   c.bottom_pinv = (double*)dalloc(c, (size_t)n * n * sizeof(double));
+  // Cyclic Jacobi (accurate, O(n^3) per sweep) for small bottom levels;
+  // cuSOLVER's symmetric eigensolver for large ones (3D hierarchies).
+  if (n > 1200 && pseudo_inverse_cusolver(c, (int)n, A, c.bottom_pinv, c.n_snapped, 1e-10)) return;
+  std::vector<double> pinv;
+  pseudo_inverse_jacobi((int)n, A, pinv, c.n_snapped, 1e-10);
   ck(cudaMemcpy(c.bottom_pinv, pinv.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice),
      "copy bottom");
 }
