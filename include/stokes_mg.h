@@ -227,6 +227,20 @@ int stk_residual_norm_static(stk_ctx* ctx, const double* x_dev, const double* b_
                              double* norm2_dev, void* stream);
 
 /*
+ * Several right-hand sides at once (up to 8): X and B are [nrhs][element][nb]
+ * FP64 device arrays, X holding the initial guesses.  The V-cycle of
+ * Algorithm 1 is applied to all right-hand sides together, so each element
+ * record streamed from memory serves every right-hand side.  Iteration: outer
+ * FP64 refinement X <- X + C with the FP64 residual R = B - A X; inside,
+ * `inner` steps of C <- C + V(0, R - A C) with the residual in the cycle's
+ * precision.  Stops when every ||B_q - A X_q|| <= rtol ||B_q|| or after
+ * maxit outer iterations; hist (may be NULL) gets (maxit+1) x nrhs relative
+ * residuals.  One outer iteration runs as one CUDA graph.
+ */
+int stk_solve_multi(stk_ctx* ctx, double* X_dev, const double* B_dev, int nrhs, double rtol, int maxit, int inner,
+                    int* iters_out, double* hist, void* stream);
+
+/*
  * Outer iteration of stk_solve: method 0 = iterative refinement
  * x <- x + V(0, b - A x) (default); method 1 = flexible GMRES(restart) in
  * FP64 with one V-cycle (of the stk_set_cycle precision, from a zero guess)

@@ -40,6 +40,18 @@ cudaError_t launch_element_pipe(const Pattern& pat, int storage, int mode, int p
                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
                                 int* err, int ctas, int stages, cudaStream_t st);
 void prepare_pipe_kernels();
+void prepare_mrhs_kernels();
+cudaError_t launch_element_mrhs(const Pattern& pat, int storage, int nr, int mode, int pos0, int npos,
+                                const int* perm, const int* nbr, const void* cpl, const void* mat, const void* b,
+                                void* x, void* r, cudaStream_t st);
+cudaError_t launch_restrict_mr(int vec64, int d, int s, int nb, int nr, const int* nc, const int* nf, int64_t nec,
+                               const void* P, const void* r, void* rc, cudaStream_t st);
+cudaError_t launch_prolong_mr(int vec64, int d, int s, int nb, int nr, const int* nf, const int* nc, int64_t nec,
+                              const void* PT, const void* xc, void* x, cudaStream_t st);
+cudaError_t launch_bottom_mr(int vec64, int64_t n, int nr, const double* pinv, const void* b, void* x, cudaStream_t st);
+cudaError_t launch_interleave(int kind, int64_t m, int nr, int nq, int to_interleaved, void* out, const void* in,
+                              cudaStream_t st);
+cudaError_t launch_sumsq_mr(int64_t m, int nr, const double* x, double* part, double* out, cudaStream_t st);
 cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
                                 int ctas, cudaStream_t st);
@@ -106,6 +118,12 @@ void free_device(Ctx& c) {
   if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
   c.cycle_graph = nullptr;
   c.cycle_graph_prec = -1;
+  if (c.mgraph) cudaGraphExecDestroy(c.mgraph);
+  c.mgraph = nullptr;
+  c.mgraph_key[0] = c.mgraph_key[1] = c.mgraph_key[2] = -1;
+  c.mr_nr = 0;
+  c.mX = c.mB = c.mR = c.mNorm = c.mPart = nullptr;
+  c.mRin = c.mRb = c.mAcc = nullptr;
   if (c.graph) cudaGraphExecDestroy(c.graph);
   c.graph = nullptr;
   c.graph_x = c.graph_b = nullptr;
@@ -442,6 +460,110 @@ int64_t count_points(const Ctx& c, int kind) {
   std::vector<double> xyz;
   face_points(c, kind, xyz, nullptr);
   return (int64_t)(xyz.size() / c.d);
+}
+
+// ---- several right-hand sides ----------------------------------------------------
+void ensure_mrhs(Ctx& c, int nr) {
+  if (c.mr_nr == nr) return;
+  if (c.mgraph) cudaGraphExecDestroy(c.mgraph);
+  c.mgraph = nullptr;
+  c.mgraph_key[0] = -1;
+  int L = nlevels(c);
+  for (int l = 0; l < L; ++l) {
+    DevLevel& D = c.dev[l];
+    int64_t n = level_ne(c, l) * c.nb * nr;
+    for (int v = 0; v < 2; ++v) {
+      if (v == 1 && c.precision == STK_FP64) continue;
+      size_t es = v == 0 ? 8 : 4;
+      D.mx[v] = dalloc(c, n * es);
+      D.mb[v] = dalloc(c, n * es);
+      D.mr[v] = dalloc(c, n * es);
+    }
+  }
+  int64_t m0 = level_ne(c, 0) * c.nb * nr;
+  size_t ec = c.precision == STK_FP64 ? 8 : 4;
+  c.mX = (double*)dalloc(c, m0 * 8);
+  c.mB = (double*)dalloc(c, m0 * 8);
+  c.mR = (double*)dalloc(c, m0 * 8);
+  c.mRin = dalloc(c, m0 * ec);
+  c.mRb = dalloc(c, m0 * ec);
+  c.mAcc = dalloc(c, m0 * ec);
+  c.mNorm = (double*)dalloc(c, 16 * 8);
+  c.mPart = (double*)dalloc(c, 1024 * 8 * 8);
+  c.mr_nr = nr;
+}
+
+void enqueue_cycle_mr(Ctx& c, int prec, int l, int nr, void* x, const void* b, cudaStream_t st) {
+  int vi = prec == STK_FP64 ? 0 : 1;
+  int L = nlevels(c);
+  if (l == L - 1) {
+    ck(launch_bottom_mr(vi == 0, c.nbot, nr, c.bottom_pinv, b, x, st), "bottom launch");
+    c.launches++;
+    return;
+  }
+  DevLevel& D = c.dev[l];
+  DevLevel& Dc = c.dev[l + 1];
+  auto smooth = [&](int sweeps) {
+    for (int it = 0; it < sweeps; ++it)
+      for (int col = 0; col < D.ncolour; ++col) {
+        int n = D.cstart[col + 1] - D.cstart[col];
+        if (n <= 0) continue;
+        ck(launch_element_mrhs(c.pat, prec, nr, MODE_GS, D.cstart[col], n, D.perm, D.nbr, D.cpl[prec], D.inv[prec],
+                               b, x, nullptr, st),
+           "gs launch");
+        c.launches++;
+      }
+  };
+  smooth(c.nu1);
+  ck(launch_element_mrhs(c.pat, prec, nr, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[prec], D.dia[prec], b, x,
+                         D.mr[vi], st),
+     "residual launch");
+  ck(launch_restrict_mr(vi == 0, c.d, c.s, c.nb, nr, Dc.n, D.n, Dc.ne, c.child_P[vi], D.mr[vi], Dc.mb[vi], st),
+     "restrict launch");
+  ck(cudaMemsetAsync(Dc.mx[vi], 0, (size_t)Dc.ne * c.nb * nr * (vi == 0 ? 8 : 4), st), "memset");
+  c.launches += 2;
+  enqueue_cycle_mr(c, prec, l + 1, nr, Dc.mx[vi], Dc.mb[vi], st);
+  ck(launch_prolong_mr(vi == 0, c.d, c.s, c.nb, nr, D.n, Dc.n, Dc.ne, c.child_PT[vi], Dc.mx[vi], x, st),
+     "prolong launch");
+  c.launches++;
+  smooth(c.nu2);
+}
+
+// One outer iteration on the interleaved level-0 FP64 vectors mX, mB:
+// mR = mB - A mX (FP64); Rb = mR in cycle precision; Acc = 0; then `inner`
+// times: Rin = Rb - A Acc (cycle precision; Rin = Rb the first time),
+// Acc += V(0, Rin); finally mX += Acc and the squared norms of the new
+// residual are left in mNorm / norm_host.
+void enqueue_mr_iteration(Ctx& c, int nr, int inner, cudaStream_t st) {
+  int prec = c.precision, vi = prec == STK_FP64 ? 0 : 1;
+  int64_t m0 = level_ne(c, 0) * c.nb * nr;
+  DevLevel& D0 = c.dev[0];
+  size_t ec = vi == 0 ? 8 : 4;
+  ck(launch_convert(vi == 0, 1, m0, c.mRb, c.mR, st), "convert");
+  ck(cudaMemsetAsync(c.mAcc, 0, m0 * ec, st), "memset");
+  c.launches++;
+  for (int k = 0; k < inner; ++k) {
+    const void* rin = c.mRb;
+    if (k > 0) {
+      ck(launch_element_mrhs(c.pat, prec, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[prec], D0.dia[prec],
+                             c.mRb, c.mAcc, c.mRin, st),
+         "inner residual");
+      c.launches++;
+      rin = c.mRin;
+    }
+    ck(cudaMemsetAsync(D0.mx[vi], 0, m0 * ec, st), "memset");
+    enqueue_cycle_mr(c, prec, 0, nr, D0.mx[vi], rin, st);
+    ck(launch_axpy(vi == 0, vi == 0, m0, c.mAcc, D0.mx[vi], st), "axpy");
+    c.launches++;
+  }
+  ck(launch_axpy(1, vi == 0, m0, c.mX, c.mAcc, st), "axpy");
+  c.launches++;
+  ck(launch_element_mrhs(c.pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0], c.mB, c.mX,
+                         c.mR, st),
+     "residual64");
+  ck(launch_sumsq_mr(level_ne(c, 0) * c.nb, nr, c.mR, c.mPart, c.mNorm, st), "norms");
+  c.launches += 3;
+  ck(cudaMemcpyAsync(c.norm_host, c.mNorm, nr * sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
 }
 
 // ---- flexible GMRES with the V-cycle as right preconditioner ----------------
@@ -808,6 +930,7 @@ int stk_setup(stk_ctx* c, void* stream) {
     static bool prepared[64] = {false};
     if (c->device >= 0 && c->device < 64 && !prepared[c->device]) {
       prepare_pipe_kernels();
+      prepare_mrhs_kernels();
       prepared[c->device] = true;
     }
     for (int pr = 0; pr < 3; ++pr)
@@ -1093,6 +1216,89 @@ int stk_set_solver(stk_ctx* c, int method, int restart) {
       c->kV = nullptr;   // re-sized on the next solve (old buffers stay owned until destroy)
       c->kcap = 0;
     }
+    return STK_OK;
+  });
+}
+
+int stk_solve_multi(stk_ctx* c, double* X, const double* B, int nrhs, double rtol, int maxit, int inner,
+                    int* iters_out, double* hist, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (!X || !B || nrhs < 1 || nrhs > 8 || maxit < 0 || inner < 1 || inner > 16 || !(rtol > 0))
+      return fail(c, STK_ERR_INVALID_ARG, "bad multi-rhs arguments (1 <= nrhs <= 8, 1 <= inner <= 16)");
+    int nr = nrhs <= 4 ? 4 : 8;
+    cudaStream_t user = (cudaStream_t)stream;
+    ck(cudaStreamSynchronize(user), "sync caller stream");
+    cudaStream_t st = c->stream;
+    ensure_mrhs(*c, nr);
+    int64_t m = level_ne(*c, 0) * c->nb;
+    ck(launch_interleave(0, m, nr, nrhs, 1, c->mB, B, st), "interleave");
+    ck(launch_interleave(0, m, nr, nrhs, 1, c->mX, X, st), "interleave");
+    c->launches += 2;
+    ck(launch_sumsq_mr(m, nr, c->mB, c->mPart, c->mNorm, st), "norms");
+    c->launches += 2;
+    ck(cudaMemcpyAsync(c->norm_host, c->mNorm, nr * 8, cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaStreamSynchronize(st), "sync");
+    std::vector<double> bn(nr), rel(nr);
+    for (int q = 0; q < nrhs; ++q) bn[q] = c->norm_host[q] > 0 ? std::sqrt(c->norm_host[q]) : 1.0;
+    DevLevel& D0 = c->dev[0];
+    ck(launch_element_mrhs(c->pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0], c->mB,
+                           c->mX, c->mR, st),
+       "residual64");
+    ck(launch_sumsq_mr(m, nr, c->mR, c->mPart, c->mNorm, st), "norms");
+    c->launches += 3;
+    ck(cudaMemcpyAsync(c->norm_host, c->mNorm, nr * 8, cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaStreamSynchronize(st), "sync");
+    auto check = [&](int it) {
+      bool done = true;
+      for (int q = 0; q < nrhs; ++q) {
+        rel[q] = std::sqrt(c->norm_host[q]) / bn[q];
+        if (hist) hist[(size_t)it * nrhs + q] = rel[q];
+        if (!(rel[q] <= rtol)) done = false;
+      }
+      return done;
+    };
+    std::vector<double> rel0;
+    bool done = check(0);
+    rel0 = rel;
+    int key[3] = {nr, inner, c->precision};
+    if (!c->mgraph || c->mgraph_key[0] != key[0] || c->mgraph_key[1] != key[1] || c->mgraph_key[2] != key[2]) {
+      if (c->mgraph) cudaGraphExecDestroy(c->mgraph);
+      c->mgraph = nullptr;
+      cudaGraph_t g;
+      int64_t before = c->launches;
+      ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+      try {
+        enqueue_mr_iteration(*c, nr, inner, st);
+      } catch (...) {
+        cudaStreamEndCapture(st, &g);
+        c->launches = before;
+        throw;
+      }
+      ck(cudaStreamEndCapture(st, &g), "end capture");
+      ck(cudaGraphInstantiate(&c->mgraph, g, 0), "graph instantiate");
+      cudaGraphDestroy(g);
+      c->mgraph_kernels = c->launches - before;
+      c->launches = before;
+      for (int i = 0; i < 3; ++i) c->mgraph_key[i] = key[i];
+    }
+    int it = 0;
+    while (!done && it < maxit) {
+      ck(cudaGraphLaunch(c->mgraph, st), "graph launch");
+      c->launches += c->mgraph_kernels;
+      ck(cudaStreamSynchronize(st), "sync");
+      ++it;
+      done = check(it);
+      for (int q = 0; q < nrhs; ++q)
+        if (!std::isfinite(rel[q]) || rel[q] > 1e6 * rel0[q]) {
+          if (iters_out) *iters_out = it;
+          return fail(c, STK_ERR_DIVERGED, "outer iteration diverged");
+        }
+    }
+    ck(launch_interleave(0, m, nr, nrhs, 0, X, c->mX, st), "deinterleave");
+    c->launches++;
+    ck(cudaStreamSynchronize(st), "sync");
+    if (iters_out) *iters_out = it;
     return STK_OK;
   });
 }

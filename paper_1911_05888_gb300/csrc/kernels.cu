@@ -1033,3 +1033,357 @@ cudaError_t launch_scale(int64_t n, double s, const double* x, double* y, cudaSt
 }
 
 }  // namespace stk
+
+namespace stk {
+
+// ---- several right-hand sides --------------------------------------------------
+// Vectors of NR right-hand sides are interleaved [element][row][rhs] so that
+// every coefficient loaded from an element record is applied to all NR
+// right-hand sides (the record traffic is shared, the arithmetic grows by NR).
+template <typename TS, typename TX, int S, int NR>
+__global__ void __launch_bounds__(kNT) element_mrhs_kernel(const __grid_constant__ Pattern pat, int mode,
+                                                           int pos0, int npos, const int* __restrict__ perm,
+                                                           const int* __restrict__ nbr,
+                                                           const TS* __restrict__ cpl,
+                                                           const TS* __restrict__ mat,
+                                                           const TX* __restrict__ b, TX* x, TX* rout) {
+  using Tr = StorageTraits<TS>;
+  using TA = typename Tr::Acc;
+  constexpr int V = Tr::V;
+  const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
+  const int NRV = NBP / V;
+  const int NCG = (kNT / NRV) > 0 ? (kNT / NRV) : 1;
+  const int CW = (nb + NCG - 1) / NCG;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TA* Xs = reinterpret_cast<TA*>(smem_raw);          // [NG*S][NR]
+  TA* part = Xs + pat.NG * S * NR;                    // [TRP][NR]
+  TA* g = part + TRP * NR;                            // [NBP][NR]
+  TA* xi = g + NBP * NR;                              // [NBP][NR]
+  TA* part2 = xi + NBP * NR;                          // [NCG*NBP][NR]
+  const int tid = threadIdx.x;
+  for (int pos = pos0 + blockIdx.x; pos < pos0 + npos; pos += gridDim.x) {
+    const int e = perm[pos];
+    const int* nbe = nbr + (size_t)pos * pat.NO;
+    for (int i = tid; i < pat.NG * S * NR; i += kNT) {
+      const int q = i % NR, gc = i / NR;
+      const int gi = gc / S, ci = gc - gi * S;
+      const int j = nbe[pat.g_o[gi]];
+      Xs[i] = (j >= 0) ? (TA)x[((size_t)j * nb + pat.g_cv[gi] * S + ci) * NR + q] : (TA)0;
+    }
+    for (int i = tid; i < nb * NR; i += kNT) {
+      g[i] = (TA)b[(size_t)e * nb * NR + i];
+      if (mode == MODE_RESID) xi[i] = (TA)x[(size_t)e * nb * NR + i];
+    }
+    __syncthreads();
+    const TS* rec = cpl + (size_t)pos * S * TRP;
+    for (int tv = tid; tv < TRP / V; tv += kNT) {
+      const int tr0 = tv * V;
+      int xo[V];
+      TA acc[V][NR];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int tr = tr0 + j;
+        xo[j] = (tr < TR) ? pat.task_g[tr / S] * S * NR : 0;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[j][q] = 0;
+      }
+      for (int ci = 0; ci < S; ++ci) {
+        TA w[V];
+        Tr::load(rec + (size_t)ci * TRP + tr0, w);
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const TA* xv = Xs + xo[j] + ci * NR;
+#pragma unroll
+          for (int q = 0; q < NR; ++q) acc[j][q] = fma(w[j], xv[q], acc[j][q]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) part[(tr0 + j) * NR + q] = acc[j][q];
+    }
+    __syncthreads();
+    for (int i = tid; i < nb * NR; i += kNT) {
+      const int r = i / NR, q = i - r * NR;
+      const int rv = r / S, rr = r - rv * S;
+      TA sum = 0;
+      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[(t * S + rr) * NR + q];
+      g[i] = g[i] - sum;
+    }
+    __syncthreads();
+    const TS* mrec = mat + (size_t)pos * nb * NBP;
+    const TA* vin = (mode == MODE_GS) ? g : xi;
+    for (int u = tid; u < NRV * NCG; u += kNT) {
+      const int rvv = u % NRV, cg = u / NRV;
+      const int c0 = cg * CW, c1 = min(nb, c0 + CW);
+      TA acc[V][NR];
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[j][q] = 0;
+      for (int ci = c0; ci < c1; ++ci) {
+        TA w[V];
+        Tr::load(mrec + (size_t)ci * NBP + rvv * V, w);
+        const TA* vv = vin + ci * NR;
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) acc[j][q] = fma(w[j], vv[q], acc[j][q]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) part2[(cg * NBP + rvv * V + j) * NR + q] = acc[j][q];
+    }
+    __syncthreads();
+    for (int i = tid; i < nb * NR; i += kNT) {
+      TA sum = 0;
+      for (int cg = 0; cg < NCG; ++cg) sum += part2[cg * NBP * NR + i];
+      if (mode == MODE_GS)
+        x[(size_t)e * nb * NR + i] = (TX)sum;
+      else
+        rout[(size_t)e * nb * NR + i] = (TX)(g[i] - sum);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TS, int NR>
+static size_t mrhs_smem(const Pattern& pat) {
+  using TA = typename StorageTraits<TS>::Acc;
+  constexpr int V = StorageTraits<TS>::V;
+  int NRV = pat.NBP / V;
+  int NCG = (kNT / NRV) > 0 ? (kNT / NRV) : 1;
+  size_t n = ((size_t)pat.NG * pat.s + pat.TRP + 2 * pat.NBP + (size_t)NCG * pat.NBP) * NR;
+  return n * sizeof(TA);
+}
+
+template <typename TS, typename TX, int S, int NR>
+static cudaError_t launch_mrhs_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
+                                 const void* cpl, const void* mat, const void* b, void* x, void* r, cudaStream_t st) {
+  if (npos <= 0) return cudaSuccess;
+  size_t smem = mrhs_smem<TS, NR>(pat);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (200 * 1024) / std::max<size_t>(smem, 1)));
+  int grid = std::min(npos, num_sms() * per_sm);
+  element_mrhs_kernel<TS, TX, S, NR><<<grid, kNT, smem, st>>>(pat, mode, pos0, npos, perm, nbr, (const TS*)cpl,
+                                                              (const TS*)mat, (const TX*)b, (TX*)x, (TX*)r);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TX, int S, int NR>
+static void prepare_mrhs_s() {
+  cudaFuncSetAttribute(element_mrhs_kernel<TS, TX, S, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+}
+
+template <typename TS, typename TX, int NR>
+static cudaError_t launch_mrhs_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
+                                 const void* cpl, const void* mat, const void* b, void* x, void* r, cudaStream_t st) {
+#define STK_MRHS_CASE(SV) \
+  case SV: return launch_mrhs_s<TS, TX, SV, NR>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+  switch (pat.s) {
+    STK_MRHS_CASE(4)
+    STK_MRHS_CASE(8)
+    STK_MRHS_CASE(9)
+    STK_MRHS_CASE(16)
+    STK_MRHS_CASE(25)
+    STK_MRHS_CASE(27)
+    default: return cudaErrorInvalidValue;
+  }
+#undef STK_MRHS_CASE
+}
+
+template <typename TS, typename TX, int NR>
+static void prepare_mrhs_t() {
+  prepare_mrhs_s<TS, TX, 4, NR>();
+  prepare_mrhs_s<TS, TX, 8, NR>();
+  prepare_mrhs_s<TS, TX, 9, NR>();
+  prepare_mrhs_s<TS, TX, 16, NR>();
+  prepare_mrhs_s<TS, TX, 25, NR>();
+  prepare_mrhs_s<TS, TX, 27, NR>();
+}
+
+void prepare_mrhs_kernels() {
+  prepare_mrhs_t<double, double, 4>();
+  prepare_mrhs_t<double, double, 8>();
+  prepare_mrhs_t<float, float, 4>();
+  prepare_mrhs_t<float, float, 8>();
+  prepare_mrhs_t<__nv_bfloat16, float, 4>();
+  prepare_mrhs_t<__nv_bfloat16, float, 8>();
+}
+
+// nr = 4 or 8 (callers pad to one of them).
+cudaError_t launch_element_mrhs(const Pattern& pat, int storage, int nr, int mode, int pos0, int npos,
+                                const int* perm, const int* nbr, const void* cpl, const void* mat, const void* b,
+                                void* x, void* r, cudaStream_t st) {
+  if (nr == 4) {
+    switch (storage) {
+      case 0: return launch_mrhs_t<double, double, 4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+      case 1: return launch_mrhs_t<float, float, 4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+      case 2: return launch_mrhs_t<__nv_bfloat16, float, 4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    }
+  } else if (nr == 8) {
+    switch (storage) {
+      case 0: return launch_mrhs_t<double, double, 8>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+      case 1: return launch_mrhs_t<float, float, 8>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+      case 2: return launch_mrhs_t<__nv_bfloat16, float, 8>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Restriction / prolongation / bottom solve on interleaved [element][row][rhs] vectors.
+template <typename TX>
+__global__ void restrict_mr_kernel(int d, int s, int nb, int nr, int nc0, int nc1, int nf0, int nf1, int64_t nec,
+                                   const TX* __restrict__ P, const TX* __restrict__ r, TX* __restrict__ rc) {
+  const int nch = 1 << d;
+  for (int64_t C = blockIdx.x; C < nec; C += gridDim.x) {
+    const int I0 = (int)(C % nc0), I1 = (int)((C / nc0) % nc1), I2 = (int)(C / ((int64_t)nc0 * nc1));
+    for (int o = threadIdx.x; o < nb * nr; o += blockDim.x) {
+      const int q = o % nr, vb = o / nr;
+      const int v = vb / s, bm = vb - v * s;
+      TX acc = 0;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int f0 = 2 * I0 + (ch & 1), f1 = 2 * I1 + ((ch >> 1) & 1), f2 = 2 * I2 + ((ch >> 2) & 1);
+        const int64_t f = (d == 2) ? f0 + (int64_t)nf0 * f1 : f0 + (int64_t)nf0 * (f1 + (int64_t)nf1 * f2);
+        const TX* pc = P + ch * s * s + bm;
+        const TX* rr = r + ((size_t)f * nb + v * s) * nr + q;
+        for (int a = 0; a < s; ++a) acc += pc[a * s] * rr[(size_t)a * nr];
+      }
+      rc[(size_t)C * nb * nr + o] = acc;
+    }
+  }
+}
+
+template <typename TX>
+__global__ void prolong_mr_kernel(int d, int s, int nb, int nr, int nf0, int nf1, int nc0, int nc1, int64_t nec,
+                                  const TX* __restrict__ PT, const TX* __restrict__ xc, TX* __restrict__ x) {
+  const int nch = 1 << d;
+  for (int64_t C = blockIdx.x; C < nec; C += gridDim.x) {
+    const int I0 = (int)(C % nc0), I1 = (int)((C / nc0) % nc1), I2 = (int)(C / ((int64_t)nc0 * nc1));
+    for (int o = threadIdx.x; o < nch * nb * nr; o += blockDim.x) {
+      const int q = o % nr, cva = o / nr;
+      const int ch = cva / nb, va = cva - ch * nb;
+      const int v = va / s, am = va - v * s;
+      const int f0 = 2 * I0 + (ch & 1), f1 = 2 * I1 + ((ch >> 1) & 1), f2 = 2 * I2 + ((ch >> 2) & 1);
+      const int64_t f = (d == 2) ? f0 + (int64_t)nf0 * f1 : f0 + (int64_t)nf0 * (f1 + (int64_t)nf1 * f2);
+      const TX* pc = PT + ch * s * s + am;
+      const TX* xv = xc + ((size_t)C * nb + v * s) * nr + q;
+      TX acc = 0;
+      for (int bm = 0; bm < s; ++bm) acc += pc[bm * s] * xv[(size_t)bm * nr];
+      x[((size_t)f * nb + va) * nr + q] += acc;
+    }
+  }
+}
+
+template <typename TX>
+__global__ void bottom_mr_kernel(int64_t n, int nr, const double* __restrict__ pinv, const TX* __restrict__ b,
+                                 TX* __restrict__ x) {
+  int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  for (int q = 0; q < nr; ++q) {
+    double acc = 0.0;
+    for (int64_t j = lane; j < n; j += 32) acc += pinv[row * n + j] * (double)b[j * nr + q];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[row * nr + q] = (TX)acc;
+  }
+}
+
+// out[e][r][q] = in[q][e][r] (to interleaved) or the reverse, with type change.
+template <typename TA, typename TB>
+__global__ void interleave_kernel(int64_t m, int nr, int nq, int to_interleaved, TA* __restrict__ out,
+                                  const TB* __restrict__ in) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m * nr) return;
+  const int64_t row = i / nr;
+  const int q = (int)(i - row * nr);
+  if (to_interleaved)
+    out[i] = (q < nq) ? (TA)in[(int64_t)q * m + row] : (TA)0;
+  else if (q < nq)
+    out[(int64_t)q * m + row] = (TA)in[i];
+}
+
+// part[blk][q] partial sums of squares per right-hand side of an interleaved vector.
+__global__ void sumsq_mr_kernel(int64_t m, int nr, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double sh[8][256];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < m; row += (int64_t)gridDim.x * blockDim.x)
+    for (int q = 0; q < nr; ++q) {
+      const double v = x[row * nr + q];
+      acc[q] += v * v;
+    }
+  for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if (threadIdx.x < s2)
+      for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s2];
+    __syncthreads();
+  }
+  if (threadIdx.x < nr) part[(int64_t)blockIdx.x * nr + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void sumsq_mr_final_kernel(int nblk, int nr, const double* __restrict__ part, double* __restrict__ out) {
+  const int q = threadIdx.x;
+  if (q >= nr) return;
+  double acc = 0.0;
+  for (int b2 = 0; b2 < nblk; ++b2) acc += part[(int64_t)b2 * nr + q];
+  out[q] = acc;
+}
+
+cudaError_t launch_restrict_mr(int vec64, int d, int s, int nb, int nr, const int* nc, const int* nf, int64_t nec,
+                               const void* P, const void* r, void* rc, cudaStream_t st) {
+  int grid = (int)std::min<int64_t>(nec, (int64_t)num_sms() * 8);
+  if (vec64)
+    restrict_mr_kernel<double><<<grid, 256, 0, st>>>(d, s, nb, nr, nc[0], nc[1], nf[0], nf[1], nec, (const double*)P,
+                                                     (const double*)r, (double*)rc);
+  else
+    restrict_mr_kernel<float><<<grid, 256, 0, st>>>(d, s, nb, nr, nc[0], nc[1], nf[0], nf[1], nec, (const float*)P,
+                                                    (const float*)r, (float*)rc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_mr(int vec64, int d, int s, int nb, int nr, const int* nf, const int* nc, int64_t nec,
+                              const void* PT, const void* xc, void* x, cudaStream_t st) {
+  int grid = (int)std::min<int64_t>(nec, (int64_t)num_sms() * 8);
+  if (vec64)
+    prolong_mr_kernel<double><<<grid, 256, 0, st>>>(d, s, nb, nr, nf[0], nf[1], nc[0], nc[1], nec, (const double*)PT,
+                                                    (const double*)xc, (double*)x);
+  else
+    prolong_mr_kernel<float><<<grid, 256, 0, st>>>(d, s, nb, nr, nf[0], nf[1], nc[0], nc[1], nec, (const float*)PT,
+                                                   (const float*)xc, (float*)x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bottom_mr(int vec64, int64_t n, int nr, const double* pinv, const void* b, void* x, cudaStream_t st) {
+  int bs = 256;
+  int64_t grid = (n * 32 + bs - 1) / bs;
+  if (vec64)
+    bottom_mr_kernel<double><<<grid, bs, 0, st>>>(n, nr, pinv, (const double*)b, (double*)x);
+  else
+    bottom_mr_kernel<float><<<grid, bs, 0, st>>>(n, nr, pinv, (const float*)b, (float*)x);
+  return cudaGetLastError();
+}
+
+// kind: 0 double<-double, 1 float<-double, 2 double<-float
+cudaError_t launch_interleave(int kind, int64_t m, int nr, int nq, int to_interleaved, void* out, const void* in,
+                              cudaStream_t st) {
+  int64_t grid = (m * nr + 255) / 256;
+  if (kind == 0)
+    interleave_kernel<double, double><<<grid, 256, 0, st>>>(m, nr, nq, to_interleaved, (double*)out, (const double*)in);
+  else if (kind == 1)
+    interleave_kernel<float, double><<<grid, 256, 0, st>>>(m, nr, nq, to_interleaved, (float*)out, (const double*)in);
+  else
+    interleave_kernel<double, float><<<grid, 256, 0, st>>>(m, nr, nq, to_interleaved, (double*)out, (const float*)in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq_mr(int64_t m, int nr, const double* x, double* part, double* out, cudaStream_t st) {
+  int grid = (int)std::min<int64_t>((m + 255) / 256, 1024);
+  if (grid < 1) grid = 1;
+  sumsq_mr_kernel<<<grid, 256, 0, st>>>(m, nr, x, part);
+  sumsq_mr_final_kernel<<<1, 32, 0, st>>>(grid, nr, part, out);
+  return cudaGetLastError();
+}
+
+}  // namespace stk

@@ -60,6 +60,10 @@ struct DevLevel {
   void* vx[2] = {nullptr, nullptr};
   void* vb[2] = {nullptr, nullptr};
   void* vr[2] = {nullptr, nullptr};
+  // the same for several right-hand sides, interleaved [element][row][rhs]
+  void* mx[2] = {nullptr, nullptr};
+  void* mb[2] = {nullptr, nullptr};
+  void* mr[2] = {nullptr, nullptr};
   int n[3] = {1, 1, 1};
 };
 
@@ -123,6 +127,17 @@ struct Ctx {
   int pipe_ctas[3] = {0, 0, 0}, pipe_stages[3] = {0, 0, 0};
   int warp_ctas[3] = {4, 4, 4};   // CTAs (of 8 warps) per SM for the warp-per-element kernel
   int* dev_err = nullptr;     // raised by a kernel whose bounded wait expired
+  // several right-hand sides (interleaved; nr = 4 or 8 once allocated)
+  int mr_nr = 0;
+  double *mX = nullptr, *mB = nullptr, *mR = nullptr;   // level-0 FP64
+  void* mRin = nullptr;                                  // inner right-hand side (cycle precision)
+  void* mRb = nullptr;                                   // outer residual in cycle precision
+  void* mAcc = nullptr;                                  // accumulated inner correction
+  double* mNorm = nullptr;                               // [nr] device, squared norms
+  double* mPart = nullptr;
+  cudaGraphExec_t mgraph = nullptr;
+  int mgraph_key[3] = {-1, -1, -1};                      // nr, inner, precision
+  int64_t mgraph_kernels = 0;
   std::vector<void*> allocations;
 };
 

@@ -55,6 +55,8 @@ SIGNATURES = {
     "stk_solve": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _c_int_p, _c_dbl_p, _vp],
     "stk_residual_norm_static": [_vp, _vp, _vp, _vp, _vp, _vp],
     "stk_set_solver": [_vp, ctypes.c_int, ctypes.c_int],
+    "stk_solve_multi": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_int_p,
+                        _c_dbl_p, _vp],
     "stk_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "stk_launch_count": [_vp, _c_i64_p],
 }
@@ -247,6 +249,14 @@ class Context:
         scalar norm2, using only the library's fixed static scratch."""
         self._check(self.lib.stk_residual_norm_static(self.h, _ptr(x), _ptr(b), _ptr(r), _ptr(norm2),
                                                       _stream(stream)), "stk_residual_norm_static")
+
+    def solve_multi(self, X, B, nrhs, rtol=1e-10, maxit=50, inner=1, stream=None):
+        it = ctypes.c_int()
+        hist = np.zeros((maxit + 1) * nrhs)
+        rc = self.lib.stk_solve_multi(self.h, _ptr(X), _ptr(B), nrhs, rtol, maxit, inner, ctypes.byref(it),
+                                      hist.ctypes.data_as(_c_dbl_p), _stream(stream))
+        self._check(rc, "stk_solve_multi")
+        return it.value, hist[: (it.value + 1) * nrhs].reshape(it.value + 1, nrhs)
 
     def set_tuning(self, variant, precision, ctas_per_sm=0, stages=0):
         self._check(self.lib.stk_set_tuning(self.h, variant, precision, ctas_per_sm, stages), "stk_set_tuning")

@@ -239,3 +239,38 @@ def test_kernel_variants_agree(name, variant):
         assert rel(r.cpu().numpy(), orc.residual(0, xo, b)) <= 1e-12
     finally:
         gpu.ctx.set_tuning(2, native.FP64)
+
+
+@pytest.mark.parametrize("nrhs", [3, 8])
+@pytest.mark.parametrize("name", ["stress16p3", "3d-mixed-p1"])
+def test_multi_rhs_iteration_matches_oracle(name, nrhs):
+    """One outer iteration for several right-hand sides at once equals, per
+    right-hand side, x1 = x0 + V(0, b - A x0) of the oracle (FP64)."""
+    prob, gpu, orc = get(name)
+    rng = np.random.default_rng(31)
+    X0 = rng.uniform(-1, 1, (nrhs, prob.n_dofs))
+    B = rng.uniform(-1, 1, (nrhs, prob.n_dofs))
+    Xd, Bd = dev(X0).reshape(nrhs, -1), dev(B).reshape(nrhs, -1)
+    it, hist = gpu.ctx.solve_multi(Xd, Bd, nrhs, rtol=1e-30, maxit=1, inner=1)
+    assert it == 1
+    Xg = Xd.cpu().numpy()
+    for q in range(nrhs):
+        ref = X0[q] + orc.precondition(B[q] - orc.A @ X0[q])
+        assert rel(Xg[q], ref) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,inner", [(native.FP64, 1), (native.FP32, 1), (native.FP32, 3), (native.BF16, 3)])
+def test_multi_rhs_solve_converges(precision, inner):
+    name = "stress16p3"
+    prob, gpu64, _ = get(name)
+    _, gpu, _ = get(name, precision)
+    nrhs = 5
+    rng = np.random.default_rng(8)
+    B = rng.uniform(-1, 1, (nrhs, prob.n_dofs))
+    Bd = dev(B).reshape(nrhs, -1)
+    Xd = torch.zeros_like(Bd)
+    it, hist = gpu.ctx.solve_multi(Xd, Bd, nrhs, rtol=1e-10, maxit=60, inner=inner)
+    assert np.all(hist[-1] <= 1e-10), hist[-1]
+    x1 = torch.zeros_like(Bd[1])
+    gpu64.ctx.solve(x1, Bd[1].contiguous(), rtol=1e-12, maxit=200)
+    assert rel(Xd[1].cpu().numpy(), x1.cpu().numpy()) <= 1e-8
