@@ -52,6 +52,25 @@ cudaError_t launch_bottom_mr(int vec64, int64_t n, int nr, const double* pinv, c
 cudaError_t launch_interleave(int kind, int64_t m, int nr, int nq, int to_interleaved, void* out, const void* in,
                               cudaStream_t st);
 cudaError_t launch_sumsq_mr(int64_t m, int nr, const double* x, double* part, double* out, cudaStream_t st);
+cudaError_t launch_features(int ne, int nb, int nface, int NO, int ldf, const int* nbr_nat, const float* r, float* F,
+                            float* nrm, cudaStream_t st);
+cudaError_t launch_sgemm(int M, int N, int K, int ta, int tb, const float* A, int lda, const float* B, int ldb,
+                         float* C, int ldc, const float* bias, int act, float alpha, float beta, cudaStream_t st);
+cudaError_t launch_colsum(int M, int N, const float* A, int lda, float* out, float alpha, cudaStream_t st);
+cudaError_t launch_mse_grad(int64_t n, float scale, const float* Y, const float* T, float* dY, float* part,
+                            cudaStream_t st);
+cudaError_t launch_tanh_back(int64_t n, const float* H, float* dH, cudaStream_t st);
+cudaError_t launch_adam(int64_t n, float lr, float b1, float b2, float c1, float c2, float eps, float* w,
+                        const float* g, float* m, float* v, cudaStream_t st);
+cudaError_t launch_apply_correction(int ne, int nb, int ldy, const float* x, const float* nrm, const float* Y, float* xt,
+                                    cudaStream_t st);
+cudaError_t launch_accept(int64_t n, const double* sums, const float* xt, float* x, int* counters, cudaStream_t st);
+cudaError_t launch_sumsq_f(int64_t n, const float* x, double* part, double* out, cudaStream_t st);
+cudaError_t launch_smooth_field(int ne, int nb, int s, int d, const int* n_dev, uint64_t seed, float* x,
+                                cudaStream_t st);
+cudaError_t launch_target(int ne, int nb, int ldt, const float* xs, const float* x, const float* nrm, float* T,
+                          cudaStream_t st);
+cudaError_t launch_scale_f(int64_t n, float a, const float* x, float* y, cudaStream_t st);
 cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
                                 int ctas, cudaStream_t st);
@@ -376,6 +395,24 @@ void setup_bottom(Ctx& c) {
      "copy bottom");
 }
 
+// ---- learned post-smoother on the finest level -------------------------------------
+void enqueue_learned(Ctx& c, int prec, void* xv, const void* bv, cudaStream_t st) {
+  DevLevel& D0 = c.dev[0];
+  const int ne = D0.ne, nb = c.nb, nface = 2 * c.d;
+  float* x = (float*)xv;
+  ck(run_element(c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bv, xv, D0.vr[1], st), "learned residual");
+  ck(launch_features(ne, nb, nface, c.pat.NO, c.l_ldf, c.l_nbr, (const float*)D0.vr[1], c.lF, c.lnrm, st), "features");
+  ck(launch_sgemm(ne, c.l_hid, c.l_in, 0, 0, c.lF, c.l_ldf, c.lW1, c.l_hid, c.lH, c.l_hid, c.lb1, 1, 1.f, 0.f, st),
+     "layer 1");
+  ck(launch_sgemm(ne, nb, c.l_hid, 0, 0, c.lH, c.l_hid, c.lW2, nb, c.lY, nb, c.lb2, 0, 1.f, 0.f, st), "layer 2");
+  ck(launch_apply_correction(ne, nb, nb, x, c.lnrm, c.lY, c.lxt, st), "correction");
+  ck(run_element(c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bv, c.lxt, c.lrt, st), "learned residual");
+  ck(launch_sumsq_f((int64_t)ne * nb, (const float*)D0.vr[1], c.lsums + 16, c.lsums, st), "norm");
+  ck(launch_sumsq_f((int64_t)ne * nb, c.lrt, c.lsums + 16, c.lsums + 1, st), "norm");
+  ck(launch_accept((int64_t)ne * nb, c.lsums, c.lxt, x, c.lcount, st), "accept");
+  c.launches += 12;
+}
+
 // ---- the V-cycle (Algorithm 1) ------------------------------------------------
 // prec: storage precision of the blocks; vectors FP64 when prec == 0, else FP32.
 void enqueue_smooth(Ctx& c, int prec, int l, int sweeps, void* x, const void* b, cudaStream_t st) {
@@ -410,6 +447,7 @@ void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t
      "prolong launch");
   c.launches++;
   enqueue_smooth(c, prec, l, c.nu2, x, b, st);
+  if (l == 0 && c.learn_on && prec != STK_FP64 && c.lW1) enqueue_learned(c, prec, x, b, st);
 }
 
 void enqueue_residual64(Ctx& c, const double* x, const double* b, double* r, cudaStream_t st) {
@@ -1299,6 +1337,295 @@ int stk_solve_multi(stk_ctx* c, double* X, const double* B, int nrhs, double rto
     c->launches++;
     ck(cudaStreamSynchronize(st), "sync");
     if (iters_out) *iters_out = it;
+    return STK_OK;
+  });
+}
+
+static void invalidate_graphs(Ctx& c) {
+  if (c.graph) cudaGraphExecDestroy(c.graph);
+  c.graph = nullptr;
+  c.graph_x = c.graph_b = nullptr;
+  if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
+  c.cycle_graph = nullptr;
+  c.cycle_graph_prec = -1;
+  if (c.mgraph) cudaGraphExecDestroy(c.mgraph);
+  c.mgraph = nullptr;
+  c.mgraph_key[0] = -1;
+}
+
+// splitmix-style deterministic weight initialisation, uniform(-a, a)
+static void init_uniform(std::vector<float>& w, uint64_t seed, float a) {
+  uint64_t z = seed;
+  for (auto& v : w) {
+    z += 0x9E3779B97F4A7C15ULL;
+    uint64_t t = z;
+    t = (t ^ (t >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    t = (t ^ (t >> 27)) * 0x94D049BB133111EBULL;
+    t ^= t >> 31;
+    v = a * (float)((double)(t >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+  }
+}
+
+int stk_learn_setup(stk_ctx* c, int hidden, uint64_t seed) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (c->precision == STK_FP64) return fail(c, STK_ERR_INVALID_ARG, "the learned smoother runs in FP32/BF16 cycles");
+    if (hidden < 8 || hidden > 512) return fail(c, STK_ERR_INVALID_ARG, "hidden width must be in 8..512");
+    const int nb = c->nb, ne = c->dev[0].ne;
+    c->l_in = (1 + 2 * c->d) * nb;
+    c->l_ldf = (c->l_in + 3) / 4 * 4;
+    c->l_hid = hidden;
+    int64_t n1 = (int64_t)c->l_in * hidden, n2 = hidden, n3 = (int64_t)hidden * nb, n4 = nb;
+    c->l_nparam = n1 + n2 + n3 + n4;
+    float* wbase = (float*)dalloc(*c, c->l_nparam * 4);
+    c->lW1 = wbase;
+    c->lb1 = wbase + n1;
+    c->lW2 = c->lb1 + n2;
+    c->lb2 = c->lW2 + n3;
+    c->lgrad = (float*)dalloc(*c, c->l_nparam * 4);
+    c->lm = (float*)dalloc(*c, c->l_nparam * 4);
+    c->lv = (float*)dalloc(*c, c->l_nparam * 4);
+    ck(cudaMemset(c->lm, 0, c->l_nparam * 4), "memset");
+    ck(cudaMemset(c->lv, 0, c->l_nparam * 4), "memset");
+    std::vector<float> w(c->l_nparam, 0.f);
+    std::vector<float> w1(n1), w2(n3);
+    init_uniform(w1, seed, 1.f / std::sqrt((float)c->l_in));
+    init_uniform(w2, seed ^ 0x5DEECE66DULL, 0.1f / std::sqrt((float)hidden));   // start near zero correction
+    std::copy(w1.begin(), w1.end(), w.begin());
+    std::copy(w2.begin(), w2.end(), w.begin() + n1 + n2);
+    ck(cudaMemcpy(wbase, w.data(), c->l_nparam * 4, cudaMemcpyHostToDevice), "copy weights");
+    c->l_adam_t = 0;
+    c->l_nbr = (int*)dalloc(*c, (size_t)ne * c->pat.NO * 4);
+    ck(cudaMemcpy(c->l_nbr, c->host[0].nbr.data(), (size_t)ne * c->pat.NO * 4, cudaMemcpyHostToDevice), "copy nbr");
+    c->lF = (float*)dalloc(*c, (size_t)ne * c->l_ldf * 4);
+    c->lH = (float*)dalloc(*c, (size_t)ne * hidden * 4);
+    c->lY = (float*)dalloc(*c, (size_t)ne * nb * 4);
+    c->lnrm = (float*)dalloc(*c, (size_t)ne * 4);
+    c->lxt = (float*)dalloc(*c, (size_t)ne * nb * 4);
+    c->lrt = (float*)dalloc(*c, (size_t)ne * nb * 4);
+    c->lsums = (double*)dalloc(*c, 1024 * 8);
+    c->lcount = (int*)dalloc(*c, 16);
+    ck(cudaMemset(c->lcount, 0, 16), "memset");
+    c->lTX = c->lTT = nullptr;
+    c->l_rows = c->l_cap = 0;
+    invalidate_graphs(*c);
+    return STK_OK;
+  });
+}
+
+int stk_learn_generate(stk_ctx* c, int nseeds, int cycles, uint64_t seed) {
+  return guard(c, [&]() -> int {
+    if (!c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
+    if (nseeds < 1 || cycles < 1) return fail(c, STK_ERR_INVALID_ARG, "bad sample counts");
+    const int nb = c->nb, ne = c->dev[0].ne, prec = c->precision;
+    DevLevel& D0 = c->dev[0];
+    cudaStream_t st = c->stream;
+    int64_t need = (int64_t)nseeds * cycles * ne;
+    if (need > c->l_cap) {
+      c->lTX = (float*)dalloc(*c, (size_t)need * c->l_ldf * 4);
+      c->lTT = (float*)dalloc(*c, (size_t)need * nb * 4);
+      c->l_cap = need;
+    }
+    c->l_rows = 0;
+    int* ndev = (int*)dalloc(*c, 16);
+    ck(cudaMemcpy(ndev, c->host[0].n, 3 * sizeof(int), cudaMemcpyHostToDevice), "copy n");
+    float* xs = (float*)dalloc(*c, (size_t)ne * nb * 4);
+    float* bb = (float*)dalloc(*c, (size_t)ne * nb * 4);
+    float* zero = (float*)dalloc(*c, (size_t)ne * nb * 4);
+    ck(cudaMemsetAsync(zero, 0, (size_t)ne * nb * 4, st), "memset");
+    int on = c->learn_on;
+    c->learn_on = 0;   // data come from the plain V-cycle
+    for (int sd = 0; sd < nseeds; ++sd) {
+      ck(launch_smooth_field(ne, nb, c->s, c->d, ndev, seed + 7919ULL * sd, xs, st), "field");
+      // b = A x*: the residual of x* against a zero right-hand side is -A x*.
+      ck(run_element(*c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], zero, xs, D0.vr[1], st), "matvec");
+      ck(launch_scale_f((int64_t)ne * nb, -1.f, (const float*)D0.vr[1], bb, st), "negate");
+      float* x = (float*)D0.vx[1];
+      ck(cudaMemsetAsync(x, 0, (size_t)ne * nb * 4, st), "memset");
+      for (int k = 0; k < cycles; ++k) {
+        enqueue_cycle(*c, prec, 0, x, bb, st);
+        ck(run_element(*c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bb, x, D0.vr[1], st), "residual");
+        float* F = c->lTX + (size_t)c->l_rows * c->l_ldf;
+        float* T = c->lTT + (size_t)c->l_rows * nb;
+        ck(launch_features(ne, nb, 2 * c->d, c->pat.NO, c->l_ldf, c->l_nbr, (const float*)D0.vr[1], F, c->lnrm, st),
+           "features");
+        ck(launch_target(ne, nb, nb, xs, x, c->lnrm, T, st), "target");
+        c->l_rows += ne;
+      }
+    }
+    ck(cudaStreamSynchronize(st), "sync");
+    c->learn_on = on;
+    return STK_OK;
+  });
+}
+
+int stk_learn_train(stk_ctx* c, int epochs, int batch, double lr, uint64_t seed, double* loss_out) {
+  return guard(c, [&]() -> int {
+    if (!c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
+    if (c->l_rows <= 0) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_generate first");
+    if (epochs < 1 || batch < 32 || !(lr > 0)) return fail(c, STK_ERR_INVALID_ARG, "bad training options");
+    const int nb = c->nb, H = c->l_hid, IN = c->l_in, ldf = c->l_ldf;
+    batch = (int)std::min<int64_t>(batch, c->l_rows);
+    cudaStream_t st = c->stream;
+    float* Hb = (float*)dalloc(*c, (size_t)batch * H * 4);
+    float* Yb = (float*)dalloc(*c, (size_t)batch * nb * 4);
+    float* dY = (float*)dalloc(*c, (size_t)batch * nb * 4);
+    float* dH = (float*)dalloc(*c, (size_t)batch * H * 4);
+    float* part = (float*)dalloc(*c, 256 * 4);
+    float* gW1 = c->lgrad;
+    float* gb1 = gW1 + (int64_t)IN * H;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + (int64_t)H * nb;
+    const int64_t nbatches = std::max<int64_t>(1, c->l_rows / batch);
+    uint64_t z = seed;
+    double loss = 0.0;
+    std::vector<float> ph(256);
+    for (int ep = 0; ep < epochs; ++ep) {
+      double ep_loss = 0.0;
+      for (int64_t bi = 0; bi < nbatches; ++bi) {
+        z = z * 6364136223846793005ULL + 1442695040888963407ULL;
+        const int64_t off = (int64_t)((z >> 33) % (uint64_t)(c->l_rows - batch + 1));
+        const float* X = c->lTX + (size_t)off * ldf;
+        const float* T = c->lTT + (size_t)off * nb;
+        ck(launch_sgemm(batch, H, IN, 0, 0, X, ldf, c->lW1, H, Hb, H, c->lb1, 1, 1.f, 0.f, st), "fwd1");
+        ck(launch_sgemm(batch, nb, H, 0, 0, Hb, H, c->lW2, nb, Yb, nb, c->lb2, 0, 1.f, 0.f, st), "fwd2");
+        ck(launch_mse_grad((int64_t)batch * nb, 1.f / batch, Yb, T, dY, part, st), "loss");
+        ck(launch_sgemm(H, nb, batch, 1, 0, Hb, H, dY, nb, gW2, nb, nullptr, 0, 1.f, 0.f, st), "gW2");
+        ck(launch_colsum(batch, nb, dY, nb, gb2, 1.f, st), "gb2");
+        ck(launch_sgemm(batch, H, nb, 0, 1, dY, nb, c->lW2, nb, dH, H, nullptr, 0, 1.f, 0.f, st), "dH");
+        ck(launch_tanh_back((int64_t)batch * H, Hb, dH, st), "tanh'");
+        ck(launch_sgemm(IN, H, batch, 1, 0, X, ldf, dH, H, gW1, H, nullptr, 0, 1.f, 0.f, st), "gW1");
+        ck(launch_colsum(batch, H, dH, H, gb1, 1.f, st), "gb1");
+        c->l_adam_t++;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - std::pow(b1, (float)c->l_adam_t), c2 = 1.f - std::pow(b2, (float)c->l_adam_t);
+        ck(launch_adam(c->l_nparam, (float)lr, b1, b2, c1, c2, 1e-8f, c->lW1, c->lgrad, c->lm, c->lv, st), "adam");
+        c->launches += 10;
+        if (bi == nbatches - 1 || (bi % 64) == 63) {
+          ck(cudaMemcpyAsync(ph.data(), part, 256 * 4, cudaMemcpyDeviceToHost, st), "copy loss");
+          ck(cudaStreamSynchronize(st), "sync");
+          double l = 0.0;
+          for (float v : ph) l += v;
+          ep_loss = l / batch;
+        }
+      }
+      loss = ep_loss;
+    }
+    if (loss_out) *loss_out = loss;
+    return STK_OK;
+  });
+}
+
+int stk_learn_infer(stk_ctx* c, const float* r, float* y, float* nrm) {
+  return guard(c, [&]() -> int {
+    if (!c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
+    if (!r || !y || !nrm) return fail(c, STK_ERR_INVALID_ARG, "null vector");
+    const int ne = c->dev[0].ne, nb = c->nb;
+    cudaStream_t st = c->stream;
+    ck(launch_features(ne, nb, 2 * c->d, c->pat.NO, c->l_ldf, c->l_nbr, r, c->lF, nrm, st), "features");
+    ck(launch_sgemm(ne, c->l_hid, c->l_in, 0, 0, c->lF, c->l_ldf, c->lW1, c->l_hid, c->lH, c->l_hid, c->lb1, 1, 1.f,
+                    0.f, st),
+       "layer 1");
+    ck(launch_sgemm(ne, nb, c->l_hid, 0, 0, c->lH, c->l_hid, c->lW2, nb, y, nb, c->lb2, 0, 1.f, 0.f, st), "layer 2");
+    c->launches += 3;
+    ck(cudaStreamSynchronize(st), "sync");
+    return STK_OK;
+  });
+}
+
+int stk_learn_rows(stk_ctx* c, int64_t row0, int rows, float* F, float* T) {
+  return guard(c, [&]() -> int {
+    if (!c->lTX || row0 < 0 || rows < 1 || row0 + rows > c->l_rows || !F || !T)
+      return fail(c, STK_ERR_INVALID_ARG, "bad training-row range");
+    ck(cudaMemcpy(F, c->lTX + (size_t)row0 * c->l_ldf, (size_t)rows * c->l_ldf * 4, cudaMemcpyDeviceToHost), "copy");
+    ck(cudaMemcpy(T, c->lTT + (size_t)row0 * c->nb, (size_t)rows * c->nb * 4, cudaMemcpyDeviceToHost), "copy");
+    return STK_OK;
+  });
+}
+
+int stk_learn_grad(stk_ctx* c, int64_t row0, int rows, float* grad, double* loss_out) {
+  return guard(c, [&]() -> int {
+    if (!c->lTX || row0 < 0 || rows < 1 || row0 + rows > c->l_rows || !grad)
+      return fail(c, STK_ERR_INVALID_ARG, "bad training-row range");
+    const int nb = c->nb, H = c->l_hid, IN = c->l_in, ldf = c->l_ldf;
+    cudaStream_t st = c->stream;
+    float* Hb = (float*)dalloc(*c, (size_t)rows * H * 4);
+    float* Yb = (float*)dalloc(*c, (size_t)rows * nb * 4);
+    float* dY = (float*)dalloc(*c, (size_t)rows * nb * 4);
+    float* dH = (float*)dalloc(*c, (size_t)rows * H * 4);
+    float* part = (float*)dalloc(*c, 256 * 4);
+    float* gW1 = c->lgrad;
+    float* gb1 = gW1 + (int64_t)IN * H;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + (int64_t)H * nb;
+    const float* X = c->lTX + (size_t)row0 * ldf;
+    const float* T = c->lTT + (size_t)row0 * nb;
+    ck(launch_sgemm(rows, H, IN, 0, 0, X, ldf, c->lW1, H, Hb, H, c->lb1, 1, 1.f, 0.f, st), "fwd1");
+    ck(launch_sgemm(rows, nb, H, 0, 0, Hb, H, c->lW2, nb, Yb, nb, c->lb2, 0, 1.f, 0.f, st), "fwd2");
+    ck(launch_mse_grad((int64_t)rows * nb, 1.f / rows, Yb, T, dY, part, st), "loss");
+    ck(launch_sgemm(H, nb, rows, 1, 0, Hb, H, dY, nb, gW2, nb, nullptr, 0, 1.f, 0.f, st), "gW2");
+    ck(launch_colsum(rows, nb, dY, nb, gb2, 1.f, st), "gb2");
+    ck(launch_sgemm(rows, H, nb, 0, 1, dY, nb, c->lW2, nb, dH, H, nullptr, 0, 1.f, 0.f, st), "dH");
+    ck(launch_tanh_back((int64_t)rows * H, Hb, dH, st), "tanh'");
+    ck(launch_sgemm(IN, H, rows, 1, 0, X, ldf, dH, H, gW1, H, nullptr, 0, 1.f, 0.f, st), "gW1");
+    ck(launch_colsum(rows, H, dH, H, gb1, 1.f, st), "gb1");
+    c->launches += 9;
+    std::vector<float> ph(256);
+    ck(cudaMemcpyAsync(ph.data(), part, 256 * 4, cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaMemcpyAsync(grad, c->lgrad, c->l_nparam * 4, cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaStreamSynchronize(st), "sync");
+    double l = 0.0;
+    for (float v : ph) l += v;
+    if (loss_out) *loss_out = l / rows;
+    return STK_OK;
+  });
+}
+
+int stk_learn_enable(stk_ctx* c, int on) {
+  return guard(c, [&]() -> int {
+    if (on && !c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
+    c->learn_on = on ? 1 : 0;
+    invalidate_graphs(*c);
+    if (c->lcount) ck(cudaMemset(c->lcount, 0, 16), "memset");
+    return STK_OK;
+  });
+}
+
+int stk_learn_sizes(stk_ctx* c, int* in, int* hidden, int* out, int64_t* nparam, int64_t* rows) {
+  return guard(c, [&]() -> int {
+    if (!c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
+    if (in) *in = c->l_in;
+    if (hidden) *hidden = c->l_hid;
+    if (out) *out = c->nb;
+    if (nparam) *nparam = c->l_nparam;
+    if (rows) *rows = c->l_rows;
+    return STK_OK;
+  });
+}
+
+int stk_learn_stats(stk_ctx* c, int64_t* accepted, int64_t* rejected) {
+  return guard(c, [&]() -> int {
+    int h[2] = {0, 0};
+    if (c->lcount) {
+      ck(cudaDeviceSynchronize(), "sync");
+      ck(cudaMemcpy(h, c->lcount, 2 * sizeof(int), cudaMemcpyDeviceToHost), "copy counters");
+    }
+    if (accepted) *accepted = h[0];
+    if (rejected) *rejected = h[1];
+    return STK_OK;
+  });
+}
+
+int stk_learn_weights(stk_ctx* c, float* host, int64_t count, int direction) {
+  return guard(c, [&]() -> int {
+    if (!c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
+    if (!host || count != c->l_nparam) return fail(c, STK_ERR_INVALID_ARG, "weight count mismatch");
+    if (direction == 0)
+      ck(cudaMemcpy(host, c->lW1, count * 4, cudaMemcpyDeviceToHost), "copy weights");
+    else {
+      ck(cudaMemcpy(c->lW1, host, count * 4, cudaMemcpyHostToDevice), "copy weights");
+      invalidate_graphs(*c);
+    }
     return STK_OK;
   });
 }

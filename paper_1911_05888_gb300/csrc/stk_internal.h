@@ -135,6 +135,18 @@ struct Ctx {
   void* mAcc = nullptr;                                  // accumulated inner correction
   double* mNorm = nullptr;                               // [nr] device, squared norms
   double* mPart = nullptr;
+  // learned element-local post-smoother (finest level, low-precision cycles)
+  int learn_on = 0, l_in = 0, l_hid = 0, l_ldf = 0;
+  float *lW1 = nullptr, *lb1 = nullptr, *lW2 = nullptr, *lb2 = nullptr;   // [in][hid], [hid], [hid][nb], [nb]
+  float *lgrad = nullptr, *lm = nullptr, *lv = nullptr;                   // packed like the weights
+  int64_t l_nparam = 0;
+  int* l_nbr = nullptr;         // natural-order neighbour table of level 0
+  float *lF = nullptr, *lH = nullptr, *lY = nullptr, *lnrm = nullptr, *lxt = nullptr, *lrt = nullptr;
+  double* lsums = nullptr;      // [0] ||r||^2, [1] ||r_t||^2, then partials
+  int* lcount = nullptr;        // accepted, rejected
+  float *lTX = nullptr, *lTT = nullptr;   // training features / targets
+  int64_t l_rows = 0, l_cap = 0;
+  int l_adam_t = 0;
   cudaGraphExec_t mgraph = nullptr;
   int mgraph_key[3] = {-1, -1, -1};                      // nr, inner, precision
   int64_t mgraph_kernels = 0;

@@ -55,6 +55,16 @@ SIGNATURES = {
     "stk_solve": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _c_int_p, _c_dbl_p, _vp],
     "stk_residual_norm_static": [_vp, _vp, _vp, _vp, _vp, _vp],
     "stk_set_solver": [_vp, ctypes.c_int, ctypes.c_int],
+    "stk_learn_setup": [_vp, ctypes.c_int, ctypes.c_uint64],
+    "stk_learn_generate": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64],
+    "stk_learn_train": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _c_dbl_p],
+    "stk_learn_enable": [_vp, ctypes.c_int],
+    "stk_learn_stats": [_vp, _c_i64_p, _c_i64_p],
+    "stk_learn_weights": [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.c_int],
+    "stk_learn_sizes": [_vp, _c_int_p, _c_int_p, _c_int_p, _c_i64_p, _c_i64_p],
+    "stk_learn_infer": [_vp, _vp, _vp, _vp],
+    "stk_learn_rows": [_vp, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+    "stk_learn_grad": [_vp, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_float), _c_dbl_p],
     "stk_solve_multi": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_int_p,
                         _c_dbl_p, _vp],
     "stk_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
@@ -257,6 +267,61 @@ class Context:
                                       hist.ctypes.data_as(_c_dbl_p), _stream(stream))
         self._check(rc, "stk_solve_multi")
         return it.value, hist[: (it.value + 1) * nrhs].reshape(it.value + 1, nrhs)
+
+    def learn_setup(self, hidden=64, seed=0):
+        self._check(self.lib.stk_learn_setup(self.h, hidden, seed), "stk_learn_setup")
+
+    def learn_generate(self, nseeds, cycles, seed=0):
+        self._check(self.lib.stk_learn_generate(self.h, nseeds, cycles, seed), "stk_learn_generate")
+
+    def learn_train(self, epochs, batch=4096, lr=1e-3, seed=0):
+        loss = ctypes.c_double()
+        self._check(self.lib.stk_learn_train(self.h, epochs, batch, lr, seed, ctypes.byref(loss)), "stk_learn_train")
+        return loss.value
+
+    def learn_sizes(self):
+        i, h, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        n, r = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.stk_learn_sizes(self.h, ctypes.byref(i), ctypes.byref(h), ctypes.byref(o),
+                                             ctypes.byref(n), ctypes.byref(r)), "stk_learn_sizes")
+        return i.value, h.value, o.value, n.value, r.value
+
+    def learn_infer(self, r, y, nrm):
+        self._check(self.lib.stk_learn_infer(self.h, _ptr(r), _ptr(y), _ptr(nrm)), "stk_learn_infer")
+
+    def learn_rows(self, row0, rows, width, nb):
+        F = np.zeros((rows, width), dtype=np.float32)
+        T = np.zeros((rows, nb), dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        self._check(self.lib.stk_learn_rows(self.h, row0, rows, F.ctypes.data_as(fp), T.ctypes.data_as(fp)),
+                    "stk_learn_rows")
+        return F, T
+
+    def learn_grad(self, row0, rows, nparam):
+        g = np.zeros(nparam, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self.lib.stk_learn_grad(self.h, row0, rows, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                            ctypes.byref(loss)), "stk_learn_grad")
+        return loss.value, g
+
+    def learn_enable(self, on):
+        self._check(self.lib.stk_learn_enable(self.h, 1 if on else 0), "stk_learn_enable")
+
+    def learn_stats(self):
+        a, r = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.stk_learn_stats(self.h, ctypes.byref(a), ctypes.byref(r)), "stk_learn_stats")
+        return a.value, r.value
+
+    def learn_weights(self, count, values=None):
+        """Read (values None) or write the learned smoother's weights."""
+        if values is None:
+            out = np.zeros(count, dtype=np.float32)
+            self._check(self.lib.stk_learn_weights(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                   count, 0), "stk_learn_weights")
+            return out
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        self._check(self.lib.stk_learn_weights(self.h, v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), count, 1),
+                    "stk_learn_weights")
 
     def set_tuning(self, variant, precision, ctas_per_sm=0, stages=0):
         self._check(self.lib.stk_set_tuning(self.h, variant, precision, ctas_per_sm, stages), "stk_set_tuning")

@@ -274,3 +274,65 @@ def test_multi_rhs_solve_converges(precision, inner):
     x1 = torch.zeros_like(Bd[1])
     gpu64.ctx.solve(x1, Bd[1].contiguous(), rtol=1e-12, maxit=200)
     assert rel(Xd[1].cpu().numpy(), x1.cpu().numpy()) <= 1e-8
+
+
+def _learned_ctx():
+    prob = P.stress_variable_mu_2d(n=16, p=3)
+    gpu = StokesMG(prob, precision=native.FP32, nu=(3, 3))
+    gpu.ctx.learn_setup(hidden=32, seed=5)
+    return prob, gpu
+
+
+def test_learned_features_and_mlp_match_oracle():
+    from oracle import learned, ldg as oldg
+    prob, gpu = _learned_ctx()
+    nin, hid, nout, npar, _ = gpu.ctx.learn_sizes()
+    w = gpu.ctx.learn_weights(npar).astype(np.float64)
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal((prob.n_elements, prob.nb)).astype(np.float32)
+    rd = torch.from_numpy(r.ravel()).cuda()
+    y = torch.empty_like(rd)
+    nrm = torch.empty(prob.n_elements, dtype=torch.float32, device="cuda")
+    gpu.ctx.learn_infer(rd, y, nrm)
+    mesh = oldg.Mesh(prob.d, prob.n, prob.lo, prob.hi, prob.bc)
+    F, n_ref = learned.features(r.astype(np.float64), learned.face_neighbours(mesh))
+    y_ref, _ = learned.forward(F, w, nin, hid, nout)
+    assert rel(nrm.cpu().numpy(), n_ref) <= 1e-6
+    assert rel(y.cpu().numpy().reshape(prob.n_elements, -1), y_ref) <= 1e-5
+    gpu.close()
+
+
+def test_learned_training_gradient_matches_oracle_backprop():
+    from oracle import learned
+    prob, gpu = _learned_ctx()
+    gpu.ctx.learn_generate(nseeds=2, cycles=2, seed=11)
+    nin, hid, nout, npar, rows = gpu.ctx.learn_sizes()
+    assert rows == 2 * 2 * prob.n_elements
+    width = (nin + 3) // 4 * 4
+    F, T = gpu.ctx.learn_rows(100, 200, width, prob.nb)
+    assert np.all(np.isfinite(F)) and np.all(np.isfinite(T))
+    loss, g = gpu.ctx.learn_grad(100, 200, npar)
+    w = gpu.ctx.learn_weights(npar).astype(np.float64)
+    loss_ref, g_ref = learned.loss_and_grad(F.astype(np.float64), T.astype(np.float64), w, nin, hid, nout)
+    assert abs(loss - loss_ref) <= 1e-4 * loss_ref
+    assert rel(g, g_ref) <= 1e-4
+    gpu.close()
+
+
+def test_learned_smoother_solve_converges_and_is_judged():
+    """Train on plain V-cycle pairs, enable, solve with FGMRES: reaches 1e-10;
+    every cycle's correction is accepted or rejected on the device."""
+    prob, gpu = _learned_ctx()
+    gpu.ctx.learn_generate(nseeds=4, cycles=3, seed=1)
+    loss0 = gpu.ctx.learn_train(epochs=1, batch=512, lr=1e-3, seed=2)
+    loss1 = gpu.ctx.learn_train(epochs=20, batch=512, lr=1e-3, seed=3)
+    assert np.isfinite(loss1) and loss1 <= loss0 * 1.5
+    gpu.ctx.learn_enable(True)
+    gpu.ctx.set_solver(native.FGMRES, 30)
+    b = dev(gpu.rhs().ravel())
+    x = torch.zeros_like(b)
+    it, hist = gpu.ctx.solve(x, b, rtol=1e-10, maxit=100)
+    assert hist[-1] <= 1e-10
+    acc, rej = gpu.ctx.learn_stats()
+    assert acc + rej >= it
+    gpu.close()

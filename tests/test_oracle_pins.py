@@ -405,3 +405,33 @@ def test_fgmres_matches_dense_solution_and_is_monotone():
     x_ref = np.linalg.solve(A, b)
     bound = (np.linalg.norm(b - A @ x) + np.linalg.norm(b - A @ x_ref)) / np.abs(lam).min()
     assert np.linalg.norm(x - x_ref) <= 1.5 * bound + 1e-14 * np.linalg.norm(x_ref)
+
+
+def test_learned_smoother_gradient_matches_finite_differences():
+    """The oracle's back-propagated gradient of the MLP loss equals central
+    finite differences of the loss (tiny network, FP64)."""
+    from oracle import learned
+    rng = np.random.default_rng(0)
+    nin, hid, nout, rows = 7, 5, 3, 11
+    F = rng.standard_normal((rows, nin))
+    T = rng.standard_normal((rows, nout))
+    w = 0.5 * rng.standard_normal(nin * hid + hid + hid * nout + nout)
+    loss, g = learned.loss_and_grad(F, T, w, nin, hid, nout)
+    eps = 1e-6
+    fd = np.zeros_like(w)
+    for i in range(w.size):
+        wp, wm = w.copy(), w.copy()
+        wp[i] += eps
+        wm[i] -= eps
+        fd[i] = (learned.loss_and_grad(F, T, wp, nin, hid, nout)[0] -
+                 learned.loss_and_grad(F, T, wm, nin, hid, nout)[0]) / (2 * eps)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-8)
+
+
+def test_learned_features_neighbour_order():
+    from oracle import learned
+    mesh = ldg.Mesh(2, (4, 3), (0, 0), (1, 1), [P.DIRICHLET, P.DIRICHLET, P.PERIODIC, P.PERIODIC])
+    nb = learned.face_neighbours(mesh)
+    e = 1 + 4 * 0       # element (1, 0)
+    assert list(nb[e]) == [0, 2, 1 + 4 * 2, 1 + 4 * 1]
+    assert nb[0, 0] == -1 and nb[3, 1] == -1
