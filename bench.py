@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides solved together (1..8)")
     ap.add_argument("--inner", type=int, default=3, help="inner refinement steps (several right-hand sides)")
+    ap.add_argument("--learned", type=int, default=0, help="1: train and enable the learned post-smoother")
+    ap.add_argument("--learn-seeds", type=int, default=8)
+    ap.add_argument("--learn-epochs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", default=None, choices=["gs", "resid", "solve"],
                     help="run only a profiling target (for ncu): 8 finest-level colour sweeps, "
@@ -261,6 +264,14 @@ def run_native(args):
     method = native.FGMRES if args.solver == "fgmres" else native.RICHARDSON
     for m_ in (mg, mg64):
         m_.ctx.set_solver(method, args.restart)
+    learned = None
+    if args.learned and prec != native.FP64:
+        t1 = time.perf_counter()
+        mg.ctx.learn_setup(hidden=64, seed=0)
+        mg.ctx.learn_generate(nseeds=args.learn_seeds, cycles=3, seed=0)
+        loss = mg.ctx.learn_train(epochs=args.learn_epochs, batch=4096, lr=1e-3, seed=1)
+        learned = {"hidden": 64, "train_seeds": args.learn_seeds, "cycles_per_seed": 3,
+                   "epochs": args.learn_epochs, "final_loss": loss, "train_s": round(time.perf_counter() - t1, 2)}
     b_host = mg.rhs().ravel()
     b = torch.from_numpy(b_host).cuda()
     x = torch.zeros_like(b)
@@ -304,10 +315,19 @@ def run_native(args):
             el = float(t.item())
         return el, iters, ctx.launch_count() - l0, hist
 
+    if learned is not None:
+        # same problem without the correction, for the comparison
+        el_nl, it_nl, _, _ = timed(mg.ctx, max(1, args.steps // 2), 1)
+        learned["without"] = {"ms_per_solve": el_nl / len(it_nl) * 1e3, "iters": it_nl[0]}
+        mg.ctx.learn_enable(True)
     clocks = Clocks(local)
     clocks.start()
     el, iters, launches, hist = timed(mg.ctx, args.steps, args.warmup)
     clk = clocks.stop()
+    if learned is not None:
+        acc, rej = mg.ctx.learn_stats()
+        learned.update({"with": {"ms_per_solve": el / args.steps * 1e3, "iters": iters[0]},
+                        "accepted_cycles": acc, "rejected_cycles": rej})
     cycles = sum(iters)
     value = prob.n_dofs * max(1, args.nrhs) * cycles * world / el
 
@@ -393,7 +413,7 @@ def run_native(args):
         "nrhs": args.nrhs,
         "plain_fp64": plain, "speedup_vs_plain_fp64": plain["ms_per_solve"] / (el / args.steps * 1e3),
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "fp64_kernels": kernels64,
-        "gs_variants": variants,
+        "gs_variants": variants, "learned_smoother": learned,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
