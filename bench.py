@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--inner", type=int, default=3, help="inner refinement steps (several right-hand sides)")
     ap.add_argument("--learned", type=int, default=0, help="1: train and enable the learned post-smoother")
     ap.add_argument("--learn-seeds", type=int, default=8)
-    ap.add_argument("--learn-epochs", type=int, default=3)
+    ap.add_argument("--learn-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", default=None, choices=["gs", "resid", "solve"],
                     help="run only a profiling target (for ncu): 8 finest-level colour sweeps, "

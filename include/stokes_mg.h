@@ -242,24 +242,24 @@ int stk_solve_multi(stk_ctx* ctx, double* X_dev, const double* B_dev, int nrhs, 
 
 /*
  * Learned element-local post-smoother (not in the paper; cycles in FP32 or
- * BF16 only).  After the post-smoothing sweeps on the finest level, each
- * element's residual and those of its 2d face neighbours, divided by
- * ||r_i||, go through a two-layer perceptron (in = (2d+1) nb, tanh hidden
- * layer of `hidden` units, out = nb) whose output times ||r_i|| corrects x_i.
- * The corrected iterate replaces the block Gauss-Seidel one only if its
- * residual norm is smaller (decided on the device each cycle), so the plain
+ * BF16 only).  After the post-smoothing sweeps on the finest level, with
+ * r = b - A x, each element's residual and those of its 2d face neighbours,
+ * divided by ||r_i||, go through a two-layer perceptron (in = (2d+1) nb, tanh
+ * hidden layer of `hidden` units, out = nb) whose output times ||r_i|| is a
+ * correction delta_i.  x + delta replaces the block Gauss-Seidel iterate only
+ * if ||r - A delta|| < ||r|| (decided on the device each cycle), so the plain
  * smoother stays the fallback and the judge.
  *  stk_learn_setup     allocate and initialise the weights (deterministic in seed);
- *  stk_learn_generate  training pairs from the plain V-cycle: for nseeds smooth
+ *  stk_learn_generate  residual states from the plain V-cycle: for nseeds smooth
  *                      random solutions x* (seeded), b = A x*, `cycles` V-cycles
- *                      from zero; after each, features of r = b - A x and target
- *                      (x* - x) / ||r_i|| for every element;
- *  stk_learn_train     Adam on the mean squared error over random mini-batches;
- *                      *loss_out gets the final mini-batch loss;
+ *                      from zero, storing r = b - A x after each;
+ *  stk_learn_train     Adam on the loss ||r - A delta(r)||^2 / ||r||^2 over the
+ *                      stored states in random order (`epochs` passes; `batch`
+ *                      is unused, one state per step); *loss_out = mean loss
+ *                      of the last pass;
  *  stk_learn_enable    include (1) or drop (0) the correction in every cycle;
  *  stk_learn_stats     cycles whose correction was accepted / rejected;
- *  stk_learn_weights   copy the count = stk-defined number of weights to
- *                      (direction 0) or from (1) a host array (checkpointing).
+ *  stk_learn_weights   copy the weights to (direction 0) or from (1) a host array.
  */
 int stk_learn_setup(stk_ctx* ctx, int hidden, uint64_t seed);
 int stk_learn_generate(stk_ctx* ctx, int nseeds, int cycles, uint64_t seed);
@@ -267,18 +267,18 @@ int stk_learn_train(stk_ctx* ctx, int epochs, int batch, double lr, uint64_t see
 int stk_learn_enable(stk_ctx* ctx, int on);
 int stk_learn_stats(stk_ctx* ctx, int64_t* accepted, int64_t* rejected);
 int stk_learn_weights(stk_ctx* ctx, float* host, int64_t count, int direction);
-/* Sizes: input width (2d+1) nb (feature rows are padded to a multiple of 4
- * floats), hidden width, output nb, number of weights (W1 [in][hidden], b1,
- * W2 [hidden][nb], b2, packed in that order), training rows generated. */
-int stk_learn_sizes(stk_ctx* ctx, int* in, int* hidden, int* out, int64_t* nparam, int64_t* rows);
+/* Sizes: input width (2d+1) nb, hidden width, output nb, number of weights
+ * (W1 [in][hidden], b1, W2 [hidden][nb], b2, packed in that order), number
+ * of stored residual states. */
+int stk_learn_sizes(stk_ctx* ctx, int* in, int* hidden, int* out, int64_t* nparam, int64_t* states);
 /* Features of a finest-level FP32 residual r_dev [element][nb] and the MLP
  * output y_dev [element][nb] (before the ||r_i|| scaling), nrm_dev [element]. */
 int stk_learn_infer(stk_ctx* ctx, const float* r_dev, float* y_dev, float* nrm_dev);
-/* Training rows [row0, row0+rows): features (host, rows x padded width) and
- * targets (rows x nb); and the loss and its gradient (host, packed like the
- * weights) on those rows, without updating the weights. */
-int stk_learn_rows(stk_ctx* ctx, int64_t row0, int rows, float* features, float* targets);
-int stk_learn_grad(stk_ctx* ctx, int64_t row0, int rows, float* grad, double* loss_out);
+/* A stored residual state (host copy), and the training loss and its
+ * gradient (host, packed like the weights) on that state, without updating
+ * the weights. */
+int stk_learn_state(stk_ctx* ctx, int64_t state, float* r);
+int stk_learn_grad(stk_ctx* ctx, int64_t state, float* grad, double* loss_out);
 
 /*
  * Outer iteration of stk_solve: method 0 = iterative refinement

@@ -69,3 +69,25 @@ def loss_and_grad(F, T, w, nin, hid, nout):
     gW1 = X.T @ dZ
     gb1 = dZ.sum(axis=0)
     return loss, np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2])
+
+
+def residual_loss_and_grad(A, r, nbrs, w, nin, hid, nout):
+    """Training objective of the correction: L = ||r - A delta||^2 / ||r||^2
+    with delta_i = ||r_i|| y_i(features of r), and dL/dw by back-propagation
+    (A symmetric, so dL/d delta = -2 A q / ||r||^2 with q = r - A delta)."""
+    ne, nb = r.shape
+    W1, b1, W2, b2 = unpack(w, nin, hid, nout)
+    F, nrm = features(r, nbrs)
+    Y, H = forward(F, w, nin, hid, nout)
+    delta = nrm[:, None] * Y
+    q = r.ravel() - A @ delta.ravel()
+    rr = float(r.ravel() @ r.ravel())
+    loss = float(q @ q) / rr
+    g = (-2.0 * (A @ q) / rr).reshape(ne, nb)
+    dY = nrm[:, None] * g
+    gW2 = H.T @ dY
+    gb2 = dY.sum(axis=0)
+    dZ = (dY @ W2.T) * (1.0 - H * H)
+    gW1 = F[:, :nin].T @ dZ
+    gb1 = dZ.sum(axis=0)
+    return loss, np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2])

@@ -71,6 +71,7 @@ cudaError_t launch_smooth_field(int ne, int nb, int s, int d, const int* n_dev, 
 cudaError_t launch_target(int ne, int nb, int ldt, const float* xs, const float* x, const float* nrm, float* T,
                           cudaStream_t st);
 cudaError_t launch_scale_f(int64_t n, float a, const float* x, float* y, cudaStream_t st);
+cudaError_t launch_scale_by_norm(int64_t n, const double* sums, float* g, cudaStream_t st);
 cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
                                 int ctas, cudaStream_t st);
@@ -1406,6 +1407,9 @@ int stk_learn_setup(stk_ctx* c, int hidden, uint64_t seed) {
     c->lsums = (double*)dalloc(*c, 1024 * 8);
     c->lcount = (int*)dalloc(*c, 16);
     ck(cudaMemset(c->lcount, 0, 16), "memset");
+    c->lF2 = (float*)dalloc(*c, (size_t)ne * hidden * 4);
+    c->l_zero = (float*)dalloc(*c, (size_t)ne * nb * 4);
+    ck(cudaMemset(c->l_zero, 0, (size_t)ne * nb * 4), "memset");
     c->lTX = c->lTT = nullptr;
     c->l_rows = c->l_cap = 0;
     invalidate_graphs(*c);
@@ -1420,37 +1424,34 @@ int stk_learn_generate(stk_ctx* c, int nseeds, int cycles, uint64_t seed) {
     const int nb = c->nb, ne = c->dev[0].ne, prec = c->precision;
     DevLevel& D0 = c->dev[0];
     cudaStream_t st = c->stream;
-    int64_t need = (int64_t)nseeds * cycles * ne;
+    const int64_t nvec = (int64_t)ne * nb;
+    int64_t need = (int64_t)nseeds * cycles;
     if (need > c->l_cap) {
-      c->lTX = (float*)dalloc(*c, (size_t)need * c->l_ldf * 4);
-      c->lTT = (float*)dalloc(*c, (size_t)need * nb * 4);
+      c->lTX = (float*)dalloc(*c, (size_t)need * nvec * 4);
       c->l_cap = need;
     }
     c->l_rows = 0;
     int* ndev = (int*)dalloc(*c, 16);
     ck(cudaMemcpy(ndev, c->host[0].n, 3 * sizeof(int), cudaMemcpyHostToDevice), "copy n");
-    float* xs = (float*)dalloc(*c, (size_t)ne * nb * 4);
-    float* bb = (float*)dalloc(*c, (size_t)ne * nb * 4);
-    float* zero = (float*)dalloc(*c, (size_t)ne * nb * 4);
-    ck(cudaMemsetAsync(zero, 0, (size_t)ne * nb * 4, st), "memset");
+    float* xs = (float*)dalloc(*c, (size_t)nvec * 4);
+    float* bb = (float*)dalloc(*c, (size_t)nvec * 4);
+    float* zero = (float*)dalloc(*c, (size_t)nvec * 4);
+    ck(cudaMemsetAsync(zero, 0, (size_t)nvec * 4, st), "memset");
     int on = c->learn_on;
-    c->learn_on = 0;   // data come from the plain V-cycle
+    c->learn_on = 0;   // states come from the plain V-cycle
     for (int sd = 0; sd < nseeds; ++sd) {
       ck(launch_smooth_field(ne, nb, c->s, c->d, ndev, seed + 7919ULL * sd, xs, st), "field");
       // b = A x*: the residual of x* against a zero right-hand side is -A x*.
       ck(run_element(*c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], zero, xs, D0.vr[1], st), "matvec");
-      ck(launch_scale_f((int64_t)ne * nb, -1.f, (const float*)D0.vr[1], bb, st), "negate");
+      ck(launch_scale_f(nvec, -1.f, (const float*)D0.vr[1], bb, st), "negate");
       float* x = (float*)D0.vx[1];
-      ck(cudaMemsetAsync(x, 0, (size_t)ne * nb * 4, st), "memset");
+      ck(cudaMemsetAsync(x, 0, (size_t)nvec * 4, st), "memset");
       for (int k = 0; k < cycles; ++k) {
         enqueue_cycle(*c, prec, 0, x, bb, st);
-        ck(run_element(*c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bb, x, D0.vr[1], st), "residual");
-        float* F = c->lTX + (size_t)c->l_rows * c->l_ldf;
-        float* T = c->lTT + (size_t)c->l_rows * nb;
-        ck(launch_features(ne, nb, 2 * c->d, c->pat.NO, c->l_ldf, c->l_nbr, (const float*)D0.vr[1], F, c->lnrm, st),
-           "features");
-        ck(launch_target(ne, nb, nb, xs, x, c->lnrm, T, st), "target");
-        c->l_rows += ne;
+        // the residual the correction would see after this cycle's post-smoothing
+        ck(run_element(*c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bb, x, c->lTX + (size_t)c->l_rows * nvec, st),
+           "residual");
+        c->l_rows += 1;
       }
     }
     ck(cudaStreamSynchronize(st), "sync");
@@ -1459,59 +1460,72 @@ int stk_learn_generate(stk_ctx* c, int nseeds, int cycles, uint64_t seed) {
   });
 }
 
+// Loss ||r - A delta||^2 / ||r||^2 of one residual state and its gradient
+// (packed like the weights) in c.lgrad; the loss goes to *loss_dev (device).
+// delta_i = ||r_i|| MLP(features_i); A is symmetric, so d loss / d delta =
+// -2 A q / ||r||^2 with q = r - A delta, and A q is minus the residual of q
+// against a zero right-hand side.
+void enqueue_residual_loss_grad(Ctx& c, const float* r, double* sums, cudaStream_t st) {
+  DevLevel& D0 = c.dev[0];
+  const int ne = D0.ne, nb = c.nb, H = c.l_hid, IN = c.l_in, ldf = c.l_ldf, prec = c.precision;
+  const int64_t nvec = (int64_t)ne * nb;
+  float* gW1 = c.lgrad;
+  float* gb1 = gW1 + (int64_t)IN * H;
+  float* gW2 = gb1 + H;
+  float* gb2 = gW2 + (int64_t)H * nb;
+  ck(launch_features(ne, nb, 2 * c.d, c.pat.NO, ldf, c.l_nbr, r, c.lF, c.lnrm, st), "features");
+  ck(launch_sgemm(ne, H, IN, 0, 0, c.lF, ldf, c.lW1, H, c.lH, H, c.lb1, 1, 1.f, 0.f, st), "fwd1");
+  ck(launch_sgemm(ne, nb, H, 0, 0, c.lH, H, c.lW2, nb, c.lY, nb, c.lb2, 0, 1.f, 0.f, st), "fwd2");
+  ck(cudaMemsetAsync(c.lrt, 0, (size_t)nvec * 4, st), "memset");
+  ck(launch_apply_correction(ne, nb, nb, c.lrt, c.lnrm, c.lY, c.lxt, st), "delta");       // lxt = delta
+  ck(run_element(c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], r, c.lxt, c.lrt, st), "q");  // lrt = q
+  ck(launch_sumsq_f(nvec, r, sums + 16, sums, st), "||r||");
+  ck(launch_sumsq_f(nvec, c.lrt, sums + 16, sums + 1, st), "||q||");
+  // g = 2 (-A q) / ||r||^2 into lxt (reusing delta's buffer), then dY = ||r_i|| g_i.
+  ck(run_element(c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], c.l_zero, c.lrt, c.lxt, st), "-A q");
+  ck(launch_scale_by_norm(nvec, sums, c.lxt, st), "scale");
+  ck(cudaMemsetAsync(c.lrt, 0, (size_t)nvec * 4, st), "memset");
+  ck(launch_apply_correction(ne, nb, nb, c.lrt, c.lnrm, c.lxt, c.lY, st), "dY");          // lY = dY
+  ck(launch_sgemm(H, nb, ne, 1, 0, c.lH, H, c.lY, nb, gW2, nb, nullptr, 0, 1.f, 0.f, st), "gW2");
+  ck(launch_colsum(ne, nb, c.lY, nb, gb2, 1.f, st), "gb2");
+  ck(launch_sgemm(ne, H, nb, 0, 1, c.lY, nb, c.lW2, nb, c.lF2, H, nullptr, 0, 1.f, 0.f, st), "dH");
+  ck(launch_tanh_back((int64_t)ne * H, c.lH, c.lF2, st), "tanh'");
+  ck(launch_sgemm(IN, H, ne, 1, 0, c.lF, ldf, c.lF2, H, gW1, H, nullptr, 0, 1.f, 0.f, st), "gW1");
+  ck(launch_colsum(ne, H, c.lF2, H, gb1, 1.f, st), "gb1");
+  c.launches += 18;
+}
+
 int stk_learn_train(stk_ctx* c, int epochs, int batch, double lr, uint64_t seed, double* loss_out) {
   return guard(c, [&]() -> int {
     if (!c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
     if (c->l_rows <= 0) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_generate first");
-    if (epochs < 1 || batch < 32 || !(lr > 0)) return fail(c, STK_ERR_INVALID_ARG, "bad training options");
-    const int nb = c->nb, H = c->l_hid, IN = c->l_in, ldf = c->l_ldf;
-    batch = (int)std::min<int64_t>(batch, c->l_rows);
+    if (epochs < 1 || !(lr > 0)) return fail(c, STK_ERR_INVALID_ARG, "bad training options");
+    (void)batch;
     cudaStream_t st = c->stream;
-    float* Hb = (float*)dalloc(*c, (size_t)batch * H * 4);
-    float* Yb = (float*)dalloc(*c, (size_t)batch * nb * 4);
-    float* dY = (float*)dalloc(*c, (size_t)batch * nb * 4);
-    float* dH = (float*)dalloc(*c, (size_t)batch * H * 4);
-    float* part = (float*)dalloc(*c, 256 * 4);
-    float* gW1 = c->lgrad;
-    float* gb1 = gW1 + (int64_t)IN * H;
-    float* gW2 = gb1 + H;
-    float* gb2 = gW2 + (int64_t)H * nb;
-    const int64_t nbatches = std::max<int64_t>(1, c->l_rows / batch);
+    const int64_t nvec = (int64_t)c->dev[0].ne * c->nb;
     uint64_t z = seed;
-    double loss = 0.0;
-    std::vector<float> ph(256);
+    double sum_loss = 0.0;
+    int nloss = 0;
     for (int ep = 0; ep < epochs; ++ep) {
-      double ep_loss = 0.0;
-      for (int64_t bi = 0; bi < nbatches; ++bi) {
+      sum_loss = 0.0;
+      nloss = 0;
+      for (int64_t k = 0; k < c->l_rows; ++k) {
         z = z * 6364136223846793005ULL + 1442695040888963407ULL;
-        const int64_t off = (int64_t)((z >> 33) % (uint64_t)(c->l_rows - batch + 1));
-        const float* X = c->lTX + (size_t)off * ldf;
-        const float* T = c->lTT + (size_t)off * nb;
-        ck(launch_sgemm(batch, H, IN, 0, 0, X, ldf, c->lW1, H, Hb, H, c->lb1, 1, 1.f, 0.f, st), "fwd1");
-        ck(launch_sgemm(batch, nb, H, 0, 0, Hb, H, c->lW2, nb, Yb, nb, c->lb2, 0, 1.f, 0.f, st), "fwd2");
-        ck(launch_mse_grad((int64_t)batch * nb, 1.f / batch, Yb, T, dY, part, st), "loss");
-        ck(launch_sgemm(H, nb, batch, 1, 0, Hb, H, dY, nb, gW2, nb, nullptr, 0, 1.f, 0.f, st), "gW2");
-        ck(launch_colsum(batch, nb, dY, nb, gb2, 1.f, st), "gb2");
-        ck(launch_sgemm(batch, H, nb, 0, 1, dY, nb, c->lW2, nb, dH, H, nullptr, 0, 1.f, 0.f, st), "dH");
-        ck(launch_tanh_back((int64_t)batch * H, Hb, dH, st), "tanh'");
-        ck(launch_sgemm(IN, H, batch, 1, 0, X, ldf, dH, H, gW1, H, nullptr, 0, 1.f, 0.f, st), "gW1");
-        ck(launch_colsum(batch, H, dH, H, gb1, 1.f, st), "gb1");
+        const int64_t state = (int64_t)((z >> 33) % (uint64_t)c->l_rows);
+        enqueue_residual_loss_grad(*c, c->lTX + (size_t)state * nvec, c->lsums, st);
         c->l_adam_t++;
         const float b1 = 0.9f, b2 = 0.999f;
         const float c1 = 1.f - std::pow(b1, (float)c->l_adam_t), c2 = 1.f - std::pow(b2, (float)c->l_adam_t);
         ck(launch_adam(c->l_nparam, (float)lr, b1, b2, c1, c2, 1e-8f, c->lW1, c->lgrad, c->lm, c->lv, st), "adam");
-        c->launches += 10;
-        if (bi == nbatches - 1 || (bi % 64) == 63) {
-          ck(cudaMemcpyAsync(ph.data(), part, 256 * 4, cudaMemcpyDeviceToHost, st), "copy loss");
-          ck(cudaStreamSynchronize(st), "sync");
-          double l = 0.0;
-          for (float v : ph) l += v;
-          ep_loss = l / batch;
-        }
+        c->launches++;
+        double h[2];
+        ck(cudaMemcpyAsync(h, c->lsums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaStreamSynchronize(st), "sync");
+        sum_loss += h[1] / h[0];
+        ++nloss;
       }
-      loss = ep_loss;
     }
-    if (loss_out) *loss_out = loss;
+    if (loss_out) *loss_out = nloss ? sum_loss / nloss : 0.0;
     return STK_OK;
   });
 }
@@ -1533,50 +1547,26 @@ int stk_learn_infer(stk_ctx* c, const float* r, float* y, float* nrm) {
   });
 }
 
-int stk_learn_rows(stk_ctx* c, int64_t row0, int rows, float* F, float* T) {
+int stk_learn_state(stk_ctx* c, int64_t state, float* r) {
   return guard(c, [&]() -> int {
-    if (!c->lTX || row0 < 0 || rows < 1 || row0 + rows > c->l_rows || !F || !T)
-      return fail(c, STK_ERR_INVALID_ARG, "bad training-row range");
-    ck(cudaMemcpy(F, c->lTX + (size_t)row0 * c->l_ldf, (size_t)rows * c->l_ldf * 4, cudaMemcpyDeviceToHost), "copy");
-    ck(cudaMemcpy(T, c->lTT + (size_t)row0 * c->nb, (size_t)rows * c->nb * 4, cudaMemcpyDeviceToHost), "copy");
+    if (!c->lTX || state < 0 || state >= c->l_rows || !r) return fail(c, STK_ERR_INVALID_ARG, "bad state index");
+    const int64_t nvec = (int64_t)c->dev[0].ne * c->nb;
+    ck(cudaMemcpy(r, c->lTX + (size_t)state * nvec, (size_t)nvec * 4, cudaMemcpyDeviceToHost), "copy");
     return STK_OK;
   });
 }
 
-int stk_learn_grad(stk_ctx* c, int64_t row0, int rows, float* grad, double* loss_out) {
+int stk_learn_grad(stk_ctx* c, int64_t state, float* grad, double* loss_out) {
   return guard(c, [&]() -> int {
-    if (!c->lTX || row0 < 0 || rows < 1 || row0 + rows > c->l_rows || !grad)
-      return fail(c, STK_ERR_INVALID_ARG, "bad training-row range");
-    const int nb = c->nb, H = c->l_hid, IN = c->l_in, ldf = c->l_ldf;
+    if (!c->lTX || state < 0 || state >= c->l_rows || !grad) return fail(c, STK_ERR_INVALID_ARG, "bad state index");
     cudaStream_t st = c->stream;
-    float* Hb = (float*)dalloc(*c, (size_t)rows * H * 4);
-    float* Yb = (float*)dalloc(*c, (size_t)rows * nb * 4);
-    float* dY = (float*)dalloc(*c, (size_t)rows * nb * 4);
-    float* dH = (float*)dalloc(*c, (size_t)rows * H * 4);
-    float* part = (float*)dalloc(*c, 256 * 4);
-    float* gW1 = c->lgrad;
-    float* gb1 = gW1 + (int64_t)IN * H;
-    float* gW2 = gb1 + H;
-    float* gb2 = gW2 + (int64_t)H * nb;
-    const float* X = c->lTX + (size_t)row0 * ldf;
-    const float* T = c->lTT + (size_t)row0 * nb;
-    ck(launch_sgemm(rows, H, IN, 0, 0, X, ldf, c->lW1, H, Hb, H, c->lb1, 1, 1.f, 0.f, st), "fwd1");
-    ck(launch_sgemm(rows, nb, H, 0, 0, Hb, H, c->lW2, nb, Yb, nb, c->lb2, 0, 1.f, 0.f, st), "fwd2");
-    ck(launch_mse_grad((int64_t)rows * nb, 1.f / rows, Yb, T, dY, part, st), "loss");
-    ck(launch_sgemm(H, nb, rows, 1, 0, Hb, H, dY, nb, gW2, nb, nullptr, 0, 1.f, 0.f, st), "gW2");
-    ck(launch_colsum(rows, nb, dY, nb, gb2, 1.f, st), "gb2");
-    ck(launch_sgemm(rows, H, nb, 0, 1, dY, nb, c->lW2, nb, dH, H, nullptr, 0, 1.f, 0.f, st), "dH");
-    ck(launch_tanh_back((int64_t)rows * H, Hb, dH, st), "tanh'");
-    ck(launch_sgemm(IN, H, rows, 1, 0, X, ldf, dH, H, gW1, H, nullptr, 0, 1.f, 0.f, st), "gW1");
-    ck(launch_colsum(rows, H, dH, H, gb1, 1.f, st), "gb1");
-    c->launches += 9;
-    std::vector<float> ph(256);
-    ck(cudaMemcpyAsync(ph.data(), part, 256 * 4, cudaMemcpyDeviceToHost, st), "copy");
+    const int64_t nvec = (int64_t)c->dev[0].ne * c->nb;
+    enqueue_residual_loss_grad(*c, c->lTX + (size_t)state * nvec, c->lsums, st);
+    double h[2];
+    ck(cudaMemcpyAsync(h, c->lsums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
     ck(cudaMemcpyAsync(grad, c->lgrad, c->l_nparam * 4, cudaMemcpyDeviceToHost, st), "copy");
     ck(cudaStreamSynchronize(st), "sync");
-    double l = 0.0;
-    for (float v : ph) l += v;
-    if (loss_out) *loss_out = l / rows;
+    if (loss_out) *loss_out = h[1] / h[0];
     return STK_OK;
   });
 }

@@ -249,7 +249,18 @@ __global__ void scale_f_kernel(int64_t n, float a, const float* __restrict__ x, 
   if (i < n) y[i] = a * x[i];
 }
 
+// g <- 2 g / ||r||^2 with ||r||^2 = sums[0]
+__global__ void scale_by_norm_kernel(int64_t n, const double* __restrict__ sums, float* __restrict__ g) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) g[i] = (float)(2.0 * (double)g[i] / (sums[0] + 1e-300));
+}
+
 // ---------------------------------------------------------------------------
+cudaError_t launch_scale_by_norm(int64_t n, const double* sums, float* g, cudaStream_t st) {
+  scale_by_norm_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, sums, g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale_f(int64_t n, float a, const float* x, float* y, cudaStream_t st) {
   scale_f_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, x, y);
   return cudaGetLastError();

@@ -144,7 +144,8 @@ struct Ctx {
   float *lF = nullptr, *lH = nullptr, *lY = nullptr, *lnrm = nullptr, *lxt = nullptr, *lrt = nullptr;
   double* lsums = nullptr;      // [0] ||r||^2, [1] ||r_t||^2, then partials
   int* lcount = nullptr;        // accepted, rejected
-  float *lTX = nullptr, *lTT = nullptr;   // training features / targets
+  float *lF2 = nullptr, *l_zero = nullptr;   // hidden-layer gradient, zero vector
+  float *lTX = nullptr, *lTT = nullptr;   // training residual states [state][element][nb]
   int64_t l_rows = 0, l_cap = 0;
   int l_adam_t = 0;
   cudaGraphExec_t mgraph = nullptr;

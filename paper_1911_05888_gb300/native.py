@@ -63,8 +63,8 @@ SIGNATURES = {
     "stk_learn_weights": [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.c_int],
     "stk_learn_sizes": [_vp, _c_int_p, _c_int_p, _c_int_p, _c_i64_p, _c_i64_p],
     "stk_learn_infer": [_vp, _vp, _vp, _vp],
-    "stk_learn_rows": [_vp, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
-    "stk_learn_grad": [_vp, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_float), _c_dbl_p],
+    "stk_learn_state": [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float)],
+    "stk_learn_grad": [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float), _c_dbl_p],
     "stk_solve_multi": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_int_p,
                         _c_dbl_p, _vp],
     "stk_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
@@ -289,18 +289,16 @@ class Context:
     def learn_infer(self, r, y, nrm):
         self._check(self.lib.stk_learn_infer(self.h, _ptr(r), _ptr(y), _ptr(nrm)), "stk_learn_infer")
 
-    def learn_rows(self, row0, rows, width, nb):
-        F = np.zeros((rows, width), dtype=np.float32)
-        T = np.zeros((rows, nb), dtype=np.float32)
-        fp = ctypes.POINTER(ctypes.c_float)
-        self._check(self.lib.stk_learn_rows(self.h, row0, rows, F.ctypes.data_as(fp), T.ctypes.data_as(fp)),
-                    "stk_learn_rows")
-        return F, T
+    def learn_state(self, state, nvec):
+        r = np.zeros(nvec, dtype=np.float32)
+        self._check(self.lib.stk_learn_state(self.h, state, r.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+                    "stk_learn_state")
+        return r
 
-    def learn_grad(self, row0, rows, nparam):
+    def learn_grad(self, state, nparam):
         g = np.zeros(nparam, dtype=np.float32)
         loss = ctypes.c_double()
-        self._check(self.lib.stk_learn_grad(self.h, row0, rows, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+        self._check(self.lib.stk_learn_grad(self.h, state, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                             ctypes.byref(loss)), "stk_learn_grad")
         return loss.value, g
 

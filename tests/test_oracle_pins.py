@@ -435,3 +435,26 @@ def test_learned_features_neighbour_order():
     e = 1 + 4 * 0       # element (1, 0)
     assert list(nb[e]) == [0, 2, 1 + 4 * 2, 1 + 4 * 1]
     assert nb[0, 0] == -1 and nb[3, 1] == -1
+
+
+def test_learned_residual_objective_gradient_matches_finite_differences():
+    """Gradient of ||r - A delta(r)||^2 / ||r||^2 (the correction's training
+    objective) against central finite differences on a 4x4, p=1 operator."""
+    from oracle import learned
+    prob = P.generic(2, 4, 1, 1, [P.DIRICHLET] * 3 + [P.STRESS])
+    lev = hierarchy.build_hierarchy(prob, max_levels=1)[0][0]
+    nbrs = learned.face_neighbours(lev.mesh)
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal((lev.ne, lev.nb))
+    nin, hid, nout = 5 * lev.nb, 6, lev.nb
+    w = 0.1 * rng.standard_normal(nin * hid + hid + hid * nout + nout)
+    loss, g = learned.residual_loss_and_grad(lev.A, r, nbrs, w, nin, hid, nout)
+    eps = 1e-6
+    idx = rng.choice(w.size, 40, replace=False)
+    for i in idx:
+        wp, wm = w.copy(), w.copy()
+        wp[i] += eps
+        wm[i] -= eps
+        fd = (learned.residual_loss_and_grad(lev.A, r, nbrs, wp, nin, hid, nout)[0] -
+              learned.residual_loss_and_grad(lev.A, r, nbrs, wm, nin, hid, nout)[0]) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-7 * np.abs(g).max()
