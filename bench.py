@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="stress2d", choices=["stress2d", "unsteady3d"],
+                    help="stress2d: 2D viscous-stress 256x256 p=3 (default); unsteady3d: 3D unsteady "
+                         "periodic 48^3 p=2, 16 warm-started time steps")
+    ap.add_argument("--re", type=float, default=100.0, help="effective Reynolds number (unsteady3d)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
@@ -469,12 +473,75 @@ def run_reference(args):
     }))
 
 
+def run_unsteady(args):
+    """3D unsteady standard-form Stokes on the periodic cube (eq. timedep1,
+    Algorithm 3 coarsening), rho = 1, mu = 1/Re, delta = 0.1 h, time-periodic
+    manufactured flow; 16 consecutive steps, each solve warm-started from the
+    previous step's solution."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1911_05888_gb300 import native, problems as P
+    from paper_1911_05888_gb300.solver import StokesMG
+    n = args.n if args.n != 256 else 48
+    p = 2 if args.p == 3 else args.p
+    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16}[args.precision]
+    prob = P.unsteady_periodic_3d(n=n, p=p, re=args.re, t=0.0, nu=(args.nu, args.nu))
+    t0 = time.perf_counter()
+    mg = StokesMG(prob, precision=prec, nu=(args.nu, args.nu))
+    setup_s = time.perf_counter() - t0
+    mg.ctx.set_solver(native.FGMRES if args.solver == "fgmres" else native.RICHARDSON, args.restart)
+    b0 = torch.from_numpy(mg.rhs().ravel()).cuda()   # data scale as cos(omega t): b(t) = cos(omega t) b(0)
+    delta = prob.delta
+    omega = 2 * math.pi / (16 * delta)
+    steps = 16
+    b = torch.empty_like(b0)
+    x = torch.zeros_like(b0)
+    stream = torch.cuda.current_stream()
+
+    def run_steps():
+        x.zero_()
+        its = []
+        for k in range(1, steps + 1):
+            b.copy_(b0 * math.cos(omega * k * delta))
+            it, hist = mg.ctx.solve(x, b, rtol=1e-10, maxit=100)
+            its.append(it)
+        return its, hist
+
+    for _ in range(max(1, args.warmup)):
+        run_steps()
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    l0 = mg.ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its, hist = run_steps()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    el = e0.elapsed_time(e1) / 1e3
+    cycles = sum(its)
+    print(json.dumps({
+        "metric": METRIC, "value": prob.n_dofs * cycles / el, "unit": "DOF-cycles/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32-storage in f64", "bf16": "bf16-storage in f64"}[
+            args.precision], "data": "synthetic (manufactured time-periodic flow)",
+        "config": {"workload": "3d-unsteady-standard-periodic", "n": [n] * 3, "p": p, "dofs": prob.n_dofs,
+                   "re": args.re, "delta": delta, "time_steps": steps, "warm_start": True,
+                   "nu": [args.nu, args.nu], "outer": args.solver},
+        "iters_per_step": its, "final_rel_residual": float(hist[-1]), "setup_s": round(setup_s, 1),
+        "gpu_launches": int(mg.ctx.launch_count() - l0), "clocks": clk}))
+
+
 def main():
     args = parse()
     if args.cpu_child:
         cpu_child(args.cpu_child)
         return
-    if args.profile:
+    if args.workload == "unsteady3d":
+        run_unsteady(args)
+    elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)
