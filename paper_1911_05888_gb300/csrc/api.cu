@@ -616,6 +616,12 @@ void ensure_krylov(Ctx& c) {
   c.kzero = (double*)dalloc(c, (size_t)n0 * 8);
   ck(cudaMemset(c.kzero, 0, (size_t)n0 * 8), "memset");
   c.kpart = (double*)dalloc(c, (size_t)1024 * 136 * 8);
+  if (c.precision != STK_FP64) {
+    c.kz32 = (float*)dalloc(c, (size_t)n0 * 4);
+    c.kw32 = (float*)dalloc(c, (size_t)n0 * 4);
+    c.kzero32 = (float*)dalloc(c, (size_t)n0 * 4);
+    ck(cudaMemset(c.kzero32, 0, (size_t)n0 * 4), "memset");
+  }
   c.kdots = (double*)dalloc(c, 272 * 8);
   if (!c.khost) ck(cudaMallocHost(&c.khost, 272 * sizeof(double)), "cudaMallocHost");
   c.kcap = m;
@@ -722,8 +728,18 @@ int fgmres(Ctx& c, double* x, const double* b, double rtol, int maxit, double* h
       double* vj = c.kV + (size_t)j * n0;
       double* zj = c.kZ + (size_t)j * n0;
       precondition(c, vj, zj, st);
-      // w = A z_j, computed as -(0 - A z_j) by the residual kernel.
-      enqueue_residual64(c, zj, c.kzero, c.kw, st);
+      // w = A z_j, computed as -(0 - A z_j) by the residual kernel; in the
+      // refined variant with the blocks of the cycle's precision.
+      if (c.solver == 2 && c.precision != STK_FP64) {
+        ck(launch_convert(0, 1, n0, c.kz32, zj, st), "convert");
+        ck(run_element(c, 0, c.precision, MODE_RESID, 0, c.dev[0].ne, c.dev[0].dia[c.precision], c.kzero32, c.kz32,
+                       c.kw32, st),
+           "matvec32");
+        ck(launch_convert(1, 0, n0, c.kw, c.kw32, st), "convert");
+        c.launches += 3;
+      } else {
+        enqueue_residual64(c, zj, c.kzero, c.kw, st);
+      }
       // Classical Gram-Schmidt, twice.
       host_dots(c, j + 1, c.kV, c.kw, h.data(), st);
       for (int i = 0; i <= j; ++i) h[i] = -h[i];
@@ -765,6 +781,9 @@ int fgmres(Ctx& c, double* x, const double* b, double rtol, int maxit, double* h
       rel = std::fabs(g[j + 1]) / bnorm;
       if (hist) hist[it] = rel;
       if (rel <= rtol || !std::isfinite(rel) || rel > 1e6 * rel0) break;
+      // Refined variant: the low-precision Krylov relation is trusted for a
+      // 1e-5 reduction, then x is updated and the FP64 residual restarts it.
+      if (c.solver == 2 && std::fabs(g[j + 1]) <= 1e-5 * beta) break;
     }
     // x += Z y with H[:k,:k] y = g[:k]
     for (int i = k - 1; i >= 0; --i) {
@@ -1170,7 +1189,7 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
     double rel = std::sqrt(c->norm_host[0]) / bnorm, rel0 = rel;
     if (hist) hist[0] = rel;
     int it = 0;
-    if (c->solver == 1) {
+    if (c->solver >= 1) {
       try {
         it = fgmres(*c, x, b, rtol, maxit, hist, bnorm, rel, st);
       } catch (const Timeout&) {
@@ -1247,8 +1266,8 @@ int stk_set_tuning(stk_ctx* c, int variant, int precision, int ctas_per_sm, int 
 
 int stk_set_solver(stk_ctx* c, int method, int restart) {
   return guard(c, [&]() -> int {
-    if (method < 0 || method > 1 || restart < 1 || restart > 100)
-      return fail(c, STK_ERR_INVALID_ARG, "bad solver options (method 0/1, restart 1..100)");
+    if (method < 0 || method > 2 || restart < 1 || restart > 100)
+      return fail(c, STK_ERR_INVALID_ARG, "bad solver options (method 0/1/2, restart 1..100)");
     c->solver = method;
     if (restart != c->restart) {
       c->restart = restart;

@@ -107,7 +107,8 @@ struct Ctx {
   int graph_prec = -1;
   int64_t graph_kernels = 0;
   cudaStream_t stream = nullptr;
-  // outer iteration: 0 Richardson, 1 flexible GMRES(restart)
+  // outer iteration: 0 Richardson, 1 flexible GMRES(restart), 2 flexible GMRES
+  // with the Krylov matvec in the cycle precision inside FP64 refinement
   int solver = 0, restart = 30;
   double* kV = nullptr;       // (restart+1) Krylov basis vectors, FP64
   double* kZ = nullptr;       // restart preconditioned vectors, FP64
@@ -116,6 +117,7 @@ struct Ctx {
   double* kpart = nullptr;    // multi-dot partials
   double* kdots = nullptr;    // multi-dot results / coefficients (device)
   double* khost = nullptr;    // pinned host staging (dots, coefficients)
+  float *kz32 = nullptr, *kw32 = nullptr, *kzero32 = nullptr;   // FP32 matvec of the refined variant
   int kcap = 0;               // restart the buffers were sized for
   // V-cycle alone on the level-0 work vectors, as a CUDA graph
   cudaGraphExec_t cycle_graph = nullptr;

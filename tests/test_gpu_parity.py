@@ -339,3 +339,23 @@ def test_learned_smoother_solve_converges_and_is_judged():
     acc, rej = gpu.ctx.learn_stats()
     assert acc + rej >= it
     gpu.close()
+
+
+@pytest.mark.parametrize("precision", [native.FP32, native.BF16])
+@pytest.mark.parametrize("name", ["stress16p3", "3d-unsteady-p2"])
+def test_fgmres_refined_variant(name, precision):
+    """Krylov matvec in the cycle's precision with FP64 restarts still reaches
+    1e-10 on the FP64 residual and the FP64 solution."""
+    prob, gpu64, _ = get(name)
+    _, gpu, _ = get(name, precision)
+    b = dev(gpu64.rhs().ravel())
+    x64 = torch.zeros_like(b)
+    gpu64.ctx.solve(x64, b, rtol=1e-11, maxit=200)
+    x = torch.zeros_like(b)
+    gpu.ctx.set_solver(native.FGMRES_IR, 30)
+    try:
+        it, hist = gpu.ctx.solve(x, b, rtol=1e-10, maxit=200)
+    finally:
+        gpu.ctx.set_solver(native.RICHARDSON, 30)
+    assert hist[-1] <= 1e-10, hist
+    assert rel(x.cpu().numpy(), x64.cpu().numpy()) <= 1e-8
