@@ -143,11 +143,26 @@ def stokes_operator(ops, gamma, delta=None):
     return sp.bmat(blocks, format="csr")
 
 
-class Level:
-    """One level of the hierarchy: the element-major Stokes operator and the
-    data the smoother and transfers need."""
+def sqrt_mu_scaling(ops, d):
+    """Section 5.6 diagonal scaling: per element mu_E^{-1/2} on the velocity
+    unknowns and mu_E^{1/2} on the pressure unknowns, with mu_E the element
+    mean of mu (M_mu(E)[0,0] / M(E)[0,0], mode 0 being the constant).  Returned
+    as the element-major diagonal."""
+    ne, s = ops["mesh"].ne, ops["s"]
+    Mmu = diag_blocks(ops["Mmu"], ne, s)[:, 0, 0]
+    M = diag_blocks(ops["M"], ne, s)[:, 0, 0]
+    mu_e = Mmu / M
+    dv = np.repeat(mu_e ** -0.5, d * s).reshape(ne, d * s)
+    dp = np.repeat(mu_e ** 0.5, s).reshape(ne, s)
+    return np.concatenate([dv, dp], axis=1).ravel()
 
-    def __init__(self, ops, gamma, delta, d):
+
+class Level:
+    """One level of the hierarchy: the element-major Stokes operator (scaled
+    by D A D when the sqrt(mu) scaling is on, every level with its own mu_E)
+    and the data the smoother and transfers need."""
+
+    def __init__(self, ops, gamma, delta, d, scale=False):
         self.ops = ops
         self.mesh = ops["mesh"]
         self.s = ops["s"]
@@ -157,6 +172,11 @@ class Level:
         Afield = stokes_operator(ops, gamma, delta)
         self.P = field_to_element_perm(self.ne, self.s, self.nvar)
         self.A = (self.P @ Afield @ self.P.T).tocsr()
+        self.D = None
+        if scale:
+            self.D = sqrt_mu_scaling(ops, d)
+            Dm = sp.diags(self.D)
+            self.A = (Dm @ self.A @ Dm).tocsr()
         self.A.sum_duplicates()
         self.A.sort_indices()
 
@@ -164,8 +184,9 @@ class Level:
 def build_hierarchy(prob, max_levels=None):
     """Fine operators (Appendix A), then recursive coarsening (Appendix B)."""
     unsteady = prob.delta is not None
+    scale = bool(prob.scale_mu)
     ops = fine_operators(prob)
-    levels = [Level(ops, prob.gamma, prob.delta, prob.d)]
+    levels = [Level(ops, prob.gamma, prob.delta, prob.d, scale)]
     injections = []
     while True:
         mesh = ops["mesh"]
@@ -173,10 +194,24 @@ def build_hierarchy(prob, max_levels=None):
             break
         if max_levels is not None and len(levels) >= max_levels:
             break
-        mesh_c = Mesh(mesh.d, [n // 2 for n in mesh.n], mesh.lo, mesh.hi, mesh.bc)
+        nc = [n // 2 for n in mesh.n]
+        chi_c = None
+        if mesh.chi is not None:
+            # Same-phase agglomeration (Section 3): a coarse cell exists only if
+            # all of its children belong to one phase; otherwise stop here.
+            parent = ((mesh.idx // 2) * np.asarray([int(np.prod(nc[:k])) for k in range(mesh.d)])).sum(axis=1)
+            nec = int(np.prod(nc))
+            lo_ph = np.full(nec, 10 ** 9)
+            hi_ph = np.full(nec, -1)
+            np.minimum.at(lo_ph, parent, mesh.chi)
+            np.maximum.at(hi_ph, parent, mesh.chi)
+            if np.any(lo_ph != hi_ph):
+                break
+            chi_c = lo_ph
+        mesh_c = Mesh(mesh.d, nc, mesh.lo, mesh.hi, mesh.bc, chi=chi_c)
         I = injection(mesh, mesh_c, prob.p)
         ops = coarsen(ops, I, mesh_c, unsteady)
-        lev = Level(ops, prob.gamma, prob.delta, prob.d)
+        lev = Level(ops, prob.gamma, prob.delta, prob.d, scale)
         # Full (all variables) injection in element-major order.
         Ifull_field = sp.block_diag([I] * (prob.d + 1), format="csr")
         injections.append((levels[-1].P @ Ifull_field @ lev.P.T).tocsr())

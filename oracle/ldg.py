@@ -42,9 +42,10 @@ from paper_1911_05888_gb300.problems import PERIODIC, DIRICHLET, STRESS
 
 
 class Mesh:
-    """Cartesian n_0 x ... x n_{d-1} grid on [lo, hi]."""
+    """Cartesian n_0 x ... x n_{d-1} grid on [lo, hi]; chi (optional) is the
+    phase of every element (Appendix A: chi(E))."""
 
-    def __init__(self, d, n, lo, hi, bc):
+    def __init__(self, d, n, lo, hi, bc, chi=None):
         self.d = d
         self.n = tuple(int(v) for v in n)
         self.lo = np.asarray(lo, dtype=np.float64)
@@ -57,13 +58,54 @@ class Mesh:
         self.idx = np.stack([(e // self.stride[k]) % self.n[k] for k in range(d)], axis=1)
         self.centre = self.lo + (self.idx + 0.5) * self.h
         self.vol = float(np.prod(self.h))
+        self.chi = None if chi is None else np.asarray(chi, dtype=np.int64)
 
     def periodic(self, k):
         return self.bc[2 * k] == PERIODIC
 
     def colour(self):
-        """Colour sum_k (i_k mod 2) 2^k of every element (Section 3: multi-coloured GS)."""
-        return (self.idx % 2 * (2 ** np.arange(self.d))).sum(axis=1)
+        """Colour of every element for the multi-coloured GS of Section 3.
+        Single phase: the parity colouring sum_k (i_k mod 2) 2^k.  With
+        phases the interphase lifts couple elements two apart along an axis,
+        so a greedy colouring is used instead: elements in order, each takes
+        the smallest colour not taken by an already coloured element at any
+        offset of the coupling stencil (+-e_k, +-2e_k, +-e_i +- e_j)."""
+        if self.chi is None:
+            return (self.idx % 2 * (2 ** np.arange(self.d))).sum(axis=1)
+        offs = []
+        for k in range(self.d):
+            for m in (1, 2):
+                for sg in (-1, 1):
+                    o = [0] * self.d
+                    o[k] = sg * m
+                    offs.append(o)
+        for i in range(self.d):
+            for j in range(i + 1, self.d):
+                for si in (-1, 1):
+                    for sj in (-1, 1):
+                        o = [0] * self.d
+                        o[i], o[j] = si, sj
+                        offs.append(o)
+        col = np.full(self.ne, -1, dtype=np.int64)
+        for e in range(self.ne):
+            used = set()
+            for o in offs:
+                idx = self.idx[e] + np.asarray(o)
+                ok = True
+                for k in range(self.d):
+                    if idx[k] < 0 or idx[k] >= self.n[k]:
+                        if not self.periodic(k):
+                            ok = False
+                        idx[k] %= self.n[k]
+                if ok:
+                    j = int((idx * np.asarray(self.stride)).sum())
+                    if col[j] >= 0:
+                        used.add(int(col[j]))
+            c = 0
+            while c in used:
+                c += 1
+            col[e] = c
+        return col
 
     def interior_faces(self, k):
         """(L, R) element pairs sharing a face orthogonal to axis k, the normal
@@ -140,6 +182,53 @@ class _Acc:
                              np.concatenate(self.b))
 
 
+def interphase_orientation(prob, mesh, L, R):
+    """For interphase faces (L left, R right along the axis): the - element
+    (lower phase index), the + element, the normal sign sigma (+1 when the
+    normal is +e_k) and the viscosity-upwinded lambda of eq. (viscosityupwind)."""
+    lowL = mesh.chi[L] < mesh.chi[R]
+    minus = np.where(lowL, L, R)
+    plus = np.where(lowL, R, L)
+    mu_ph = np.asarray(prob.mu_phase, dtype=np.float64)
+    mu_m, mu_p = mu_ph[mesh.chi[minus] - 1], mu_ph[mesh.chi[plus] - 1]
+    lam = np.where(mu_m < mu_p, 0.0, np.where(mu_m == mu_p, 0.5, 1.0))
+    return lowL, minus, plus, lam, mu_m, mu_p
+
+
+def interphase_faces(prob, mesh, k, L, R, F, g, Et):
+    """Interphase faces orthogonal to axis k (Appendix A, eq. gsum and
+    eq. Epenalty): lift (1 - lambda)(u^+ - u^-) v^- n + lambda (u^+ - u^-) v^+ n
+    and the velocity penalty tau_ij [u][v] with tau_ij = 3 p min(mu^-, mu^+)/h
+    (Cartesian value of Appendix A.1); no pressure penalty."""
+    if len(L) == 0:
+        return
+    hk = mesh.h[k]
+    area = mesh.vol / hk
+    lowL, minus, plus, lam, mu_m, mu_p = interphase_orientation(prob, mesh, L, R)
+    tau_ij = 3.0 * prob.p * np.minimum(mu_m, mu_p) / hk
+    for orient in (True, False):
+        m = lowL == orient
+        if not np.any(m):
+            continue
+        sig = 1.0 if orient else -1.0          # normal from - into +
+        sm, sp_ = (1, -1) if orient else (-1, 1)   # face side of the - and + element
+        a_m = ((1.0 - lam[m]) * sig * area)[:, None, None]
+        a_p = (lam[m] * sig * area)[:, None, None]
+        g.add(minus[m], plus[m], a_m * F(k, sm, sp_))
+        g.add(minus[m], minus[m], -a_m * F(k, sm, sm))
+        g.add(plus[m], plus[m], a_p * F(k, sp_, sp_))
+        g.add(plus[m], minus[m], -a_p * F(k, sp_, sm))
+        t = (tau_ij[m] * area)[:, None, None]
+        Et.add(minus[m], minus[m], t * F(k, sm, sm))
+        Et.add(minus[m], plus[m], -t * F(k, sm, sp_))
+        Et.add(plus[m], minus[m], -t * F(k, sp_, sm))
+        Et.add(plus[m], plus[m], t * F(k, sp_, sp_))
+
+
+def element_phases(prob, mesh):
+    return None if prob.phase is None else np.asarray(prob.phase(mesh.centre), dtype=np.int64)
+
+
 def fine_operators(prob, quad=None):
     """Assemble the fine-level operators of Appendix A for Problem prob.
 
@@ -148,6 +237,7 @@ def fine_operators(prob, quad=None):
     d, p = prob.d, prob.p
     s = (p + 1) ** d
     mesh = Mesh(d, prob.n, prob.lo, prob.hi, prob.bc)
+    mesh.chi = element_phases(prob, mesh)
     ne = mesh.ne
     q = 2 * p + 2 if quad is None else quad
     unsteady = prob.delta is not None
@@ -189,6 +279,10 @@ def fine_operators(prob, quad=None):
         e = np.arange(ne)
         g.add(e, e, (mesh.vol / hk) * basis.axis_op(d, p, k, K))
         L, R = mesh.interior_faces(k)
+        if mesh.chi is not None:
+            same = mesh.chi[L] == mesh.chi[R]
+            interphase_faces(prob, mesh, k, L[~same], R[~same], F, g, Et)
+            L, R = L[same], R[same]
         # Lift of intraphase faces into the + (right) element rows.
         g.add(R, R, area * F(k, -1, -1))
         g.add(R, L, -area * F(k, -1, 1))
@@ -272,6 +366,44 @@ def rhs(prob, ops, quad=None):
                 for i in range(d):
                     integ = fj * np.einsum("fq,qa->fa", hv[..., i] * w[None, :], PhiF)
                     np.add.at(bu[i].reshape(ne, s), B, integ)
+    if mesh.chi is not None:
+        for k in range(d):
+            L, R = mesh.interior_faces(k)
+            diff = mesh.chi[L] != mesh.chi[R]
+            L, R = L[diff], R[diff]
+            if len(L) == 0:
+                continue
+            hk = mesh.h[k]
+            area = mesh.vol / hk
+            fj = area / 2 ** (d - 1)
+            lowL, minus, plus, lam, mu_m, mu_p = interphase_orientation(prob, mesh, L, R)
+            tau_ij = 3.0 * p * np.minimum(mu_m, mu_p) / hk
+            for orient in (True, False):
+                m = lowL == orient
+                if not np.any(m):
+                    continue
+                sig = 1.0 if orient else -1.0
+                sm, sp_ = (1, -1) if orient else (-1, 1)
+                x, w = mesh.face_points(minus[m], k, sm, q)
+                nvec = np.zeros(d)
+                nvec[k] = sig
+                shp = x.shape[:-1]
+                gj, hj = ex.jumps(x.reshape(-1, d), nvec,
+                                  np.repeat(mesh.chi[minus[m]], shp[1]), np.repeat(mesh.chi[plus[m]], shp[1]))
+                gj, hj = gj.reshape(shp + (d,)), hj.reshape(shp + (d,))
+                Pm, Pp = basis.face_basis(d, p, q, k, sm), basis.face_basis(d, p, q, k, sp_)
+                lm, lp, tij = (1.0 - lam[m])[:, None], lam[m][:, None], tau_ij[m][:, None]
+                for i in range(d):
+                    gm = fj * np.einsum("fq,qa->fa", gj[..., i] * w[None, :], Pm)
+                    gp = fj * np.einsum("fq,qa->fa", gj[..., i] * w[None, :], Pp)
+                    hm = fj * np.einsum("fq,qa->fa", hj[..., i] * w[None, :], Pm)
+                    hp = fj * np.einsum("fq,qa->fa", hj[..., i] * w[None, :], Pp)
+                    # J_g,ik (eq. gsum), J_h (eq. wworkings) and -E_{u,g}(0) (eq. Epenalty)
+                    np.add.at(jg[i][k].reshape(ne, s), minus[m], lm * sig * gm)
+                    np.add.at(jg[i][k].reshape(ne, s), plus[m], lp * sig * gp)
+                    np.add.at(bu[i].reshape(ne, s), minus[m], lp * hm + tij * gm)
+                    np.add.at(bu[i].reshape(ne, s), plus[m], lm * hp - tij * gp)
+                    # J_{g.n} (eq. ewv) = sum_i J_g,ii enters b_p below.
     Minv = 1.0 / mesh.vol
     for i in range(d):
         for j in range(d):

@@ -63,7 +63,7 @@ class SmootherLevel:
             self.Aoff.data = round_bf16(self.Aoff.data)
             self.diag = round_bf16(self.diag)
         self.colour = lev.mesh.colour()
-        self.ncol = 2 ** lev.mesh.d
+        self.ncol = int(self.colour.max()) + 1
         self.elems = [np.nonzero(self.colour == c)[0] for c in range(self.ncol)]
         self.rows = [(e[:, None] * self.nb + np.arange(self.nb)[None, :]).ravel() for e in self.elems]
         self.Aoff_rows = [self.Aoff[r, :].tocsr() for r in self.rows]
@@ -116,6 +116,16 @@ class Multigrid:
     @property
     def A(self):
         return self.levels[0].A
+
+    def scale_rhs(self, b):
+        """b~ = D b for the sqrt(mu)-scaled system (identity without scaling)."""
+        D = self.levels[0].D
+        return b if D is None else D * b
+
+    def unscale(self, x):
+        """x = D x~ (identity without scaling)."""
+        D = self.levels[0].D
+        return x if D is None else D * x
 
     def bottom_solve(self, b, refine=3):
         """Least-squares solution A_c^+ b of the bottom level (Section 3

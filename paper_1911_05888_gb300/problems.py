@@ -71,6 +71,13 @@ class Problem:
     nu2: int = 1
     exact: "Manufactured" = None
     name: str = ""
+    # Multi-phase (grid-aligned phases): phase(x) -> phase index 1..P of the
+    # points x[..., d] (elements never straddle an interface); mu_phase[c-1]
+    # is the viscosity of phase c; scale_mu applies the sqrt(mu) diagonal
+    # scaling of the Stokes operator.
+    phase: Optional[Callable] = None
+    mu_phase: Optional[Sequence[float]] = None
+    scale_mu: bool = False
 
     def __post_init__(self):
         if self.lo is None:
@@ -218,6 +225,81 @@ def timeperiodic_solution_3d(t, omega, re, rho=1.0, delta=None):
     mu_expr = lambda xs: sp.Float(1.0 / re)
     rho_expr = lambda xs: sp.Float(rho)
     return Manufactured(3, u_exprs, p_expr, mu_expr, 0, rho_expr, delta)
+
+
+class MultiPhaseManufactured:
+    """Appendix C manufactured solution per phase: u_i = prod_j sin 2pi(x_j -
+    0.2 i - 0.25(chi-1)), p = mu_chi prod_j sin 2pi(x_j + 0.2 - 0.25(chi-1)),
+    with the phase chi of each point; jump data g_ij = u_i - u_j and
+    h_ij = sigma_i n - sigma_j n on an interface with normal n from phase i
+    (the lower index) into phase j."""
+
+    def __init__(self, d, gamma, mu_phase, phase):
+        import sympy as sp
+        self.d, self.gamma, self.phase = d, gamma, phase
+        self.sol = []
+        for c, muc in enumerate(mu_phase, start=1):
+            sh = sp.Rational(1, 4) * (c - 1)
+            u_exprs = [lambda xs, i=i, sh=sh: sp.Mul(*[_sin(xs[j] - sp.Rational(i, 5) - sh) for j in range(d)])
+                       for i in range(1, d + 1)]
+            p_expr = lambda xs, sh=sh, muc=muc: sp.Float(muc) * sp.Mul(*[_sin(xs[j] + sp.Rational(1, 5) - sh)
+                                                                         for j in range(d)])
+            self.sol.append(Manufactured(d, u_exprs, p_expr, lambda xs, muc=muc: sp.Float(muc), gamma))
+
+    def _per_phase(self, name, x, *args, chi=None):
+        x = np.asarray(x, dtype=np.float64)
+        chi = self.phase(x) if chi is None else np.broadcast_to(chi, x.shape[:-1])
+        out = None
+        for c, sol in enumerate(self.sol, start=1):
+            m = chi == c
+            if not np.any(m):
+                continue
+            v = getattr(sol, name)(x[m], *args)
+            if out is None:
+                out = np.zeros(x.shape[:-1] + v.shape[1:])
+            out[m] = v
+        return out
+
+    def u(self, x, chi=None):
+        return self._per_phase("u", x, chi=chi)
+
+    def p(self, x, chi=None):
+        return self._per_phase("p", x, chi=chi)
+
+    def f(self, x, chi=None):
+        return self._per_phase("f", x, chi=chi)
+
+    def fdiv(self, x, chi=None):
+        return self._per_phase("fdiv", x, chi=chi)
+
+    def stress(self, x, nrm, chi=None):
+        return self._per_phase("stress", x, nrm, chi=chi)
+
+    def jumps(self, x, nrm, chi_minus, chi_plus):
+        """(g, h) on interface points x with normal nrm from chi_minus to chi_plus."""
+        g = self.u(x, chi=chi_minus) - self.u(x, chi=chi_plus)
+        h = self.stress(x, nrm, chi=chi_minus) - self.stress(x, nrm, chi=chi_plus)
+        return g, h
+
+
+def square_interface(d=2, n=16, p=2, mu_inner=1e-3, mu_outer=1.0, nu=(3, 3), tau=None, scale_mu=True,
+                     bc=None):
+    """Multi-phase test of Section 5.6: phase 1 = (1/4, 3/4)^d with viscosity
+    mu_inner, phase 2 outside with mu_outer, viscous-stress form, periodic."""
+    mu_phase = [mu_inner, mu_outer]
+
+    def phase(x):
+        x = np.asarray(x, dtype=np.float64)
+        inside = np.all((x > 0.25) & (x < 0.75), axis=-1)
+        return np.where(inside, 1, 2)
+
+    def mu(x):
+        return np.where(phase(x) == 1, mu_inner, mu_outer).astype(np.float64)
+
+    ex = MultiPhaseManufactured(d, 1, mu_phase, phase)
+    return Problem(d=d, n=(n,) * d, p=p, gamma=1, bc=tuple(bc or (PERIODIC,) * (2 * d)), mu=mu, tau=tau,
+                   nu1=nu[0], nu2=nu[1], exact=ex, phase=phase, mu_phase=mu_phase, scale_mu=scale_mu,
+                   name="%dd-square-interface-n%d-p%d-ratio%g" % (d, n, p, mu_inner / mu_outer))
 
 
 def mu_variable_2d(seed=0, n_extra=0):

@@ -458,3 +458,63 @@ def test_learned_residual_objective_gradient_matches_finite_differences():
         fd = (learned.residual_loss_and_grad(lev.A, r, nbrs, wp, nin, hid, nout)[0] -
               learned.residual_loss_and_grad(lev.A, r, nbrs, wm, nin, hid, nout)[0]) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-7 * np.abs(g).max()
+
+
+# ------------------------------------------------------------ multi-phase ----
+
+@pytest.mark.parametrize("ratio", [1e-3, 1e3])
+def test_multiphase_symmetry_kernel_and_colouring(ratio):
+    """Section 5.6 square interface: symmetric operator (also after the sqrt(mu)
+    scaling), periodic kernel of dimension d+1, and the greedy colouring
+    separates every pair of coupled elements (interphase lifts couple
+    elements two apart)."""
+    prob = P.square_interface(n=8, p=1, mu_inner=ratio)
+    levels, _ = hierarchy.build_hierarchy(prob)
+    assert [l.ne for l in levels] == [64, 16]      # same-phase agglomeration stops at 4x4
+    for lev in levels:
+        A = lev.A
+        assert abs(A - A.T).max() <= 1e-13 * abs(A).max()
+        col = lev.mesh.colour()
+        coo = A.tocoo()
+        ei, ej = coo.row // lev.nb, coo.col // lev.nb
+        off = (ei != ej) & (np.abs(coo.data) > 0)
+        assert not np.any(col[ei[off]] == col[ej[off]])
+    lam = np.linalg.eigvalsh(levels[0].A.toarray())
+    assert int((np.abs(lam) <= 1e-10 * np.abs(lam).max()).sum()) == 3
+
+
+def _mp_errors(prob, mg, x):
+    lev = mg.levels[0]
+    mesh, d, p, s = lev.mesh, prob.d, prob.p, lev.s
+    q = p + 3
+    xv, wv = mesh.volume_points(q)
+    Phi = basis.tensor_basis(d, p, q)
+    jac = mesh.vol / 2 ** d
+    vals = np.einsum("qa,eva->eqv", Phi, x.reshape(mesh.ne, d + 1, s))
+    ue, pe = prob.exact.u(xv), prob.exact.p(xv)
+    out = []
+    for v in range(d + 1):
+        err = vals[..., v] - (ue[..., v] if v < d else pe)
+        err = err - (err * wv).sum() / (wv.sum() * mesh.ne)
+        out.append(np.sqrt(jac * (err ** 2 * wv).sum()))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("ratio", [1e-3, 1e3])
+def test_multiphase_orders_and_rate(ratio):
+    """Section 5.6: viscosity-upwinded fluxes with jump data and the sqrt(mu)
+    scaling: velocity order p+1, pressure about p+1/2 (p = 2), and
+    V(3,3)-preconditioned GMRES needs 7-10 iterations per 1e8 (rho <= 0.16)."""
+    errs = []
+    for n in (8, 16):
+        prob = P.square_interface(n=n, p=2, mu_inner=ratio, nu=(3, 3))
+        mg = multigrid.Multigrid(prob)
+        b = mg.scale_rhs(mg.levels[0].P @ ldg.rhs(prob, mg.levels[0].ops))
+        x, hist = mg.fgmres(b, rtol=1e-12, maxit=60, restart=60)
+        assert hist[-1] <= 1e-12
+        errs.append(_mp_errors(prob, mg, mg.unscale(x)))
+    rate = np.log2(errs[0] / errs[1])
+    assert np.all(rate[:2] > 2.7), rate
+    assert rate[2] > 1.9, rate
+    rho, it = mg.gmres_rho(P.random_vector(prob.n_elements, prob.nb, seed=1).ravel())
+    assert rho <= 0.16, rho
