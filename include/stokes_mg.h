@@ -159,6 +159,36 @@ int stk_get_block(stk_ctx* ctx, int level, int64_t i, int64_t j, double* out);
  * sides).  Writes the host array b [element][nb]. */
 int stk_assemble_rhs(stk_ctx* ctx, const double* f_vol, const double* bdata, double* b);
 
+/*
+ * Phases (Section 5.6 and Appendix A): chi [element] in 1..nphase gives the
+ * phase of each finest element (interfaces along element faces), mu_phase
+ * [nphase] the viscosity of each phase.  Interphase faces get the
+ * viscosity-upwinded fluxes of eq. (viscosityupwind) with lambda = 0, 1/2, 1,
+ * the penalty tau_ij = 3 p min(mu-, mu+) / h and no pressure penalty; coarse
+ * levels agglomerate only same-phase children (the hierarchy ends at the
+ * first level where a coarse cell would mix phases); smoothing uses a greedy
+ * colouring (elements in order, smallest colour unused within the coupling
+ * stencil).  scale = 1 replaces every level's operator by D A D with D =
+ * mu_E^{-1/2} on velocity and mu_E^{1/2} on pressure unknowns (mu_E the
+ * element mean of mu); every call then works on that scaled system
+ * (b~ = D b, x = D x~; stk_get_scaling gives D).  nphase = 0 clears phases.
+ * Call after stk_set_discretisation and before stk_setup.
+ */
+int stk_set_phases(stk_ctx* ctx, int nphase, const int* chi, const double* mu_phase, int scale);
+/* For every interior-face point: the phase of the - and + element of an
+ * interphase face (0 and 0 on faces inside one phase) and the face normal
+ * [point][d] (from the lower phase into the higher on interphase faces). */
+int stk_get_interface(stk_ctx* ctx, int* chi_minus, int* chi_plus, double* normals);
+/* stk_assemble_rhs with interface jump data: idata [interior-face
+ * point][2d] = (g_ij, h_ij) with g_ij = u(-) - u(+) and h_ij = sigma(-) n -
+ * sigma(+) n on interphase faces (ignored elsewhere; may be NULL without
+ * phases).  b is the right-hand side of the unscaled system. */
+int stk_assemble_rhs2(stk_ctx* ctx, const double* f_vol, const double* bdata, const double* idata, double* b);
+/* Colour of every element (natural order) on a smoothing level. */
+int stk_get_colours(stk_ctx* ctx, int level, int* colours);
+/* Level-0 diagonal scaling D [element][nb] (all ones without scaling). */
+int stk_get_scaling(stk_ctx* ctx, double* D);
+
 /* ---- hot path ------------------------------------------------------------ */
 
 /* r = b - A x on level 0 in FP64 (eq. blockform); optional ||r||_2 into

@@ -191,14 +191,23 @@ void pack_level(Ctx& c, int l, cudaStream_t st) {
   int64_t ne = H.ne;
   D.ne = (int)ne;
   for (int k = 0; k < 3; ++k) D.n[k] = H.n[k];
-  int ncol = 1 << c.d;
+  // Parity colouring (single phase) or greedy colouring (phases: the
+  // interphase lifts couple elements two apart along an axis).
+  std::vector<int> colour(ne);
+  if (!H.chi.empty())
+    greedy_colours(c, H.n, colour);
+  else
+    for (int64_t e = 0; e < ne; ++e) colour[e] = colour_of(c, H.n, e);
+  int ncol = 0;
+  for (int v : colour) ncol = std::max(ncol, v + 1);
+  if (ncol > 64) throw std::runtime_error("more than 64 colours");
   D.ncolour = ncol;
   std::vector<int> perm;
   perm.reserve(ne);
   D.cstart[0] = 0;
   for (int col = 0; col < ncol; ++col) {
     for (int64_t e = 0; e < ne; ++e)
-      if (colour_of(c, H.n, e) == col) perm.push_back((int)e);
+      if (colour[e] == col) perm.push_back((int)e);
     D.cstart[col + 1] = (int)perm.size();
   }
   std::vector<int> nbr((size_t)ne * P.NO);
@@ -870,7 +879,9 @@ int stk_set_discretisation(stk_ctx* c, int p, int gamma) {
     c->nb = (c->d + 1) * s;
     c->q = 2 * p + 2;
     if (c->tau0 < 0) c->tau0 = 0.5 * p;
-    build_pattern(c->d, p, gamma, c->pat);
+    build_pattern(c->d, p, gamma, false, c->pat);
+    c->chi.clear();
+    c->mu_phase.clear();
     c->mu_vol.clear();
     return STK_OK;
   });
@@ -969,6 +980,7 @@ int stk_setup(stk_ctx* c, void* stream) {
     if (c->mu_vol.empty()) return fail(c, STK_ERR_INVALID_ARG, "set the viscosity first");
     ck(cudaSetDevice(c->device), "cudaSetDevice");
     free_device(*c);
+    build_pattern(c->d, c->p, c->gamma, !c->chi.empty(), c->pat);
     int rc = setup_host(*c);
     if (rc != STK_OK) return rc;
     int L = nlevels(*c);
@@ -1635,6 +1647,79 @@ int stk_learn_weights(stk_ctx* c, float* host, int64_t count, int direction) {
       ck(cudaMemcpy(c->lW1, host, count * 4, cudaMemcpyHostToDevice), "copy weights");
       invalidate_graphs(*c);
     }
+    return STK_OK;
+  });
+}
+
+int stk_set_phases(stk_ctx* c, int nphase, const int* chi, const double* mu_phase, int scale) {
+  return guard(c, [&]() -> int {
+    if (c->p < 0) return fail(c, STK_ERR_INVALID_ARG, "set mesh and discretisation first");
+    free_device(*c);
+    if (nphase == 0) {
+      c->chi.clear();
+      c->mu_phase.clear();
+      c->scale_mu = 0;
+      return STK_OK;
+    }
+    if (nphase < 1 || nphase > 64 || !chi || !mu_phase) return fail(c, STK_ERR_INVALID_ARG, "bad phase arguments");
+    int64_t ne = 1;
+    for (int k = 0; k < c->d; ++k) ne *= c->n[k];
+    for (int64_t e = 0; e < ne; ++e)
+      if (chi[e] < 1 || chi[e] > nphase) return fail(c, STK_ERR_INVALID_ARG, "phase index out of range");
+    for (int i = 0; i < nphase; ++i)
+      if (!(mu_phase[i] > 0) || !std::isfinite(mu_phase[i]))
+        return fail(c, STK_ERR_INVALID_ARG, "phase viscosity must be finite and positive");
+    c->chi.assign(chi, chi + ne);
+    c->mu_phase.assign(mu_phase, mu_phase + nphase);
+    c->scale_mu = scale ? 1 : 0;
+    return STK_OK;
+  });
+}
+
+int stk_get_interface(stk_ctx* c, int* chi_minus, int* chi_plus, double* normals) {
+  return guard(c, [&]() -> int {
+    if (c->p < 0) return fail(c, STK_ERR_INVALID_ARG, "set mesh and discretisation first");
+    std::vector<int> cm, cp;
+    std::vector<double> nr;
+    interface_info(*c, cm, cp, nr);
+    if (chi_minus) std::copy(cm.begin(), cm.end(), chi_minus);
+    if (chi_plus) std::copy(cp.begin(), cp.end(), chi_plus);
+    if (normals) std::copy(nr.begin(), nr.end(), normals);
+    return STK_OK;
+  });
+}
+
+int stk_assemble_rhs2(stk_ctx* c, const double* f_vol, const double* bdata, const double* idata, double* b) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (!f_vol || !b) return fail(c, STK_ERR_INVALID_ARG, "null argument");
+    if (count_points(*c, 2) > 0 && !bdata) return fail(c, STK_ERR_INVALID_ARG, "null boundary data");
+    return assemble_rhs_host2(*c, f_vol, bdata, idata, b);
+  });
+}
+
+int stk_get_colours(stk_ctx* c, int level, int* colours) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (level < 0 || level >= nlevels(*c) - 1 || !colours) return fail(c, STK_ERR_INVALID_ARG, "bad level");
+    const DevLevel& D = c->dev[level];
+    std::vector<int> perm(D.ne);
+    ck(cudaMemcpy(perm.data(), D.perm, D.ne * sizeof(int), cudaMemcpyDeviceToHost), "copy perm");
+    for (int col = 0; col < D.ncolour; ++col)
+      for (int pos = D.cstart[col]; pos < D.cstart[col + 1]; ++pos) colours[perm[pos]] = col;
+    return STK_OK;
+  });
+}
+
+int stk_get_scaling(stk_ctx* c, double* D) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (!D) return fail(c, STK_ERR_INVALID_ARG, "null argument");
+    const HostLevel& H = c->host[0];
+    if (H.Dscale.empty())
+      std::fill(D, D + (size_t)H.ne * c->nb, 1.0);
+    else
+      std::copy(H.Dscale.begin(), H.Dscale.end(), D);
     return STK_OK;
   });
 }

@@ -5,6 +5,7 @@
 // pseudo-inverse.  Setup runs once per problem; the V-cycle itself runs in
 // the CUDA kernels of kernels.cu.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -344,12 +345,14 @@ static int64_t neighbour(const Ctx& c, const int* n, int64_t e, const int* off) 
 
 static inline int slot_minus(int k) { return 1 + 2 * k; }
 static inline int slot_plus(int k) { return 2 + 2 * k; }
+// G_k slots: 0 the element, 1 its -e_k neighbour, 2 its +e_k neighbour.
+constexpr int kGS = 3;
 
 // ---------------------------------------------------------------------------
 // Coupling pattern (derived from the one-sided fluxes u^ = u^-, sigma^ = sigma^+
 // of eq. ustarflux / qstarflux and the lift into the + element, eq. gsum)
 // ---------------------------------------------------------------------------
-void build_pattern(int d, int p, int gamma, Pattern& pat) {
+void build_pattern(int d, int p, int gamma, bool multiphase, Pattern& pat) {
   std::memset(&pat, 0, sizeof(pat));
   int s = 1;
   for (int k = 0; k < d; ++k) s *= (p + 1);
@@ -374,7 +377,8 @@ void build_pattern(int d, int p, int gamma, Pattern& pat) {
     pat.task_cv[t] = cv;
     pat.task_o[t] = offset_slot(o[0], o[1], o[2]);
   };
-  // Fixed offset order: -e_k, +e_k for every axis, then the diagonal ones.
+  // Fixed offset order: -e_k, +e_k for every axis first (the learned
+  // smoother's features rely on it), then the others.
   for (int k = 0; k < d; ++k) {
     int o[3];
     unit(k, -1, o);
@@ -382,6 +386,10 @@ void build_pattern(int d, int p, int gamma, Pattern& pat) {
     unit(k, 1, o);
     offset_slot(o[0], o[1], o[2]);
   }
+  // Single phase: G_k(E, .) is nonzero at E and E - e_k (one-sided fluxes).
+  // With interphase faces the lift can also land at E + e_k, so G_k has the
+  // offsets {0, -e_k, +e_k} and products G^T M G reach +-2e_k and the
+  // diagonal neighbours +-e_i +- e_j.
   for (int rv = 0; rv <= d; ++rv) {
     pat.rv_t0[rv] = pat.T;
     int o[3];
@@ -392,26 +400,51 @@ void build_pattern(int d, int p, int gamma, Pattern& pat) {
         add(i, i, o);
         unit(k, 1, o);
         add(i, i, o);
+        if (multiphase) {
+          unit(k, -2, o);
+          add(i, i, o);
+          unit(k, 2, o);
+          add(i, i, o);
+        }
       }
       if (gamma) {
         for (int j = 0; j < d; ++j) {
           if (j == i) continue;
-          unit(i, -1, o);
-          add(i, j, o);
-          unit(j, 1, o);
-          add(i, j, o);
-          o[0] = o[1] = o[2] = 0;
-          o[j] = 1;
-          o[i] = -1;
-          add(i, j, o);
+          if (!multiphase) {
+            unit(i, -1, o);
+            add(i, j, o);
+            unit(j, 1, o);
+            add(i, j, o);
+            o[0] = o[1] = o[2] = 0;
+            o[j] = 1;
+            o[i] = -1;
+            add(i, j, o);
+          } else {
+            for (int si = -1; si <= 1; ++si)
+              for (int sj = -1; sj <= 1; ++sj) {
+                if (si == 0 && sj == 0) continue;
+                o[0] = o[1] = o[2] = 0;
+                o[i] = si;
+                o[j] = sj;
+                add(i, j, o);
+              }
+          }
         }
       }
       unit(i, 1, o);
       add(i, d, o);
+      if (multiphase) {
+        unit(i, -1, o);
+        add(i, d, o);
+      }
     } else {
       for (int j = 0; j < d; ++j) {
         unit(j, -1, o);
         add(d, j, o);
+        if (multiphase) {
+          unit(j, 1, o);
+          add(d, j, o);
+        }
       }
       for (int k = 0; k < d; ++k) {
         unit(k, -1, o);
@@ -641,7 +674,7 @@ static void fine_assembly(Ctx& c, const Tensors& T, HostLevel& L) {
   L.M.assign((size_t)ne * ss, 0.0);
   L.Mmu.assign((size_t)ne * ss, 0.0);
   if (unsteady) L.Mrho.assign((size_t)ne * ss, 0.0);
-  L.G.assign((size_t)d * ne * 2 * ss, 0.0);
+  L.G.assign((size_t)d * ne * kGS * ss, 0.0);
   L.Et.assign((size_t)ne * nsl * ss, 0.0);
   L.E.assign((size_t)ne * nsl * ss, 0.0);
   if (unsteady) {
@@ -663,7 +696,7 @@ static void fine_assembly(Ctx& c, const Tensors& T, HostLevel& L) {
           }
       }
       for (int k = 0; k < d; ++k)
-        axpy_block(s, 1.0 / L.h[k], T.Kax[k], &L.G[(((size_t)k * ne + e) * 2 + 0) * ss]);
+        axpy_block(s, 1.0 / L.h[k], T.Kax[k], &L.G[(((size_t)k * ne + e) * kGS + 0) * ss]);
     }
   });
   double wsum = 0.0;
@@ -676,8 +709,34 @@ static void fine_assembly(Ctx& c, const Tensors& T, HostLevel& L) {
     int k = faces[f].k;
     int64_t R = faces[f].e, Lf = faces[f].L;
     double hk = L.h[k], area = L.vol / hk;
-    double* GRR = &L.G[(((size_t)k * ne + R) * 2 + 0) * ss];
-    double* GRL = &L.G[(((size_t)k * ne + R) * 2 + 1) * ss];
+    if (!L.chi.empty() && L.chi[Lf] != L.chi[R]) {
+      // Interphase face (eq. gsum, eq. Epenalty): normal from the lower phase
+      // (the - element) into the higher; lift (1-lambda)(u+ - u-) v- n +
+      // lambda (u+ - u-) v+ n, lambda by viscosity upwinding
+      // (eq. viscosityupwind); penalty tau_ij [u][v] with
+      // tau_ij = 3 p min(mu-, mu+) / h; no pressure penalty.
+      const bool lowL = L.chi[Lf] < L.chi[R];
+      const int64_t mi = lowL ? Lf : R, pl = lowL ? R : Lf;
+      const double sig = lowL ? 1.0 : -1.0;
+      const int sm = lowL ? 1 : 0, sp = lowL ? 0 : 1;             // face-side index of - / + element
+      const int slot_mp = lowL ? 2 : 1, slot_pm = lowL ? 1 : 2;   // G slot of the other element
+      const double mum = c.mu_phase[L.chi[mi] - 1], mup = c.mu_phase[L.chi[pl] - 1];
+      const double lam = mum < mup ? 0.0 : (mum == mup ? 0.5 : 1.0);
+      const double am = (1.0 - lam) * sig * area / L.vol, ap = lam * sig * area / L.vol;
+      axpy_block(s, am, T.F[k][sm][sp], &L.G[(((size_t)k * ne + mi) * kGS + slot_mp) * ss]);
+      axpy_block(s, -am, T.F[k][sm][sm], &L.G[(((size_t)k * ne + mi) * kGS + 0) * ss]);
+      axpy_block(s, ap, T.F[k][sp][sp], &L.G[(((size_t)k * ne + pl) * kGS + 0) * ss]);
+      axpy_block(s, -ap, T.F[k][sp][sm], &L.G[(((size_t)k * ne + pl) * kGS + slot_pm) * ss]);
+      const double t = 3.0 * c.p * std::min(mum, mup) / hk * area;
+      const int psl_mp = lowL ? slot_plus(k) : slot_minus(k), psl_pm = lowL ? slot_minus(k) : slot_plus(k);
+      axpy_block(s, t, T.F[k][sm][sm], &L.Et[((size_t)mi * nsl + 0) * ss]);
+      axpy_block(s, -t, T.F[k][sm][sp], &L.Et[((size_t)mi * nsl + psl_mp) * ss]);
+      axpy_block(s, -t, T.F[k][sp][sm], &L.Et[((size_t)pl * nsl + psl_pm) * ss]);
+      axpy_block(s, t, T.F[k][sp][sp], &L.Et[((size_t)pl * nsl + 0) * ss]);
+      continue;
+    }
+    double* GRR = &L.G[(((size_t)k * ne + R) * kGS + 0) * ss];
+    double* GRL = &L.G[(((size_t)k * ne + R) * kGS + 1) * ss];
     axpy_block(s, area / L.vol, T.F[k][0][0], GRR);
     axpy_block(s, -area / L.vol, T.F[k][0][1], GRL);
     double muf = 0.0, rhof = 0.0;
@@ -715,7 +774,7 @@ static void fine_assembly(Ctx& c, const Tensors& T, HostLevel& L) {
     int64_t e = faces[f].e;
     double hk = L.h[k], area = L.vol / hk;
     axpy_block(s, -sd * area / L.vol, T.F[k][sidx(sd)][sidx(sd)],
-               &L.G[(((size_t)k * ne + e) * 2 + 0) * ss]);
+               &L.G[(((size_t)k * ne + e) * kGS + 0) * ss]);
     double muf = 0.0;
     for (int qi = 0; qi < T.Qf; ++qi) muf += T.wF[qi] * c.mu_bf[f * T.Qf + qi];
     muf /= wsum;
@@ -735,7 +794,7 @@ static void coarsen_level(const Ctx& c, const std::vector<double>& Pch, const Ho
   Cl.M.assign((size_t)ne * ss, 0.0);
   Cl.Mmu.assign((size_t)ne * ss, 0.0);
   if (unsteady) Cl.Mrho.assign((size_t)ne * ss, 0.0);
-  Cl.G.assign((size_t)d * ne * 2 * ss, 0.0);
+  Cl.G.assign((size_t)d * ne * kGS * ss, 0.0);
   Cl.Et.assign((size_t)ne * nsl * ss, 0.0);
   Cl.E.assign((size_t)ne * nsl * ss, 0.0);
   std::vector<double> Emu2, Erho2;
@@ -797,38 +856,35 @@ static void coarsen_level(const Ctx& c, const std::vector<double>& Pch, const Ho
       std::string err;
       invert_dense(s, &Cl.M[(size_t)C * ss], Minv.data());
       for (int k = 0; k < d; ++k) {
-        double* out[2] = {&Cl.G[(((size_t)k * ne + C) * 2 + 0) * ss],
-                          &Cl.G[(((size_t)k * ne + C) * 2 + 1) * ss]};
-        std::vector<double> sum0(ss, 0.0), sum1(ss, 0.0);
+        std::vector<double> sum[kGS];
+        for (int t = 0; t < kGS; ++t) sum[t].assign(ss, 0.0);
         for (int ch = 0; ch < (1 << d); ++ch) {
           int fi[3];
           for (int kk = 0; kk < d; ++kk) fi[kk] = 2 * I[kk] + ((ch >> kk) & 1);
           int64_t f = element_of(F.n, d, fi);
           const double* Pf = &Pch[(size_t)ch * ss];
-          for (int sl = 0; sl < 2; ++sl) {
-            int fo[3] = {fi[0], fi[1], fi[2]};
-            int chg = ch;
-            double* dst = &sum0[0];
-            if (sl == 1) {
-              int v = fi[k] - 1;
-              if (v < 0 && c.bc[2 * k] != STK_BC_PERIODIC) continue;
-              int vc = (v >= 0) ? v / 2 : -1;
-              dst = (vc - I[k] == 0) ? &sum0[0] : &sum1[0];
-              fo[k] = (v + F.n[k]) % F.n[k];
+          for (int sl = 0; sl < kGS; ++sl) {
+            int chg = ch, csl = 0;
+            if (sl > 0) {
+              const int sg = (sl == 1) ? -1 : 1;
+              const int v = fi[k] + sg;                 // unwrapped fine neighbour index
+              if ((v < 0 || v >= F.n[k]) && c.bc[2 * k] != STK_BC_PERIODIC) continue;
+              const int vc = (v >= 0) ? v / 2 : -1;     // floor(v / 2) for v >= -1
+              const int co = vc - I[k];
+              csl = (co == 0) ? 0 : (co < 0 ? 1 : 2);
               chg = ch ^ (1 << k);
             }
-            (void)fo;
-            // P_f^T M_f G_f(slot) P_g
+            // P_f^T M_f G_f(slot) P_g  (Algorithm 2 line 3, before M_2h^{-1})
             std::vector<double> MG(ss, 0.0);
-            gemm_acc(s, 1.0, &F.M[(size_t)f * ss], false,
-                     &F.G[(((size_t)k * nef + f) * 2 + sl) * ss], MG.data());
-            triple_acc(s, 1.0, Pf, MG.data(), &Pch[(size_t)chg * ss], dst, tmp);
+            gemm_acc(s, 1.0, &F.M[(size_t)f * ss], false, &F.G[(((size_t)k * nef + f) * kGS + sl) * ss], MG.data());
+            triple_acc(s, 1.0, Pf, MG.data(), &Pch[(size_t)chg * ss], sum[csl].data(), tmp);
           }
         }
-        std::fill(out[0], out[0] + ss, 0.0);
-        std::fill(out[1], out[1] + ss, 0.0);
-        gemm_acc(s, 1.0, Minv.data(), false, sum0.data(), out[0]);
-        gemm_acc(s, 1.0, Minv.data(), false, sum1.data(), out[1]);
+        for (int t = 0; t < kGS; ++t) {
+          double* out = &Cl.G[(((size_t)k * ne + C) * kGS + t) * ss];
+          std::fill(out, out + ss, 0.0);
+          gemm_acc(s, 1.0, Minv.data(), false, sum[t].data(), out);
+        }
       }
     }
   });
@@ -864,8 +920,9 @@ static const double* Gblk(const HostLevel& L, int d, int s, int k, int64_t E, co
   int sl;
   if (rel[k] == 0) sl = 0;
   else if (rel[k] == -1) sl = 1;
+  else if (rel[k] == 1) sl = 2;
   else return nullptr;
-  return &L.G[(((size_t)k * L.ne + E) * 2 + sl) * s * s];
+  return &L.G[(((size_t)k * L.ne + E) * kGS + sl) * s * s];
 }
 
 // Slot of a face-penalty operator for offset o (0, -e_k, +e_k), or -1.
@@ -877,7 +934,7 @@ static int pen_slot(int d, const int* o) {
       k = j;
     }
   if (nz == 0) return 0;
-  if (nz > 1) return -1;
+  if (nz > 1 || (o[k] != 1 && o[k] != -1)) return -1;
   return o[k] < 0 ? slot_minus(k) : slot_plus(k);
 }
 
@@ -896,10 +953,11 @@ static void stokes_block(const Ctx& c, const HostLevel& L, int64_t a, int rv, in
     int i = rv, j = cv;
     // delta_ij sum_k G_k^T M_mu G_k  and  gamma G_j^T M_mu G_i
     auto add_term = [&](int kr, int kc, double alpha) {
-      // sum over E = a + oE, oE in {0, +e_kr}: G_kr(E, a)^T M_mu(E) G_kc(E, a + o)
-      for (int t = 0; t < 2; ++t) {
+      // sum over E = a + oE, oE in {0, +e_kr, -e_kr}: G_kr(E, a)^T M_mu(E) G_kc(E, a + o)
+      for (int t = 0; t < 3; ++t) {
         int oE[3] = {0, 0, 0};
         if (t == 1) oE[kr] = 1;
+        if (t == 2) oE[kr] = -1;
         int64_t E;
         if (!exists(oE, E)) continue;
         int relA[3] = {-oE[0], -oE[1], -oE[2]};
@@ -973,6 +1031,70 @@ static void stokes_level(const Ctx& c, HostLevel& L) {
 // ---------------------------------------------------------------------------
 // Setup driver
 // ---------------------------------------------------------------------------
+// Greedy colouring of a level with phases (the coupling stencil reaches
+// +-e_k, +-2e_k and +-e_i +- e_j): elements in order, each takes the smallest
+// colour not taken by an already coloured element at any of those offsets.
+void greedy_colours(const Ctx& c, const int* n, std::vector<int>& colour) {
+  const int d = c.d;
+  std::vector<std::array<int, 3>> offs;
+  for (int k = 0; k < d; ++k)
+    for (int m = 1; m <= 2; ++m)
+      for (int sg = -1; sg <= 1; sg += 2) {
+        std::array<int, 3> o = {0, 0, 0};
+        o[k] = sg * m;
+        offs.push_back(o);
+      }
+  for (int i = 0; i < d; ++i)
+    for (int j = i + 1; j < d; ++j)
+      for (int si = -1; si <= 1; si += 2)
+        for (int sj = -1; sj <= 1; sj += 2) {
+          std::array<int, 3> o = {0, 0, 0};
+          o[i] = si;
+          o[j] = sj;
+          offs.push_back(o);
+        }
+  int64_t ne = 1;
+  for (int k = 0; k < d; ++k) ne *= n[k];
+  colour.assign(ne, -1);
+  for (int64_t e = 0; e < ne; ++e) {
+    uint64_t used = 0;
+    for (const auto& o : offs) {
+      int64_t j = neighbour(c, n, e, o.data());
+      if (j >= 0 && colour[j] >= 0 && colour[j] < 64) used |= (1ULL << colour[j]);
+    }
+    int col = 0;
+    while (used & (1ULL << col)) ++col;
+    colour[e] = col;
+  }
+}
+
+// sqrt(mu) scaling of Section 5.6 (multi-phase): per element mu_E^{-1/2} on
+// velocity rows/columns, mu_E^{1/2} on pressure, mu_E the element mean of mu
+// (M_mu(E)[0][0] / M(E)[0][0]); every level with its own mu_E.
+static void scale_level(const Ctx& c, HostLevel& L) {
+  const Pattern& P = c.pat;
+  const int s = c.s, nb = c.nb, ss = s * s, d = c.d;
+  const int64_t ne = L.ne;
+  L.Dscale.assign((size_t)ne * nb, 1.0);
+  for (int64_t e = 0; e < ne; ++e) {
+    const double mu = L.Mmu[(size_t)e * ss] / L.M[(size_t)e * ss];
+    for (int r = 0; r < nb; ++r) L.Dscale[(size_t)e * nb + r] = (r < d * s) ? 1.0 / std::sqrt(mu) : std::sqrt(mu);
+  }
+  for (int64_t a = 0; a < ne; ++a) {
+    const double* da = &L.Dscale[(size_t)a * nb];
+    double* D = &L.D[(size_t)a * nb * nb];
+    for (int r = 0; r < nb; ++r)
+      for (int q = 0; q < nb; ++q) D[(size_t)r * nb + q] *= da[r] * da[q];
+    for (int t = 0; t < P.T; ++t) {
+      const int64_t bb = L.nbr[(size_t)a * P.NO + P.task_o[t]];
+      if (bb < 0) continue;
+      const double fr = da[P.task_rv[t] * s], fc = L.Dscale[(size_t)bb * nb + P.task_cv[t] * s];
+      double* C = &L.C[((size_t)a * P.T + t) * ss];
+      for (int i = 0; i < ss; ++i) C[i] *= fr * fc;
+    }
+  }
+}
+
 int setup_host(Ctx& c) {
   int d = c.d;
   Tensors T = make_tensors(d, c.p, c.q);
@@ -990,6 +1112,7 @@ int setup_host(Ctx& c) {
     L0.ne *= L0.n[k];
     L0.vol *= L0.h[k];
   }
+  L0.chi = c.chi;
   fine_assembly(c, T, L0);
   c.host.push_back(std::move(L0));
   for (;;) {
@@ -1007,10 +1130,28 @@ int setup_host(Ctx& c) {
       Cl.ne *= Cl.n[k];
       Cl.vol *= Cl.h[k];
     }
+    if (!F.chi.empty()) {
+      // Same-phase agglomeration (Section 3): every coarse cell must hold
+      // children of a single phase, otherwise this is the bottom level.
+      Cl.chi.assign(Cl.ne, 0);
+      bool ok = true;
+      for (int64_t f = 0; f < F.ne && ok; ++f) {
+        int idx[3];
+        element_index(F.n, d, f, idx);
+        for (int k = 0; k < d; ++k) idx[k] /= 2;
+        const int64_t C = element_of(Cl.n, d, idx);
+        if (Cl.chi[C] == 0) Cl.chi[C] = F.chi[f];
+        else if (Cl.chi[C] != F.chi[f]) ok = false;
+      }
+      if (!ok) break;
+    }
     coarsen_level(c, Pch, F, Cl);
     c.host.push_back(std::move(Cl));
   }
-  for (auto& L : c.host) stokes_level(c, L);
+  for (auto& L : c.host) {
+    stokes_level(c, L);
+    if (c.scale_mu) scale_level(c, L);
+  }
   return STK_OK;
 }
 
@@ -1019,9 +1160,11 @@ int setup_host(Ctx& c) {
 namespace stk {
 
 // Right-hand side (Appendix A, eq. appstokes1 / appstokes2, times M) from
-// samples at the volume points (f_1..f_d, fdiv) and boundary-face points
-// (Dirichlet g or stress h).  b is [ne][nb], element-major.
-int assemble_rhs_host(const Ctx& c, const double* f_vol, const double* bdata, double* b) {
+// samples at the volume points (f_1..f_d, fdiv), boundary-face points
+// (Dirichlet g or stress h) and, for interphase faces, interior-face points
+// (g_ij then h_ij, normal from the lower phase into the higher).  b is
+// [ne][nb], element-major, of the unscaled system.
+int assemble_rhs_host2(const Ctx& c, const double* f_vol, const double* bdata, const double* idata, double* b) {
   int d = c.d, s = c.s, nb = c.nb, ss = s * s;
   Tensors T = make_tensors(d, c.p, c.q);
   const HostLevel& L = c.host[0];
@@ -1035,11 +1178,12 @@ int assemble_rhs_host(const Ctx& c, const double* f_vol, const double* bdata, do
         for (int a = 0; a < s; ++a) b[(size_t)e * nb + v * s + a] += val * T.Phi[(size_t)qi * s + a];
       }
   std::vector<double> jg((size_t)d * d * ne * s, 0.0);   // [i][j][e][a]
+  auto JG = [&](int i, int j, int64_t e, int a) -> double& { return jg[(((size_t)i * d + j) * ne + e) * s + a]; };
   std::vector<Face> faces;
   enumerate_faces(c, STK_PTS_BOUNDARY_FACE, faces);
   double wsum = 0.0;
   for (double w : T.wF) wsum += w;
-  std::vector<double> integ(s);
+  std::vector<double> integ(s), integ2(s);
   for (size_t f = 0; f < faces.size(); ++f) {
     int k = faces[f].k, sd = faces[f].side;
     int type = c.bc[2 * k + (sd < 0 ? 0 : 1)];
@@ -1059,45 +1203,92 @@ int assemble_rhs_host(const Ctx& c, const double* f_vol, const double* bdata, do
         double tb = c.c_bdry * c.p * muf / hk;
         for (int a = 0; a < s; ++a) {
           b[(size_t)e * nb + i * s + a] += tb * integ[a];                     // -E_{u,g}(0)
-          jg[(((size_t)i * d + k) * ne + e) * s + a] += sd * integ[a];        // J_g,ik
-          if (i == k) b[(size_t)e * nb + d * s + a] += sd * integ[a];         // J_{g.n}
+          JG(i, k, e, a) += sd * integ[a];                                     // J_g,ik
         }
       } else if (type == STK_BC_STRESS) {
         for (int a = 0; a < s; ++a) b[(size_t)e * nb + i * s + a] += integ[a];  // J_h
       }
     }
   }
+  // Interphase faces: J_g (eq. gsum), J_h (eq. wworkings), -E_{u,g}(0) (eq. Epenalty).
+  if (!L.chi.empty() && idata) {
+    enumerate_faces(c, STK_PTS_INTERIOR_FACE, faces);
+    for (size_t f = 0; f < faces.size(); ++f) {
+      const int64_t R = faces[f].e, Lf = faces[f].L;
+      if (L.chi[Lf] == L.chi[R]) continue;
+      const int k = faces[f].k;
+      const bool lowL = L.chi[Lf] < L.chi[R];
+      const int64_t mi = lowL ? Lf : R, pl = lowL ? R : Lf;
+      const double sig = lowL ? 1.0 : -1.0;
+      const int sm = lowL ? 1 : 0, sp = lowL ? 0 : 1;
+      const double mum = c.mu_phase[L.chi[mi] - 1], mup = c.mu_phase[L.chi[pl] - 1];
+      const double lam = mum < mup ? 0.0 : (mum == mup ? 0.5 : 1.0);
+      const double hk = L.h[k], area = L.vol / hk, fj = area / std::pow(2.0, d - 1);
+      const double tij = 3.0 * c.p * std::min(mum, mup) / hk;
+      const double* Pm = T.PhiF[k][sm].data();
+      const double* Pp = T.PhiF[k][sp].data();
+      for (int i = 0; i < d; ++i) {
+        // g part: components i of g at the face points; h part likewise
+        for (int part = 0; part < 2; ++part) {
+          std::fill(integ.begin(), integ.end(), 0.0);
+          std::fill(integ2.begin(), integ2.end(), 0.0);
+          for (int qi = 0; qi < T.Qf; ++qi) {
+            const double val = fj * T.wF[qi] * idata[(f * T.Qf + qi) * 2 * d + part * d + i];
+            for (int a = 0; a < s; ++a) {
+              integ[a] += val * Pm[(size_t)qi * s + a];
+              integ2[a] += val * Pp[(size_t)qi * s + a];
+            }
+          }
+          for (int a = 0; a < s; ++a) {
+            if (part == 0) {
+              JG(i, k, mi, a) += (1.0 - lam) * sig * integ[a];
+              JG(i, k, pl, a) += lam * sig * integ2[a];
+              b[(size_t)mi * nb + i * s + a] += tij * integ[a];
+              b[(size_t)pl * nb + i * s + a] -= tij * integ2[a];
+            } else {
+              b[(size_t)mi * nb + i * s + a] += lam * integ[a];
+              b[(size_t)pl * nb + i * s + a] += (1.0 - lam) * integ2[a];
+            }
+          }
+        }
+      }
+    }
+  }
+  // J_{g.n} = sum_i J_g,ii into the pressure rows (eq. ewv).
+  for (int64_t e = 0; e < ne; ++e)
+    for (int i = 0; i < d; ++i)
+      for (int a = 0; a < s; ++a) b[(size_t)e * nb + d * s + a] += JG(i, i, e, a);
   // - sum_j G_j^T M_mu M^{-1} (J_g,ij + gamma J_g,ji)
   std::vector<double> w((size_t)ne * s);
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) {
       bool any = false;
-      for (int64_t e = 0; e < ne && !any; ++e)
-        for (int a = 0; a < s; ++a)
-          if (jg[(((size_t)i * d + j) * ne + e) * s + a] != 0.0 ||
-              (c.gamma && jg[(((size_t)j * d + i) * ne + e) * s + a] != 0.0)) {
-            any = true;
-            break;
-          }
+      for (size_t t = 0; t < (size_t)ne * s && !any; ++t) {
+        const int64_t e = (int64_t)(t / s);
+        const int a = (int)(t % s);
+        if (JG(i, j, e, a) != 0.0 || (c.gamma && JG(j, i, e, a) != 0.0)) any = true;
+      }
       if (!any) continue;
       for (int64_t e = 0; e < ne; ++e) {
         double t[64];
         for (int a = 0; a < s; ++a)
-          t[a] = (jg[(((size_t)i * d + j) * ne + e) * s + a] +
-                  c.gamma * jg[(((size_t)j * d + i) * ne + e) * s + a]) / L.M[(size_t)e * ss + a * s + a];
+          t[a] = (JG(i, j, e, a) + c.gamma * JG(j, i, e, a)) / L.M[(size_t)e * ss + a * s + a];
         for (int a = 0; a < s; ++a) {
           double acc = 0.0;
           for (int bb = 0; bb < s; ++bb) acc += L.Mmu[(size_t)e * ss + a * s + bb] * t[bb];
           w[(size_t)e * s + a] = acc;
         }
       }
+      // (G_j^T w)(a) = sum over E with G_j(E, a) != 0: E = a (slot 0),
+      // E = a + e_j (slot 1 of E), E = a - e_j (slot 2 of E).
       for (int64_t a = 0; a < ne; ++a) {
-        for (int tt = 0; tt < 2; ++tt) {
+        for (int tt = 0; tt < kGS; ++tt) {
           int oE[3] = {0, 0, 0};
           if (tt == 1) oE[j] = 1;
+          if (tt == 2) oE[j] = -1;
           int64_t E = neighbour(c, L.n, a, oE);
           if (E < 0) continue;
-          const double* G = &L.G[(((size_t)j * ne + E) * 2 + tt) * ss];
+          const double* G = &L.G[(((size_t)j * ne + E) * kGS + tt) * ss];
           for (int m = 0; m < s; ++m) {
             double acc = 0.0;
             for (int r = 0; r < s; ++r) acc += G[r * s + m] * w[(size_t)E * s + r];
@@ -1107,6 +1298,39 @@ int assemble_rhs_host(const Ctx& c, const double* f_vol, const double* bdata, do
       }
     }
   return STK_OK;
+}
+
+int assemble_rhs_host(const Ctx& c, const double* f_vol, const double* bdata, double* b) {
+  return assemble_rhs_host2(c, f_vol, bdata, nullptr, b);
+}
+
+// Interior-face points: phase of the - and + element (0, 0 on intraphase
+// faces) and the normal (+e_k, or the interphase normal from the lower phase).
+void interface_info(const Ctx& c, std::vector<int>& chim, std::vector<int>& chip, std::vector<double>& nrm) {
+  std::vector<Face> faces;
+  enumerate_faces(c, STK_PTS_INTERIOR_FACE, faces);
+  int Qf = 1;
+  for (int k = 0; k < c.d - 1; ++k) Qf *= c.q;
+  chim.assign(faces.size() * Qf, 0);
+  chip.assign(faces.size() * Qf, 0);
+  nrm.assign(faces.size() * Qf * c.d, 0.0);
+  for (size_t f = 0; f < faces.size(); ++f) {
+    const int64_t R = faces[f].e, Lf = faces[f].L;
+    const int k = faces[f].k;
+    double sig = 1.0;
+    int cm = 0, cp = 0;
+    if (!c.chi.empty() && c.chi[Lf] != c.chi[R]) {
+      const bool lowL = c.chi[Lf] < c.chi[R];
+      sig = lowL ? 1.0 : -1.0;
+      cm = lowL ? c.chi[Lf] : c.chi[R];
+      cp = lowL ? c.chi[R] : c.chi[Lf];
+    }
+    for (int qi = 0; qi < Qf; ++qi) {
+      chim[f * Qf + qi] = cm;
+      chip[f * Qf + qi] = cp;
+      nrm[(f * Qf + qi) * c.d + k] = sig;
+    }
+  }
 }
 
 }  // namespace stk

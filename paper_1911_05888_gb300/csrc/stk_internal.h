@@ -38,7 +38,9 @@ struct HostLevel {
   double h[3] = {0, 0, 0};
   double vol = 0;
   std::vector<double> M, Mmu, Mrho;     // [ne][s*s]
-  std::vector<double> G;                // [d][ne][2][s*s]: G_k(e,e), G_k(e,e-e_k)
+  std::vector<double> G;                // [d][ne][3][s*s]: G_k(e,e), G_k(e,e-e_k), G_k(e,e+e_k)
+  std::vector<int> chi;                 // phase of every element (multi-phase problems)
+  std::vector<double> Dscale;           // [ne][nb] sqrt(mu) diagonal scaling (when enabled)
   std::vector<double> Et, E, Emu, Erho; // [ne][1+2d][s*s]
   // Stokes operator blocks
   std::vector<double> D;                // [ne][nb*nb] diagonal blocks (row-major)
@@ -49,7 +51,7 @@ struct HostLevel {
 // Device data of one level.
 struct DevLevel {
   int ne = 0;
-  int cstart[9] = {0};                  // colour ranges in colour-major positions
+  int cstart[65] = {0};                 // colour ranges in colour-major positions
   int ncolour = 0;
   int* perm = nullptr;                  // [ne] position -> element
   int* nbr = nullptr;                   // [ne][NO] per position
@@ -76,6 +78,11 @@ struct Ctx {
   int p = -1, gamma = 0;
   double tau = 0.1, tau0 = -1, c_bdry = 10.0, c_intra = 0.0;
   std::vector<double> mu_vol, mu_if, mu_bf, rho_vol, rho_if;
+  // phases (grid-aligned, 1-based) of the finest elements, viscosity per phase,
+  // sqrt(mu) diagonal scaling on/off
+  std::vector<int> chi;
+  std::vector<double> mu_phase;
+  int scale_mu = 0;
   double delta = 0.0;
   int nu1 = 1, nu2 = 1, precision = 0;
   // derived
@@ -157,7 +164,10 @@ struct Ctx {
 };
 
 // ---- setup.cpp --------------------------------------------------------------
-void build_pattern(int d, int p, int gamma, Pattern& pat);
+void build_pattern(int d, int p, int gamma, bool multiphase, Pattern& pat);
+void greedy_colours(const Ctx& c, const int* n, std::vector<int>& colour);
+int assemble_rhs_host2(const Ctx& c, const double* f_vol, const double* bdata, const double* idata, double* b);
+void interface_info(const Ctx& c, std::vector<int>& chim, std::vector<int>& chip, std::vector<double>& nrm);
 int setup_host(Ctx& c);                    // fine assembly, coarsening, Stokes blocks
 void child_matrices(int d, int p, std::vector<double>& out);   // [2^d][s][s]
 void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w);

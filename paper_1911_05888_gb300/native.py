@@ -68,6 +68,11 @@ SIGNATURES = {
     "stk_solve_multi": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_int_p,
                         _c_dbl_p, _vp],
     "stk_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "stk_set_phases": [_vp, ctypes.c_int, _c_int_p, _c_dbl_p, ctypes.c_int],
+    "stk_get_interface": [_vp, _c_int_p, _c_int_p, _c_dbl_p],
+    "stk_assemble_rhs2": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p],
+    "stk_get_colours": [_vp, ctypes.c_int, _c_int_p],
+    "stk_get_scaling": [_vp, _c_dbl_p],
     "stk_launch_count": [_vp, _c_i64_p],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
@@ -326,6 +331,39 @@ class Context:
 
     def set_solver(self, method, restart=30):
         self._check(self.lib.stk_set_solver(self.h, method, restart), "stk_set_solver")
+
+    def set_phases(self, chi, mu_phase, scale=True):
+        chi = np.ascontiguousarray(chi, dtype=np.int32)
+        mu = np.ascontiguousarray(mu_phase, dtype=np.float64)
+        self._check(self.lib.stk_set_phases(self.h, len(mu), chi.ctypes.data_as(_c_int_p),
+                                            mu.ctypes.data_as(_c_dbl_p), 1 if scale else 0), "stk_set_phases")
+
+    def get_interface(self, npts, d):
+        cm = np.zeros(npts, dtype=np.int32)
+        cp = np.zeros(npts, dtype=np.int32)
+        nr = np.zeros((npts, d))
+        self._check(self.lib.stk_get_interface(self.h, cm.ctypes.data_as(_c_int_p), cp.ctypes.data_as(_c_int_p),
+                                               nr.ctypes.data_as(_c_dbl_p)), "stk_get_interface")
+        return cm, cp, nr
+
+    def assemble_rhs2(self, f_vol, bdata, idata, ne, nb):
+        b = np.zeros((ne, nb))
+        f = _dbl(f_vol)
+        bd = _dbl(bdata) if bdata is not None else (None, None)
+        idd = _dbl(idata) if idata is not None else (None, None)
+        self._check(self.lib.stk_assemble_rhs2(self.h, f[0], bd[0], idd[0], b.ctypes.data_as(_c_dbl_p)),
+                    "stk_assemble_rhs2")
+        return b
+
+    def get_colours(self, level, ne):
+        out = np.zeros(ne, dtype=np.int32)
+        self._check(self.lib.stk_get_colours(self.h, level, out.ctypes.data_as(_c_int_p)), "stk_get_colours")
+        return out
+
+    def get_scaling(self, ne, nb):
+        out = np.zeros((ne, nb))
+        self._check(self.lib.stk_get_scaling(self.h, out.ctypes.data_as(_c_dbl_p)), "stk_get_scaling")
+        return out
 
     def launch_count(self):
         n = ctypes.c_int64()

@@ -24,6 +24,11 @@ class StokesMG:
                                prob.mu(xb) if len(xb) else np.zeros(0))
         if prob.delta is not None:
             self.ctx.set_density(prob.rho(xv), prob.rho(xi) if len(xi) else np.zeros(0), prob.delta)
+        self.chi = None
+        if prob.phase is not None:
+            centres = xv.reshape(prob.n_elements, -1, d).mean(axis=1)
+            self.chi = np.asarray(prob.phase(centres), dtype=np.int32)
+            self.ctx.set_phases(self.chi, prob.mu_phase, scale=prob.scale_mu)
         nu1, nu2 = (prob.nu1, prob.nu2) if nu is None else nu
         self.ctx.set_cycle(nu1, nu2, precision)
         if setup:
@@ -52,7 +57,26 @@ class StokesMG:
                         nvec = np.zeros(d)
                         nvec[k] = s
                         bdata[m] = ex.stress(xb[m], nvec)
-        return self.ctx.assemble_rhs(f_vol, bdata, prob.n_elements, prob.nb)
+        if self.chi is None:
+            return self.ctx.assemble_rhs(f_vol, bdata, prob.n_elements, prob.nb)
+        cm, cp, nrm_i = self.ctx.get_interface(len(xi), d)
+        idata = np.zeros((len(xi), 2 * d))
+        m = cm > 0
+        if m.any():
+            for k in range(d):
+                for sg in (-1.0, 1.0):
+                    sel = m & (nrm_i[:, k] == sg)
+                    if sel.any():
+                        nvec = np.zeros(d)
+                        nvec[k] = sg
+                        g, h = ex.jumps(xi[sel], nvec, cm[sel], cp[sel])
+                        idata[sel, :d] = g
+                        idata[sel, d:] = h
+        return self.ctx.assemble_rhs2(f_vol, bdata, idata, prob.n_elements, prob.nb)
+
+    def scaling(self):
+        """Level-0 diagonal D of the sqrt(mu) scaling (ones without it)."""
+        return self.ctx.get_scaling(self.prob.n_elements, self.prob.nb)
 
     def close(self):
         self.ctx.close()
