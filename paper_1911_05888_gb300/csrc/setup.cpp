@@ -362,6 +362,7 @@ void build_pattern(int d, int p, int gamma, bool multiphase, Pattern& pat) {
   auto offset_slot = [&](int o0, int o1, int o2) {
     for (int i = 0; i < pat.NO; ++i)
       if (pat.off[i][0] == o0 && pat.off[i][1] == o1 && pat.off[i][2] == o2) return i;
+    if (pat.NO >= kMaxOffsets) return 0;
     pat.off[pat.NO][0] = o0;
     pat.off[pat.NO][1] = o1;
     pat.off[pat.NO][2] = o2;
@@ -372,6 +373,7 @@ void build_pattern(int d, int p, int gamma, bool multiphase, Pattern& pat) {
     o[k] = sgn;
   };
   auto add = [&](int rv, int cv, const int* o) {
+    if (pat.T >= kMaxTasks) return;
     int t = pat.T++;
     pat.task_rv[t] = rv;
     pat.task_cv[t] = cv;

@@ -9,9 +9,9 @@
 
 namespace stk {
 
-constexpr int kMaxTasks = 64;
-constexpr int kMaxGather = 64;
-constexpr int kMaxOffsets = 32;
+constexpr int kMaxTasks = 112;
+constexpr int kMaxGather = 112;
+constexpr int kMaxOffsets = 48;
 
 // Coupling pattern of one element with its neighbours (identical on every
 // level for given d and gamma).  A "task" is one s x s sub-block of the
