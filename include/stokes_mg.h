@@ -197,8 +197,9 @@ int stk_residual(stk_ctx* ctx, const double* x_dev, const double* b_dev, double*
                  double* norm_out, void* stream);
 
 /* One colour step of the block Gauss-Seidel smoother on level `level` in
- * FP64: every element i of colour c (parity colouring sum_k (i_k mod 2) 2^k)
- * gets x_i = A_ii^{-1} (b_i - sum_{j != i} A_ij x_j) (Section 3). */
+ * FP64: every element i of colour c (parity colouring sum_k (i_k mod 2) 2^k,
+ * or the greedy colouring with phases; stk_get_colours) gets
+ * x_i = A_ii^{-1} (b_i - sum_{j != i} A_ij x_j) (Section 3). */
 int stk_gs_colour(stk_ctx* ctx, int level, int colour, double* x_dev, const double* b_dev,
                   void* stream);
 

@@ -1091,7 +1091,7 @@ int stk_gs_colour(stk_ctx* c, int level, int colour, double* x, const double* b,
   return guard(c, [&]() -> int {
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
     if (level < 0 || level >= nlevels(*c) - 1) return fail(c, STK_ERR_INVALID_ARG, "bad level");
-    if (colour < 0 || colour >= (1 << c->d) || !x || !b) return fail(c, STK_ERR_INVALID_ARG, "bad colour");
+    if (colour < 0 || colour >= c->dev[level].ncolour || !x || !b) return fail(c, STK_ERR_INVALID_ARG, "bad colour");
     DevLevel& D = c->dev[level];
     int n = D.cstart[colour + 1] - D.cstart[colour];
     ck(run_element(*c, level, STK_FP64, MODE_GS, D.cstart[colour], n, D.inv[0], b, x, nullptr,
@@ -1111,7 +1111,7 @@ int stk_gs_colour_ex(stk_ctx* c, int level, int colour, int precision, void* x, 
   return guard(c, [&]() -> int {
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
     if (level < 0 || level >= nlevels(*c) - 1) return fail(c, STK_ERR_INVALID_ARG, "bad level");
-    if (colour < 0 || colour >= (1 << c->d) || !x || !b) return fail(c, STK_ERR_INVALID_ARG, "bad colour");
+    if (colour < 0 || colour >= c->dev[level].ncolour || !x || !b) return fail(c, STK_ERR_INVALID_ARG, "bad colour");
     if (!have_precision(*c, precision)) return fail(c, STK_ERR_INVALID_ARG, "precision not set up");
     DevLevel& D = c->dev[level];
     int n = D.cstart[colour + 1] - D.cstart[colour];
