@@ -318,9 +318,10 @@ int stk_learn_grad(stk_ctx* ctx, int64_t state, float* grad, double* loss_out);
  * as the right preconditioner -- Section 3 uses the V-cycle as a GMRES
  * preconditioner; the flexible form keeps the FP64 residual exact when the
  * cycle runs in FP32/BF16.  method 2 = the same flexible GMRES with the
- * Krylov matvec in the cycle's precision (FP32/BF16 blocks), trusted for a
- * 1e-5 reduction per restart cycle, inside FP64 refinement: each restart
- * recomputes the residual in FP64.  restart in 1..100.
+ * Krylov matvec on FP32 blocks and vectors (also when the cycle runs in BF16),
+ * trusted for a 1e-5 reduction per restart cycle, inside FP64 refinement:
+ * each restart recomputes the residual in FP64.  With an FP64 cycle method 2
+ * equals method 1.  restart in 1..100.
  */
 int stk_set_solver(stk_ctx* ctx, int method, int restart);
 

@@ -267,6 +267,18 @@ void pack_level(Ctx& c, int l, cudaStream_t st) {
         ck(launch_to_bf16((int64_t)cnt[i], *dst[i], (const double*)src[i], st), "convert bf16");
     }
   }
+  // With BF16 smoother records the refined Krylov matvec still runs on FP32
+  // couplings and diagonal blocks: its Arnoldi relation needs u * cond(A) < 1,
+  // which BF16's unit roundoff (2^-8) does not give on these operators.
+  if (l == 0 && c.precision == STK_BF16) {
+    void* src[2] = {D.cpl[0], D.dia[0]};
+    size_t cnt[2] = {cpl_n, mat_n};
+    void** dst[2] = {&D.cpl[STK_FP32], &D.dia[STK_FP32]};
+    for (int i = 0; i < 2; ++i) {
+      *dst[i] = dalloc(c, cnt[i] * 4);
+      ck(launch_convert(0, 1, (int64_t)cnt[i], *dst[i], src[i], st), "convert fp32");
+    }
+  }
   (void)st;
 }
 
@@ -738,10 +750,10 @@ int fgmres(Ctx& c, double* x, const double* b, double rtol, int maxit, double* h
       double* zj = c.kZ + (size_t)j * n0;
       precondition(c, vj, zj, st);
       // w = A z_j, computed as -(0 - A z_j) by the residual kernel; in the
-      // refined variant with the blocks of the cycle's precision.
+      // refined variant with FP32 blocks (FP32 vectors, FP32 accumulation).
       if (c.solver == 2 && c.precision != STK_FP64) {
         ck(launch_convert(0, 1, n0, c.kz32, zj, st), "convert");
-        ck(run_element(c, 0, c.precision, MODE_RESID, 0, c.dev[0].ne, c.dev[0].dia[c.precision], c.kzero32, c.kz32,
+        ck(run_element(c, 0, STK_FP32, MODE_RESID, 0, c.dev[0].ne, c.dev[0].dia[STK_FP32], c.kzero32, c.kz32,
                        c.kw32, st),
            "matvec32");
         ck(launch_convert(1, 0, n0, c.kw, c.kw32, st), "convert");

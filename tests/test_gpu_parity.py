@@ -373,8 +373,8 @@ def test_learned_smoother_solve_converges_and_is_judged():
 @pytest.mark.parametrize("precision", [native.FP32, native.BF16])
 @pytest.mark.parametrize("name", ["stress16p3", "3d-unsteady-p2"])
 def test_fgmres_refined_variant(name, precision):
-    """Krylov matvec in the cycle's precision with FP64 restarts still reaches
-    1e-10 on the FP64 residual and the FP64 solution."""
+    """Krylov matvec on FP32 blocks (FP32 or BF16 cycle) with FP64 restarts
+    still reaches 1e-10 on the FP64 residual and the FP64 solution."""
     prob, gpu64, _ = get(name)
     _, gpu, _ = get(name, precision)
     b = dev(gpu64.rhs().ravel())
