@@ -340,6 +340,17 @@ int stk_set_solver(stk_ctx* ctx, int method, int restart);
  */
 int stk_set_tuning(stk_ctx* ctx, int variant, int precision, int ctas_per_sm, int stages);
 
+/*
+ * Element-kernel launches over at most max_positions elements (the colour
+ * steps and residuals of coarse levels) use one CTA of 256 threads per
+ * element instead of the configured variant: with few elements per launch
+ * the time is one element's load latency, which a whole CTA shortens by
+ * issuing all of the element's record loads at once.  Same arithmetic per
+ * row (FP32/FP64 sums in a different association order).  0 disables it;
+ * default 1024.  Errors: STK_ERR_INVALID_ARG for a negative value.
+ */
+int stk_set_wide_launch(stk_ctx* ctx, int max_positions);
+
 /* Number of kernel launches the library enqueued since the context was
  * created (all of them are this library's own kernels). */
 int stk_launch_count(stk_ctx* ctx, int64_t* count);

@@ -72,6 +72,9 @@ cudaError_t launch_target(int ne, int nb, int ldt, const float* xs, const float*
                           cudaStream_t st);
 cudaError_t launch_scale_f(int64_t n, float a, const float* x, float* y, cudaStream_t st);
 cudaError_t launch_scale_by_norm(int64_t n, const double* sums, float* g, cudaStream_t st);
+cudaError_t launch_element_wide(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
+                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                cudaStream_t st);
 cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
                                 int ctas, cudaStream_t st);
@@ -162,12 +165,17 @@ int colour_of(const Ctx& c, const int* n, int64_t e) {
   return col;
 }
 
-// One element-kernel launch (colour step or residual) on level l with the
-// configured variant; the pipelined variant falls back to direct loads when
-// its records do not fit in shared memory.
+// One element-kernel launch (colour step or residual) on level l: launches of
+// few elements (npos <= wide_max) take the one-CTA-per-element latency
+// variant, the others the configured variant; the pipelined variant falls
+// back to direct loads when its records do not fit in shared memory.
 cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, const void* mat, const void* b,
                         void* x, void* r, cudaStream_t st) {
   DevLevel& D = c.dev[l];
+  if (npos <= c.wide_max) {
+    cudaError_t e = launch_element_wide(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r, st);
+    if (e != cudaErrorInvalidValue) return e;
+  }
   if (c.variant == 2) {
     cudaError_t e = launch_element_warp(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
                                         c.warp_ctas[prec], st);
@@ -1280,6 +1288,20 @@ int stk_set_tuning(stk_ctx* c, int variant, int precision, int ctas_per_sm, int 
     } else if (c->ready) {
       pipe_default_shape(c->pat, precision, &c->pipe_ctas[precision], &c->pipe_stages[precision]);
     }
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_x = c->graph_b = nullptr;
+    if (c->cycle_graph) cudaGraphExecDestroy(c->cycle_graph);
+    c->cycle_graph = nullptr;
+    c->cycle_graph_prec = -1;
+    return STK_OK;
+  });
+}
+
+int stk_set_wide_launch(stk_ctx* c, int max_positions) {
+  return guard(c, [&]() -> int {
+    if (max_positions < 0) return fail(c, STK_ERR_INVALID_ARG, "max_positions must be >= 0");
+    c->wide_max = max_positions;
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
     c->graph_x = c->graph_b = nullptr;

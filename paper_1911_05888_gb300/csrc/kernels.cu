@@ -33,6 +33,11 @@ template <> struct StorageTraits<double> {
     w[0] = v.x;
     w[1] = v.y;
   }
+  __device__ static inline void load_keep(const double* p, double* w) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    w[0] = v.x;
+    w[1] = v.y;
+  }
   __device__ static inline void load_shared(const double* p, double* w) {
     double2 v = *reinterpret_cast<const double2*>(p);
     w[0] = v.x;
@@ -44,6 +49,13 @@ template <> struct StorageTraits<float> {
   static constexpr int V = 4;
   __device__ static inline void load(const float* p, float* w) {
     float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = v.z;
+    w[3] = v.w;
+  }
+  __device__ static inline void load_keep(const float* p, float* w) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
     w[0] = v.x;
     w[1] = v.y;
     w[2] = v.z;
@@ -62,6 +74,15 @@ template <> struct StorageTraits<__nv_bfloat16> {
   static constexpr int V = 8;
   __device__ static inline void load(const __nv_bfloat16* p, float* w) {
     uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+    uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      w[2 * i] = __uint_as_float(u[i] << 16);
+      w[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+    }
+  }
+  __device__ static inline void load_keep(const __nv_bfloat16* p, float* w) {
+    uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
     uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -538,6 +559,144 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
   }
 }
 
+// ---- latency variant for launches with few elements ---------------------------
+// On coarse levels a colour holds a handful of elements, so the time of a
+// launch is the latency of one element, not bandwidth.  Here one CTA of
+// kWideNT threads owns one element and issues all of its loads in a few
+// dependent rounds: neighbour indices, b and x_i first; then the gather;
+// then every (task-row vector, column group) pair of the coupling record at
+// once (the S columns split into CGc groups), then every (row vector, column
+// group) pair of the dense block.  Records are read with L2-keeping loads:
+// a coarse level's blocks are re-read by each of its sweeps and fit in L2.
+constexpr int kWideNT = 256;
+
+struct WideGeom {
+  int CGc, KC;   // coupling column groups and columns per group
+  int NCG, CW;   // dense column groups and columns per group
+  int XS;        // gathered slot stride
+  size_t words;  // accumulator words of shared memory (after the index block)
+};
+
+template <typename TS>
+__host__ __device__ inline WideGeom wide_geometry(const Pattern& pat) {
+  constexpr int V = StorageTraits<TS>::V;
+  WideGeom g;
+  const int nvr = pat.TRP / V;
+  g.CGc = nvr > 0 ? kWideNT / nvr : 1;
+  if (g.CGc < 1) g.CGc = 1;
+  if (g.CGc > pat.s) g.CGc = pat.s;
+  g.KC = (pat.s + g.CGc - 1) / g.CGc;
+  const int NRV = pat.NBP / V;
+  g.NCG = kWideNT / NRV;
+  if (g.NCG < 1) g.NCG = 1;
+  if (g.NCG > pat.nb) g.NCG = pat.nb;
+  g.CW = (pat.nb + g.NCG - 1) / g.NCG;
+  g.XS = pat.s + 1;
+  g.words = (size_t)pat.NG * g.XS + (size_t)g.CGc * pat.TRP + 2 * (size_t)pat.NBP + (size_t)g.NCG * pat.NBP;
+  return g;
+}
+
+template <typename TS, typename TX, int S>
+__global__ void __launch_bounds__(kWideNT) element_wide_kernel(const __grid_constant__ Pattern pat,
+                                                               const WideGeom wg, int mode, int pos0, int npos,
+                                                               const int* __restrict__ perm,
+                                                               const int* __restrict__ nbr,
+                                                               const TS* __restrict__ cpl,
+                                                               const TS* __restrict__ mat,
+                                                               const TX* __restrict__ b, TX* x, TX* rout) {
+  using Tr = StorageTraits<TS>;
+  using TA = typename Tr::Acc;
+  constexpr int V = Tr::V;
+  const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
+  const int NRV = NBP / V, nvr = TRP / V;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* nbs = reinterpret_cast<int*>(smem_raw);   // kMaxOffsets neighbour indices
+  TA* Xs = reinterpret_cast<TA*>(smem_raw + kMaxOffsets * sizeof(int));
+  TA* part = Xs + pat.NG * wg.XS;
+  TA* g = part + wg.CGc * TRP;
+  TA* xi = g + NBP;
+  TA* part2 = xi + NBP;
+
+  const int tid = threadIdx.x;
+  for (int pos = pos0 + blockIdx.x; pos < pos0 + npos; pos += gridDim.x) {
+    const int e = perm[pos];
+    for (int i = tid; i < pat.NO; i += kWideNT) nbs[i] = nbr[(size_t)pos * pat.NO + i];
+    for (int i = tid; i < nb; i += kWideNT) {
+      g[i] = (TA)b[(size_t)e * nb + i];
+      if (mode == MODE_RESID) xi[i] = (TA)x[(size_t)e * nb + i];
+    }
+    __syncthreads();
+    for (int i = tid; i < pat.NG * S; i += kWideNT) {
+      const int gi = i / S, ci = i - gi * S;
+      const int j = nbs[pat.g_o[gi]];
+      Xs[gi * wg.XS + ci] = (j >= 0) ? (TA)x[(size_t)j * nb + pat.g_cv[gi] * S + ci] : (TA)0;
+    }
+    __syncthreads();
+    const TS* rec = cpl + (size_t)pos * S * TRP;
+    for (int u = tid; u < nvr * wg.CGc; u += kWideNT) {
+      const int tv = u % nvr, cg = u / nvr;
+      const int c0 = cg * wg.KC, c1 = min(S, c0 + wg.KC);
+      const int tr0 = tv * V;
+      const TA* xp[V];
+      TA acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int tr = tr0 + j;
+        xp[j] = (tr < TR) ? Xs + pat.task_g[tr / S] * wg.XS : Xs;
+        acc[j] = 0;
+      }
+#pragma unroll 8
+      for (int ci = c0; ci < c1; ++ci) {
+        TA w[V];
+        Tr::load_keep(rec + (size_t)ci * TRP + tr0, w);
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = fma(w[j], xp[j][ci], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) part[cg * TRP + tr0 + j] = acc[j];
+    }
+    __syncthreads();
+    for (int r = tid; r < nb; r += kWideNT) {
+      const int rv = r / S, rr = r - rv * S;
+      TA sum = 0;
+      for (int cg = 0; cg < wg.CGc; ++cg)
+        for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[cg * TRP + t * S + rr];
+      g[r] = g[r] - sum;
+    }
+    __syncthreads();
+    const TS* mrec = mat + (size_t)pos * nb * NBP;
+    const TA* vin = (mode == MODE_GS) ? g : xi;
+    for (int u = tid; u < NRV * wg.NCG; u += kWideNT) {
+      const int rvv = u % NRV, cg = u / NRV;
+      const int c0 = cg * wg.CW, c1 = min(nb, c0 + wg.CW);
+      TA acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) acc[j] = 0;
+#pragma unroll 4
+      for (int ci = c0; ci < c1; ++ci) {
+        TA w[V];
+        Tr::load_keep(mrec + (size_t)ci * NBP + rvv * V, w);
+        const TA v = vin[ci];
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = fma(w[j], v, acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) part2[cg * NBP + rvv * V + j] = acc[j];
+    }
+    __syncthreads();
+    for (int r = tid; r < nb; r += kWideNT) {
+      TA sum = 0;
+      for (int cg = 0; cg < wg.NCG; ++cg) sum += part2[cg * NBP + r];
+      if (mode == MODE_GS)
+        x[(size_t)e * nb + r] = (TX)sum;
+      else
+        rout[(size_t)e * nb + r] = (TX)(g[r] - sum);
+    }
+    __syncthreads();
+  }
+}
+
 template <typename TS>
 static size_t element_smem(const Pattern& pat) {
   using TA = typename StorageTraits<TS>::Acc;
@@ -823,6 +982,67 @@ cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int p
   }
 }
 
+template <typename TS, typename TX, int S>
+static cudaError_t launch_wide_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
+                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x,
+                                 void* r, cudaStream_t st) {
+  if (npos <= 0) return cudaSuccess;
+  const WideGeom wg = wide_geometry<TS>(pat);
+  size_t smem = kMaxOffsets * sizeof(int) + wg.words * sizeof(typename StorageTraits<TS>::Acc);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  int grid = std::min(npos, num_sms() * (2048 / kWideNT));
+  element_wide_kernel<TS, TX, S><<<grid, kWideNT, smem, st>>>(pat, wg, mode, pos0, npos, perm, nbr,
+                                                             (const TS*)cpl, (const TS*)mat, (const TX*)b,
+                                                             (TX*)x, (TX*)r);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TX, int S>
+static void prepare_wide_s() {
+  cudaFuncSetAttribute(element_wide_kernel<TS, TX, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+}
+
+template <typename TS, typename TX>
+static cudaError_t launch_wide_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
+                                 const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                 cudaStream_t st) {
+#define STK_WIDE_CASE(SV) \
+  case SV: return launch_wide_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+  switch (pat.s) {
+    STK_WIDE_CASE(4)
+    STK_WIDE_CASE(8)
+    STK_WIDE_CASE(9)
+    STK_WIDE_CASE(16)
+    STK_WIDE_CASE(25)
+    STK_WIDE_CASE(27)
+    default: return cudaErrorInvalidValue;
+  }
+#undef STK_WIDE_CASE
+}
+
+template <typename TS, typename TX>
+static void prepare_wide_t() {
+  prepare_wide_s<TS, TX, 4>();
+  prepare_wide_s<TS, TX, 8>();
+  prepare_wide_s<TS, TX, 9>();
+  prepare_wide_s<TS, TX, 16>();
+  prepare_wide_s<TS, TX, 25>();
+  prepare_wide_s<TS, TX, 27>();
+}
+
+// One CTA per element (latency variant); cudaErrorInvalidValue when the
+// geometry does not fit in shared memory.
+cudaError_t launch_element_wide(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
+                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                cudaStream_t st) {
+  switch (storage) {
+    case 0: return launch_wide_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 1: return launch_wide_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 2: return launch_wide_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Raise the shared-memory limit of the pipelined kernels (call outside any
 // stream capture, once per process and device).
 void prepare_pipe_kernels() {
@@ -832,6 +1052,9 @@ void prepare_pipe_kernels() {
   prepare_warp_t<double, double>();
   prepare_warp_t<float, float>();
   prepare_warp_t<__nv_bfloat16, float>();
+  prepare_wide_t<double, double>();
+  prepare_wide_t<float, float>();
+  prepare_wide_t<__nv_bfloat16, float>();
 }
 
 // Default pipeline shape for a record size: CTAs per SM and ring depth.

@@ -135,6 +135,8 @@ struct Ctx {
   int variant = 2;
   int pipe_ctas[3] = {0, 0, 0}, pipe_stages[3] = {0, 0, 0};
   int warp_ctas[3] = {4, 4, 4};   // CTAs (of 8 warps) per SM for the warp-per-element kernel
+  // launches of at most this many elements use one CTA per element (latency variant), whatever the variant
+  int wide_max = 1024;
   int* dev_err = nullptr;     // raised by a kernel whose bounded wait expired
   // several right-hand sides (interleaved; nr = 4 or 8 once allocated)
   int mr_nr = 0;

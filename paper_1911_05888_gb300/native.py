@@ -68,6 +68,7 @@ SIGNATURES = {
     "stk_solve_multi": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_int_p,
                         _c_dbl_p, _vp],
     "stk_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "stk_set_wide_launch": [_vp, ctypes.c_int],
     "stk_set_phases": [_vp, ctypes.c_int, _c_int_p, _c_dbl_p, ctypes.c_int],
     "stk_get_interface": [_vp, _c_int_p, _c_int_p, _c_dbl_p],
     "stk_assemble_rhs2": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p],
@@ -328,6 +329,9 @@ class Context:
 
     def set_tuning(self, variant, precision, ctas_per_sm=0, stages=0):
         self._check(self.lib.stk_set_tuning(self.h, variant, precision, ctas_per_sm, stages), "stk_set_tuning")
+
+    def set_wide_launch(self, max_positions):
+        self._check(self.lib.stk_set_wide_launch(self.h, max_positions), "stk_set_wide_launch")
 
     def set_solver(self, method, restart=30):
         self._check(self.lib.stk_set_solver(self.h, method, restart), "stk_set_solver")

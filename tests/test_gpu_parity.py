@@ -245,13 +245,19 @@ def test_fgmres_solve(name, precision):
         assert it <= (len(ho) - 1) + 3
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, "wide"])
 @pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-mixed-p1"])
 def test_kernel_variants_agree(name, variant):
     """All element-kernel variants (direct loads, bulk-copy ring, warp per
-    element) give the oracle's colour step and residual in FP64."""
+    element, and the one-CTA-per-element latency variant of small launches)
+    give the oracle's colour step and residual in FP64."""
     prob, gpu, orc = get(name)
-    gpu.ctx.set_tuning(variant, native.FP64)
+    if variant == "wide":
+        gpu.ctx.set_tuning(2, native.FP64)
+        gpu.ctx.set_wide_launch(1 << 30)
+    else:
+        gpu.ctx.set_tuning(variant, native.FP64)
+        gpu.ctx.set_wide_launch(0)
     try:
         rng = np.random.default_rng(13)
         x0 = rng.uniform(-1, 1, prob.n_dofs)
@@ -268,6 +274,7 @@ def test_kernel_variants_agree(name, variant):
         assert rel(r.cpu().numpy(), orc.residual(0, xo, b)) <= 1e-12
     finally:
         gpu.ctx.set_tuning(2, native.FP64)
+        gpu.ctx.set_wide_launch(1024)
 
 
 @pytest.mark.parametrize("nrhs", [3, 8])
