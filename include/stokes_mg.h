@@ -203,7 +203,7 @@ int stk_residual(stk_ctx* ctx, const double* x_dev, const double* b_dev, double*
 int stk_gs_colour(stk_ctx* ctx, int level, int colour, double* x_dev, const double* b_dev,
                   void* stream);
 
-/* The colour step of stk_gs_colour and the residual of Algorithm 1 line 5
+/* The colour step of stk_gs_colour and the residual of Algorithm 1
  * on any smoothing level with the blocks stored in `precision`: STK_FP64
  * (x, b, r are double) or the precision given to stk_set_cycle before
  * stk_setup (x, b, r are float, accumulation in FP32).  These run the same
@@ -217,7 +217,7 @@ int stk_residual_ex(stk_ctx* ctx, int level, int precision, const void* x_dev, c
 int stk_vcycle(stk_ctx* ctx, double* x_dev, const double* b_dev, void* stream);
 
 /* Restriction r_c = (I_2h^h)^T r (level -> level+1) and prolongation
- * x += I_2h^h x_c (level+1 -> level), FP64 (Algorithm 1 lines 5 and 7). */
+ * x += I_2h^h x_c (level+1 -> level), FP64 (the transfers of Algorithm 1). */
 int stk_restrict(stk_ctx* ctx, int level, const double* r_dev, double* rc_dev, void* stream);
 int stk_prolong(stk_ctx* ctx, int level, const double* xc_dev, double* x_dev, void* stream);
 /* Bottom solve x = A_c^+ b on the last level (FP64). */

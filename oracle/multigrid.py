@@ -143,7 +143,7 @@ class Multigrid:
         return b - self.levels[l].A @ x
 
     def restrict(self, l, r):
-        """r_2h = (I_2h^h)^T r_h (Algorithm 1, line 5)."""
+        """r_2h = (I_2h^h)^T r_h, the coarse right-hand side of Algorithm 1."""
         return self.I[l].T @ r
 
     def prolong(self, l, xc):

@@ -2,8 +2,8 @@
 //
 // element_kernel: one colour step of the block Gauss-Seidel smoother
 //   x_i = A_ii^{-1} (b_i - sum_{j != i} A_ij x_j)            (Section 3)
-// or the residual r_i = b_i - sum_{j != i} A_ij x_j - A_ii x_i (Algorithm 1,
-// line 5), over a contiguous range of element "positions" (elements stored
+// or the residual r_i = b_i - sum_{j != i} A_ij x_j - A_ii x_i (Algorithm 1),
+// over a contiguous range of element "positions" (elements stored
 // colour-major so that one colour is one contiguous stream of records).
 //
 // Per element the kernel streams two records from HBM with 16-byte

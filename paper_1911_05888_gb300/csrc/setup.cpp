@@ -815,7 +815,7 @@ static void coarsen_level(const Ctx& c, const std::vector<double>& Pch, const Ho
         for (int k = 0; k < d; ++k) fi[k] = 2 * I[k] + ((ch >> k) & 1);
         int64_t f = element_of(F.n, d, fi);
         const double* Pf = &Pch[(size_t)ch * ss];
-        // Mass-type blocks: M_2h = I^T M I (Algorithm 2 lines 1-2, Algorithm 3 line 3).
+        // Mass-type blocks: M_2h = I^T M I (Algorithms 2 and 3).
         triple_acc(s, 1.0, Pf, &F.M[(size_t)f * ss], Pf, &Cl.M[(size_t)C * ss], tmp);
         triple_acc(s, 1.0, Pf, &F.Mmu[(size_t)f * ss], Pf, &Cl.Mmu[(size_t)C * ss], tmp);
         if (unsteady)
@@ -840,7 +840,8 @@ static void coarsen_level(const Ctx& c, const std::vector<double>& Pch, const Ho
           int csl = 0;
           for (int kk = 0; kk < d; ++kk)
             if (co[kk] != 0) csl = co[kk] < 0 ? slot_minus(kk) : slot_plus(kk);
-          // Algorithm 2 line 5 (1/2) and line 6 (x2); Algorithm 3 lines 7-8.
+          // Penalty coarsening: velocity penalty x1/2 and pressure penalty x2 (Algorithm 2);
+          // E_mu x2 and E_rho x1/2 (Algorithm 3).
           triple_acc(s, 0.5, Pf, &F.Et[((size_t)f * nsl + sl) * ss], Pg,
                      &Cl.Et[((size_t)C * nsl + csl) * ss], tmp);
           if (unsteady) {
@@ -854,7 +855,7 @@ static void coarsen_level(const Ctx& c, const std::vector<double>& Pch, const Ho
           }
         }
       }
-      // G_2h = M_2h^{-1} I^T M_h G_h I (Algorithm 2 line 3).
+      // G_2h = M_2h^{-1} I^T M_h G_h I (Algorithm 2).
       std::string err;
       invert_dense(s, &Cl.M[(size_t)C * ss], Minv.data());
       for (int k = 0; k < d; ++k) {
@@ -876,7 +877,7 @@ static void coarsen_level(const Ctx& c, const std::vector<double>& Pch, const Ho
               csl = (co == 0) ? 0 : (co < 0 ? 1 : 2);
               chg = ch ^ (1 << k);
             }
-            // P_f^T M_f G_f(slot) P_g  (Algorithm 2 line 3, before M_2h^{-1})
+            // P_f^T M_f G_f(slot) P_g  (Algorithm 2, before M_2h^{-1})
             std::vector<double> MG(ss, 0.0);
             gemm_acc(s, 1.0, &F.M[(size_t)f * ss], false, &F.G[(((size_t)k * nef + f) * kGS + sl) * ss], MG.data());
             triple_acc(s, 1.0, Pf, MG.data(), &Pch[(size_t)chg * ss], sum[csl].data(), tmp);
