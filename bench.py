@@ -68,6 +68,20 @@ def workload(n, p):
     return P.stress_variable_mu_2d(n=n, p=p, nu=(1, 1))
 
 
+def aggregate(dist, seconds, units, device):
+    """Whole-job figures over the ranks of a replicas run: the slowest rank's
+    time (max) and the units all ranks processed (sum).  dist is None for one
+    process."""
+    if dist is None:
+        return seconds, units
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def config(args, prob):
     return {"workload": "2d-viscous-stress-varmu-dirichlet3-stress1", "n": [args.n, args.n], "p": args.p,
             "dofs": prob.n_dofs, "nu": [args.nu, args.nu], "rtol": 1e-10,
@@ -314,10 +328,6 @@ def run_native(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         el = ev0.elapsed_time(ev1) / 1e3
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
         return el, iters, ctx.launch_count() - l0, hist
 
     if learned is not None:
@@ -334,7 +344,8 @@ def run_native(args):
         learned.update({"with": {"ms_per_solve": el / args.steps * 1e3, "iters": iters[0]},
                         "accepted_cycles": acc, "rejected_cycles": rej})
     cycles = sum(iters)
-    value = prob.n_dofs * max(1, args.nrhs) * cycles * world / el
+    el, units = aggregate(dist, el, prob.n_dofs * max(1, args.nrhs) * cycles, "cuda")
+    value = units / el
 
     # Plain FP64 on the same problem (the comparison the metric names).
     el64, it64, _, hist64 = timed(mg64.ctx, max(1, args.steps // 2), 1)
@@ -350,6 +361,8 @@ def run_native(args):
         b.copy_(bh, non_blocking=True)
         solve(mg.ctx)
         xh.copy_(x, non_blocking=True)
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -361,8 +374,9 @@ def run_native(args):
         xh.copy_(x, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    e2e = {"value": prob.n_dofs * e2e_cycles * world / e2e_s, "unit": "DOF-cycles/s",
+    e2e_s, e2e_units = aggregate(dist, e0.elapsed_time(e1) / 1e3, prob.n_dofs * max(1, args.nrhs) * e2e_cycles,
+                                 "cuda")
+    e2e = {"value": e2e_units / e2e_s, "unit": "DOF-cycles/s",
            "h2d_bytes_per_step": int(bh.numel() * 8), "d2h_bytes_per_step": int(xh.numel() * 8),
            "ms_per_solve": e2e_s / args.steps * 1e3}
 

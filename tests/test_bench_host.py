@@ -1,0 +1,51 @@
+"""Host logic of bench.py's multi-process (replicas) mode on CPU: two gloo
+ranks aggregate the slowest rank's time and the units of all ranks; under the
+reference arm only rank 0 works and prints."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank_main(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        seconds, units = bench.aggregate(dist, 1.0 + rank, 10.0 * (rank + 1), "cpu")
+        out[rank] = (seconds, units)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_aggregate_two_gloo_ranks():
+    port = 29500 + (os.getpid() % 2000)
+    with mp.Manager() as manager:
+        out = manager.dict()
+        mp.spawn(_rank_main, args=(2, port, out), nprocs=2, join=True)
+        got = dict(out)
+    # max of (1, 2) seconds, sum of (10, 20) units, on every rank
+    assert got == {0: (2.0, 30.0), 1: (2.0, 30.0)}
+
+
+def test_aggregate_single_process_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.aggregate(None, 1.5, 7, "cpu") == (1.5, 7)
+
+
+def test_reference_arm_nonzero_rank_exits_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0, p.stderr
+    assert p.stdout.strip() == ""
