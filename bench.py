@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--re", type=float, default=100.0, help="effective Reynolds number (unsteady3d)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--p", type=int, default=3)
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16", "fp16"])
     ap.add_argument("--solver", default="fgmres", choices=["fgmres", "fgmres-ir", "richardson"])
     ap.add_argument("--nu", type=int, default=3, help="pre- and post-smoothing sweeps")
     ap.add_argument("--restart", type=int, default=30)
@@ -186,13 +186,16 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # Native (GPU) arm
 # ---------------------------------------------------------------------------
-def algorithmic_bytes_gs(mg, prob, storage_bytes, vec_bytes, level_ne):
+def algorithmic_bytes_gs(mg, prob, storage_bytes, vec_bytes, level_ne, scaled=False):
     """Bytes one colour launch must move at the finest level: stored nonzero
     coupling sub-blocks and the dense inverse of every element of the colour,
-    plus b_i read and x_i written."""
+    plus b_i read and x_i written (and, for scaled FP16 records, one float
+    scale per coupling sub-block and per row of the inverse)."""
     d, s, nb = prob.d, (prob.p + 1) ** prob.d, prob.nb
     tasks = 2 * d * (d + 2) if prob.gamma == 0 else 2 * d * (2 * d + 1) + d * (d - 1)
     per_elem = (tasks * s * s + nb * nb) * storage_bytes + 2 * nb * vec_bytes
+    if scaled:
+        per_elem += (tasks + nb) * 4
     return per_elem * (level_ne // 2 ** d)
 
 
@@ -234,7 +237,7 @@ def run_profile(args):
     import torch
     from paper_1911_05888_gb300 import native
     from paper_1911_05888_gb300.solver import StokesMG
-    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16}[args.precision]
+    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16, "fp16": native.FP16}[args.precision]
     prob = workload(args.n, args.p)
     mg = StokesMG(prob, precision=prec, nu=(args.nu, args.nu))
     mg.ctx.set_solver({"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR,
@@ -272,7 +275,7 @@ def run_native(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16}[args.precision]
+    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16, "fp16": native.FP16}[args.precision]
     prob = workload(args.n, args.p)
 
     t0 = time.perf_counter()
@@ -386,9 +389,9 @@ def run_native(args):
     xv = torch.zeros(prob.n_dofs, dtype=vdt, device="cuda")
     bv = torch.ones(prob.n_dofs, dtype=vdt, device="cuda")
     t_gs = time_kernel(lambda: mg.ctx.gs_colour_ex(0, 0, prec, xv, bv, stream), 20, stream)
-    sb = {native.FP64: 8, native.FP32: 4, native.BF16: 2}[prec]
+    sb = {native.FP64: 8, native.FP32: 4, native.BF16: 2, native.FP16: 2}[prec]
     vb = 8 if prec == native.FP64 else 4
-    alg = algorithmic_bytes_gs(mg, prob, sb, vb, int(ne_levels[0]))
+    alg = algorithmic_bytes_gs(mg, prob, sb, vb, int(ne_levels[0]), scaled=prec == native.FP16)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -404,7 +407,7 @@ def run_native(args):
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     variants = {}
     names = {0: "direct", 1: "bulk_pipeline", 2: "warp_per_element"}
-    for var in (0, 1, 2):
+    for var in ((2,) if prec == native.FP16 else (0, 1, 2)):   # FP16 records: warp kernel only
         mg.ctx.set_tuning(var, prec)
         tv = time_kernel(lambda: mg.ctx.gs_colour_ex(0, 0, prec, xv, bv, stream), 20, stream)
         variants[names[var]] = {"launch_ms": round(tv * 1e3, 4), "GBps": round(alg / tv / 1e9, 1)}
@@ -425,7 +428,8 @@ def run_native(args):
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32-storage/f32-accum in f64 refinement",
-                  "bf16": "bf16-storage/f32-accum in f64 refinement"}[args.precision],
+                  "bf16": "bf16-storage/f32-accum in f64 refinement",
+                  "fp16": "f16-storage(pow2-scaled)/f32-accum in f64 refinement"}[args.precision],
         "data": "synthetic (manufactured solution, seeded)", "config": config(args, prob),
         "time_to_1e-10_ms": el / args.steps * 1e3, "iters_per_solve": iters[0],
         "final_rel_residual": final_residual(hist), "setup_s": round(setup_s, 2),
@@ -500,7 +504,7 @@ def run_unsteady(args):
     from paper_1911_05888_gb300.solver import StokesMG
     n = args.n if args.n != 256 else 48
     p = 2 if args.p == 3 else args.p
-    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16}[args.precision]
+    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16, "fp16": native.FP16}[args.precision]
     prob = P.unsteady_periodic_3d(n=n, p=p, re=args.re, t=0.0, nu=(args.nu, args.nu))
     t0 = time.perf_counter()
     mg = StokesMG(prob, precision=prec, nu=(args.nu, args.nu))
@@ -543,7 +547,8 @@ def run_unsteady(args):
     print(json.dumps({
         "metric": METRIC, "value": prob.n_dofs * cycles / el, "unit": "DOF-cycles/s", "n_gpus": 1, "steps": steps,
         "warmup": args.warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32-storage in f64", "bf16": "bf16-storage in f64"}[
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32-storage in f64", "bf16": "bf16-storage in f64",
+                                   "fp16": "f16-storage(pow2-scaled) in f64"}[
             args.precision], "data": "synthetic (manufactured time-periodic flow)",
         "config": {"workload": "3d-unsteady-standard-periodic", "n": [n] * 3, "p": p, "dofs": prob.n_dofs,
                    "re": args.re, "delta": delta, "time_steps": steps, "warm_start": True,

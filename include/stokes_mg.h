@@ -53,7 +53,7 @@ enum {
 enum { STK_BC_PERIODIC = 0, STK_BC_DIRICHLET = 1, STK_BC_STRESS = 2 };
 
 /* Storage precision of the element blocks inside the V-cycle. */
-enum { STK_FP64 = 0, STK_FP32 = 1, STK_BF16 = 2 };
+enum { STK_FP64 = 0, STK_FP32 = 1, STK_BF16 = 2, STK_FP16 = 3 };
 
 /* Point sets at which the caller samples coefficients and data. */
 enum { STK_PTS_VOLUME = 0, STK_PTS_INTERIOR_FACE = 1, STK_PTS_BOUNDARY_FACE = 2 };
@@ -123,9 +123,14 @@ int stk_set_density(stk_ctx* ctx, const double* rho_vol, const double* rho_iface
 /*
  * V-cycle options (Algorithm 1): nu1 pre- and nu2 post-smoothing sweeps of
  * the coloured block Gauss-Seidel method; precision = STK_FP64 (plain) or
- * STK_FP32 / STK_BF16 (element blocks stored in that type and accumulated
- * in FP32 inside the cycle; the outer residual and the bottom solve stay
- * FP64).
+ * STK_FP32 / STK_BF16 / STK_FP16 (element blocks stored in that type and
+ * accumulated in FP32 inside the cycle; the outer residual and the bottom
+ * solve stay FP64).  STK_FP16 blocks carry a power-of-two scale per s x s
+ * coupling sub-block and per row of A_ii^{-1} and A_ii (the group's largest
+ * magnitude scaled into [2^14, 2^15), entries rounded to nearest even from
+ * FP64), so FP16's 11-bit significand holds over the blocks' whole range.
+ * Several right-hand sides (stk_solve_multi) and element-kernel variants 0
+ * and 1 take FP64, FP32 or BF16 blocks only.  Errors: STK_ERR_INVALID_ARG.
  */
 int stk_set_cycle(stk_ctx* ctx, int nu1, int nu2, int precision);
 

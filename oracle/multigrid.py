@@ -18,6 +18,12 @@ Readings: post-smoothing visits the colours in the same ascending order; the
 snap threshold is |lambda| <= 1e-10 max|lambda|; the A_ii^{-1} applied by the
 smoother is the explicit inverse (numpy.linalg.inv); the outer iteration is
 x <- x + V(0, b - A x) until ||b - A x||_2 <= rtol ||b||_2.
+
+Low-precision storage (not in the paper; emulated here as the library stores
+it): every block of the smoother -- A_ii^{-1}, A_ii and the couplings -- is
+rounded once from FP64, and a cycle with rounded blocks also forms its
+in-cycle residual b - A x from those rounded blocks (the outer residual stays
+FP64).  Vectors and sums stay FP64 in the emulation.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -29,6 +35,36 @@ SNAP_THETA = 1e-10
 
 def round_fp32(a):
     return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def round_fp16_scaled(a, axis):
+    """Round to IEEE binary16 (round to nearest even) with one power-of-two
+    scale per group of entries, a group being the entries that share all
+    indices except those of `axis`: with 2^(e-1) <= max|a| < 2^e over the
+    group, the entries are multiplied by 2^(15-e) (largest magnitude in
+    [2^14, 2^15)), rounded, and multiplied back.  An all-zero group stays zero."""
+    a = np.asarray(a, dtype=np.float64)
+    mx = np.abs(a).max(axis=axis, keepdims=True)
+    _, e = np.frexp(mx)
+    e = np.where(mx > 0, e, 0).astype(np.float64)
+    up = np.exp2(15.0 - e)
+    return (a * up).astype(np.float16).astype(np.float64) / up
+
+
+def round_fp16_subblocks(A, s):
+    """round_fp16_scaled on a sparse matrix whose groups are its s x s
+    sub-blocks (row block i, column block j), as scipy CSR."""
+    coo = sp.coo_matrix(A)
+    nbc = A.shape[1] // s
+    key = (coo.row // s).astype(np.int64) * nbc + coo.col // s
+    uniq, inv = np.unique(key, return_inverse=True)
+    mx = np.zeros(len(uniq))
+    np.maximum.at(mx, inv, np.abs(coo.data))
+    _, e = np.frexp(mx)
+    e = np.where(mx > 0, e, 0).astype(np.float64)
+    up = np.exp2(15.0 - e)[inv]
+    data = (coo.data * up).astype(np.float16).astype(np.float64) / up
+    return sp.csr_matrix((data, (coo.row, coo.col)), shape=A.shape)
 
 
 def round_bf16(a):
@@ -62,6 +98,11 @@ class SmootherLevel:
             self.inv = round_bf16(self.inv)
             self.Aoff.data = round_bf16(self.Aoff.data)
             self.diag = round_bf16(self.diag)
+        elif storage == "fp16":
+            # one scale per row of A_ii^{-1} and of A_ii, one per s x s coupling sub-block
+            self.inv = round_fp16_scaled(self.inv, axis=2)
+            self.diag = round_fp16_scaled(self.diag, axis=2)
+            self.Aoff = round_fp16_subblocks(self.Aoff, lev.s)
         self.colour = lev.mesh.colour()
         self.ncol = int(self.colour.max()) + 1
         self.elems = [np.nonzero(self.colour == c)[0] for c in range(self.ncol)]
@@ -142,6 +183,15 @@ class Multigrid:
     def residual(self, l, x, b):
         return b - self.levels[l].A @ x
 
+    def cycle_residual(self, l, x, b):
+        """Residual inside the V-cycle: from the smoother's stored blocks
+        (rounded ones for a low-precision cycle; = residual() in FP64)."""
+        if self.storage is None:
+            return self.residual(l, x, b)
+        sm = self.sm[l]
+        y = np.einsum("eij,ej->ei", sm.diag, x.reshape(-1, sm.nb)).ravel()
+        return b - (y + sm.Aoff @ x)
+
     def restrict(self, l, r):
         """r_2h = (I_2h^h)^T r_h, the coarse right-hand side of Algorithm 1."""
         return self.I[l].T @ r
@@ -160,7 +210,7 @@ class Multigrid:
         sm = self.sm[l]
         for _ in range(nu1):
             (sm.sweep_lexicographic if lexicographic else sm.sweep)(x, b)
-        r2 = self.restrict(l, self.residual(l, x, b))
+        r2 = self.restrict(l, self.cycle_residual(l, x, b))
         x2 = np.zeros_like(r2)
         self.vcycle(x2, r2, l + 1, nu1, nu2, lexicographic)
         x += self.prolong(l, x2)

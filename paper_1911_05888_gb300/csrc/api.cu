@@ -73,11 +73,15 @@ cudaError_t launch_target(int ne, int nb, int ldt, const float* xs, const float*
 cudaError_t launch_scale_f(int64_t n, float a, const float* x, float* y, cudaStream_t st);
 cudaError_t launch_scale_by_norm(int64_t n, const double* sums, float* g, cudaStream_t st);
 cudaError_t launch_element_wide(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
-                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
+                                const void* b, void* x, void* r, cudaStream_t st);
+cudaError_t launch_to_fp16_tasks(int64_t npos, int S, int T, int TRP, void* dst, float* tsc, const double* src,
+                                 cudaStream_t st);
+cudaError_t launch_to_fp16_rows(int64_t npos, int nb, int NBP, void* dst, float* rsc, const double* src,
                                 cudaStream_t st);
 cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
-                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
-                                int ctas, cudaStream_t st);
+                                const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
+                                const void* b, void* x, void* r, int ctas, cudaStream_t st);
 void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages);
 }  // namespace stk
 
@@ -172,14 +176,19 @@ int colour_of(const Ctx& c, const int* n, int64_t e) {
 cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, const void* mat, const void* b,
                         void* x, void* r, cudaStream_t st) {
   DevLevel& D = c.dev[l];
+  // FP16 records carry scales and run on the warp and wide kernels only.
+  const bool scaled = prec == STK_FP16;
+  const float* tsc = scaled ? D.csc : nullptr;
+  const float* rsc = scaled ? (mode == MODE_GS ? D.isc : D.dsc) : nullptr;
   if (npos <= c.wide_max) {
-    cudaError_t e = launch_element_wide(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r, st);
-    if (e != cudaErrorInvalidValue) return e;
+    cudaError_t e = launch_element_wide(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
+                                        x, r, st);
+    if (e != cudaErrorInvalidValue || scaled) return e;
   }
-  if (c.variant == 2) {
-    cudaError_t e = launch_element_warp(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
-                                        c.warp_ctas[prec], st);
-    if (e != cudaErrorInvalidValue) return e;
+  if (c.variant == 2 || scaled) {
+    cudaError_t e = launch_element_warp(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
+                                        x, r, c.warp_ctas[prec], st);
+    if (e != cudaErrorInvalidValue || scaled) return e;
   }
   if (c.variant == 1) {
     cudaError_t e = launch_element_pipe(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
@@ -261,7 +270,7 @@ void pack_level(Ctx& c, int l, cudaStream_t st) {
   pack_mat(Dinv, D.inv[0]);
   pack_mat(H.D, D.dia[0]);
   // Low-precision copies (rounded once from FP64: round to nearest even).
-  if (c.precision != STK_FP64) {
+  if (c.precision == STK_FP32 || c.precision == STK_BF16) {
     int pr = c.precision;
     size_t es = (pr == STK_FP32) ? 4 : 2;
     void* src[3] = {D.cpl[0], D.inv[0], D.dia[0]};
@@ -275,10 +284,25 @@ void pack_level(Ctx& c, int l, cudaStream_t st) {
         ck(launch_to_bf16((int64_t)cnt[i], *dst[i], (const double*)src[i], st), "convert bf16");
     }
   }
-  // With BF16 smoother records the refined Krylov matvec still runs on FP32
+  // FP16 copies with power-of-two scales per coupling sub-block and per row
+  // of the dense blocks.
+  if (c.precision == STK_FP16) {
+    const int TP = (P.T + 3) / 4 * 4;
+    D.cpl[STK_FP16] = dalloc(c, cpl_n * 2);
+    D.csc = (float*)dalloc(c, (size_t)ne * TP * sizeof(float));
+    ck(launch_to_fp16_tasks(ne, s, P.T, P.TRP, D.cpl[STK_FP16], D.csc, (const double*)D.cpl[0], st),
+       "convert fp16 couplings");
+    D.inv[STK_FP16] = dalloc(c, mat_n * 2);
+    D.isc = (float*)dalloc(c, (size_t)ne * P.NBP * sizeof(float));
+    ck(launch_to_fp16_rows(ne, nb, P.NBP, D.inv[STK_FP16], D.isc, (const double*)D.inv[0], st), "convert fp16 inv");
+    D.dia[STK_FP16] = dalloc(c, mat_n * 2);
+    D.dsc = (float*)dalloc(c, (size_t)ne * P.NBP * sizeof(float));
+    ck(launch_to_fp16_rows(ne, nb, P.NBP, D.dia[STK_FP16], D.dsc, (const double*)D.dia[0], st), "convert fp16 dia");
+  }
+  // With 16-bit smoother records the refined Krylov matvec still runs on FP32
   // couplings and diagonal blocks: its Arnoldi relation needs u * cond(A) < 1,
-  // which BF16's unit roundoff (2^-8) does not give on these operators.
-  if (l == 0 && c.precision == STK_BF16) {
+  // which 16-bit unit roundoffs (2^-8, 2^-11) do not give on these operators.
+  if (l == 0 && (c.precision == STK_BF16 || c.precision == STK_FP16)) {
     void* src[2] = {D.cpl[0], D.dia[0]};
     size_t cnt[2] = {cpl_n, mat_n};
     void** dst[2] = {&D.cpl[STK_FP32], &D.dia[STK_FP32]};
@@ -984,7 +1008,7 @@ int stk_set_density(stk_ctx* c, const double* rho_vol, const double* rho_iface, 
 
 int stk_set_cycle(stk_ctx* c, int nu1, int nu2, int precision) {
   return guard(c, [&]() -> int {
-    if (nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0 || precision < 0 || precision > 2)
+    if (nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0 || precision < 0 || precision > 3)
       return fail(c, STK_ERR_INVALID_ARG, "bad cycle options");
     if (c->ready && precision != c->precision) free_device(*c);
     c->nu1 = nu1;
@@ -1123,7 +1147,7 @@ int stk_gs_colour(stk_ctx* c, int level, int colour, double* x, const double* b,
 }
 
 static bool have_precision(const Ctx& c, int precision) {
-  return precision == STK_FP64 || (precision == c.precision && precision > 0 && precision <= 2);
+  return precision == STK_FP64 || (precision == c.precision && precision > 0 && precision <= 3);
 }
 
 int stk_gs_colour_ex(stk_ctx* c, int level, int colour, int precision, void* x, const void* b,
@@ -1277,7 +1301,7 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
 
 int stk_set_tuning(stk_ctx* c, int variant, int precision, int ctas_per_sm, int stages) {
   return guard(c, [&]() -> int {
-    if (variant < 0 || variant > 2 || precision < 0 || precision > 2 || ctas_per_sm < 0 || ctas_per_sm > 32 ||
+    if (variant < 0 || variant > 2 || precision < 0 || precision > 3 || ctas_per_sm < 0 || ctas_per_sm > 32 ||
         stages < 0 || stages > 16)
       return fail(c, STK_ERR_INVALID_ARG, "bad tuning options");
     c->variant = variant;
@@ -1332,6 +1356,8 @@ int stk_solve_multi(stk_ctx* c, double* X, const double* B, int nrhs, double rto
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
     if (!X || !B || nrhs < 1 || nrhs > 8 || maxit < 0 || inner < 1 || inner > 16 || !(rtol > 0))
       return fail(c, STK_ERR_INVALID_ARG, "bad multi-rhs arguments (1 <= nrhs <= 8, 1 <= inner <= 16)");
+    if (c->precision == STK_FP16)
+      return fail(c, STK_ERR_INVALID_ARG, "several right-hand sides take FP64, FP32 or BF16 blocks");
     int nr = nrhs <= 4 ? 4 : 8;
     cudaStream_t user = (cudaStream_t)stream;
     ck(cudaStreamSynchronize(user), "sync caller stream");

@@ -15,8 +15,11 @@
 // Neighbour values are gathered once per element into shared memory; the
 // per-task partial sums are reduced per row in shared memory.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "stk_internal.h"
 
@@ -100,6 +103,35 @@ template <> struct StorageTraits<__nv_bfloat16> {
     }
   }
 };
+
+// FP16 records carry a power-of-two scale per coupling sub-block and per row
+// of the dense blocks (applied in the row sums, see element_warp_kernel).
+template <> struct StorageTraits<__half> {
+  using Acc = float;
+  static constexpr int V = 8;
+  __device__ static inline void cvt(uint4 v, float* w) {
+    uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2 h = *reinterpret_cast<const __half2*>(&u[i]);
+      float2 f = __half22float2(h);
+      w[2 * i] = f.x;
+      w[2 * i + 1] = f.y;
+    }
+  }
+  __device__ static inline void load(const __half* p, float* w) { cvt(__ldcs(reinterpret_cast<const uint4*>(p)), w); }
+  __device__ static inline void load_keep(const __half* p, float* w) {
+    cvt(__ldg(reinterpret_cast<const uint4*>(p)), w);
+  }
+  __device__ static inline void load_shared(const __half* p, float* w) {
+    cvt(*reinterpret_cast<const uint4*>(p), w);
+  }
+};
+
+template <typename TS>
+constexpr bool kScaledStorage = std::is_same<TS, __half>::value;
+
+__host__ __device__ inline int task_scale_stride(const Pattern& pat) { return (pat.T + 3) / 4 * 4; }
 
 enum { MODE_GS = 0, MODE_RESID = 1 };
 
@@ -456,6 +488,7 @@ __host__ __device__ inline WarpGeom<TS> warp_geometry(const Pattern& pat) {
   g.CW = (pat.nb + g.NCG - 1) / g.NCG;
   g.XS = pat.s + 1;
   int w = pat.NG * g.XS + pat.TRP + 2 * pat.NBP + g.NCG * pat.NBP;
+  if (kScaledStorage<TS>) w += task_scale_stride(pat);
   g.words = (w + 3) / 4 * 4;
   return g;
 }
@@ -467,12 +500,15 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
                                                                    const int* __restrict__ nbr,
                                                                    const TS* __restrict__ cpl,
                                                                    const TS* __restrict__ mat,
+                                                                   const float* __restrict__ tsc,
+                                                                   const float* __restrict__ rsc,
                                                                    const TX* __restrict__ b, TX* x, TX* rout) {
   using Tr = StorageTraits<TS>;
   using TA = typename Tr::Acc;
   constexpr int V = Tr::V;
   const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
   const int NRV = NBP / V;
+  const int TP = task_scale_stride(pat);
   const WarpGeom<TS> wg = warp_geometry<TS>(pat);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
@@ -483,6 +519,7 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
   TA* g = part + TRP;
   TA* xi = g + NBP;
   TA* part2 = xi + NBP;
+  TA* tss = part2 + wg.NCG * NBP;   // task scales (FP16 records only)
 
   const int nwarps = gridDim.x * kWarps;
   for (int pos = pos0 + blockIdx.x * kWarps + wid; pos < pos0 + npos; pos += nwarps) {
@@ -497,6 +534,8 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
       g[i] = (TA)b[(size_t)e * nb + i];
       if (mode == MODE_RESID) xi[i] = (TA)x[(size_t)e * nb + i];
     }
+    if constexpr (kScaledStorage<TS>)
+      for (int i = lane; i < pat.T; i += 32) tss[i] = tsc[(size_t)pos * TP + i];
     __syncwarp();
     const TS* rec = cpl + (size_t)pos * S * TRP;
     for (int tv = lane; tv < TRP / V; tv += 32) {
@@ -523,7 +562,11 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
     for (int r = lane; r < nb; r += 32) {
       const int rv = r / S, rr = r - rv * S;
       TA sum = 0;
-      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[t * S + rr];
+      if constexpr (kScaledStorage<TS>) {
+        for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[t * S + rr] * tss[t];
+      } else {
+        for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[t * S + rr];
+      }
       g[r] = g[r] - sum;
     }
     __syncwarp();
@@ -550,6 +593,7 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
     for (int r = lane; r < nb; r += 32) {
       TA sum = 0;
       for (int cg = 0; cg < wg.NCG; ++cg) sum += part2[cg * NBP + r];
+      if constexpr (kScaledStorage<TS>) sum *= rsc[(size_t)pos * NBP + r];
       if (mode == MODE_GS)
         x[(size_t)e * nb + r] = (TX)sum;
       else
@@ -593,6 +637,7 @@ __host__ __device__ inline WideGeom wide_geometry(const Pattern& pat) {
   g.CW = (pat.nb + g.NCG - 1) / g.NCG;
   g.XS = pat.s + 1;
   g.words = (size_t)pat.NG * g.XS + (size_t)g.CGc * pat.TRP + 2 * (size_t)pat.NBP + (size_t)g.NCG * pat.NBP;
+  if (kScaledStorage<TS>) g.words += task_scale_stride(pat);
   return g;
 }
 
@@ -603,12 +648,15 @@ __global__ void __launch_bounds__(kWideNT) element_wide_kernel(const __grid_cons
                                                                const int* __restrict__ nbr,
                                                                const TS* __restrict__ cpl,
                                                                const TS* __restrict__ mat,
+                                                               const float* __restrict__ tsc,
+                                                               const float* __restrict__ rsc,
                                                                const TX* __restrict__ b, TX* x, TX* rout) {
   using Tr = StorageTraits<TS>;
   using TA = typename Tr::Acc;
   constexpr int V = Tr::V;
   const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
   const int NRV = NBP / V, nvr = TRP / V;
+  const int TP = task_scale_stride(pat);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* nbs = reinterpret_cast<int*>(smem_raw);   // kMaxOffsets neighbour indices
@@ -617,6 +665,7 @@ __global__ void __launch_bounds__(kWideNT) element_wide_kernel(const __grid_cons
   TA* g = part + wg.CGc * TRP;
   TA* xi = g + NBP;
   TA* part2 = xi + NBP;
+  TA* tss = part2 + wg.NCG * NBP;   // task scales (FP16 records only)
 
   const int tid = threadIdx.x;
   for (int pos = pos0 + blockIdx.x; pos < pos0 + npos; pos += gridDim.x) {
@@ -626,6 +675,8 @@ __global__ void __launch_bounds__(kWideNT) element_wide_kernel(const __grid_cons
       g[i] = (TA)b[(size_t)e * nb + i];
       if (mode == MODE_RESID) xi[i] = (TA)x[(size_t)e * nb + i];
     }
+    if constexpr (kScaledStorage<TS>)
+      for (int i = tid; i < pat.T; i += kWideNT) tss[i] = tsc[(size_t)pos * TP + i];
     __syncthreads();
     for (int i = tid; i < pat.NG * S; i += kWideNT) {
       const int gi = i / S, ci = i - gi * S;
@@ -660,8 +711,12 @@ __global__ void __launch_bounds__(kWideNT) element_wide_kernel(const __grid_cons
     for (int r = tid; r < nb; r += kWideNT) {
       const int rv = r / S, rr = r - rv * S;
       TA sum = 0;
-      for (int cg = 0; cg < wg.CGc; ++cg)
-        for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[cg * TRP + t * S + rr];
+      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) {
+        TA st = 0;
+        for (int cg = 0; cg < wg.CGc; ++cg) st += part[cg * TRP + t * S + rr];
+        if constexpr (kScaledStorage<TS>) st *= tss[t];
+        sum += st;
+      }
       g[r] = g[r] - sum;
     }
     __syncthreads();
@@ -688,6 +743,7 @@ __global__ void __launch_bounds__(kWideNT) element_wide_kernel(const __grid_cons
     for (int r = tid; r < nb; r += kWideNT) {
       TA sum = 0;
       for (int cg = 0; cg < wg.NCG; ++cg) sum += part2[cg * NBP + r];
+      if constexpr (kScaledStorage<TS>) sum *= rsc[(size_t)pos * NBP + r];
       if (mode == MODE_GS)
         x[(size_t)e * nb + r] = (TX)sum;
       else
@@ -925,15 +981,16 @@ static void prepare_pipe_t() {
 
 template <typename TS, typename TX, int S>
 static cudaError_t launch_warp_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
-                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x,
-                                 void* r, int ctas, cudaStream_t st) {
+                                 const int* nbr, const void* cpl, const void* mat, const float* tsc,
+                                 const float* rsc, const void* b, void* x, void* r, int ctas, cudaStream_t st) {
   if (npos <= 0) return cudaSuccess;
   WarpGeom<TS> wg = warp_geometry<TS>(pat);
   size_t smem = (size_t)kWarps * wg.words * sizeof(typename StorageTraits<TS>::Acc);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
   int grid = std::min((npos + kWarps - 1) / kWarps, num_sms() * std::max(1, ctas));
+  if (kScaledStorage<TS> && (!tsc || !rsc)) return cudaErrorInvalidValue;
   element_warp_kernel<TS, TX, S><<<grid, 32 * kWarps, smem, st>>>(pat, mode, pos0, npos, perm, nbr,
-                                                                   (const TS*)cpl, (const TS*)mat,
+                                                                   (const TS*)cpl, (const TS*)mat, tsc, rsc,
                                                                    (const TX*)b, (TX*)x, (TX*)r);
   return cudaGetLastError();
 }
@@ -945,10 +1002,11 @@ static void prepare_warp_s() {
 
 template <typename TS, typename TX>
 static cudaError_t launch_warp_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
-                                 const void* cpl, const void* mat, const void* b, void* x, void* r, int ctas,
-                                 cudaStream_t st) {
+                                 const void* cpl, const void* mat, const float* tsc, const float* rsc, const void* b,
+                                 void* x, void* r, int ctas, cudaStream_t st) {
 #define STK_WARP_CASE(SV) \
-  case SV: return launch_warp_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, ctas, st);
+  case SV:                \
+    return launch_warp_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st);
   switch (pat.s) {
     STK_WARP_CASE(4)
     STK_WARP_CASE(8)
@@ -971,29 +1029,37 @@ static void prepare_warp_t() {
   prepare_warp_s<TS, TX, 27>();
 }
 
+// tsc / rsc: the FP16 records' task and row scales (ignored for the other storages).
 cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
-                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
-                                int ctas, cudaStream_t st) {
+                                const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
+                                const void* b, void* x, void* r, int ctas, cudaStream_t st) {
   switch (storage) {
-    case 0: return launch_warp_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, ctas, st);
-    case 1: return launch_warp_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, ctas, st);
-    case 2: return launch_warp_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, ctas, st);
+    case 0:
+      return launch_warp_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st);
+    case 1:
+      return launch_warp_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st);
+    case 2:
+      return launch_warp_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas,
+                                                  st);
+    case 3:
+      return launch_warp_t<__half, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename TS, typename TX, int S>
 static cudaError_t launch_wide_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
-                                 const int* nbr, const void* cpl, const void* mat, const void* b, void* x,
-                                 void* r, cudaStream_t st) {
+                                 const int* nbr, const void* cpl, const void* mat, const float* tsc,
+                                 const float* rsc, const void* b, void* x, void* r, cudaStream_t st) {
   if (npos <= 0) return cudaSuccess;
   const WideGeom wg = wide_geometry<TS>(pat);
   size_t smem = kMaxOffsets * sizeof(int) + wg.words * sizeof(typename StorageTraits<TS>::Acc);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
   int grid = std::min(npos, num_sms() * (2048 / kWideNT));
+  if (kScaledStorage<TS> && (!tsc || !rsc)) return cudaErrorInvalidValue;
   element_wide_kernel<TS, TX, S><<<grid, kWideNT, smem, st>>>(pat, wg, mode, pos0, npos, perm, nbr,
-                                                             (const TS*)cpl, (const TS*)mat, (const TX*)b,
-                                                             (TX*)x, (TX*)r);
+                                                             (const TS*)cpl, (const TS*)mat, tsc, rsc,
+                                                             (const TX*)b, (TX*)x, (TX*)r);
   return cudaGetLastError();
 }
 
@@ -1004,10 +1070,10 @@ static void prepare_wide_s() {
 
 template <typename TS, typename TX>
 static cudaError_t launch_wide_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
-                                 const void* cpl, const void* mat, const void* b, void* x, void* r,
-                                 cudaStream_t st) {
+                                 const void* cpl, const void* mat, const float* tsc, const float* rsc, const void* b,
+                                 void* x, void* r, cudaStream_t st) {
 #define STK_WIDE_CASE(SV) \
-  case SV: return launch_wide_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+  case SV: return launch_wide_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
   switch (pat.s) {
     STK_WIDE_CASE(4)
     STK_WIDE_CASE(8)
@@ -1033,12 +1099,14 @@ static void prepare_wide_t() {
 // One CTA per element (latency variant); cudaErrorInvalidValue when the
 // geometry does not fit in shared memory.
 cudaError_t launch_element_wide(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
-                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
-                                cudaStream_t st) {
+                                const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
+                                const void* b, void* x, void* r, cudaStream_t st) {
   switch (storage) {
-    case 0: return launch_wide_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
-    case 1: return launch_wide_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
-    case 2: return launch_wide_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 0: return launch_wide_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 1: return launch_wide_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 2:
+      return launch_wide_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 3: return launch_wide_t<__half, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1052,9 +1120,11 @@ void prepare_pipe_kernels() {
   prepare_warp_t<double, double>();
   prepare_warp_t<float, float>();
   prepare_warp_t<__nv_bfloat16, float>();
+  prepare_warp_t<__half, float>();
   prepare_wide_t<double, double>();
   prepare_wide_t<float, float>();
   prepare_wide_t<__nv_bfloat16, float>();
+  prepare_wide_t<__half, float>();
 }
 
 // Default pipeline shape for a record size: CTAs per SM and ring depth.
@@ -1150,6 +1220,81 @@ cudaError_t launch_convert(int y64, int x64, int64_t n, void* y, const void* x, 
   else if (y64) convert_kernel<double, float><<<grid, bs, 0, st>>>(n, (double*)y, (const float*)x);
   else if (x64) convert_kernel<float, double><<<grid, bs, 0, st>>>(n, (float*)y, (const double*)x);
   else convert_kernel<float, float><<<grid, bs, 0, st>>>(n, (float*)y, (const float*)x);
+  return cudaGetLastError();
+}
+
+// FP16 records with power-of-two scales.  Each group of entries (one s x s
+// coupling sub-block, or one row of a dense block) is multiplied by 2^(15-e),
+// where 2^(e-1) <= max|a| < 2^e, so that its largest magnitude lands in
+// [2^14, 2^15) and the group keeps the full FP16 precision over 29 binades
+// below it; the entries are rounded to nearest even from FP64 and the
+// inverse factor 2^(e-15) is stored as float.
+__device__ inline int fp16_group_exponent(double mx) {
+  int e = 0;
+  if (mx > 0) frexp(mx, &e);
+  return e;
+}
+
+// Coupling records [pos][c][TRP] (task t = rows t*S .. t*S+S-1): one thread
+// per (position, task); the thread of the last task also zeroes the padding
+// rows TR..TRP-1.
+__global__ void to_fp16_tasks_kernel(int64_t npos, int S, int T, int TRP, int TP, const double* __restrict__ src,
+                                     __half* __restrict__ dst, float* __restrict__ tsc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npos * TP) return;
+  const int64_t pos = i / TP;
+  const int t = (int)(i - pos * TP);
+  if (t >= T) {
+    tsc[i] = 0.f;
+    return;
+  }
+  const double* rec = src + (size_t)pos * S * TRP;
+  __half* out = dst + (size_t)pos * S * TRP;
+  double mx = 0;
+  for (int c = 0; c < S; ++c)
+    for (int a = 0; a < S; ++a) mx = fmax(mx, fabs(rec[(size_t)c * TRP + t * S + a]));
+  const int e = fp16_group_exponent(mx);
+  const double up = ldexp(1.0, 15 - e);
+  for (int c = 0; c < S; ++c)
+    for (int a = 0; a < S; ++a) out[(size_t)c * TRP + t * S + a] = __double2half(rec[(size_t)c * TRP + t * S + a] * up);
+  tsc[i] = (float)ldexp(1.0, e - 15);
+  if (t == T - 1)
+    for (int c = 0; c < S; ++c)
+      for (int r = T * S; r < TRP; ++r) out[(size_t)c * TRP + r] = __float2half(0.f);
+}
+
+// Dense blocks [pos][c][NBP] (column-major): one thread per (position, row).
+__global__ void to_fp16_rows_kernel(int64_t npos, int nb, int NBP, const double* __restrict__ src,
+                                    __half* __restrict__ dst, float* __restrict__ rsc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npos * NBP) return;
+  const int64_t pos = i / NBP;
+  const int r = (int)(i - pos * NBP);
+  const double* rec = src + (size_t)pos * nb * NBP;
+  __half* out = dst + (size_t)pos * nb * NBP;
+  double mx = 0;
+  if (r < nb)
+    for (int c = 0; c < nb; ++c) mx = fmax(mx, fabs(rec[(size_t)c * NBP + r]));
+  const int e = fp16_group_exponent(mx);
+  const double up = ldexp(1.0, 15 - e);
+  for (int c = 0; c < nb; ++c) out[(size_t)c * NBP + r] = __double2half(r < nb ? rec[(size_t)c * NBP + r] * up : 0.0);
+  rsc[i] = r < nb ? (float)ldexp(1.0, e - 15) : 0.f;
+}
+
+cudaError_t launch_to_fp16_tasks(int64_t npos, int S, int T, int TRP, void* dst, float* tsc, const double* src,
+                                 cudaStream_t st) {
+  const int TP = (T + 3) / 4 * 4;
+  int64_t n = npos * TP;
+  if (n <= 0) return cudaSuccess;
+  to_fp16_tasks_kernel<<<(n + 127) / 128, 128, 0, st>>>(npos, S, T, TRP, TP, src, (__half*)dst, tsc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_fp16_rows(int64_t npos, int nb, int NBP, void* dst, float* rsc, const double* src,
+                                cudaStream_t st) {
+  int64_t n = npos * NBP;
+  if (n <= 0) return cudaSuccess;
+  to_fp16_rows_kernel<<<(n + 127) / 128, 128, 0, st>>>(npos, nb, NBP, src, (__half*)dst, rsc);
   return cudaGetLastError();
 }
 

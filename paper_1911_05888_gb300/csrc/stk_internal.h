@@ -55,9 +55,15 @@ struct DevLevel {
   int ncolour = 0;
   int* perm = nullptr;                  // [ne] position -> element
   int* nbr = nullptr;                   // [ne][NO] per position
-  void* cpl[3] = {nullptr, nullptr, nullptr};   // per precision: [pos][s][TRP]
-  void* inv[3] = {nullptr, nullptr, nullptr};   // [pos][nb][NBP] column-major A_ii^{-1}
-  void* dia[3] = {nullptr, nullptr, nullptr};   // [pos][nb][NBP] column-major A_ii
+  // per storage precision (FP64, FP32, BF16, FP16):
+  void* cpl[4] = {nullptr, nullptr, nullptr, nullptr};   // [pos][s][TRP]
+  void* inv[4] = {nullptr, nullptr, nullptr, nullptr};   // [pos][nb][NBP] column-major A_ii^{-1}
+  void* dia[4] = {nullptr, nullptr, nullptr, nullptr};   // [pos][nb][NBP] column-major A_ii
+  // power-of-two scales of the FP16 records: per coupling task [pos][T padded to 4],
+  // per row of inv and of dia [pos][NBP]
+  float* csc = nullptr;
+  float* isc = nullptr;
+  float* dsc = nullptr;
   // cycle vectors: index 0 FP64, index 1 FP32
   void* vx[2] = {nullptr, nullptr};
   void* vb[2] = {nullptr, nullptr};
@@ -133,8 +139,8 @@ struct Ctx {
   // element-kernel variant: 0 direct loads, 1 bulk-copy pipeline, 2 warp per element (default),
   // with the pipeline shape per storage precision (CTAs per SM, ring depth)
   int variant = 2;
-  int pipe_ctas[3] = {0, 0, 0}, pipe_stages[3] = {0, 0, 0};
-  int warp_ctas[3] = {4, 4, 4};   // CTAs (of 8 warps) per SM for the warp-per-element kernel
+  int pipe_ctas[4] = {0, 0, 0, 0}, pipe_stages[4] = {0, 0, 0, 0};
+  int warp_ctas[4] = {4, 4, 4, 4};   // CTAs (of 8 warps) per SM for the warp-per-element kernel
   // launches of at most this many elements use one CTA per element (latency variant), whatever the variant
   int wide_max = 1024;
   int* dev_err = nullptr;     // raised by a kernel whose bounded wait expired

@@ -18,7 +18,7 @@ STK_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "TIMEOUT", -5: "DIVERGED",
           -6: "NOT_SETUP", -7: "CUDA"}
 BC_PERIODIC, BC_DIRICHLET, BC_STRESS = 0, 1, 2
-FP64, FP32, BF16 = 0, 1, 2
+FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 RICHARDSON, FGMRES, FGMRES_IR = 0, 1, 2
 PTS_VOLUME, PTS_INTERIOR_FACE, PTS_BOUNDARY_FACE = 0, 1, 2
 

@@ -88,20 +88,30 @@ def element_terms(gpu, i, x, b):
     return Aii, g, mag, nterms
 
 
-@pytest.mark.parametrize("precision", [native.FP64, native.FP32])
+def round_subblocks16(A, s):
+    """FP16 with one power-of-two scale per s x s sub-block (the library's
+    coupling records), via the oracle's rounding."""
+    nb = A.shape[0]
+    q = nb // s
+    B = A.reshape(q, s, q, s).transpose(0, 2, 1, 3)
+    return multigrid.round_fp16_scaled(B, axis=(2, 3)).transpose(0, 2, 1, 3).reshape(nb, nb)
+
+
+@pytest.mark.parametrize("precision", [native.FP64, native.FP32, native.FP16])
 def test_fullsize_colour_step_sampled(precision):
     """One finest-level colour step at full size, sampled elements.
-    FP32 blocks: against x_i = A_ii^{-1} (b_i - sum_j A_ij x_j) evaluated in
-    FP64 on the same FP32-rounded inputs and blocks, within gamma_n of FP32
-    arithmetic (plus one unit in the last place of each rounded inverse
-    entry, as the two FP64 inverses round independently).  FP64 blocks: the
-    new x_i solves A_ii x_i = g_i to a backward error of 1e-12."""
+    FP32 / FP16 blocks: against x_i = A_ii^{-1} (b_i - sum_j A_ij x_j)
+    evaluated in FP64 on the same FP32-rounded inputs and the same rounded
+    blocks, within gamma_n of FP32 arithmetic (plus one unit in the last place
+    of each rounded inverse entry, as the library's and numpy's FP64 inverses
+    round independently).  FP64 blocks: the new x_i solves A_ii x_i = g_i to
+    a backward error of 1e-12."""
     gpu = solver(precision)
     nb = gpu.nb
     rng = np.random.default_rng(7)
     x0 = rng.uniform(-1, 1, (N * N, nb))
     b = rng.uniform(-1, 1, (N * N, nb))
-    fp32 = precision == native.FP32
+    fp32 = precision != native.FP64
     if fp32:
         x0 = x0.astype(np.float32).astype(np.float64)
         b = b.astype(np.float32).astype(np.float64)
@@ -111,7 +121,16 @@ def test_fullsize_colour_step_sampled(precision):
     gpu.ctx.gs_colour_ex(0, 0, precision, xd, bd)
     torch.cuda.synchronize()
     xg = xd.double().cpu().numpy().reshape(N * N, nb)
-    rnd = (lambda a: a.astype(np.float32).astype(np.float64)) if fp32 else (lambda a: a)
+    if precision == native.FP32:
+        rnd = rnd_inv = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+        u_inv = U32
+    elif precision == native.FP16:
+        s = (DEG + 1) ** 2
+        rnd = lambda a: round_subblocks16(a, s)  # noqa: E731
+        rnd_inv = lambda a: multigrid.round_fp16_scaled(a, axis=1)  # noqa: E731
+        u_inv = 2.0 ** -11
+    else:
+        rnd = rnd_inv = lambda a: a  # noqa: E731
     for i in sampled_colour0(rng, 48):
         g = b[i].copy()
         mag = np.abs(b[i]).copy()
@@ -124,10 +143,10 @@ def test_fullsize_colour_step_sampled(precision):
                 nterms += nb
         Aii = gpu.ctx.get_block(0, int(i), int(i), nb)
         if fp32:
-            Ainv = rnd(np.linalg.inv(Aii))
+            Ainv = rnd_inv(np.linalg.inv(Aii))
             ref = Ainv @ g
-            gn = gamma(nterms, U32) * mag
-            bound = (np.abs(Ainv) @ gn + (gamma(nb, U32) + 2 * U32) * (np.abs(Ainv) @ (np.abs(g) + gn))
+            gn = gamma(nterms + 8, U32) * mag
+            bound = (np.abs(Ainv) @ gn + (gamma(nb + 1, U32) + 2 * u_inv) * (np.abs(Ainv) @ (np.abs(g) + gn))
                      + U32 * np.abs(ref))
             err = np.abs(xg[i] - ref)
             assert np.all(err <= bound), (i, err.max(), bound.max(), np.linalg.cond(Aii))

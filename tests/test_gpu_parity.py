@@ -169,7 +169,7 @@ def test_solve_fp64_matches_oracle(name):
     assert rel(xd.cpu().numpy(), xo) <= 1e-11
 
 
-@pytest.mark.parametrize("precision", [native.FP32, native.BF16])
+@pytest.mark.parametrize("precision", [native.FP32, native.BF16, native.FP16])
 @pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-unsteady-p2"])
 def test_mixed_precision_refinement(name, precision):
     """Low-precision V-cycles inside FP64 refinement reach 1e-10 and the same
@@ -186,19 +186,57 @@ def test_mixed_precision_refinement(name, precision):
     assert rel(x.cpu().numpy(), x64.cpu().numpy()) <= 1e-8
 
 
-def test_fp32_cycle_close_to_oracle_emulation():
-    """One FP32 cycle against the oracle with blocks rounded to FP32 (the
-    accumulation order differs, so the bar is FP32-level agreement)."""
-    name = "stress16p3"
+STORAGE = {native.FP32: "fp32", native.BF16: "bf16", native.FP16: "fp16"}
+
+
+@pytest.mark.parametrize("precision", [native.FP32, native.BF16, native.FP16])
+@pytest.mark.parametrize("name", ["stress16p3", "3d-unsteady-p2"])
+def test_low_precision_cycle_close_to_oracle_emulation(name, precision):
+    """One low-precision cycle against the oracle with the same rounded
+    blocks (FP32, BF16, or FP16 with per-sub-block / per-row power-of-two
+    scales) and the in-cycle residual from them.  The library keeps FP32
+    vectors and sums, the emulation FP64, so the bar is FP32-level agreement
+    (amplified by the cycle)."""
     prob, gpu64, _ = get(name)
-    _, gpu, _ = get(name, native.FP32)
-    orc32 = multigrid.Multigrid(prob, storage="fp32")
+    _, gpu, _ = get(name, precision)
+    orc = multigrid.Multigrid(prob, storage=STORAGE[precision])
     b = gpu64.rhs().ravel()
     bd = dev(b)
     x = torch.zeros_like(bd)
     it, hist = gpu.ctx.solve(x, bd, rtol=1e-30, maxit=1)
-    xo = orc32.precondition(b)
+    xo = orc.precondition(b)
     assert rel(x.cpu().numpy(), xo) <= 1e-4
+    if precision != native.FP32:
+        # and it is the rounded operator that is being emulated: the FP32 one differs more
+        orc32 = multigrid.Multigrid(prob, storage="fp32")
+        assert rel(x.cpu().numpy(), orc32.precondition(b)) > 10 * rel(x.cpu().numpy(), xo)
+
+
+@pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-mixed-p1"])
+def test_fp16_colour_step_warp_and_wide_kernels(name):
+    """FP16 colour steps of both kernels (one warp per element; one CTA per
+    element) against the oracle's colour step with the same scaled FP16
+    blocks, in FP32-level agreement."""
+    prob, _, _ = get(name)
+    _, gpu, _ = get(name, native.FP16)
+    orc = multigrid.Multigrid(prob, storage="fp16")
+    sm = orc.sm[0]
+    rng = np.random.default_rng(17)
+    x0 = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
+    b = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
+    xo = x0.copy()
+    for c in range(sm.ncol):
+        sm.colour_step(xo, b, c)
+    try:
+        for wide in (0, 1 << 30):
+            gpu.ctx.set_wide_launch(wide)
+            xd = torch.from_numpy(x0).float().cuda()
+            bd = torch.from_numpy(b).float().cuda()
+            for c in range(sm.ncol):
+                gpu.ctx.gs_colour_ex(0, c, native.FP16, xd, bd)
+            assert rel(xd.double().cpu().numpy(), xo) <= 1e-4, wide
+    finally:
+        gpu.ctx.set_wide_launch(1024)
 
 
 def test_invalid_arguments_are_rejected():
@@ -221,7 +259,7 @@ def test_invalid_arguments_are_rejected():
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", [native.FP64, native.FP32, native.BF16])
+@pytest.mark.parametrize("precision", [native.FP64, native.FP32, native.BF16, native.FP16])
 @pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-unsteady-p2"])
 def test_fgmres_solve(name, precision):
     """Flexible GMRES with the V-cycle as right preconditioner (Section 3):
@@ -377,7 +415,7 @@ def test_learned_smoother_solve_converges_and_is_judged():
     gpu.close()
 
 
-@pytest.mark.parametrize("precision", [native.FP32, native.BF16])
+@pytest.mark.parametrize("precision", [native.FP32, native.BF16, native.FP16])
 @pytest.mark.parametrize("name", ["stress16p3", "3d-unsteady-p2"])
 def test_fgmres_refined_variant(name, precision):
     """Krylov matvec on FP32 blocks (FP32 or BF16 cycle) with FP64 restarts

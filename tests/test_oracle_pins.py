@@ -375,6 +375,47 @@ def test_bf16_rounding_is_round_to_nearest_even():
     np.testing.assert_array_equal(multigrid.round_bf16(v), [1.0, 1.0 + 2 * 2.0 ** -7, 1.0, -3.140625])
 
 
+def test_fp16_scaled_rounding_values():
+    """Scaled FP16 storage: hand-computed values.  [1, 3, 1e-3]: max 3 =
+    0.75 * 2^2, so the group is multiplied by 2^13; 8.192 rounds to 1049 * 2^-7
+    (FP16 spacing 2^-7 on [8, 16)).  1 + 2^-11 is scaled by 2^14 to 16392, a tie
+    between 16384 and 16400 (spacing 16), which goes to the even 16384.  A
+    member 2^-41 below the maximum falls under half the smallest subnormal and
+    becomes 0."""
+    got = multigrid.round_fp16_scaled(np.array([[1.0, 3.0, 1e-3]]), axis=1)
+    np.testing.assert_array_equal(got, [[1.0, 3.0, 1049 * 2.0 ** -7 / 2.0 ** 13]])
+    np.testing.assert_array_equal(multigrid.round_fp16_scaled(np.array([1.0 + 2.0 ** -11]), axis=0), [1.0])
+    np.testing.assert_array_equal(multigrid.round_fp16_scaled(np.array([1.0, 2.0 ** -41]), axis=0), [1.0, 0.0])
+    np.testing.assert_array_equal(multigrid.round_fp16_scaled(np.zeros((2, 3)), axis=1), np.zeros((2, 3)))
+
+
+def test_fp16_scaled_rounding_error_bound_and_groups():
+    """Each entry is off by at most half an FP16 unit of its scaled value
+    (relative 2^-11 for normal scaled values, absolute 2^-25 of the scale
+    below), the groups are independent, and the sparse sub-block version
+    equals the dense one applied per s x s sub-block."""
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal((5, 6, 7)) * np.exp2(rng.integers(-30, 30, (5, 6, 1)))
+    r = multigrid.round_fp16_scaled(a, axis=2)
+    mx = np.abs(a).max(axis=2, keepdims=True)
+    _, e = np.frexp(mx)
+    scaled = np.abs(a) * np.exp2(15.0 - e)
+    tol = np.where(scaled >= 2.0 ** -14, scaled * 2.0 ** -11, 2.0 ** -25) * np.exp2(e - 15.0)
+    assert np.all(np.abs(r - a) <= tol)
+    # rows are independent: rounding one row alone gives the same values
+    np.testing.assert_array_equal(multigrid.round_fp16_scaled(a[2:3, 4:5], axis=2), r[2:3, 4:5])
+    s, nbk = 3, 4
+    A = sp.random(nbk * s, nbk * s, density=0.5, random_state=1, format="csr")
+    A.data *= np.exp2(rng.integers(-20, 20, A.nnz))
+    Rs = multigrid.round_fp16_subblocks(A, s).toarray()
+    D = A.toarray().reshape(nbk, s, nbk, s)
+    mxb = np.abs(D).max(axis=(1, 3), keepdims=True)
+    _, eb = np.frexp(mxb)
+    upb = np.exp2(15.0 - np.where(mxb > 0, eb, 0))
+    ref = ((D * upb).astype(np.float16).astype(np.float64) / upb).reshape(nbk * s, nbk * s)
+    np.testing.assert_array_equal(Rs, ref)
+
+
 def test_bottom_solve_is_least_squares_solution():
     """The bottom solver returns the least-squares solution: orthogonal to the
     kernel, residual orthogonal to the range (Section 3 footnote)."""
