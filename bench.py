@@ -30,7 +30,6 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DEFAULT_VARIANT = 2
 METRIC = "time to 1e-10 rel. residual & DOFs/s per V-cycle: mixed+learned vs plain FP64"
 
 
@@ -283,6 +282,9 @@ def run_native(args):
     setup_s = time.perf_counter() - t0
     mg64 = StokesMG(prob, precision=native.FP64, device=local, nu=(args.nu, args.nu)) \
         if prec != native.FP64 else mg
+    # launch shapes picked by the library's autotuner (outside the timed region)
+    tuned, tuned_ms = mg.ctx.autotune()
+    tuned64 = mg64.ctx.autotune()[0] if mg64 is not mg else tuned
     method = {"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR, "richardson": native.RICHARDSON}[args.solver]
     mg.ctx.set_solver(method, args.restart)
     mg64.ctx.set_solver(native.FGMRES if method == native.FGMRES_IR else method, args.restart)
@@ -416,7 +418,8 @@ def run_native(args):
                 mg.ctx.set_tuning(2, prec, c_)
                 tv = time_kernel(lambda: mg.ctx.gs_colour_ex(0, 0, prec, xv, bv, stream), 20, stream)
                 variants["warp_ctas%d" % c_] = {"launch_ms": round(tv * 1e3, 4), "GBps": round(alg / tv / 1e9, 1)}
-    mg.ctx.set_tuning(DEFAULT_VARIANT, prec)
+    mg.ctx.set_tuning(tuned["variant"], prec, tuned["ctas_cycle"])
+    mg.ctx.set_wide_launch(tuned["wide_max"])
     t_gs64 = time_kernel(lambda: mg64.ctx.gs_colour(0, 0, x, b, stream), 10, stream)
     alg64 = algorithmic_bytes_gs(mg64, prob, 8, 8, int(ne_levels[0]))
     kernels64 = {"gs_sweep_fp64_ms": round(t_gs64 * 1e3, 4),
@@ -436,7 +439,9 @@ def run_native(args):
         "nrhs": args.nrhs,
         "plain_fp64": plain, "speedup_vs_plain_fp64": plain["ms_per_solve"] / (el / args.steps * 1e3),
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "fp64_kernels": kernels64,
-        "gs_variants": variants, "learned_smoother": learned,
+        "gs_variants": variants, "autotune": {"cycle": tuned, "fp64": tuned64,
+                                              "best_colour_step_ms": [round(v, 4) for v in tuned_ms]},
+        "learned_smoother": learned,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -509,6 +514,7 @@ def run_unsteady(args):
     t0 = time.perf_counter()
     mg = StokesMG(prob, precision=prec, nu=(args.nu, args.nu))
     setup_s = time.perf_counter() - t0
+    mg.ctx.autotune()
     mg.ctx.set_solver({"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR,
                        "richardson": native.RICHARDSON}[args.solver], args.restart)
     # The manufactured flow is (1.5 + cos(omega t)) times a fixed field: every

@@ -356,6 +356,24 @@ int stk_set_tuning(stk_ctx* ctx, int variant, int precision, int ctas_per_sm, in
  */
 int stk_set_wide_launch(stk_ctx* ctx, int max_positions);
 
+/*
+ * Autotuner for the element-kernel launches (no counterpart in the paper):
+ * on this context's own finest-level records it times one colour step for
+ * the warp-per-element kernel at 2, 3, 4, 6 and 8 CTAs per SM and for the
+ * one-CTA-per-element kernel with direct loads, in the cycle's precision and
+ * in FP64 (the outer residual), and keeps the fastest shapes; then, from the
+ * coarsest smoothing level upwards, it keeps the one-CTA-per-element latency
+ * kernel (stk_set_wide_launch) for as long as it beats that choice.  Call
+ * after stk_setup, outside any stream capture; it runs colour steps on the
+ * library's own work vectors (zeroed before and after) and synchronises
+ * `stream`.  choice (may be NULL, 4 ints) receives {variant, CTAs per SM in
+ * the cycle precision, CTAs per SM in FP64, latency-kernel limit};
+ * best_ms (may be NULL, 2 doubles) the fastest finest-level colour step in
+ * the cycle precision and in FP64.  Results are unchanged up to the
+ * association order of sums.  Errors: STK_ERR_NOT_SETUP, STK_ERR_CUDA.
+ */
+int stk_autotune(stk_ctx* ctx, int* choice, double* best_ms, void* stream);
+
 /* Number of kernel launches the library enqueued since the context was
  * created (all of them are this library's own kernels). */
 int stk_launch_count(stk_ctx* ctx, int64_t* count);

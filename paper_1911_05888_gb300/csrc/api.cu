@@ -1336,6 +1336,113 @@ int stk_set_wide_launch(stk_ctx* c, int max_positions) {
   });
 }
 
+// Autotuner (no counterpart in the paper; the launch-shape choice of a10):
+// times one finest-level colour step for each candidate shape on this
+// context's own records, keeps the fastest, then finds the launch size below
+// which the one-CTA-per-element kernel beats it, level by level.
+int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int L = nlevels(*c);
+    for (int l = 0; l < L - 1; ++l)
+      for (int v = 0; v < 2; ++v) {
+        DevLevel& D = c->dev[l];
+        const size_t es = v == 0 ? 8 : 4;
+        if (D.vx[v]) ck(cudaMemsetAsync(D.vx[v], 0, (size_t)D.ne * c->nb * es, st), "memset");
+        if (D.vb[v]) ck(cudaMemsetAsync(D.vb[v], 0, (size_t)D.ne * c->nb * es, st), "memset");
+      }
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0), "event");
+    ck(cudaEventCreate(&e1), "event");
+    // mean time of `reps` colour-0 steps on level l in precision prec (ms)
+    auto time_step = [&](int l, int prec, int reps) -> double {
+      DevLevel& D = c->dev[l];
+      const int vi = prec == STK_FP64 ? 0 : 1;
+      const int n = D.cstart[1] - D.cstart[0];
+      ck(run_element(*c, l, prec, MODE_GS, D.cstart[0], n, D.inv[prec], D.vb[vi], D.vx[vi], nullptr, st), "tune");
+      ck(cudaEventRecord(e0, st), "event");
+      for (int i = 0; i < reps; ++i)
+        ck(run_element(*c, l, prec, MODE_GS, D.cstart[0], n, D.inv[prec], D.vb[vi], D.vx[vi], nullptr, st), "tune");
+      ck(cudaEventRecord(e1, st), "event");
+      ck(cudaEventSynchronize(e1), "event");
+      float ms = 0;
+      ck(cudaEventElapsedTime(&ms, e0, e1), "event");
+      return (double)ms / reps;
+    };
+    c->wide_max = 0;
+    const int precs[2] = {c->precision, STK_FP64};
+    double best[2] = {0, 0};
+    int chosen_variant = c->variant;
+    for (int pi = 0; pi < (c->precision == STK_FP64 ? 1 : 2); ++pi) {
+      const int prec = precs[pi];
+      // warp-per-element kernel: CTAs of 8 warps per SM
+      double t2 = 1e300;
+      int bc = c->warp_ctas[prec];
+      c->variant = 2;
+      for (int ctas : {2, 3, 4, 6, 8}) {
+        c->warp_ctas[prec] = ctas;
+        const double t = time_step(0, prec, 10);
+        if (t < t2) {
+          t2 = t;
+          bc = ctas;
+        }
+      }
+      c->warp_ctas[prec] = bc;
+      // one CTA per element with direct loads (not for scaled FP16 records)
+      double t0 = 1e300;
+      if (prec != STK_FP16) {
+        c->variant = 0;
+        t0 = time_step(0, prec, 10);
+      }
+      if (pi == 0) chosen_variant = t0 < t2 ? 0 : 2;
+      best[pi] = std::min(t0, t2);
+      c->variant = chosen_variant;
+    }
+    // Latency kernel: from the coarsest smoothing level up, as long as it wins.
+    int wide = 0;
+    for (int l = L - 2; l >= 0; --l) {
+      DevLevel& D = c->dev[l];
+      const int n = D.cstart[1] - D.cstart[0];
+      c->wide_max = 0;
+      const double t_cfg = time_step(l, c->precision, 10);
+      c->wide_max = n;
+      const double t_wide = time_step(l, c->precision, 10);
+      if (t_wide < t_cfg)
+        wide = n;
+      else
+        break;
+    }
+    c->wide_max = wide;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int l = 0; l < L - 1; ++l)
+      for (int v = 0; v < 2; ++v) {
+        DevLevel& D = c->dev[l];
+        const size_t es = v == 0 ? 8 : 4;
+        if (D.vx[v]) ck(cudaMemsetAsync(D.vx[v], 0, (size_t)D.ne * c->nb * es, st), "memset");
+      }
+    ck(cudaStreamSynchronize(st), "sync");
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_x = c->graph_b = nullptr;
+    if (c->cycle_graph) cudaGraphExecDestroy(c->cycle_graph);
+    c->cycle_graph = nullptr;
+    c->cycle_graph_prec = -1;
+    if (choice) {
+      choice[0] = c->variant;
+      choice[1] = c->warp_ctas[c->precision];
+      choice[2] = c->warp_ctas[STK_FP64];
+      choice[3] = c->wide_max;
+    }
+    if (best_ms) {
+      best_ms[0] = best[0];
+      best_ms[1] = c->precision == STK_FP64 ? best[0] : best[1];
+    }
+    return STK_OK;
+  });
+}
+
 int stk_set_solver(stk_ctx* c, int method, int restart) {
   return guard(c, [&]() -> int {
     if (method < 0 || method > 2 || restart < 1 || restart > 100)

@@ -110,13 +110,11 @@ template <> struct StorageTraits<__half> {
   using Acc = float;
   static constexpr int V = 8;
   __device__ static inline void cvt(uint4 v, float* w) {
-    uint32_t u[4] = {v.x, v.y, v.z, v.w};
+    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      __half2 h = *reinterpret_cast<const __half2*>(&u[i]);
-      float2 f = __half22float2(h);
-      w[2 * i] = f.x;
-      w[2 * i + 1] = f.y;
+      w[2 * i] = __half2float(__ushort_as_half((unsigned short)(u[i] & 0xffffu)));
+      w[2 * i + 1] = __half2float(__ushort_as_half((unsigned short)(u[i] >> 16)));
     }
   }
   __device__ static inline void load(const __half* p, float* w) { cvt(__ldcs(reinterpret_cast<const uint4*>(p)), w); }
@@ -572,6 +570,13 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
     __syncwarp();
     const TS* mrec = mat + (size_t)pos * nb * NBP;
     const TA* vin = (mode == MODE_GS) ? g : xi;
+    // row scales of the FP16 dense block, fetched before its loads (nb <= 128)
+    float rs[4] = {1.f, 1.f, 1.f, 1.f};
+    if constexpr (kScaledStorage<TS>) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (lane + 32 * q < nb) rs[q] = rsc[(size_t)pos * NBP + lane + 32 * q];
+    }
     for (int u = lane; u < NRV * wg.NCG; u += 32) {
       const int rvv = u % NRV, cg = u / NRV;
       const int c0 = cg * wg.CW, c1 = min(nb, c0 + wg.CW);
@@ -590,10 +595,13 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
       for (int j = 0; j < V; ++j) part2[cg * NBP + rvv * V + j] = acc[j];
     }
     __syncwarp();
-    for (int r = lane; r < nb; r += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = lane + 32 * q;
+      if (r >= nb) break;
       TA sum = 0;
       for (int cg = 0; cg < wg.NCG; ++cg) sum += part2[cg * NBP + r];
-      if constexpr (kScaledStorage<TS>) sum *= rsc[(size_t)pos * NBP + r];
+      if constexpr (kScaledStorage<TS>) sum *= rs[q];
       if (mode == MODE_GS)
         x[(size_t)e * nb + r] = (TX)sum;
       else
@@ -984,6 +992,7 @@ static cudaError_t launch_warp_s(const Pattern& pat, int mode, int pos0, int npo
                                  const int* nbr, const void* cpl, const void* mat, const float* tsc,
                                  const float* rsc, const void* b, void* x, void* r, int ctas, cudaStream_t st) {
   if (npos <= 0) return cudaSuccess;
+  if (pat.nb > 128) return cudaErrorInvalidValue;   // the final row loop covers 4 x 32 rows
   WarpGeom<TS> wg = warp_geometry<TS>(pat);
   size_t smem = (size_t)kWarps * wg.words * sizeof(typename StorageTraits<TS>::Acc);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;

@@ -69,6 +69,7 @@ SIGNATURES = {
                         _c_dbl_p, _vp],
     "stk_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "stk_set_wide_launch": [_vp, ctypes.c_int],
+    "stk_autotune": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _vp],
     "stk_set_phases": [_vp, ctypes.c_int, _c_int_p, _c_dbl_p, ctypes.c_int],
     "stk_get_interface": [_vp, _c_int_p, _c_int_p, _c_dbl_p],
     "stk_assemble_rhs2": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p],
@@ -332,6 +333,15 @@ class Context:
 
     def set_wide_launch(self, max_positions):
         self._check(self.lib.stk_set_wide_launch(self.h, max_positions), "stk_set_wide_launch")
+
+    def autotune(self, stream=None):
+        """Time the element-kernel launch shapes and keep the fastest; returns
+        ({variant, ctas_cycle, ctas_fp64, wide_max}, (best_ms_cycle, best_ms_fp64))."""
+        choice = (ctypes.c_int * 4)()
+        best = (ctypes.c_double * 2)()
+        self._check(self.lib.stk_autotune(self.h, choice, best, _stream(stream)), "stk_autotune")
+        keys = ("variant", "ctas_cycle", "ctas_fp64", "wide_max")
+        return dict(zip(keys, list(choice))), (best[0], best[1])
 
     def set_solver(self, method, restart=30):
         self._check(self.lib.stk_set_solver(self.h, method, restart), "stk_set_solver")

@@ -458,3 +458,34 @@ def test_multiphase_colours_and_solve(name):
     xo, ho = orc.fgmres(b, rtol=1e-11, maxit=100, restart=40)
     assert abs(it - (len(ho) - 1)) <= 1
     assert rel(x.cpu().numpy(), xo) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", [native.FP64, native.FP32])
+def test_autotune_keeps_results(precision):
+    """The autotuner (launch shapes timed on the context's own records) picks
+    valid shapes, and afterwards the FP64 V-cycle iterates still match the
+    oracle's to 1e-12 and a low-precision solve still reaches 1e-10."""
+    name = "stress16p3"
+    prob, _, orc = get(name)
+    gpu = StokesMG(prob, precision=precision)
+    try:
+        choice, best = gpu.ctx.autotune()
+        assert choice["variant"] in (0, 2)
+        assert choice["ctas_cycle"] in (2, 3, 4, 6, 8) and choice["ctas_fp64"] in (2, 3, 4, 6, 8)
+        assert choice["wide_max"] >= 0 and best[0] > 0 and best[1] > 0
+        rng = np.random.default_rng(23)
+        b = rng.uniform(-1, 1, prob.n_dofs)
+        if precision == native.FP64:
+            xd, bd = torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda"), dev(b)
+            xo = np.zeros(prob.n_dofs)
+            for _ in range(5):
+                gpu.ctx.vcycle(xd, bd)
+                orc.vcycle(xo, b)
+            assert rel(xd.cpu().numpy(), xo) <= 1e-12
+        else:
+            bd = dev(gpu.rhs().ravel())
+            x = torch.zeros_like(bd)
+            it, hist = gpu.ctx.solve(x, bd, rtol=1e-10, maxit=100)
+            assert hist[-1] <= 1e-10
+    finally:
+        gpu.close()
