@@ -239,6 +239,7 @@ def run_profile(args):
     prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16, "fp16": native.FP16}[args.precision]
     prob = workload(args.n, args.p)
     mg = StokesMG(prob, precision=prec, nu=(args.nu, args.nu))
+    mg.ctx.autotune()
     mg.ctx.set_solver({"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR,
                        "richardson": native.RICHARDSON}[args.solver], args.restart)
     torch.cuda.synchronize()
