@@ -361,11 +361,13 @@ int stk_set_wide_launch(stk_ctx* ctx, int max_positions);
  * on this context's own finest-level records it times one colour step for
  * the warp-per-element kernel at 2, 3, 4, 6 and 8 CTAs per SM and for the
  * one-CTA-per-element kernel with direct loads, in the cycle's precision and
- * in FP64 (the outer residual), and keeps the fastest shapes; then, from the
- * coarsest smoothing level upwards, it keeps the one-CTA-per-element latency
- * kernel (stk_set_wide_launch) for as long as it beats that choice.  Call
- * after stk_setup, outside any stream capture; it runs colour steps on the
- * library's own work vectors (zeroed before and after) and synchronises
+ * in FP64 (the outer residual), and keeps the fastest shapes; then it times
+ * both that choice and the one-CTA-per-element latency kernel on every
+ * smoothing level and sets the stk_set_wide_launch threshold with the least
+ * total time.  Each timing replays a CUDA graph of repeated launches on the
+ * library's own stream, so host launch overhead does not mask the kernels.
+ * Call after stk_setup, outside any stream capture; it runs colour steps on
+ * the library's own work vectors (zeroed before and after) and synchronises
  * `stream`.  choice (may be NULL, 4 ints) receives {variant, CTAs per SM in
  * the cycle precision, CTAs per SM in FP64, latency-kernel limit};
  * best_ms (may be NULL, 2 doubles) the fastest finest-level colour step in

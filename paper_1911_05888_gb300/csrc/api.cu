@@ -1355,19 +1355,37 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
     cudaEvent_t e0, e1;
     ck(cudaEventCreate(&e0), "event");
     ck(cudaEventCreate(&e1), "event");
-    // mean time of `reps` colour-0 steps on level l in precision prec (ms)
+    // Mean time (ms) of one colour-0 step on level l in precision prec: `reps`
+    // steps captured in a CUDA graph on the library's own stream and replayed,
+    // so that host launch overhead does not hide the kernels' own durations.
+    cudaStream_t ts = c->stream;
+    ck(cudaStreamSynchronize(st), "sync");
     auto time_step = [&](int l, int prec, int reps) -> double {
       DevLevel& D = c->dev[l];
       const int vi = prec == STK_FP64 ? 0 : 1;
       const int n = D.cstart[1] - D.cstart[0];
-      ck(run_element(*c, l, prec, MODE_GS, D.cstart[0], n, D.inv[prec], D.vb[vi], D.vx[vi], nullptr, st), "tune");
-      ck(cudaEventRecord(e0, st), "event");
-      for (int i = 0; i < reps; ++i)
-        ck(run_element(*c, l, prec, MODE_GS, D.cstart[0], n, D.inv[prec], D.vb[vi], D.vx[vi], nullptr, st), "tune");
-      ck(cudaEventRecord(e1, st), "event");
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      ck(cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal), "capture");
+      for (int i = 0; i < reps; ++i) {
+        cudaError_t e = run_element(*c, l, prec, MODE_GS, D.cstart[0], n, D.inv[prec], D.vb[vi], D.vx[vi], nullptr, ts);
+        if (e != cudaSuccess) {
+          cudaStreamEndCapture(ts, &graph);
+          if (graph) cudaGraphDestroy(graph);
+          ck(e, "tune launch");
+        }
+      }
+      ck(cudaStreamEndCapture(ts, &graph), "capture");
+      ck(cudaGraphInstantiate(&exec, graph, 0), "instantiate");
+      ck(cudaGraphLaunch(exec, ts), "graph");
+      ck(cudaEventRecord(e0, ts), "event");
+      ck(cudaGraphLaunch(exec, ts), "graph");
+      ck(cudaEventRecord(e1, ts), "event");
       ck(cudaEventSynchronize(e1), "event");
       float ms = 0;
       ck(cudaEventElapsedTime(&ms, e0, e1), "event");
+      cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
       return (double)ms / reps;
     };
     c->wide_max = 0;
@@ -1399,19 +1417,30 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
       best[pi] = std::min(t0, t2);
       c->variant = chosen_variant;
     }
-    // Latency kernel: from the coarsest smoothing level up, as long as it wins.
-    int wide = 0;
-    for (int l = L - 2; l >= 0; --l) {
+    // Latency kernel: time both kernels on every smoothing level's colour
+    // step and keep the threshold (0 or one level's colour size) with the
+    // least total time over the levels.
+    std::vector<int> nl(L - 1);
+    std::vector<double> t_cfg(L - 1), t_wide(L - 1);
+    for (int l = 0; l < L - 1; ++l) {
       DevLevel& D = c->dev[l];
-      const int n = D.cstart[1] - D.cstart[0];
+      nl[l] = D.cstart[1] - D.cstart[0];
       c->wide_max = 0;
-      const double t_cfg = time_step(l, c->precision, 10);
-      c->wide_max = n;
-      const double t_wide = time_step(l, c->precision, 10);
-      if (t_wide < t_cfg)
-        wide = n;
-      else
-        break;
+      t_cfg[l] = time_step(l, c->precision, 20);
+      c->wide_max = nl[l];
+      t_wide[l] = time_step(l, c->precision, 20);
+    }
+    int wide = 0;
+    double best_total = 1e300;
+    std::vector<int> cand(nl);
+    cand.push_back(0);
+    for (int thr : cand) {
+      double tot = 0;
+      for (int l = 0; l < L - 1; ++l) tot += nl[l] <= thr ? t_wide[l] : t_cfg[l];
+      if (tot < best_total) {
+        best_total = tot;
+        wide = thr;
+      }
     }
     c->wide_max = wide;
     cudaEventDestroy(e0);
