@@ -39,9 +39,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="stress2d", choices=["stress2d", "unsteady3d"],
+    ap.add_argument("--workload", default="stress2d", choices=["stress2d", "unsteady3d", "batch"],
                     help="stress2d: 2D viscous-stress 256x256 p=3 (default); unsteady3d: 3D unsteady "
-                         "periodic 48^3 p=2, 16 warm-started time steps")
+                         "periodic 48^3 p=2, 16 warm-started time steps; batch: the serving mix of --batch "
+                         "unsteady viscous-stress problems (32^2..256^2, p 2/3) solved together")
+    ap.add_argument("--batch", type=int, default=64, help="problems in the batch workload")
+    ap.add_argument("--batch-threads", type=int, default=16, help="host threads driving the batch")
     ap.add_argument("--re", type=float, default=100.0, help="effective Reynolds number (unsteady3d)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--p", type=int, default=3)
@@ -564,6 +567,118 @@ def run_unsteady(args):
         "gpu_launches": int(mg.ctx.launch_count() - l0), "clocks": clk}))
 
 
+def run_batch(args):
+    """Batched serving mix: independent 2D unsteady viscous-stress problems
+    (mesh sizes drawn from 32^2..256^2, p in {2, 3}, seeded viscosity
+    contrasts up to 1e2), each solved from zero to 1e-10 by FGMRES with a
+    V(nu, nu) preconditioner, all at once through stk_solve_batch; a step is
+    one solve of the whole batch.  The same batch with FP64 blocks follows
+    (the metric's plain comparison), after the first batch is freed."""
+    import threading
+    import torch
+    from paper_1911_05888_gb300 import native, problems as P
+    from paper_1911_05888_gb300.solver import StokesMG
+    prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16, "fp16": native.FP16}[args.precision]
+    probs = [q.with_(nu1=args.nu, nu2=args.nu) for q in P.serving_mix(args.batch, seed=0)]
+
+    def build(precision):
+        out = [None] * len(probs)
+
+        def make(i):
+            out[i] = StokesMG(probs[i], precision=precision)
+        for k in range(0, len(probs), args.batch_threads):
+            ths = [threading.Thread(target=make, args=(i,)) for i in range(k, min(len(probs), k + args.batch_threads))]
+            for t in ths:
+                t.start()
+            for t in ths:
+                t.join()
+        for g in out:
+            g.ctx.autotune()
+            g.ctx.set_solver(native.FGMRES, args.restart)
+        return out
+
+    def measure(gpus, steps, warmup, threads=None):
+        threads = args.batch_threads if threads is None else threads
+        bs = [torch.from_numpy(g.rhs().ravel()).cuda() for g in gpus]
+        xs = [torch.zeros_like(b) for b in bs]
+        ctxs = [g.ctx for g in gpus]
+
+        def step():
+            for x in xs:
+                x.zero_()
+            return native.solve_batch(ctxs, xs, bs, rtol=1e-10, maxit=200, threads=threads)[0]
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        l0 = sum(c.launch_count() for c in ctxs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        its = []
+        for _ in range(steps):
+            its = step()
+        e1.record()
+        torch.cuda.synchronize()
+        el = e0.elapsed_time(e1) / 1e3
+        units = steps * sum(g.prob.n_dofs * it for g, it in zip(gpus, its))
+        launches = sum(c.launch_count() for c in ctxs) - l0
+        # end to end: host right-hand sides in, solutions out, every step
+        bh = [b.cpu().pin_memory() for b in bs]
+        xh = [torch.empty_like(h).pin_memory() for h in bh]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for b, h in zip(bs, bh):
+                b.copy_(h, non_blocking=True)
+            step()
+            for x, h in zip(xs, xh):
+                h.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        worst = 0.0
+        for g, x, b in zip(gpus, xs, bs):
+            r = torch.empty_like(b)
+            worst = max(worst, g.ctx.residual(x, b, r, want_norm=True) / torch.linalg.norm(b).item())
+        return el, units, its, launches, e2e_s, sum(b.numel() * 8 for b in bs), worst
+
+    t0 = time.perf_counter()
+    gpus = build(prec)
+    setup_s = time.perf_counter() - t0
+    clocks = Clocks(0)
+    clocks.start()
+    el, units, its, launches, e2e_s, nbytes, worst = measure(gpus, args.steps, args.warmup)
+    clk = clocks.stop()
+    # the same batch driven by one host thread: problems one after another
+    el_seq = measure(gpus, 1, 0, threads=1)[0]
+    dofs = sum(g.prob.n_dofs for g in gpus)
+    for g in gpus:
+        g.close()
+    del gpus
+    torch.cuda.empty_cache()
+    plain = None
+    if prec != native.FP64:
+        g64 = build(native.FP64)
+        el64, units64, its64, _, _, _, worst64 = measure(g64, max(1, args.steps // 2), 1)
+        plain = {"ms_per_step": el64 / max(1, args.steps // 2) * 1e3, "dof_cycles_per_s": units64 / el64,
+                 "iters": its64, "worst_rel_residual": worst64}
+        for g in g64:
+            g.close()
+    print(json.dumps({
+        "metric": METRIC, "value": units / el, "unit": "DOF-cycles/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32-storage in f64", "bf16": "bf16-storage in f64",
+                                   "fp16": "f16-storage(pow2-scaled) in f64"}[args.precision],
+        "data": "synthetic (manufactured unsteady flows, seeded viscosities)",
+        "config": {"workload": "batched-serving-mix-2d-unsteady-viscous-stress", "problems": len(probs),
+                   "sizes": [q.n[0] for q in probs], "degrees": [q.p for q in probs], "dofs": dofs,
+                   "nu": [args.nu, args.nu], "outer": "fgmres(%d)" % args.restart, "rtol": 1e-10,
+                   "host_threads": args.batch_threads, "cache": "inputs larger than L2"},
+        "iters": its, "worst_rel_residual": worst, "setup_s": round(setup_s, 1),
+        "e2e": {"value": units / e2e_s, "unit": "DOF-cycles/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_s / args.steps * 1e3},
+        "sequential_ms_per_step": el_seq * 1e3,
+        "plain_fp64": plain, "gpu_launches": int(launches), "clocks": clk}))
+
+
 def main():
     args = parse()
     if args.cpu_child:
@@ -571,6 +686,8 @@ def main():
         return
     if args.workload == "unsteady3d":
         run_unsteady(args)
+    elif args.workload == "batch":
+        run_batch(args)
     elif args.profile:
         run_profile(args)
     elif args.impl == "reference":

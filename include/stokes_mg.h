@@ -277,6 +277,27 @@ int stk_solve_multi(stk_ctx* ctx, double* X_dev, const double* B_dev, int nrhs, 
                     int* iters_out, double* hist, void* stream);
 
 /*
+ * A batch of independent problems (no counterpart in the paper; a batching
+ * layer over stk_solve / stk_solve_multi): solves ctx[i] x[i] = b[i] for
+ * i < n, each context set up for its own problem (any mesh size, degree,
+ * boundary conditions or precision; every context distinct).  A pool of
+ * `threads` host threads (0: one per hardware thread, at most n) takes the
+ * problems in order; each problem's whole outer iteration runs on its own
+ * context's stream, so the kernels of different problems overlap on the GPU
+ * (the coarse levels of one problem leave most SMs idle).  nrhs = 1 calls
+ * stk_solve with the context's solver options; nrhs in 2..8 calls
+ * stk_solve_multi with `inner` (x[i], b[i] then hold nrhs right-hand sides,
+ * [nrhs][element][nb]).  The caller's `stream` is synchronised first.
+ * iters_out and status_out (may be NULL, n entries) get each problem's
+ * iteration count and status code; stk_last_error(ctx[i]) holds its message.
+ * Returns STK_OK when every problem succeeded, else the first failing
+ * problem's code.  Errors: STK_ERR_INVALID_ARG (null or repeated context,
+ * n < 1, nrhs outside 1..8), STK_ERR_CUDA.
+ */
+int stk_solve_batch(stk_ctx* const* ctx, int n, double* const* x, const double* const* b, int nrhs, double rtol,
+                    int maxit, int inner, int threads, int* iters_out, int* status_out, void* stream);
+
+/*
  * Learned element-local post-smoother (not in the paper; cycles in FP32 or
  * BF16 only).  After the post-smoothing sweeps on the finest level, with
  * r = b - A x, each element's residual and those of its 2d face neighbours,

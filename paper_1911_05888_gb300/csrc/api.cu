@@ -7,11 +7,13 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "stk_internal.h"
@@ -1926,6 +1928,51 @@ int stk_launch_count(stk_ctx* c, int64_t* count) {
   if (!c || !count) return STK_ERR_INVALID_ARG;
   *count = c->launches;
   return STK_OK;
+}
+
+int stk_solve_batch(stk_ctx* const* ctx, int n, double* const* x, const double* const* b, int nrhs, double rtol,
+                    int maxit, int inner, int threads, int* iters_out, int* status_out, void* stream) {
+  if (!ctx || !x || !b || n < 1 || nrhs < 1 || nrhs > 8) return STK_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctx[i] || !x[i] || !b[i]) return STK_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctx[j] == ctx[i]) return STK_ERR_INVALID_ARG;   // one context serves one problem at a time
+  }
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return STK_ERR_CUDA;
+  int nt = threads > 0 ? threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  nt = std::min(nt, n);
+  std::vector<int> status(n, STK_OK), iters(n, 0);
+  std::atomic<int> next(0);
+  // Each worker takes the next unsolved problem and runs its whole outer
+  // iteration on the problem's own context stream; the problems' kernels
+  // therefore overlap on the GPU wherever one problem alone leaves it idle.
+  auto worker = [&]() {
+    for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
+      if (cudaSetDevice(ctx[i]->device) != cudaSuccess) {
+        status[i] = STK_ERR_CUDA;
+        continue;
+      }
+      int it = 0;
+      status[i] = nrhs == 1 ? stk_solve(ctx[i], x[i], b[i], rtol, maxit, &it, nullptr, nullptr)
+                            : stk_solve_multi(ctx[i], x[i], b[i], nrhs, rtol, maxit, inner, &it, nullptr, nullptr);
+      iters[i] = it;
+    }
+  };
+  std::vector<std::thread> pool;
+  try {
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  } catch (...) {
+    // fewer workers than asked for: the ones started (and this thread) do the rest
+  }
+  worker();
+  for (auto& th : pool) th.join();
+  int rc = STK_OK;
+  for (int i = 0; i < n; ++i) {
+    if (iters_out) iters_out[i] = iters[i];
+    if (status_out) status_out[i] = status[i];
+    if (rc == STK_OK && status[i] != STK_OK) rc = status[i];
+  }
+  return rc;
 }
 
 }  // extern "C"

@@ -70,6 +70,9 @@ SIGNATURES = {
     "stk_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "stk_set_wide_launch": [_vp, ctypes.c_int],
     "stk_autotune": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _vp],
+    "stk_solve_batch": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
+                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                        ctypes.POINTER(ctypes.c_int), _vp],
     "stk_set_phases": [_vp, ctypes.c_int, _c_int_p, _c_dbl_p, ctypes.c_int],
     "stk_get_interface": [_vp, _c_int_p, _c_int_p, _c_dbl_p],
     "stk_assemble_rhs2": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p],
@@ -383,3 +386,26 @@ class Context:
         n = ctypes.c_int64()
         self._check(self.lib.stk_launch_count(self.h, ctypes.byref(n)), "stk_launch_count")
         return n.value
+
+
+def solve_batch(contexts, xs, bs, rtol=1e-10, maxit=200, nrhs=1, inner=3, threads=0, stream=None):
+    """stk_solve_batch over Context objects and device tensors (x, b per
+    problem).  Returns (iterations, status codes); raises StkError naming the
+    first failing problem."""
+    n = len(contexts)
+    if not (len(xs) == len(bs) == n):
+        raise ValueError("one x and one b per context")
+    lib = contexts[0].lib
+    hs = (_vp * n)(*[c.h.value for c in contexts])
+    xp = (_vp * n)(*[_ptr(t).value for t in xs])
+    bp = (_vp * n)(*[_ptr(t).value for t in bs])
+    it = (ctypes.c_int * n)()
+    st = (ctypes.c_int * n)()
+    rc = lib.stk_solve_batch(hs, n, xp, bp, nrhs, rtol, maxit, inner, threads, it, st, _stream(stream))
+    if rc != STK_OK:
+        bad = [i for i in range(n) if st[i] != STK_OK]
+        i = bad[0] if bad else 0
+        msg = lib.stk_last_error(contexts[i].h)
+        raise StkError("stk_solve_batch: problem %d: %s (%s)" % (i, msg.decode() if msg else "",
+                                                                ERRORS.get(rc, rc)))
+    return list(it), list(st)

@@ -358,6 +358,50 @@ def unsteady_periodic_3d(n=48, p=2, re=1.0, t=0.0, nu=(1, 1), tau=None, omega=No
                    nu1=nu[0], nu2=nu[1], exact=ex, name="3d-unsteady-periodic-n%d-p%d-re%g" % (n, p, re))
 
 
+def mu_contrast_2d(seed, contrast):
+    """Smooth seeded viscosity mu = exp(a s(x, y)) with s a normalised sum of
+    three Fourier modes (|s| <= 1) and a = ln(contrast) / 2, so that
+    max mu / min mu <= contrast."""
+    import sympy as sp
+    rng = np.random.default_rng(seed)
+    modes = [(int(rng.integers(1, 3)), int(rng.integers(1, 3)), float(rng.uniform(0.2, 1.0)),
+              float(rng.uniform(0, 1))) for _ in range(3)]
+    total = sum(m[2] for m in modes)
+    a = math.log(contrast) / 2
+
+    def expr(xs):
+        s = 0
+        for kx, ky, amp, ph in modes:
+            s = s + amp / total * sp.sin(2 * sp.pi * (kx * xs[0] + ph)) * sp.cos(2 * sp.pi * ky * xs[1])
+        return sp.exp(a * s)
+    return expr
+
+
+def unsteady_stress_2d(n=64, p=3, seed=0, contrast=100.0, nu=(3, 3), tau=None):
+    """2D unsteady viscous-stress form (eq. timedep1 with gamma = 1): Dirichlet
+    on three sides and a stress condition on the top, rho = 1, delta = 0.1 h,
+    seeded smooth viscosity with max / min <= contrast (mu_contrast_2d), the
+    manufactured solution of Appendix C with its mass term."""
+    import sympy as sp
+    h = 1.0 / n
+    delta = 0.1 * h
+    mu_expr = mu_contrast_2d(seed, contrast)
+    ex = paper_solution(2, 1, mu_expr=mu_expr, rho_expr=lambda xs: sp.Integer(1), delta=delta)
+    return Problem(d=2, n=(n, n), p=p, gamma=1, bc=(DIRICHLET, DIRICHLET, DIRICHLET, STRESS),
+                   mu=ex.mu, rho=lambda x: np.ones(x.shape[:-1]), delta=delta, tau=tau,
+                   nu1=nu[0], nu2=nu[1], exact=ex, name="2d-unsteady-stress-n%d-p%d-seed%d" % (n, p, seed))
+
+
+def serving_mix(count=64, seed=0, sizes=(32, 64, 128, 256), degrees=(2, 3), contrast=100.0):
+    """The batched serving mix: `count` unsteady viscous-stress problems with
+    mesh sizes and degrees drawn uniformly (seeded) and viscosity contrasts
+    up to `contrast` (problem i uses viscosity seed 1000 + i)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(sizes, count)
+    ps = rng.choice(degrees, count)
+    return [unsteady_stress_2d(n=int(ns[i]), p=int(ps[i]), seed=1000 + i, contrast=contrast) for i in range(count)]
+
+
 # ---------------------------------------------------------------------------
 # Seeded vectors
 # ---------------------------------------------------------------------------

@@ -489,3 +489,60 @@ def test_autotune_keeps_results(precision):
             assert hist[-1] <= 1e-10
     finally:
         gpu.close()
+
+
+BATCH = [(8, 2, 0, native.FP32), (16, 3, 1, native.FP64), (12, 2, 2, native.FP32), (16, 2, 3, native.FP16),
+         (8, 3, 4, native.FP32), (24, 2, 5, native.BF16)]
+
+
+def test_solve_batch_matches_individual_solves():
+    """A batch of independent unsteady viscous-stress problems of different
+    sizes, degrees and storage precisions solved concurrently
+    (stk_solve_batch, four host threads) gives every problem what solving it
+    alone gives: the same iteration count and solution, at 1e-10."""
+    gpus = []
+    try:
+        for n, p, seed, prec in BATCH:
+            g = StokesMG(P.unsteady_stress_2d(n=n, p=p, seed=seed), precision=prec)
+            g.ctx.set_solver(native.FGMRES, 30)
+            gpus.append(g)
+        bs = [dev(g.rhs().ravel()) for g in gpus]
+        xs = [torch.zeros_like(b) for b in bs]
+        its, status = native.solve_batch([g.ctx for g in gpus], xs, bs, rtol=1e-10, maxit=100, threads=4)
+        assert status == [native.STK_OK] * len(gpus)
+        for g, b, x, it in zip(gpus, bs, xs, its):
+            x1 = torch.zeros_like(b)
+            it1, hist = g.ctx.solve(x1, b, rtol=1e-10, maxit=100)
+            assert hist[-1] <= 1e-10 and abs(it1 - it) <= 1, (it1, it)
+            assert rel(x.cpu().numpy(), x1.cpu().numpy()) <= 1e-9
+            r = torch.empty_like(b)
+            assert g.ctx.residual(x, b, r, want_norm=True) <= 1e-10 * torch.linalg.norm(b).item()
+        with pytest.raises(native.StkError):
+            native.solve_batch([gpus[0].ctx, gpus[0].ctx], xs[:2], bs[:2])
+    finally:
+        for g in gpus:
+            g.close()
+
+
+def test_solve_batch_several_right_hand_sides():
+    """The batch with three right-hand sides per problem runs stk_solve_multi
+    for each problem; every right-hand side reaches 1e-10."""
+    gpus = []
+    try:
+        for n, p, seed, prec in BATCH[:3]:
+            if prec == native.FP16:
+                continue
+            gpus.append(StokesMG(P.unsteady_stress_2d(n=n, p=p, seed=seed), precision=prec))
+        rng = np.random.default_rng(31)
+        bs = [dev(rng.uniform(-1, 1, 3 * g.prob.n_dofs)) for g in gpus]
+        xs = [torch.zeros_like(b) for b in bs]
+        its, status = native.solve_batch([g.ctx for g in gpus], xs, bs, nrhs=3, rtol=1e-10, maxit=100, inner=3)
+        for g, b, x in zip(gpus, bs, xs):
+            nd = g.prob.n_dofs
+            for q in range(3):
+                r = torch.empty(nd, dtype=torch.float64, device="cuda")
+                nrm = g.ctx.residual(x[q * nd:(q + 1) * nd], b[q * nd:(q + 1) * nd], r, want_norm=True)
+                assert nrm <= 1e-10 * torch.linalg.norm(b[q * nd:(q + 1) * nd]).item()
+    finally:
+        for g in gpus:
+            g.close()
