@@ -236,6 +236,7 @@ def read_profile_traffic(name):
 
 def run_profile(args):
     """Small, self-contained launch sequences for ncu captures."""
+    import numpy as np
     import torch
     from paper_1911_05888_gb300 import native
     from paper_1911_05888_gb300.solver import StokesMG
@@ -256,6 +257,14 @@ def run_profile(args):
                 mg.ctx.gs_colour_ex(0, i % 4, prec, xv, bv)
             else:
                 mg.ctx.residual_ex(0, prec, xv, bv, rv)
+    elif args.nrhs > 1:
+        b_host = mg.rhs().ravel()
+        rng = np.random.default_rng(0)
+        Bm = torch.from_numpy(np.stack([b_host] + [rng.uniform(-1, 1, b_host.size)
+                                                   for _ in range(args.nrhs - 1)])).cuda()
+        Xm = torch.zeros_like(Bm)
+        it, hist = mg.ctx.solve_multi(Xm, Bm, args.nrhs, rtol=1e-10, maxit=100, inner=args.inner)
+        print("profile solve: %d right-hand sides, %d iterations to %.2e" % (args.nrhs, it, float(np.max(hist[-1]))))
     else:
         b = torch.from_numpy(mg.rhs().ravel()).cuda()
         x = torch.zeros_like(b)
@@ -315,8 +324,9 @@ def run_native(args):
         if args.nrhs > 1:
             Xm.zero_()
             it, hist = ctx.solve_multi(Xm, Bm, args.nrhs, rtol=1e-10, maxit=100, inner=args.inner)
-            # cycles per right-hand side: inner V-cycles per outer iteration
-            return it * args.inner, hist
+            # cycles per right-hand side: one per lockstep FGMRES step, or
+            # `inner` per outer refinement iteration
+            return (it if args.solver != "richardson" else it * args.inner), hist
         x.zero_()
         it, hist = ctx.solve(x, b, rtol=1e-10, maxit=200)
         return it, hist

@@ -266,15 +266,30 @@ int stk_residual_norm_static(stk_ctx* ctx, const double* x_dev, const double* b_
  * Several right-hand sides at once (up to 8): X and B are [nrhs][element][nb]
  * FP64 device arrays, X holding the initial guesses.  The V-cycle of
  * Algorithm 1 is applied to all right-hand sides together, so each element
- * record streamed from memory serves every right-hand side.  Iteration: outer
- * FP64 refinement X <- X + C with the FP64 residual R = B - A X; inside,
- * `inner` steps of C <- C + V(0, R - A C) with the residual in the cycle's
- * precision.  Stops when every ||B_q - A X_q|| <= rtol ||B_q|| or after
- * maxit outer iterations; hist (may be NULL) gets (maxit+1) x nrhs relative
- * residuals.  One outer iteration runs as one CUDA graph.
+ * record streamed from memory serves every right-hand side.  With
+ * stk_set_solver method 1 or 2: flexible GMRES(restart) in FP64, run in
+ * lockstep over the right-hand sides (one multi-RHS V-cycle and one FP64
+ * multi-RHS matvec per step, dots and rotations per right-hand side, a
+ * converged one drops out; restart capped at 256 / 8 = 32); *iters_out counts
+ * Arnoldi steps.  With method 0: outer FP64 refinement X <- X + C with the
+ * FP64 residual R = B - A X; inside, `inner` steps of C <- C + V(0, R - A C)
+ * with the residual in the cycle's precision, one outer iteration as one CUDA
+ * graph.  Stops when every ||B_q - A X_q|| <= rtol ||B_q|| or after maxit
+ * iterations; hist (may be NULL) gets (maxit+1) x nrhs relative residuals.
  */
 int stk_solve_multi(stk_ctx* ctx, double* X_dev, const double* B_dev, int nrhs, double rtol, int maxit, int inner,
                     int* iters_out, double* hist, void* stream);
+
+/*
+ * With eight right-hand sides (nrhs 5..8) and FP32 blocks, the element
+ * products of stk_solve_multi are small dense GEMMs (each s x s coupling
+ * sub-block times s x 8 neighbour values, the nb x nb block times nb x 8
+ * values): on = 1 (default) computes them on the tensor cores (mma.sync
+ * m16n8k8 TF32, each FP32 operand split into two TF32 parts, three products
+ * accumulated in FP32, about FP32 accuracy); on = 0 on the FP32 CUDA cores.
+ * Other precisions and four right-hand sides always use the CUDA cores.
+ */
+int stk_set_mrhs_tensor(stk_ctx* ctx, int on);
 
 /*
  * A batch of independent problems (no counterpart in the paper; a batching

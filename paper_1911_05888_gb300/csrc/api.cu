@@ -45,7 +45,7 @@ void prepare_pipe_kernels();
 void prepare_mrhs_kernels();
 cudaError_t launch_element_mrhs(const Pattern& pat, int storage, int nr, int mode, int pos0, int npos,
                                 const int* perm, const int* nbr, const void* cpl, const void* mat, const void* b,
-                                void* x, void* r, cudaStream_t st);
+                                void* x, void* r, cudaStream_t st, int tensor = 0);
 cudaError_t launch_restrict_mr(int vec64, int d, int s, int nb, int nr, const int* nc, const int* nf, int64_t nec,
                                const void* P, const void* r, void* rc, cudaStream_t st);
 cudaError_t launch_prolong_mr(int vec64, int d, int s, int nb, int nr, const int* nf, const int* nc, int64_t nec,
@@ -54,6 +54,11 @@ cudaError_t launch_bottom_mr(int vec64, int64_t n, int nr, const double* pinv, c
 cudaError_t launch_interleave(int kind, int64_t m, int nr, int nq, int to_interleaved, void* out, const void* in,
                               cudaStream_t st);
 cudaError_t launch_sumsq_mr(int64_t m, int nr, const double* x, double* part, double* out, cudaStream_t st);
+cudaError_t launch_multidot_mr(int64_t n, int nr, int k, const double* V, int64_t ldv, const double* w,
+                               double* part, double* out, cudaStream_t st);
+cudaError_t launch_multiaxpy_mr(int64_t n, int nr, int k, double alpha, const double* coef, const double* V,
+                                int64_t ldv, double* w, cudaStream_t st);
+cudaError_t launch_scale_mr(int64_t n, int nr, const double* s, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_features(int ne, int nb, int nface, int NO, int ldf, const int* nbr_nat, const float* r, float* F,
                             float* nrm, cudaStream_t st);
 cudaError_t launch_sgemm(int M, int N, int K, int ta, int tb, const float* A, int lda, const float* B, int ldb,
@@ -142,6 +147,11 @@ void free_device(Ctx& c) {
   c.norm_host = nullptr;
   if (c.khost) cudaFreeHost(c.khost);
   c.khost = nullptr;
+  if (c.mkhost) cudaFreeHost(c.mkhost);
+  c.mkhost = nullptr;
+  c.mkV = c.mkZ = c.mkw = c.mkzero = c.mkpart = c.mkdev = nullptr;
+  c.mkz32 = c.mkw32 = c.mkzero32 = nullptr;
+  c.mk_cap = c.mk_nr = 0;
   c.kV = c.kZ = c.kw = c.kzero = c.kpart = c.kdots = nullptr;
   c.kcap = 0;
   if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
@@ -603,14 +613,14 @@ void enqueue_cycle_mr(Ctx& c, int prec, int l, int nr, void* x, const void* b, c
         int n = D.cstart[col + 1] - D.cstart[col];
         if (n <= 0) continue;
         ck(launch_element_mrhs(c.pat, prec, nr, MODE_GS, D.cstart[col], n, D.perm, D.nbr, D.cpl[prec], D.inv[prec],
-                               b, x, nullptr, st),
+                               b, x, nullptr, st, c.mrhs_tensor),
            "gs launch");
         c.launches++;
       }
   };
   smooth(c.nu1);
   ck(launch_element_mrhs(c.pat, prec, nr, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[prec], D.dia[prec], b, x,
-                         D.mr[vi], st),
+                         D.mr[vi], st, c.mrhs_tensor),
      "residual launch");
   ck(launch_restrict_mr(vi == 0, c.d, c.s, c.nb, nr, Dc.n, D.n, Dc.ne, c.child_P[vi], D.mr[vi], Dc.mb[vi], st),
      "restrict launch");
@@ -640,7 +650,7 @@ void enqueue_mr_iteration(Ctx& c, int nr, int inner, cudaStream_t st) {
     const void* rin = c.mRb;
     if (k > 0) {
       ck(launch_element_mrhs(c.pat, prec, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[prec], D0.dia[prec],
-                             c.mRb, c.mAcc, c.mRin, st),
+                             c.mRb, c.mAcc, c.mRin, st, c.mrhs_tensor),
          "inner residual");
       c.launches++;
       rin = c.mRin;
@@ -653,11 +663,236 @@ void enqueue_mr_iteration(Ctx& c, int nr, int inner, cudaStream_t st) {
   ck(launch_axpy(1, vi == 0, m0, c.mX, c.mAcc, st), "axpy");
   c.launches++;
   ck(launch_element_mrhs(c.pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0], c.mB, c.mX,
-                         c.mR, st),
+                         c.mR, st, c.mrhs_tensor),
      "residual64");
   ck(launch_sumsq_mr(level_ne(c, 0) * c.nb, nr, c.mR, c.mPart, c.mNorm, st), "norms");
   c.launches += 3;
   ck(cudaMemcpyAsync(c.norm_host, c.mNorm, nr * sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
+}
+
+// ---- lockstep flexible GMRES for several right-hand sides ----------------------
+// nr Krylov sequences advance together on interleaved vectors: one multi-RHS
+// V-cycle per Arnoldi step preconditions all of them (one record stream for
+// nr products), one FP64 multi-RHS residual kernel forms A z for all of
+// them; dots, norms and Givens rotations stay per right-hand side.  A
+// right-hand side that has converged keeps zero basis vectors from then on.
+void ensure_krylov_mr(Ctx& c, int nr, int m) {
+  if (c.mkV && c.mk_cap >= m && c.mk_nr == nr) return;
+  const int64_t n = level_ne(c, 0) * c.nb * nr;
+  c.mkV = (double*)dalloc(c, (size_t)(m + 1) * n * 8);
+  c.mkZ = (double*)dalloc(c, (size_t)m * n * 8);
+  c.mkw = (double*)dalloc(c, (size_t)n * 8);
+  c.mkzero = (double*)dalloc(c, (size_t)n * 8);
+  ck(cudaMemset(c.mkzero, 0, (size_t)n * 8), "memset");
+  c.mkpart = (double*)dalloc(c, (size_t)1024 * 256 * 8);
+  c.mkdev = (double*)dalloc(c, 3 * 256 * 8);
+  if (!c.mkhost) ck(cudaMallocHost(&c.mkhost, 3 * 256 * sizeof(double)), "cudaMallocHost");
+  if (c.precision != STK_FP64) {
+    c.mkz32 = (float*)dalloc(c, (size_t)n * 4);
+    c.mkw32 = (float*)dalloc(c, (size_t)n * 4);
+    c.mkzero32 = (float*)dalloc(c, (size_t)n * 4);
+    ck(cudaMemset(c.mkzero32, 0, (size_t)n * 4), "memset");
+  }
+  c.mk_cap = m;
+  c.mk_nr = nr;
+}
+
+// z = V(0, v) for all right-hand sides (FP64 interleaved in and out).
+void precondition_mr(Ctx& c, int nr, const double* v, double* z, cudaStream_t st) {
+  const int prec = c.precision, vi = prec == STK_FP64 ? 0 : 1;
+  const int64_t n = level_ne(c, 0) * c.nb * nr;
+  DevLevel& D0 = c.dev[0];
+  if (vi == 0) {
+    ck(cudaMemsetAsync(z, 0, (size_t)n * 8, st), "memset");
+    enqueue_cycle_mr(c, prec, 0, nr, z, v, st);
+    return;
+  }
+  ck(launch_convert(0, 1, n, c.mRin, v, st), "convert");
+  ck(cudaMemsetAsync(D0.mx[1], 0, (size_t)n * 4, st), "memset");
+  enqueue_cycle_mr(c, prec, 0, nr, D0.mx[1], c.mRin, st);
+  ck(launch_convert(1, 0, n, z, D0.mx[1], st), "convert");
+  c.launches += 2;
+}
+
+// out[i * nr + q] = V_i . w over right-hand side q, i < k (host copy).
+void mr_dots(Ctx& c, int nr, int k, const double* V, const double* w, double* out, cudaStream_t st) {
+  const int64_t n = level_ne(c, 0) * c.nb * nr;
+  ck(launch_multidot_mr(n, nr, k, V, n, w, c.mkpart, c.mkdev, st), "multidot");
+  c.launches += 2;
+  ck(cudaMemcpyAsync(c.mkhost, c.mkdev, (size_t)k * nr * 8, cudaMemcpyDeviceToHost, st), "copy dots");
+  ck(cudaStreamSynchronize(st), "sync");
+  std::copy(c.mkhost, c.mkhost + (size_t)k * nr, out);
+}
+
+// w = alpha w + sum_i coef[i * nr + q] V_i (per right-hand side q).
+void mr_axpy(Ctx& c, int nr, int k, double alpha, const double* coef, const double* V, double* w, cudaStream_t st) {
+  const int64_t n = level_ne(c, 0) * c.nb * nr;
+  double* hc = c.mkhost + 256;
+  std::copy(coef, coef + (size_t)k * nr, hc);
+  ck(cudaMemcpyAsync(c.mkdev + 256, hc, (size_t)std::max(k * nr, 1) * 8, cudaMemcpyHostToDevice, st), "copy coef");
+  ck(launch_multiaxpy_mr(n, nr, k, alpha, c.mkdev + 256, V, n, w, st), "multiaxpy");
+  c.launches++;
+  ck(cudaStreamSynchronize(st), "sync");   // hc is reused by the next call
+}
+
+// y = s[q] x (per right-hand side q).
+void mr_scale(Ctx& c, int nr, const double* sc, const double* x, double* y, cudaStream_t st) {
+  const int64_t n = level_ne(c, 0) * c.nb * nr;
+  double* hs = c.mkhost + 512;
+  std::copy(sc, sc + nr, hs);
+  ck(cudaMemcpyAsync(c.mkdev + 512, hs, (size_t)nr * 8, cudaMemcpyHostToDevice, st), "copy scales");
+  ck(launch_scale_mr(n, nr, c.mkdev + 512, x, y, st), "scale");
+  c.launches++;
+  ck(cudaStreamSynchronize(st), "sync");
+}
+
+// squared norms per right-hand side (host copy, nr entries).
+void mr_norms(Ctx& c, int nr, const double* v, double* out, cudaStream_t st) {
+  ck(launch_sumsq_mr(level_ne(c, 0) * c.nb, nr, v, c.mPart, c.mNorm, st), "norms");
+  c.launches += 2;
+  ck(cudaMemcpyAsync(c.mkhost + 768 - 16, c.mNorm, (size_t)nr * 8, cudaMemcpyDeviceToHost, st), "copy norms");
+  ck(cudaStreamSynchronize(st), "sync");
+  std::copy(c.mkhost + 768 - 16, c.mkhost + 768 - 16 + nr, out);
+}
+
+// On entry c.mR = B - A X and rel[q] its relative norms; returns the number
+// of Arnoldi steps, X (c.mX) updated and rel[q] the final true residuals.
+int fgmres_mr(Ctx& c, int nr, int nrhs, double rtol, int maxit, double* hist, const std::vector<double>& bn,
+              std::vector<double>& rel, cudaStream_t st) {
+  const int m = std::max(1, std::min(c.restart, 256 / nr));
+  ensure_krylov_mr(c, nr, m);
+  // refined variant: FP32 Krylov matvec, each right-hand side's cycle trusted
+  // for a 1e-5 reduction before the FP64 residual restarts it
+  const bool refined = c.solver == 2 && c.precision != STK_FP64;
+  const int64_t n = level_ne(c, 0) * c.nb * nr;
+  DevLevel& D0 = c.dev[0];
+  std::vector<double> H((size_t)nr * (m + 1) * m), g((size_t)nr * (m + 1)), cs((size_t)nr * m),
+      sn((size_t)nr * m), h((size_t)(m + 1) * nr), h2((size_t)(m + 1) * nr), coef((size_t)(m + 1) * nr),
+      hn(nr), scl(nr), beta(nr);
+  std::vector<int> kq(nr, 0);
+  std::vector<char> active(nr, 0);
+  auto Hq = [&](int q, int i, int j) -> double& { return H[((size_t)q * (m + 1) + i) * m + j]; };
+  int it = 0;
+  auto any_left = [&]() {
+    for (int q = 0; q < nrhs; ++q)
+      if (!(rel[q] <= rtol)) return true;
+    return false;
+  };
+  while (any_left() && it < maxit) {
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    for (int q = 0; q < nr; ++q) {
+      beta[q] = rel[q] * (q < nrhs ? bn[q] : 0.0);
+      active[q] = q < nrhs && !(rel[q] <= rtol) && beta[q] > 0;
+      scl[q] = active[q] ? 1.0 / beta[q] : 0.0;
+      g[(size_t)q * (m + 1)] = active[q] ? beta[q] : 0.0;
+      kq[q] = 0;
+    }
+    mr_scale(c, nr, scl.data(), c.mR, c.mkV, st);
+    int k = 0;
+    for (int j = 0; j < m && it < maxit; ++j) {
+      double* vj = c.mkV + (size_t)j * n;
+      double* zj = c.mkZ + (size_t)j * n;
+      precondition_mr(c, nr, vj, zj, st);
+      // w' = 0 - A z_j (FP64, or FP32 blocks and vectors in the refined
+      // variant); classical Gram-Schmidt twice on w = -w'
+      if (refined) {
+        ck(launch_convert(0, 1, n, c.mkz32, zj, st), "convert");
+        ck(launch_element_mrhs(c.pat, STK_FP32, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[STK_FP32],
+                               D0.dia[STK_FP32], c.mkzero32, c.mkz32, c.mkw32, st, 0),   // exact FP32 sums
+           "matvec32");
+        ck(launch_convert(1, 0, n, c.mkw, c.mkw32, st), "convert");
+        c.launches += 3;
+      } else {
+        ck(launch_element_mrhs(c.pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0],
+                               c.mkzero, zj, c.mkw, st, c.mrhs_tensor),
+           "matvec64");
+        c.launches++;
+      }
+      mr_dots(c, nr, j + 1, c.mkV, c.mkw, h.data(), st);
+      for (size_t u = 0; u < (size_t)(j + 1) * nr; ++u) {
+        h[u] = -h[u];
+        coef[u] = -h[u];
+      }
+      mr_axpy(c, nr, j + 1, -1.0, coef.data(), c.mkV, c.mkw, st);
+      mr_dots(c, nr, j + 1, c.mkV, c.mkw, h2.data(), st);
+      for (size_t u = 0; u < (size_t)(j + 1) * nr; ++u) {
+        h[u] += h2[u];
+        coef[u] = -h2[u];
+      }
+      mr_axpy(c, nr, j + 1, 1.0, coef.data(), c.mkV, c.mkw, st);
+      mr_norms(c, nr, c.mkw, hn.data(), st);
+      for (int q = 0; q < nr; ++q) {
+        hn[q] = std::sqrt(hn[q]);
+        scl[q] = active[q] && hn[q] > 0 && std::isfinite(hn[q]) ? 1.0 / hn[q] : 0.0;
+      }
+      mr_scale(c, nr, scl.data(), c.mkw, c.mkV + (size_t)(j + 1) * n, st);
+      ++it;
+      k = j + 1;
+      for (int q = 0; q < nrhs; ++q) {
+        if (!active[q]) {
+          if (hist) hist[(size_t)it * nrhs + q] = rel[q];
+          continue;
+        }
+        if (!std::isfinite(hn[q])) {
+          rel[q] = hn[q];
+          return it;
+        }
+        for (int i = 0; i <= j; ++i) Hq(q, i, j) = h[(size_t)i * nr + q];
+        Hq(q, j + 1, j) = hn[q];
+        double* gq = &g[(size_t)q * (m + 1)];
+        double* cq = &cs[(size_t)q * m];
+        double* sq = &sn[(size_t)q * m];
+        for (int i = 0; i < j; ++i) {
+          const double a = Hq(q, i, j), bb = Hq(q, i + 1, j);
+          Hq(q, i, j) = cq[i] * a + sq[i] * bb;
+          Hq(q, i + 1, j) = -sq[i] * a + cq[i] * bb;
+        }
+        const double a = Hq(q, j, j), bb = Hq(q, j + 1, j);
+        const double den = std::hypot(a, bb);
+        cq[j] = den > 0 ? a / den : 1.0;
+        sq[j] = den > 0 ? bb / den : 0.0;
+        Hq(q, j, j) = den;
+        Hq(q, j + 1, j) = 0.0;
+        gq[j + 1] = -sq[j] * gq[j];
+        gq[j] = cq[j] * gq[j];
+        kq[q] = j + 1;
+        rel[q] = std::fabs(gq[j + 1]) / bn[q];
+        if (hist) hist[(size_t)it * nrhs + q] = rel[q];
+        if (rel[q] <= rtol || (refined && std::fabs(gq[j + 1]) <= 1e-5 * beta[q])) active[q] = 0;
+      }
+      bool any = false;
+      for (int q = 0; q < nrhs; ++q) any = any || active[q];
+      if (!any) break;
+    }
+    // X += Z y_q per right-hand side, y_q from its own triangular system
+    std::fill(coef.begin(), coef.end(), 0.0);
+    for (int q = 0; q < nrhs; ++q) {
+      const int kk = kq[q];
+      const double* gq = &g[(size_t)q * (m + 1)];
+      std::vector<double> y(kk);
+      for (int i = kk - 1; i >= 0; --i) {
+        double acc = gq[i];
+        for (int jj = i + 1; jj < kk; ++jj) acc -= Hq(q, i, jj) * y[jj];
+        y[i] = Hq(q, i, i) != 0 ? acc / Hq(q, i, i) : 0.0;
+      }
+      for (int i = 0; i < kk; ++i) coef[(size_t)i * nr + q] = y[i];
+    }
+    mr_axpy(c, nr, k, 1.0, coef.data(), c.mkZ, c.mX, st);
+    // true FP64 residual and its norms
+    ck(launch_element_mrhs(c.pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0], c.mB,
+                           c.mX, c.mR, st, c.mrhs_tensor),
+       "residual64");
+    c.launches++;
+    std::vector<double> r2(nr);
+    mr_norms(c, nr, c.mR, r2.data(), st);
+    for (int q = 0; q < nrhs; ++q) {
+      rel[q] = std::sqrt(r2[q]) / bn[q];
+      if (hist) hist[(size_t)it * nrhs + q] = rel[q];
+      if (!std::isfinite(rel[q])) return it;
+    }
+  }
+  return it;
 }
 
 // ---- flexible GMRES with the V-cycle as right preconditioner ----------------
@@ -1474,6 +1709,16 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
   });
 }
 
+int stk_set_mrhs_tensor(stk_ctx* c, int on) {
+  return guard(c, [&]() -> int {
+    c->mrhs_tensor = on ? 1 : 0;
+    if (c->mgraph) cudaGraphExecDestroy(c->mgraph);
+    c->mgraph = nullptr;
+    c->mgraph_key[0] = -1;
+    return STK_OK;
+  });
+}
+
 int stk_set_solver(stk_ctx* c, int method, int restart) {
   return guard(c, [&]() -> int {
     if (method < 0 || method > 2 || restart < 1 || restart > 100)
@@ -1513,7 +1758,7 @@ int stk_solve_multi(stk_ctx* c, double* X, const double* B, int nrhs, double rto
     for (int q = 0; q < nrhs; ++q) bn[q] = c->norm_host[q] > 0 ? std::sqrt(c->norm_host[q]) : 1.0;
     DevLevel& D0 = c->dev[0];
     ck(launch_element_mrhs(c->pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0], c->mB,
-                           c->mX, c->mR, st),
+                           c->mX, c->mR, st, c->mrhs_tensor),
        "residual64");
     ck(launch_sumsq_mr(m, nr, c->mR, c->mPart, c->mNorm, st), "norms");
     c->launches += 3;
@@ -1531,6 +1776,17 @@ int stk_solve_multi(stk_ctx* c, double* X, const double* B, int nrhs, double rto
     std::vector<double> rel0;
     bool done = check(0);
     rel0 = rel;
+    if (c->solver >= 1) {
+      // flexible GMRES in lockstep over the right-hand sides
+      int it = done ? 0 : fgmres_mr(*c, nr, nrhs, rtol, maxit, hist, bn, rel, st);
+      ck(launch_interleave(0, m, nr, nrhs, 0, X, c->mX, st), "deinterleave");
+      c->launches++;
+      ck(cudaStreamSynchronize(st), "sync");
+      if (iters_out) *iters_out = it;
+      for (int q = 0; q < nrhs; ++q)
+        if (!std::isfinite(rel[q]) || rel[q] > 1e6 * rel0[q]) return fail(c, STK_ERR_DIVERGED, "outer iteration diverged");
+      return STK_OK;
+    }
     int key[3] = {nr, inner, c->precision};
     if (!c->mgraph || c->mgraph_key[0] != key[0] || c->mgraph_key[1] != key[1] || c->mgraph_key[2] != key[2]) {
       if (c->mgraph) cudaGraphExecDestroy(c->mgraph);

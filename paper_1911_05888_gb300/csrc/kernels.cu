@@ -1409,6 +1409,100 @@ cudaError_t launch_scale(int64_t n, double s, const double* x, double* y, cudaSt
   return cudaGetLastError();
 }
 
+// ---- Krylov vectors of several right-hand sides ---------------------------------
+// Interleaved vectors [element][row][rhs] hold nr independent Krylov
+// sequences; entry e belongs to right-hand side e % nr.  With a grid stride
+// that is a multiple of nr (a power of two <= 8), every thread stays on one
+// right-hand side, and the block reduction keeps the nr residues apart by
+// stopping at stride nr.
+// part[(blk * k + i) * nr + q] = block blk's share of sum_{e % nr == q} V_i[e] w[e].
+__global__ void multidot_mr_kernel(int64_t n, int nr, int k, const double* __restrict__ V, int64_t ldv,
+                                   const double* __restrict__ w, double* __restrict__ part) {
+  __shared__ double sh[8][256];
+  for (int i0 = 0; i0 < k; i0 += 8) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int ni = min(8, k - i0);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const double we = w[e];
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t < ni) acc[t] += V[(int64_t)(i0 + t) * ldv + e] * we;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) sh[t][threadIdx.x] = acc[t];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s >= nr; s >>= 1) {
+      if (threadIdx.x < s)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) sh[t][threadIdx.x] += sh[t][threadIdx.x + s];
+      __syncthreads();
+    }
+    for (int u = threadIdx.x; u < ni * nr; u += blockDim.x) {
+      const int t = u / nr, q = u - t * nr;
+      part[((int64_t)blockIdx.x * k + i0 + t) * nr + q] = sh[t][q];
+    }
+    __syncthreads();
+  }
+}
+
+// out[i * nr + q] = sum over blocks of part[(blk * k + i) * nr + q]
+__global__ void multidot_mr_final_kernel(int k, int nr, int nblk, const double* __restrict__ part,
+                                         double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int iq = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += part[(int64_t)b * k * nr + iq];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[iq] = sh[0];
+}
+
+// w[e] = alpha w[e] + sum_i coef[i * nr + e % nr] V_i[e]   (k * nr <= 256)
+__global__ void multiaxpy_mr_kernel(int64_t n, int nr, int k, double alpha, const double* __restrict__ coef,
+                                    const double* __restrict__ V, int64_t ldv, double* __restrict__ w) {
+  __shared__ double c[256];
+  for (int i = threadIdx.x; i < k * nr; i += blockDim.x) c[i] = coef[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % nr);
+    double acc = alpha * w[e];
+    for (int i = 0; i < k; ++i) acc += c[i * nr + q] * V[(int64_t)i * ldv + e];
+    w[e] = acc;
+  }
+}
+
+// y[e] = s[e % nr] x[e]
+__global__ void scale_mr_kernel(int64_t n, int nr, const double* __restrict__ s, const double* __restrict__ x,
+                                double* __restrict__ y) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = s[i % nr] * x[i];
+}
+
+cudaError_t launch_multidot_mr(int64_t n, int nr, int k, const double* V, int64_t ldv, const double* w,
+                               double* part, double* out, cudaStream_t st) {
+  if (nr < 1 || nr > 8 || (nr & (nr - 1)) || k < 1 || k * nr > 256) return cudaErrorInvalidValue;
+  multidot_mr_kernel<<<kDotBlocks, 256, 0, st>>>(n, nr, k, V, ldv, w, part);
+  multidot_mr_final_kernel<<<k * nr, 256, 0, st>>>(k, nr, kDotBlocks, part, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multiaxpy_mr(int64_t n, int nr, int k, double alpha, const double* coef, const double* V,
+                                int64_t ldv, double* w, cudaStream_t st) {
+  if (nr < 1 || k < 0 || k * nr > 256) return cudaErrorInvalidValue;
+  multiaxpy_mr_kernel<<<num_sms() * 8, 256, 0, st>>>(n, nr, k, alpha, coef, V, ldv, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_mr(int64_t n, int nr, const double* s, const double* x, double* y, cudaStream_t st) {
+  scale_mr_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, nr, s, x, y);
+  return cudaGetLastError();
+}
+
 }  // namespace stk
 
 namespace stk {
@@ -1580,7 +1674,257 @@ static void prepare_mrhs_t() {
   prepare_mrhs_s<TS, TX, 27, NR>();
 }
 
+// ---- eight right-hand sides on the tensor cores --------------------------------
+// With eight right-hand sides every element product is a small dense GEMM:
+// each s x s coupling sub-block times the gathered s x 8 neighbour values,
+// and the nb x nb block times the nb x 8 values g (or x_i).  One warp per
+// element computes them with mma.sync m16n8k8 on TF32 operands: the task-rows
+// are cut into 16-row tiles (a tile that straddles tasks is multiplied once
+// per task, with the other task's rows masked to zero, since each task has
+// its own neighbour values), K runs over the sub-block's s columns in steps
+// of 8 (columns >= s masked).  Each FP32 operand is split into two TF32
+// parts and three products are accumulated (lo*hi + hi*lo + hi*hi), which
+// keeps about FP32 accuracy in the FP32 accumulator.  A fragments are read
+// straight from the column-major FP32 records (a quarter of the warp reads 8
+// consecutive rows of one column: one full 32-byte sector per load), B
+// fragments from the warp's shared memory.  The coupling tiles subtract
+// their products from g in shared memory; the dense tiles write x_i (colour
+// step) or r_i (residual) from the accumulators.
+constexpr int kTcWarps = 4;   // elements (warps) per CTA of element_mrhs_tc_kernel
+constexpr int kTcGroup = 4;   // coupling tiles whose A fragments are loaded together
+
+__device__ inline uint32_t f32_to_tf32(float f) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+  return r;
+}
+
+__device__ inline void mma_m16n8k8_tf32(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// d += A B with A (4 fragment values) and B (2) split into TF32 hi + lo parts.
+__device__ inline void mma_3xtf32(float* d, const float* af, const float* bf) {
+  uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    ah[i] = f32_to_tf32(af[i]);
+    al[i] = f32_to_tf32(af[i] - __uint_as_float(ah[i]));
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    bh[i] = f32_to_tf32(bf[i]);
+    bl[i] = f32_to_tf32(bf[i] - __uint_as_float(bh[i]));
+  }
+  mma_m16n8k8_tf32(d, al, bh);
+  mma_m16n8k8_tf32(d, ah, bl);
+  mma_m16n8k8_tf32(d, ah, bh);
+}
+
+template <int S>
+__global__ void __launch_bounds__(32 * kTcWarps) element_mrhs_tc_kernel(const __grid_constant__ Pattern pat, int mode,
+                                                                      int pos0, int npos,
+                                                                      const int* __restrict__ perm,
+                                                                      const int* __restrict__ nbr,
+                                                                      const float* __restrict__ cpl,
+                                                                      const float* __restrict__ mat,
+                                                                      const float* __restrict__ b, float* x,
+                                                                      float* rout) {
+  constexpr int NR = 8;
+  const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int words = (pat.NG * S + 2 * NBP) * NR + kMaxGather;
+  extern __shared__ __align__(16) float tc_smem[];
+  float* Xs = tc_smem + (size_t)wid * words;   // [NG * S][NR] gathered neighbour values
+  float* g = Xs + pat.NG * S * NR;              // [NBP][NR]   b_i, then g = b_i - sum_j A_ij x_j
+  float* xi = g + NBP * NR;                     // [NBP][NR]   x_i (residual)
+  int* gj = reinterpret_cast<int*>(xi + NBP * NR);   // [NG] neighbour element of each gathered slot
+  for (int pos = pos0 + blockIdx.x * kTcWarps + wid; pos < pos0 + npos; pos += gridDim.x * kTcWarps) {
+    const int e = perm[pos];
+    const int* nbe = nbr + (size_t)pos * pat.NO;
+    for (int gi = lane; gi < pat.NG; gi += 32) gj[gi] = nbe[pat.g_o[gi]];
+    __syncwarp();
+    // the eight values of one (slot, mode) are 32 contiguous bytes: two
+    // 16-byte loads, four of them in flight per lane (neighbours belong to
+    // other colours: not written by this launch, read-only path)
+    const int nv = pat.NG * S * 2;
+    for (int v0 = 0; v0 < nv; v0 += 32 * 4) {
+      float4 val[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int v = v0 + u * 32 + lane;
+        val[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (v < nv) {
+          const int gc = v >> 1, gi = gc / S, ci = gc - gi * S;
+          const int j = gj[gi];
+          if (j >= 0)
+            val[u] = __ldg(reinterpret_cast<const float4*>(x + ((size_t)j * nb + pat.g_cv[gi] * S + ci) * NR) +
+                           (v & 1));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int v = v0 + u * 32 + lane;
+        if (v < nv) reinterpret_cast<float4*>(Xs)[v] = val[u];
+      }
+    }
+    for (int i = lane; i < NBP * NR; i += 32) {
+      const bool in = i < nb * NR;
+      g[i] = in ? b[(size_t)e * nb * NR + i] : 0.f;
+      xi[i] = (in && mode == MODE_RESID) ? x[(size_t)e * nb * NR + i] : 0.f;
+    }
+    __syncwarp();
+    // coupling tiles: g -= A_t X_slot(t) for every task t.  The A fragments
+    // of kTcGroup tiles are loaded before any of their products, so that a
+    // warp keeps that many tiles' loads in flight.
+    const float* rec = cpl + (size_t)pos * S * TRP;
+    constexpr int KT = (S + 7) / 8;
+    const int ntiles = (TR + 15) / 16;
+    for (int tb = 0; tb < ntiles; tb += kTcGroup) {
+      float af[kTcGroup][KT][4];
+#pragma unroll
+      for (int u = 0; u < kTcGroup; ++u) {
+        const int ra = (tb + u) * 16 + gid, rb = ra + 8;
+        const bool oka = tb + u < ntiles && ra < TRP, okb = tb + u < ntiles && rb < TRP;
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) {
+          const int ca = kt * 8 + tig, cb = ca + 4;
+          af[u][kt][0] = (oka && ca < S) ? __ldcs(rec + (size_t)ca * TRP + ra) : 0.f;
+          af[u][kt][1] = (okb && ca < S) ? __ldcs(rec + (size_t)ca * TRP + rb) : 0.f;
+          af[u][kt][2] = (oka && cb < S) ? __ldcs(rec + (size_t)cb * TRP + ra) : 0.f;
+          af[u][kt][3] = (okb && cb < S) ? __ldcs(rec + (size_t)cb * TRP + rb) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kTcGroup; ++u) {
+        if (tb + u >= ntiles) break;
+        const int m0 = (tb + u) * 16;
+        const int t_first = m0 / S, t_last = min(pat.T - 1, (m0 + 15) / S);
+        for (int t = t_first; t <= t_last; ++t) {
+          const int r_lo = t * S - m0, r_hi = r_lo + S;   // tile rows of task t: [r_lo, r_hi) within [0, 16)
+          const bool in_a = gid >= r_lo && gid < r_hi, in_b = gid + 8 >= r_lo && gid + 8 < r_hi;
+          const float* xs = Xs + pat.task_g[t] * S * NR;
+          float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int kt = 0; kt < KT; ++kt) {
+            const int ca = kt * 8 + tig, cb = ca + 4;
+            float a[4], bf[2];
+            a[0] = in_a ? af[u][kt][0] : 0.f;
+            a[1] = in_b ? af[u][kt][1] : 0.f;
+            a[2] = in_a ? af[u][kt][2] : 0.f;
+            a[3] = in_b ? af[u][kt][3] : 0.f;
+            bf[0] = ca < S ? xs[ca * NR + gid] : 0.f;
+            bf[1] = cb < S ? xs[cb * NR + gid] : 0.f;
+            mma_3xtf32(d, a, bf);
+          }
+          const int rv = pat.task_rv[t];
+          if (in_a) {
+            float* gr = g + (rv * S + (m0 + gid - t * S)) * NR + 2 * tig;
+            gr[0] -= d[0];
+            gr[1] -= d[1];
+          }
+          if (in_b) {
+            float* gr = g + (rv * S + (m0 + gid + 8 - t * S)) * NR + 2 * tig;
+            gr[0] -= d[2];
+            gr[1] -= d[3];
+          }
+          __syncwarp();
+        }
+      }
+    }
+    // dense block: x_i = A_ii^{-1} g (colour step) or r_i = g - A_ii x_i
+    const float* mrec = mat + (size_t)pos * nb * NBP;
+    const float* vin = (mode == MODE_GS) ? g : xi;
+    constexpr int KD = (4 * S + 7) / 8;   // k steps over nb <= (d + 1) S <= 4 S columns
+    for (int m0 = 0; m0 < nb; m0 += 16) {
+      const int ra = m0 + gid, rb = m0 + gid + 8;
+      float am[KD][4];
+#pragma unroll
+      for (int kt = 0; kt < KD; ++kt) {
+        const int ca = kt * 8 + tig, cb = ca + 4;
+        am[kt][0] = (ra < NBP && ca < nb) ? __ldcs(mrec + (size_t)ca * NBP + ra) : 0.f;
+        am[kt][1] = (rb < NBP && ca < nb) ? __ldcs(mrec + (size_t)ca * NBP + rb) : 0.f;
+        am[kt][2] = (ra < NBP && cb < nb) ? __ldcs(mrec + (size_t)cb * NBP + ra) : 0.f;
+        am[kt][3] = (rb < NBP && cb < nb) ? __ldcs(mrec + (size_t)cb * NBP + rb) : 0.f;
+      }
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kt = 0; kt < KD; ++kt) {
+        if (kt * 8 >= nb) break;
+        const int ca = kt * 8 + tig, cb = ca + 4;
+        float bf[2];
+        bf[0] = ca < nb ? vin[ca * NR + gid] : 0.f;
+        bf[1] = cb < nb ? vin[cb * NR + gid] : 0.f;
+        mma_3xtf32(d, am[kt], bf);
+      }
+      const int q0 = 2 * tig;
+      if (ra < nb) {
+        const size_t o = ((size_t)e * nb + ra) * NR + q0;
+        if (mode == MODE_GS) {
+          x[o] = d[0];
+          x[o + 1] = d[1];
+        } else {
+          rout[o] = g[ra * NR + q0] - d[0];
+          rout[o + 1] = g[ra * NR + q0 + 1] - d[1];
+        }
+      }
+      if (rb < nb) {
+        const size_t o = ((size_t)e * nb + rb) * NR + q0;
+        if (mode == MODE_GS) {
+          x[o] = d[2];
+          x[o + 1] = d[3];
+        } else {
+          rout[o] = g[rb * NR + q0] - d[2];
+          rout[o + 1] = g[rb * NR + q0 + 1] - d[3];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int S>
+static cudaError_t launch_mrhs_tc_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
+                                   const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                   cudaStream_t st) {
+  if (npos <= 0) return cudaSuccess;
+  const size_t smem = (size_t)kTcWarps * ((pat.NG * S + 2 * pat.NBP) * 8 + kMaxGather) * sizeof(float);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (220 * 1024) / smem));
+  const int grid = std::min((npos + kTcWarps - 1) / kTcWarps, num_sms() * per_sm);
+  element_mrhs_tc_kernel<S><<<grid, 32 * kTcWarps, smem, st>>>(pat, mode, pos0, npos, perm, nbr, (const float*)cpl,
+                                                              (const float*)mat, (const float*)b, (float*)x,
+                                                              (float*)r);
+  return cudaGetLastError();
+}
+
+// Eight right-hand sides, FP32 records: the tensor-core kernel.
+cudaError_t launch_element_mrhs_tc(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
+                                   const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                   cudaStream_t st) {
+  switch (pat.s) {
+    case 4: return launch_mrhs_tc_s<4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 8: return launch_mrhs_tc_s<8>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 9: return launch_mrhs_tc_s<9>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 16: return launch_mrhs_tc_s<16>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 25: return launch_mrhs_tc_s<25>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    case 27: return launch_mrhs_tc_s<27>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 void prepare_mrhs_kernels() {
+  cudaFuncSetAttribute(element_mrhs_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc_kernel<25>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc_kernel<27>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
   prepare_mrhs_t<double, double, 4>();
   prepare_mrhs_t<double, double, 8>();
   prepare_mrhs_t<float, float, 4>();
@@ -1589,10 +1933,15 @@ void prepare_mrhs_kernels() {
   prepare_mrhs_t<__nv_bfloat16, float, 8>();
 }
 
-// nr = 4 or 8 (callers pad to one of them).
+// nr = 4 or 8 (callers pad to one of them); tensor != 0 sends eight
+// right-hand sides with FP32 records to the tensor-core kernel.
 cudaError_t launch_element_mrhs(const Pattern& pat, int storage, int nr, int mode, int pos0, int npos,
                                 const int* perm, const int* nbr, const void* cpl, const void* mat, const void* b,
-                                void* x, void* r, cudaStream_t st) {
+                                void* x, void* r, cudaStream_t st, int tensor) {
+  if (tensor && nr == 8 && storage == 1) {
+    cudaError_t e = launch_element_mrhs_tc(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    if (e != cudaErrorInvalidValue) return e;
+  }
   if (nr == 4) {
     switch (storage) {
       case 0: return launch_mrhs_t<double, double, 4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);

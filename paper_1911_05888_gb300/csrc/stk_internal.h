@@ -132,6 +132,12 @@ struct Ctx {
   double* khost = nullptr;    // pinned host staging (dots, coefficients)
   float *kz32 = nullptr, *kw32 = nullptr, *kzero32 = nullptr;   // FP32 matvec of the refined variant
   int kcap = 0;               // restart the buffers were sized for
+  // the same for the lockstep FGMRES of several right-hand sides (interleaved vectors)
+  double *mkV = nullptr, *mkZ = nullptr, *mkw = nullptr, *mkzero = nullptr, *mkpart = nullptr, *mkdev = nullptr;
+  double* mkhost = nullptr;   // pinned staging: dots, coefficients, scales
+  float *mkz32 = nullptr, *mkw32 = nullptr, *mkzero32 = nullptr;   // FP32 matvec of the refined variant
+  int mk_cap = 0, mk_nr = 0;
+  int mrhs_tensor = 1;   // eight right-hand sides with FP32 records: tensor-core kernel
   // V-cycle alone on the level-0 work vectors, as a CUDA graph
   cudaGraphExec_t cycle_graph = nullptr;
   int cycle_graph_prec = -1;

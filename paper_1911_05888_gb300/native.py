@@ -69,6 +69,7 @@ SIGNATURES = {
                         _c_dbl_p, _vp],
     "stk_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "stk_set_wide_launch": [_vp, ctypes.c_int],
+    "stk_set_mrhs_tensor": [_vp, ctypes.c_int],
     "stk_autotune": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _vp],
     "stk_solve_batch": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
                         ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -333,6 +334,9 @@ class Context:
 
     def set_tuning(self, variant, precision, ctas_per_sm=0, stages=0):
         self._check(self.lib.stk_set_tuning(self.h, variant, precision, ctas_per_sm, stages), "stk_set_tuning")
+
+    def set_mrhs_tensor(self, on):
+        self._check(self.lib.stk_set_mrhs_tensor(self.h, 1 if on else 0), "stk_set_mrhs_tensor")
 
     def set_wide_launch(self, max_positions):
         self._check(self.lib.stk_set_wide_launch(self.h, max_positions), "stk_set_wide_launch")

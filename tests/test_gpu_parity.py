@@ -316,7 +316,7 @@ def test_kernel_variants_agree(name, variant):
 
 
 @pytest.mark.parametrize("nrhs", [3, 8])
-@pytest.mark.parametrize("name", ["stress16p3", "3d-mixed-p1"])
+@pytest.mark.parametrize("name", ["stress16p3", "3d-mixed-p1", "3d-unsteady-p2"])
 def test_multi_rhs_iteration_matches_oracle(name, nrhs):
     """One outer iteration for several right-hand sides at once equals, per
     right-hand side, x1 = x0 + V(0, b - A x0) of the oracle (FP64)."""
@@ -348,6 +348,70 @@ def test_multi_rhs_solve_converges(precision, inner):
     x1 = torch.zeros_like(Bd[1])
     gpu64.ctx.solve(x1, Bd[1].contiguous(), rtol=1e-12, maxit=200)
     assert rel(Xd[1].cpu().numpy(), x1.cpu().numpy()) <= 1e-8
+
+
+@pytest.mark.parametrize("precision,method", [(native.FP64, native.FGMRES), (native.FP32, native.FGMRES),
+                                              (native.FP32, native.FGMRES_IR)])
+@pytest.mark.parametrize("name", ["stress16p3", "3d-unsteady-p2"])
+def test_multi_rhs_fgmres_lockstep(name, precision, method):
+    """Several right-hand sides by flexible GMRES in lockstep (one multi-RHS
+    V-cycle per step; the refined variant with an FP32 Krylov matvec):
+    every right-hand side reaches 1e-10, its solution is the
+    single-right-hand-side solution (up to the kernel), and the step count is
+    that of the slowest single solve (+-1; +-3 for the refined variant)."""
+    prob, _, orc = get(name)
+    _, gpu, _ = get(name, precision)
+    nrhs = 6
+    rng = np.random.default_rng(12)
+    B = rng.uniform(-1, 1, (nrhs, prob.n_dofs))
+    Z = trivial_kernel(prob, orc)   # consistent right-hand sides for singular (periodic) operators
+    B -= (B @ Z) @ Z.T
+    Bd = dev(B).reshape(nrhs, -1)
+    Xd = torch.zeros_like(Bd)
+    gpu.ctx.set_solver(method, 30)
+    try:
+        it, hist = gpu.ctx.solve_multi(Xd, Bd, nrhs, rtol=1e-10, maxit=80)
+        assert np.all(hist[-1] <= 1e-10), hist[-1]
+        singles = []
+        for q in range(nrhs):
+            x1 = torch.zeros_like(Bd[q])
+            it1, h1 = gpu.ctx.solve(x1, Bd[q].contiguous(), rtol=1e-10, maxit=80)
+            singles.append(it1)
+            xa, xb = Xd[q].cpu().numpy(), x1.cpu().numpy()
+            assert rel(xa - Z @ (Z.T @ xa), xb - Z @ (Z.T @ xb)) <= 1e-8   # unique up to the kernel
+            r = torch.empty_like(x1)
+            assert gpu.ctx.residual(Xd[q].contiguous(), Bd[q].contiguous(), r, want_norm=True) <= \
+                1e-10 * np.linalg.norm(B[q])
+        assert abs(it - max(singles)) <= (1 if method == native.FGMRES else 3), (it, singles)
+    finally:
+        gpu.ctx.set_solver(native.RICHARDSON, 30)
+
+
+@pytest.mark.parametrize("name", ["stress16p3", "3d-mixed-p1", "3d-unsteady-p2"])
+def test_multi_rhs_tensor_cores_match_cuda_cores(name):
+    """Eight right-hand sides with FP32 blocks: the tensor-core kernel (3xTF32
+    mma.sync) and the CUDA-core kernel give the same outer iteration to
+    FP32-level agreement, and both stay within 1e-4 of the oracle's cycle
+    with FP32-rounded blocks."""
+    prob, _, _ = get(name)
+    _, gpu, _ = get(name, native.FP32)
+    orc32 = multigrid.Multigrid(prob, storage="fp32")
+    nrhs = 8
+    rng = np.random.default_rng(41)
+    B = rng.uniform(-1, 1, (nrhs, prob.n_dofs))
+    out = {}
+    try:
+        for on in (1, 0):
+            gpu.ctx.set_mrhs_tensor(on)
+            Xd = torch.zeros(nrhs, prob.n_dofs, dtype=torch.float64, device="cuda")
+            gpu.ctx.solve_multi(Xd, dev(B).reshape(nrhs, -1), nrhs, rtol=1e-30, maxit=1, inner=1)
+            out[on] = Xd.cpu().numpy()
+    finally:
+        gpu.ctx.set_mrhs_tensor(1)
+    for q in range(nrhs):
+        assert rel(out[1][q], out[0][q]) <= 1e-5
+        ref = orc32.precondition(B[q])
+        assert rel(out[1][q], ref) <= 1e-4
 
 
 def _learned_ctx():
