@@ -583,8 +583,11 @@ def run_batch(args):
     contrasts up to 1e2), each solved from zero to 1e-10 by FGMRES with a
     V(nu, nu) preconditioner, all at once through stk_solve_batch; a step is
     one solve of the whole batch.  The same batch with FP64 blocks follows
-    (the metric's plain comparison), after the first batch is freed."""
+    (the metric's plain comparison), after the first batch is freed.  With
+    --nrhs > 1 every problem carries that many right-hand sides (its
+    manufactured one and seeded random ones), solved together."""
     import threading
+    import numpy as np
     import torch
     from paper_1911_05888_gb300 import native, problems as P
     from paper_1911_05888_gb300.solver import StokesMG
@@ -602,21 +605,33 @@ def run_batch(args):
                 t.start()
             for t in ths:
                 t.join()
+        method = {"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR,
+                  "richardson": native.RICHARDSON}[args.solver]
         for g in out:
             g.ctx.autotune()
-            g.ctx.set_solver(native.FGMRES, args.restart)
+            g.ctx.set_solver(method if precision != native.FP64 or method != native.FGMRES_IR else native.FGMRES,
+                             args.restart)
         return out
+
+    nrhs = max(1, args.nrhs)
+
+    def rhs_of(g, i):
+        b = g.rhs().ravel()
+        if nrhs == 1:
+            return torch.from_numpy(b).cuda()
+        rng = np.random.default_rng(100 + i)
+        return torch.from_numpy(np.concatenate([b] + [rng.uniform(-1, 1, b.size) for _ in range(nrhs - 1)])).cuda()
 
     def measure(gpus, steps, warmup, threads=None):
         threads = args.batch_threads if threads is None else threads
-        bs = [torch.from_numpy(g.rhs().ravel()).cuda() for g in gpus]
+        bs = [rhs_of(g, i) for i, g in enumerate(gpus)]
         xs = [torch.zeros_like(b) for b in bs]
         ctxs = [g.ctx for g in gpus]
 
         def step():
             for x in xs:
                 x.zero_()
-            return native.solve_batch(ctxs, xs, bs, rtol=1e-10, maxit=200, threads=threads)[0]
+            return native.solve_batch(ctxs, xs, bs, nrhs=nrhs, rtol=1e-10, maxit=200, threads=threads)[0]
         for _ in range(warmup):
             step()
         torch.cuda.synchronize()
@@ -629,7 +644,7 @@ def run_batch(args):
         e1.record()
         torch.cuda.synchronize()
         el = e0.elapsed_time(e1) / 1e3
-        units = steps * sum(g.prob.n_dofs * it for g, it in zip(gpus, its))
+        units = steps * nrhs * sum(g.prob.n_dofs * it for g, it in zip(gpus, its))
         launches = sum(c.launch_count() for c in ctxs) - l0
         # end to end: host right-hand sides in, solutions out, every step
         bh = [b.cpu().pin_memory() for b in bs]
@@ -646,8 +661,11 @@ def run_batch(args):
         e2e_s = time.perf_counter() - t0
         worst = 0.0
         for g, x, b in zip(gpus, xs, bs):
-            r = torch.empty_like(b)
-            worst = max(worst, g.ctx.residual(x, b, r, want_norm=True) / torch.linalg.norm(b).item())
+            nd = g.prob.n_dofs
+            for q in range(nrhs):
+                xq, bq = x[q * nd:(q + 1) * nd], b[q * nd:(q + 1) * nd]
+                r = torch.empty_like(bq)
+                worst = max(worst, g.ctx.residual(xq, bq, r, want_norm=True) / torch.linalg.norm(bq).item())
         return el, units, its, launches, e2e_s, sum(b.numel() * 8 for b in bs), worst
 
     t0 = time.perf_counter()
@@ -680,7 +698,7 @@ def run_batch(args):
         "data": "synthetic (manufactured unsteady flows, seeded viscosities)",
         "config": {"workload": "batched-serving-mix-2d-unsteady-viscous-stress", "problems": len(probs),
                    "sizes": [q.n[0] for q in probs], "degrees": [q.p for q in probs], "dofs": dofs,
-                   "nu": [args.nu, args.nu], "outer": "fgmres(%d)" % args.restart, "rtol": 1e-10,
+                   "nu": [args.nu, args.nu], "outer": "fgmres(%d)" % args.restart, "rtol": 1e-10, "nrhs": nrhs,
                    "host_threads": args.batch_threads, "cache": "inputs larger than L2"},
         "iters": its, "worst_rel_residual": worst, "setup_s": round(setup_s, 1),
         "e2e": {"value": units / e2e_s, "unit": "DOF-cycles/s", "h2d_bytes_per_step": nbytes,
