@@ -1683,8 +1683,8 @@ static void prepare_mrhs_t() {
 // per task, with the other task's rows masked to zero, since each task has
 // its own neighbour values), K runs over the sub-block's s columns in steps
 // of 8 (columns >= s masked).  Each FP32 operand is split into two TF32
-// parts and three products are accumulated (lo*hi + hi*lo + hi*hi), which
-// keeps about FP32 accuracy in the FP32 accumulator.  A fragments are read
+// parts (split_tf32) and three products are accumulated (lo*hi + hi*lo +
+// hi*hi), which keeps about FP32 accuracy in the FP32 accumulator.  A fragments are read
 // straight from the column-major FP32 records (a quarter of the warp reads 8
 // consecutive rows of one column: one full 32-byte sector per load), B
 // fragments from the warp's shared memory.  The coupling tiles subtract
@@ -1692,12 +1692,6 @@ static void prepare_mrhs_t() {
 // step) or r_i (residual) from the accumulators.
 constexpr int kTcWarps = 4;   // elements (warps) per CTA of element_mrhs_tc_kernel
 constexpr int kTcGroup = 4;   // coupling tiles whose A fragments are loaded together
-
-__device__ inline uint32_t f32_to_tf32(float f) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
-  return r;
-}
 
 __device__ inline void mma_m16n8k8_tf32(float* d, const uint32_t* a, const uint32_t* b) {
   asm volatile(
@@ -1707,19 +1701,22 @@ __device__ inline void mma_m16n8k8_tf32(float* d, const uint32_t* a, const uint3
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// d += A B with A (4 fragment values) and B (2) split into TF32 hi + lo parts.
+// d += A B with A (4 fragment values) and B (2) split into TF32 hi + lo
+// parts.  hi keeps the sign, exponent and top 10 mantissa bits (the TF32
+// value obtained by truncation), lo = v - hi is exact in FP32 and enters the
+// MMA as TF32 (its low 13 mantissa bits are not used by the tensor core, a
+// truncation), so hi + lo carries about 21 bits of v.
+__device__ inline void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
+  hi = __float_as_uint(v) & 0xffffe000u;
+  lo = __float_as_uint(v - __uint_as_float(hi));
+}
+
 __device__ inline void mma_3xtf32(float* d, const float* af, const float* bf) {
   uint32_t ah[4], al[4], bh[2], bl[2];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    ah[i] = f32_to_tf32(af[i]);
-    al[i] = f32_to_tf32(af[i] - __uint_as_float(ah[i]));
-  }
+  for (int i = 0; i < 4; ++i) split_tf32(af[i], ah[i], al[i]);
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    bh[i] = f32_to_tf32(bf[i]);
-    bl[i] = f32_to_tf32(bf[i] - __uint_as_float(bh[i]));
-  }
+  for (int i = 0; i < 2; ++i) split_tf32(bf[i], bh[i], bl[i]);
   mma_m16n8k8_tf32(d, al, bh);
   mma_m16n8k8_tf32(d, ah, bl);
   mma_m16n8k8_tf32(d, ah, bh);
@@ -1807,7 +1804,9 @@ __global__ void __launch_bounds__(32 * kTcWarps) element_mrhs_tc_kernel(const __
         const int t_first = m0 / S, t_last = min(pat.T - 1, (m0 + 15) / S);
         for (int t = t_first; t <= t_last; ++t) {
           const int r_lo = t * S - m0, r_hi = r_lo + S;   // tile rows of task t: [r_lo, r_hi) within [0, 16)
-          const bool in_a = gid >= r_lo && gid < r_hi, in_b = gid + 8 >= r_lo && gid + 8 < r_hi;
+          // (with S a multiple of 16 every tile is one task: nothing to mask)
+          const bool in_a = (S % 16 == 0) || (gid >= r_lo && gid < r_hi);
+          const bool in_b = (S % 16 == 0) || (gid + 8 >= r_lo && gid + 8 < r_hi);
           const float* xs = Xs + pat.task_g[t] * S * NR;
           float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
