@@ -387,8 +387,10 @@ int stk_set_tuning(stk_ctx* ctx, int variant, int precision, int ctas_per_sm, in
  * element instead of the configured variant: with few elements per launch
  * the time is one element's load latency, which a whole CTA shortens by
  * issuing all of the element's record loads at once.  Same arithmetic per
- * row (FP32/FP64 sums in a different association order).  0 disables it;
- * default 1024.  Errors: STK_ERR_INVALID_ARG for a negative value.
+ * row (FP32/FP64 sums in a different association order).  The same limit
+ * sends eight-right-hand-side tensor-core launches to their four-warps-per-
+ * element kernel.  0 disables it; default 1024.  Errors: STK_ERR_INVALID_ARG
+ * for a negative value.
  */
 int stk_set_wide_launch(stk_ctx* ctx, int max_positions);
 

@@ -45,7 +45,7 @@ void prepare_pipe_kernels();
 void prepare_mrhs_kernels();
 cudaError_t launch_element_mrhs(const Pattern& pat, int storage, int nr, int mode, int pos0, int npos,
                                 const int* perm, const int* nbr, const void* cpl, const void* mat, const void* b,
-                                void* x, void* r, cudaStream_t st, int tensor = 0);
+                                void* x, void* r, cudaStream_t st, int tensor = 0, int tensor_small = 0);
 cudaError_t launch_restrict_mr(int vec64, int d, int s, int nb, int nr, const int* nc, const int* nf, int64_t nec,
                                const void* P, const void* r, void* rc, cudaStream_t st);
 cudaError_t launch_prolong_mr(int vec64, int d, int s, int nb, int nr, const int* nf, const int* nc, int64_t nec,
@@ -613,14 +613,14 @@ void enqueue_cycle_mr(Ctx& c, int prec, int l, int nr, void* x, const void* b, c
         int n = D.cstart[col + 1] - D.cstart[col];
         if (n <= 0) continue;
         ck(launch_element_mrhs(c.pat, prec, nr, MODE_GS, D.cstart[col], n, D.perm, D.nbr, D.cpl[prec], D.inv[prec],
-                               b, x, nullptr, st, c.mrhs_tensor),
+                               b, x, nullptr, st, c.mrhs_tensor, c.wide_max),
            "gs launch");
         c.launches++;
       }
   };
   smooth(c.nu1);
   ck(launch_element_mrhs(c.pat, prec, nr, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[prec], D.dia[prec], b, x,
-                         D.mr[vi], st, c.mrhs_tensor),
+                         D.mr[vi], st, c.mrhs_tensor, c.wide_max),
      "residual launch");
   ck(launch_restrict_mr(vi == 0, c.d, c.s, c.nb, nr, Dc.n, D.n, Dc.ne, c.child_P[vi], D.mr[vi], Dc.mb[vi], st),
      "restrict launch");
@@ -650,7 +650,7 @@ void enqueue_mr_iteration(Ctx& c, int nr, int inner, cudaStream_t st) {
     const void* rin = c.mRb;
     if (k > 0) {
       ck(launch_element_mrhs(c.pat, prec, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[prec], D0.dia[prec],
-                             c.mRb, c.mAcc, c.mRin, st, c.mrhs_tensor),
+                             c.mRb, c.mAcc, c.mRin, st, c.mrhs_tensor, c.wide_max),
          "inner residual");
       c.launches++;
       rin = c.mRin;
@@ -663,7 +663,7 @@ void enqueue_mr_iteration(Ctx& c, int nr, int inner, cudaStream_t st) {
   ck(launch_axpy(1, vi == 0, m0, c.mX, c.mAcc, st), "axpy");
   c.launches++;
   ck(launch_element_mrhs(c.pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0], c.mB, c.mX,
-                         c.mR, st, c.mrhs_tensor),
+                         c.mR, st, c.mrhs_tensor, c.wide_max),
      "residual64");
   ck(launch_sumsq_mr(level_ne(c, 0) * c.nb, nr, c.mR, c.mPart, c.mNorm, st), "norms");
   c.launches += 3;
@@ -805,7 +805,7 @@ int fgmres_mr(Ctx& c, int nr, int nrhs, double rtol, int maxit, double* hist, co
         c.launches += 3;
       } else {
         ck(launch_element_mrhs(c.pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0],
-                               c.mkzero, zj, c.mkw, st, c.mrhs_tensor),
+                               c.mkzero, zj, c.mkw, st, c.mrhs_tensor, c.wide_max),
            "matvec64");
         c.launches++;
       }
@@ -881,7 +881,7 @@ int fgmres_mr(Ctx& c, int nr, int nrhs, double rtol, int maxit, double* hist, co
     mr_axpy(c, nr, k, 1.0, coef.data(), c.mkZ, c.mX, st);
     // true FP64 residual and its norms
     ck(launch_element_mrhs(c.pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0], c.mB,
-                           c.mX, c.mR, st, c.mrhs_tensor),
+                           c.mX, c.mR, st, c.mrhs_tensor, c.wide_max),
        "residual64");
     c.launches++;
     std::vector<double> r2(nr);
@@ -1569,6 +1569,9 @@ int stk_set_wide_launch(stk_ctx* c, int max_positions) {
     if (c->cycle_graph) cudaGraphExecDestroy(c->cycle_graph);
     c->cycle_graph = nullptr;
     c->cycle_graph_prec = -1;
+    if (c->mgraph) cudaGraphExecDestroy(c->mgraph);   // the eight-RHS tensor kernels use the same limit
+    c->mgraph = nullptr;
+    c->mgraph_key[0] = -1;
     return STK_OK;
   });
 }
@@ -1758,7 +1761,7 @@ int stk_solve_multi(stk_ctx* c, double* X, const double* B, int nrhs, double rto
     for (int q = 0; q < nrhs; ++q) bn[q] = c->norm_host[q] > 0 ? std::sqrt(c->norm_host[q]) : 1.0;
     DevLevel& D0 = c->dev[0];
     ck(launch_element_mrhs(c->pat, STK_FP64, nr, MODE_RESID, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[0], D0.dia[0], c->mB,
-                           c->mX, c->mR, st, c->mrhs_tensor),
+                           c->mX, c->mR, st, c->mrhs_tensor, c->wide_max),
        "residual64");
     ck(launch_sumsq_mr(m, nr, c->mR, c->mPart, c->mNorm, st), "norms");
     c->launches += 3;

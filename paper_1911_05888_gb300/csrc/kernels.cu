@@ -1887,6 +1887,147 @@ __global__ void __launch_bounds__(32 * kTcWarps) element_mrhs_tc_kernel(const __
   }
 }
 
+// Latency variant for launches of few elements (coarse levels): one CTA of
+// four warps per element.  The gather is shared by the CTA; warp w computes
+// the coupling tasks of row variable w (their rows of g are disjoint from the
+// other warps'), then the dense tiles w, w + 4, ...  Same arithmetic per
+// product as element_mrhs_tc_kernel; the per-element chain of dependent loads
+// is about a third as long.
+constexpr int kTc4Warps = 4;
+
+template <int S>
+__global__ void __launch_bounds__(32 * kTc4Warps) element_mrhs_tc4_kernel(const __grid_constant__ Pattern pat,
+                                                                        int mode, int pos0, int npos,
+                                                                        const int* __restrict__ perm,
+                                                                        const int* __restrict__ nbr,
+                                                                        const float* __restrict__ cpl,
+                                                                        const float* __restrict__ mat,
+                                                                        const float* __restrict__ b, float* x,
+                                                                        float* rout) {
+  constexpr int NR = 8;
+  constexpr int KT = (S + 7) / 8;
+  const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  extern __shared__ __align__(16) float tc4_smem[];
+  float* Xs = tc4_smem;                  // [NG * S][NR]
+  float* g = Xs + pat.NG * S * NR;       // [NBP][NR]
+  float* xi = g + NBP * NR;              // [NBP][NR]
+  int* gj = reinterpret_cast<int*>(xi + NBP * NR);
+  for (int pos = pos0 + blockIdx.x; pos < pos0 + npos; pos += gridDim.x) {
+    const int e = perm[pos];
+    const int* nbe = nbr + (size_t)pos * pat.NO;
+    for (int gi = tid; gi < pat.NG; gi += 32 * kTc4Warps) gj[gi] = nbe[pat.g_o[gi]];
+    for (int i = tid; i < NBP * NR; i += 32 * kTc4Warps) {
+      const bool in = i < nb * NR;
+      g[i] = in ? b[(size_t)e * nb * NR + i] : 0.f;
+      xi[i] = (in && mode == MODE_RESID) ? x[(size_t)e * nb * NR + i] : 0.f;
+    }
+    __syncthreads();
+    const int nv = pat.NG * S * 2;
+    for (int v = tid; v < nv; v += 32 * kTc4Warps) {
+      const int gc = v >> 1, gi = gc / S, ci = gc - gi * S;
+      const int j = gj[gi];
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j >= 0)
+        val = __ldg(reinterpret_cast<const float4*>(x + ((size_t)j * nb + pat.g_cv[gi] * S + ci) * NR) + (v & 1));
+      reinterpret_cast<float4*>(Xs)[v] = val;
+    }
+    __syncthreads();
+    const float* rec = cpl + (size_t)pos * S * TRP;
+    if (wid <= pat.d) {
+      const int rv = wid;
+      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) {
+        const float* xs = Xs + pat.task_g[t] * S * NR;
+        // tiles of 16 task-rows covering this task's rows [t S, t S + S)
+        for (int m0 = (t * S) / 16 * 16; m0 < t * S + S; m0 += 16) {
+          const int ra = m0 + gid, rb = ra + 8;
+          const bool in_a = ra >= t * S && ra < t * S + S, in_b = rb >= t * S && rb < t * S + S;
+          float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int kt = 0; kt < KT; ++kt) {
+            const int ca = kt * 8 + tig, cb = ca + 4;
+            float a[4], bf[2];
+            a[0] = (in_a && ca < S) ? __ldcs(rec + (size_t)ca * TRP + ra) : 0.f;
+            a[1] = (in_b && ca < S) ? __ldcs(rec + (size_t)ca * TRP + rb) : 0.f;
+            a[2] = (in_a && cb < S) ? __ldcs(rec + (size_t)cb * TRP + ra) : 0.f;
+            a[3] = (in_b && cb < S) ? __ldcs(rec + (size_t)cb * TRP + rb) : 0.f;
+            bf[0] = ca < S ? xs[ca * NR + gid] : 0.f;
+            bf[1] = cb < S ? xs[cb * NR + gid] : 0.f;
+            mma_3xtf32(d, a, bf);
+          }
+          if (in_a) {
+            float* gr = g + (rv * S + (ra - t * S)) * NR + 2 * tig;
+            gr[0] -= d[0];
+            gr[1] -= d[1];
+          }
+          if (in_b) {
+            float* gr = g + (rv * S + (rb - t * S)) * NR + 2 * tig;
+            gr[0] -= d[2];
+            gr[1] -= d[3];
+          }
+          __syncwarp();
+        }
+      }
+    }
+    __syncthreads();
+    const float* mrec = mat + (size_t)pos * nb * NBP;
+    const float* vin = (mode == MODE_GS) ? g : xi;
+    for (int m0 = wid * 16; m0 < nb; m0 += 16 * kTc4Warps) {
+      const int ra = m0 + gid, rb = m0 + gid + 8;
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int k0 = 0; k0 < nb; k0 += 8) {
+        const int ca = k0 + tig, cb = ca + 4;
+        float a[4], bf[2];
+        a[0] = (ra < NBP && ca < nb) ? __ldcs(mrec + (size_t)ca * NBP + ra) : 0.f;
+        a[1] = (rb < NBP && ca < nb) ? __ldcs(mrec + (size_t)ca * NBP + rb) : 0.f;
+        a[2] = (ra < NBP && cb < nb) ? __ldcs(mrec + (size_t)cb * NBP + ra) : 0.f;
+        a[3] = (rb < NBP && cb < nb) ? __ldcs(mrec + (size_t)cb * NBP + rb) : 0.f;
+        bf[0] = ca < nb ? vin[ca * NR + gid] : 0.f;
+        bf[1] = cb < nb ? vin[cb * NR + gid] : 0.f;
+        mma_3xtf32(d, a, bf);
+      }
+      const int q0 = 2 * tig;
+      if (ra < nb) {
+        const size_t o = ((size_t)e * nb + ra) * NR + q0;
+        if (mode == MODE_GS) {
+          x[o] = d[0];
+          x[o + 1] = d[1];
+        } else {
+          rout[o] = g[ra * NR + q0] - d[0];
+          rout[o + 1] = g[ra * NR + q0 + 1] - d[1];
+        }
+      }
+      if (rb < nb) {
+        const size_t o = ((size_t)e * nb + rb) * NR + q0;
+        if (mode == MODE_GS) {
+          x[o] = d[2];
+          x[o + 1] = d[3];
+        } else {
+          rout[o] = g[rb * NR + q0] - d[2];
+          rout[o + 1] = g[rb * NR + q0 + 1] - d[3];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int S>
+static cudaError_t launch_mrhs_tc4_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
+                                    const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                    cudaStream_t st) {
+  if (npos <= 0) return cudaSuccess;
+  if (pat.d + 1 > kTc4Warps) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)(pat.NG * S + 2 * pat.NBP) * 8 + kMaxGather) * sizeof(float);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const int grid = std::min(npos, num_sms() * 8);
+  element_mrhs_tc4_kernel<S><<<grid, 32 * kTc4Warps, smem, st>>>(pat, mode, pos0, npos, perm, nbr,
+                                                                (const float*)cpl, (const float*)mat,
+                                                                (const float*)b, (float*)x, (float*)r);
+  return cudaGetLastError();
+}
+
 template <int S>
 static cudaError_t launch_mrhs_tc_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
                                    const void* cpl, const void* mat, const void* b, void* x, void* r,
@@ -1902,10 +2043,24 @@ static cudaError_t launch_mrhs_tc_s(const Pattern& pat, int mode, int pos0, int 
   return cudaGetLastError();
 }
 
-// Eight right-hand sides, FP32 records: the tensor-core kernel.
+// Eight right-hand sides, FP32 records: the tensor-core kernel (one CTA of
+// four warps per element for launches of at most `small` elements).
 cudaError_t launch_element_mrhs_tc(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
                                    const void* cpl, const void* mat, const void* b, void* x, void* r,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, int small) {
+  if (npos <= small) {
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (pat.s) {
+      case 4: e = launch_mrhs_tc4_s<4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st); break;
+      case 8: e = launch_mrhs_tc4_s<8>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st); break;
+      case 9: e = launch_mrhs_tc4_s<9>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st); break;
+      case 16: e = launch_mrhs_tc4_s<16>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st); break;
+      case 25: e = launch_mrhs_tc4_s<25>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st); break;
+      case 27: e = launch_mrhs_tc4_s<27>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st); break;
+      default: break;
+    }
+    if (e != cudaErrorInvalidValue) return e;
+  }
   switch (pat.s) {
     case 4: return launch_mrhs_tc_s<4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
     case 8: return launch_mrhs_tc_s<8>(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
@@ -1918,6 +2073,12 @@ cudaError_t launch_element_mrhs_tc(const Pattern& pat, int mode, int pos0, int n
 }
 
 void prepare_mrhs_kernels() {
+  cudaFuncSetAttribute(element_mrhs_tc4_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc4_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc4_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc4_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc4_kernel<25>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_mrhs_tc4_kernel<27>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
   cudaFuncSetAttribute(element_mrhs_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
   cudaFuncSetAttribute(element_mrhs_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
   cudaFuncSetAttribute(element_mrhs_tc_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
@@ -1936,9 +2097,9 @@ void prepare_mrhs_kernels() {
 // right-hand sides with FP32 records to the tensor-core kernel.
 cudaError_t launch_element_mrhs(const Pattern& pat, int storage, int nr, int mode, int pos0, int npos,
                                 const int* perm, const int* nbr, const void* cpl, const void* mat, const void* b,
-                                void* x, void* r, cudaStream_t st, int tensor) {
+                                void* x, void* r, cudaStream_t st, int tensor, int tensor_small) {
   if (tensor && nr == 8 && storage == 1) {
-    cudaError_t e = launch_element_mrhs_tc(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st);
+    cudaError_t e = launch_element_mrhs_tc(pat, mode, pos0, npos, perm, nbr, cpl, mat, b, x, r, st, tensor_small);
     if (e != cudaErrorInvalidValue) return e;
   }
   if (nr == 4) {

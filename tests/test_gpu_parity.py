@@ -389,10 +389,11 @@ def test_multi_rhs_fgmres_lockstep(name, precision, method):
 
 @pytest.mark.parametrize("name", ["stress16p3", "3d-mixed-p1", "3d-unsteady-p2"])
 def test_multi_rhs_tensor_cores_match_cuda_cores(name):
-    """Eight right-hand sides with FP32 blocks: the tensor-core kernel (3xTF32
-    mma.sync) and the CUDA-core kernel give the same outer iteration to
-    FP32-level agreement, and both stay within 1e-4 of the oracle's cycle
-    with FP32-rounded blocks."""
+    """Eight right-hand sides with FP32 blocks: the tensor-core kernels (3xTF32
+    mma.sync; one warp per element, and four warps per element for small
+    launches) and the CUDA-core kernel give the same outer iteration to
+    FP32-level agreement, and all stay within 1e-4 of the oracle's cycle with
+    FP32-rounded blocks."""
     prob, _, _ = get(name)
     _, gpu, _ = get(name, native.FP32)
     orc32 = multigrid.Multigrid(prob, storage="fp32")
@@ -401,17 +402,20 @@ def test_multi_rhs_tensor_cores_match_cuda_cores(name):
     B = rng.uniform(-1, 1, (nrhs, prob.n_dofs))
     out = {}
     try:
-        for on in (1, 0):
+        for key, on, small in (("warp", 1, 0), ("cta", 1, 1 << 30), ("cuda", 0, 1024)):
             gpu.ctx.set_mrhs_tensor(on)
+            gpu.ctx.set_wide_launch(small)
             Xd = torch.zeros(nrhs, prob.n_dofs, dtype=torch.float64, device="cuda")
             gpu.ctx.solve_multi(Xd, dev(B).reshape(nrhs, -1), nrhs, rtol=1e-30, maxit=1, inner=1)
-            out[on] = Xd.cpu().numpy()
+            out[key] = Xd.cpu().numpy()
     finally:
         gpu.ctx.set_mrhs_tensor(1)
+        gpu.ctx.set_wide_launch(1024)
     for q in range(nrhs):
-        assert rel(out[1][q], out[0][q]) <= 1e-5
         ref = orc32.precondition(B[q])
-        assert rel(out[1][q], ref) <= 1e-4
+        for key in ("warp", "cta"):
+            assert rel(out[key][q], out["cuda"][q]) <= 1e-5, key
+            assert rel(out[key][q], ref) <= 1e-4, key
 
 
 def _learned_ctx():
