@@ -372,8 +372,8 @@ int stk_set_solver(stk_ctx* ctx, int method, int restart);
  * records; variant 1 = the records streamed into a shared-memory ring of
  * `stages` buffers by 1-D bulk copies (cp.async.bulk, mbarrier completion);
  * variant 2 (default) = one warp per element, no block-wide barriers.
- * `ctas_per_sm` sets the grid (CTAs per SM) of variants 1 and 2, for blocks
- * stored in `precision`.  Zero for ctas_per_sm and stages selects the
+ * The variant and `ctas_per_sm` (the grid of variants 1 and 2, CTAs per SM)
+ * apply to the blocks stored in `precision` only.  Zero for ctas_per_sm and stages selects the
  * built-in shape for the record size.
  * Shapes whose ring does not fit in shared memory fall back to variant 0.
  * If a bulk copy never completes, the kernel's bounded wait (about one
@@ -406,8 +406,10 @@ int stk_set_wide_launch(stk_ctx* ctx, int max_positions);
  * library's own stream, so host launch overhead does not mask the kernels.
  * Call after stk_setup, outside any stream capture; it runs colour steps on
  * the library's own work vectors (zeroed before and after) and synchronises
- * `stream`.  choice (may be NULL, 4 ints) receives {variant, CTAs per SM in
- * the cycle precision, CTAs per SM in FP64, latency-kernel limit};
+ * `stream`.  The variant and the CTAs per SM are kept per storage precision
+ * (the FP64 outer residual may take another kernel than the cycle).  choice
+ * (may be NULL, 5 ints) receives {variant and CTAs per SM in the cycle
+ * precision, variant and CTAs per SM in FP64, latency-kernel limit};
  * best_ms (may be NULL, 2 doubles) the fastest finest-level colour step in
  * the cycle precision and in FP64.  Results are unchanged up to the
  * association order of sums.  Errors: STK_ERR_NOT_SETUP, STK_ERR_CUDA.

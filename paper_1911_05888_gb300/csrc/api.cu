@@ -197,12 +197,13 @@ cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, c
                                         x, r, st);
     if (e != cudaErrorInvalidValue || scaled) return e;
   }
-  if (c.variant == 2 || scaled) {
+  const int variant = c.variant_of[prec];
+  if (variant == 2 || scaled) {
     cudaError_t e = launch_element_warp(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
                                         x, r, c.warp_ctas[prec], st);
     if (e != cudaErrorInvalidValue || scaled) return e;
   }
-  if (c.variant == 1) {
+  if (variant == 1) {
     cudaError_t e = launch_element_pipe(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
                                         c.dev_err, c.pipe_ctas[prec], c.pipe_stages[prec], st);
     if (e != cudaErrorInvalidValue) return e;
@@ -1541,7 +1542,7 @@ int stk_set_tuning(stk_ctx* c, int variant, int precision, int ctas_per_sm, int 
     if (variant < 0 || variant > 2 || precision < 0 || precision > 3 || ctas_per_sm < 0 || ctas_per_sm > 32 ||
         stages < 0 || stages > 16)
       return fail(c, STK_ERR_INVALID_ARG, "bad tuning options");
-    c->variant = variant;
+    c->variant_of[precision] = variant;
     if (variant == 2 && ctas_per_sm > 0) c->warp_ctas[precision] = ctas_per_sm;
     if (variant == 1 && ctas_per_sm > 0 && stages > 0) {
       c->pipe_ctas[precision] = ctas_per_sm;
@@ -1631,13 +1632,12 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
     c->wide_max = 0;
     const int precs[2] = {c->precision, STK_FP64};
     double best[2] = {0, 0};
-    int chosen_variant = c->variant;
     for (int pi = 0; pi < (c->precision == STK_FP64 ? 1 : 2); ++pi) {
       const int prec = precs[pi];
       // warp-per-element kernel: CTAs of 8 warps per SM
       double t2 = 1e300;
       int bc = c->warp_ctas[prec];
-      c->variant = 2;
+      c->variant_of[prec] = 2;
       for (int ctas : {2, 3, 4, 6, 8}) {
         c->warp_ctas[prec] = ctas;
         const double t = time_step(0, prec, 10);
@@ -1650,12 +1650,11 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
       // one CTA per element with direct loads (not for scaled FP16 records)
       double t0 = 1e300;
       if (prec != STK_FP16) {
-        c->variant = 0;
+        c->variant_of[prec] = 0;
         t0 = time_step(0, prec, 10);
       }
-      if (pi == 0) chosen_variant = t0 < t2 ? 0 : 2;
+      c->variant_of[prec] = t0 < t2 ? 0 : 2;
       best[pi] = std::min(t0, t2);
-      c->variant = chosen_variant;
     }
     // Latency kernel: time both kernels on every smoothing level's colour
     // step and keep the threshold (0 or one level's colour size) with the
@@ -1699,10 +1698,11 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
     c->cycle_graph = nullptr;
     c->cycle_graph_prec = -1;
     if (choice) {
-      choice[0] = c->variant;
+      choice[0] = c->variant_of[c->precision];
       choice[1] = c->warp_ctas[c->precision];
-      choice[2] = c->warp_ctas[STK_FP64];
-      choice[3] = c->wide_max;
+      choice[2] = c->variant_of[STK_FP64];
+      choice[3] = c->warp_ctas[STK_FP64];
+      choice[4] = c->wide_max;
     }
     if (best_ms) {
       best_ms[0] = best[0];

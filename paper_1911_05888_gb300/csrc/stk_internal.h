@@ -144,7 +144,7 @@ struct Ctx {
   int64_t cycle_graph_kernels = 0;
   // element-kernel variant: 0 direct loads, 1 bulk-copy pipeline, 2 warp per element (default),
   // with the pipeline shape per storage precision (CTAs per SM, ring depth)
-  int variant = 2;
+  int variant_of[4] = {2, 2, 2, 2};   // per storage precision
   int pipe_ctas[4] = {0, 0, 0, 0}, pipe_stages[4] = {0, 0, 0, 0};
   int warp_ctas[4] = {4, 4, 4, 4};   // CTAs (of 8 warps) per SM for the warp-per-element kernel
   // launches of at most this many elements use one CTA per element (latency variant), whatever the variant
