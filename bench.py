@@ -101,11 +101,11 @@ def config(args, prob):
 def cpu_child(spec):
     """Runs in a fresh single-threaded process: time oracle V-cycles plus the
     outer residual on the sample problem; prints one JSON line."""
-    n, p, seconds = [float(v) for v in spec.split(",")]
-    n, p = int(n), int(p)
+    n, p, nu, seconds = [float(v) for v in spec.split(",")]
+    n, p, nu = int(n), int(p), int(nu)
     import numpy as np
     from oracle import multigrid
-    prob = workload(n, p)
+    prob = workload(n, p).with_(nu1=nu, nu2=nu)
     mg = multigrid.Multigrid(prob)
     rng = np.random.default_rng(0)
     b = rng.uniform(-1, 1, prob.n_dofs)
@@ -125,14 +125,15 @@ def cpu_baseline(args, seconds=12.0):
     n = min(args.n, 64)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child",
-                          "%d,%d,%f" % (n, args.p, seconds)], capture_output=True, text=True, env=env,
+                          "%d,%d,%d,%f" % (n, args.p, args.nu, seconds)], capture_output=True, text=True, env=env,
                          timeout=900)
     rec = json.loads(out.stdout.strip().splitlines()[-1])
     value = rec["dofs"] * rec["cycles"] / rec["seconds"]
     return {"value": value, "unit": "DOF-cycles/s", "cores": 1, "kind": "oracle",
-            "sample": "same problem class on a %dx%d mesh (p=%d, %d DOFs): %d V(1,1) cycles + FP64 "
+            "sample": "same problem class on a %dx%d mesh (p=%d, %d DOFs): %d V(%d,%d) cycles + FP64 "
                       "residuals in %.1f s, numpy/scipy single thread" % (n, n, args.p, rec["dofs"],
-                                                                          rec["cycles"], rec["seconds"])}
+                                                                          rec["cycles"], args.nu, args.nu,
+                                                                          rec["seconds"])}
 
 
 # ---------------------------------------------------------------------------
@@ -481,7 +482,7 @@ def run_reference(args):
     n = min(args.n, 64)
     import numpy as np
     from oracle import multigrid
-    prob = workload(n, args.p)
+    prob = workload(n, args.p).with_(nu1=args.nu, nu2=args.nu)
     mg = multigrid.Multigrid(prob)
     b = np.random.default_rng(0).uniform(-1, 1, prob.n_dofs)
     x = np.zeros_like(b)
@@ -502,8 +503,8 @@ def run_reference(args):
         tot_s += s
     value = prob.n_dofs * tot_c / tot_s
     sample = ("oracle (numpy/scipy, single process) on the same problem class at %dx%d, p=%d "
-              "(%d DOFs); each step = %.0f s of V(1,1) cycles with FP64 residuals" % (n, n, args.p,
-                                                                                     prob.n_dofs, per_step))
+              "(%d DOFs); each step = %.0f s of V(%d,%d) cycles with FP64 residuals" % (
+                  n, n, args.p, prob.n_dofs, per_step, args.nu, args.nu))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-cycles/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,
