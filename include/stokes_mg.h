@@ -292,6 +292,18 @@ int stk_solve_multi(stk_ctx* ctx, double* X_dev, const double* B_dev, int nrhs, 
 int stk_set_mrhs_tensor(stk_ctx* ctx, int on);
 
 /*
+ * The FP64 matvec of flexible GMRES (method 1) under an FP32, BF16 or FP16
+ * cycle (no counterpart in the paper): the preconditioned vector z_j is the
+ * cycle's FP32 output, so A z_j is formed from the level-0 FP32 records and
+ * their FP32 remainders (A_hi + A_lo, ~48 bits) with exact FP32 products and
+ * two-sum accumulation on the FP32 units, to about 2^-44 relative to
+ * |A| |z_j| per entry, instead of on the FP64 units (64 times slower on this
+ * GPU).  on = 1 (default) or 0 (FP64 records and arithmetic).  The outer
+ * residual at each restart stays FP64.
+ */
+int stk_set_df_matvec(stk_ctx* ctx, int on);
+
+/*
  * A batch of independent problems (no counterpart in the paper; a batching
  * layer over stk_solve / stk_solve_multi): solves ctx[i] x[i] = b[i] for
  * i < n, each context set up for its own problem (any mesh size, degree,

@@ -82,6 +82,11 @@ cudaError_t launch_scale_by_norm(int64_t n, const double* sums, float* g, cudaSt
 cudaError_t launch_element_wide(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
                                 const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
                                 const void* b, void* x, void* r, cudaStream_t st);
+cudaError_t launch_element_df(const Pattern& pat, int pos0, int npos, const int* perm, const int* nbr,
+                              const void* cpl_hi, const void* cpl_lo, const void* dia_hi, const void* dia_lo,
+                              const float* z, double* w, int ctas, cudaStream_t st);
+cudaError_t launch_fp32_remainder(int64_t n, const double* a, void* lo, cudaStream_t st);
+void prepare_df_kernels();
 cudaError_t launch_to_fp16_tasks(int64_t npos, int S, int T, int TRP, void* dst, float* tsc, const double* src,
                                  cudaStream_t st);
 cudaError_t launch_to_fp16_rows(int64_t npos, int nb, int NBP, void* dst, float* rsc, const double* src,
@@ -323,6 +328,13 @@ void pack_level(Ctx& c, int l, cudaStream_t st) {
       *dst[i] = dalloc(c, cnt[i] * 4);
       ck(launch_convert(0, 1, (int64_t)cnt[i], *dst[i], src[i], st), "convert fp32");
     }
+  }
+  // FP32 remainders for the FP64-accurate FGMRES matvec on the FP32 units
+  if (l == 0 && c.precision != STK_FP64) {
+    D.cpl_lo = dalloc(c, cpl_n * 4);
+    D.dia_lo = dalloc(c, mat_n * 4);
+    ck(launch_fp32_remainder((int64_t)cpl_n, (const double*)D.cpl[0], D.cpl_lo, st), "remainder");
+    ck(launch_fp32_remainder((int64_t)mat_n, (const double*)D.dia[0], D.dia_lo, st), "remainder");
   }
   (void)st;
 }
@@ -1028,6 +1040,14 @@ int fgmres(Ctx& c, double* x, const double* b, double rtol, int maxit, double* h
            "matvec32");
         ck(launch_convert(1, 0, n0, c.kw, c.kw32, st), "convert");
         c.launches += 3;
+      } else if (c.precision != STK_FP64 && c.df_matvec && c.dev[0].cpl_lo) {
+        // z_j is an FP32 vector (the cycle's output, still in vx[1]): -A z_j to
+        // about 2^-44 with FP32 records and remainders on the FP32 units
+        DevLevel& D0 = c.dev[0];
+        ck(launch_element_df(c.pat, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[STK_FP32], D0.cpl_lo, D0.dia[STK_FP32],
+                             D0.dia_lo, (const float*)D0.vx[1], c.kw, c.warp_ctas[STK_FP32], st),
+           "matvec df");
+        c.launches++;
       } else {
         enqueue_residual64(c, zj, c.kzero, c.kw, st);
       }
@@ -1285,6 +1305,7 @@ int stk_setup(stk_ctx* c, void* stream) {
     if (c->device >= 0 && c->device < 64 && !prepared[c->device]) {
       prepare_pipe_kernels();
       prepare_mrhs_kernels();
+      prepare_df_kernels();
       prepared[c->device] = true;
     }
     for (int pr = 0; pr < 3; ++pr)
@@ -1708,6 +1729,13 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
       best_ms[0] = best[0];
       best_ms[1] = c->precision == STK_FP64 ? best[0] : best[1];
     }
+    return STK_OK;
+  });
+}
+
+int stk_set_df_matvec(stk_ctx* c, int on) {
+  return guard(c, [&]() -> int {
+    c->df_matvec = on ? 1 : 0;
     return STK_OK;
   });
 }

@@ -611,6 +611,205 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
   }
 }
 
+// ---- FP64-accurate matvec on the FP32 units ------------------------------------
+// w = -A z for a vector z whose entries are FP32 values (the output of an
+// FP32 V-cycle), with A held as two FP32 records, A = A_hi + A_lo (A_hi the
+// FP32 rounding of the FP64 entry, A_lo the FP32 rounding of the
+// remainder, so that A_hi + A_lo carries about 48 bits).  Every product
+// A_hi z is exact as the pair (p, e) with p = fl(A_hi z) and e = fma(A_hi, z,
+// -p); sums are kept as unevaluated pairs (hi, lo) with Knuth's two-sum for
+// the leading part, and the small terms (e, A_lo z, the two-sum errors)
+// accumulate in lo.  The result agrees with an FP64 matvec to about 2^-44
+// relative to |A| |z| per entry, while the arithmetic runs on the FP32
+// pipes (about 12 FP32 operations per entry against one FP64 FMA at a
+// 1/64 rate), so the kernel is bound by its 8 bytes per entry of records.
+// One warp per element, the same layout and loop structure as
+// element_warp_kernel; shared memory holds hi and lo of every partial sum.
+static int num_sms();
+
+struct DFloat {
+  float hi, lo;
+};
+
+// (explicitly rounded operations: the compiler must not contract them into
+// fused multiply-adds, which would break the two-sum identity)
+__device__ inline void df_add(DFloat& a, float p) {
+  const float s = __fadd_rn(a.hi, p);
+  const float v = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  a.lo = __fadd_rn(a.lo, err);
+  a.hi = s;
+}
+
+__device__ inline void df_add_prod(DFloat& a, float m_hi, float m_lo, float z) {
+  const float p = __fmul_rn(m_hi, z);
+  const float e = __fmaf_rn(m_hi, z, -p);
+  df_add(a, p);
+  a.lo = __fmaf_rn(m_lo, z, __fadd_rn(a.lo, e));
+}
+
+__device__ inline void df_add_df(DFloat& a, const DFloat& b) {
+  df_add(a, b.hi);
+  a.lo += b.lo;
+}
+
+template <int S>
+__global__ void __launch_bounds__(32 * kWarps) element_df_kernel(const __grid_constant__ Pattern pat, int pos0,
+                                                                 int npos, const int* __restrict__ perm,
+                                                                 const int* __restrict__ nbr,
+                                                                 const float* __restrict__ cpl_hi,
+                                                                 const float* __restrict__ cpl_lo,
+                                                                 const float* __restrict__ dia_hi,
+                                                                 const float* __restrict__ dia_lo,
+                                                                 const float* __restrict__ z, double* __restrict__ w) {
+  constexpr int V = 4;
+  const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
+  const int NRV = NBP / V;
+  const int NCG = (32 / NRV) > 0 ? (32 / NRV) : 1;
+  const int CW = (nb + NCG - 1) / NCG;
+  const int XS = S + 1;
+  const int words = (pat.NG * XS + 2 * TRP + NBP + 2 * NCG * NBP + 3) / 4 * 4;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  extern __shared__ __align__(16) float df_smem[];
+  float* Xs = df_smem + (size_t)wid * words;   // gathered neighbour values (exact FP32)
+  float* ph = Xs + pat.NG * XS;                 // task-row partial sums, hi
+  float* pl = ph + TRP;                         //                         lo
+  float* zi = pl + TRP;                         // z_i
+  float* qh = zi + NBP;                         // column-group partials of A_ii z_i, hi
+  float* ql = qh + NCG * NBP;                   //                                     lo
+  const int nwarps = gridDim.x * kWarps;
+  for (int pos = pos0 + blockIdx.x * kWarps + wid; pos < pos0 + npos; pos += nwarps) {
+    const int e = perm[pos];
+    const int* nbe = nbr + (size_t)pos * pat.NO;
+    for (int i = lane; i < pat.NG * S; i += 32) {
+      const int gi = i / S, ci = i - gi * S;
+      const int j = nbe[pat.g_o[gi]];
+      Xs[gi * XS + ci] = (j >= 0) ? z[(size_t)j * nb + pat.g_cv[gi] * S + ci] : 0.f;
+    }
+    for (int i = lane; i < nb; i += 32) zi[i] = z[(size_t)e * nb + i];
+    __syncwarp();
+    const float* rh = cpl_hi + (size_t)pos * S * TRP;
+    const float* rl = cpl_lo + (size_t)pos * S * TRP;
+    for (int tv = lane; tv < TRP / V; tv += 32) {
+      const int tr0 = tv * V;
+      const float* xp[V];
+      DFloat acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int tr = tr0 + j;
+        xp[j] = (tr < TR) ? Xs + pat.task_g[tr / S] * XS : Xs;
+        acc[j].hi = acc[j].lo = 0.f;
+      }
+#pragma unroll 4
+      for (int ci = 0; ci < S; ++ci) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(rh + (size_t)ci * TRP + tr0));
+        const float4 b = __ldcs(reinterpret_cast<const float4*>(rl + (size_t)ci * TRP + tr0));
+        df_add_prod(acc[0], a.x, b.x, xp[0][ci]);
+        df_add_prod(acc[1], a.y, b.y, xp[1][ci]);
+        df_add_prod(acc[2], a.z, b.z, xp[2][ci]);
+        df_add_prod(acc[3], a.w, b.w, xp[3][ci]);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        ph[tr0 + j] = acc[j].hi;
+        pl[tr0 + j] = acc[j].lo;
+      }
+    }
+    __syncwarp();
+    const float* mh = dia_hi + (size_t)pos * nb * NBP;
+    const float* ml = dia_lo + (size_t)pos * nb * NBP;
+    for (int u = lane; u < NRV * NCG; u += 32) {
+      const int rvv = u % NRV, cg = u / NRV;
+      const int c0 = cg * CW, c1 = min(nb, c0 + CW);
+      DFloat acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) acc[j].hi = acc[j].lo = 0.f;
+#pragma unroll 4
+      for (int ci = c0; ci < c1; ++ci) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(mh + (size_t)ci * NBP + rvv * V));
+        const float4 b = __ldcs(reinterpret_cast<const float4*>(ml + (size_t)ci * NBP + rvv * V));
+        const float v = zi[ci];
+        df_add_prod(acc[0], a.x, b.x, v);
+        df_add_prod(acc[1], a.y, b.y, v);
+        df_add_prod(acc[2], a.z, b.z, v);
+        df_add_prod(acc[3], a.w, b.w, v);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        qh[cg * NBP + rvv * V + j] = acc[j].hi;
+        ql[cg * NBP + rvv * V + j] = acc[j].lo;
+      }
+    }
+    __syncwarp();
+    for (int r = lane; r < nb; r += 32) {
+      const int rv = r / S, rr = r - rv * S;
+      DFloat sum = {0.f, 0.f};
+      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) df_add_df(sum, DFloat{ph[t * S + rr], pl[t * S + rr]});
+      for (int cg = 0; cg < NCG; ++cg) df_add_df(sum, DFloat{qh[cg * NBP + r], ql[cg * NBP + r]});
+      w[(size_t)e * nb + r] = -((double)sum.hi + (double)sum.lo);
+    }
+    __syncwarp();
+  }
+}
+
+template <int S>
+static cudaError_t launch_df_s(const Pattern& pat, int pos0, int npos, const int* perm, const int* nbr,
+                               const float* cpl_hi, const float* cpl_lo, const float* dia_hi, const float* dia_lo,
+                               const float* z, double* w, int ctas, cudaStream_t st) {
+  if (npos <= 0) return cudaSuccess;
+  const int NRV = pat.NBP / 4;
+  const int NCG = (32 / NRV) > 0 ? (32 / NRV) : 1;
+  const int words = (pat.NG * (S + 1) + 2 * pat.TRP + pat.NBP + 2 * NCG * pat.NBP + 3) / 4 * 4;
+  const size_t smem = (size_t)kWarps * words * sizeof(float);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const int grid = std::min((npos + kWarps - 1) / kWarps, num_sms() * std::max(1, ctas));
+  element_df_kernel<S><<<grid, 32 * kWarps, smem, st>>>(pat, pos0, npos, perm, nbr, cpl_hi, cpl_lo, dia_hi, dia_lo,
+                                                         z, w);
+  return cudaGetLastError();
+}
+
+// w = -(A_hi + A_lo) z over positions [pos0, pos0 + npos) of level 0 (see
+// element_df_kernel); cudaErrorInvalidValue when the shape does not fit.
+cudaError_t launch_element_df(const Pattern& pat, int pos0, int npos, const int* perm, const int* nbr,
+                              const void* cpl_hi, const void* cpl_lo, const void* dia_hi, const void* dia_lo,
+                              const float* z, double* w, int ctas, cudaStream_t st) {
+#define STK_DF_CASE(SV)                                                                                       \
+  case SV:                                                                                                    \
+    return launch_df_s<SV>(pat, pos0, npos, perm, nbr, (const float*)cpl_hi, (const float*)cpl_lo,          \
+                           (const float*)dia_hi, (const float*)dia_lo, z, w, ctas, st);
+  switch (pat.s) {
+    STK_DF_CASE(4)
+    STK_DF_CASE(8)
+    STK_DF_CASE(9)
+    STK_DF_CASE(16)
+    STK_DF_CASE(25)
+    STK_DF_CASE(27)
+    default: return cudaErrorInvalidValue;
+  }
+#undef STK_DF_CASE
+}
+
+// FP32 remainder records: lo = fl32(a - fl32(a)) for every FP64 entry.
+__global__ void fp32_remainder_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ lo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) lo[i] = (float)(a[i] - (double)(float)a[i]);
+}
+
+cudaError_t launch_fp32_remainder(int64_t n, const double* a, void* lo, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  fp32_remainder_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, (float*)lo);
+  return cudaGetLastError();
+}
+
+void prepare_df_kernels() {
+  cudaFuncSetAttribute(element_df_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_df_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_df_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_df_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_df_kernel<25>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_df_kernel<27>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+}
+
 // ---- latency variant for launches with few elements ---------------------------
 // On coarse levels a colour holds a handful of elements, so the time of a
 // launch is the latency of one element, not bandwidth.  Here one CTA of

@@ -64,6 +64,10 @@ struct DevLevel {
   float* csc = nullptr;
   float* isc = nullptr;
   float* dsc = nullptr;
+  // level 0 of a low-precision cycle: FP32 remainders of the FP64 coupling and
+  // diagonal records (cpl[1] + cpl_lo, dia[1] + dia_lo carry ~48 bits)
+  void* cpl_lo = nullptr;
+  void* dia_lo = nullptr;
   // cycle vectors: index 0 FP64, index 1 FP32
   void* vx[2] = {nullptr, nullptr};
   void* vb[2] = {nullptr, nullptr};
@@ -138,6 +142,7 @@ struct Ctx {
   float *mkz32 = nullptr, *mkw32 = nullptr, *mkzero32 = nullptr;   // FP32 matvec of the refined variant
   int mk_cap = 0, mk_nr = 0;
   int mrhs_tensor = 1;   // eight right-hand sides with FP32 records: tensor-core kernel
+  int df_matvec = 1;     // FGMRES matvec of a low-precision cycle on the FP32 units (double-float)
   // V-cycle alone on the level-0 work vectors, as a CUDA graph
   cudaGraphExec_t cycle_graph = nullptr;
   int cycle_graph_prec = -1;
