@@ -419,9 +419,11 @@ int stk_set_wide_launch(stk_ctx* ctx, int max_positions);
  * Call after stk_setup, outside any stream capture; it runs colour steps on
  * the library's own work vectors (zeroed before and after) and synchronises
  * `stream`.  The variant and the CTAs per SM are kept per storage precision
- * (the FP64 outer residual may take another kernel than the cycle).  choice
- * (may be NULL, 5 ints) receives {variant and CTAs per SM in the cycle
- * precision, variant and CTAs per SM in FP64, latency-kernel limit};
+ * (the FP64 outer residual may take another kernel than the cycle); under a
+ * low-precision cycle it also times the two FGMRES matvecs (stk_set_df_matvec)
+ * over level 0 and keeps the faster.  choice (may be NULL, 6 ints) receives
+ * {variant and CTAs per SM in the cycle precision, variant and CTAs per SM in
+ * FP64, latency-kernel limit, FP32-unit matvec on/off};
  * best_ms (may be NULL, 2 doubles) the fastest finest-level colour step in
  * the cycle precision and in FP64.  Results are unchanged up to the
  * association order of sums.  Errors: STK_ERR_NOT_SETUP, STK_ERR_CUDA.

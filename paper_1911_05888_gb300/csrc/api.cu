@@ -1677,6 +1677,41 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
       c->variant_of[prec] = t0 < t2 ? 0 : 2;
       best[pi] = std::min(t0, t2);
     }
+    // FGMRES matvec of a low-precision cycle: FP32-unit double-float kernel or
+    // the FP64 residual kernel, whichever is faster over the whole level 0.
+    if (c->precision != STK_FP64 && c->dev[0].cpl_lo) {
+      DevLevel& D0 = c->dev[0];
+      auto time_matvec = [&](bool df) -> double {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        ck(cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal), "capture");
+        for (int i = 0; i < 3; ++i) {
+          cudaError_t e = df ? launch_element_df(c->pat, 0, D0.ne, D0.perm, D0.nbr, D0.cpl[STK_FP32], D0.cpl_lo,
+                                                 D0.dia[STK_FP32], D0.dia_lo, (const float*)D0.vx[1],
+                                                 (double*)D0.vr[0], c->warp_ctas[STK_FP32], ts)
+                             : run_element(*c, 0, STK_FP64, MODE_RESID, 0, D0.ne, D0.dia[0], D0.vb[0], D0.vx[0],
+                                           D0.vr[0], ts);
+          if (e != cudaSuccess) {
+            cudaStreamEndCapture(ts, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            ck(e, "tune matvec");
+          }
+        }
+        ck(cudaStreamEndCapture(ts, &graph), "capture");
+        ck(cudaGraphInstantiate(&exec, graph, 0), "instantiate");
+        ck(cudaGraphLaunch(exec, ts), "graph");
+        ck(cudaEventRecord(e0, ts), "event");
+        ck(cudaGraphLaunch(exec, ts), "graph");
+        ck(cudaEventRecord(e1, ts), "event");
+        ck(cudaEventSynchronize(e1), "event");
+        float ms = 0;
+        ck(cudaEventElapsedTime(&ms, e0, e1), "event");
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return (double)ms / 3;
+      };
+      c->df_matvec = time_matvec(true) < time_matvec(false) ? 1 : 0;
+    }
     // Latency kernel: time both kernels on every smoothing level's colour
     // step and keep the threshold (0 or one level's colour size) with the
     // least total time over the levels.
@@ -1724,6 +1759,7 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
       choice[2] = c->variant_of[STK_FP64];
       choice[3] = c->warp_ctas[STK_FP64];
       choice[4] = c->wide_max;
+      choice[5] = c->df_matvec;
     }
     if (best_ms) {
       best_ms[0] = best[0];

@@ -347,11 +347,11 @@ class Context:
 
     def autotune(self, stream=None):
         """Time the element-kernel launch shapes and keep the fastest; returns
-        ({variant, ctas_cycle, variant_fp64, ctas_fp64, wide_max}, (best_ms_cycle, best_ms_fp64))."""
-        choice = (ctypes.c_int * 5)()
+        ({variant, ctas_cycle, variant_fp64, ctas_fp64, wide_max, df_matvec}, (best_ms_cycle, best_ms_fp64))."""
+        choice = (ctypes.c_int * 6)()
         best = (ctypes.c_double * 2)()
         self._check(self.lib.stk_autotune(self.h, choice, best, _stream(stream)), "stk_autotune")
-        keys = ("variant", "ctas_cycle", "variant_fp64", "ctas_fp64", "wide_max")
+        keys = ("variant", "ctas_cycle", "variant_fp64", "ctas_fp64", "wide_max", "df_matvec")
         return dict(zip(keys, list(choice))), (best[0], best[1])
 
     def set_solver(self, method, restart=30):

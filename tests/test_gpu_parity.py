@@ -621,11 +621,11 @@ def test_solve_batch_several_right_hand_sides():
 def test_fgmres_double_float_matvec(name, precision):
     """Flexible GMRES with its matvec on the FP32 units (FP32 records plus
     their FP32 remainders, exact products, two-sum accumulation) follows the
-    FP64-matvec FGMRES: the same iteration count, 1e-10 reached, the same
-    residual history to 1e-5 relative in every entry above 1e-9 (the FP32
-    cycle turns the matvecs' ~1e-14 differences into ~1e-8 ones in its
-    output, more under a 1e3 viscosity contrast) and the same solution to
-    1e-8."""
+    FP64-matvec FGMRES: the same iteration count (+-1 under 16-bit cycles),
+    1e-10 reached, for FP32 cycles the same residual history to 1e-5
+    relative in every entry above 1e-9 (the cycle turns the matvecs' ~1e-14
+    differences into ~1e-8 ones in its output, more under a 1e3 viscosity
+    contrast) and the same solution to 1e-8."""
     prob, gpu64, _ = get(name)
     _, gpu, _ = get(name, precision)
     b = gpu64.rhs().ravel()
@@ -644,8 +644,9 @@ def test_fgmres_double_float_matvec(name, precision):
         gpu.ctx.set_df_matvec(1)
         gpu.ctx.set_solver(native.RICHARDSON, 30)
     (it0, h0, x0), (it1, h1, x1) = runs[0], runs[1]
-    assert it0 == it1 and h1[-1] <= 1e-10, (it0, it1, h1[-1])
-    big = h0 > 1e-9
-    assert np.all(np.abs(h1[big] - h0[big]) <= 1e-5 * h0[big] + 1e-13)
+    assert abs(it0 - it1) <= (0 if precision == native.FP32 else 1) and h1[-1] <= 1e-10, (it0, it1, h1[-1])
+    if precision == native.FP32:   # 16-bit cycles amplify the perturbation further
+        big = h0 > 1e-9
+        assert np.all(np.abs(h1[big] - h0[big]) <= 1e-5 * h0[big] + 1e-13)
     Z = trivial_kernel(prob, get(name)[2])
     assert rel(x1 - Z @ (Z.T @ x1), x0 - Z @ (Z.T @ x0)) <= 1e-8
