@@ -1622,15 +1622,19 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
     // so that host launch overhead does not hide the kernels' own durations.
     cudaStream_t ts = c->stream;
     ck(cudaStreamSynchronize(st), "sync");
+    // The steps cycle through the level's colours, as a sweep does, so that
+    // a level whose one colour would fit in L2 is not timed from L2.
     auto time_step = [&](int l, int prec, int reps) -> double {
       DevLevel& D = c->dev[l];
       const int vi = prec == STK_FP64 ? 0 : 1;
-      const int n = D.cstart[1] - D.cstart[0];
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
       ck(cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal), "capture");
       for (int i = 0; i < reps; ++i) {
-        cudaError_t e = run_element(*c, l, prec, MODE_GS, D.cstart[0], n, D.inv[prec], D.vb[vi], D.vx[vi], nullptr, ts);
+        const int col = i % D.ncolour;
+        const int n = D.cstart[col + 1] - D.cstart[col];
+        cudaError_t e = run_element(*c, l, prec, MODE_GS, D.cstart[col], n, D.inv[prec], D.vb[vi], D.vx[vi], nullptr,
+                                    ts);
         if (e != cudaSuccess) {
           cudaStreamEndCapture(ts, &graph);
           if (graph) cudaGraphDestroy(graph);
@@ -1719,7 +1723,8 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
     std::vector<double> t_cfg(L - 1), t_wide(L - 1);
     for (int l = 0; l < L - 1; ++l) {
       DevLevel& D = c->dev[l];
-      nl[l] = D.cstart[1] - D.cstart[0];
+      nl[l] = 0;
+      for (int col = 0; col < D.ncolour; ++col) nl[l] = std::max(nl[l], D.cstart[col + 1] - D.cstart[col]);
       c->wide_max = 0;
       t_cfg[l] = time_step(l, c->precision, 20);
       c->wide_max = nl[l];
