@@ -135,6 +135,20 @@ int stk_set_density(stk_ctx* ctx, const double* rho_vol, const double* rho_iface
 int stk_set_cycle(stk_ctx* ctx, int nu1, int nu2, int precision);
 
 /*
+ * Cycle shape (Section 6 names W-cycles and variable V-cycles as the
+ * alternatives to Algorithm 1's V-cycle).  gamma = visits of level l+1 per
+ * visit of level l (1: V-cycle, 2: W-cycle, 3); the coarse correction starts
+ * from zero and each further visit continues from the previous visit's
+ * result; the coarsest level is solved exactly and visited once.  Smoothing
+ * on level l takes min(nu * growth^l, max(nu, max_sweeps)) sweeps for
+ * nu = nu1 and nu = nu2 (growth 1: fixed counts; growth 2: the variable
+ * V-cycle).  Defaults 1, 1, 64.  Applies to every cycle of the context
+ * (single and several right-hand sides).  Errors: STK_ERR_INVALID_ARG
+ * unless 1 <= gamma <= 3, 1 <= growth <= 4, 1 <= max_sweeps <= 256.
+ */
+int stk_set_cycle_shape(stk_ctx* ctx, int gamma, int growth, int max_sweeps);
+
+/*
  * Setup: fine-level LDG assembly (Appendix A), operator coarsening
  * (Algorithm 2, or 3 when unsteady) down to the bottom level (some n_k odd or
  * equal to 2), the Stokes blocks of every level, element-block inverses (FP64

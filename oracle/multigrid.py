@@ -8,6 +8,8 @@ Section 3 (Multigrid design):
     (element-order) sweep is kept as the second reference.
   * Algorithm 1: V(E_h, x_h, b_h) with nu1 pre- and nu2 post-smoothing sweeps,
     r_2h = (I_2h^h)^T (b_h - A_h x_h), coarse guess 0, x_h += I_2h^h x_2h.
+  * Section 6's alternatives to the V-cycle: W-cycles (gamma coarse visits
+    per level) and variable V-cycles (smoothing counts growing per level).
   * Bottom solver (Section 3 footnote on the trivial kernel): symmetric
     eigendecomposition of the coarsest operator with near-zero eigenvalues
     snapped to zero (least-squares solution).
@@ -143,8 +145,11 @@ def bottom_pseudo_inverse(A, theta=SNAP_THETA):
 class Multigrid:
     """The V-cycle hierarchy of a problem (oracle)."""
 
-    def __init__(self, prob, storage=None, levels=None, injections=None, max_levels=None):
+    def __init__(self, prob, storage=None, levels=None, injections=None, max_levels=None, shape=(1, 1, 64)):
         self.prob = prob
+        # cycle shape (Section 6): coarse visits per level (1 V, 2 W), growth
+        # of the smoothing counts per coarser level, cap on the counts
+        self.gamma, self.growth, self.max_sweeps = shape
         if levels is None:
             levels, injections = build_hierarchy(prob, max_levels=max_levels)
         self.levels = levels
@@ -200,21 +205,34 @@ class Multigrid:
         """I_2h^h x_2h (injection)."""
         return self.I[l] @ xc
 
+    def sweeps(self, nu, l):
+        """Smoothing sweeps of one phase on level l.  Section 6 names the
+        variable V-cycle, whose smoothing counts change from level to level;
+        here they grow geometrically, nu * growth^l, up to max(nu, cap).
+        growth = 1 gives Algorithm 1's fixed counts."""
+        return min(nu * self.growth ** l, max(nu, self.max_sweeps))
+
     def vcycle(self, x, b, l=0, nu1=None, nu2=None, lexicographic=False):
-        """Algorithm 1: returns x after one V-cycle (x is updated in place)."""
+        """Algorithm 1: returns x after one V-cycle (x is updated in place).
+        With gamma > 1 the coarse problem of every level is visited gamma
+        times (the W-cycle for gamma = 2, Section 6), the first visit from a
+        zero guess and each later one from the previous result; the coarsest
+        level is solved exactly, so it is visited once."""
         nu1 = self.nu1 if nu1 is None else nu1
         nu2 = self.nu2 if nu2 is None else nu2
         if l == len(self.levels) - 1:
             x[:] = self.bottom_solve(b)
             return x
         sm = self.sm[l]
-        for _ in range(nu1):
+        for _ in range(self.sweeps(nu1, l)):
             (sm.sweep_lexicographic if lexicographic else sm.sweep)(x, b)
         r2 = self.restrict(l, self.cycle_residual(l, x, b))
         x2 = np.zeros_like(r2)
-        self.vcycle(x2, r2, l + 1, nu1, nu2, lexicographic)
+        visits = 1 if l + 1 == len(self.levels) - 1 else self.gamma
+        for _ in range(visits):
+            self.vcycle(x2, r2, l + 1, nu1, nu2, lexicographic)
         x += self.prolong(l, x2)
-        for _ in range(nu2):
+        for _ in range(self.sweeps(nu2, l)):
             (sm.sweep_lexicographic if lexicographic else sm.sweep)(x, b)
         return x
 

@@ -493,6 +493,20 @@ void enqueue_learned(Ctx& c, int prec, void* xv, const void* bv, cudaStream_t st
 }
 
 // ---- the V-cycle (Algorithm 1) ------------------------------------------------
+// Smoothing sweeps of one phase on level l: nu * growth^l, but no more than
+// max(nu, cap).  growth 1 keeps Algorithm 1's fixed counts; growth 2 is the
+// variable V-cycle named in Section 6 (more smoothing on coarser levels).
+int level_sweeps(const Ctx& c, int nu, int l) {
+  int64_t s = nu;
+  const int64_t cap = std::max<int64_t>(nu, c.cyc_cap);
+  for (int k = 0; k < l && s < cap; ++k) s *= c.cyc_growth;
+  return (int)std::min(s, cap);
+}
+
+// Visits to level l+1 per visit of level l: gamma (1 = V-cycle, 2 = W-cycle,
+// Section 6), except that the coarsest level, solved exactly, is visited once.
+int coarse_visits(const Ctx& c, int l) { return l + 1 == nlevels(c) - 1 ? 1 : c.cyc_gamma; }
+
 // prec: storage precision of the blocks; vectors FP64 when prec == 0, else FP32.
 void enqueue_smooth(Ctx& c, int prec, int l, int sweeps, void* x, const void* b, cudaStream_t st) {
   DevLevel& D = c.dev[l];
@@ -515,17 +529,17 @@ void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t
   }
   DevLevel& D = c.dev[l];
   DevLevel& Dc = c.dev[l + 1];
-  enqueue_smooth(c, prec, l, c.nu1, x, b, st);
+  enqueue_smooth(c, prec, l, level_sweeps(c, c.nu1, l), x, b, st);
   ck(run_element(c, l, prec, MODE_RESID, 0, D.ne, D.dia[prec], b, x, D.vr[vi], st), "residual launch");
   ck(launch_restrict(vi == 0, c.d, c.s, c.nb, Dc.n, D.n, Dc.ne, c.child_P[vi], D.vr[vi], Dc.vb[vi], st),
      "restrict launch");
   ck(cudaMemsetAsync(Dc.vx[vi], 0, (size_t)Dc.ne * c.nb * (vi == 0 ? 8 : 4), st), "memset");
   c.launches += 2;  // residual + restriction
-  enqueue_cycle(c, prec, l + 1, Dc.vx[vi], Dc.vb[vi], st);
+  for (int v = coarse_visits(c, l); v > 0; --v) enqueue_cycle(c, prec, l + 1, Dc.vx[vi], Dc.vb[vi], st);
   ck(launch_prolong(vi == 0, c.d, c.s, c.nb, D.n, Dc.n, Dc.ne, c.child_PT[vi], Dc.vx[vi], x, st),
      "prolong launch");
   c.launches++;
-  enqueue_smooth(c, prec, l, c.nu2, x, b, st);
+  enqueue_smooth(c, prec, l, level_sweeps(c, c.nu2, l), x, b, st);
   if (l == 0 && c.learn_on && prec != STK_FP64 && c.lW1) enqueue_learned(c, prec, x, b, st);
 }
 
@@ -631,7 +645,7 @@ void enqueue_cycle_mr(Ctx& c, int prec, int l, int nr, void* x, const void* b, c
         c.launches++;
       }
   };
-  smooth(c.nu1);
+  smooth(level_sweeps(c, c.nu1, l));
   ck(launch_element_mrhs(c.pat, prec, nr, MODE_RESID, 0, D.ne, D.perm, D.nbr, D.cpl[prec], D.dia[prec], b, x,
                          D.mr[vi], st, c.mrhs_tensor, c.wide_max),
      "residual launch");
@@ -639,11 +653,11 @@ void enqueue_cycle_mr(Ctx& c, int prec, int l, int nr, void* x, const void* b, c
      "restrict launch");
   ck(cudaMemsetAsync(Dc.mx[vi], 0, (size_t)Dc.ne * c.nb * nr * (vi == 0 ? 8 : 4), st), "memset");
   c.launches += 2;
-  enqueue_cycle_mr(c, prec, l + 1, nr, Dc.mx[vi], Dc.mb[vi], st);
+  for (int v = coarse_visits(c, l); v > 0; --v) enqueue_cycle_mr(c, prec, l + 1, nr, Dc.mx[vi], Dc.mb[vi], st);
   ck(launch_prolong_mr(vi == 0, c.d, c.s, c.nb, nr, D.n, Dc.n, Dc.ne, c.child_PT[vi], Dc.mx[vi], x, st),
      "prolong launch");
   c.launches++;
-  smooth(c.nu2);
+  smooth(level_sweeps(c, c.nu2, l));
 }
 
 // One outer iteration on the interleaved level-0 FP64 vectors mX, mB:
@@ -1264,6 +1278,18 @@ int stk_set_density(stk_ctx* c, const double* rho_vol, const double* rho_iface, 
   });
 }
 
+static void invalidate_graphs(Ctx& c) {
+  if (c.graph) cudaGraphExecDestroy(c.graph);
+  c.graph = nullptr;
+  c.graph_x = c.graph_b = nullptr;
+  if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
+  c.cycle_graph = nullptr;
+  c.cycle_graph_prec = -1;
+  if (c.mgraph) cudaGraphExecDestroy(c.mgraph);
+  c.mgraph = nullptr;
+  c.mgraph_key[0] = -1;
+}
+
 int stk_set_cycle(stk_ctx* c, int nu1, int nu2, int precision) {
   return guard(c, [&]() -> int {
     if (nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0 || precision < 0 || precision > 3)
@@ -1272,6 +1298,19 @@ int stk_set_cycle(stk_ctx* c, int nu1, int nu2, int precision) {
     c->nu1 = nu1;
     c->nu2 = nu2;
     c->precision = precision;
+    invalidate_graphs(*c);
+    return STK_OK;
+  });
+}
+
+int stk_set_cycle_shape(stk_ctx* c, int gamma, int growth, int max_sweeps) {
+  return guard(c, [&]() -> int {
+    if (gamma < 1 || gamma > 3 || growth < 1 || growth > 4 || max_sweeps < 1 || max_sweeps > 256)
+      return fail(c, STK_ERR_INVALID_ARG, "bad cycle shape");
+    c->cyc_gamma = gamma;
+    c->cyc_growth = growth;
+    c->cyc_cap = max_sweeps;
+    invalidate_graphs(*c);
     return STK_OK;
   });
 }
@@ -1899,18 +1938,6 @@ int stk_solve_multi(stk_ctx* c, double* X, const double* B, int nrhs, double rto
     if (iters_out) *iters_out = it;
     return STK_OK;
   });
-}
-
-static void invalidate_graphs(Ctx& c) {
-  if (c.graph) cudaGraphExecDestroy(c.graph);
-  c.graph = nullptr;
-  c.graph_x = c.graph_b = nullptr;
-  if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
-  c.cycle_graph = nullptr;
-  c.cycle_graph_prec = -1;
-  if (c.mgraph) cudaGraphExecDestroy(c.mgraph);
-  c.mgraph = nullptr;
-  c.mgraph_key[0] = -1;
 }
 
 // splitmix-style deterministic weight initialisation, uniform(-a, a)

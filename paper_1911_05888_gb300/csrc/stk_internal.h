@@ -95,6 +95,9 @@ struct Ctx {
   int scale_mu = 0;
   double delta = 0.0;
   int nu1 = 1, nu2 = 1, precision = 0;
+  // cycle shape: coarse-level visits per level (1 = V-cycle, 2 = W-cycle) and the
+  // per-level growth of the smoothing counts (variable V-cycle), capped
+  int cyc_gamma = 1, cyc_growth = 1, cyc_cap = 64;
   // derived
   int s = 0, nb = 0, q = 0;
   Pattern pat{};

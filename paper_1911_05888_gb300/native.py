@@ -40,6 +40,7 @@ SIGNATURES = {
     "stk_set_viscosity": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
     "stk_set_density": [_vp, _c_dbl_p, _c_dbl_p, ctypes.c_double],
     "stk_set_cycle": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "stk_set_cycle_shape": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "stk_setup": [_vp, _vp],
     "stk_get_sizes": [_vp, _c_int_p, _c_i64_p, _c_int_p, _c_int_p],
     "stk_get_block": [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _c_dbl_p],
@@ -198,6 +199,11 @@ class Context:
 
     def set_cycle(self, nu1, nu2, precision=FP64):
         self._check(self.lib.stk_set_cycle(self.h, nu1, nu2, precision), "stk_set_cycle")
+
+    def set_cycle_shape(self, gamma=1, growth=1, max_sweeps=64):
+        """gamma coarse visits per level (1 V-cycle, 2 W-cycle); smoothing
+        counts nu * growth^level, at most max(nu, max_sweeps)."""
+        self._check(self.lib.stk_set_cycle_shape(self.h, gamma, growth, max_sweeps), "stk_set_cycle_shape")
 
     def setup(self, stream=None):
         self._check(self.lib.stk_setup(self.h, _stream(stream)), "stk_setup")

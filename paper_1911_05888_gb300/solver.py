@@ -9,7 +9,7 @@ from .problems import PERIODIC, DIRICHLET, STRESS
 
 
 class StokesMG:
-    def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True):
+    def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True, shape=None):
         self.prob = prob
         self.ctx = native.Context(device)
         d = prob.d
@@ -31,6 +31,8 @@ class StokesMG:
             self.ctx.set_phases(self.chi, prob.mu_phase, scale=prob.scale_mu)
         nu1, nu2 = (prob.nu1, prob.nu2) if nu is None else nu
         self.ctx.set_cycle(nu1, nu2, precision)
+        if shape is not None:
+            self.ctx.set_cycle_shape(*shape)
         if setup:
             self.ctx.setup()
             self.nlevels, self.ne_levels, self.nb, self.n_snapped = self.ctx.sizes()

@@ -650,3 +650,70 @@ def test_fgmres_double_float_matvec(name, precision):
         assert np.all(np.abs(h1[big] - h0[big]) <= 1e-5 * h0[big] + 1e-13)
     Z = trivial_kernel(prob, get(name)[2])
     assert rel(x1 - Z @ (Z.T @ x1), x0 - Z @ (Z.T @ x0)) <= 1e-8
+
+
+@pytest.mark.parametrize("shape", [(2, 1, 64), (1, 2, 64), (3, 2, 6)])
+@pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-unsteady-p2"])
+def test_cycle_shapes_match_oracle(name, shape):
+    """W-cycles and variable V-cycles (Section 6) in FP64: four cycle iterates
+    (modulo the trivial kernel), one outer iteration for three right-hand sides
+    at once, and the graph-replayed solve equal the oracle's with the same
+    cycle shape; the shape is set after earlier solves, so cached graphs must
+    be rebuilt."""
+    prob, gpu, orc = get(name)
+    rng = np.random.default_rng(41)
+    Z = trivial_kernel(prob, orc)
+    b = rng.uniform(-1, 1, prob.n_dofs)
+    b -= Z @ (Z.T @ b)
+    gpu.ctx.set_cycle_shape(*shape)
+    orc.gamma, orc.growth, orc.max_sweeps = shape
+    try:
+        bd = dev(b)
+        xd = torch.zeros_like(bd)
+        xo = np.zeros(prob.n_dofs)
+        for k in range(4):
+            gpu.ctx.vcycle(xd, bd)
+            orc.vcycle(xo, b)
+            xg = xd.cpu().numpy()
+            assert rel(xg - Z @ (Z.T @ xg), xo - Z @ (Z.T @ xo)) <= 1e-12, k
+        X0 = rng.uniform(-1, 1, (3, prob.n_dofs))
+        B = rng.uniform(-1, 1, (3, prob.n_dofs))
+        Xd, Bd = dev(X0).reshape(3, -1), dev(B).reshape(3, -1)
+        it, _ = gpu.ctx.solve_multi(Xd, Bd, 3, rtol=1e-30, maxit=1, inner=1)
+        assert it == 1
+        Xg = Xd.cpu().numpy()
+        for q in range(3):
+            assert rel(Xg[q], X0[q] + orc.precondition(B[q] - orc.A @ X0[q])) <= 1e-12, q
+        bs = gpu.rhs().ravel()
+        xd = torch.zeros_like(dev(bs))
+        it, hist = gpu.ctx.solve(xd, dev(bs), rtol=1e-10, maxit=100)
+        xo, ho = orc.solve(bs, rtol=1e-10, maxit=100)
+        assert hist[-1] <= 1e-10 and abs(it - (len(ho) - 1)) <= 1
+        assert rel(xd.cpu().numpy(), xo) <= 1e-11
+    finally:
+        gpu.ctx.set_cycle_shape(1, 1, 64)
+        orc.gamma, orc.growth, orc.max_sweeps = 1, 1, 64
+
+
+@pytest.mark.parametrize("precision", [native.FP32, native.FP16])
+def test_w_cycle_low_precision_solve(precision):
+    """A W-cycle of FP32 / scaled-FP16 blocks inside FGMRES reaches 1e-10 in no
+    more iterations than the V-cycle of the same blocks, and a bad shape is
+    rejected."""
+    prob, gpu, _ = get("stress16p3", precision)
+    b = dev(gpu.rhs().ravel())
+    its = {}
+    gpu.ctx.set_solver(native.FGMRES, 30)
+    try:
+        for shape in [(1, 1, 64), (2, 1, 64)]:
+            gpu.ctx.set_cycle_shape(*shape)
+            x = torch.zeros_like(b)
+            its[shape], hist = gpu.ctx.solve(x, b, rtol=1e-10, maxit=60)
+            assert hist[-1] <= 1e-10, shape
+    finally:
+        gpu.ctx.set_cycle_shape(1, 1, 64)
+        gpu.ctx.set_solver(native.RICHARDSON, 30)
+    assert its[(2, 1, 64)] <= its[(1, 1, 64)], its
+    for bad in [(0, 1, 64), (4, 1, 64), (1, 0, 64), (1, 5, 64), (1, 1, 0), (1, 1, 257)]:
+        with pytest.raises(RuntimeError):
+            gpu.ctx.set_cycle_shape(*bad)

@@ -559,3 +559,74 @@ def test_multiphase_orders_and_rate(ratio):
     assert rate[2] > 1.9, rate
     rho, it = mg.gmres_rho(P.random_vector(prob.n_elements, prob.nb, seed=1).ravel())
     assert rho <= 0.16, rho
+
+
+# ------------------------------------------------------------ cycle shapes ----
+
+@pytest.mark.parametrize("shape", [(2, 1, 64), (3, 1, 64), (1, 2, 64), (1, 2, 5), (2, 3, 7)])
+def test_cycle_shape_visit_and_sweep_counts(shape):
+    """W-cycles and variable V-cycles (Section 6) in closed form: level l < L-1
+    is visited gamma^l times and smooths min(nu growth^l, max(nu, cap)) times
+    before and after the coarse correction on every visit; the exactly solved
+    bottom is entered once per visit of level L-2, gamma^(L-2) times."""
+    gamma, growth, cap = shape
+    prob = P.generic(2, 16, 1, 0, [P.DIRICHLET] * 3 + [P.STRESS], nu=(2, 1))
+    mg = multigrid.Multigrid(prob, shape=shape)
+    L = len(mg.levels)
+    assert L == 4
+    counts = [0] * (L - 1)
+    bottoms = [0]
+    for l, sm in enumerate(mg.sm):
+        def counted(x, b, l=l, f=sm.sweep):
+            counts[l] += 1
+            return f(x, b)
+        sm.sweep = counted
+    solve = mg.bottom_solve
+
+    def counted_bottom(b):
+        bottoms[0] += 1
+        return solve(b)
+    mg.bottom_solve = counted_bottom
+    b = np.random.default_rng(0).standard_normal(mg.A.shape[0])
+    mg.vcycle(np.zeros_like(b), b)
+    for l in range(L - 1):
+        per_visit = sum(min(nu * growth ** l, max(nu, cap)) for nu in (2, 1))
+        assert counts[l] == gamma ** l * per_visit, (l, counts)
+    assert bottoms[0] == gamma ** (L - 2)
+
+
+def test_w_cycle_limit_is_two_grid_cycle():
+    """With many coarse visits the W-cycle's coarse correction converges to
+    the exact coarse solution, so one cycle equals the two-grid cycle
+    S^nu2 (x + I A_1^{-1} I^T (b - A S^nu1 x)) with a dense solve on level 1
+    (kernel-free boundary conditions, three levels)."""
+    prob = P.generic(2, 8, 2, 0, [P.DIRICHLET] * 3 + [P.STRESS], nu=(2, 2))
+    mg = multigrid.Multigrid(prob, shape=(30, 1, 64))
+    assert len(mg.levels) == 3
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(mg.A.shape[0])
+    x0 = rng.standard_normal(mg.A.shape[0])
+    xw = mg.vcycle(x0.copy(), b)
+    x = x0.copy()
+    for _ in range(2):
+        mg.sm[0].sweep(x, b)
+    rc = mg.I[0].T @ (b - mg.A @ x)
+    x += mg.I[0] @ np.linalg.solve(mg.levels[1].A.toarray(), rc)
+    for _ in range(2):
+        mg.sm[0].sweep(x, b)
+    assert np.linalg.norm(xw - x) <= 1e-12 * np.linalg.norm(x)
+    # and a V-cycle is not that limit
+    xv = multigrid.Multigrid(prob).vcycle(x0.copy(), b)
+    assert np.linalg.norm(xv - x) >= 1e-4 * np.linalg.norm(x)
+
+
+def test_w_cycle_contracts_faster_than_v_cycle():
+    """More coarse-grid work per cycle (W, or the variable V-cycle) gives a
+    smaller rho of eq. (rho) than V(1,1) on the viscous-stress problem with
+    mixed boundary conditions (Section 6 names both as candidates)."""
+    prob = P.generic(2, 16, 2, 1, [P.DIRICHLET] * 3 + [P.STRESS], nu=(1, 1))
+    x0 = P.random_vector(prob.n_elements, prob.nb, seed=1).ravel()
+    rho_v, _ = multigrid.Multigrid(prob).gmres_rho(x0)
+    rho_w, _ = multigrid.Multigrid(prob, shape=(2, 1, 64)).gmres_rho(x0)
+    rho_vv, _ = multigrid.Multigrid(prob, shape=(1, 2, 64)).gmres_rho(x0)
+    assert rho_w < 0.9 * rho_v and rho_vv < 0.9 * rho_v, (rho_v, rho_w, rho_vv)
