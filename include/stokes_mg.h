@@ -243,6 +243,24 @@ int stk_prolong(stk_ctx* ctx, int level, const double* xc_dev, double* x_dev, vo
 int stk_bottom_solve(stk_ctx* ctx, const double* b_dev, double* x_dev, void* stream);
 
 /*
+ * Convergence rate rho of eq. (rho) (Section 4): GMRES, not restarted, on the
+ * left-preconditioned system V A x = V b with b = 0 from the initial guess
+ * x0_dev (caller-owned device array [element][nb], FP64, not modified); V is
+ * one cycle of the context's precision and shape from a zero guess.  Stops at
+ * the first iteration n with ||V A x_n|| <= reduction ||V A x_0|| (the paper
+ * uses 1e-8) or at maxit; *rho_out = (||V A x_n|| / ||V A x_0||)^(1/n),
+ * *iters_out = n (may be NULL).  hist (host, maxit+1 entries, may be NULL):
+ * the relative preconditioned residual per iteration.  hess (host,
+ * (maxit+1) x maxit row-major, may be NULL): the Arnoldi matrix before the
+ * Givens rotations; the eigenvalues of its leading n x n block estimate the
+ * spectrum of V A (Section 4's spectral estimate).  Errors:
+ * STK_ERR_NOT_SETUP, STK_ERR_INVALID_ARG (reduction outside (0,1), maxit
+ * outside 1..100, NULL x0_dev or rho_out), STK_ERR_TIMEOUT, STK_ERR_DIVERGED.
+ */
+int stk_gmres_rho(stk_ctx* ctx, const double* x0_dev, double reduction, int maxit, double* rho_out,
+                  int* iters_out, double* hist, double* hess, void* stream);
+
+/*
  * Solve A x = b to ||b - A x||_2 <= rtol ||b||_2 by the outer iteration
  * x <- x + V(0, b - A x) (iterative refinement with the V-cycle of
  * stk_set_cycle's precision as preconditioner; residual in FP64).  x_dev

@@ -305,9 +305,13 @@ class Multigrid:
             hist[-1] = np.linalg.norm(r) / bn
         return x, hist
 
-    def gmres_rho(self, x0, reduction=1e-8, maxit=200, **kw):
+    def gmres_rho(self, x0, reduction=1e-8, maxit=200, details=False, **kw):
         """eq. (rho): average reduction per iteration of left-preconditioned
-        GMRES on V A x = V b with b = 0 from x0; returns (rho, iterations)."""
+        GMRES on V A x = V b with b = 0 from x0; returns (rho, iterations),
+        with details=True also the relative preconditioned residual per
+        iteration and the Arnoldi matrix before the Givens rotations (its
+        leading n x n block's eigenvalues estimate the spectrum of V A, the
+        estimate Section 4 uses)."""
         A = self.A
 
         def op(v):
@@ -321,12 +325,15 @@ class Multigrid:
         g = np.zeros(maxit + 1)
         g[0] = beta
         n = 0
+        Hraw = np.zeros_like(H)
+        hist = [1.0]
         for j in range(maxit):
             w = op(Q[j])
             for i in range(j + 1):
                 H[i, j] = np.dot(Q[i], w)
                 w = w - H[i, j] * Q[i]
             H[j + 1, j] = np.linalg.norm(w)
+            Hraw[: j + 2, j] = H[: j + 2, j]
             Q.append(w / H[j + 1, j] if H[j + 1, j] > 0 else w)
             for i in range(j):
                 t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
@@ -339,6 +346,10 @@ class Multigrid:
             g[j + 1] = -sn[j] * g[j]
             g[j] = cs[j] * g[j]
             n = j + 1
+            hist.append(abs(g[n]) / beta)
             if abs(g[j + 1]) <= reduction * beta:
                 break
-        return float(np.exp(np.log(abs(g[n]) / beta) / n)), n
+        rho = float(np.exp(np.log(abs(g[n]) / beta) / n))
+        if details:
+            return rho, n, np.array(hist), Hraw
+        return rho, n

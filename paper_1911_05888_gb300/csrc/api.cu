@@ -923,10 +923,10 @@ int fgmres_mr(Ctx& c, int nr, int nrhs, double rtol, int maxit, double* hist, co
 }
 
 // ---- flexible GMRES with the V-cycle as right preconditioner ----------------
-void ensure_krylov(Ctx& c) {
-  if (c.kcap >= c.restart && c.kV) return;
+// Krylov buffers for m basis directions (m+1 vectors of V, m of Z).
+void ensure_krylov(Ctx& c, int m) {
+  if (c.kcap >= m && c.kV) return;
   int64_t n0 = level_ne(c, 0) * c.nb;
-  int m = c.restart;
   c.kV = (double*)dalloc(c, (size_t)(m + 1) * n0 * 8);
   c.kZ = (double*)dalloc(c, (size_t)m * n0 * 8);
   c.kw = (double*)dalloc(c, (size_t)n0 * 8);
@@ -1024,7 +1024,7 @@ double host_norm(Ctx& c, const double* v, cudaStream_t st) {
 // Returns the iteration count; rel holds the final true relative residual.
 int fgmres(Ctx& c, double* x, const double* b, double rtol, int maxit, double* hist, double bnorm,
            double& rel, cudaStream_t st) {
-  ensure_krylov(c);
+  ensure_krylov(c, c.restart);
   ensure_cycle_graph(c, st);
   int64_t n0 = level_ne(c, 0) * c.nb;
   const int m = c.restart;
@@ -1124,6 +1124,80 @@ int fgmres(Ctx& c, double* x, const double* b, double rtol, int maxit, double* h
     if (!std::isfinite(rel) || rel > 1e6 * rel0) break;
   }
   return it;
+}
+
+// eq. (rho): GMRES, not restarted, on the left-preconditioned system
+// V A x = V b with b = 0 from x0 (Section 4), V = one cycle of the context's
+// precision from a zero guess.  The preconditioned residual r_k = -V A x_k is
+// minimised over x0 + K_k(V A, r0); stops at the first n with
+// ||r_n|| <= reduction ||r_0|| or at maxit.  hist[k] = ||r_k|| / ||r_0||;
+// hess (optional) gets the Arnoldi matrix H (row-major, (maxit+1) x maxit)
+// before the Givens rotations, whose leading n x n block's eigenvalues
+// estimate the spectrum of V A (Section 4's spectral estimate).
+int gmres_rho(Ctx& c, const double* x0, double reduction, int maxit, double* hist, double* hess, double& rho,
+              cudaStream_t st) {
+  ensure_krylov(c, maxit);
+  ensure_cycle_graph(c, st);
+  const int64_t n0 = level_ne(c, 0) * c.nb;
+  const int m = maxit;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1, 0.0), cs(m), sn(m), h(m + 1), h2(m + 1), negh(m + 1);
+  // r0 = V(0 - A x0) = -V A x0
+  enqueue_residual64(c, x0, c.kzero, c.kw, st);
+  precondition(c, c.kw, c.kV, st);
+  const double beta = host_norm(c, c.kV, st);
+  if (hist) hist[0] = 1.0;
+  if (!(beta > 0) || !std::isfinite(beta)) {
+    rho = beta > 0 ? beta : 0.0;
+    return 0;
+  }
+  ck(launch_scale(n0, 1.0 / beta, c.kV, c.kV, st), "scale");
+  c.launches++;
+  g[0] = beta;
+  int n = 0;
+  for (int j = 0; j < m; ++j) {
+    double* vj = c.kV + (size_t)j * n0;
+    double* w = c.kV + (size_t)(j + 1) * n0;
+    // w = V A v_j: the residual kernel forms -A v_j, the cycle is linear
+    enqueue_residual64(c, vj, c.kzero, c.kw, st);
+    precondition(c, c.kw, w, st);
+    ck(launch_scale(n0, -1.0, w, w, st), "scale");
+    c.launches++;
+    // classical Gram-Schmidt, twice
+    host_dots(c, j + 1, c.kV, w, h.data(), st);
+    for (int i = 0; i <= j; ++i) negh[i] = -h[i];
+    host_axpy(c, j + 1, 1.0, negh.data(), c.kV, w, st);
+    host_dots(c, j + 1, c.kV, w, h2.data(), st);
+    for (int i = 0; i <= j; ++i) {
+      negh[i] = -h2[i];
+      h[i] += h2[i];
+    }
+    host_axpy(c, j + 1, 1.0, negh.data(), c.kV, w, st);
+    const double hn = host_norm(c, w, st);
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i];
+    H[(size_t)(j + 1) * m + j] = hn;
+    if (hess)
+      for (int i = 0; i <= j + 1; ++i) hess[(size_t)i * m + j] = H[(size_t)i * m + j];
+    if (hn > 0) {
+      ck(launch_scale(n0, 1.0 / hn, w, w, st), "scale");
+      c.launches++;
+    }
+    for (int i = 0; i < j; ++i) {
+      const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+      H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+      H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+    }
+    const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+    const double den = std::hypot(a, bb);
+    cs[j] = a / den;
+    sn[j] = bb / den;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    n = j + 1;
+    if (hist) hist[n] = std::fabs(g[n]) / beta;
+    if (!std::isfinite(g[n]) || std::fabs(g[n]) <= reduction * beta || hn == 0) break;
+  }
+  rho = std::exp(std::log(std::fabs(g[n]) / beta) / n);
+  return n;
 }
 
 }  // namespace
@@ -1826,6 +1900,28 @@ int stk_set_mrhs_tensor(stk_ctx* c, int on) {
     if (c->mgraph) cudaGraphExecDestroy(c->mgraph);
     c->mgraph = nullptr;
     c->mgraph_key[0] = -1;
+    return STK_OK;
+  });
+}
+
+int stk_gmres_rho(stk_ctx* c, const double* x0, double reduction, int maxit, double* rho_out, int* iters_out,
+                  double* hist, double* hess, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (!x0 || !rho_out || !(reduction > 0 && reduction < 1) || maxit < 1 || maxit > 100)
+      return fail(c, STK_ERR_INVALID_ARG, "bad arguments (reduction in (0,1), maxit 1..100)");
+    ck(cudaStreamSynchronize((cudaStream_t)stream), "sync caller stream");
+    if (hess) std::fill(hess, hess + (size_t)(maxit + 1) * maxit, 0.0);
+    double rho = 0;
+    int n = 0;
+    try {
+      n = gmres_rho(*c, x0, reduction, maxit, hist, hess, rho, c->stream);
+    } catch (const Timeout&) {
+      return fail(c, STK_ERR_TIMEOUT, "a kernel's bounded wait for its records expired");
+    }
+    *rho_out = rho;
+    if (iters_out) *iters_out = n;
+    if (!std::isfinite(rho)) return fail(c, STK_ERR_DIVERGED, "GMRES residual not finite");
     return STK_OK;
   });
 }

@@ -41,6 +41,7 @@ SIGNATURES = {
     "stk_set_density": [_vp, _c_dbl_p, _c_dbl_p, ctypes.c_double],
     "stk_set_cycle": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "stk_set_cycle_shape": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "stk_gmres_rho": [_vp, _vp, ctypes.c_double, ctypes.c_int, _c_dbl_p, _c_int_p, _c_dbl_p, _c_dbl_p, _vp],
     "stk_setup": [_vp, _vp],
     "stk_get_sizes": [_vp, _c_int_p, _c_i64_p, _c_int_p, _c_int_p],
     "stk_get_block": [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _c_dbl_p],
@@ -271,6 +272,20 @@ class Context:
                                 hist.ctypes.data_as(_c_dbl_p), _stream(stream))
         self._check(rc, "stk_solve")
         return it.value, hist[: it.value + 1]
+
+    def gmres_rho(self, x0, reduction=1e-8, maxit=100, stream=None):
+        """eq. (rho): (rho, iterations, relative preconditioned residual
+        history, Arnoldi matrix (maxit+1) x maxit) of left-preconditioned
+        GMRES on V A x = 0 from the device vector x0."""
+        rho = ctypes.c_double()
+        it = ctypes.c_int()
+        hist = np.zeros(maxit + 1)
+        hess = np.zeros((maxit + 1, maxit))
+        self._check(self.lib.stk_gmres_rho(self.h, _ptr(x0), reduction, maxit, ctypes.byref(rho), ctypes.byref(it),
+                                           hist.ctypes.data_as(_c_dbl_p), hess.ctypes.data_as(_c_dbl_p),
+                                           _stream(stream)), "stk_gmres_rho")
+        n = it.value
+        return rho.value, n, hist[: n + 1], hess
 
     def residual_norm_static(self, x, b, r, norm2, stream=None):
         """stk_residual_norm_static: r = b - A x and ||r||^2 into the device

@@ -630,3 +630,27 @@ def test_w_cycle_contracts_faster_than_v_cycle():
     rho_w, _ = multigrid.Multigrid(prob, shape=(2, 1, 64)).gmres_rho(x0)
     rho_vv, _ = multigrid.Multigrid(prob, shape=(1, 2, 64)).gmres_rho(x0)
     assert rho_w < 0.9 * rho_v and rho_vv < 0.9 * rho_v, (rho_v, rho_w, rho_vv)
+
+
+def test_gmres_rho_history_and_spectrum_estimate():
+    """Left-preconditioned GMRES of eq. (rho): every recorded residual equals
+    the least-squares minimum min_y ||beta e1 - H_k y|| recomputed by numpy
+    from the Arnoldi matrix; rho^n equals the final reduction; and the Ritz
+    values of H_n (Section 4's GMRES estimate of the spectrum of V A) cluster
+    tightly around 1 at Table 1's tau and spread for tau well above it."""
+    spread = {}
+    for tau in (None, 1.0):
+        prob = P.periodic_standard_2d(n=16, p=2, nu=(3, 3), tau=tau)
+        mg = multigrid.Multigrid(prob)
+        x0 = P.random_vector(prob.n_elements, prob.nb, seed=1).ravel()
+        rho, n, hist, H = mg.gmres_rho(x0, details=True)
+        assert np.allclose(np.triu(H[: n + 1, :n], -1), H[: n + 1, :n])       # upper Hessenberg
+        e1 = np.zeros(n + 1)
+        e1[0] = 1.0
+        for k in range(1, n + 1):
+            y = np.linalg.lstsq(H[: k + 1, :k], e1[: k + 1], rcond=None)[0]
+            assert abs(np.linalg.norm(e1[: k + 1] - H[: k + 1, :k] @ y) - hist[k]) <= 1e-10 * hist[k]
+        assert hist[n] <= 1e-8 < hist[n - 1]
+        assert abs(rho ** n - hist[n]) <= 1e-12 * hist[n]
+        spread[tau] = np.abs(np.linalg.eigvals(H[:n, :n]) - 1.0).max()
+    assert spread[None] <= 0.25 and spread[1.0] >= 2 * spread[None], spread
