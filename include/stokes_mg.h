@@ -239,6 +239,21 @@ int stk_vcycle(stk_ctx* ctx, double* x_dev, const double* b_dev, void* stream);
  * x += I_2h^h x_c (level+1 -> level), FP64 (the transfers of Algorithm 1). */
 int stk_restrict(stk_ctx* ctx, int level, const double* r_dev, double* rc_dev, void* stream);
 int stk_prolong(stk_ctx* ctx, int level, const double* xc_dev, double* x_dev, void* stream);
+/*
+ * The bottom solver's least-squares (Moore-Penrose) inverse on the host
+ * (Section 3 footnote) of the symmetric n x n matrix A (row-major host array,
+ * caller-owned, not modified; its symmetric part is used).  A is equilibrated
+ * to A^ = S A S (S_i = row 1-norm^(-1/2)); the eigenvalues of A^ with
+ * |lambda| <= theta max|lambda| are snapped to zero (Householder reduction to
+ * tridiagonal form, shifted implicit QR; cyclic Jacobi if that does not
+ * converge), and the result is projected off the kernel of A.  pinv:
+ * caller-owned host array n x n; *snapped (may be NULL) = eigenvalues set to
+ * zero.  Needs no device; stk_setup uses it for bottom levels of 301 to 1200
+ * unknowns.  Errors: STK_ERR_INVALID_ARG (n outside 1..20000, NULL arrays,
+ * theta outside [0,1)), STK_ERR_OOM.
+ */
+int stk_host_pseudo_inverse(int n, const double* A, double theta, double* pinv, int* snapped);
+
 /* Bottom solve x = A_c^+ b on the last level (FP64). */
 int stk_bottom_solve(stk_ctx* ctx, const double* b_dev, double* x_dev, void* stream);
 

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <limits>
 #include <thread>
 
 #include "stk_internal.h"
@@ -305,6 +306,232 @@ int pseudo_inverse_jacobi(int n, std::vector<double>& A, std::vector<double>& pi
       if (f == 0.0) continue;
       for (int j = 0; j < n; ++j) pinv[(size_t)i * n + j] += f * V[(size_t)j * n + k];
     }
+  return STK_OK;
+}
+
+// Symmetric eigendecomposition by Householder reduction to tridiagonal form
+// and the implicit symmetric QR iteration with Wilkinson shifts (the textbook
+// method, e.g. Golub and Van Loan, Matrix Computations, Sections 8.3.1-8.3.3).
+// A (row-major, symmetric, destroyed) = sum_k lam[k] q_k q_k^T with q_k the
+// rows of Qt.  O(n^3) once, against cyclic Jacobi's O(n^3) per sweep.
+// Returns false if the QR iteration does not converge in 30 n steps.
+static bool symmetric_eigen(int n, std::vector<double>& A, std::vector<double>& lam, std::vector<double>& Qt) {
+  std::vector<double> d(n, 0.0), e(std::max(n - 1, 1), 0.0), beta(std::max(n, 1), 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double m = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = m;
+    }
+  // 1. Householder: H_k = I - beta_k v v^T maps A[k+1:, k] to e[k] e_1; the
+  //    reflector v is kept in row k of A (right of the diagonal).
+  std::vector<double> pv(n), w(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    double* v = &A[(size_t)k * n + k + 1];
+    const int m = n - k - 1;
+    double alpha = 0.0;
+    for (int i = 0; i < m; ++i) alpha += v[i] * v[i];
+    alpha = std::sqrt(alpha);
+    d[k] = A[(size_t)k * n + k];
+    if (alpha == 0.0) {
+      e[k] = 0.0;
+      beta[k] = 0.0;
+      continue;
+    }
+    const double sg = v[0] >= 0 ? 1.0 : -1.0;
+    e[k] = -sg * alpha;
+    v[0] += sg * alpha;
+    double vv = 0.0;
+    for (int i = 0; i < m; ++i) vv += v[i] * v[i];
+    const double b = 2.0 / vv;
+    beta[k] = b;
+    // trailing block B = A[k+1:, k+1:]: p = b B v, w = p - (b/2)(p.v) v,
+    // B <- B - v w^T - w v^T
+    double pvdot = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double* Bi = &A[(size_t)(k + 1 + i) * n + k + 1];
+      double acc = 0.0;
+      for (int j = 0; j < m; ++j) acc += Bi[j] * v[j];
+      pv[i] = b * acc;
+      pvdot += pv[i] * v[i];
+    }
+    const double K = 0.5 * b * pvdot;
+    for (int i = 0; i < m; ++i) w[i] = pv[i] - K * v[i];
+    for (int i = 0; i < m; ++i) {
+      double* Bi = &A[(size_t)(k + 1 + i) * n + k + 1];
+      const double vi = v[i], wi = w[i];
+      for (int j = 0; j < m; ++j) Bi[j] -= vi * w[j] + wi * v[j];
+    }
+  }
+  if (n >= 2) {
+    d[n - 2] = A[(size_t)(n - 2) * n + n - 2];
+    e[n - 2] = A[(size_t)(n - 2) * n + n - 1];
+  }
+  d[n - 1] = A[(size_t)(n - 1) * n + n - 1];
+  // Qt = Q^T = H_{n-3} ... H_1 H_0 (rows k+1.. of Qt touched by H_k)
+  Qt.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
+  std::vector<double> u(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    if (beta[k] == 0.0) continue;
+    const double* v = &A[(size_t)k * n + k + 1];
+    const int m = n - k - 1;
+    std::fill(u.begin(), u.end(), 0.0);
+    for (int i = 0; i < m; ++i) {
+      const double* row = &Qt[(size_t)(k + 1 + i) * n];
+      for (int j = 0; j < n; ++j) u[j] += v[i] * row[j];
+    }
+    for (int i = 0; i < m; ++i) {
+      double* row = &Qt[(size_t)(k + 1 + i) * n];
+      const double f = beta[k] * v[i];
+      for (int j = 0; j < n; ++j) row[j] -= f * u[j];
+    }
+  }
+  // 2. Implicit symmetric QR on (d, e): each step chases the bulge of one
+  //    Wilkinson-shifted rotation down the unreduced block [l, m]; the
+  //    rotations R act as T <- R T R^T and Qt <- R Qt on rows k, k+1.
+  //    An off-diagonal entry counts as zero below eps times its two diagonal
+  //    neighbours or eps times the largest row sum of T (a backward error of
+  //    the size every stable eigensolver makes).
+  const double eps = 0.5 * std::numeric_limits<double>::epsilon();
+  double tnorm = 0.0;
+  for (int i = 0; i < n; ++i)
+    tnorm = std::max(tnorm, std::fabs(d[i]) + (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(e[i]) : 0.0));
+  auto negligible = [&](int i) {
+    const double a = std::fabs(e[i]);
+    return a <= eps * (std::fabs(d[i]) + std::fabs(d[i + 1])) || a <= eps * tnorm;
+  };
+  int m = n - 1, steps = 0;
+  while (m > 0) {
+    if (negligible(m - 1)) {
+      e[m - 1] = 0.0;
+      --m;
+      continue;
+    }
+    int l = m - 1;
+    while (l > 0 && !negligible(l - 1)) --l;
+    if (++steps > 30 * n) return false;
+    const double delta = 0.5 * (d[m - 1] - d[m]), bm = e[m - 1];
+    const double mu = d[m] - bm * bm / (delta + std::copysign(std::hypot(delta, bm), delta));
+    double x = d[l] - mu, z = e[l];
+    for (int k = l; k < m; ++k) {
+      const double r = std::hypot(x, z);
+      const double c = r == 0.0 ? 1.0 : x / r, sn = r == 0.0 ? 0.0 : z / r;
+      if (k > l) e[k - 1] = r;
+      const double a = d[k], b = e[k], cc = d[k + 1];
+      d[k] = c * c * a + 2.0 * c * sn * b + sn * sn * cc;
+      d[k + 1] = sn * sn * a - 2.0 * c * sn * b + c * c * cc;
+      e[k] = c * sn * (cc - a) + (c * c - sn * sn) * b;
+      if (k + 1 < m) {
+        z = sn * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+        x = e[k];
+      }
+      double* q0 = &Qt[(size_t)k * n];
+      double* q1 = &Qt[(size_t)(k + 1) * n];
+      for (int j = 0; j < n; ++j) {
+        const double t0 = q0[j], t1 = q1[j];
+        q0[j] = c * t0 + sn * t1;
+        q1[j] = -sn * t0 + c * t1;
+      }
+    }
+  }
+  lam = d;
+  return true;
+}
+
+// Least-squares (Moore-Penrose) inverse of a symmetric matrix, the bottom
+// solver of Section 3's footnote.  The matrix is first equilibrated,
+// A^ = S A S with S_i = (sum_j |A_ij|)^(-1/2): the eigenvalues of A^ with
+// |lambda| <= theta max|lambda| are snapped to zero (a congruence keeps the
+// number of zero eigenvalues, so an exact kernel is snapped alike), and
+// G = S A^+ S solves A x = b for every b in the range of A.  With K the
+// kernel of A (S times the snapped eigenvectors, orthonormalised) and
+// P = I - K K^T, the least-squares inverse is P G P.  The equilibration keeps
+// the blocks' graded scales (velocity against pressure rows, phases of
+// different viscosity) out of the eigensolver's rounding error.
+int pseudo_inverse_sym(int n, std::vector<double>& A, std::vector<double>& pinv, int& snapped, double theta) {
+  if (n < 1) return STK_ERR_INVALID_ARG;
+  std::vector<double> S(n, 1.0);
+  for (int i = 0; i < n; ++i) {
+    double r = 0.0;
+    for (int j = 0; j < n; ++j) r += std::fabs(A[(size_t)i * n + j]);
+    if (r > 0 && std::isfinite(r)) S[i] = 1.0 / std::sqrt(r);
+  }
+  std::vector<double> Ah((size_t)n * n), lam, Qt;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Ah[(size_t)i * n + j] = S[i] * A[(size_t)i * n + j] * S[j];
+  if (!symmetric_eigen(n, Ah, lam, Qt)) return pseudo_inverse_jacobi(n, A, pinv, snapped, theta);
+  double lmax = 0.0;
+  for (int i = 0; i < n; ++i) lmax = std::max(lmax, std::fabs(lam[i]));
+  std::vector<double> inv(n, 0.0);
+  std::vector<int> kern;
+  for (int i = 0; i < n; ++i) {
+    if (std::fabs(lam[i]) <= theta * lmax) kern.push_back(i);
+    else inv[i] = 1.0 / lam[i];
+  }
+  snapped = (int)kern.size();
+  // G = S (sum_k q_k q_k^T / lam_k) S
+  pinv.assign((size_t)n * n, 0.0);
+  parallel_for(n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      double* row = &pinv[(size_t)i * n];
+      for (int k = 0; k < n; ++k) {
+        const double f = Qt[(size_t)k * n + i] * inv[k];
+        if (f == 0.0) continue;
+        const double* q = &Qt[(size_t)k * n];
+        for (int j = 0; j < n; ++j) row[j] += f * q[j];
+      }
+      for (int j = 0; j < n; ++j) row[j] *= S[i] * S[j];
+    }
+  });
+  const int nk = snapped;
+  if (nk == 0) return STK_OK;
+  // K: S q_k for the snapped k, orthonormalised by Gram-Schmidt done twice
+  std::vector<double> K((size_t)nk * n);
+  for (int a = 0; a < nk; ++a) {
+    double* ka = &K[(size_t)a * n];
+    for (int j = 0; j < n; ++j) ka[j] = S[j] * Qt[(size_t)kern[a] * n + j];
+    for (int pass = 0; pass < 2; ++pass)
+      for (int bb = 0; bb < a; ++bb) {
+        const double* kb = &K[(size_t)bb * n];
+        double dot = 0.0;
+        for (int j = 0; j < n; ++j) dot += kb[j] * ka[j];
+        for (int j = 0; j < n; ++j) ka[j] -= dot * kb[j];
+      }
+    double nrm = 0.0;
+    for (int j = 0; j < n; ++j) nrm += ka[j] * ka[j];
+    nrm = std::sqrt(nrm);
+    for (int j = 0; j < n; ++j) ka[j] = nrm > 0 ? ka[j] / nrm : 0.0;
+  }
+  // pinv <- P G P with P = I - K^T K (K's rows orthonormal); G symmetric
+  std::vector<double> GK((size_t)n * nk, 0.0), KGK((size_t)nk * nk, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < nk; ++a) {
+      double acc = 0.0;
+      const double* ka = &K[(size_t)a * n];
+      const double* gi = &pinv[(size_t)i * n];
+      for (int j = 0; j < n; ++j) acc += gi[j] * ka[j];
+      GK[(size_t)i * nk + a] = acc;
+    }
+  for (int a = 0; a < nk; ++a)
+    for (int bb = 0; bb < nk; ++bb) {
+      double acc = 0.0;
+      for (int i = 0; i < n; ++i) acc += K[(size_t)a * n + i] * GK[(size_t)i * nk + bb];
+      KGK[(size_t)a * nk + bb] = acc;
+    }
+  // P G P = G - GK K - K^T GK^T + K^T (K G K^T) K
+  parallel_for(n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      double* row = &pinv[(size_t)i * n];
+      for (int a = 0; a < nk; ++a) {
+        const double* ka = &K[(size_t)a * n];
+        double ci = -GK[(size_t)i * nk + a];
+        for (int bb = 0; bb < nk; ++bb) ci += K[(size_t)bb * n + i] * KGK[(size_t)bb * nk + a];
+        const double kia = K[(size_t)a * n + i];
+        for (int j = 0; j < n; ++j) row[j] += ci * ka[j] - kia * GK[(size_t)j * nk + a];
+      }
+    }
+  });
   return STK_OK;
 }
 
@@ -1337,3 +1564,18 @@ void interface_info(const Ctx& c, std::vector<int>& chim, std::vector<int>& chip
 }
 
 }  // namespace stk
+
+extern "C" int stk_host_pseudo_inverse(int n, const double* A, double theta, double* pinv, int* snapped) {
+  if (n < 1 || n > 20000 || !A || !pinv || !(theta >= 0 && theta < 1)) return STK_ERR_INVALID_ARG;
+  try {
+    std::vector<double> a(A, A + (size_t)n * n), p;
+    int sn = 0;
+    int rc = stk::pseudo_inverse_sym(n, a, p, sn, theta);
+    if (rc != STK_OK) return rc;
+    std::copy(p.begin(), p.end(), pinv);
+    if (snapped) *snapped = sn;
+    return STK_OK;
+  } catch (const std::bad_alloc&) {
+    return STK_ERR_OOM;
+  }
+}

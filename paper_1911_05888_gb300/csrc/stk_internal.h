@@ -194,6 +194,7 @@ int setup_host(Ctx& c);                    // fine assembly, coarsening, Stokes 
 void child_matrices(int d, int p, std::vector<double>& out);   // [2^d][s][s]
 void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w);
 int invert_blocks(int n, int count, const double* A, double* Ainv, std::string& err);
+int pseudo_inverse_sym(int n, std::vector<double>& A, std::vector<double>& pinv, int& snapped, double theta);
 int pseudo_inverse_jacobi(int n, std::vector<double>& A, std::vector<double>& pinv, int& snapped,
                           double theta);
 void element_index(const int* n, int d, int64_t e, int* idx);

@@ -41,6 +41,7 @@ SIGNATURES = {
     "stk_set_density": [_vp, _c_dbl_p, _c_dbl_p, ctypes.c_double],
     "stk_set_cycle": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "stk_set_cycle_shape": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "stk_host_pseudo_inverse": [ctypes.c_int, _c_dbl_p, ctypes.c_double, _c_dbl_p, _c_int_p],
     "stk_gmres_rho": [_vp, _vp, ctypes.c_double, ctypes.c_int, _c_dbl_p, _c_int_p, _c_dbl_p, _c_dbl_p, _vp],
     "stk_setup": [_vp, _vp],
     "stk_get_sizes": [_vp, _c_int_p, _c_i64_p, _c_int_p, _c_int_p],
@@ -438,3 +439,20 @@ def solve_batch(contexts, xs, bs, rtol=1e-10, maxit=200, nrhs=1, inner=3, thread
         raise StkError("stk_solve_batch: problem %d: %s (%s)" % (i, msg.decode() if msg else "",
                                                                 ERRORS.get(rc, rc)))
     return list(it), list(st)
+
+
+def host_pseudo_inverse(A, theta=1e-10):
+    """stk_host_pseudo_inverse: the bottom solver's least-squares inverse of
+    the symmetric matrix A on the host (no device needed).  Returns
+    (pinv, number of eigenvalues snapped to zero)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    if A.shape != (n, n):
+        raise ValueError("square matrix expected")
+    out = np.zeros((n, n))
+    sn = ctypes.c_int()
+    rc = load().stk_host_pseudo_inverse(n, A.ctypes.data_as(_c_dbl_p), theta, out.ctypes.data_as(_c_dbl_p),
+                                        ctypes.byref(sn))
+    if rc != STK_OK:
+        raise StkError("stk_host_pseudo_inverse: %s" % ERRORS.get(rc, rc))
+    return out, sn.value
