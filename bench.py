@@ -106,15 +106,26 @@ def config(args, prob):
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample: the same problem on a 64 x 64 mesh)
 # ---------------------------------------------------------------------------
+def cycle_name(args):
+    """V(nu1,nu2), W(nu1,nu2), ... with the growth of the variable V-cycle."""
+    g, growth, cap = shape_of(args)
+    nu2 = args.nu if args.nu2 is None else args.nu2
+    name = {1: "V", 2: "W"}.get(g, "gamma%d-" % g) + "(%d,%d)" % (args.nu, nu2)
+    return name + (" growth %d cap %d" % (growth, cap) if growth > 1 else "")
+
+
 def cpu_child(spec):
-    """Runs in a fresh single-threaded process: time oracle V-cycles plus the
-    outer residual on the sample problem; prints one JSON line."""
-    n, p, nu, seconds = [float(v) for v in spec.split(",")]
-    n, p, nu = int(n), int(p), int(nu)
+    """Runs in a fresh single-threaded process: time oracle cycles plus the
+    outer residual on the sample problem; prints one JSON line.  spec:
+    n,p,nu1,nu2,seconds,gamma,growth,max_sweeps."""
+    v = spec.split(",")
+    n, p, nu1, nu2 = (int(t) for t in v[:4])
+    seconds = float(v[4])
+    shape = tuple(int(t) for t in v[5:8])
     import numpy as np
     from oracle import multigrid
-    prob = workload(n, p).with_(nu1=nu, nu2=nu)
-    mg = multigrid.Multigrid(prob)
+    prob = workload(n, p).with_(nu1=nu1, nu2=nu2)
+    mg = multigrid.Multigrid(prob, shape=shape)
     rng = np.random.default_rng(0)
     b = rng.uniform(-1, 1, prob.n_dofs)
     x = np.zeros_like(b)
@@ -132,15 +143,16 @@ def cpu_child(spec):
 def cpu_baseline(args, seconds=12.0):
     n = min(args.n, 64)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child",
-                          "%d,%d,%d,%f" % (n, args.p, args.nu, seconds)], capture_output=True, text=True, env=env,
-                         timeout=900)
+    nu2 = args.nu if args.nu2 is None else args.nu2
+    spec = "%d,%d,%d,%d,%f,%d,%d,%d" % ((n, args.p, args.nu, nu2, seconds) + tuple(shape_of(args)))
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", spec], capture_output=True,
+                         text=True, env=env, timeout=900)
     rec = json.loads(out.stdout.strip().splitlines()[-1])
     value = rec["dofs"] * rec["cycles"] / rec["seconds"]
     return {"value": value, "unit": "DOF-cycles/s", "cores": 1, "kind": "oracle",
-            "sample": "same problem class on a %dx%d mesh (p=%d, %d DOFs): %d V(%d,%d) cycles + FP64 "
+            "sample": "same problem class on a %dx%d mesh (p=%d, %d DOFs): %d %s cycles + FP64 "
                       "residuals in %.1f s, numpy/scipy single thread" % (n, n, args.p, rec["dofs"],
-                                                                          rec["cycles"], args.nu, args.nu,
+                                                                          rec["cycles"], cycle_name(args),
                                                                           rec["seconds"])}
 
 
@@ -493,8 +505,8 @@ def run_reference(args):
     n = min(args.n, 64)
     import numpy as np
     from oracle import multigrid
-    prob = workload(n, args.p).with_(nu1=args.nu, nu2=args.nu)
-    mg = multigrid.Multigrid(prob)
+    prob = workload(n, args.p).with_(nu1=args.nu, nu2=args.nu if args.nu2 is None else args.nu2)
+    mg = multigrid.Multigrid(prob, shape=tuple(shape_of(args)))
     b = np.random.default_rng(0).uniform(-1, 1, prob.n_dofs)
     x = np.zeros_like(b)
 
@@ -514,8 +526,8 @@ def run_reference(args):
         tot_s += s
     value = prob.n_dofs * tot_c / tot_s
     sample = ("oracle (numpy/scipy, single process) on the same problem class at %dx%d, p=%d "
-              "(%d DOFs); each step = %.0f s of V(%d,%d) cycles with FP64 residuals" % (
-                  n, n, args.p, prob.n_dofs, per_step, args.nu, args.nu))
+              "(%d DOFs); each step = %.0f s of %s cycles with FP64 residuals" % (
+                  n, n, args.p, prob.n_dofs, per_step, cycle_name(args)))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-cycles/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,

@@ -49,3 +49,20 @@ def test_reference_arm_nonzero_rank_exits_without_work():
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_cpu_child_runs_the_configured_cycle_shape():
+    """The oracle arm's sample process takes the native arm's cycle: V(2,1)
+    and W(2,1) on the same 8 x 8 p=1 sample; a W-cycle costs more per cycle,
+    so fewer of them fit the same time."""
+    recs = {}
+    for shape in ("1,1,64", "2,1,64"):
+        p = subprocess.run([sys.executable, "bench.py", "--cpu-child", "8,1,2,1,0.5," + shape], cwd=ROOT,
+                           capture_output=True, text=True, timeout=300)
+        assert p.returncode == 0, p.stderr
+        recs[shape] = __import__("json").loads(p.stdout.strip().splitlines()[-1])
+    assert recs["1,1,64"]["dofs"] == recs["2,1,64"]["dofs"] == 8 * 8 * 3 * 4
+    assert recs["2,1,64"]["cycles"] >= 2
+    v = recs["1,1,64"]["cycles"] / recs["1,1,64"]["seconds"]
+    w = recs["2,1,64"]["cycles"] / recs["2,1,64"]["seconds"]
+    assert w < v
