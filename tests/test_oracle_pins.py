@@ -620,6 +620,28 @@ def test_w_cycle_limit_is_two_grid_cycle():
     assert np.linalg.norm(xv - x) >= 1e-4 * np.linalg.norm(x)
 
 
+def test_variable_v_cycle_limit_is_two_grid_cycle():
+    """A variable V-cycle whose smoothing on level 1 grows without bound (200
+    sweeps per phase there) solves the level-1 problem exactly, so one cycle
+    equals the same two-grid cycle with a dense coarse solve (three levels,
+    kernel-free boundary conditions); the finest level keeps nu = 2."""
+    prob = P.generic(2, 8, 2, 0, [P.DIRICHLET] * 3 + [P.STRESS], nu=(2, 2))
+    mg = multigrid.Multigrid(prob, shape=(1, 100, 400))
+    assert mg.sweeps(2, 0) == 2 and mg.sweeps(2, 1) == 200
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(mg.A.shape[0])
+    x0 = rng.standard_normal(mg.A.shape[0])
+    xv = mg.vcycle(x0.copy(), b)
+    x = x0.copy()
+    for _ in range(2):
+        mg.sm[0].sweep(x, b)
+    rc = mg.I[0].T @ (b - mg.A @ x)
+    x += mg.I[0] @ np.linalg.solve(mg.levels[1].A.toarray(), rc)
+    for _ in range(2):
+        mg.sm[0].sweep(x, b)
+    assert np.linalg.norm(xv - x) <= 1e-12 * np.linalg.norm(x)
+
+
 def test_w_cycle_contracts_faster_than_v_cycle():
     """More coarse-grid work per cycle (W, or the variable V-cycle) gives a
     smaller rho of eq. (rho) than V(1,1) on the viscous-stress problem with
