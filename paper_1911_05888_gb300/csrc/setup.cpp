@@ -914,15 +914,29 @@ static void fine_assembly(Ctx& c, const Tensors& T, HostLevel& L) {
   parallel_for(ne, [&](int64_t a, int64_t b) {
     for (int64_t e = a; e < b; ++e) {
       for (int i = 0; i < s; ++i) L.M[(size_t)e * ss + i * s + i] = L.vol;
+      // M_mu (and M_rho) = sum_q w_q mu_q phi(x_q) phi(x_q)^T, one rank-one
+      // update per quadrature point, row by row (vectorisable inner loop)
+      double* __restrict__ mm = &L.Mmu[(size_t)e * ss];
       for (int qi = 0; qi < T.Q; ++qi) {
-        double wm = jac * T.wQ[qi] * c.mu_vol[(size_t)e * T.Q + qi];
-        double wr = unsteady ? jac * T.wQ[qi] * c.rho_vol[(size_t)e * T.Q + qi] : 0.0;
-        const double* ph = &T.Phi[(size_t)qi * s];
-        for (int i = 0; i < s; ++i)
-          for (int j = 0; j < s; ++j) {
-            L.Mmu[(size_t)e * ss + i * s + j] += wm * ph[i] * ph[j];
-            if (unsteady) L.Mrho[(size_t)e * ss + i * s + j] += wr * ph[i] * ph[j];
+        const double wm = jac * T.wQ[qi] * c.mu_vol[(size_t)e * T.Q + qi];
+        const double* __restrict__ ph = &T.Phi[(size_t)qi * s];
+        for (int i = 0; i < s; ++i) {
+          const double a = wm * ph[i];
+          double* __restrict__ row = mm + i * s;
+          for (int j = 0; j < s; ++j) row[j] += a * ph[j];
+        }
+      }
+      if (unsteady) {
+        double* __restrict__ mr = &L.Mrho[(size_t)e * ss];
+        for (int qi = 0; qi < T.Q; ++qi) {
+          const double wr = jac * T.wQ[qi] * c.rho_vol[(size_t)e * T.Q + qi];
+          const double* __restrict__ ph = &T.Phi[(size_t)qi * s];
+          for (int i = 0; i < s; ++i) {
+            const double a = wr * ph[i];
+            double* __restrict__ row = mr + i * s;
+            for (int j = 0; j < s; ++j) row[j] += a * ph[j];
           }
+        }
       }
       for (int k = 0; k < d; ++k)
         axpy_block(s, 1.0 / L.h[k], T.Kax[k], &L.G[(((size_t)k * ne + e) * kGS + 0) * ss]);
@@ -1168,10 +1182,23 @@ static int pen_slot(int d, const int* o) {
   return o[k] < 0 ? slot_minus(k) : slot_plus(k);
 }
 
+// Per-thread cache of the viscous term sum_k sum_E G_k(E, a)^T M_mu(E) G_k(E, a+o)
+// of one element a, keyed by the offset o (each component in [-2, 2]): every
+// diagonal velocity block (i, i) at offset o shares it.
+struct LapCache {
+  std::vector<double> val;
+  std::vector<int64_t> owner;   // element whose term the slot holds, -1 if none
+  void init(int ss) {
+    val.assign((size_t)125 * ss, 0.0);
+    owner.assign(125, -1);
+  }
+  static int key(const int* o) { return (o[0] + 2) * 25 + (o[1] + 2) * 5 + (o[2] + 2); }
+};
+
 // s x s block of the operator, row variable rv at element a, column variable
 // cv at element a + o.
 static void stokes_block(const Ctx& c, const HostLevel& L, int64_t a, int rv, int cv, const int* o,
-                         double* out, std::vector<double>& tmp) {
+                         double* out, std::vector<double>& tmp, LapCache* lap = nullptr) {
   int d = c.d, s = c.s, ss = s * s, nsl = 1 + 2 * d;
   std::fill(out, out + ss, 0.0);
   auto exists = [&](const int* off, int64_t& id) {
@@ -1198,8 +1225,25 @@ static void stokes_block(const Ctx& c, const HostLevel& L, int64_t a, int rv, in
         triple_acc(s, alpha, Ga, &L.Mmu[(size_t)E * ss], Gb, out, tmp);
       }
     };
-    if (i == j)
-      for (int k = 0; k < d; ++k) add_term(k, k, 1.0);
+    if (i == j) {
+      // the same for every i: computed once per (a, o) when a cache is given,
+      // in the same order of accumulation, so the block is bit-identical
+      double* cached = nullptr;
+      if (lap) {
+        const int key = LapCache::key(o);
+        cached = &lap->val[(size_t)key * ss];
+        if (lap->owner[key] != a) {
+          std::fill(cached, cached + ss, 0.0);
+          std::swap(cached, out);
+          for (int k = 0; k < d; ++k) add_term(k, k, 1.0);
+          std::swap(cached, out);
+          lap->owner[key] = a;
+        }
+        std::copy(cached, cached + ss, out);
+      } else {
+        for (int k = 0; k < d; ++k) add_term(k, k, 1.0);
+      }
+    }
     if (c.gamma) add_term(j, i, 1.0);
     if (i == j) {
       int sl = pen_slot(d, o);
@@ -1240,18 +1284,20 @@ static void stokes_level(const Ctx& c, HostLevel& L) {
   L.nbr.assign((size_t)ne * P.NO, -1);
   parallel_for(ne, [&](int64_t a0, int64_t a1) {
     std::vector<double> blk(ss), tmp;
+    LapCache lap;
+    lap.init(ss);
     int zero[3] = {0, 0, 0};
     for (int64_t a = a0; a < a1; ++a) {
       for (int rv = 0; rv <= c.d; ++rv)
         for (int cv = 0; cv <= c.d; ++cv) {
-          stokes_block(c, L, a, rv, cv, zero, blk.data(), tmp);
+          stokes_block(c, L, a, rv, cv, zero, blk.data(), tmp, &lap);
           for (int i = 0; i < s; ++i)
             for (int j = 0; j < s; ++j)
               L.D[(size_t)a * nb * nb + (size_t)(rv * s + i) * nb + cv * s + j] = blk[i * s + j];
         }
       for (int t = 0; t < P.T; ++t) {
         const int* o = P.off[P.task_o[t]];
-        stokes_block(c, L, a, P.task_rv[t], P.task_cv[t], o, &L.C[((size_t)a * P.T + t) * ss], tmp);
+        stokes_block(c, L, a, P.task_rv[t], P.task_cv[t], o, &L.C[((size_t)a * P.T + t) * ss], tmp, &lap);
       }
       for (int oi = 0; oi < P.NO; ++oi) L.nbr[(size_t)a * P.NO + oi] = neighbour(c, L.n, a, P.off[oi]);
     }
