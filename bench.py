@@ -137,7 +137,8 @@ def cpu_child(spec):
         el = time.perf_counter() - t0
         if el >= seconds and cycles >= 2:
             break
-    print(json.dumps({"dofs": prob.n_dofs, "cycles": cycles, "seconds": el}))
+    print(json.dumps({"dofs": prob.n_dofs, "cycles": cycles, "seconds": el, "nu": [mg.nu1, mg.nu2],
+                      "shape": [mg.gamma, mg.growth, mg.max_sweeps]}))
 
 
 def cpu_baseline(args, seconds=12.0):

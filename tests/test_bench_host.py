@@ -53,8 +53,7 @@ def test_reference_arm_nonzero_rank_exits_without_work():
 
 def test_cpu_child_runs_the_configured_cycle_shape():
     """The oracle arm's sample process takes the native arm's cycle: V(2,1)
-    and W(2,1) on the same 8 x 8 p=1 sample; a W-cycle costs more per cycle,
-    so fewer of them fit the same time."""
+    and W(2,1) on the same 8 x 8 p=1 sample."""
     recs = {}
     for shape in ("1,1,64", "2,1,64"):
         p = subprocess.run([sys.executable, "bench.py", "--cpu-child", "8,1,2,1,0.5," + shape], cwd=ROOT,
@@ -63,6 +62,5 @@ def test_cpu_child_runs_the_configured_cycle_shape():
         recs[shape] = __import__("json").loads(p.stdout.strip().splitlines()[-1])
     assert recs["1,1,64"]["dofs"] == recs["2,1,64"]["dofs"] == 8 * 8 * 3 * 4
     assert recs["2,1,64"]["cycles"] >= 2
-    v = recs["1,1,64"]["cycles"] / recs["1,1,64"]["seconds"]
-    w = recs["2,1,64"]["cycles"] / recs["2,1,64"]["seconds"]
-    assert w < v
+    assert recs["1,1,64"]["shape"] == [1, 1, 64] and recs["2,1,64"]["shape"] == [2, 1, 64]
+    assert recs["1,1,64"]["nu"] == recs["2,1,64"]["nu"] == [2, 1]
