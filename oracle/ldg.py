@@ -63,6 +63,13 @@ class Mesh:
     def periodic(self, k):
         return self.bc[2 * k] == PERIODIC
 
+    def colour_two(self):
+        """Two colours (i_1 + ... + i_d) mod 2, the checkerboard: a valid
+        colouring of the block GS of Section 3 when the operator couples face
+        neighbours only (standard form, gamma = 0, single phase; every level
+        of the hierarchy has even n_k or is the unsmoothed bottom)."""
+        return self.idx.sum(axis=1) % 2
+
     def colour(self):
         """Colour of every element for the multi-coloured GS of Section 3.
         Single phase: the parity colouring sum_k (i_k mod 2) 2^k.  With

@@ -82,7 +82,7 @@ class SmootherLevel:
     """Smoother data of one level: A_ii, A_ii^{-1}, and the off-block-diagonal
     part of A restricted to the rows of each colour."""
 
-    def __init__(self, lev, storage=None):
+    def __init__(self, lev, storage=None, two_colours=False):
         self.lev = lev
         self.nb = lev.nb
         self.ne = lev.ne
@@ -105,7 +105,7 @@ class SmootherLevel:
             self.inv = round_fp16_scaled(self.inv, axis=2)
             self.diag = round_fp16_scaled(self.diag, axis=2)
             self.Aoff = round_fp16_subblocks(self.Aoff, lev.s)
-        self.colour = lev.mesh.colour()
+        self.colour = lev.mesh.colour_two() if two_colours else lev.mesh.colour()
         self.ncol = int(self.colour.max()) + 1
         self.elems = [np.nonzero(self.colour == c)[0] for c in range(self.ncol)]
         self.rows = [(e[:, None] * self.nb + np.arange(self.nb)[None, :]).ravel() for e in self.elems]
@@ -145,7 +145,8 @@ def bottom_pseudo_inverse(A, theta=SNAP_THETA):
 class Multigrid:
     """The V-cycle hierarchy of a problem (oracle)."""
 
-    def __init__(self, prob, storage=None, levels=None, injections=None, max_levels=None, shape=(1, 1, 64)):
+    def __init__(self, prob, storage=None, levels=None, injections=None, max_levels=None, shape=(1, 1, 64),
+                 two_colours=False):
         self.prob = prob
         # cycle shape (Section 6): coarse visits per level (1 V, 2 W), growth
         # of the smoothing counts per coarser level, cap on the counts
@@ -155,7 +156,9 @@ class Multigrid:
         self.levels = levels
         self.I = injections
         self.storage = storage
-        self.sm = [SmootherLevel(l, storage) for l in levels[:-1]]
+        # two_colours: the checkerboard instead of the 2^d parity colours
+        # (valid for face-coupled operators only: gamma = 0, single phase)
+        self.sm = [SmootherLevel(l, storage, two_colours) for l in levels[:-1]]
         self.bottom, self.kernel_dim_bottom = bottom_pseudo_inverse(levels[-1].A)
         self.nu1, self.nu2 = prob.nu1, prob.nu2
 

@@ -676,3 +676,43 @@ def test_gmres_rho_history_and_spectrum_estimate():
         assert abs(rho ** n - hist[n]) <= 1e-12 * hist[n]
         spread[tau] = np.abs(np.linalg.eigvals(H[:n, :n]) - 1.0).max()
     assert spread[None] <= 0.25 and spread[1.0] >= 2 * spread[None], spread
+
+
+@pytest.mark.parametrize("prob", [
+    P.generic(2, 8, 2, 0, [P.PERIODIC] * 4),
+    P.generic(2, 8, 1, 0, [P.DIRICHLET, P.STRESS, P.DIRICHLET, P.DIRICHLET]),
+    P.generic(3, 4, 1, 0, [P.PERIODIC] * 6),
+    P.unsteady_periodic_3d(n=4, p=1, re=10.0),
+], ids=lambda q: q.name or str(q.bc))
+def test_two_colours_separate_standard_form_couplings(prob):
+    """The standard form (gamma = 0, single phase) couples face neighbours
+    only, so the checkerboard (i_1 + ... + i_d) mod 2 is a valid colouring of
+    the block GS on every smoothing level; for the viscous-stress form the
+    edge couplings join elements of the same checkerboard colour."""
+    levels, _ = hierarchy.build_hierarchy(prob)
+    for lev in levels[:-1]:
+        col = lev.mesh.colour_two()
+        coo = lev.A.tocoo()
+        ei, ej = coo.row // lev.nb, coo.col // lev.nb
+        off = ei != ej
+        assert not np.any(col[ei[off]] == col[ej[off]])
+    vs = hierarchy.build_hierarchy(P.generic(2, 4, 1, 1, [P.PERIODIC] * 4), max_levels=1)[0][0]
+    coo = vs.A.tocoo()
+    ei, ej = coo.row // vs.nb, coo.col // vs.nb
+    col = vs.mesh.colour_two()
+    assert np.any((ei != ej) & (col[ei] == col[ej]))
+
+
+def test_two_colour_gs_contracts_at_least_as_well():
+    """Checkerboard block GS (two launches per sweep in any dimension) against
+    the 2^d parity colours on the standard form: rho of eq. (rho) is no larger
+    (0.060 vs 0.078 for periodic p=2, 16^2; 0.065 vs 0.077 for the periodic
+    cube, p=2, 8^3)."""
+    for prob in (P.periodic_standard_2d(n=16, p=2, nu=(3, 3)),
+                 P.generic(2, 16, 2, 0, [P.DIRICHLET] * 4, nu=(3, 3))):
+        x0 = P.random_vector(prob.n_elements, prob.nb, seed=1).ravel()
+        mg = multigrid.Multigrid(prob)
+        rho_par, _ = mg.gmres_rho(x0)
+        rho_two, _ = multigrid.Multigrid(prob, levels=mg.levels, injections=mg.I, two_colours=True).gmres_rho(x0)
+        assert mg.sm[0].ncol == 4
+        assert rho_two <= 0.9 * rho_par, (rho_two, rho_par)
