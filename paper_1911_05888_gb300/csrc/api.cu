@@ -1151,7 +1151,7 @@ int gmres_rho(Ctx& c, const double* x0, double reduction, int maxit, double* his
   const double beta = host_norm(c, c.kV, st);
   if (hist) hist[0] = 1.0;
   if (!(beta > 0) || !std::isfinite(beta)) {
-    rho = beta > 0 ? beta : 0.0;
+    rho = std::isfinite(beta) ? 0.0 : beta;   // x0 in the kernel: rho 0; NaN / Inf reported
     return 0;
   }
   ck(launch_scale(n0, 1.0 / beta, c.kV, c.kV, st), "scale");
