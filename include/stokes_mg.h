@@ -268,9 +268,11 @@ int stk_bottom_solve(stk_ctx* ctx, const double* b_dev, double* x_dev, void* str
  * the relative preconditioned residual per iteration.  hess (host,
  * (maxit+1) x maxit row-major, may be NULL): the Arnoldi matrix before the
  * Givens rotations; the eigenvalues of its leading n x n block estimate the
- * spectrum of V A (Section 4's spectral estimate).  Errors:
- * STK_ERR_NOT_SETUP, STK_ERR_INVALID_ARG (reduction outside (0,1), maxit
- * outside 1..100, NULL x0_dev or rho_out), STK_ERR_TIMEOUT, STK_ERR_DIVERGED.
+ * spectrum of V A (Section 4's spectral estimate).  An x0 with V A x0 = 0
+ * gives rho = 0 after 0 iterations.  Errors: STK_ERR_NOT_SETUP,
+ * STK_ERR_INVALID_ARG (reduction outside (0,1), maxit outside 1..100, NULL
+ * x0_dev or rho_out), STK_ERR_TIMEOUT, STK_ERR_DIVERGED (a non-finite
+ * residual).
  */
 int stk_gmres_rho(stk_ctx* ctx, const double* x0_dev, double reduction, int maxit, double* rho_out,
                   int* iters_out, double* hist, double* hess, void* stream);
