@@ -381,7 +381,7 @@ int stk_solve_batch(stk_ctx* const* ctx, int n, double* const* x, const double* 
  * hidden layer of `hidden` units, out = nb) whose output times ||r_i|| is a
  * correction delta_i.  x + delta replaces the block Gauss-Seidel iterate only
  * if ||r - A delta|| < ||r|| (decided on the device each cycle), so the plain
- * smoother stays the fallback and the judge.
+ * smoother stays both the fallback and the yardstick of acceptance.
  *  stk_learn_setup     allocate and initialise the weights (deterministic in seed);
  *  stk_learn_generate  residual states from the plain V-cycle: for nseeds smooth
  *                      random solutions x* (seeded), b = A x*, `cycles` V-cycles

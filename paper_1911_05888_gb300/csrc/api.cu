@@ -1401,7 +1401,7 @@ int stk_setup(stk_ctx* c, void* stream) {
     free_device(*c);
     build_pattern(c->d, c->p, c->gamma, !c->chi.empty(), c->pat);
     if (c->pat.T >= kMaxTasks || c->pat.NG >= kMaxGather || c->pat.NO >= kMaxOffsets)
-      return fail(c, STK_ERR_INVALID_ARG, "coupling pattern too large for this build");
+      return fail(c, STK_ERR_INVALID_ARG, "coupling pattern exceeds the library's compiled limits");
     int rc = setup_host(*c);
     if (rc != STK_OK) return rc;
     int L = nlevels(*c);
