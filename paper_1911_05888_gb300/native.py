@@ -164,12 +164,24 @@ class Context:
             msg = self.lib.stk_last_error(self.h)
             raise StkError("%s: %s (%s)" % (name, msg.decode() if msg else "", ERRORS.get(rc, rc)))
 
+    @staticmethod
+    def _expect(name, a, rows, cols=1):
+        """Host arrays cross the ABI as bare pointers: refuse one whose size
+        is not rows x cols before the library reads it."""
+        size = np.asarray(a).size
+        if size != rows * cols:
+            raise ValueError("%s: %d values, expected %d x %d" % (name, size, rows, cols))
+
     def set_mesh(self, d, n, lo, hi, bc):
+        if not (len(n) == len(lo) == len(hi) == d and len(bc) == 2 * d):
+            raise ValueError("set_mesh: n, lo, hi need d entries and bc 2d")
         n_ = (ctypes.c_int * d)(*n)
         lo_ = (ctypes.c_double * d)(*lo)
         hi_ = (ctypes.c_double * d)(*hi)
         bc_ = (ctypes.c_int * (2 * d))(*bc)
         self._check(self.lib.stk_set_mesh(self.h, d, n_, lo_, hi_, bc_), "stk_set_mesh")
+        self.d = d
+        self.ne = int(np.prod(n))
 
     def set_discretisation(self, p, gamma):
         self._check(self.lib.stk_set_discretisation(self.h, p, gamma), "stk_set_discretisation")
@@ -191,10 +203,17 @@ class Context:
         return xyz, nrm
 
     def set_viscosity(self, mu_vol, mu_if, mu_bf):
+        self._expect("mu_vol", mu_vol, self.num_points(PTS_VOLUME))
+        self._expect("mu_iface", mu_if, self.num_points(PTS_INTERIOR_FACE))
+        self._expect("mu_bface", mu_bf, self.num_points(PTS_BOUNDARY_FACE))
         a, b, c = _dbl(mu_vol), _dbl(mu_if), _dbl(mu_bf)
         self._check(self.lib.stk_set_viscosity(self.h, a[0], b[0], c[0]), "stk_set_viscosity")
 
     def set_density(self, rho_vol, rho_if, delta):
+        if rho_vol is not None:
+            self._expect("rho_vol", rho_vol, self.num_points(PTS_VOLUME))
+        if rho_if is not None:
+            self._expect("rho_iface", rho_if, self.num_points(PTS_INTERIOR_FACE))
         a = _dbl(rho_vol) if rho_vol is not None else (None, None)
         b = _dbl(rho_if) if rho_if is not None else (None, None)
         self._check(self.lib.stk_set_density(self.h, a[0], b[0], float(delta)), "stk_set_density")
@@ -227,7 +246,18 @@ class Context:
                     "stk_get_block")
         return out
 
+    def _check_rhs_data(self, f_vol, bdata, ne, idata=None):
+        d = self.d
+        if ne != self.ne:
+            raise ValueError("assemble_rhs: ne = %d, the mesh has %d elements" % (ne, self.ne))
+        self._expect("f_vol", f_vol, self.num_points(PTS_VOLUME), d + 1)
+        if bdata is not None:
+            self._expect("bdata", bdata, self.num_points(PTS_BOUNDARY_FACE), d)
+        if idata is not None:
+            self._expect("idata", idata, self.num_points(PTS_INTERIOR_FACE), 2 * d)
+
     def assemble_rhs(self, f_vol, bdata, ne, nb):
+        self._check_rhs_data(f_vol, bdata, ne)
         b = np.zeros((ne, nb))
         f = _dbl(f_vol)
         bd = _dbl(bdata) if bdata is not None else (None, None)
@@ -382,6 +412,9 @@ class Context:
     def set_phases(self, chi, mu_phase, scale=True):
         chi = np.ascontiguousarray(chi, dtype=np.int32)
         mu = np.ascontiguousarray(mu_phase, dtype=np.float64)
+        self._expect("chi", chi, self.ne)
+        if chi.size and (chi.min() < 1 or chi.max() > len(mu)):
+            raise ValueError("set_phases: phase indices must lie in 1..%d" % len(mu))
         self._check(self.lib.stk_set_phases(self.h, len(mu), chi.ctypes.data_as(_c_int_p),
                                             mu.ctypes.data_as(_c_dbl_p), 1 if scale else 0), "stk_set_phases")
 
@@ -394,6 +427,7 @@ class Context:
         return cm, cp, nr
 
     def assemble_rhs2(self, f_vol, bdata, idata, ne, nb):
+        self._check_rhs_data(f_vol, bdata, ne, idata)
         b = np.zeros((ne, nb))
         f = _dbl(f_vol)
         bd = _dbl(bdata) if bdata is not None else (None, None)
