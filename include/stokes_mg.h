@@ -166,6 +166,25 @@ int stk_setup(stk_ctx* ctx, void* stream);
  */
 int stk_get_sizes(stk_ctx* ctx, int* nlevels, int64_t* n_elements, int* nb, int* n_snapped);
 
+/*
+ * Introspection of a context (not a step of the method): *value receives
+ *   STK_INFO_BOTTOM_SOLVER   eigensolver of the last setup's bottom pseudo-
+ *                            inverse (Section 3 footnote): 0 cyclic Jacobi
+ *                            (host, <= 300 unknowns), 1 equilibrated
+ *                            Householder + implicit QR (host, <= 1200),
+ *                            2 equilibrated cuSOLVER syevd (device, above);
+ *   STK_INFO_BOTTOM_UNKNOWNS unknowns of the bottom level;
+ *   STK_INFO_COLOURS         colours of the level-0 smoother;
+ *   STK_INFO_DEVICE_BYTES    device bytes the library holds for the context.
+ * The first three need stk_setup (else STK_ERR_NOT_SETUP); an unknown key is
+ * STK_ERR_INVALID_ARG.
+ */
+#define STK_INFO_BOTTOM_SOLVER 0
+#define STK_INFO_BOTTOM_UNKNOWNS 1
+#define STK_INFO_COLOURS 2
+#define STK_INFO_DEVICE_BYTES 3
+int stk_get_info(stk_ctx* ctx, int what, int64_t* value);
+
 /* Dense nb x nb block A_ij (row element i, column element j, natural
  * element indices) of the level-`level` operator, row-major, into a host
  * array; zero when the elements do not couple. */
@@ -302,8 +321,10 @@ int stk_solve(stk_ctx* ctx, double* x_dev, const double* b_dev, double rtol, int
  *  - at most 33,554,432 unknowns on level 0 (16384 chunks of 2048);
  *    larger problems return STK_ERR_INVALID_ARG with a message;
  *  - the first call on a device looks up the array's device address (with
- *    that device made current) and caches it; make that first call before
- *    any stream capture;
+ *    that device made current) and caches it for the life of the process;
+ *    make that first call before any stream capture; a cudaDeviceReset (or
+ *    unloading the library) invalidates the cached address, so do not call
+ *    this entry point again after one;
  *  - all calls share the array; each call writes every slot it reads, but
  *    calls that overlap on the GPU (e.g. on two streams) race on it;
  *  - on failure only the context's host-side error message is updated.

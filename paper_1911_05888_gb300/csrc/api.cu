@@ -19,91 +19,45 @@
 #include "stk_internal.h"
 #include "../../include/stokes_mg.h"
 
-namespace stk {
-cudaError_t launch_element(const Pattern& pat, int storage, int mode, int pos0, int npos,
-                           const int* perm, const int* nbr, const void* cpl, const void* mat,
-                           const void* b, void* x, void* r, cudaStream_t st);
-cudaError_t launch_restrict(int vec64, int d, int s, int nb, const int* nc, const int* nf, int64_t nec,
-                            const void* P, const void* r, void* rc, cudaStream_t st);
-cudaError_t launch_prolong(int vec64, int d, int s, int nb, const int* nf, const int* nc, int64_t nec,
-                           const void* PT, const void* xc, void* x, cudaStream_t st);
-cudaError_t launch_bottom(int vec64, int64_t n, const double* pinv, const void* b, void* x,
-                          cudaStream_t st);
-cudaError_t launch_axpy(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st);
-cudaError_t launch_convert(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st);
-cudaError_t launch_to_bf16(int64_t n, void* y, const double* x, cudaStream_t st);
-cudaError_t launch_sumsq(int64_t n, const double* x, double* part, double* out, cudaStream_t st);
-cudaError_t launch_multidot(int64_t n, int k, const double* V, int64_t ldv, const double* w, double* part,
-                            double* out, cudaStream_t st);
-cudaError_t launch_multiaxpy(int64_t n, int k, double alpha, const double* coef, const double* V, int64_t ldv,
-                             double* w, cudaStream_t st);
-cudaError_t launch_scale(int64_t n, double s, const double* x, double* y, cudaStream_t st);
-cudaError_t launch_element_pipe(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
-                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
-                                int* err, int ctas, int stages, cudaStream_t st);
-void prepare_pipe_kernels();
-void prepare_mrhs_kernels();
-cudaError_t launch_element_mrhs(const Pattern& pat, int storage, int nr, int mode, int pos0, int npos,
-                                const int* perm, const int* nbr, const void* cpl, const void* mat, const void* b,
-                                void* x, void* r, cudaStream_t st, int tensor = 0, int tensor_small = 0);
-cudaError_t launch_restrict_mr(int vec64, int d, int s, int nb, int nr, const int* nc, const int* nf, int64_t nec,
-                               const void* P, const void* r, void* rc, cudaStream_t st);
-cudaError_t launch_prolong_mr(int vec64, int d, int s, int nb, int nr, const int* nf, const int* nc, int64_t nec,
-                              const void* PT, const void* xc, void* x, cudaStream_t st);
-cudaError_t launch_bottom_mr(int vec64, int64_t n, int nr, const double* pinv, const void* b, void* x, cudaStream_t st);
-cudaError_t launch_interleave(int kind, int64_t m, int nr, int nq, int to_interleaved, void* out, const void* in,
-                              cudaStream_t st);
-cudaError_t launch_sumsq_mr(int64_t m, int nr, const double* x, double* part, double* out, cudaStream_t st);
-cudaError_t launch_multidot_mr(int64_t n, int nr, int k, const double* V, int64_t ldv, const double* w,
-                               double* part, double* out, cudaStream_t st);
-cudaError_t launch_multiaxpy_mr(int64_t n, int nr, int k, double alpha, const double* coef, const double* V,
-                                int64_t ldv, double* w, cudaStream_t st);
-cudaError_t launch_scale_mr(int64_t n, int nr, const double* s, const double* x, double* y, cudaStream_t st);
-cudaError_t launch_features(int ne, int nb, int nface, int NO, int ldf, const int* nbr_nat, const float* r, float* F,
-                            float* nrm, cudaStream_t st);
-cudaError_t launch_sgemm(int M, int N, int K, int ta, int tb, const float* A, int lda, const float* B, int ldb,
-                         float* C, int ldc, const float* bias, int act, float alpha, float beta, cudaStream_t st);
-cudaError_t launch_colsum(int M, int N, const float* A, int lda, float* out, float alpha, cudaStream_t st);
-cudaError_t launch_mse_grad(int64_t n, float scale, const float* Y, const float* T, float* dY, float* part,
-                            cudaStream_t st);
-cudaError_t launch_tanh_back(int64_t n, const float* H, float* dH, cudaStream_t st);
-cudaError_t launch_adam(int64_t n, float lr, float b1, float b2, float c1, float c2, float eps, float* w,
-                        const float* g, float* m, float* v, cudaStream_t st);
-cudaError_t launch_apply_correction(int ne, int nb, int ldy, const float* x, const float* nrm, const float* Y, float* xt,
-                                    cudaStream_t st);
-cudaError_t launch_accept(int64_t n, const double* sums, const float* xt, float* x, int* counters, cudaStream_t st);
-cudaError_t launch_sumsq_f(int64_t n, const float* x, double* part, double* out, cudaStream_t st);
-cudaError_t launch_smooth_field(int ne, int nb, int s, int d, const int* n_dev, uint64_t seed, float* x,
-                                cudaStream_t st);
-cudaError_t launch_target(int ne, int nb, int ldt, const float* xs, const float* x, const float* nrm, float* T,
-                          cudaStream_t st);
-cudaError_t launch_scale_f(int64_t n, float a, const float* x, float* y, cudaStream_t st);
-cudaError_t launch_scale_by_norm(int64_t n, const double* sums, float* g, cudaStream_t st);
-cudaError_t launch_element_wide(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
-                                const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
-                                const void* b, void* x, void* r, cudaStream_t st);
-cudaError_t launch_element_df(const Pattern& pat, int pos0, int npos, const int* perm, const int* nbr,
-                              const void* cpl_hi, const void* cpl_lo, const void* dia_hi, const void* dia_lo,
-                              const float* z, double* w, int ctas, cudaStream_t st);
-cudaError_t launch_fp32_remainder(int64_t n, const double* a, void* lo, cudaStream_t st);
-void prepare_df_kernels();
-cudaError_t launch_to_fp16_tasks(int64_t npos, int S, int T, int TRP, void* dst, float* tsc, const double* src,
-                                 cudaStream_t st);
-cudaError_t launch_to_fp16_rows(int64_t npos, int nb, int NBP, void* dst, float* rsc, const double* src,
-                                cudaStream_t st);
-cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
-                                const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
-                                const void* b, void* x, void* r, int ctas, cudaStream_t st);
-void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages);
-}  // namespace stk
 
 using namespace stk;
 
-struct stk_ctx : public Ctx {};
+namespace stk {
+
+// One element-kernel launch (colour step or residual) on level l: launches of
+// few elements (npos <= wide_max) take the one-CTA-per-element latency
+// variant, the others the configured variant; the pipelined variant falls
+// back to direct loads when its records do not fit in shared memory.
+cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, const void* mat, const void* b,
+                        void* x, void* r, cudaStream_t st) {
+  DevLevel& D = c.dev[l];
+  // FP16 records carry scales and run on the warp and wide kernels only.
+  const bool scaled = prec == STK_FP16;
+  const float* tsc = scaled ? D.csc : nullptr;
+  const float* rsc = scaled ? (mode == MODE_GS ? D.isc : D.dsc) : nullptr;
+  if (npos <= c.wide_max) {
+    cudaError_t e = launch_element_wide(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
+                                        x, r, st);
+    if (e != cudaErrorInvalidValue || scaled) return e;
+  }
+  const int variant = c.variant_of[prec];
+  if (variant == 2 || scaled) {
+    cudaError_t e = launch_element_warp(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
+                                        x, r, c.warp_ctas[prec], st);
+    if (e != cudaErrorInvalidValue || scaled) return e;
+  }
+  if (variant == 1) {
+    cudaError_t e = launch_element_pipe(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
+                                        c.dev_err, c.pipe_ctas[prec], c.pipe_stages[prec], st);
+    if (e != cudaErrorInvalidValue) return e;
+  }
+  return launch_element(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r, st);
+}
+
+}  // namespace stk
 
 namespace {
 
-constexpr int MODE_GS = 0, MODE_RESID = 1;
 
 struct CudaFail {
   cudaError_t e;
@@ -142,12 +96,14 @@ void* dalloc(Ctx& c, size_t bytes) {
   cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
   if (e != cudaSuccess) throw CudaFail{e, "cudaMalloc"};
   c.allocations.push_back(p);
+  c.device_bytes += (int64_t)(bytes ? bytes : 16);
   return p;
 }
 
 void free_device(Ctx& c) {
   for (void* p : c.allocations) cudaFree(p);
   c.allocations.clear();
+  c.device_bytes = 0;
   if (c.norm_host) cudaFreeHost(c.norm_host);
   c.norm_host = nullptr;
   if (c.khost) cudaFreeHost(c.khost);
@@ -184,36 +140,6 @@ int colour_of(const Ctx& c, const int* n, int64_t e) {
   int col = 0;
   for (int k = 0; k < c.d; ++k) col |= (idx[k] & 1) << k;
   return col;
-}
-
-// One element-kernel launch (colour step or residual) on level l: launches of
-// few elements (npos <= wide_max) take the one-CTA-per-element latency
-// variant, the others the configured variant; the pipelined variant falls
-// back to direct loads when its records do not fit in shared memory.
-cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, const void* mat, const void* b,
-                        void* x, void* r, cudaStream_t st) {
-  DevLevel& D = c.dev[l];
-  // FP16 records carry scales and run on the warp and wide kernels only.
-  const bool scaled = prec == STK_FP16;
-  const float* tsc = scaled ? D.csc : nullptr;
-  const float* rsc = scaled ? (mode == MODE_GS ? D.isc : D.dsc) : nullptr;
-  if (npos <= c.wide_max) {
-    cudaError_t e = launch_element_wide(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
-                                        x, r, st);
-    if (e != cudaErrorInvalidValue || scaled) return e;
-  }
-  const int variant = c.variant_of[prec];
-  if (variant == 2 || scaled) {
-    cudaError_t e = launch_element_warp(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
-                                        x, r, c.warp_ctas[prec], st);
-    if (e != cudaErrorInvalidValue || scaled) return e;
-  }
-  if (variant == 1) {
-    cudaError_t e = launch_element_pipe(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
-                                        c.dev_err, c.pipe_ctas[prec], c.pipe_stages[prec], st);
-    if (e != cudaErrorInvalidValue) return e;
-  }
-  return launch_element(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r, st);
 }
 
 // Pack the Stokes blocks of smoothing level l into the colour-major device
@@ -362,9 +288,14 @@ void alloc_vectors(Ctx& c) {
 }
 
 // ---- large bottom levels: eigendecomposition by cuSOLVER (loaded at run time)
-// pinv(i, j) = sum_k V(i, k) w_k V(j, k), V column-major (n x n), w = 1/lambda or 0.
+// The same steps as the host solver for 301-1200 unknowns (stk_host_pseudo_inverse):
+// equilibrate A^ = S A S (S_i = row 1-norm^(-1/2)), eigendecompose A^ (here on
+// the device), snap |lambda| <= theta max|lambda|, G = S A^+ S, then project G
+// off the kernel of A (the vectors S v_k of the snapped eigenvalues).
+// pinv(i, j) = S_i S_j sum_k V(i, k) w_k V(j, k), V column-major (n x n),
+// w = 1/lambda or 0.
 __global__ void pinv_gemm_kernel(int n, const double* __restrict__ V, const double* __restrict__ w,
-                                 double* __restrict__ P) {
+                                 const double* __restrict__ S, double* __restrict__ P) {
   __shared__ double As[16][17], Bs[16][17];
   const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
   double acc = 0.0;
@@ -378,7 +309,7 @@ __global__ void pinv_gemm_kernel(int n, const double* __restrict__ V, const doub
     for (int k = 0; k < 16; ++k) acc += As[threadIdx.y][k] * Bs[k][threadIdx.x];
     __syncthreads();
   }
-  if (i < n && j < n) P[(size_t)i * n + j] = acc;
+  if (i < n && j < n) P[(size_t)i * n + j] = S[i] * S[j] * acc;
 }
 
 typedef int (*syevd_buf_fn)(void*, int, int, int, const double*, int, const double*, int*);
@@ -386,60 +317,88 @@ typedef int (*syevd_fn)(void*, int, int, int, double*, int, double*, double*, in
 typedef int (*create_fn)(void**);
 typedef int (*destroy_fn)(void*);
 
-// Returns false when cuSOLVER cannot be loaded (the caller then uses Jacobi).
+// Owns what the cuSOLVER path acquires; releases all of it on every return.
+struct CusolverScope {
+  void* so = nullptr;
+  void* handle = nullptr;
+  destroy_fn destroy = nullptr;
+  std::vector<void*> dev;
+  ~CusolverScope() {
+    for (void* p : dev) cudaFree(p);
+    if (handle && destroy) destroy(handle);
+    if (so) dlclose(so);
+  }
+  bool alloc(void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+    dev.push_back(*p);
+    return true;
+  }
+};
+
+// Returns false when cuSOLVER cannot be loaded or fails (the caller then uses
+// the host solver).
 bool pseudo_inverse_cusolver(Ctx& c, int n, const std::vector<double>& A, double* d_pinv, int& snapped,
                              double theta) {
-  void* so = nullptr;
+  CusolverScope g;
   for (const char* name : {"libcusolver.so", "libcusolver.so.12", "libcusolver.so.11"})
-    if ((so = dlopen(name, RTLD_NOW | RTLD_LOCAL))) break;
-  if (!so) return false;
-  auto create = (create_fn)dlsym(so, "cusolverDnCreate");
-  auto destroy = (destroy_fn)dlsym(so, "cusolverDnDestroy");
-  auto bufsz = (syevd_buf_fn)dlsym(so, "cusolverDnDsyevd_bufferSize");
-  auto syevd = (syevd_fn)dlsym(so, "cusolverDnDsyevd");
-  if (!create || !destroy || !bufsz || !syevd) return false;
-  void* h = nullptr;
-  if (create(&h) != 0) return false;
+    if ((g.so = dlopen(name, RTLD_NOW | RTLD_LOCAL))) break;
+  if (!g.so) return false;
+  auto create = (create_fn)dlsym(g.so, "cusolverDnCreate");
+  g.destroy = (destroy_fn)dlsym(g.so, "cusolverDnDestroy");
+  auto bufsz = (syevd_buf_fn)dlsym(g.so, "cusolverDnDsyevd_bufferSize");
+  auto syevd = (syevd_fn)dlsym(g.so, "cusolverDnDsyevd");
+  if (!create || !g.destroy || !bufsz || !syevd) return false;
+  if (create(&g.handle) != 0) {
+    g.handle = nullptr;
+    return false;
+  }
   const int JOBZ_VECTOR = 1, FILL_LOWER = 0;   // CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER
-  double *dA = nullptr, *dW = nullptr, *dWork = nullptr, *dInv = nullptr;
+  std::vector<double> S, Ah;
+  equilibrate_sym(n, A, S, Ah);
+  double *dA = nullptr, *dW = nullptr, *dWork = nullptr, *dInv = nullptr, *dS = nullptr;
   int* dInfo = nullptr;
-  bool ok = false;
   int lwork = 0, info = 1;
   std::vector<double> lam(n), inv(n, 0.0);
-  if (cudaMalloc(&dA, (size_t)n * n * 8) != cudaSuccess || cudaMalloc(&dW, (size_t)n * 8) != cudaSuccess ||
-      cudaMalloc(&dInv, (size_t)n * 8) != cudaSuccess || cudaMalloc(&dInfo, sizeof(int)) != cudaSuccess)
-    goto done;
-  // A is symmetric: row-major and column-major storage coincide.
-  if (cudaMemcpy(dA, A.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice) != cudaSuccess) goto done;
-  if (bufsz(h, JOBZ_VECTOR, FILL_LOWER, n, dA, n, dW, &lwork) != 0) goto done;
-  if (cudaMalloc(&dWork, (size_t)std::max(lwork, 1) * 8) != cudaSuccess) goto done;
-  if (syevd(h, JOBZ_VECTOR, FILL_LOWER, n, dA, n, dW, dWork, lwork, dInfo) != 0) goto done;
-  if (cudaMemcpy(&info, dInfo, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || info != 0) goto done;
-  if (cudaMemcpy(lam.data(), dW, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) goto done;
-  {
-    double lmax = 0.0;
-    for (double l : lam) lmax = std::max(lmax, std::fabs(l));
-    snapped = 0;
-    for (int k = 0; k < n; ++k) {
-      if (std::fabs(lam[k]) <= theta * lmax) ++snapped;
-      else inv[k] = 1.0 / lam[k];
-    }
+  if (!g.alloc((void**)&dA, (size_t)n * n * 8) || !g.alloc((void**)&dW, (size_t)n * 8) ||
+      !g.alloc((void**)&dInv, (size_t)n * 8) || !g.alloc((void**)&dS, (size_t)n * 8) ||
+      !g.alloc((void**)&dInfo, sizeof(int)))
+    return false;
+  // A^ is symmetric: row-major and column-major storage coincide.
+  if (cudaMemcpy(dA, Ah.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice) != cudaSuccess) return false;
+  if (cudaMemcpy(dS, S.data(), (size_t)n * 8, cudaMemcpyHostToDevice) != cudaSuccess) return false;
+  if (bufsz(g.handle, JOBZ_VECTOR, FILL_LOWER, n, dA, n, dW, &lwork) != 0) return false;
+  if (!g.alloc((void**)&dWork, (size_t)std::max(lwork, 1) * 8)) return false;
+  if (syevd(g.handle, JOBZ_VECTOR, FILL_LOWER, n, dA, n, dW, dWork, lwork, dInfo) != 0) return false;
+  if (cudaMemcpy(&info, dInfo, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || info != 0) return false;
+  if (cudaMemcpy(lam.data(), dW, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  std::vector<int> kern;
+  double lmax = 0.0;
+  for (double l : lam) lmax = std::max(lmax, std::fabs(l));
+  for (int k = 0; k < n; ++k) {
+    if (std::fabs(lam[k]) <= theta * lmax) kern.push_back(k);
+    else inv[k] = 1.0 / lam[k];
   }
-  if (cudaMemcpy(dInv, inv.data(), (size_t)n * 8, cudaMemcpyHostToDevice) != cudaSuccess) goto done;
-  {
-    dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
-    pinv_gemm_kernel<<<grd, blk>>>(n, dA, dInv, d_pinv);
-    c.launches++;
-    ok = cudaDeviceSynchronize() == cudaSuccess;
+  if (cudaMemcpy(dInv, inv.data(), (size_t)n * 8, cudaMemcpyHostToDevice) != cudaSuccess) return false;
+  dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
+  pinv_gemm_kernel<<<grd, blk>>>(n, dA, dInv, dS, d_pinv);
+  c.launches++;
+  if (cudaDeviceSynchronize() != cudaSuccess) return false;
+  const int nk = (int)kern.size();
+  if (nk > 0) {
+    // kernel vectors of A: S v_k (column kern[a] of the column-major V)
+    std::vector<double> K((size_t)nk * n), G((size_t)n * n);
+    for (int a = 0; a < nk; ++a)
+      if (cudaMemcpy(&K[(size_t)a * n], dA + (size_t)kern[a] * n, (size_t)n * 8, cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+        return false;
+    for (int a = 0; a < nk; ++a)
+      for (int j = 0; j < n; ++j) K[(size_t)a * n + j] *= S[j];
+    if (cudaMemcpy(G.data(), d_pinv, (size_t)n * n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    project_off_kernel(n, G, K, nk);
+    if (cudaMemcpy(d_pinv, G.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice) != cudaSuccess) return false;
   }
-done:
-  if (dA) cudaFree(dA);
-  if (dW) cudaFree(dW);
-  if (dWork) cudaFree(dWork);
-  if (dInv) cudaFree(dInv);
-  if (dInfo) cudaFree(dInfo);
-  destroy(h);
-  return ok;
+  snapped = nk;
+  return true;
 }
 
 // Bottom level: dense operator, eigen pseudo-inverse, to device.
@@ -469,8 +428,12 @@ void setup_bottom(Ctx& c) {
   // small bottom levels; the equilibrated Householder-QR solver up to 1200
   // (a 864-unknown 3D bottom: 0.8 s instead of 30-90 s); cuSOLVER's symmetric
   // eigensolver above.
-  if (n > 1200 && pseudo_inverse_cusolver(c, (int)n, A, c.bottom_pinv, c.n_snapped, 1e-10)) return;
+  if (n > 1200 && pseudo_inverse_cusolver(c, (int)n, A, c.bottom_pinv, c.n_snapped, 1e-10)) {
+    c.bottom_solver = 2;
+    return;
+  }
   std::vector<double> pinv;
+  c.bottom_solver = n <= 300 ? 0 : 1;
   const int rc = n <= 300 ? pseudo_inverse_jacobi((int)n, A, pinv, c.n_snapped, 1e-10)
                           : pseudo_inverse_sym((int)n, A, pinv, c.n_snapped, 1e-10);
   if (rc != STK_OK) throw std::runtime_error("bottom solver");
@@ -1460,6 +1423,31 @@ int stk_get_sizes(stk_ctx* c, int* nl, int64_t* ne, int* nb, int* snapped) {
     if (nb) *nb = c->nb;
     if (snapped) *snapped = c->n_snapped;
     return STK_OK;
+  });
+}
+
+int stk_get_info(stk_ctx* c, int what, int64_t* value) {
+  return guard(c, [&]() -> int {
+    if (!value) return fail(c, STK_ERR_INVALID_ARG, "null output");
+    switch (what) {
+      case STK_INFO_BOTTOM_SOLVER:
+        if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+        *value = c->bottom_solver;
+        return STK_OK;
+      case STK_INFO_BOTTOM_UNKNOWNS:
+        if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+        *value = c->nbot;
+        return STK_OK;
+      case STK_INFO_COLOURS:
+        if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+        *value = nlevels(*c) > 1 ? c->dev[0].ncolour : 0;
+        return STK_OK;
+      case STK_INFO_DEVICE_BYTES:
+        *value = c->device_bytes;
+        return STK_OK;
+      default:
+        return fail(c, STK_ERR_INVALID_ARG, "unknown info key");
+    }
   });
 }
 

@@ -131,7 +131,7 @@ constexpr bool kScaledStorage = std::is_same<TS, __half>::value;
 
 __host__ __device__ inline int task_scale_stride(const Pattern& pat) { return (pat.T + 3) / 4 * 4; }
 
-enum { MODE_GS = 0, MODE_RESID = 1 };
+// MODE_GS, MODE_RESID: stk_internal.h
 
 template <typename TS, typename TX, int S>
 __global__ void __launch_bounds__(kNT) element_kernel(const __grid_constant__ Pattern pat, int mode,

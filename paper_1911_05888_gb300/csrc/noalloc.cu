@@ -15,14 +15,6 @@
 #include "stk_internal.h"
 #include "../../include/stokes_mg.h"
 
-struct stk_ctx : public stk::Ctx {};
-
-namespace stk {
-cudaError_t launch_element(const Pattern& pat, int storage, int mode, int pos0, int npos,
-                           const int* perm, const int* nbr, const void* cpl, const void* mat,
-                           const void* b, void* x, void* r, cudaStream_t st);
-}
-
 namespace {
 
 constexpr int kChunk = 2048;                      // entries summed by one partial (256 x 8)
@@ -68,7 +60,9 @@ __global__ void partials_total_kernel(int nparts, const double* __restrict__ par
   if (threadIdx.x == 0) out[0] = sh[0];
 }
 
-// Device address of g_static_partials on `device` (which must be current).
+// Device address of g_static_partials on `device` (which must be current),
+// fetched on the first call on that device and kept for the life of the
+// process: a cudaDeviceReset (or unloading the library) invalidates it.
 cudaError_t partials_address(int device, double** out) {
   std::lock_guard<std::mutex> guard(g_lock);
   if (!g_partials_addr[device]) {
@@ -119,9 +113,10 @@ extern "C" int stk_residual_norm_static(stk_ctx* c, const double* x, const doubl
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = partials_address(c->device, &part);
   if (e == cudaSuccess) {
+    // The same launch as stk_residual: the FP64 residual on the kernel
+    // variant the context's tuning picks for level 0 (none of them allocates).
     const stk::DevLevel& D = c->dev[0];
-    e = stk::launch_element(c->pat, STK_FP64, 1, 0, D.ne, D.perm, D.nbr, D.cpl[0], D.dia[0], b, (void*)x, r,
-                            st);
+    e = stk::run_element(*c, 0, STK_FP64, stk::MODE_RESID, 0, D.ne, D.dia[0], b, (void*)x, r, st);
   }
   if (e == cudaSuccess) {
     chunk_sumsq_kernel<<<(unsigned)nparts, 256, 0, st>>>(n, r, part);

@@ -449,48 +449,23 @@ static bool symmetric_eigen(int n, std::vector<double>& A, std::vector<double>& 
 // P = I - K K^T, the least-squares inverse is P G P.  The equilibration keeps
 // the blocks' graded scales (velocity against pressure rows, phases of
 // different viscosity) out of the eigensolver's rounding error.
-int pseudo_inverse_sym(int n, std::vector<double>& A, std::vector<double>& pinv, int& snapped, double theta) {
-  if (n < 1) return STK_ERR_INVALID_ARG;
-  std::vector<double> S(n, 1.0);
+void equilibrate_sym(int n, const std::vector<double>& A, std::vector<double>& S, std::vector<double>& Ah) {
+  S.assign(n, 1.0);
   for (int i = 0; i < n; ++i) {
     double r = 0.0;
     for (int j = 0; j < n; ++j) r += std::fabs(A[(size_t)i * n + j]);
     if (r > 0 && std::isfinite(r)) S[i] = 1.0 / std::sqrt(r);
   }
-  std::vector<double> Ah((size_t)n * n), lam, Qt;
+  Ah.resize((size_t)n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) Ah[(size_t)i * n + j] = S[i] * A[(size_t)i * n + j] * S[j];
-  if (!symmetric_eigen(n, Ah, lam, Qt)) return pseudo_inverse_jacobi(n, A, pinv, snapped, theta);
-  double lmax = 0.0;
-  for (int i = 0; i < n; ++i) lmax = std::max(lmax, std::fabs(lam[i]));
-  std::vector<double> inv(n, 0.0);
-  std::vector<int> kern;
-  for (int i = 0; i < n; ++i) {
-    if (std::fabs(lam[i]) <= theta * lmax) kern.push_back(i);
-    else inv[i] = 1.0 / lam[i];
-  }
-  snapped = (int)kern.size();
-  // G = S (sum_k q_k q_k^T / lam_k) S
-  pinv.assign((size_t)n * n, 0.0);
-  parallel_for(n, [&](int64_t i0, int64_t i1) {
-    for (int64_t i = i0; i < i1; ++i) {
-      double* row = &pinv[(size_t)i * n];
-      for (int k = 0; k < n; ++k) {
-        const double f = Qt[(size_t)k * n + i] * inv[k];
-        if (f == 0.0) continue;
-        const double* q = &Qt[(size_t)k * n];
-        for (int j = 0; j < n; ++j) row[j] += f * q[j];
-      }
-      for (int j = 0; j < n; ++j) row[j] *= S[i] * S[j];
-    }
-  });
-  const int nk = snapped;
-  if (nk == 0) return STK_OK;
-  // K: S q_k for the snapped k, orthonormalised by Gram-Schmidt done twice
-  std::vector<double> K((size_t)nk * n);
+}
+
+void project_off_kernel(int n, std::vector<double>& pinv, std::vector<double>& K, int nk) {
+  if (nk == 0) return;
+  // orthonormalise the rows of K by Gram-Schmidt done twice
   for (int a = 0; a < nk; ++a) {
     double* ka = &K[(size_t)a * n];
-    for (int j = 0; j < n; ++j) ka[j] = S[j] * Qt[(size_t)kern[a] * n + j];
     for (int pass = 0; pass < 2; ++pass)
       for (int bb = 0; bb < a; ++bb) {
         const double* kb = &K[(size_t)bb * n];
@@ -532,6 +507,41 @@ int pseudo_inverse_sym(int n, std::vector<double>& A, std::vector<double>& pinv,
       }
     }
   });
+}
+
+int pseudo_inverse_sym(int n, std::vector<double>& A, std::vector<double>& pinv, int& snapped, double theta) {
+  if (n < 1) return STK_ERR_INVALID_ARG;
+  std::vector<double> S, Ah, lam, Qt;
+  equilibrate_sym(n, A, S, Ah);
+  if (!symmetric_eigen(n, Ah, lam, Qt)) return pseudo_inverse_jacobi(n, A, pinv, snapped, theta);
+  double lmax = 0.0;
+  for (int i = 0; i < n; ++i) lmax = std::max(lmax, std::fabs(lam[i]));
+  std::vector<double> inv(n, 0.0);
+  std::vector<int> kern;
+  for (int i = 0; i < n; ++i) {
+    if (std::fabs(lam[i]) <= theta * lmax) kern.push_back(i);
+    else inv[i] = 1.0 / lam[i];
+  }
+  snapped = (int)kern.size();
+  // G = S (sum_k q_k q_k^T / lam_k) S
+  pinv.assign((size_t)n * n, 0.0);
+  parallel_for(n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      double* row = &pinv[(size_t)i * n];
+      for (int k = 0; k < n; ++k) {
+        const double f = Qt[(size_t)k * n + i] * inv[k];
+        if (f == 0.0) continue;
+        const double* q = &Qt[(size_t)k * n];
+        for (int j = 0; j < n; ++j) row[j] += f * q[j];
+      }
+      for (int j = 0; j < n; ++j) row[j] *= S[i] * S[j];
+    }
+  });
+  // K: S q_k for the snapped k (kernel vectors of A)
+  std::vector<double> K((size_t)snapped * n);
+  for (int a = 0; a < snapped; ++a)
+    for (int j = 0; j < n; ++j) K[(size_t)a * n + j] = S[j] * Qt[(size_t)kern[a] * n + j];
+  project_off_kernel(n, pinv, K, snapped);
   return STK_OK;
 }
 

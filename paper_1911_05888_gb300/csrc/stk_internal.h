@@ -1,6 +1,7 @@
 // Internal data structures of the Stokes multigrid library (not part of the C ABI).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -106,6 +107,7 @@ struct Ctx {
   bool ready = false;
   // bottom
   int n_snapped = 0;
+  int bottom_solver = -1;   // STK_INFO_BOTTOM_SOLVER value of the last setup
   int64_t nbot = 0;
   double* bottom_pinv = nullptr;  // [nbot][nbot]
   double* bot_b64 = nullptr;      // FP64 staging for mixed cycles
@@ -119,7 +121,7 @@ struct Ctx {
   double* c64 = nullptr;
   double* norm_buf = nullptr;     // device scalars
   double* norm_host = nullptr;    // pinned
-  int64_t launches = 0;
+  std::atomic<int64_t> launches{0};   // kernels enqueued (calls on one context may come from several threads)
   // graph of one outer iteration, keyed by the caller's x and b pointers
   cudaGraphExec_t graph = nullptr;
   const void* graph_x = nullptr;
@@ -183,6 +185,7 @@ struct Ctx {
   int mgraph_key[3] = {-1, -1, -1};                      // nr, inner, precision
   int64_t mgraph_kernels = 0;
   std::vector<void*> allocations;
+  int64_t device_bytes = 0;   // bytes the library allocated for this context
 };
 
 // ---- setup.cpp --------------------------------------------------------------
@@ -195,10 +198,104 @@ void child_matrices(int d, int p, std::vector<double>& out);   // [2^d][s][s]
 void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w);
 int invert_blocks(int n, int count, const double* A, double* Ainv, std::string& err);
 int pseudo_inverse_sym(int n, std::vector<double>& A, std::vector<double>& pinv, int& snapped, double theta);
+// Equilibration of a symmetric matrix for the bottom eigensolvers:
+// S_i = (row 1-norm)^(-1/2), Ah = S A S.
+void equilibrate_sym(int n, const std::vector<double>& A, std::vector<double>& S, std::vector<double>& Ah);
+// pinv <- P pinv P with P the orthogonal projector off the span of the nk rows
+// of K (row-major nk x n, orthonormalised here); pinv symmetric n x n.
+void project_off_kernel(int n, std::vector<double>& pinv, std::vector<double>& K, int nk);
 int pseudo_inverse_jacobi(int n, std::vector<double>& A, std::vector<double>& pinv, int& snapped,
                           double theta);
 void element_index(const int* n, int d, int64_t e, int* idx);
 void face_points(const Ctx& c, int kind, std::vector<double>& xyz, std::vector<double>* nrm);
 int assemble_rhs_host(const Ctx& c, const double* f_vol, const double* bdata, double* b);
 
+
+// ---- kernels.cu / learn.cu launchers ------------------------------------------
+constexpr int MODE_GS = 0, MODE_RESID = 1;   // element kernel: colour step, or residual
+cudaError_t launch_element(const Pattern& pat, int storage, int mode, int pos0, int npos,
+                           const int* perm, const int* nbr, const void* cpl, const void* mat,
+                           const void* b, void* x, void* r, cudaStream_t st);
+cudaError_t launch_restrict(int vec64, int d, int s, int nb, const int* nc, const int* nf, int64_t nec,
+                            const void* P, const void* r, void* rc, cudaStream_t st);
+cudaError_t launch_prolong(int vec64, int d, int s, int nb, const int* nf, const int* nc, int64_t nec,
+                           const void* PT, const void* xc, void* x, cudaStream_t st);
+cudaError_t launch_bottom(int vec64, int64_t n, const double* pinv, const void* b, void* x,
+                          cudaStream_t st);
+cudaError_t launch_axpy(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st);
+cudaError_t launch_convert(int y64, int x64, int64_t n, void* y, const void* x, cudaStream_t st);
+cudaError_t launch_to_bf16(int64_t n, void* y, const double* x, cudaStream_t st);
+cudaError_t launch_sumsq(int64_t n, const double* x, double* part, double* out, cudaStream_t st);
+cudaError_t launch_multidot(int64_t n, int k, const double* V, int64_t ldv, const double* w, double* part,
+                            double* out, cudaStream_t st);
+cudaError_t launch_multiaxpy(int64_t n, int k, double alpha, const double* coef, const double* V, int64_t ldv,
+                             double* w, cudaStream_t st);
+cudaError_t launch_scale(int64_t n, double s, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_element_pipe(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
+                                const int* nbr, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                                int* err, int ctas, int stages, cudaStream_t st);
+void prepare_pipe_kernels();
+void prepare_mrhs_kernels();
+cudaError_t launch_element_mrhs(const Pattern& pat, int storage, int nr, int mode, int pos0, int npos,
+                                const int* perm, const int* nbr, const void* cpl, const void* mat, const void* b,
+                                void* x, void* r, cudaStream_t st, int tensor = 0, int tensor_small = 0);
+cudaError_t launch_restrict_mr(int vec64, int d, int s, int nb, int nr, const int* nc, const int* nf, int64_t nec,
+                               const void* P, const void* r, void* rc, cudaStream_t st);
+cudaError_t launch_prolong_mr(int vec64, int d, int s, int nb, int nr, const int* nf, const int* nc, int64_t nec,
+                              const void* PT, const void* xc, void* x, cudaStream_t st);
+cudaError_t launch_bottom_mr(int vec64, int64_t n, int nr, const double* pinv, const void* b, void* x, cudaStream_t st);
+cudaError_t launch_interleave(int kind, int64_t m, int nr, int nq, int to_interleaved, void* out, const void* in,
+                              cudaStream_t st);
+cudaError_t launch_sumsq_mr(int64_t m, int nr, const double* x, double* part, double* out, cudaStream_t st);
+cudaError_t launch_multidot_mr(int64_t n, int nr, int k, const double* V, int64_t ldv, const double* w,
+                               double* part, double* out, cudaStream_t st);
+cudaError_t launch_multiaxpy_mr(int64_t n, int nr, int k, double alpha, const double* coef, const double* V,
+                                int64_t ldv, double* w, cudaStream_t st);
+cudaError_t launch_scale_mr(int64_t n, int nr, const double* s, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_features(int ne, int nb, int nface, int NO, int ldf, const int* nbr_nat, const float* r, float* F,
+                            float* nrm, cudaStream_t st);
+cudaError_t launch_sgemm(int M, int N, int K, int ta, int tb, const float* A, int lda, const float* B, int ldb,
+                         float* C, int ldc, const float* bias, int act, float alpha, float beta, cudaStream_t st);
+cudaError_t launch_colsum(int M, int N, const float* A, int lda, float* out, float alpha, cudaStream_t st);
+cudaError_t launch_mse_grad(int64_t n, float scale, const float* Y, const float* T, float* dY, float* part,
+                            cudaStream_t st);
+cudaError_t launch_tanh_back(int64_t n, const float* H, float* dH, cudaStream_t st);
+cudaError_t launch_adam(int64_t n, float lr, float b1, float b2, float c1, float c2, float eps, float* w,
+                        const float* g, float* m, float* v, cudaStream_t st);
+cudaError_t launch_apply_correction(int ne, int nb, int ldy, const float* x, const float* nrm, const float* Y, float* xt,
+                                    cudaStream_t st);
+cudaError_t launch_accept(int64_t n, const double* sums, const float* xt, float* x, int* counters, cudaStream_t st);
+cudaError_t launch_sumsq_f(int64_t n, const float* x, double* part, double* out, cudaStream_t st);
+cudaError_t launch_smooth_field(int ne, int nb, int s, int d, const int* n_dev, uint64_t seed, float* x,
+                                cudaStream_t st);
+cudaError_t launch_target(int ne, int nb, int ldt, const float* xs, const float* x, const float* nrm, float* T,
+                          cudaStream_t st);
+cudaError_t launch_scale_f(int64_t n, float a, const float* x, float* y, cudaStream_t st);
+cudaError_t launch_scale_by_norm(int64_t n, const double* sums, float* g, cudaStream_t st);
+cudaError_t launch_element_wide(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
+                                const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
+                                const void* b, void* x, void* r, cudaStream_t st);
+cudaError_t launch_element_df(const Pattern& pat, int pos0, int npos, const int* perm, const int* nbr,
+                              const void* cpl_hi, const void* cpl_lo, const void* dia_hi, const void* dia_lo,
+                              const float* z, double* w, int ctas, cudaStream_t st);
+cudaError_t launch_fp32_remainder(int64_t n, const double* a, void* lo, cudaStream_t st);
+void prepare_df_kernels();
+cudaError_t launch_to_fp16_tasks(int64_t npos, int S, int T, int TRP, void* dst, float* tsc, const double* src,
+                                 cudaStream_t st);
+cudaError_t launch_to_fp16_rows(int64_t npos, int nb, int NBP, void* dst, float* rsc, const double* src,
+                                cudaStream_t st);
+cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
+                                const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
+                                const void* b, void* x, void* r, int ctas, cudaStream_t st);
+void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages);
+
+// ---- api.cu -------------------------------------------------------------------
+// One element-kernel launch (colour step in MODE_GS, residual in MODE_RESID) on
+// level l of c, on the kernel variant the context's tuning picks for it.
+cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, const void* mat, const void* b,
+                        void* x, void* r, cudaStream_t st);
+
 }  // namespace stk
+
+// The opaque handle of the C ABI is the library context.
+struct stk_ctx : public stk::Ctx {};

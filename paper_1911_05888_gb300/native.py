@@ -21,6 +21,8 @@ BC_PERIODIC, BC_DIRICHLET, BC_STRESS = 0, 1, 2
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 RICHARDSON, FGMRES, FGMRES_IR = 0, 1, 2
 PTS_VOLUME, PTS_INTERIOR_FACE, PTS_BOUNDARY_FACE = 0, 1, 2
+INFO_BOTTOM_SOLVER, INFO_BOTTOM_UNKNOWNS, INFO_COLOURS, INFO_DEVICE_BYTES = 0, 1, 2, 3
+BOTTOM_JACOBI, BOTTOM_HOST_QR, BOTTOM_CUSOLVER = 0, 1, 2
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
@@ -84,6 +86,7 @@ SIGNATURES = {
     "stk_get_colours": [_vp, ctypes.c_int, _c_int_p],
     "stk_get_scaling": [_vp, _c_dbl_p],
     "stk_launch_count": [_vp, _c_i64_p],
+    "stk_get_info": [_vp, ctypes.c_int, _c_i64_p],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
 
@@ -129,6 +132,27 @@ def _ptr(t):
     if not t.is_cuda or not t.is_contiguous():
         raise StkError("expected a contiguous CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+_DTYPE_NAMES = {8: "float64", 4: "float32"}
+
+
+def _vec(name, t, count, itemsize=8, at_least=False):
+    """Device pointer of a vector argument after checking what the kernels
+    will assume about it: a contiguous CUDA tensor of the stated element size
+    (8 = float64, 4 = float32) floating dtype and exactly `count` entries (at
+    least `count` with at_least).  Device vectors cross the ABI as bare
+    pointers, so a short or mistyped tensor would be read or written past its
+    end; it is refused here, before the call."""
+    if t is None:
+        raise ValueError("%s: a device tensor is required" % name)
+    if not t.is_floating_point() or t.element_size() != itemsize:
+        raise ValueError("%s: expected %s, got %s" % (name, _DTYPE_NAMES.get(itemsize, itemsize),
+                                                         getattr(t, "dtype", "%d-byte entries" % t.element_size())))
+    n = t.numel()
+    if (n < count) if at_least else (n != count):
+        raise ValueError("%s: %d entries, expected %s%d" % (name, n, ">= " if at_least else "", count))
+    return _ptr(t)
 
 
 def _stream(stream):
@@ -228,6 +252,19 @@ class Context:
 
     def setup(self, stream=None):
         self._check(self.lib.stk_setup(self.h, _stream(stream)), "stk_setup")
+        nl, ne, nb, _ = self.sizes()
+        self._level_n = [int(v) * nb for v in ne]   # unknowns per level, for the vector checks
+        self._nb = nb
+
+    def _n(self, level=0):
+        """Unknowns of a level (known after setup; the library itself rejects
+        calls before setup)."""
+        sizes = getattr(self, "_level_n", None)
+        if sizes is None:
+            raise StkError("call setup first")
+        if not 0 <= level < len(sizes):
+            raise ValueError("level %d outside 0..%d" % (level, len(sizes) - 1))
+        return sizes[level]
 
     def sizes(self):
         nl = ctypes.c_int()
@@ -267,39 +304,51 @@ class Context:
 
     def residual(self, x, b, r, want_norm=False, stream=None):
         nrm = ctypes.c_double()
-        self._check(self.lib.stk_residual(self.h, _ptr(x), _ptr(b), _ptr(r),
+        n = self._n()
+        self._check(self.lib.stk_residual(self.h, _vec("x", x, n), _vec("b", b, n), _vec("r", r, n),
                                           ctypes.byref(nrm) if want_norm else None, _stream(stream)),
                     "stk_residual")
         return nrm.value if want_norm else None
 
     def gs_colour(self, level, colour, x, b, stream=None):
-        self._check(self.lib.stk_gs_colour(self.h, level, colour, _ptr(x), _ptr(b), _stream(stream)),
+        n = self._n(level)
+        self._check(self.lib.stk_gs_colour(self.h, level, colour, _vec("x", x, n), _vec("b", b, n),
+                                           _stream(stream)),
                     "stk_gs_colour")
 
     def gs_colour_ex(self, level, colour, precision, x, b, stream=None):
-        self._check(self.lib.stk_gs_colour_ex(self.h, level, colour, precision, _ptr(x), _ptr(b),
-                                              _stream(stream)), "stk_gs_colour_ex")
+        n, es = self._n(level), 8 if precision == FP64 else 4
+        self._check(self.lib.stk_gs_colour_ex(self.h, level, colour, precision, _vec("x", x, n, es),
+                                              _vec("b", b, n, es), _stream(stream)), "stk_gs_colour_ex")
 
     def residual_ex(self, level, precision, x, b, r, stream=None):
-        self._check(self.lib.stk_residual_ex(self.h, level, precision, _ptr(x), _ptr(b), _ptr(r),
-                                             _stream(stream)), "stk_residual_ex")
+        n, es = self._n(level), 8 if precision == FP64 else 4
+        self._check(self.lib.stk_residual_ex(self.h, level, precision, _vec("x", x, n, es), _vec("b", b, n, es),
+                                             _vec("r", r, n, es), _stream(stream)), "stk_residual_ex")
 
     def vcycle(self, x, b, stream=None):
-        self._check(self.lib.stk_vcycle(self.h, _ptr(x), _ptr(b), _stream(stream)), "stk_vcycle")
+        n = self._n()
+        self._check(self.lib.stk_vcycle(self.h, _vec("x", x, n), _vec("b", b, n), _stream(stream)), "stk_vcycle")
 
     def restrict(self, level, r, rc, stream=None):
-        self._check(self.lib.stk_restrict(self.h, level, _ptr(r), _ptr(rc), _stream(stream)), "stk_restrict")
+        self._check(self.lib.stk_restrict(self.h, level, _vec("r", r, self._n(level)),
+                                          _vec("rc", rc, self._n(level + 1)), _stream(stream)), "stk_restrict")
 
     def prolong(self, level, xc, x, stream=None):
-        self._check(self.lib.stk_prolong(self.h, level, _ptr(xc), _ptr(x), _stream(stream)), "stk_prolong")
+        self._check(self.lib.stk_prolong(self.h, level, _vec("xc", xc, self._n(level + 1)),
+                                         _vec("x", x, self._n(level)), _stream(stream)), "stk_prolong")
 
     def bottom_solve(self, b, x, stream=None):
-        self._check(self.lib.stk_bottom_solve(self.h, _ptr(b), _ptr(x), _stream(stream)), "stk_bottom_solve")
+        sizes = getattr(self, "_level_n", None)
+        n = self._n(len(sizes) - 1 if sizes else 0)
+        self._check(self.lib.stk_bottom_solve(self.h, _vec("b", b, n), _vec("x", x, n), _stream(stream)),
+                    "stk_bottom_solve")
 
     def solve(self, x, b, rtol=1e-10, maxit=100, stream=None):
         it = ctypes.c_int()
         hist = np.zeros(maxit + 1)
-        rc = self.lib.stk_solve(self.h, _ptr(x), _ptr(b), rtol, maxit, ctypes.byref(it),
+        n = self._n()
+        rc = self.lib.stk_solve(self.h, _vec("x", x, n), _vec("b", b, n), rtol, maxit, ctypes.byref(it),
                                 hist.ctypes.data_as(_c_dbl_p), _stream(stream))
         self._check(rc, "stk_solve")
         return it.value, hist[: it.value + 1]
@@ -312,7 +361,7 @@ class Context:
         it = ctypes.c_int()
         hist = np.zeros(maxit + 1)
         hess = np.zeros((maxit + 1, maxit))
-        self._check(self.lib.stk_gmres_rho(self.h, _ptr(x0), reduction, maxit, ctypes.byref(rho), ctypes.byref(it),
+        self._check(self.lib.stk_gmres_rho(self.h, _vec("x0", x0, self._n()), reduction, maxit, ctypes.byref(rho), ctypes.byref(it),
                                            hist.ctypes.data_as(_c_dbl_p), hess.ctypes.data_as(_c_dbl_p),
                                            _stream(stream)), "stk_gmres_rho")
         n = it.value
@@ -321,13 +370,16 @@ class Context:
     def residual_norm_static(self, x, b, r, norm2, stream=None):
         """stk_residual_norm_static: r = b - A x and ||r||^2 into the device
         scalar norm2, using only the library's fixed static scratch."""
-        self._check(self.lib.stk_residual_norm_static(self.h, _ptr(x), _ptr(b), _ptr(r), _ptr(norm2),
-                                                      _stream(stream)), "stk_residual_norm_static")
+        n = self._n()
+        self._check(self.lib.stk_residual_norm_static(self.h, _vec("x", x, n), _vec("b", b, n), _vec("r", r, n),
+                                                      _vec("norm2", norm2, 1, at_least=True), _stream(stream)),
+                    "stk_residual_norm_static")
 
     def solve_multi(self, X, B, nrhs, rtol=1e-10, maxit=50, inner=1, stream=None):
         it = ctypes.c_int()
         hist = np.zeros((maxit + 1) * nrhs)
-        rc = self.lib.stk_solve_multi(self.h, _ptr(X), _ptr(B), nrhs, rtol, maxit, inner, ctypes.byref(it),
+        n = self._n() * nrhs
+        rc = self.lib.stk_solve_multi(self.h, _vec("X", X, n), _vec("B", B, n), nrhs, rtol, maxit, inner, ctypes.byref(it),
                                       hist.ctypes.data_as(_c_dbl_p), _stream(stream))
         self._check(rc, "stk_solve_multi")
         return it.value, hist[: (it.value + 1) * nrhs].reshape(it.value + 1, nrhs)
@@ -351,7 +403,9 @@ class Context:
         return i.value, h.value, o.value, n.value, r.value
 
     def learn_infer(self, r, y, nrm):
-        self._check(self.lib.stk_learn_infer(self.h, _ptr(r), _ptr(y), _ptr(nrm)), "stk_learn_infer")
+        n = self._n()
+        self._check(self.lib.stk_learn_infer(self.h, _vec("r", r, n, 4), _vec("y", y, n, 4),
+                                             _vec("nrm", nrm, n // self._nb, 4)), "stk_learn_infer")
 
     def learn_state(self, state, nvec):
         r = np.zeros(nvec, dtype=np.float32)
@@ -446,6 +500,12 @@ class Context:
         self._check(self.lib.stk_get_scaling(self.h, out.ctypes.data_as(_c_dbl_p)), "stk_get_scaling")
         return out
 
+    def info(self, what):
+        """stk_get_info: one of the INFO_* keys."""
+        v = ctypes.c_int64()
+        self._check(self.lib.stk_get_info(self.h, what, ctypes.byref(v)), "stk_get_info")
+        return v.value
+
     def launch_count(self):
         n = ctypes.c_int64()
         self._check(self.lib.stk_launch_count(self.h, ctypes.byref(n)), "stk_launch_count")
@@ -461,8 +521,8 @@ def solve_batch(contexts, xs, bs, rtol=1e-10, maxit=200, nrhs=1, inner=3, thread
         raise ValueError("one x and one b per context")
     lib = contexts[0].lib
     hs = (_vp * n)(*[c.h.value for c in contexts])
-    xp = (_vp * n)(*[_ptr(t).value for t in xs])
-    bp = (_vp * n)(*[_ptr(t).value for t in bs])
+    xp = (_vp * n)(*[_vec("x", t, c._n() * nrhs).value for c, t in zip(contexts, xs)])
+    bp = (_vp * n)(*[_vec("b", t, c._n() * nrhs).value for c, t in zip(contexts, bs)])
     it = (ctypes.c_int * n)()
     st = (ctypes.c_int * n)()
     rc = lib.stk_solve_batch(hs, n, xp, bp, nrhs, rtol, maxit, inner, threads, it, st, _stream(stream))

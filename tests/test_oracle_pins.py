@@ -716,3 +716,83 @@ def test_two_colour_gs_contracts_at_least_as_well():
         rho_two, _ = multigrid.Multigrid(prob, levels=mg.levels, injections=mg.I, two_colours=True).gmres_rho(x0)
         assert mg.sm[0].ncol == 4
         assert rho_two <= 0.9 * rho_par, (rho_two, rho_par)
+
+
+# ------------------------------------------------ unsteady and 3D pins ----
+
+def _rho_var():
+    """Variable density rho = 1 + 0.5 sin 2pi x sin 2pi y (sympy and numpy forms)."""
+    import sympy as sp
+    rho_expr = lambda xs: 1 + sp.Rational(1, 2) * sp.sin(2 * sp.pi * xs[0]) * sp.sin(2 * sp.pi * xs[1])
+    rho_np = lambda x: 1.0 + 0.5 * np.sin(2 * np.pi * x[..., 0]) * np.sin(2 * np.pi * x[..., 1])
+    return rho_expr, rho_np
+
+
+@pytest.mark.parametrize("gamma", [0, 1])
+def test_unsteady_delta_limits(gamma):
+    """eq. (timedep2) against its two limits, on every level (Algorithm 3):
+    as delta -> 0 the mass term dominates, delta A_uu -> M_rho, which for a
+    constant rho is rho |E| I in an orthonormal basis (|E| = (2^l h)^d on
+    level l); as delta -> infinity the operator tends to the steady one of
+    Algorithm 2 (eq. taupgeneral tends to tau h / mu).  A wrong 1/delta or
+    rho scale, or a wrong combination of E_mu and E_rho, fails one of them."""
+    rho0 = 2.5
+    bc = [P.DIRICHLET] * 3 + [P.STRESS]
+    rho = lambda x: np.full(x.shape[:-1], rho0)
+    steady = P.generic(2, 8, 2, gamma, bc)
+    lev_s, _ = hierarchy.build_hierarchy(steady)
+    small, _ = hierarchy.build_hierarchy(steady.with_(rho=rho, delta=1e-14))
+    large, _ = hierarchy.build_hierarchy(steady.with_(rho=rho, delta=1e12))
+    assert len(lev_s) == len(small) == len(large) >= 2
+    s = (steady.p + 1) ** 2
+    nb = 3 * s
+    for l, (ls, lsm, llg) in enumerate(zip(lev_s, small, large)):
+        h = 1.0 / ls.mesh.n[0]
+        # delta -> 0: velocity diagonal blocks of delta A are rho h^2 I (the
+        # viscous part contributes delta A_visc ~ 1e-14 x O(500))
+        Ad = hierarchy.diag_blocks(lsm.A, lsm.ne, nb) * 1e-14
+        for v in range(2):
+            blk = Ad[:, v * s:(v + 1) * s, v * s:(v + 1) * s]
+            np.testing.assert_allclose(blk, np.broadcast_to(rho0 * h * h * np.eye(s), blk.shape),
+                                       rtol=0, atol=1e-9 * rho0 * h * h)
+        # delta -> infinity: the steady operator
+        diff = abs(llg.A - ls.A).max()
+        assert diff <= 1e-9 * abs(ls.A).max(), (l, diff)
+
+
+def _unsteady_manufactured(n, gamma):
+    rho_expr, rho_np = _rho_var()
+    delta = 0.05
+    ex = P.paper_solution(2, gamma, rho_expr=rho_expr, delta=delta)
+    return P.generic(2, n, 2, gamma, [P.DIRICHLET] * 3 + [P.STRESS], rho=rho_np, delta=delta, exact=ex)
+
+
+@pytest.mark.parametrize("gamma", [0, 1])
+def test_order_unsteady_mass_term(gamma):
+    """eq. (timedep1) with a fixed delta = 0.05 and variable density
+    rho = 1 + 0.5 sin 2pi x sin 2pi y, Dirichlet on three sides and a stress
+    condition on the fourth (p = 2): the velocity converges at order p+1 and
+    the pressure at about p+1/2, as in the steady case (Section 5).  The mass
+    term rho/delta u is as large as the viscous term here, so a wrong M_rho,
+    1/delta factor or right-hand-side mass term would stop the convergence."""
+    e8 = _solve_manufactured(_unsteady_manufactured(8, gamma))
+    e16 = _solve_manufactured(_unsteady_manufactured(16, gamma))
+    rate = np.log2(e8 / e16)
+    assert np.all(np.abs(rate[:2] - 3.0) < 0.3), rate
+    assert 2.0 < rate[2] < 3.3, rate
+
+
+@pytest.mark.parametrize("gamma", [0, 1])
+def test_order_3d(gamma):
+    """3D assembly (faces orthogonal to all three axes, edge couplings of the
+    viscous-stress form, 3D boundary and stress data): the manufactured
+    solution of Appendix C on the unit cube with Dirichlet on five sides and a
+    stress condition on the top (p = 1) converges at order p+1 = 2 in the
+    velocity and at least p+1/2 in the pressure."""
+    def prob(n):
+        return P.generic(3, n, 1, gamma, [P.DIRICHLET] * 5 + [P.STRESS], exact=P.paper_solution(3, gamma))
+    e4 = _solve_manufactured(prob(4))
+    e8 = _solve_manufactured(prob(8))
+    rate = np.log2(e4 / e8)
+    assert np.all(np.abs(rate[:3] - 2.0) < 0.35), rate
+    assert 1.4 < rate[3] < 2.4, rate
