@@ -117,7 +117,8 @@ def cycle_name(args):
 def cpu_child(spec):
     """Runs in a fresh single-threaded process: time oracle cycles plus the
     outer residual on the sample problem; prints one JSON line.  spec:
-    n,p,nu1,nu2,seconds,gamma,growth,max_sweeps."""
+    n,p,nu1,nu2,seconds,gamma,growth,max_sweeps (seconds 0: exactly one outer
+    iteration, the residual and one cycle, after the untimed setup)."""
     v = spec.split(",")
     n, p, nu1, nu2 = (int(t) for t in v[:4])
     seconds = float(v[4])
@@ -125,7 +126,9 @@ def cpu_child(spec):
     import numpy as np
     from oracle import multigrid
     prob = workload(n, p).with_(nu1=nu1, nu2=nu2)
-    mg = multigrid.Multigrid(prob, shape=shape)
+    t_setup = time.perf_counter()
+    mg = multigrid.Multigrid(prob, shape=shape, two_colours=prob.gamma == 0 and prob.phase is None)
+    t_setup = time.perf_counter() - t_setup
     rng = np.random.default_rng(0)
     b = rng.uniform(-1, 1, prob.n_dofs)
     x = np.zeros_like(b)
@@ -135,19 +138,79 @@ def cpu_child(spec):
         x += mg.precondition(r)
         cycles += 1
         el = time.perf_counter() - t0
-        if el >= seconds and cycles >= 2:
+        if el >= seconds and (cycles >= 2 or seconds == 0):
             break
     print(json.dumps({"dofs": prob.n_dofs, "cycles": cycles, "seconds": el, "nu": [mg.nu1, mg.nu2],
-                      "shape": [mg.gamma, mg.growth, mg.max_sweeps]}))
+                      "shape": [mg.gamma, mg.growth, mg.max_sweeps], "setup_s": t_setup}))
+
+
+def _child_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
+def _child_cmd(args, n, seconds):
+    nu2 = args.nu if args.nu2 is None else args.nu2
+    spec = "%d,%d,%d,%d,%f,%d,%d,%d" % ((n, args.p, args.nu, nu2, seconds) + tuple(shape_of(args)))
+    return [sys.executable, os.path.abspath(__file__), "--cpu-child", spec]
+
+
+def start_cpu_full(args):
+    """The oracle on the benchmarked configuration itself (single thread, its
+    own process, started before the GPU work so that its minutes of setup
+    overlap it): untimed setup, then one outer iteration (FP64 residual and
+    one cycle) timed."""
+    return subprocess.Popen(_child_cmd(args, args.n, 0.0), stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                            text=True, env=_child_env())
+
+
+def finish_cpu_full(args, proc, gpu_iters):
+    try:
+        out, _ = proc.communicate(timeout=1800)
+        rec = json.loads(out.strip().splitlines()[-1])
+    except (subprocess.TimeoutExpired, ValueError, IndexError) as e:
+        proc.kill()
+        return {"value": None, "unit": "DOF-cycles/s", "cores": 1, "kind": "oracle",
+                "sample": "oracle on the %dx%d configuration did not finish: %s" % (args.n, args.n, type(e).__name__)}
+    per_iter = rec["seconds"] / rec["cycles"]
+    value = rec["dofs"] * rec["cycles"] / rec["seconds"]
+    return {"value": value, "unit": "DOF-cycles/s", "cores": 1, "kind": "oracle",
+            "sample": "the benchmarked configuration itself (%dx%d, p=%d, %d DOFs): one outer iteration "
+                      "(FP64 residual + one %s cycle) in %.2f s after a %.0f s untimed setup, numpy/scipy "
+                      "single thread; time to 1e-10 extrapolated by the GPU's %d iterations: %.1f s "
+                      "(extrapolated)" % (args.n, args.n, args.p, rec["dofs"], cycle_name(args), per_iter,
+                                          rec["setup_s"], gpu_iters, per_iter * gpu_iters),
+            "setup_s": round(rec["setup_s"], 1), "extrapolated_time_to_1e-10_s": round(per_iter * gpu_iters, 2)}
+
+
+def cpu_all_cores(args, seconds=12.0):
+    """All host cores at once: one single-threaded oracle process per core
+    (os.sched_getaffinity), each timing cycles of the same problem class on a
+    64 x 64 mesh; the aggregate DOF-cycles/s of the replicas (the method is
+    the same per process; the cores share the host's memory bandwidth)."""
+    cores = len(os.sched_getaffinity(0))
+    n = min(args.n, 64)
+    procs = [subprocess.Popen(_child_cmd(args, n, seconds), stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                              text=True, env=_child_env()) for _ in range(cores)]
+    total, recs = 0.0, []
+    for pr in procs:
+        try:
+            out, _ = pr.communicate(timeout=900)
+            rec = json.loads(out.strip().splitlines()[-1])
+            recs.append(rec)
+            total += rec["dofs"] * rec["cycles"] / rec["seconds"]
+        except (subprocess.TimeoutExpired, ValueError, IndexError):
+            pr.kill()
+    return {"value": total, "unit": "DOF-cycles/s", "cores": cores, "kind": "oracle",
+            "sample": "%d single-threaded oracle processes at once, one per core, each timing %.0f s of %s "
+                      "cycles + FP64 residuals on the same problem class at %dx%d (p=%d); %d finished" % (
+                          cores, seconds, cycle_name(args), n, n, args.p, len(recs))}
 
 
 def cpu_baseline(args, seconds=12.0):
+    """The single-threaded oracle on a 64 x 64 sample of the problem class."""
     n = min(args.n, 64)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    nu2 = args.nu if args.nu2 is None else args.nu2
-    spec = "%d,%d,%d,%d,%f,%d,%d,%d" % ((n, args.p, args.nu, nu2, seconds) + tuple(shape_of(args)))
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", spec], capture_output=True,
-                         text=True, env=env, timeout=900)
+    out = subprocess.run(_child_cmd(args, n, seconds), capture_output=True, text=True, env=_child_env(),
+                         timeout=900)
     rec = json.loads(out.stdout.strip().splitlines()[-1])
     value = rec["dofs"] * rec["cycles"] / rec["seconds"]
     return {"value": value, "unit": "DOF-cycles/s", "cores": 1, "kind": "oracle",
@@ -315,6 +378,8 @@ def run_native(args):
     torch.cuda.set_device(local)
     prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16, "fp16": native.FP16}[args.precision]
     prob = workload(args.n, args.p)
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    cpu_full = start_cpu_full(args) if want_cpu else None
 
     t0 = time.perf_counter()
     nu2 = args.nu if args.nu2 is None else args.nu2
@@ -465,9 +530,17 @@ def run_native(args):
     mg.ctx.set_wide_launch(tuned["wide_max"])
     t_gs64 = time_kernel(lambda: mg64.ctx.gs_colour(0, 0, x, b, stream), 10, stream)
     alg64 = algorithmic_bytes_gs(mg64, prob, 8, 8, int(ne_levels[0]))
+    flops64 = algorithmic_bytes_gs(mg64, prob, 2, 0, int(ne_levels[0]))   # 2 flops per stored entry
+    fp64_peak = mg64.ctx.fp64_fma_rate(stream)
+    bound_s = max(alg64 / (hbm_peak * 1e9), flops64 / (fp64_peak * 1e12))
     kernels64 = {"gs_sweep_fp64_ms": round(t_gs64 * 1e3, 4),
                  "gs_sweep_fp64_GBps": round(alg64 / t_gs64 / 1e9, 1),
-                 "gs_sweep_fp64_TFLOPs": round(alg64 / 8 * 2 / t_gs64 / 1e12, 3)}
+                 "gs_sweep_fp64_TFLOPs": round(flops64 / t_gs64 / 1e12, 3),
+                 "fp64_fma_peak_TFLOPs": round(fp64_peak, 3),
+                 "fp64_peak_source": "measured by the library's FMA-chain kernel (stk_fp64_fma_rate)",
+                 "bound": "fp64" if flops64 / (fp64_peak * 1e12) > alg64 / (hbm_peak * 1e9) else "hbm",
+                 "roofline_frac": round(bound_s / t_gs64, 3),
+                 "roofline_note": "time / max(bytes / measured HBM peak, flops / measured FP64 FMA rate)"}
 
     result = {
         "metric": METRIC, "value": value, "unit": "DOF-cycles/s", "n_gpus": world, "steps": args.steps,
@@ -487,8 +560,15 @@ def run_native(args):
         "learned_smoother": learned,
         "clocks": clk,
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(args)
+    if want_cpu:
+        full = finish_cpu_full(args, cpu_full, iters[0])
+        single = cpu_baseline(args)
+        allc = cpu_all_cores(args)
+        # the headline baseline: the benchmarked configuration itself when the
+        # oracle finished it, else the 64 x 64 single-thread sample
+        result["cpu_baseline"] = dict(full if full.get("value") else single)
+        result["cpu_baseline"]["single_thread_64x64"] = single
+        result["cpu_baseline"]["all_cores"] = allc
     if rank == 0:
         print(json.dumps(result))
     if dist:
@@ -499,42 +579,42 @@ def run_native(args):
 # Reference arm: the CPU oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 def run_reference(args):
+    """The oracle (numpy/scipy, the plain CPU implementation the tests compare
+    the library with) on the benchmarked configuration itself: untimed setup,
+    then W warm-up and K timed steps, each step one outer iteration (the FP64
+    residual and one cycle of the native arm's shape) of the solve from x = 0."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    n = min(args.n, 64)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"   # before numpy loads its BLAS: one core, as reported
     import numpy as np
     from oracle import multigrid
-    prob = workload(n, args.p).with_(nu1=args.nu, nu2=args.nu if args.nu2 is None else args.nu2)
-    mg = multigrid.Multigrid(prob, shape=tuple(shape_of(args)))
+    prob = workload(args.n, args.p).with_(nu1=args.nu, nu2=args.nu if args.nu2 is None else args.nu2)
+    t_setup = time.perf_counter()
+    mg = multigrid.Multigrid(prob, shape=tuple(shape_of(args)), two_colours=prob.gamma == 0 and prob.phase is None)
+    t_setup = time.perf_counter() - t_setup
     b = np.random.default_rng(0).uniform(-1, 1, prob.n_dofs)
     x = np.zeros_like(b)
 
     def step():
-        cyc, t0 = 0, time.perf_counter()
-        while True:
-            x[:] += mg.precondition(b - mg.A @ x)
-            cyc += 1
-            if time.perf_counter() - t0 >= per_step:
-                return cyc, time.perf_counter() - t0
+        t0 = time.perf_counter()
+        x[:] += mg.precondition(b - mg.A @ x)
+        return time.perf_counter() - t0
     for _ in range(args.warmup):
         step()
-    tot_c, tot_s = 0, 0.0
-    for _ in range(args.steps):
-        c, s = step()
-        tot_c += c
-        tot_s += s
-    value = prob.n_dofs * tot_c / tot_s
-    sample = ("oracle (numpy/scipy, single process) on the same problem class at %dx%d, p=%d "
-              "(%d DOFs); each step = %.0f s of %s cycles with FP64 residuals" % (
-                  n, n, args.p, prob.n_dofs, per_step, cycle_name(args)))
+    tot_s = sum(step() for _ in range(args.steps))
+    value = prob.n_dofs * args.steps / tot_s
+    cores = 1
+    sample = ("oracle (numpy/scipy, one process, one thread for BLAS) on the benchmarked configuration "
+              "(%dx%d, p=%d, %d DOFs); each step = one outer iteration (FP64 residual + one %s cycle); "
+              "setup %.0f s untimed" % (args.n, args.n, args.p, prob.n_dofs, cycle_name(args), t_setup))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-cycles/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config(args, workload(args.n, args.p)),
-        "cpu_baseline": {"value": value, "unit": "DOF-cycles/s", "cores": 1, "kind": "oracle",
+        "data": "synthetic", "config": config(args, prob),
+        "cpu_baseline": {"value": value, "unit": "DOF-cycles/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "DOF-cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))

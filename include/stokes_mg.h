@@ -149,6 +149,24 @@ int stk_set_cycle(stk_ctx* ctx, int nu1, int nu2, int precision);
 int stk_set_cycle_shape(stk_ctx* ctx, int gamma, int growth, int max_sweeps);
 
 /*
+ * Colouring of the block Gauss-Seidel sweep on single-phase levels (Section 3:
+ * the elements of one colour are updated together, so no two of them may
+ * couple).  STK_COLOURS_AUTO (default): the checkerboard (i_1+...+i_d) mod 2
+ * for the standard form (gamma = 0), whose operator couples face neighbours
+ * only, and the 2^d parity colours sum_k (i_k mod 2) 2^k for the
+ * viscous-stress form, whose diagonal (2D) / edge (3D) couplings the
+ * checkerboard would not separate.  STK_COLOURS_PARITY forces the 2^d colours;
+ * STK_COLOURS_CHECKERBOARD forces two colours (stk_setup then returns
+ * STK_ERR_INVALID_ARG unless gamma = 0 and the problem has one phase).  Problems
+ * with phases always take the greedy colouring.  Takes effect at the next
+ * stk_setup.  Errors: STK_ERR_INVALID_ARG for an unknown mode.
+ */
+#define STK_COLOURS_AUTO 0
+#define STK_COLOURS_PARITY 1
+#define STK_COLOURS_CHECKERBOARD 2
+int stk_set_colouring(stk_ctx* ctx, int mode);
+
+/*
  * Setup: fine-level LDG assembly (Appendix A), operator coarsening
  * (Algorithm 2, or 3 when unsteady) down to the bottom level (some n_k odd or
  * equal to 2), the Stokes blocks of every level, element-block inverses (FP64
@@ -503,6 +521,17 @@ int stk_autotune(stk_ctx* ctx, int* choice, double* best_ms, void* stream);
 /* Number of kernel launches the library enqueued since the context was
  * created (all of them are this library's own kernels). */
 int stk_launch_count(stk_ctx* ctx, int64_t* count);
+
+/*
+ * Measured FP64 FMA rate of the context's device (not a step of the method;
+ * it is the denominator of the FP64 element kernels' roofline, whose
+ * arithmetic intensity of 0.25 flop/B can be bound by the FP64 pipe rather
+ * than by HBM).  A project kernel runs eight independent FMA chains per
+ * thread on 8 CTAs of 256 threads per SM, 2^16 FMAs per chain; *tflops gets
+ * the best of three timed launches (CUDA events on `stream`, after one
+ * warm-up), in TFLOP/s counting 2 flops per FMA.  Needs stk_setup.
+ */
+int stk_fp64_fma_rate(stk_ctx* ctx, double* tflops, void* stream);
 
 #ifdef __cplusplus
 }

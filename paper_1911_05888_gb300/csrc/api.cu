@@ -134,10 +134,23 @@ void free_device(Ctx& c) {
 int64_t level_ne(const Ctx& c, int l) { return c.host[l].ne; }
 int nlevels(const Ctx& c) { return (int)c.host.size(); }
 
+// Colouring of a single-phase level: the checkerboard (i_1 + ... + i_d) mod 2
+// when the operator couples face neighbours only (standard form), else the
+// 2^d parity colouring sum_k (i_k mod 2) 2^k, which also separates the
+// diagonal / edge couplings of the viscous-stress form (Section 3 asks only
+// for a valid multi-colouring).
+bool checkerboard(const Ctx& c) {
+  return c.colouring == STK_COLOURS_CHECKERBOARD || (c.colouring == STK_COLOURS_AUTO && c.gamma == 0);
+}
+
 int colour_of(const Ctx& c, const int* n, int64_t e) {
   int idx[3];
   element_index(n, c.d, e, idx);
   int col = 0;
+  if (checkerboard(c)) {
+    for (int k = 0; k < c.d; ++k) col += idx[k];
+    return col & 1;
+  }
   for (int k = 0; k < c.d; ++k) col |= (idx[k] & 1) << k;
   return col;
 }
@@ -1344,6 +1357,15 @@ int stk_set_cycle(stk_ctx* c, int nu1, int nu2, int precision) {
   });
 }
 
+int stk_set_colouring(stk_ctx* c, int mode) {
+  return guard(c, [&]() -> int {
+    if (mode < STK_COLOURS_AUTO || mode > STK_COLOURS_CHECKERBOARD)
+      return fail(c, STK_ERR_INVALID_ARG, "bad colouring mode");
+    c->colouring = mode;
+    return STK_OK;
+  });
+}
+
 int stk_set_cycle_shape(stk_ctx* c, int gamma, int growth, int max_sweeps) {
   return guard(c, [&]() -> int {
     if (gamma < 1 || gamma > 3 || growth < 1 || growth > 4 || max_sweeps < 1 || max_sweeps > 256)
@@ -1360,6 +1382,9 @@ int stk_setup(stk_ctx* c, void* stream) {
   return guard(c, [&]() -> int {
     if (c->p < 0) return fail(c, STK_ERR_INVALID_ARG, "set mesh and discretisation first");
     if (c->mu_vol.empty()) return fail(c, STK_ERR_INVALID_ARG, "set the viscosity first");
+    if (c->colouring == STK_COLOURS_CHECKERBOARD && (c->gamma != 0 || !c->chi.empty()))
+      return fail(c, STK_ERR_INVALID_ARG,
+                  "the checkerboard is a valid colouring only for the single-phase standard form");
     ck(cudaSetDevice(c->device), "cudaSetDevice");
     free_device(*c);
     build_pattern(c->d, c->p, c->gamma, !c->chi.empty(), c->pat);
@@ -2363,6 +2388,37 @@ int stk_get_scaling(stk_ctx* c, double* D) {
       std::fill(D, D + (size_t)H.ne * c->nb, 1.0);
     else
       std::copy(H.Dscale.begin(), H.Dscale.end(), D);
+    return STK_OK;
+  });
+}
+
+int stk_fp64_fma_rate(stk_ctx* c, double* tflops, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!tflops) return fail(c, STK_ERR_INVALID_ARG, "null output");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    int sms = 0;
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attribute");
+    const int blocks = sms * 8, iters = 1 << 16;
+    if (!c->norm_buf) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0), "event");
+    ck(cudaEventCreate(&e1), "event");
+    double best = 0.0;
+    for (int rep = 0; rep < 4; ++rep) {
+      ck(cudaEventRecord(e0, st), "record");
+      ck(launch_fp64_fma(blocks, iters, c->norm_buf + 32, st), "fp64 probe");
+      ck(cudaEventRecord(e1, st), "record");
+      ck(cudaEventSynchronize(e1), "sync");
+      float ms = 0.f;
+      ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+      const double flops = 2.0 * 8.0 * iters * (double)blocks * 256.0;
+      if (rep > 0 && ms > 0) best = std::max(best, flops / (ms * 1e-3) / 1e12);   // rep 0 warms up
+      c->launches++;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *tflops = best;
     return STK_OK;
   });
 }

@@ -1514,6 +1514,31 @@ cudaError_t launch_to_bf16(int64_t n, void* y, const double* x, cudaStream_t st)
 }
 
 // ||x||_2^2 into out[0] (device); part holds 1024 partials.
+// ---- FP64 FMA rate probe ----------------------------------------------------
+// Eight independent chains of dependent FMAs per thread (enough instruction-
+// level parallelism to cover the FP64 pipe latency with 8 warps per SM
+// scheduler); the result is written only when it takes an impossible value,
+// so the compiler keeps every FMA.  2 flops per FMA.
+__global__ void __launch_bounds__(256) fp64_fma_kernel(int iters, double seed, double* __restrict__ out) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + 1e-3 * (threadIdx.x + k);
+  const double m = 0.9999999, c = 1e-7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == -1.0) out[0] = s;   // never taken (s stays near 8); one slot, always in bounds
+}
+
+cudaError_t launch_fp64_fma(int blocks, int iters, double* out, cudaStream_t st) {
+  fp64_fma_kernel<<<blocks, 256, 0, st>>>(iters, 0.5, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sumsq(int64_t n, const double* x, double* part, double* out, cudaStream_t st) {
   int64_t blocks = (n + 255) / 256;
   int grid = (int)std::min<int64_t>(blocks, 1024);

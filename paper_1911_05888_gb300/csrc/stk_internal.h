@@ -99,6 +99,8 @@ struct Ctx {
   // cycle shape: coarse-level visits per level (1 = V-cycle, 2 = W-cycle) and the
   // per-level growth of the smoothing counts (variable V-cycle), capped
   int cyc_gamma = 1, cyc_growth = 1, cyc_cap = 64;
+  // smoother colouring of single-phase levels (STK_COLOURS_*)
+  int colouring = 0;
   // derived
   int s = 0, nb = 0, q = 0;
   Pattern pat{};
@@ -288,6 +290,8 @@ cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int p
                                 const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
                                 const void* b, void* x, void* r, int ctas, cudaStream_t st);
 void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages);
+
+cudaError_t launch_fp64_fma(int blocks, int iters, double* out, cudaStream_t st);
 
 // ---- api.cu -------------------------------------------------------------------
 // One element-kernel launch (colour step in MODE_GS, residual in MODE_RESID) on

@@ -23,6 +23,7 @@ RICHARDSON, FGMRES, FGMRES_IR = 0, 1, 2
 PTS_VOLUME, PTS_INTERIOR_FACE, PTS_BOUNDARY_FACE = 0, 1, 2
 INFO_BOTTOM_SOLVER, INFO_BOTTOM_UNKNOWNS, INFO_COLOURS, INFO_DEVICE_BYTES = 0, 1, 2, 3
 BOTTOM_JACOBI, BOTTOM_HOST_QR, BOTTOM_CUSOLVER = 0, 1, 2
+COLOURS_AUTO, COLOURS_PARITY, COLOURS_CHECKERBOARD = 0, 1, 2
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
@@ -87,6 +88,8 @@ SIGNATURES = {
     "stk_get_scaling": [_vp, _c_dbl_p],
     "stk_launch_count": [_vp, _c_i64_p],
     "stk_get_info": [_vp, ctypes.c_int, _c_i64_p],
+    "stk_set_colouring": [_vp, ctypes.c_int],
+    "stk_fp64_fma_rate": [_vp, _c_dbl_p, _vp],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
 
@@ -249,6 +252,12 @@ class Context:
         """gamma coarse visits per level (1 V-cycle, 2 W-cycle); smoothing
         counts nu * growth^level, at most max(nu, max_sweeps)."""
         self._check(self.lib.stk_set_cycle_shape(self.h, gamma, growth, max_sweeps), "stk_set_cycle_shape")
+
+    def set_colouring(self, mode):
+        """COLOURS_AUTO (checkerboard for the single-phase standard form,
+        2^d parity colours otherwise), COLOURS_PARITY or COLOURS_CHECKERBOARD;
+        takes effect at the next setup."""
+        self._check(self.lib.stk_set_colouring(self.h, mode), "stk_set_colouring")
 
     def setup(self, stream=None):
         self._check(self.lib.stk_setup(self.h, _stream(stream)), "stk_setup")
@@ -504,6 +513,12 @@ class Context:
         """stk_get_info: one of the INFO_* keys."""
         v = ctypes.c_int64()
         self._check(self.lib.stk_get_info(self.h, what, ctypes.byref(v)), "stk_get_info")
+        return v.value
+
+    def fp64_fma_rate(self, stream=None):
+        """Measured FP64 FMA rate of the device in TFLOP/s (stk_fp64_fma_rate)."""
+        v = ctypes.c_double()
+        self._check(self.lib.stk_fp64_fma_rate(self.h, ctypes.byref(v), _stream(stream)), "stk_fp64_fma_rate")
         return v.value
 
     def launch_count(self):

@@ -9,7 +9,8 @@ from .problems import PERIODIC, DIRICHLET, STRESS
 
 
 class StokesMG:
-    def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True, shape=None):
+    def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True, shape=None,
+                 colouring=native.COLOURS_AUTO):
         self.prob = prob
         self.ctx = native.Context(device)
         d = prob.d
@@ -33,6 +34,7 @@ class StokesMG:
         self.ctx.set_cycle(nu1, nu2, precision)
         if shape is not None:
             self.ctx.set_cycle_shape(*shape)
+        self.ctx.set_colouring(colouring)
         if setup:
             self.ctx.setup()
             self.nlevels, self.ne_levels, self.nb, self.n_snapped = self.ctx.sizes()

@@ -64,3 +64,30 @@ def test_cpu_child_runs_the_configured_cycle_shape():
     assert recs["2,1,64"]["cycles"] >= 2
     assert recs["1,1,64"]["shape"] == [1, 1, 64] and recs["2,1,64"]["shape"] == [2, 1, 64]
     assert recs["1,1,64"]["nu"] == recs["2,1,64"]["nu"] == [2, 1]
+
+
+def test_reference_arm_reports_the_configuration_it_ran():
+    """The reference arm runs the oracle on the configuration named by the
+    arguments and says so: its config's mesh and DOF count are those of the
+    problem it timed."""
+    import json
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--n", "8", "--p", "1",
+                        "--steps", "2", "--warmup", "1", "--nu", "1"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert p.returncode == 0, p.stderr
+    rec = json.loads(p.stdout.strip().splitlines()[-1])
+    assert rec["impl"] == "reference"
+    assert rec["config"]["n"] == [8, 8] and rec["config"]["dofs"] == 8 * 8 * 3 * 4
+    assert "8x8" in rec["cpu_baseline"]["sample"] and rec["cpu_baseline"]["cores"] == 1
+    assert rec["value"] > 0 and rec["e2e"]["value"] == rec["value"]
+
+
+def test_cpu_child_single_outer_iteration():
+    """seconds = 0: exactly one outer iteration after the untimed setup (the
+    full-configuration baseline)."""
+    import json
+    p = subprocess.run([sys.executable, "bench.py", "--cpu-child", "8,1,1,1,0,1,1,64"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr
+    rec = json.loads(p.stdout.strip().splitlines()[-1])
+    assert rec["cycles"] == 1 and rec["setup_s"] >= 0

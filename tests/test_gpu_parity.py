@@ -36,12 +36,18 @@ CASES = {
 _cache = {}
 
 
+def oracle_for(prob, **kw):
+    """The oracle with the library's default colouring: the checkerboard for
+    the single-phase standard form, the 2^d parity colours otherwise."""
+    return multigrid.Multigrid(prob, two_colours=(prob.gamma == 0 and prob.phase is None), **kw)
+
+
 def get(name, precision=native.FP64):
     key = (name, precision)
     if key not in _cache:
         prob = CASES[name]()
         gpu = StokesMG(prob, precision=precision)
-        orc = multigrid.Multigrid(prob) if (name, native.FP64) not in _cache else _cache[(name, native.FP64)][2]
+        orc = oracle_for(prob) if (name, native.FP64) not in _cache else _cache[(name, native.FP64)][2]
         _cache[key] = (prob, gpu, orc)
     return _cache[key]
 
@@ -254,7 +260,7 @@ def test_low_precision_cycle_close_to_oracle_emulation(name, precision):
     (amplified by the cycle)."""
     prob, gpu64, _ = get(name)
     _, gpu, _ = get(name, precision)
-    orc = multigrid.Multigrid(prob, storage=STORAGE[precision])
+    orc = oracle_for(prob, storage=STORAGE[precision])
     b = gpu64.rhs().ravel()
     bd = dev(b)
     x = torch.zeros_like(bd)
@@ -263,7 +269,7 @@ def test_low_precision_cycle_close_to_oracle_emulation(name, precision):
     assert rel(x.cpu().numpy(), xo) <= 1e-4
     if precision != native.FP32:
         # and it is the rounded operator that is being emulated: the FP32 one differs more
-        orc32 = multigrid.Multigrid(prob, storage="fp32")
+        orc32 = oracle_for(prob, storage="fp32")
         assert rel(x.cpu().numpy(), orc32.precondition(b)) > 10 * rel(x.cpu().numpy(), xo)
 
 
@@ -274,7 +280,7 @@ def test_fp16_colour_step_warp_and_wide_kernels(name):
     blocks, in FP32-level agreement."""
     prob, _, _ = get(name)
     _, gpu, _ = get(name, native.FP16)
-    orc = multigrid.Multigrid(prob, storage="fp16")
+    orc = oracle_for(prob, storage="fp16")
     sm = orc.sm[0]
     rng = np.random.default_rng(17)
     x0 = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
@@ -451,7 +457,7 @@ def test_multi_rhs_tensor_cores_match_cuda_cores(name):
     FP32-rounded blocks."""
     prob, _, _ = get(name)
     _, gpu, _ = get(name, native.FP32)
-    orc32 = multigrid.Multigrid(prob, storage="fp32")
+    orc32 = oracle_for(prob, storage="fp32")
     nrhs = 8
     rng = np.random.default_rng(41)
     B = rng.uniform(-1, 1, (nrhs, prob.n_dofs))
@@ -841,5 +847,45 @@ def test_tau_sweep_valley_contains_table1_tau():
     assert rhos[mid] <= rhos.min() ** (1 - T.EPS)
     q = P.generic(2, 32, 2, 0, [P.PERIODIC] * 4, nu=(3, 3), tau=taus[mid])
     x0 = P.random_vector(q.n_elements, q.nb, seed=1).ravel()
-    rho_o, n_o = multigrid.Multigrid(q).gmres_rho(x0, maxit=100)
+    rho_o, n_o = oracle_for(q).gmres_rho(x0, maxit=100)
     assert its[mid] == n_o and abs(rhos[mid] - rho_o) <= 1e-9 * rho_o
+
+
+@pytest.mark.parametrize("name", ["periodic16p2", "dirichlet-rect", "3d-unsteady-p2"])
+def test_colouring_modes(name):
+    """Standard form (Section 3's block GS with a valid multi-colouring): by
+    default the library colours every smoothing level with the checkerboard
+    (two colours; the oracle's colour_two), and on request with the 2^d parity
+    colours; in both modes the level colours equal the oracle's and four
+    V-cycle iterates match the oracle with the same colouring to 1e-12."""
+    prob, gpu, orc = get(name)
+    assert gpu.ctx.info(native.INFO_COLOURS) == 2
+    for l in range(len(orc.levels) - 1):
+        assert np.array_equal(gpu.ctx.get_colours(l, orc.levels[l].ne), orc.levels[l].mesh.colour_two())
+    par = StokesMG(prob, colouring=native.COLOURS_PARITY)
+    try:
+        orc_par = multigrid.Multigrid(prob, levels=orc.levels, injections=orc.I)
+        assert par.ctx.info(native.INFO_COLOURS) == 2 ** prob.d
+        for l in range(len(orc.levels) - 1):
+            assert np.array_equal(par.ctx.get_colours(l, orc.levels[l].ne), orc.levels[l].mesh.colour())
+        rng = np.random.default_rng(2)
+        Z = trivial_kernel(prob, orc)
+        b = rng.uniform(-1, 1, prob.n_dofs)
+        b -= Z @ (Z.T @ b)
+        for g, o in ((gpu, orc), (par, orc_par)):
+            xd, xo = torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda"), np.zeros(prob.n_dofs)
+            for _ in range(4):
+                g.ctx.vcycle(xd, dev(b))
+                o.vcycle(xo, b)
+                xg = xd.cpu().numpy()
+                xg, xr = xg - Z @ (Z.T @ xg), xo - Z @ (Z.T @ xo)
+                assert rel(xg, xr) <= 1e-12 and maxrel(xg, xr) <= 1e-12
+    finally:
+        par.close()
+
+
+def test_checkerboard_refused_for_viscous_stress_form():
+    """The viscous-stress form couples diagonal neighbours, which the
+    checkerboard puts in one colour: setup refuses it."""
+    with pytest.raises(native.StkError):
+        StokesMG(CASES["stress16p3"](), colouring=native.COLOURS_CHECKERBOARD)
