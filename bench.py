@@ -59,7 +59,11 @@ def parse():
                     help="gamma,growth,max_sweeps: 1,1,64 = V-cycle, 2,1,64 = W-cycle, 1,2,N = variable V-cycle")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides solved together (1..8)")
     ap.add_argument("--inner", type=int, default=3, help="inner refinement steps (several right-hand sides)")
-    ap.add_argument("--learned", type=int, default=0, help="1: train and enable the learned post-smoother")
+    ap.add_argument("--learned", type=int, default=1,
+                    help="1 (default): time the learned post-smoother arm (iterative refinement with the "
+                         "acceptance rule) as the mixed_learned sub-record; 0: skip it")
+    ap.add_argument("--learn-objective", type=int, default=0, choices=[0, 1],
+                    help="0: residual objective; 1: supervised error target")
     ap.add_argument("--learn-seeds", type=int, default=8)
     ap.add_argument("--learn-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -362,6 +366,63 @@ def run_profile(args):
     torch.cuda.synchronize()
 
 
+def learned_arm(mg, args, stream, prec, objective=0):
+    """The learned post-smoother on the benchmarked problem (FP32 cycle): the
+    outer iteration is iterative refinement, whose per-cycle FP64 residual the
+    acceptance rule judges (kappa from two plain iterations; a correction is
+    kept only if ||r_new|| < kappa ||r_old||).  Timed beside the same
+    refinement with plain V(nu, nu) cycles and with V(nu, nu+1), which costs
+    about what the correction costs (one finest-level residual and the
+    network).  Training (seeded smooth fields, plain-cycle states) is setup,
+    outside the timings."""
+    import torch
+    from paper_1911_05888_gb300 import native
+    b = torch.from_numpy(mg.rhs().ravel()).cuda()
+    x = torch.zeros_like(b)
+
+    def timed(steps=3):
+        mg.ctx.solve(x.zero_(), b, rtol=1e-10, maxit=200)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            it, hist = mg.ctx.solve(x.zero_(), b, rtol=1e-10, maxit=200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"ms_per_solve": round(e0.elapsed_time(e1) / steps, 3), "iters": int(it),
+                "final_rel_residual": float(hist[-1])}
+
+    mg.ctx.set_solver(native.RICHARDSON, args.restart)
+    out = {"outer": "iterative refinement (the acceptance rule needs each cycle's outer residual)",
+           "objective": ["residual ||r - A delta||^2/||r||^2", "supervised MSE of the normalised error"][objective]}
+    learn_ready = False
+    try:
+        out["plain"] = timed()
+        mg.ctx.set_cycle(args.nu, args.nu + 1, prec)
+        out["plain_one_more_post_sweep"] = timed()
+        mg.ctx.set_cycle(args.nu, args.nu, prec)
+        t1 = time.perf_counter()
+        mg.ctx.learn_setup(hidden=64, seed=0)
+        learn_ready = True
+        mg.ctx.learn_objective(objective)
+        mg.ctx.learn_generate(nseeds=args.learn_seeds, cycles=3, seed=0)
+        loss = mg.ctx.learn_train(epochs=args.learn_epochs, batch=0, lr=1e-3, seed=1)
+        out["train"] = {"hidden": 64, "seeds": args.learn_seeds, "cycles_per_seed": 3, "epochs": args.learn_epochs,
+                        "final_loss": loss, "train_s": round(time.perf_counter() - t1, 2)}
+        mg.ctx.learn_enable(True)
+        out["learned"] = timed()
+        acc, rej = mg.ctx.learn_stats()
+        dec, ratio, kappa = mg.ctx.learn_history()
+        out["learned"].update({"accepted": int(acc), "rejected": int(rej), "kappa": kappa,
+                               "decisions_last_solve": [int(v) for v in dec],
+                               "ratios_last_solve": [round(float(v), 4) for v in ratio]})
+    finally:
+        if learn_ready:
+            mg.ctx.learn_enable(False)
+        mg.ctx.set_cycle(args.nu, args.nu, prec)
+    return out
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -395,14 +456,6 @@ def run_native(args):
     method = {"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR, "richardson": native.RICHARDSON}[args.solver]
     mg.ctx.set_solver(method, args.restart)
     mg64.ctx.set_solver(native.FGMRES if method == native.FGMRES_IR else method, args.restart)
-    learned = None
-    if args.learned and prec != native.FP64:
-        t1 = time.perf_counter()
-        mg.ctx.learn_setup(hidden=64, seed=0)
-        mg.ctx.learn_generate(nseeds=args.learn_seeds, cycles=3, seed=0)
-        loss = mg.ctx.learn_train(epochs=args.learn_epochs, batch=4096, lr=1e-3, seed=1)
-        learned = {"hidden": 64, "train_seeds": args.learn_seeds, "cycles_per_seed": 3,
-                   "epochs": args.learn_epochs, "final_loss": loss, "train_s": round(time.perf_counter() - t1, 2)}
     b_host = mg.rhs().ravel()
     b = torch.from_numpy(b_host).cuda()
     x = torch.zeros_like(b)
@@ -443,19 +496,10 @@ def run_native(args):
         el = ev0.elapsed_time(ev1) / 1e3
         return el, iters, ctx.launch_count() - l0, hist
 
-    if learned is not None:
-        # same problem without the correction, for the comparison
-        el_nl, it_nl, _, _ = timed(mg.ctx, max(1, args.steps // 2), 1)
-        learned["without"] = {"ms_per_solve": el_nl / len(it_nl) * 1e3, "iters": it_nl[0]}
-        mg.ctx.learn_enable(True)
     clocks = Clocks(local)
     clocks.start()
     el, iters, launches, hist = timed(mg.ctx, args.steps, args.warmup)
     clk = clocks.stop()
-    if learned is not None:
-        acc, rej = mg.ctx.learn_stats()
-        learned.update({"with": {"ms_per_solve": el / args.steps * 1e3, "iters": iters[0]},
-                        "accepted_cycles": acc, "rejected_cycles": rej})
     cycles = sum(iters)
     el, units = aggregate(dist, el, prob.n_dofs * max(1, args.nrhs) * cycles, "cuda")
     value = units / el
@@ -528,6 +572,11 @@ def run_native(args):
                 variants["warp_ctas%d" % c_] = {"launch_ms": round(tv * 1e3, 4), "GBps": round(alg / tv / 1e9, 1)}
     mg.ctx.set_tuning(tuned["variant"], prec, tuned["ctas_cycle"])
     mg.ctx.set_wide_launch(tuned["wide_max"])
+    mixed_learned = None
+    if args.learned and prec != native.FP64 and args.nrhs == 1:
+        mixed_learned = learned_arm(mg, args, stream, prec, args.learn_objective)
+        mixed_learned["headline_arm"] = "the faster arm, %s without the correction" % config(args, prob)["outer"]
+        mg.ctx.set_solver(method, args.restart)
     t_gs64 = time_kernel(lambda: mg64.ctx.gs_colour(0, 0, x, b, stream), 10, stream)
     alg64 = algorithmic_bytes_gs(mg64, prob, 8, 8, int(ne_levels[0]))
     flops64 = algorithmic_bytes_gs(mg64, prob, 2, 0, int(ne_levels[0]))   # 2 flops per stored entry
@@ -557,7 +606,7 @@ def run_native(args):
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "fp64_kernels": kernels64,
         "gs_variants": variants, "autotune": {"cycle": tuned, "fp64": tuned64,
                                               "best_colour_step_ms": [round(v, 4) for v in tuned_ms]},
-        "learned_smoother": learned,
+        "mixed_learned": mixed_learned,
         "clocks": clk,
     }
     if want_cpu:

@@ -414,23 +414,44 @@ int stk_solve_batch(stk_ctx* const* ctx, int n, double* const* x, const double* 
 
 /*
  * Learned element-local post-smoother (not in the paper; cycles in FP32 or
- * BF16 only).  After the post-smoothing sweeps on the finest level, with
- * r = b - A x, each element's residual and those of its 2d face neighbours,
- * divided by ||r_i||, go through a two-layer perceptron (in = (2d+1) nb, tanh
- * hidden layer of `hidden` units, out = nb) whose output times ||r_i|| is a
- * correction delta_i.  x + delta replaces the block Gauss-Seidel iterate only
- * if ||r - A delta|| < ||r|| (decided on the device each cycle), so the plain
- * smoother stays both the fallback and the yardstick of acceptance.
+ * BF16 only).  After a V-cycle c = V(0, r) on the finest level, with
+ * r_c = r - A c the cycle's own residual after its post-smoothing sweeps
+ * (FP32, the cycle's records), each element's r_c,i and those of its 2d face
+ * neighbours, divided by ||r_c,i||, go through a two-layer perceptron
+ * (in = (2d+1) nb, tanh hidden layer of `hidden` units, out = nb) whose
+ * output times ||r_c,i|| is a correction delta_i.
+ * Acceptance (kept only where its measured contraction beats plain block
+ * Gauss-Seidel): stk_solve with outer method 0 (iterative refinement) runs
+ * its first two iterations with plain cycles and measures their contraction
+ * kappa = (||r_2|| / ||r_0||)^(1/2); every later iteration applies
+ * x <- x + c + delta and keeps delta only if the new FP64 outer residual
+ * (computed anyway) satisfies ||r_new|| < kappa ||r_old||; otherwise delta is
+ * subtracted again (x + c, the plain cycle's result, with its residual
+ * recomputed), and after two consecutive rejections the correction is
+ * switched off for the rest of that solve.  The plain smoother is thus both
+ * the fallback and the yardstick.  stk_solve with a Krylov outer method and
+ * the correction enabled returns STK_ERR_INVALID_ARG (the rule needs the
+ * outer residual of every cycle).
  *  stk_learn_setup     allocate and initialise the weights (deterministic in seed);
- *  stk_learn_generate  residual states from the plain V-cycle: for nseeds smooth
+ *  stk_learn_generate  training states from the plain V-cycle: for nseeds smooth
  *                      random solutions x* (seeded), b = A x*, `cycles` V-cycles
- *                      from zero, storing r = b - A x after each;
- *  stk_learn_train     Adam on the loss ||r - A delta(r)||^2 / ||r||^2 over the
- *                      stored states in random order (`epochs` passes; `batch`
- *                      is unused, one state per step); *loss_out = mean loss
- *                      of the last pass;
- *  stk_learn_enable    include (1) or drop (0) the correction in every cycle;
- *  stk_learn_stats     cycles whose correction was accepted / rejected;
+ *                      from zero, storing r = b - A x and e = x* - x after each;
+ *  stk_learn_objective 0 (default): Adam minimises ||r - A delta(r)||^2 / ||r||^2;
+ *                      1: the supervised error target, the mean over elements
+ *                      of ||delta_i / ||r_i|| - e_i / ||r_i||||^2 (MSE of the
+ *                      per-element normalised error);
+ *  stk_learn_train     Adam on the chosen objective over the stored states in
+ *                      random order (`epochs` passes; `batch` is unused, one
+ *                      state per step); *loss_out = mean loss of the last pass;
+ *  stk_learn_enable    apply (1) or drop (0) the correction in stk_solve;
+ *  stk_learn_stats     outer iterations whose correction was kept / undone
+ *                      since stk_learn_enable;
+ *  stk_learn_history   per outer iteration of the last stk_solve: decision[k]
+ *                      = -1 plain cycle (kappa measurement, or switched off),
+ *                      1 kept, 0 undone, and ratio[k] = ||r_new|| /
+ *                      (kappa ||r_old||) of the judged iterations (0 for
+ *                      plain ones); *count = iterations (at most max entries
+ *                      are written); *kappa_out = kappa;
  *  stk_learn_weights   copy the weights to (direction 0) or from (1) a host array.
  */
 int stk_learn_setup(stk_ctx* ctx, int hidden, uint64_t seed);
@@ -439,6 +460,8 @@ int stk_learn_train(stk_ctx* ctx, int epochs, int batch, double lr, uint64_t see
 int stk_learn_enable(stk_ctx* ctx, int on);
 int stk_learn_stats(stk_ctx* ctx, int64_t* accepted, int64_t* rejected);
 int stk_learn_weights(stk_ctx* ctx, float* host, int64_t count, int direction);
+int stk_learn_objective(stk_ctx* ctx, int objective);
+int stk_learn_history(stk_ctx* ctx, int* decision, double* ratio, int max, int* count, double* kappa_out);
 /* Sizes: input width (2d+1) nb, hidden width, output nb, number of weights
  * (W1 [in][hidden], b1, W2 [hidden][nb], b2, packed in that order), number
  * of stored residual states. */
@@ -446,10 +469,12 @@ int stk_learn_sizes(stk_ctx* ctx, int* in, int* hidden, int* out, int64_t* npara
 /* Features of a finest-level FP32 residual r_dev [element][nb] and the MLP
  * output y_dev [element][nb] (before the ||r_i|| scaling), nrm_dev [element]. */
 int stk_learn_infer(stk_ctx* ctx, const float* r_dev, float* y_dev, float* nrm_dev);
-/* A stored residual state (host copy), and the training loss and its
- * gradient (host, packed like the weights) on that state, without updating
- * the weights. */
+/* Host copies of a stored residual state r (stk_learn_state) and of the error
+ * e = x* - x stored with it (stk_learn_error_state), and the training loss of
+ * the current objective and its gradient (host, packed like the weights) on
+ * that state, without updating the weights. */
 int stk_learn_state(stk_ctx* ctx, int64_t state, float* r);
+int stk_learn_error_state(stk_ctx* ctx, int64_t state, float* e);
 int stk_learn_grad(stk_ctx* ctx, int64_t state, float* grad, double* loss_out);
 
 /*

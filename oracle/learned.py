@@ -1,11 +1,20 @@
 """Learned element-local post-smoother: the plain definition of its features,
-two-layer perceptron, mean-squared-error loss and gradient (oracle).
+two-layer perceptron, mean-squared-error loss and gradient, and the outer
+iteration that judges the correction (oracle).
 
 Not a step of the paper: the correction is an addition on top of the V-cycle.
 Features of element i: [r_i, r_{i-e_0}, r_{i+e_0}, ..., r_{i+e_{d-1}}] / ||r_i||
 (zeros where the neighbour is outside a non-periodic box); the network is
 y = tanh(F W1 + b1) W2 + b2; the loss over a set of rows is
 sum_rows ||y - t||^2 / rows.
+
+Acceptance (the reading of "kept only in cycles where its measured residual
+contraction beats plain block Gauss-Seidel"): the outer iteration is
+x <- x + V(0, b - A x); its first two iterations use the plain cycle and
+measure kappa = (||r_2|| / ||r_0||)^(1/2); every later iteration adds the
+correction delta computed from the cycle's own residual after post-smoothing
+and keeps it only if ||r_new|| < kappa ||r_old||, else returns to the plain
+cycle's result; two consecutive rejections switch the correction off.
 """
 import numpy as np
 
@@ -91,3 +100,60 @@ def residual_loss_and_grad(A, r, nbrs, w, nin, hid, nout):
     gW1 = F[:, :nin].T @ dZ
     gb1 = dZ.sum(axis=0)
     return loss, np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2])
+
+
+def correction(mg, c, r, w, nin, hid, nout, nbrs):
+    """delta = ||r_c,i|| y_i with y the network on the features of the
+    cycle's own residual r_c = r - A c after its post-smoothing (from the
+    smoother's stored blocks, as the cycle forms its residuals)."""
+    ne = mg.levels[0].ne
+    rc = mg.cycle_residual(0, c, r).reshape(ne, -1)
+    F, nrm = features(rc, nbrs)
+    y, _ = forward(F, w, nin, hid, nout)
+    return (nrm[:, None] * y).ravel()
+
+
+def solve_with_correction(mg, b, w, nin, hid, nout, nbrs, rtol=1e-10, maxit=100):
+    """Outer iteration x <- x + V(0, b - A x) from x = 0 with the learned
+    correction judged by the acceptance rule above.  Returns (x, relative
+    residual history, decisions, ratios, kappa): decision -1 for a plain
+    iteration, 1 kept, 0 undone; ratio = ||r_new|| / (kappa ||r_old||) for the
+    judged iterations (0 otherwise)."""
+    A = mg.A
+    x = np.zeros_like(b)
+    bn = np.linalg.norm(b)
+    bn = bn if bn > 0 else 1.0
+    r = b - A @ x
+    rel0 = rel = np.linalg.norm(r) / bn
+    hist, dec, ratios = [rel], [], []
+    kappa, active, consecutive, it = None, True, 0, 0
+    while rel > rtol and it < maxit:
+        c = mg.precondition(r)
+        if active and it >= 2:
+            delta = correction(mg, c, r, w, nin, hid, nout, nbrs)
+            x_new = x + c + delta
+            r_new = b - A @ x_new
+            ratio = (np.linalg.norm(r_new) / bn) / (kappa * rel)
+            ratios.append(ratio)
+            if ratio < 1.0:
+                x, r = x_new, r_new
+                dec.append(1)
+                consecutive = 0
+            else:
+                x = x + c
+                r = b - A @ x
+                dec.append(0)
+                consecutive += 1
+                if consecutive >= 2:
+                    active = False
+        else:
+            x = x + c
+            r = b - A @ x
+            dec.append(-1)
+            ratios.append(0.0)
+        rel = np.linalg.norm(r) / bn
+        it += 1
+        hist.append(rel)
+        if it == 2:
+            kappa = np.sqrt(rel / rel0)
+    return x, hist, dec, ratios, kappa

@@ -127,6 +127,10 @@ void free_device(Ctx& c) {
   if (c.graph) cudaGraphExecDestroy(c.graph);
   c.graph = nullptr;
   c.graph_x = c.graph_b = nullptr;
+  if (c.lgraph) cudaGraphExecDestroy(c.lgraph);
+  if (c.rgraph) cudaGraphExecDestroy(c.rgraph);
+  c.lgraph = c.rgraph = nullptr;
+  c.lgraph_x = c.lgraph_b = nullptr;
   c.dev.clear();
   c.ready = false;
 }
@@ -455,21 +459,19 @@ void setup_bottom(Ctx& c) {
 }
 
 // ---- learned post-smoother on the finest level -------------------------------------
-void enqueue_learned(Ctx& c, int prec, void* xv, const void* bv, cudaStream_t st) {
+// delta (into c.lxt) from the cycle's own residual after its post-smoothing:
+// r_c = b_c - A x_c with the cycle's records (FP32 vectors), features of r_c,
+// the two layers, delta_i = ||r_c,i|| y_i.
+void enqueue_learned_delta(Ctx& c, int prec, const void* xv, const void* bv, cudaStream_t st) {
   DevLevel& D0 = c.dev[0];
   const int ne = D0.ne, nb = c.nb, nface = 2 * c.d;
-  float* x = (float*)xv;
-  ck(run_element(c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bv, xv, D0.vr[1], st), "learned residual");
+  ck(run_element(c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bv, (void*)xv, D0.vr[1], st), "learned residual");
   ck(launch_features(ne, nb, nface, c.pat.NO, c.l_ldf, c.l_nbr, (const float*)D0.vr[1], c.lF, c.lnrm, st), "features");
   ck(launch_sgemm(ne, c.l_hid, c.l_in, 0, 0, c.lF, c.l_ldf, c.lW1, c.l_hid, c.lH, c.l_hid, c.lb1, 1, 1.f, 0.f, st),
      "layer 1");
   ck(launch_sgemm(ne, nb, c.l_hid, 0, 0, c.lH, c.l_hid, c.lW2, nb, c.lY, nb, c.lb2, 0, 1.f, 0.f, st), "layer 2");
-  ck(launch_apply_correction(ne, nb, nb, x, c.lnrm, c.lY, c.lxt, st), "correction");
-  ck(run_element(c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bv, c.lxt, c.lrt, st), "learned residual");
-  ck(launch_sumsq_f((int64_t)ne * nb, (const float*)D0.vr[1], c.lsums + 16, c.lsums, st), "norm");
-  ck(launch_sumsq_f((int64_t)ne * nb, c.lrt, c.lsums + 16, c.lsums + 1, st), "norm");
-  ck(launch_accept((int64_t)ne * nb, c.lsums, c.lxt, x, c.lcount, st), "accept");
-  c.launches += 12;
+  ck(launch_apply_correction(ne, nb, nb, c.l_zero, c.lnrm, c.lY, c.lxt, st), "delta");
+  c.launches += 5;
 }
 
 // ---- the V-cycle (Algorithm 1) ------------------------------------------------
@@ -520,7 +522,6 @@ void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t
      "prolong launch");
   c.launches++;
   enqueue_smooth(c, prec, l, level_sweeps(c, c.nu2, l), x, b, st);
-  if (l == 0 && c.learn_on && prec != STK_FP64 && c.lW1) enqueue_learned(c, prec, x, b, st);
 }
 
 void enqueue_residual64(Ctx& c, const double* x, const double* b, double* r, cudaStream_t st) {
@@ -556,6 +557,59 @@ void enqueue_iteration(Ctx& c, double* x, const double* b, cudaStream_t st) {
   c.launches++;
   enqueue_residual64(c, x, b, c.r64, st);
   enqueue_norm(c, c.r64, st);
+}
+
+// One outer iteration with the learned correction (low-precision cycle):
+// c = V(0, r), delta from the cycle's residual, x += c + delta, r64 = b - A x,
+// ||r64||^2 -> host.  The host then keeps or undoes delta (enqueue_undo).
+void enqueue_learned_iteration(Ctx& c, double* x, const double* b, cudaStream_t st) {
+  const int prec = c.precision;
+  const int64_t n0 = level_ne(c, 0) * c.nb;
+  DevLevel& D0 = c.dev[0];
+  ck(launch_convert(0, 1, n0, D0.vb[1], c.r64, st), "convert");
+  ck(cudaMemsetAsync(D0.vx[1], 0, n0 * 4, st), "memset");
+  enqueue_cycle(c, prec, 0, D0.vx[1], D0.vb[1], st);
+  enqueue_learned_delta(c, prec, D0.vx[1], D0.vb[1], st);
+  ck(launch_axpy(1, 0, n0, x, D0.vx[1], st), "axpy");
+  ck(launch_axpy(1, 0, n0, x, c.lxt, st), "axpy delta");
+  c.launches += 3;
+  enqueue_residual64(c, x, b, c.r64, st);
+  enqueue_norm(c, c.r64, st);
+}
+
+// Undo the correction of the last learned iteration: x -= delta (leaving the
+// plain cycle's result x + c), r64 = b - A x, ||r64||^2 -> host.
+void enqueue_undo(Ctx& c, double* x, const double* b, cudaStream_t st) {
+  const int64_t n0 = level_ne(c, 0) * c.nb;
+  ck(launch_scale_f(n0, -1.f, c.lxt, c.lrt, st), "negate delta");
+  ck(launch_axpy(1, 0, n0, x, c.lrt, st), "axpy -delta");
+  c.launches += 2;
+  enqueue_residual64(c, x, b, c.r64, st);
+  enqueue_norm(c, c.r64, st);
+}
+
+// Capture what `enqueue` puts on st as an instantiated CUDA graph; the
+// kernels it enqueued are counted into *kernels instead of c.launches.
+template <typename F>
+cudaGraphExec_t capture_graph(Ctx& c, cudaStream_t st, F&& enqueue, int64_t* kernels) {
+  cudaGraph_t g;
+  cudaGraphExec_t exec = nullptr;
+  const int64_t before = c.launches;
+  ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    enqueue();
+  } catch (...) {
+    cudaStreamEndCapture(st, &g);
+    c.launches = before;
+    throw;
+  }
+  ck(cudaStreamEndCapture(st, &g), "end capture");
+  cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  *kernels = c.launches - before;
+  c.launches = before;
+  ck(e, "graph instantiate");
+  return exec;
 }
 
 bool valid_bc(const int* bc, int d) {
@@ -1342,6 +1396,10 @@ static void invalidate_graphs(Ctx& c) {
   if (c.mgraph) cudaGraphExecDestroy(c.mgraph);
   c.mgraph = nullptr;
   c.mgraph_key[0] = -1;
+  if (c.lgraph) cudaGraphExecDestroy(c.lgraph);
+  if (c.rgraph) cudaGraphExecDestroy(c.rgraph);
+  c.lgraph = c.rgraph = nullptr;
+  c.lgraph_x = c.lgraph_b = nullptr;
 }
 
 int stk_set_cycle(stk_ctx* c, int nu1, int nu2, int precision) {
@@ -1636,6 +1694,10 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
     double rel = std::sqrt(c->norm_host[0]) / bnorm, rel0 = rel;
     if (hist) hist[0] = rel;
     int it = 0;
+    const bool learned = c->learn_on && c->lW1 && c->precision != STK_FP64;
+    if (learned && c->solver != 0)
+      return fail(c, STK_ERR_INVALID_ARG,
+                  "the learned correction is judged on the outer residual of every cycle: use outer method 0");
     if (c->solver >= 1) {
       try {
         it = fgmres(*c, x, b, rtol, maxit, hist, bnorm, rel, st);
@@ -1669,14 +1731,59 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
       c->graph_b = b;
       c->graph_prec = c->precision;
     }
-    while (rel > rtol && it < maxit) {
-      ck(cudaGraphLaunch(c->graph, st), "graph launch");
-      c->launches += c->graph_kernels;
+    if (learned && (!c->lgraph || c->lgraph_x != x || c->lgraph_b != b)) {
+      if (c->lgraph) cudaGraphExecDestroy(c->lgraph);
+      if (c->rgraph) cudaGraphExecDestroy(c->rgraph);
+      c->lgraph = c->rgraph = nullptr;
+      c->lgraph = capture_graph(*c, st, [&]() { enqueue_learned_iteration(*c, x, b, st); }, &c->lgraph_kernels);
+      c->rgraph = capture_graph(*c, st, [&]() { enqueue_undo(*c, x, b, st); }, &c->rgraph_kernels);
+      c->lgraph_x = x;
+      c->lgraph_b = b;
+    }
+    // Learned correction: kappa from the first two (plain) iterations, then
+    // each correction kept only if ||r_new|| < kappa ||r_old||; two
+    // consecutive rejections switch it off for the rest of the solve.
+    c->l_hist.clear();
+    c->l_ratio.clear();
+    c->l_kappa = 0.0;
+    bool active = learned;
+    int consecutive = 0;
+    auto run = [&](cudaGraphExec_t g, int64_t kernels) -> int {
+      ck(cudaGraphLaunch(g, st), "graph launch");
+      c->launches += kernels;
       ck(cudaStreamSynchronize(st), "sync");
       if (reinterpret_cast<int*>(c->norm_host + 1)[0] != 0)
         return fail(c, STK_ERR_TIMEOUT, "a kernel's bounded wait for its records expired");
+      return STK_OK;
+    };
+    while (rel > rtol && it < maxit) {
+      const double rel_old = rel;
+      if (active && it >= 2) {
+        int rc2 = run(c->lgraph, c->lgraph_kernels);
+        if (rc2 != STK_OK) return rc2;
+        const double rel_new = std::sqrt(c->norm_host[0]) / bnorm;
+        const double ratio = rel_new / (c->l_kappa * rel_old);
+        c->l_ratio.push_back(ratio);
+        if (ratio < 1.0) {
+          c->l_hist.push_back(1);
+          c->l_acc++;
+          consecutive = 0;
+        } else {
+          rc2 = run(c->rgraph, c->rgraph_kernels);
+          if (rc2 != STK_OK) return rc2;
+          c->l_hist.push_back(0);
+          c->l_rej++;
+          if (++consecutive >= 2) active = false;
+        }
+      } else {
+        int rc2 = run(c->graph, c->graph_kernels);
+        if (rc2 != STK_OK) return rc2;
+        c->l_hist.push_back(-1);
+        c->l_ratio.push_back(0.0);
+      }
       rel = std::sqrt(c->norm_host[0]) / bnorm;
       ++it;
+      if (it == 2) c->l_kappa = std::sqrt(rel / rel0);
       if (hist) hist[it] = rel;
       if (!std::isfinite(rel) || rel > 1e6 * rel0) {
         if (iters_out) *iters_out = it;
@@ -2104,12 +2211,12 @@ int stk_learn_setup(stk_ctx* c, int hidden, uint64_t seed) {
     c->lxt = (float*)dalloc(*c, (size_t)ne * nb * 4);
     c->lrt = (float*)dalloc(*c, (size_t)ne * nb * 4);
     c->lsums = (double*)dalloc(*c, 1024 * 8);
-    c->lcount = (int*)dalloc(*c, 16);
-    ck(cudaMemset(c->lcount, 0, 16), "memset");
+    c->lTg = (float*)dalloc(*c, (size_t)ne * nb * 4);
+    c->l_acc = c->l_rej = 0;
     c->lF2 = (float*)dalloc(*c, (size_t)ne * hidden * 4);
     c->l_zero = (float*)dalloc(*c, (size_t)ne * nb * 4);
     ck(cudaMemset(c->l_zero, 0, (size_t)ne * nb * 4), "memset");
-    c->lTX = c->lTT = nullptr;
+    c->lTX = c->lTT = c->lTE = nullptr;
     c->l_rows = c->l_cap = 0;
     invalidate_graphs(*c);
     return STK_OK;
@@ -2127,6 +2234,7 @@ int stk_learn_generate(stk_ctx* c, int nseeds, int cycles, uint64_t seed) {
     int64_t need = (int64_t)nseeds * cycles;
     if (need > c->l_cap) {
       c->lTX = (float*)dalloc(*c, (size_t)need * nvec * 4);
+      c->lTE = (float*)dalloc(*c, (size_t)need * nvec * 4);
       c->l_cap = need;
     }
     c->l_rows = 0;
@@ -2150,6 +2258,11 @@ int stk_learn_generate(stk_ctx* c, int nseeds, int cycles, uint64_t seed) {
         // the residual the correction would see after this cycle's post-smoothing
         ck(run_element(*c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bb, x, c->lTX + (size_t)c->l_rows * nvec, st),
            "residual");
+        // and the error e = x* - x the cycle left (the supervised target)
+        float* e = c->lTE + (size_t)c->l_rows * nvec;
+        ck(launch_scale_f(nvec, -1.f, x, e, st), "error");
+        ck(launch_axpy(0, 0, nvec, e, xs, st), "error");
+        c->launches += 3;
         c->l_rows += 1;
       }
     }
@@ -2194,6 +2307,40 @@ void enqueue_residual_loss_grad(Ctx& c, const float* r, double* sums, cudaStream
   c.launches += 18;
 }
 
+// Supervised objective on one stored state: features of r, y = MLP, target
+// t_i = e_i / ||r_i||, loss = sum_i ||y_i - t_i||^2 / ne (into sums[1]; sums[0]
+// = 1), and its gradient (packed like the weights) in c.lgrad.
+void enqueue_supervised_loss_grad(Ctx& c, const float* r, const float* e, double* sums, cudaStream_t st) {
+  DevLevel& D0 = c.dev[0];
+  const int ne = D0.ne, nb = c.nb, H = c.l_hid, IN = c.l_in, ldf = c.l_ldf;
+  const int64_t nvec = (int64_t)ne * nb;
+  float* gW1 = c.lgrad;
+  float* gb1 = gW1 + (int64_t)IN * H;
+  float* gW2 = gb1 + H;
+  float* gb2 = gW2 + (int64_t)H * nb;
+  ck(launch_features(ne, nb, 2 * c.d, c.pat.NO, ldf, c.l_nbr, r, c.lF, c.lnrm, st), "features");
+  ck(launch_sgemm(ne, H, IN, 0, 0, c.lF, ldf, c.lW1, H, c.lH, H, c.lb1, 1, 1.f, 0.f, st), "fwd1");
+  ck(launch_sgemm(ne, nb, H, 0, 0, c.lH, H, c.lW2, nb, c.lY, nb, c.lb2, 0, 1.f, 0.f, st), "fwd2");
+  ck(launch_target(ne, nb, nb, e, c.l_zero, c.lnrm, c.lTg, st), "targets");
+  ck(launch_mse_grad(nvec, 1.f / (float)ne, c.lY, c.lTg, c.lY, sums + 16, sums + 1, st), "mse");   // lY = dY
+  ck(launch_fill1(sums, st), "one");
+  ck(launch_sgemm(H, nb, ne, 1, 0, c.lH, H, c.lY, nb, gW2, nb, nullptr, 0, 1.f, 0.f, st), "gW2");
+  ck(launch_colsum(ne, nb, c.lY, nb, gb2, 1.f, st), "gb2");
+  ck(launch_sgemm(ne, H, nb, 0, 1, c.lY, nb, c.lW2, nb, c.lF2, H, nullptr, 0, 1.f, 0.f, st), "dH");
+  ck(launch_tanh_back((int64_t)ne * H, c.lH, c.lF2, st), "tanh'");
+  ck(launch_sgemm(IN, H, ne, 1, 0, c.lF, ldf, c.lF2, H, gW1, H, nullptr, 0, 1.f, 0.f, st), "gW1");
+  ck(launch_colsum(ne, H, c.lF2, H, gb1, 1.f, st), "gb1");
+  c.launches += 13;
+}
+
+void enqueue_loss_grad(Ctx& c, int64_t state, cudaStream_t st) {
+  const int64_t nvec = (int64_t)c.dev[0].ne * c.nb;
+  if (c.l_objective == 1)
+    enqueue_supervised_loss_grad(c, c.lTX + (size_t)state * nvec, c.lTE + (size_t)state * nvec, c.lsums, st);
+  else
+    enqueue_residual_loss_grad(c, c.lTX + (size_t)state * nvec, c.lsums, st);
+}
+
 int stk_learn_train(stk_ctx* c, int epochs, int batch, double lr, uint64_t seed, double* loss_out) {
   return guard(c, [&]() -> int {
     if (!c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
@@ -2211,7 +2358,7 @@ int stk_learn_train(stk_ctx* c, int epochs, int batch, double lr, uint64_t seed,
       for (int64_t k = 0; k < c->l_rows; ++k) {
         z = z * 6364136223846793005ULL + 1442695040888963407ULL;
         const int64_t state = (int64_t)((z >> 33) % (uint64_t)c->l_rows);
-        enqueue_residual_loss_grad(*c, c->lTX + (size_t)state * nvec, c->lsums, st);
+        enqueue_loss_grad(*c, state, st);
         c->l_adam_t++;
         const float b1 = 0.9f, b2 = 0.999f;
         const float c1 = 1.f - std::pow(b1, (float)c->l_adam_t), c2 = 1.f - std::pow(b2, (float)c->l_adam_t);
@@ -2255,12 +2402,41 @@ int stk_learn_state(stk_ctx* c, int64_t state, float* r) {
   });
 }
 
+int stk_learn_error_state(stk_ctx* c, int64_t state, float* e) {
+  return guard(c, [&]() -> int {
+    if (!c->lTE || state < 0 || state >= c->l_rows || !e) return fail(c, STK_ERR_INVALID_ARG, "bad state index");
+    const int64_t nvec = (int64_t)c->dev[0].ne * c->nb;
+    ck(cudaMemcpy(e, c->lTE + (size_t)state * nvec, (size_t)nvec * 4, cudaMemcpyDeviceToHost), "copy");
+    return STK_OK;
+  });
+}
+
+int stk_learn_objective(stk_ctx* c, int objective) {
+  return guard(c, [&]() -> int {
+    if (objective != 0 && objective != 1) return fail(c, STK_ERR_INVALID_ARG, "objective must be 0 or 1");
+    c->l_objective = objective;
+    return STK_OK;
+  });
+}
+
+int stk_learn_history(stk_ctx* c, int* decision, double* ratio, int max, int* count, double* kappa_out) {
+  return guard(c, [&]() -> int {
+    const int n = (int)c->l_hist.size();
+    for (int k = 0; k < n && k < max; ++k) {
+      if (decision) decision[k] = c->l_hist[k];
+      if (ratio) ratio[k] = c->l_ratio[k];
+    }
+    if (count) *count = n;
+    if (kappa_out) *kappa_out = c->l_kappa;
+    return STK_OK;
+  });
+}
+
 int stk_learn_grad(stk_ctx* c, int64_t state, float* grad, double* loss_out) {
   return guard(c, [&]() -> int {
     if (!c->lTX || state < 0 || state >= c->l_rows || !grad) return fail(c, STK_ERR_INVALID_ARG, "bad state index");
     cudaStream_t st = c->stream;
-    const int64_t nvec = (int64_t)c->dev[0].ne * c->nb;
-    enqueue_residual_loss_grad(*c, c->lTX + (size_t)state * nvec, c->lsums, st);
+    enqueue_loss_grad(*c, state, st);
     double h[2];
     ck(cudaMemcpyAsync(h, c->lsums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
     ck(cudaMemcpyAsync(grad, c->lgrad, c->l_nparam * 4, cudaMemcpyDeviceToHost, st), "copy");
@@ -2275,7 +2451,7 @@ int stk_learn_enable(stk_ctx* c, int on) {
     if (on && !c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
     c->learn_on = on ? 1 : 0;
     invalidate_graphs(*c);
-    if (c->lcount) ck(cudaMemset(c->lcount, 0, 16), "memset");
+    c->l_acc = c->l_rej = 0;
     return STK_OK;
   });
 }
@@ -2294,13 +2470,8 @@ int stk_learn_sizes(stk_ctx* c, int* in, int* hidden, int* out, int64_t* nparam,
 
 int stk_learn_stats(stk_ctx* c, int64_t* accepted, int64_t* rejected) {
   return guard(c, [&]() -> int {
-    int h[2] = {0, 0};
-    if (c->lcount) {
-      ck(cudaDeviceSynchronize(), "sync");
-      ck(cudaMemcpy(h, c->lcount, 2 * sizeof(int), cudaMemcpyDeviceToHost), "copy counters");
-    }
-    if (accepted) *accepted = h[0];
-    if (rejected) *rejected = h[1];
+    if (accepted) *accepted = c->l_acc;
+    if (rejected) *rejected = c->l_rej;
     return STK_OK;
   });
 }

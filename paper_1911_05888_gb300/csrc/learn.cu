@@ -4,9 +4,9 @@
 // Not part of the paper's method: after the post-smoothing sweeps of the
 // finest level, each element's residual and the residuals of its 2d face
 // neighbours (scaled by 1/||r_i||) are mapped by a small MLP to a correction
-// of x_i (scaled back by ||r_i||).  The corrected iterate is kept only when
-// its residual norm is below that of the plain block Gauss-Seidel iterate, so
-// the correction can never make a cycle worse.
+// of x_i (scaled back by ||r_i||).  Whether a correction is kept is decided
+// by the outer iteration in api.cu (its residual contraction against the plain
+// cycles' measured contraction).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -109,15 +109,16 @@ __global__ void colsum_kernel(int M, int N, const float* __restrict__ A, int lda
   out[n] = alpha * s;
 }
 
-// dY = 2 (Y - T) / rows ; loss partial sums per block
-__global__ void mse_grad_kernel(int64_t n, float scale, const float* __restrict__ Y, const float* __restrict__ T,
-                                float* __restrict__ dY, float* __restrict__ loss_part) {
-  __shared__ float sh[256];
-  float acc = 0.f;
+// dY = 2 scale (Y - T) (scale = 1 / rows); per-block partial sums of
+// (Y - T)^2 in FP64 (dY may alias Y: each entry is read before it is written)
+__global__ void mse_grad_kernel(int64_t n, float scale, const float* Y, const float* __restrict__ T, float* dY,
+                                double* __restrict__ loss_part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float d = Y[i] - T[i];
     dY[i] = 2.f * scale * d;
-    acc += d * d;
+    acc += (double)d * (double)d;
   }
   sh[threadIdx.x] = acc;
   __syncthreads();
@@ -155,16 +156,6 @@ __global__ void apply_correction_kernel(int ne, int nb, int ldy, const float* __
   if (i >= (int64_t)ne * nb) return;
   const int e = (int)(i / nb), k = (int)(i - (int64_t)e * nb);
   xt[i] = x[i] + nrm[e] * Y[(size_t)e * ldy + k];
-}
-
-// Accept: x = x_t when ||r_t||^2 < ||r||^2 (both sums in sums[0], sums[1]).
-__global__ void accept_kernel(int64_t n, const double* __restrict__ sums, const float* __restrict__ xt,
-                              float* __restrict__ x, int* __restrict__ counters) {
-  const bool take = sums[1] < sums[0];
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&counters[take ? 0 : 1], 1);
-  if (!take) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = xt[i];
 }
 
 // sum of squares of a float vector into out[0] (double), deterministic two-pass
@@ -284,9 +275,15 @@ cudaError_t launch_colsum(int M, int N, const float* A, int lda, float* out, flo
   return cudaGetLastError();
 }
 
-cudaError_t launch_mse_grad(int64_t n, float scale, const float* Y, const float* T, float* dY, float* part,
-                            cudaStream_t st) {
+__global__ void fill1_kernel(double* v) { v[0] = 1.0; }
+cudaError_t launch_fill1(double* v, cudaStream_t st) {
+  fill1_kernel<<<1, 1, 0, st>>>(v);
+  return cudaGetLastError();
+}
+cudaError_t launch_mse_grad(int64_t n, float scale, const float* Y, const float* T, float* dY, double* part,
+                            double* out, cudaStream_t st) {
   mse_grad_kernel<<<256, 256, 0, st>>>(n, scale, Y, T, dY, part);
+  sum_partials_kernel<<<1, 256, 0, st>>>(256, part, out);
   return cudaGetLastError();
 }
 
@@ -308,10 +305,6 @@ cudaError_t launch_apply_correction(int ne, int nb, int ldy, const float* x, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_accept(int64_t n, const double* sums, const float* xt, float* x, int* counters, cudaStream_t st) {
-  accept_kernel<<<1024, 256, 0, st>>>(n, sums, xt, x, counters);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_sumsq_f(int64_t n, const float* x, double* part, double* out, cudaStream_t st) {
   sumsq_f_partial_kernel<<<512, 256, 0, st>>>(n, x, part);

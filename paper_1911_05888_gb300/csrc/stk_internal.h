@@ -178,9 +178,21 @@ struct Ctx {
   int* l_nbr = nullptr;         // natural-order neighbour table of level 0
   float *lF = nullptr, *lH = nullptr, *lY = nullptr, *lnrm = nullptr, *lxt = nullptr, *lrt = nullptr;
   double* lsums = nullptr;      // [0] ||r||^2, [1] ||r_t||^2, then partials
-  int* lcount = nullptr;        // accepted, rejected
   float *lF2 = nullptr, *l_zero = nullptr;   // hidden-layer gradient, zero vector
   float *lTX = nullptr, *lTT = nullptr;   // training residual states [state][element][nb]
+  float* lTE = nullptr;         // training error states x* - x [state][element][nb] (supervised objective)
+  float* lTg = nullptr;         // MSE targets [element][nb]
+  int l_objective = 0;          // 0: ||r - A delta||^2 / ||r||^2, 1: MSE of delta / ||r_i|| against e / ||r_i||
+  // outer-iteration acceptance (kappa rule): decisions of the last solve, per
+  // outer iteration: -1 plain cycle, 1 correction kept, 0 correction undone
+  std::vector<int> l_hist;
+  std::vector<double> l_ratio;  // ||r_new|| / (kappa ||r_old||) of each judged iteration
+  double l_kappa = 0.0;         // plain contraction of the last solve's first two iterations
+  int64_t l_acc = 0, l_rej = 0; // totals since stk_learn_enable
+  cudaGraphExec_t lgraph = nullptr, rgraph = nullptr;   // learned iteration, undo
+  const void* lgraph_x = nullptr;
+  const void* lgraph_b = nullptr;
+  int64_t lgraph_kernels = 0, rgraph_kernels = 0;
   int64_t l_rows = 0, l_cap = 0;
   int l_adam_t = 0;
   cudaGraphExec_t mgraph = nullptr;
@@ -259,14 +271,14 @@ cudaError_t launch_features(int ne, int nb, int nface, int NO, int ldf, const in
 cudaError_t launch_sgemm(int M, int N, int K, int ta, int tb, const float* A, int lda, const float* B, int ldb,
                          float* C, int ldc, const float* bias, int act, float alpha, float beta, cudaStream_t st);
 cudaError_t launch_colsum(int M, int N, const float* A, int lda, float* out, float alpha, cudaStream_t st);
-cudaError_t launch_mse_grad(int64_t n, float scale, const float* Y, const float* T, float* dY, float* part,
-                            cudaStream_t st);
+cudaError_t launch_fill1(double* v, cudaStream_t st);
+cudaError_t launch_mse_grad(int64_t n, float scale, const float* Y, const float* T, float* dY, double* part,
+                            double* out, cudaStream_t st);
 cudaError_t launch_tanh_back(int64_t n, const float* H, float* dH, cudaStream_t st);
 cudaError_t launch_adam(int64_t n, float lr, float b1, float b2, float c1, float c2, float eps, float* w,
                         const float* g, float* m, float* v, cudaStream_t st);
 cudaError_t launch_apply_correction(int ne, int nb, int ldy, const float* x, const float* nrm, const float* Y, float* xt,
                                     cudaStream_t st);
-cudaError_t launch_accept(int64_t n, const double* sums, const float* xt, float* x, int* counters, cudaStream_t st);
 cudaError_t launch_sumsq_f(int64_t n, const float* x, double* part, double* out, cudaStream_t st);
 cudaError_t launch_smooth_field(int ne, int nb, int s, int d, const int* n_dev, uint64_t seed, float* x,
                                 cudaStream_t st);

@@ -90,6 +90,9 @@ SIGNATURES = {
     "stk_get_info": [_vp, ctypes.c_int, _c_i64_p],
     "stk_set_colouring": [_vp, ctypes.c_int],
     "stk_fp64_fma_rate": [_vp, _c_dbl_p, _vp],
+    "stk_learn_objective": [_vp, ctypes.c_int],
+    "stk_learn_history": [_vp, _c_int_p, _c_dbl_p, ctypes.c_int, _c_int_p, _c_dbl_p],
+    "stk_learn_error_state": [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float)],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
 
@@ -421,6 +424,29 @@ class Context:
         self._check(self.lib.stk_learn_state(self.h, state, r.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
                     "stk_learn_state")
         return r
+
+    def learn_error_state(self, state, nvec):
+        e = np.zeros(nvec, dtype=np.float32)
+        self._check(self.lib.stk_learn_error_state(self.h, state, e.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+                    "stk_learn_error_state")
+        return e
+
+    def learn_objective(self, objective):
+        """0: residual objective ||r - A delta||^2 / ||r||^2; 1: supervised
+        MSE against the normalised error e_i / ||r_i||."""
+        self._check(self.lib.stk_learn_objective(self.h, objective), "stk_learn_objective")
+
+    def learn_history(self, max_iters=1000):
+        """(decisions, ratios, kappa) of the last solve: per outer iteration
+        -1 plain, 1 kept, 0 undone; ratio ||r_new|| / (kappa ||r_old||)."""
+        dec = np.zeros(max_iters, dtype=np.int32)
+        rat = np.zeros(max_iters)
+        n = ctypes.c_int()
+        kap = ctypes.c_double()
+        self._check(self.lib.stk_learn_history(self.h, dec.ctypes.data_as(_c_int_p), rat.ctypes.data_as(_c_dbl_p),
+                                               max_iters, ctypes.byref(n), ctypes.byref(kap)), "stk_learn_history")
+        m = min(n.value, max_iters)
+        return dec[:m], rat[:m], kap.value
 
     def learn_grad(self, state, nparam):
         g = np.zeros(nparam, dtype=np.float32)

@@ -526,21 +526,89 @@ def test_learned_training_gradient_matches_oracle_backprop():
 
 
 def test_learned_smoother_solve_converges_and_is_judged():
-    """Train on plain V-cycle pairs, enable, solve with FGMRES: reaches 1e-10;
-    every cycle's correction is accepted or rejected on the device."""
+    """Train on plain V-cycle pairs, enable, solve by iterative refinement:
+    reaches 1e-10; after the two plain iterations that measure kappa every
+    correction is kept or undone (or the correction is switched off after two
+    undone in a row); a Krylov outer method is refused while it is enabled."""
     prob, gpu = _learned_ctx()
     gpu.ctx.learn_generate(nseeds=4, cycles=3, seed=1)
     loss0 = gpu.ctx.learn_train(epochs=1, batch=0, lr=1e-3, seed=2)
     loss1 = gpu.ctx.learn_train(epochs=20, batch=0, lr=1e-3, seed=3)
     assert np.isfinite(loss1) and loss1 <= loss0
     gpu.ctx.learn_enable(True)
-    gpu.ctx.set_solver(native.FGMRES, 30)
     b = dev(gpu.rhs().ravel())
     x = torch.zeros_like(b)
     it, hist = gpu.ctx.solve(x, b, rtol=1e-10, maxit=100)
     assert hist[-1] <= 1e-10
+    dec, ratio, kappa = gpu.ctx.learn_history()
+    assert len(dec) == it and list(dec[:2]) == [-1, -1] and 0 < kappa < 1
     acc, rej = gpu.ctx.learn_stats()
-    assert acc + rej >= it
+    assert acc == int((dec == 1).sum()) and rej == int((dec == 0).sum())
+    judged = [k for k in range(it) if dec[k] >= 0]
+    assert all((ratio[k] < 1) == (dec[k] == 1) for k in judged)
+    gpu.ctx.set_solver(native.FGMRES, 30)
+    with pytest.raises(native.StkError):
+        gpu.ctx.solve(x.zero_(), b, rtol=1e-10, maxit=100)
+    gpu.close()
+
+
+def test_learned_acceptance_matches_oracle():
+    """The acceptance rule on the GPU (FP32 cycle and network) against the
+    oracle's (FP32-rounded blocks, FP64 arithmetic, the same weights): the
+    same kappa to 1e-5, the same decision in every judged iteration whose
+    margin |ratio - 1| exceeds 1e-3 (up to the first closer call, after which
+    the iterates may legitimately differ), and iteration counts within one."""
+    from oracle import learned, ldg as oldg
+    prob, gpu = _learned_ctx()
+    gpu.ctx.learn_generate(nseeds=4, cycles=3, seed=1)
+    gpu.ctx.learn_train(epochs=5, batch=0, lr=1e-3, seed=2)
+    nin, hid, nout, npar, _ = gpu.ctx.learn_sizes()
+    w = gpu.ctx.learn_weights(npar).astype(np.float64)
+    gpu.ctx.learn_enable(True)
+    b_host = gpu.rhs().ravel()
+    b = dev(b_host)
+    x = torch.zeros_like(b)
+    it, hist = gpu.ctx.solve(x, b, rtol=1e-10, maxit=100)
+    dec, ratio, kappa = gpu.ctx.learn_history()
+    orc = multigrid.Multigrid(prob, storage="fp32")
+    mesh = oldg.Mesh(prob.d, prob.n, prob.lo, prob.hi, prob.bc)
+    xo, ho, dec_o, ratio_o, kappa_o = learned.solve_with_correction(orc, b_host, w, nin, hid, nout,
+                                                                    learned.face_neighbours(mesh), rtol=1e-10,
+                                                                    maxit=100)
+    assert abs(kappa - kappa_o) <= 1e-5 * kappa_o
+    compared = 0
+    for k in range(min(len(dec), len(dec_o))):
+        if dec_o[k] >= 0 and abs(ratio_o[k] - 1.0) <= 1e-3:
+            break
+        assert dec[k] == dec_o[k], (k, list(dec), dec_o)
+        compared += 1
+    assert compared >= 3
+    assert abs(it - (len(ho) - 1)) <= 1 and hist[-1] <= 1e-10
+
+
+def test_learned_supervised_gradient_matches_oracle():
+    """The supervised objective (MSE of delta_i / ||r_i|| against the
+    normalised error e_i / ||r_i|| of the stored plain-cycle states): loss and
+    back-propagated gradient on a stored state equal the oracle's
+    loss_and_grad on the same residual, error and weights."""
+    from oracle import learned, ldg as oldg
+    prob, gpu = _learned_ctx()
+    gpu.ctx.learn_generate(nseeds=2, cycles=2, seed=11)
+    gpu.ctx.learn_objective(1)
+    nin, hid, nout, npar, states = gpu.ctx.learn_sizes()
+    r = gpu.ctx.learn_state(2, prob.n_dofs).astype(np.float64).reshape(prob.n_elements, prob.nb)
+    e = gpu.ctx.learn_error_state(2, prob.n_dofs).astype(np.float64).reshape(prob.n_elements, prob.nb)
+    assert np.all(np.isfinite(e)) and np.abs(e).max() > 0
+    loss, g = gpu.ctx.learn_grad(2, npar)
+    w = gpu.ctx.learn_weights(npar).astype(np.float64)
+    mesh = oldg.Mesh(prob.d, prob.n, prob.lo, prob.hi, prob.bc)
+    F, nrm = learned.features(r, learned.face_neighbours(mesh))
+    T = e / (nrm[:, None] + 1e-30)
+    loss_ref, g_ref = learned.loss_and_grad(F, T, w, nin, hid, nout)
+    assert abs(loss - loss_ref) <= 1e-4 * loss_ref
+    assert rel(g, g_ref) <= 1e-3
+    loss_tr = gpu.ctx.learn_train(epochs=3, batch=0, lr=1e-3, seed=5)
+    assert np.isfinite(loss_tr)
     gpu.close()
 
 

@@ -796,3 +796,61 @@ def test_order_3d(gamma):
     rate = np.log2(e4 / e8)
     assert np.all(np.abs(rate[:3] - 2.0) < 0.35), rate
     assert 1.4 < rate[3] < 2.4, rate
+
+
+def _learned_setup(n=8):
+    from oracle import learned
+    prob = P.stress_variable_mu_2d(n=n, p=2, nu=(3, 3))
+    mg = multigrid.Multigrid(prob)
+    mesh = mg.levels[0].mesh
+    nbrs = learned.face_neighbours(mesh)
+    nb = prob.nb
+    nin, hid = (1 + 2 * prob.d) * nb, 16
+    nparam = nin * hid + hid + hid * nb + nb
+    b = mg.levels[0].P @ ldg.rhs(prob, mg.levels[0].ops)
+    return learned, prob, mg, nbrs, nin, hid, nb, nparam, b
+
+
+def test_learned_solve_with_zero_correction_is_plain_refinement():
+    """With all weights zero the correction is zero: every judged iteration
+    then contracts exactly like the plain one, the iterates and the residual
+    history are those of plain iterative refinement, whatever is decided."""
+    learned, prob, mg, nbrs, nin, hid, nb, nparam, b = _learned_setup()
+    x, hist, dec, ratios, kappa = learned.solve_with_correction(mg, b, np.zeros(nparam), nin, hid, nb, nbrs,
+                                                                rtol=1e-10, maxit=60)
+    x_ref, hist_ref = mg.solve(b, rtol=1e-10, maxit=60)
+    assert len(hist) == len(hist_ref)
+    np.testing.assert_allclose(hist, hist_ref, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(x, x_ref, rtol=0, atol=1e-12 * np.abs(x_ref).max())
+    assert dec[:2] == [-1, -1] and abs(kappa - np.sqrt(hist[2] / hist[0])) <= 1e-15
+
+
+def test_learned_solve_rejects_harmful_correction_and_switches_off():
+    """A correction that destroys the iterate (huge random output weights) is
+    undone in the two judged iterations after the kappa measurement, then
+    switched off: decisions [-1, -1, 0, 0, -1, ...] and exactly the plain
+    refinement's residual history."""
+    learned, prob, mg, nbrs, nin, hid, nb, nparam, b = _learned_setup()
+    w = np.random.default_rng(4).standard_normal(nparam) * 100.0
+    x, hist, dec, ratios, kappa = learned.solve_with_correction(mg, b, w, nin, hid, nb, nbrs, rtol=1e-10, maxit=60)
+    x_ref, hist_ref = mg.solve(b, rtol=1e-10, maxit=60)
+    assert dec[:4] == [-1, -1, 0, 0] and all(v == -1 for v in dec[4:])
+    assert ratios[2] > 1 and ratios[3] > 1
+    np.testing.assert_allclose(hist, hist_ref, rtol=1e-9, atol=0)
+
+
+def test_learned_solve_keeps_an_exact_correction():
+    """A correction that is the exact remaining error would end the solve:
+    replacing the network by delta = A^+ r_c (a perfect post-smoother, used
+    here to check the bookkeeping) is kept at the first judged iteration and
+    the next residual is at rounding level."""
+    learned, prob, mg, nbrs, nin, hid, nb, nparam, b = _learned_setup()
+    A = mg.A.toarray()
+    orig = learned.correction
+    try:
+        learned.correction = lambda mg_, c, r, *a: np.linalg.lstsq(A, mg_.cycle_residual(0, c, r), rcond=None)[0]
+        x, hist, dec, ratios, kappa = learned.solve_with_correction(mg, b, np.zeros(nparam), nin, hid, nb, nbrs,
+                                                                    rtol=1e-10, maxit=60)
+    finally:
+        learned.correction = orig
+    assert dec == [-1, -1, 1] and hist[-1] <= 1e-10 and ratios[2] < 1e-3
