@@ -55,6 +55,10 @@ def parse():
                     help="post-smoothing sweeps of the timed cycle (default --nu; the plain FP64 comparison "
                          "keeps V(nu, nu))")
     ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="levels below level 0 with at most this many elements run as one persistent "
+                         "cooperative launch per cycle (0: one launch per step)")
+    ap.add_argument("--persistent-ctas", type=int, default=1, help="CTAs per SM of the persistent launch")
     ap.add_argument("--cycle-shape", default="1,1,64",
                     help="gamma,growth,max_sweeps: 1,1,64 = V-cycle, 2,1,64 = W-cycle, 1,2,N = variable V-cycle")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides solved together (1..8)")
@@ -102,7 +106,7 @@ def config(args, prob):
     return {"workload": "2d-viscous-stress-varmu-dirichlet3-stress1", "n": [args.n, args.n], "p": args.p,
             "dofs": prob.n_dofs, "nu": [args.nu, args.nu if args.nu2 is None else args.nu2], "rtol": 1e-10,
             "outer": "%s(%d)" % (args.solver, args.restart) if args.solver != "richardson" else "richardson",
-            "cycle_shape": shape_of(args),
+            "cycle_shape": shape_of(args), "persistent_coarse": [args.persistent, args.persistent_ctas],
             "cache": "inputs larger than L2 (element blocks >= 3.6 GB per solve)",
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -453,6 +457,8 @@ def run_native(args):
     mg64.ctx.set_cycle_shape(*shape_of(args))
     tuned, tuned_ms = mg.ctx.autotune()
     tuned64 = mg64.ctx.autotune()[0] if mg64 is not mg else tuned
+    mg.ctx.set_persistent(args.persistent, args.persistent_ctas)
+    mg64.ctx.set_persistent(args.persistent, args.persistent_ctas)
     method = {"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR, "richardson": native.RICHARDSON}[args.solver]
     mg.ctx.set_solver(method, args.restart)
     mg64.ctx.set_solver(native.FGMRES if method == native.FGMRES_IR else method, args.restart)

@@ -161,6 +161,32 @@ int stk_set_cycle_shape(stk_ctx* ctx, int gamma, int growth, int max_sweeps);
  * with phases always take the greedy colouring.  Takes effect at the next
  * stk_setup.  Errors: STK_ERR_INVALID_ARG for an unknown mode.
  */
+/*
+ * Persistent coarse cycle (not in the paper; Algorithm 1 unchanged): every
+ * level below level 0 with at most max_elements elements, from the first
+ * such level down to the bottom and back (its colour steps, residual,
+ * restriction with the coarse iterate zeroed, coarse visits of the cycle
+ * shape, bottom solve, prolongation), runs as ONE cooperative launch of
+ * ctas_per_sm CTAs per SM that walks a phase program built at setup, with a
+ * grid barrier between phases.  Each phase runs the same per-element code as
+ * the kernel it replaces, so iterates are unchanged bit for bit.  Every
+ * barrier wait is bounded (about a second of clock ticks); on expiry the
+ * launch sets the context's error word and returns, and the solve reports
+ * STK_ERR_TIMEOUT.  max_elements = 0 (the default) turns it off.  Errors:
+ * STK_ERR_INVALID_ARG unless max_elements >= 0 and 1 <= ctas_per_sm <= 8.
+ */
+int stk_set_persistent(stk_ctx* ctx, int max_elements, int ctas_per_sm);
+/*
+ * Self-test of the bounded grid barrier (a diagnostic, no solver state is
+ * touched): a cooperative launch of the persistent cycle's grid passes four
+ * barriers; with absent >= 0 that CTA returns at once and never arrives, so
+ * every other CTA must give up after limit_ticks clock ticks
+ * (1e3 <= limit_ticks <= 4e9).  *passed = barrier passages counted (CTAs x
+ * barriers passed).  Returns STK_OK when all barriers completed,
+ * STK_ERR_TIMEOUT when the bound expired; the context stays usable either way.
+ */
+int stk_barrier_selftest(stk_ctx* ctx, int absent, int64_t limit_ticks, int64_t* passed);
+
 #define STK_COLOURS_AUTO 0
 #define STK_COLOURS_PARITY 1
 #define STK_COLOURS_CHECKERBOARD 2

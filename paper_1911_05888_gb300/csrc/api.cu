@@ -58,6 +58,10 @@ cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, c
 
 namespace {
 
+void free_persist(Ctx& c);
+int persist_grid(const Ctx& c);
+void build_persist(Ctx& c);
+
 
 struct CudaFail {
   cudaError_t e;
@@ -104,6 +108,8 @@ void free_device(Ctx& c) {
   for (void* p : c.allocations) cudaFree(p);
   c.allocations.clear();
   c.device_bytes = 0;
+  free_persist(c);
+  c.gbar = nullptr;
   if (c.norm_host) cudaFreeHost(c.norm_host);
   c.norm_host = nullptr;
   if (c.khost) cudaFreeHost(c.khost);
@@ -300,7 +306,7 @@ void alloc_vectors(Ctx& c) {
   int64_t n0 = level_ne(c, 0) * c.nb;
   c.r64 = (double*)dalloc(c, n0 * 8);
   c.c64 = (double*)dalloc(c, n0 * 8);
-  c.norm_buf = (double*)dalloc(c, 1040 * 8);
+  c.norm_buf = (double*)dalloc(c, 1104 * 8);   // scalars, 1024 partials, probe slots
   ck(cudaMallocHost(&c.norm_host, 8 * sizeof(double)), "cudaMallocHost");
 }
 
@@ -504,6 +510,16 @@ void enqueue_smooth(Ctx& c, int prec, int l, int sweeps, void* x, const void* b,
 void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t st) {
   int vi = prec == STK_FP64 ? 0 : 1;
   int L = nlevels(c);
+  if (l >= 1 && l == c.persist_level[prec] && c.persist_prog[prec] && x == c.dev[l].vx[vi] &&
+      b == c.dev[l].vb[vi]) {
+    // levels l .. L-1 in one cooperative launch (persist.cu)
+    ck(cudaMemsetAsync(c.gbar, 0, sizeof(GridBarrierWords), st), "barrier reset");
+    ck(launch_coarse_cycle(c.pat, prec, c.persist_prog[prec], c.persist_nphase[prec], c.gbar, c.dev_err,
+                           c.barrier_limit, persist_grid(c), st),
+       "persistent coarse cycle");
+    c.launches++;
+    return;
+  }
   if (l == L - 1) {
     ck(launch_bottom(vi == 0, c.nbot, c.bottom_pinv, b, x, st), "bottom launch");
     c.launches++;
@@ -522,6 +538,127 @@ void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t
      "prolong launch");
   c.launches++;
   enqueue_smooth(c, prec, l, level_sweeps(c, c.nu2, l), x, b, st);
+}
+
+// ---- persistent coarse cycle: the phase program -------------------------------
+int persist_grid(const Ctx& c) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
+  return std::max(1, sms * c.persist_ctas);
+}
+
+// The phases enqueue_cycle would launch from level l down, in the same order.
+void emit_cycle_phases(Ctx& c, int prec, int l, std::vector<CyclePhase>& prog) {
+  const int vi = prec == STK_FP64 ? 0 : 1;
+  const int L = nlevels(c);
+  DevLevel& D = c.dev[l];
+  const bool scaled = prec == STK_FP16;
+  if (l == L - 1) {
+    CyclePhase ph{};
+    ph.op = PHASE_BOTTOM;
+    ph.n = c.nbot;
+    ph.tr = c.bottom_pinv;
+    ph.in = D.vb[vi];
+    ph.out = D.vx[vi];
+    prog.push_back(ph);
+    return;
+  }
+  DevLevel& Dc = c.dev[l + 1];
+  auto smooth = [&](int sweeps) {
+    for (int it = 0; it < sweeps; ++it)
+      for (int col = 0; col < D.ncolour; ++col) {
+        const int n = D.cstart[col + 1] - D.cstart[col];
+        if (n <= 0) continue;
+        CyclePhase ph{};
+        ph.op = PHASE_GS;
+        ph.pos0 = D.cstart[col];
+        ph.n = n;
+        ph.cpl = D.cpl[prec];
+        ph.mat = D.inv[prec];
+        ph.perm = D.perm;
+        ph.nbr = D.nbr;
+        ph.tsc = scaled ? D.csc : nullptr;
+        ph.rsc = scaled ? D.isc : nullptr;
+        ph.b = D.vb[vi];
+        ph.x = D.vx[vi];
+        prog.push_back(ph);
+      }
+  };
+  smooth(level_sweeps(c, c.nu1, l));
+  CyclePhase rs{};
+  rs.op = PHASE_RESID;
+  rs.n = D.ne;
+  rs.cpl = D.cpl[prec];
+  rs.mat = D.dia[prec];
+  rs.perm = D.perm;
+  rs.nbr = D.nbr;
+  rs.tsc = scaled ? D.csc : nullptr;
+  rs.rsc = scaled ? D.dsc : nullptr;
+  rs.b = D.vb[vi];
+  rs.x = D.vx[vi];
+  rs.r = D.vr[vi];
+  prog.push_back(rs);
+  CyclePhase rt{};
+  rt.op = PHASE_RESTRICT;
+  rt.n = Dc.ne;
+  rt.dims[0] = Dc.n[0];
+  rt.dims[1] = Dc.n[1];
+  rt.dims[2] = D.n[0];
+  rt.dims[3] = D.n[1];
+  rt.tr = c.child_P[vi];
+  rt.in = D.vr[vi];
+  rt.out = Dc.vb[vi];
+  rt.xz = Dc.vx[vi];
+  prog.push_back(rt);
+  for (int v = coarse_visits(c, l); v > 0; --v) emit_cycle_phases(c, prec, l + 1, prog);
+  CyclePhase pr{};
+  pr.op = PHASE_PROLONG;
+  pr.n = Dc.ne;
+  pr.dims[0] = D.n[0];
+  pr.dims[1] = D.n[1];
+  pr.dims[2] = Dc.n[0];
+  pr.dims[3] = Dc.n[1];
+  pr.tr = c.child_PT[vi];
+  pr.in = Dc.vx[vi];
+  pr.out = D.vx[vi];
+  prog.push_back(pr);
+  smooth(level_sweeps(c, c.nu2, l));
+}
+
+void free_persist(Ctx& c) {
+  for (int pr = 0; pr < 4; ++pr) {
+    if (c.persist_prog[pr]) cudaFree(c.persist_prog[pr]);
+    c.persist_prog[pr] = nullptr;
+    c.persist_nphase[pr] = 0;
+    c.persist_level[pr] = -1;
+  }
+}
+
+// (Re)build the programs of the storage precisions the context runs cycles in
+// (its cycle precision, and FP64), from the first level of at most
+// persist_max elements below level 0; none when persist_max is 0.
+void build_persist(Ctx& c) {
+  free_persist(c);
+  if (!c.ready || c.persist_max <= 0) return;
+  const int L = nlevels(c);
+  int l0 = -1;
+  for (int l = 1; l < L; ++l)
+    if (level_ne(c, l) <= c.persist_max) {
+      l0 = l;
+      break;
+    }
+  if (l0 < 0 || l0 >= L - 1) return;   // nothing to smooth below level 0 within the bound
+  for (int pr : {c.precision, (int)STK_FP64}) {
+    if (c.persist_prog[pr] || !c.dev[l0].cpl[pr] || !c.dev[l0].vx[pr == STK_FP64 ? 0 : 1]) continue;
+    std::vector<CyclePhase> prog;
+    emit_cycle_phases(c, pr, l0, prog);
+    CyclePhase* d = nullptr;
+    ck(cudaMalloc(&d, prog.size() * sizeof(CyclePhase)), "cudaMalloc program");
+    ck(cudaMemcpy(d, prog.data(), prog.size() * sizeof(CyclePhase), cudaMemcpyHostToDevice), "copy program");
+    c.persist_prog[pr] = d;
+    c.persist_nphase[pr] = (int)prog.size();
+    c.persist_level[pr] = l0;
+  }
 }
 
 void enqueue_residual64(Ctx& c, const double* x, const double* b, double* r, cudaStream_t st) {
@@ -1411,6 +1548,7 @@ int stk_set_cycle(stk_ctx* c, int nu1, int nu2, int precision) {
     c->nu2 = nu2;
     c->precision = precision;
     invalidate_graphs(*c);
+    build_persist(*c);
     return STK_OK;
   });
 }
@@ -1424,6 +1562,46 @@ int stk_set_colouring(stk_ctx* c, int mode) {
   });
 }
 
+int stk_set_persistent(stk_ctx* c, int max_elements, int ctas_per_sm) {
+  return guard(c, [&]() -> int {
+    if (max_elements < 0 || ctas_per_sm < 1 || ctas_per_sm > 8)
+      return fail(c, STK_ERR_INVALID_ARG, "bad persistent-cycle settings");
+    c->persist_max = max_elements;
+    c->persist_ctas = ctas_per_sm;
+    invalidate_graphs(*c);
+    build_persist(*c);
+    return STK_OK;
+  });
+}
+
+int stk_barrier_selftest(stk_ctx* c, int absent, int64_t limit_ticks, int64_t* passed) {
+  return guard(c, [&]() -> int {
+    if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (limit_ticks < 1000 || limit_ticks > 4000000000LL) return fail(c, STK_ERR_INVALID_ARG, "bad wait bound");
+    const int grid = persist_grid(*c);
+    if (absent >= grid) return fail(c, STK_ERR_INVALID_ARG, "no such CTA");
+    cudaStream_t st = c->stream;
+    unsigned int* cnt = reinterpret_cast<unsigned int*>(c->norm_buf + 1040);
+    ck(cudaMemsetAsync(c->gbar, 0, sizeof(GridBarrierWords), st), "memset");
+    ck(cudaMemsetAsync(c->dev_err, 0, sizeof(int), st), "memset");
+    ck(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st), "memset");
+    ck(launch_barrier_selftest(c->gbar, c->dev_err, (long long)limit_ticks, 4, absent, grid, cnt, st), "selftest");
+    c->launches++;
+    int err = 0;
+    unsigned int n = 0;
+    ck(cudaMemcpyAsync(&err, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaMemcpyAsync(&n, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaStreamSynchronize(st), "sync");
+    ck(cudaMemsetAsync(c->dev_err, 0, sizeof(int), st), "memset");
+    ck(cudaMemsetAsync(c->gbar, 0, sizeof(GridBarrierWords), st), "memset");
+    ck(cudaStreamSynchronize(st), "sync");
+    if (passed) *passed = n;
+    if (err == kErrBarrierTimeout) return fail(c, STK_ERR_TIMEOUT, "a grid-barrier wait reached its bound");
+    if (err != 0) return fail(c, STK_ERR_CUDA, "unexpected error word");
+    return STK_OK;
+  });
+}
+
 int stk_set_cycle_shape(stk_ctx* c, int gamma, int growth, int max_sweeps) {
   return guard(c, [&]() -> int {
     if (gamma < 1 || gamma > 3 || growth < 1 || growth > 4 || max_sweeps < 1 || max_sweeps > 256)
@@ -1432,6 +1610,7 @@ int stk_set_cycle_shape(stk_ctx* c, int gamma, int growth, int max_sweeps) {
     c->cyc_growth = growth;
     c->cyc_cap = max_sweeps;
     invalidate_graphs(*c);
+    build_persist(*c);
     return STK_OK;
   });
 }
@@ -1490,9 +1669,12 @@ int stk_setup(stk_ctx* c, void* stream) {
     ck(cudaMemcpy(c->child_PT[0], PT.data(), P.size() * 8, cudaMemcpyHostToDevice), "copy P");
     ck(cudaMemcpy(c->child_P[1], P32.data(), P.size() * 4, cudaMemcpyHostToDevice), "copy P");
     ck(cudaMemcpy(c->child_PT[1], PT32.data(), P.size() * 4, cudaMemcpyHostToDevice), "copy P");
+    c->gbar = (GridBarrierWords*)dalloc(*c, 64);
+    ck(cudaMemset(c->gbar, 0, 64), "memset");
     ck(cudaStreamSynchronize(st), "setup sync");
     ck(cudaDeviceSynchronize(), "setup sync");
     c->ready = true;
+    build_persist(*c);
     return STK_OK;
   });
 }
@@ -1683,6 +1865,7 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
     cudaStream_t user = (cudaStream_t)stream;
     ck(cudaStreamSynchronize(user), "sync caller stream");
     cudaStream_t st = c->stream;
+    ck(cudaMemsetAsync(c->dev_err, 0, sizeof(int), st), "clear error word");
     // ||b||
     enqueue_norm(*c, b, st);
     ck(cudaStreamSynchronize(st), "sync");
@@ -2578,7 +2761,7 @@ int stk_fp64_fma_rate(stk_ctx* c, double* tflops, void* stream) {
     double best = 0.0;
     for (int rep = 0; rep < 4; ++rep) {
       ck(cudaEventRecord(e0, st), "record");
-      ck(launch_fp64_fma(blocks, iters, c->norm_buf + 32, st), "fp64 probe");
+      ck(launch_fp64_fma(blocks, iters, c->norm_buf + 1048, st), "fp64 probe");
       ck(cudaEventRecord(e1, st), "record");
       ck(cudaEventSynchronize(e1), "sync");
       float ms = 0.f;

@@ -31,6 +31,35 @@ struct Pattern {
   int off[kMaxOffsets][3];          // offset vectors
 };
 
+// One phase of the persistent coarse cycle (persist.cu): a data-parallel step
+// of Algorithm 1 over n units, followed by a grid barrier.
+enum PhaseOp { PHASE_GS = 0, PHASE_RESID = 1, PHASE_RESTRICT = 2, PHASE_PROLONG = 3, PHASE_BOTTOM = 4 };
+struct CyclePhase {
+  int op;
+  int pos0;            // GS / RESID: first element position
+  int64_t n;           // units: element positions, coarse elements, or bottom rows
+  int dims[4];         // RESTRICT: nc0 nc1 nf0 nf1; PROLONG: nf0 nf1 nc0 nc1
+  const void* cpl;     // GS / RESID records
+  const void* mat;
+  const int* perm;
+  const int* nbr;
+  const float* tsc;    // FP16 record scales
+  const float* rsc;
+  const void* b;
+  void* x;
+  void* r;
+  const void* tr;      // RESTRICT: P, PROLONG: P^T, BOTTOM: pseudo-inverse
+  const void* in;
+  void* out;
+  void* xz;            // RESTRICT: coarse iterate, zeroed in the same phase
+};
+// Grid barrier words (device): arrivals at the current barrier, barriers passed.
+struct GridBarrierWords {
+  unsigned int count;
+  unsigned int gen;
+};
+constexpr int kErrBarrierTimeout = 2;   // error word value of an expired grid-barrier wait
+
 // Host-side operators of one level, stored per element with offset slots.
 //   slot 0: the element itself; slot 1+2k: offset -e_k; slot 2+2k: offset +e_k.
 struct HostLevel {
@@ -162,6 +191,14 @@ struct Ctx {
   // launches of at most this many elements use one CTA per element (latency variant), whatever the variant
   int wide_max = 1024;
   int* dev_err = nullptr;     // raised by a kernel whose bounded wait expired
+  // persistent coarse cycle: levels of at most persist_max elements (0: off)
+  // run inside one cooperative launch of persist_ctas CTAs per SM
+  int persist_max = 0, persist_ctas = 1;
+  long long barrier_limit = 2000000000LL;   // clock ticks a grid-barrier wait may take (about 1 s)
+  GridBarrierWords* gbar = nullptr;
+  int persist_level[4] = {-1, -1, -1, -1};  // first level of the program, per storage precision
+  CyclePhase* persist_prog[4] = {nullptr, nullptr, nullptr, nullptr};
+  int persist_nphase[4] = {0, 0, 0, 0};
   // several right-hand sides (interleaved; nr = 4 or 8 once allocated)
   int mr_nr = 0;
   double *mX = nullptr, *mB = nullptr, *mR = nullptr;   // level-0 FP64
@@ -304,6 +341,10 @@ cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int p
 void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages);
 
 cudaError_t launch_fp64_fma(int blocks, int iters, double* out, cudaStream_t st);
+cudaError_t launch_coarse_cycle(const Pattern& pat, int storage, const CyclePhase* phases, int nphase,
+                                GridBarrierWords* gb, int* err, long long limit, int grid, cudaStream_t st);
+cudaError_t launch_barrier_selftest(GridBarrierWords* gb, int* err, long long limit, int rounds, int absent, int grid,
+                                    unsigned int* passed, cudaStream_t st);
 
 // ---- api.cu -------------------------------------------------------------------
 // One element-kernel launch (colour step in MODE_GS, residual in MODE_RESID) on

@@ -93,6 +93,8 @@ SIGNATURES = {
     "stk_learn_objective": [_vp, ctypes.c_int],
     "stk_learn_history": [_vp, _c_int_p, _c_dbl_p, ctypes.c_int, _c_int_p, _c_dbl_p],
     "stk_learn_error_state": [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float)],
+    "stk_set_persistent": [_vp, ctypes.c_int, ctypes.c_int],
+    "stk_barrier_selftest": [_vp, ctypes.c_int, ctypes.c_int64, _c_i64_p],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
 
@@ -255,6 +257,20 @@ class Context:
         """gamma coarse visits per level (1 V-cycle, 2 W-cycle); smoothing
         counts nu * growth^level, at most max(nu, max_sweeps)."""
         self._check(self.lib.stk_set_cycle_shape(self.h, gamma, growth, max_sweeps), "stk_set_cycle_shape")
+
+    def set_persistent(self, max_elements, ctas_per_sm=1):
+        """Run the levels of at most max_elements elements (below level 0) as
+        one cooperative launch per cycle (0 turns it off)."""
+        self._check(self.lib.stk_set_persistent(self.h, max_elements, ctas_per_sm), "stk_set_persistent")
+
+    def barrier_selftest(self, absent=-1, limit_ticks=2_000_000):
+        """(status, passages): STK_OK or the TIMEOUT code of the bounded grid
+        barrier's self-test; raises nothing for a timeout."""
+        n = ctypes.c_int64()
+        rc = self.lib.stk_barrier_selftest(self.h, absent, limit_ticks, ctypes.byref(n))
+        if rc not in (STK_OK, -4):
+            self._check(rc, "stk_barrier_selftest")
+        return rc, n.value
 
     def set_colouring(self, mode):
         """COLOURS_AUTO (checkerboard for the single-phase standard form,

@@ -741,7 +741,9 @@ def test_solve_batch_matches_individual_solves():
             assert rel(x.cpu().numpy(), x1.cpu().numpy()) <= 1e-9
             r = torch.empty_like(b)
             assert g.ctx.residual(x, b, r, want_norm=True) <= 1e-10 * torch.linalg.norm(b).item()
-        with pytest.raises(native.StkError):
+        with pytest.raises(native.StkError):   # one context twice in a batch is refused by the library
+            native.solve_batch([gpus[0].ctx, gpus[0].ctx], [xs[0], xs[0]], [bs[0], bs[0]])
+        with pytest.raises(ValueError):        # vectors of another problem's size, by the binding
             native.solve_batch([gpus[0].ctx, gpus[0].ctx], xs[:2], bs[:2])
     finally:
         for g in gpus:
