@@ -2491,8 +2491,8 @@ void enqueue_residual_loss_grad(Ctx& c, const float* r, double* sums, cudaStream
 }
 
 // Supervised objective on one stored state: features of r, y = MLP, target
-// t_i = e_i / ||r_i||, loss = sum_i ||y_i - t_i||^2 / ne (into sums[1]; sums[0]
-// = 1), and its gradient (packed like the weights) in c.lgrad.
+// t_i = e_i / ||r_i||, loss = sum_i ||y_i - t_i||^2 / ne (sums[1] / sums[0]
+// with sums[0] = ne), and its gradient (packed like the weights) in c.lgrad.
 void enqueue_supervised_loss_grad(Ctx& c, const float* r, const float* e, double* sums, cudaStream_t st) {
   DevLevel& D0 = c.dev[0];
   const int ne = D0.ne, nb = c.nb, H = c.l_hid, IN = c.l_in, ldf = c.l_ldf;
@@ -2506,7 +2506,7 @@ void enqueue_supervised_loss_grad(Ctx& c, const float* r, const float* e, double
   ck(launch_sgemm(ne, nb, H, 0, 0, c.lH, H, c.lW2, nb, c.lY, nb, c.lb2, 0, 1.f, 0.f, st), "fwd2");
   ck(launch_target(ne, nb, nb, e, c.l_zero, c.lnrm, c.lTg, st), "targets");
   ck(launch_mse_grad(nvec, 1.f / (float)ne, c.lY, c.lTg, c.lY, sums + 16, sums + 1, st), "mse");   // lY = dY
-  ck(launch_fill1(sums, st), "one");
+  ck(launch_fill(sums, (double)ne, st), "rows");
   ck(launch_sgemm(H, nb, ne, 1, 0, c.lH, H, c.lY, nb, gW2, nb, nullptr, 0, 1.f, 0.f, st), "gW2");
   ck(launch_colsum(ne, nb, c.lY, nb, gb2, 1.f, st), "gb2");
   ck(launch_sgemm(ne, H, nb, 0, 1, c.lY, nb, c.lW2, nb, c.lF2, H, nullptr, 0, 1.f, 0.f, st), "dH");

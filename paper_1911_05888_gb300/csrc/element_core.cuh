@@ -128,7 +128,25 @@ struct WideGeom {
   int NCG, CW;   // dense column groups and columns per group
   int XS;        // gathered slot stride
   size_t words;  // accumulator words of shared memory (after the index block)
+  // the element's records staged in shared memory by cp.async (when they fit):
+  // byte offset of the staging area, its size, and 1 when staging is used
+  size_t rec_off, rec_bytes;
+  int prefetch;
 };
+
+constexpr size_t kWideStageBudget = 96 * 1024;   // shared bytes per CTA above which records are not staged
+
+// Shared bytes one CTA of the one-CTA-per-element body needs.
+__host__ __device__ inline size_t wide_smem_bytes(const WideGeom& g) {
+  return g.prefetch ? g.rec_off + g.rec_bytes : g.rec_off;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned int d = (unsigned int)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <typename TS>
 __host__ __device__ inline WideGeom wide_geometry(const Pattern& pat) {
@@ -147,7 +165,28 @@ __host__ __device__ inline WideGeom wide_geometry(const Pattern& pat) {
   g.XS = pat.s + 1;
   g.words = (size_t)pat.NG * g.XS + (size_t)g.CGc * pat.TRP + 2 * (size_t)pat.NBP + (size_t)g.NCG * pat.NBP;
   if (kScaledStorage<TS>) g.words += task_scale_stride(pat);
+  using TA = typename StorageTraits<TS>::Acc;
+  g.rec_off = (kMaxOffsets * sizeof(int) + g.words * sizeof(TA) + 15) / 16 * 16;
+  g.rec_bytes = ((size_t)pat.s * pat.TRP + (size_t)pat.nb * pat.NBP) * sizeof(TS);
+  g.prefetch = g.rec_off + g.rec_bytes <= kWideStageBudget ? 1 : 0;
   return g;
+}
+
+// Start copying element pos's coupling record and dense block (A_ii^{-1} or
+// A_ii) into the CTA's staging area; they do not depend on x, so the copy
+// overlaps the neighbour gather (and, in the persistent cycle, the grid
+// barrier before the phase).  Records are 16-byte aligned: TRP and NBP are
+// multiples of 8 entries.
+template <typename TS>
+__device__ __forceinline__ void wide_stage(const Pattern& pat, const WideGeom& wg, int pos, const TS* cpl,
+                                           const TS* mat, unsigned char* smem_raw) {
+  unsigned char* dst = smem_raw + wg.rec_off;
+  const size_t cb = (size_t)pat.s * pat.TRP * sizeof(TS), mb = (size_t)pat.nb * pat.NBP * sizeof(TS);
+  const unsigned char* c0 = reinterpret_cast<const unsigned char*>(cpl + (size_t)pos * pat.s * pat.TRP);
+  const unsigned char* m0 = reinterpret_cast<const unsigned char*>(mat + (size_t)pos * pat.nb * pat.NBP);
+  for (size_t i = (size_t)threadIdx.x * 16; i < cb; i += (size_t)blockDim.x * 16) cp_async16(dst + i, c0 + i);
+  for (size_t i = (size_t)threadIdx.x * 16; i < mb; i += (size_t)blockDim.x * 16) cp_async16(dst + cb + i, m0 + i);
+  cp_async_commit();
 }
 
 // One element (position pos) of a colour step (MODE_GS) or residual
@@ -158,12 +197,13 @@ __host__ __device__ inline WideGeom wide_geometry(const Pattern& pat) {
 // all threads of the CTA in step.  b, x and rout carry no __restrict__: in the
 // persistent cycle earlier phases of the same launch write them, so their
 // loads must not take the read-only (non-coherent) path.
-template <typename TS, typename TX, int S>
-__device__ __forceinline__ void wide_element(const Pattern& pat, const WideGeom& wg, int mode, int pos,
-                                             const int* __restrict__ perm, const int* __restrict__ nbr,
-                                             const TS* __restrict__ cpl, const TS* __restrict__ mat,
-                                             const float* __restrict__ tsc, const float* __restrict__ rsc,
-                                             const TX* b, TX* x, TX* rout, unsigned char* smem_raw) {
+template <typename TS, typename TX, int S, bool ST>
+__device__ __forceinline__ void wide_element_impl(const Pattern& pat, const WideGeom& wg, int mode, int pos,
+                                                  const int* __restrict__ perm, const int* __restrict__ nbr,
+                                                  const TS* __restrict__ cpl, const TS* __restrict__ mat,
+                                                  const float* __restrict__ tsc, const float* __restrict__ rsc,
+                                                  const TX* b, TX* x, TX* rout, unsigned char* smem_raw,
+                                                  bool staged) {
   using Tr = StorageTraits<TS>;
   using TA = typename Tr::Acc;
   constexpr int V = Tr::V;
@@ -180,6 +220,7 @@ __device__ __forceinline__ void wide_element(const Pattern& pat, const WideGeom&
   TA* tss = part2 + wg.NCG * NBP;   // task scales (FP16 records only)
 
   const int tid = threadIdx.x;
+  if (ST && !staged) wide_stage<TS>(pat, wg, pos, cpl, mat, smem_raw);
   const int e = perm[pos];
   for (int i = tid; i < pat.NO; i += kWideNT) nbs[i] = nbr[(size_t)pos * pat.NO + i];
   for (int i = tid; i < nb; i += kWideNT) {
@@ -195,7 +236,11 @@ __device__ __forceinline__ void wide_element(const Pattern& pat, const WideGeom&
     Xs[gi * wg.XS + ci] = (j >= 0) ? (TA)x[(size_t)j * nb + pat.g_cv[gi] * S + ci] : (TA)0;
   }
   __syncthreads();
-  const TS* rec = cpl + (size_t)pos * S * TRP;
+  if (ST) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  const TS* rec = ST ? reinterpret_cast<const TS*>(smem_raw + wg.rec_off) : cpl + (size_t)pos * S * TRP;
   for (int u = tid; u < nvr * wg.CGc; u += kWideNT) {
     const int tv = u % nvr, cg = u / nvr;
     const int c0 = cg * wg.KC, c1 = min(S, c0 + wg.KC);
@@ -211,7 +256,10 @@ __device__ __forceinline__ void wide_element(const Pattern& pat, const WideGeom&
 #pragma unroll 8
     for (int ci = c0; ci < c1; ++ci) {
       TA w[V];
-      Tr::load_keep(rec + (size_t)ci * TRP + tr0, w);
+      if (ST)
+        Tr::load_shared(rec + (size_t)ci * TRP + tr0, w);
+      else
+        Tr::load_keep(rec + (size_t)ci * TRP + tr0, w);
 #pragma unroll
       for (int j = 0; j < V; ++j) acc[j] = fma(w[j], xp[j][ci], acc[j]);
     }
@@ -231,7 +279,7 @@ __device__ __forceinline__ void wide_element(const Pattern& pat, const WideGeom&
     g[r] = g[r] - sum;
   }
   __syncthreads();
-  const TS* mrec = mat + (size_t)pos * nb * NBP;
+  const TS* mrec = ST ? rec + (size_t)S * TRP : mat + (size_t)pos * nb * NBP;
   const TA* vin = (mode == MODE_GS) ? g : xi;
   for (int u = tid; u < NRV * wg.NCG; u += kWideNT) {
     const int rvv = u % NRV, cg = u / NRV;
@@ -242,7 +290,10 @@ __device__ __forceinline__ void wide_element(const Pattern& pat, const WideGeom&
 #pragma unroll 4
     for (int ci = c0; ci < c1; ++ci) {
       TA w[V];
-      Tr::load_keep(mrec + (size_t)ci * NBP + rvv * V, w);
+      if (ST)
+        Tr::load_shared(mrec + (size_t)ci * NBP + rvv * V, w);
+      else
+        Tr::load_keep(mrec + (size_t)ci * NBP + rvv * V, w);
       const TA v = vin[ci];
 #pragma unroll
       for (int j = 0; j < V; ++j) acc[j] = fma(w[j], v, acc[j]);
@@ -261,6 +312,24 @@ __device__ __forceinline__ void wide_element(const Pattern& pat, const WideGeom&
       rout[(size_t)e * nb + r] = (TX)(g[r] - sum);
   }
   __syncthreads();
+}
+
+// The element body with or without staging its records (wg.prefetch; same
+// arithmetic, same bits).  staged: the caller already issued wide_stage for
+// this pos (the persistent cycle does so before its grid barrier).
+template <typename TS, typename TX, int S>
+__device__ __forceinline__ void wide_element(const Pattern& pat, const WideGeom& wg, int mode, int pos,
+                                             const int* __restrict__ perm, const int* __restrict__ nbr,
+                                             const TS* __restrict__ cpl, const TS* __restrict__ mat,
+                                             const float* __restrict__ tsc, const float* __restrict__ rsc,
+                                             const TX* b, TX* x, TX* rout, unsigned char* smem_raw,
+                                             bool staged = false) {
+  if (wg.prefetch)
+    wide_element_impl<TS, TX, S, true>(pat, wg, mode, pos, perm, nbr, cpl, mat, tsc, rsc, b, x, rout, smem_raw,
+                                       staged);
+  else
+    wide_element_impl<TS, TX, S, false>(pat, wg, mode, pos, perm, nbr, cpl, mat, tsc, rsc, b, x, rout, smem_raw,
+                                        false);
 }
 
 // ---- restriction / prolongation of one coarse element -------------------------

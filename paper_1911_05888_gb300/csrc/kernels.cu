@@ -995,7 +995,7 @@ static cudaError_t launch_wide_s(const Pattern& pat, int mode, int pos0, int npo
                                  const float* rsc, const void* b, void* x, void* r, cudaStream_t st) {
   if (npos <= 0) return cudaSuccess;
   const WideGeom wg = wide_geometry<TS>(pat);
-  size_t smem = kMaxOffsets * sizeof(int) + wg.words * sizeof(typename StorageTraits<TS>::Acc);
+  size_t smem = wide_smem_bytes(wg);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
   int grid = std::min(npos, num_sms() * (2048 / kWideNT));
   if (kScaledStorage<TS> && (!tsc || !rsc)) return cudaErrorInvalidValue;

@@ -275,9 +275,9 @@ cudaError_t launch_colsum(int M, int N, const float* A, int lda, float* out, flo
   return cudaGetLastError();
 }
 
-__global__ void fill1_kernel(double* v) { v[0] = 1.0; }
-cudaError_t launch_fill1(double* v, cudaStream_t st) {
-  fill1_kernel<<<1, 1, 0, st>>>(v);
+__global__ void fill_kernel(double* v, double a) { v[0] = a; }
+cudaError_t launch_fill(double* v, double a, cudaStream_t st) {
+  fill_kernel<<<1, 1, 0, st>>>(v, a);
   return cudaGetLastError();
 }
 cudaError_t launch_mse_grad(int64_t n, float scale, const float* Y, const float* T, float* dY, double* part,

@@ -19,6 +19,7 @@
 // a correct program never reaches the bound.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -74,13 +75,16 @@ __global__ void __launch_bounds__(kWideNT) coarse_cycle_kernel(const __grid_cons
                                                                GridBarrierWords* gb, int* err, long long limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int d = pat.d, s = pat.s, nb = pat.nb;
+  bool staged = false;   // this CTA's first element of the phase has its records in flight already
   for (int ph = 0; ph < nphase; ++ph) {
     const CyclePhase P = phases[ph];
     if (P.op == PHASE_GS || P.op == PHASE_RESID) {
       const int mode = P.op == PHASE_GS ? MODE_GS : MODE_RESID;
-      for (int pos = P.pos0 + (int)blockIdx.x; pos < P.pos0 + (int)P.n; pos += gridDim.x)
+      for (int pos = P.pos0 + (int)blockIdx.x; pos < P.pos0 + (int)P.n; pos += gridDim.x) {
         wide_element<TS, TX, S>(pat, wg, mode, pos, P.perm, P.nbr, (const TS*)P.cpl, (const TS*)P.mat, P.tsc,
-                                P.rsc, (const TX*)P.b, (TX*)P.x, (TX*)P.r, smem_raw);
+                                P.rsc, (const TX*)P.b, (TX*)P.x, (TX*)P.r, smem_raw, staged);
+        staged = false;
+      }
     } else if (P.op == PHASE_RESTRICT) {
       // r_c = I^T r, and the coarse iterate starts from zero (Algorithm 1)
       for (int64_t C = blockIdx.x; C < P.n; C += gridDim.x) {
@@ -106,7 +110,21 @@ __global__ void __launch_bounds__(kWideNT) coarse_cycle_kernel(const __grid_cons
         if (lane == 0) xx[row] = (TX)acc;
       }
     }
-    if (ph + 1 < nphase && !grid_barrier(gb, err, limit)) return;
+    staged = false;
+    if (ph + 1 < nphase) {
+      // records are never written: start the next phase's first element copy
+      // now, so that it overlaps the barrier
+      const CyclePhase& N = phases[ph + 1];
+      if (wg.prefetch && (N.op == PHASE_GS || N.op == PHASE_RESID) && (int)blockIdx.x < (int)N.n) {
+        __syncthreads();
+        wide_stage<TS>(pat, wg, N.pos0 + (int)blockIdx.x, (const TS*)N.cpl, (const TS*)N.mat, smem_raw);
+        staged = true;
+      }
+      if (!grid_barrier(gb, err, limit)) {
+        if (staged) cp_async_wait_all();   // no copy may outlive the launch's shared memory
+        return;
+      }
+    }
   }
 }
 
@@ -126,8 +144,7 @@ template <typename TS, typename TX, int S>
 cudaError_t launch_coarse_s(const Pattern& pat, const CyclePhase* phases, int nphase, GridBarrierWords* gb, int* err,
                             long long limit, int grid, cudaStream_t st) {
   const WideGeom wg = wide_geometry<TS>(pat);
-  using TA = typename StorageTraits<TS>::Acc;
-  size_t smem = kMaxOffsets * sizeof(int) + wg.words * sizeof(TA);
+  size_t smem = wide_smem_bytes(wg);
   const size_t tr = (size_t)(1 << pat.d) * pat.nb * sizeof(TX);   // transfer staging
   if (tr > smem) smem = tr;
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
@@ -169,7 +186,190 @@ cudaError_t launch_coarse_t(const Pattern& pat, const CyclePhase* phases, int np
 #undef STK_COARSE_CASE
 }
 
+// ---- batched outer iteration ----------------------------------------------------
+// One element unit of a batch step: the cycle's colour step or residual on the
+// FP32 records, or the outer FP64 residual on the FP64 records.
+template <int S>
+__device__ __forceinline__ void batch_element(const Pattern& pat, int op, const CyclePhase& P, int pos,
+                                              unsigned char* smem) {
+  if (op == PHASE_RESID64) {
+    const WideGeom wg = wide_geometry<double>(pat);
+    wide_element<double, double, S>(pat, wg, MODE_RESID, pos, P.perm, P.nbr, (const double*)P.cpl,
+                                    (const double*)P.mat, nullptr, nullptr, (const double*)P.b, (double*)P.x,
+                                    (double*)P.r, smem);
+  } else {
+    const WideGeom wg = wide_geometry<float>(pat);
+    wide_element<float, float, S>(pat, wg, op == PHASE_GS ? MODE_GS : MODE_RESID, pos, P.perm, P.nbr,
+                                  (const float*)P.cpl, (const float*)P.mat, nullptr, nullptr, (const float*)P.b,
+                                  (float*)P.x, (float*)P.r, smem);
+  }
+}
+
+__device__ __forceinline__ void batch_unit(const BatchProblem& B, const CyclePhase& P, int64_t v, int it, double rtol,
+                                           unsigned char* smem_raw) {
+  const Pattern& pat = B.pat;
+  const int d = pat.d, s = pat.s, nb = pat.nb;
+  switch (P.op) {
+    case PHASE_GS:
+    case PHASE_RESID:
+    case PHASE_RESID64: {
+      const int pos = P.pos0 + (int)v;
+      switch (s) {
+        case 4: batch_element<4>(pat, P.op, P, pos, smem_raw); break;
+        case 8: batch_element<8>(pat, P.op, P, pos, smem_raw); break;
+        case 9: batch_element<9>(pat, P.op, P, pos, smem_raw); break;
+        case 16: batch_element<16>(pat, P.op, P, pos, smem_raw); break;
+        case 27: batch_element<27>(pat, P.op, P, pos, smem_raw); break;
+        default: break;
+      }
+      break;
+    }
+    case PHASE_RESTRICT:
+      restrict_coarse<float>(d, s, nb, P.dims[0], P.dims[1], P.dims[2], P.dims[3], v, (const float*)P.tr,
+                             (const float*)P.in, (float*)P.out, reinterpret_cast<float*>(smem_raw));
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) ((float*)P.xz)[v * nb + i] = 0.f;
+      break;
+    case PHASE_PROLONG:
+      prolong_coarse<float>(d, s, nb, P.dims[0], P.dims[1], P.dims[2], P.dims[3], v, (const float*)P.tr,
+                            (const float*)P.in, (float*)P.out, reinterpret_cast<float*>(smem_raw));
+      break;
+    case PHASE_BOTTOM: {
+      const int lane = threadIdx.x & 31;
+      const int64_t row = v * (blockDim.x / 32) + threadIdx.x / 32;
+      if (row < P.n) {
+        const double* pinv = (const double*)P.tr;
+        const float* bb = (const float*)P.in;
+        double acc = 0.0;
+        for (int64_t j = lane; j < P.n; j += 32) acc += pinv[row * P.n + j] * (double)bb[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) ((float*)P.out)[row] = (float)acc;
+      }
+      break;
+    }
+    case PHASE_CONVERT: {   // cycle right-hand side from the outer residual, zero initial guess
+      const int64_t i0 = v * kBatchChunk, i1 = min(B.n0, i0 + kBatchChunk);
+      const double* r = (const double*)P.in;
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        ((float*)P.out)[i] = (float)r[i];
+        ((float*)P.xz)[i] = 0.f;
+      }
+      break;
+    }
+    case PHASE_AXPY: {      // x += c (the cycle's FP32 correction into the FP64 iterate)
+      const int64_t i0 = v * kBatchChunk, i1 = min(B.n0, i0 + kBatchChunk);
+      const float* c = (const float*)P.in;
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) ((double*)P.out)[i] += (double)c[i];
+      break;
+    }
+    case PHASE_NORM: {      // partial sum of squares of one chunk, fixed reduction order
+      double* red = reinterpret_cast<double*>(smem_raw);
+      const int64_t i0 = v * kBatchChunk, i1 = min(B.n0, i0 + kBatchChunk);
+      const double* r = (const double*)P.in;
+      double acc = 0.0;
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += r[i] * r[i];
+      __syncthreads();
+      red[threadIdx.x] = acc;
+      __syncthreads();
+      for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) B.part[v] = red[0];
+      __syncthreads();
+      break;
+    }
+    case PHASE_CHECK: {     // ||r|| / ||b|| after this iteration; stop when converged or diverged
+      if (threadIdx.x == 0) {
+        const int64_t nch = (B.n0 + kBatchChunk - 1) / kBatchChunk;
+        double sum = 0.0;
+        for (int64_t c = 0; c < nch; ++c) sum += *((volatile double*)&B.part[c]);
+        const double rel = sqrt(sum) / B.bnorm;
+        B.hist[it + 1] = rel;
+        *B.iters = it + 1;
+        if (rel <= rtol) {
+          *((volatile int*)B.active) = 0;
+        } else if (!isfinite(rel) || rel > 1e6 * B.rel0) {
+          *B.status = -5;   // STK_ERR_DIVERGED
+          *((volatile int*)B.active) = 0;
+        }
+      }
+      break;
+    }
+    default: break;
+  }
+}
+
+// Every outer iteration of every problem of the batch in one cooperative
+// launch: x <- x + V(0, b - A x) with the V-cycle in FP32 records, the
+// residual in FP64; the steps of one iteration run in order with a grid
+// barrier after each; a problem whose residual reached rtol stops taking part.
+__global__ void __launch_bounds__(kWideNT) batch_solve_kernel(const BatchProblem* __restrict__ probs, int nprob,
+                                                              const BatchStep* __restrict__ steps, int nsteps,
+                                                              const BatchTask* __restrict__ tasks, int maxit,
+                                                              double rtol, GridBarrierWords* gb, int* err,
+                                                              long long limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_any;
+  for (int it = 0; it < maxit; ++it) {
+    for (int k = 0; k < nsteps; ++k) {
+      const BatchStep stp = steps[k];
+      int t = stp.t0;
+      for (int64_t u = blockIdx.x; u < stp.units; u += gridDim.x) {
+        while (t + 1 < stp.t1 && tasks[t + 1].ustart <= u) ++t;
+        const BatchProblem& B = probs[tasks[t].prob];
+        if (*((volatile int*)B.active) == 0) continue;
+        const CyclePhase P = tasks[t].ph;
+        batch_unit(B, P, u - tasks[t].ustart, it, rtol, smem_raw);
+      }
+      if (!grid_barrier(gb, err, limit)) return;
+    }
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int q = 0; q < nprob; ++q) any |= *((volatile int*)probs[q].active);
+      s_any = any;
+    }
+    __syncthreads();
+    if (!s_any) return;
+  }
+}
+
 }  // namespace
+
+size_t batch_smem_bytes(const Pattern& pat) {
+  const WideGeom w32 = wide_geometry<float>(pat), w64 = wide_geometry<double>(pat);
+  size_t smem = std::max(wide_smem_bytes(w32), wide_smem_bytes(w64));
+  smem = std::max(smem, (size_t)(1 << pat.d) * pat.nb * sizeof(float));
+  smem = std::max(smem, (size_t)kWideNT * sizeof(double));
+  return smem;
+}
+
+cudaError_t launch_batch_solve(const BatchProblem* probs, int nprob, const BatchStep* steps, int nsteps,
+                               const BatchTask* tasks, int maxit, double rtol, int smax, size_t smem,
+                               GridBarrierWords* gb, int* err, long long limit, int grid, cudaStream_t st) {
+  (void)smax;
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(batch_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0, dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_solve_kernel, kWideNT, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidValue;
+  grid = std::min(grid, per_sm * sms);
+  if (grid < 1) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kWideNT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_solve_kernel, probs, nprob, steps, nsteps, tasks, maxit, rtol, gb, err, limit);
+}
 
 cudaError_t launch_coarse_cycle(const Pattern& pat, int storage, const CyclePhase* phases, int nphase,
                                 GridBarrierWords* gb, int* err, long long limit, int grid, cudaStream_t st) {

@@ -33,7 +33,13 @@ struct Pattern {
 
 // One phase of the persistent coarse cycle (persist.cu): a data-parallel step
 // of Algorithm 1 over n units, followed by a grid barrier.
-enum PhaseOp { PHASE_GS = 0, PHASE_RESID = 1, PHASE_RESTRICT = 2, PHASE_PROLONG = 3, PHASE_BOTTOM = 4 };
+enum PhaseOp {
+  PHASE_GS = 0, PHASE_RESID = 1, PHASE_RESTRICT = 2, PHASE_PROLONG = 3, PHASE_BOTTOM = 4,
+  // batched outer iteration (stk_solve_batch_persistent): FP64 residual on the
+  // FP64 records, cycle input vb = (float) r64 with vx = 0, x64 += vx, partial
+  // sums of ||r64||^2, and the per-problem convergence check
+  PHASE_RESID64 = 5, PHASE_CONVERT = 6, PHASE_AXPY = 7, PHASE_NORM = 8, PHASE_CHECK = 9
+};
 struct CyclePhase {
   int op;
   int pos0;            // GS / RESID: first element position
@@ -53,6 +59,33 @@ struct CyclePhase {
   void* out;
   void* xz;            // RESTRICT: coarse iterate, zeroed in the same phase
 };
+// One problem of a persistent batch (device copy): its coupling pattern and
+// shared-memory geometries, and the vectors of its outer iteration.
+constexpr int kBatchChunk = 2048;   // entries per unit of the batch's vector phases
+struct BatchProblem {
+  Pattern pat;
+  int64_t n0;           // level-0 unknowns
+  double* x64;          // caller's iterate (FP64)
+  double* r64;          // outer residual (context work vector)
+  double* part;         // partial sums of ||r64||^2, one per chunk
+  double bnorm, rel0;   // ||b|| and the initial relative residual
+  int* active;          // 1 while iterating
+  int* iters;           // outer iterations done
+  int* status;          // 0, or STK_ERR_DIVERGED
+  double* hist;         // relative residual after each iteration [maxit + 1]
+};
+// One step of a batch program: tasks [t0, t1) of the task table, run
+// together; task t owns units [ustart[t], ustart[t + 1]) of the step.
+struct BatchStep {
+  int t0, t1;
+  int64_t units;
+};
+struct BatchTask {
+  int prob;
+  int64_t ustart;
+  CyclePhase ph;
+};
+
 // Grid barrier words (device): arrivals at the current barrier, barriers passed.
 struct GridBarrierWords {
   unsigned int count;
@@ -308,7 +341,7 @@ cudaError_t launch_features(int ne, int nb, int nface, int NO, int ldf, const in
 cudaError_t launch_sgemm(int M, int N, int K, int ta, int tb, const float* A, int lda, const float* B, int ldb,
                          float* C, int ldc, const float* bias, int act, float alpha, float beta, cudaStream_t st);
 cudaError_t launch_colsum(int M, int N, const float* A, int lda, float* out, float alpha, cudaStream_t st);
-cudaError_t launch_fill1(double* v, cudaStream_t st);
+cudaError_t launch_fill(double* v, double a, cudaStream_t st);
 cudaError_t launch_mse_grad(int64_t n, float scale, const float* Y, const float* T, float* dY, double* part,
                             double* out, cudaStream_t st);
 cudaError_t launch_tanh_back(int64_t n, const float* H, float* dH, cudaStream_t st);
@@ -343,6 +376,10 @@ void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages)
 cudaError_t launch_fp64_fma(int blocks, int iters, double* out, cudaStream_t st);
 cudaError_t launch_coarse_cycle(const Pattern& pat, int storage, const CyclePhase* phases, int nphase,
                                 GridBarrierWords* gb, int* err, long long limit, int grid, cudaStream_t st);
+cudaError_t launch_batch_solve(const BatchProblem* probs, int nprob, const BatchStep* steps, int nsteps,
+                               const BatchTask* tasks, int maxit, double rtol, int smax, size_t smem,
+                               GridBarrierWords* gb, int* err, long long limit, int grid, cudaStream_t st);
+size_t batch_smem_bytes(const Pattern& pat);
 cudaError_t launch_barrier_selftest(GridBarrierWords* gb, int* err, long long limit, int rounds, int absent, int grid,
                                     unsigned int* passed, cudaStream_t st);
 

@@ -570,7 +570,7 @@ def test_learned_acceptance_matches_oracle():
     x = torch.zeros_like(b)
     it, hist = gpu.ctx.solve(x, b, rtol=1e-10, maxit=100)
     dec, ratio, kappa = gpu.ctx.learn_history()
-    orc = multigrid.Multigrid(prob, storage="fp32")
+    orc = multigrid.Multigrid(prob.with_(nu1=3, nu2=3), storage="fp32")   # the context's V(3,3)
     mesh = oldg.Mesh(prob.d, prob.n, prob.lo, prob.hi, prob.bc)
     xo, ho, dec_o, ratio_o, kappa_o = learned.solve_with_correction(orc, b_host, w, nin, hid, nout,
                                                                     learned.face_neighbours(mesh), rtol=1e-10,
@@ -959,3 +959,53 @@ def test_checkerboard_refused_for_viscous_stress_form():
     checkerboard puts in one colour: setup refuses it."""
     with pytest.raises(native.StkError):
         StokesMG(CASES["stress16p3"](), colouring=native.COLOURS_CHECKERBOARD)
+
+
+EXTREME = {
+    "square-1e-6": lambda: P.square_interface(n=16, p=2, mu_inner=1e-6),
+    "square-1e6-p3": lambda: P.square_interface(n=8, p=3, mu_inner=1e6),
+}
+
+
+@pytest.mark.parametrize("name", list(EXTREME))
+def test_multiphase_extreme_viscosity_ratios(name):
+    """Section 5.6's square interface at viscosity ratios 1e-6 and 1e6: the
+    library's greedy colours, sqrt(mu) scaling, right-hand side with jump data
+    and ten V-cycle iterates equal the oracle's (1e-13 / 1e-14 / 1e-13 / 1e-12),
+    and FGMRES reaches 1e-11 on the scaled system with the oracle's iteration
+    count and a velocity of the same discretisation error below 1e-3."""
+    prob = EXTREME[name]()
+    gpu = StokesMG(prob)
+    orc = oracle_for(prob)
+    try:
+        for l in range(len(orc.levels) - 1):
+            assert np.array_equal(gpu.ctx.get_colours(l, orc.levels[l].ne), orc.levels[l].mesh.colour())
+        D = gpu.scaling().ravel()
+        np.testing.assert_allclose(D, orc.levels[0].D, rtol=1e-14)
+        b = gpu.rhs().ravel()
+        bo = oracle_rhs(prob, orc)
+        assert maxrel(b, bo) <= 1e-13
+        Z = trivial_kernel(prob, orc)
+        rng = np.random.default_rng(21)
+        bs = rng.uniform(-1, 1, prob.n_dofs)
+        bs -= Z @ (Z.T @ bs)
+        xd = torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda")
+        xo = np.zeros(prob.n_dofs)
+        for k in range(10):
+            gpu.ctx.vcycle(xd, dev(bs))
+            orc.vcycle(xo, bs)
+            xg = xd.cpu().numpy()
+            assert rel(xg - Z @ (Z.T @ xg), xo - Z @ (Z.T @ xo)) <= 1e-12, k
+        bsc = D * b
+        x = torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda")
+        gpu.ctx.set_solver(native.FGMRES, 40)
+        it, hist = gpu.ctx.solve(x, dev(bsc), rtol=1e-11, maxit=100)
+        assert hist[-1] <= 1e-11
+        xo, ho = orc.fgmres(bsc, rtol=1e-11, maxit=100, restart=40)
+        assert abs(it - (len(ho) - 1)) <= 1
+        eg = velocity_error(prob, orc, D * x.cpu().numpy())
+        eo = velocity_error(prob, orc, orc.unscale(xo))
+        assert np.all(eg <= 1e-3), eg
+        np.testing.assert_allclose(eg, eo, rtol=1e-6)
+    finally:
+        gpu.close()

@@ -503,7 +503,7 @@ def test_learned_residual_objective_gradient_matches_finite_differences():
 
 # ------------------------------------------------------------ multi-phase ----
 
-@pytest.mark.parametrize("ratio", [1e-3, 1e3])
+@pytest.mark.parametrize("ratio", [1e-6, 1e-3, 1e3, 1e6])
 def test_multiphase_symmetry_kernel_and_colouring(ratio):
     """Section 5.6 square interface: symmetric operator (also after the sqrt(mu)
     scaling), periodic kernel of dimension d+1, and the greedy colouring
@@ -541,7 +541,7 @@ def _mp_errors(prob, mg, x):
     return np.array(out)
 
 
-@pytest.mark.parametrize("ratio", [1e-3, 1e3])
+@pytest.mark.parametrize("ratio", [1e-6, 1e-3, 1e3, 1e6])
 def test_multiphase_orders_and_rate(ratio):
     """Section 5.6: viscosity-upwinded fluxes with jump data and the sqrt(mu)
     scaling: velocity order p+1, pressure about p+1/2 (p = 2), and
