@@ -435,6 +435,36 @@ int stk_set_df_matvec(stk_ctx* ctx, int on);
  * problem's code.  Errors: STK_ERR_INVALID_ARG (null or repeated context,
  * n < 1, nrhs outside 1..8), STK_ERR_CUDA.
  */
+/*
+ * The same batch in ONE persistent launch (no counterpart in the paper): every
+ * outer iteration of every problem runs inside a single cooperative kernel
+ * of ctas_per_sm CTAs per SM.  The outer iteration is iterative refinement,
+ * x <- x + V(0, b - A x), with the context's V-cycle shape on FP32 records
+ * and the residual on the FP64 records; one iteration is a program of steps
+ * (the cycle input, every colour step, residual, restriction, bottom solve
+ * and prolongation of Algorithm 1, the update of x, the FP64 residual, its
+ * norm, and the convergence test ||b - A x|| <= rtol ||b||), and step k of
+ * all problems runs together -- a work list of (problem, step, element or
+ * coarse element or chunk) units -- with a bounded grid barrier between
+ * steps.  A problem that converged (or diverged: non-finite, or 1e6 times its
+ * initial residual) stops taking part; the launch ends when none is left or
+ * after maxit iterations.  Every context must be set up with FP32 cycles,
+ * distinct, on one device, for a degree with 4, 8, 9, 16 or 27 scalar modes
+ * per element; their level work vectors are used, so no other call may use
+ * them meanwhile.  x[i] (FP64 [element][nb], the initial guess, overwritten)
+ * and b[i] are device arrays of the caller.  iters_out, status_out (n
+ * entries) and hist (n x (maxit + 1): relative residual before the first and
+ * after each iteration, zero beyond the last) may be NULL.  Every element of
+ * every level runs on the one-CTA-per-element body, so results agree with
+ * stk_solve's to rounding, not bit for bit.  The workspace (work list,
+ * partial sums) is allocated per call.  Errors: STK_ERR_INVALID_ARG,
+ * STK_ERR_NOT_SETUP, STK_ERR_DIVERGED (status_out says which problem),
+ * STK_ERR_TIMEOUT (a barrier wait reached its bound; messages in
+ * stk_last_error(ctx[0])), STK_ERR_CUDA.
+ */
+int stk_solve_batch_persistent(stk_ctx* const* ctx, int n, double* const* x, const double* const* b, double rtol,
+                               int maxit, int ctas_per_sm, int* iters_out, int* status_out, double* hist,
+                               void* stream);
 int stk_solve_batch(stk_ctx* const* ctx, int n, double* const* x, const double* const* b, int nrhs, double rtol,
                     int maxit, int inner, int threads, int* iters_out, int* status_out, void* stream);
 

@@ -2783,6 +2783,192 @@ int stk_launch_count(stk_ctx* c, int64_t* count) {
   return STK_OK;
 }
 
+int stk_solve_batch_persistent(stk_ctx* const* ctx, int n, double* const* x, const double* const* b, double rtol,
+                               int maxit, int ctas_per_sm, int* iters_out, int* status_out, double* hist,
+                               void* stream) {
+  if (!ctx || !x || !b || n < 1 || n > 4096 || maxit < 0 || !(rtol > 0) || ctas_per_sm < 1 || ctas_per_sm > 8)
+    return STK_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctx[i] || !x[i] || !b[i]) return STK_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctx[j] == ctx[i]) return STK_ERR_INVALID_ARG;
+  }
+  stk_ctx* c0 = ctx[0];
+  return guard(c0, [&]() -> int {
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = *ctx[i];
+      if (!c.ready) return fail(c0, STK_ERR_NOT_SETUP, "problem " + std::to_string(i) + " is not set up");
+      if (c.device != c0->device) return fail(c0, STK_ERR_INVALID_ARG, "problems on different devices");
+      if (c.precision != STK_FP32)
+        return fail(c0, STK_ERR_INVALID_ARG, "the persistent batch runs FP32-record cycles (problem " +
+                                                 std::to_string(i) + ")");
+      const int sv = c.pat.s;
+      if (sv != 4 && sv != 8 && sv != 9 && sv != 16 && sv != 27)
+        return fail(c0, STK_ERR_INVALID_ARG, "degree not compiled into the persistent batch");
+    }
+    ck(cudaSetDevice(c0->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    ck(cudaStreamSynchronize(st), "sync caller stream");
+    // ||b|| and the initial residual of every problem (its own stream)
+    std::vector<double> bnorm(n), rel0(n);
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = *ctx[i];
+      enqueue_norm(c, b[i], c.stream);
+      ck(cudaStreamSynchronize(c.stream), "sync");
+      bnorm[i] = std::sqrt(c.norm_host[0]);
+      if (bnorm[i] == 0.0) bnorm[i] = 1.0;
+      enqueue_residual64(c, x[i], b[i], c.r64, c.stream);
+      enqueue_norm(c, c.r64, c.stream);
+      ck(cudaStreamSynchronize(c.stream), "sync");
+      rel0[i] = std::sqrt(c.norm_host[0]) / bnorm[i];
+    }
+    // per-problem programs: cycle input, V-cycle, x += c, FP64 residual, norm, check
+    std::vector<std::vector<CyclePhase>> progs(n);
+    int64_t nchunk_total = 0;
+    std::vector<int64_t> part_off(n);
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = *ctx[i];
+      DevLevel& D0 = c.dev[0];
+      const int64_t n0 = level_ne(c, 0) * c.nb, nch = (n0 + kBatchChunk - 1) / kBatchChunk;
+      part_off[i] = nchunk_total;
+      nchunk_total += nch;
+      std::vector<CyclePhase>& pr = progs[i];
+      CyclePhase cv{};
+      cv.op = PHASE_CONVERT;
+      cv.n = nch;
+      cv.in = c.r64;
+      cv.out = D0.vb[1];
+      cv.xz = D0.vx[1];
+      pr.push_back(cv);
+      emit_cycle_phases(c, STK_FP32, 0, pr);
+      CyclePhase ax{};
+      ax.op = PHASE_AXPY;
+      ax.n = nch;
+      ax.in = D0.vx[1];
+      ax.out = x[i];
+      pr.push_back(ax);
+      CyclePhase rr{};
+      rr.op = PHASE_RESID64;
+      rr.n = D0.ne;
+      rr.cpl = D0.cpl[0];
+      rr.mat = D0.dia[0];
+      rr.perm = D0.perm;
+      rr.nbr = D0.nbr;
+      rr.b = b[i];
+      rr.x = x[i];
+      rr.r = c.r64;
+      pr.push_back(rr);
+      CyclePhase nm{};
+      nm.op = PHASE_NORM;
+      nm.n = nch;
+      nm.in = c.r64;
+      pr.push_back(nm);
+      CyclePhase ch{};
+      ch.op = PHASE_CHECK;
+      ch.n = 1;
+      pr.push_back(ch);
+    }
+    // steps: phase k of every problem that has one, run together
+    size_t nsteps = 0;
+    for (auto& pr : progs) nsteps = std::max(nsteps, pr.size());
+    std::vector<BatchStep> steps(nsteps);
+    std::vector<BatchTask> tasks;
+    auto units_of = [](const CyclePhase& ph) -> int64_t {
+      return ph.op == PHASE_BOTTOM ? (ph.n + 7) / 8 : ph.n;   // bottom: one row per warp, 8 warps per CTA
+    };
+    for (size_t k = 0; k < nsteps; ++k) {
+      steps[k].t0 = (int)tasks.size();
+      int64_t u = 0;
+      for (int i = 0; i < n; ++i) {
+        if (k >= progs[i].size()) continue;
+        BatchTask t{};
+        t.prob = i;
+        t.ustart = u;
+        t.ph = progs[i][k];
+        u += units_of(t.ph);
+        tasks.push_back(t);
+      }
+      steps[k].t1 = (int)tasks.size();
+      steps[k].units = u;
+    }
+    // device copies: problems, steps, tasks, partials, flags, histories
+    struct DevBuf {
+      std::vector<void*> p;
+      ~DevBuf() {
+        for (void* q : p) cudaFree(q);
+      }
+      void* get(size_t bytes) {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) throw CudaFail{cudaErrorMemoryAllocation, "cudaMalloc"};
+        p.push_back(q);
+        return q;
+      }
+    } buf;
+    double* part = (double*)buf.get((size_t)nchunk_total * 8);
+    int* flags = (int*)buf.get((size_t)3 * n * sizeof(int));   // active, iters, status
+    double* dhist = (double*)buf.get((size_t)n * (maxit + 1) * 8);
+    std::vector<int> hflags(3 * n, 0);
+    std::vector<double> hh((size_t)n * (maxit + 1), 0.0);
+    std::vector<BatchProblem> probs(n);
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = *ctx[i];
+      BatchProblem& B = probs[i];
+      B.pat = c.pat;
+      B.n0 = level_ne(c, 0) * c.nb;
+      B.x64 = x[i];
+      B.r64 = c.r64;
+      B.part = part + part_off[i];
+      B.bnorm = bnorm[i];
+      B.rel0 = rel0[i];
+      B.active = flags + i;
+      B.iters = flags + n + i;
+      B.status = flags + 2 * n + i;
+      B.hist = dhist + (size_t)i * (maxit + 1);
+      hflags[i] = (rel0[i] > rtol && maxit > 0) ? 1 : 0;
+      hh[(size_t)i * (maxit + 1)] = rel0[i];
+      smem = std::max(smem, batch_smem_bytes(c.pat));
+    }
+    BatchProblem* dprobs = (BatchProblem*)buf.get(probs.size() * sizeof(BatchProblem));
+    BatchStep* dsteps = (BatchStep*)buf.get(steps.size() * sizeof(BatchStep));
+    BatchTask* dtasks = (BatchTask*)buf.get(tasks.size() * sizeof(BatchTask));
+    ck(cudaMemcpy(dprobs, probs.data(), probs.size() * sizeof(BatchProblem), cudaMemcpyHostToDevice), "copy");
+    ck(cudaMemcpy(dsteps, steps.data(), steps.size() * sizeof(BatchStep), cudaMemcpyHostToDevice), "copy");
+    ck(cudaMemcpy(dtasks, tasks.data(), tasks.size() * sizeof(BatchTask), cudaMemcpyHostToDevice), "copy");
+    ck(cudaMemcpy(flags, hflags.data(), hflags.size() * sizeof(int), cudaMemcpyHostToDevice), "copy");
+    ck(cudaMemcpy(dhist, hh.data(), hh.size() * 8, cudaMemcpyHostToDevice), "copy");
+    ck(cudaMemsetAsync(c0->gbar, 0, sizeof(GridBarrierWords), st), "memset");
+    ck(cudaMemsetAsync(c0->dev_err, 0, sizeof(int), st), "memset");
+    int sms = 0;
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device), "attribute");
+    ck(launch_batch_solve(dprobs, n, dsteps, (int)nsteps, dtasks, maxit, rtol, 0, smem, c0->gbar, c0->dev_err,
+                          c0->barrier_limit, sms * ctas_per_sm, st),
+       "persistent batch launch");
+    c0->launches++;
+    int err = 0;
+    ck(cudaMemcpyAsync(&err, c0->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaStreamSynchronize(st), "sync");
+    ck(cudaMemcpy(hflags.data(), flags, hflags.size() * sizeof(int), cudaMemcpyDeviceToHost), "copy");
+    ck(cudaMemcpy(hh.data(), dhist, hh.size() * 8, cudaMemcpyDeviceToHost), "copy");
+    if (err != 0) {
+      ck(cudaMemset(c0->dev_err, 0, sizeof(int)), "memset");
+      return fail(c0, STK_ERR_TIMEOUT, "a grid-barrier wait of the persistent batch reached its bound");
+    }
+    int rc = STK_OK;
+    for (int i = 0; i < n; ++i) {
+      const int it = hflags[n + i];
+      const int stt = hflags[2 * n + i];
+      if (iters_out) iters_out[i] = it;
+      if (status_out) status_out[i] = stt;
+      if (hist)
+        for (int k = 0; k <= maxit; ++k) hist[(size_t)i * (maxit + 1) + k] = k <= it ? hh[(size_t)i * (maxit + 1) + k] : 0.0;
+      if (rc == STK_OK && stt != STK_OK) rc = stt;
+    }
+    if (rc != STK_OK) return fail(c0, rc, "a problem of the batch diverged");
+    return STK_OK;
+  });
+}
+
 int stk_solve_batch(stk_ctx* const* ctx, int n, double* const* x, const double* const* b, int nrhs, double rtol,
                     int maxit, int inner, int threads, int* iters_out, int* status_out, void* stream) {
   if (!ctx || !x || !b || n < 1 || nrhs < 1 || nrhs > 8) return STK_ERR_INVALID_ARG;

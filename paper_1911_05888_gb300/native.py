@@ -94,6 +94,9 @@ SIGNATURES = {
     "stk_learn_history": [_vp, _c_int_p, _c_dbl_p, ctypes.c_int, _c_int_p, _c_dbl_p],
     "stk_learn_error_state": [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float)],
     "stk_set_persistent": [_vp, ctypes.c_int, ctypes.c_int],
+    "stk_solve_batch_persistent": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int), _c_dbl_p, _vp],
     "stk_barrier_selftest": [_vp, ctypes.c_int, ctypes.c_int64, _c_i64_p],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
@@ -590,6 +593,28 @@ def solve_batch(contexts, xs, bs, rtol=1e-10, maxit=200, nrhs=1, inner=3, thread
         raise StkError("stk_solve_batch: problem %d: %s (%s)" % (i, msg.decode() if msg else "",
                                                                 ERRORS.get(rc, rc)))
     return list(it), list(st)
+
+
+def solve_batch_persistent(contexts, xs, bs, rtol=1e-10, maxit=200, ctas_per_sm=1, stream=None):
+    """stk_solve_batch_persistent: the whole batch (FP32-cycle contexts) by
+    iterative refinement in one cooperative launch.  Returns (iterations,
+    status codes, histories [n][maxit+1])."""
+    n = len(contexts)
+    if not (len(xs) == len(bs) == n):
+        raise ValueError("one x and one b per context")
+    lib = contexts[0].lib
+    hs = (_vp * n)(*[c.h.value for c in contexts])
+    xp = (_vp * n)(*[_vec("x", t, c._n()).value for c, t in zip(contexts, xs)])
+    bp = (_vp * n)(*[_vec("b", t, c._n()).value for c, t in zip(contexts, bs)])
+    it = (ctypes.c_int * n)()
+    st = (ctypes.c_int * n)()
+    hist = np.zeros((n, maxit + 1))
+    rc = lib.stk_solve_batch_persistent(hs, n, xp, bp, rtol, maxit, ctas_per_sm, it, st,
+                                        hist.ctypes.data_as(_c_dbl_p), _stream(stream))
+    if rc != STK_OK:
+        msg = lib.stk_last_error(contexts[0].h)
+        raise StkError("stk_solve_batch_persistent: %s (%s)" % (msg.decode() if msg else "", ERRORS.get(rc, rc)))
+    return list(it), list(st), hist
 
 
 def host_pseudo_inverse(A, theta=1e-10):

@@ -970,10 +970,15 @@ EXTREME = {
 @pytest.mark.parametrize("name", list(EXTREME))
 def test_multiphase_extreme_viscosity_ratios(name):
     """Section 5.6's square interface at viscosity ratios 1e-6 and 1e6: the
-    library's greedy colours, sqrt(mu) scaling, right-hand side with jump data
-    and ten V-cycle iterates equal the oracle's (1e-13 / 1e-14 / 1e-13 / 1e-12),
-    and FGMRES reaches 1e-11 on the scaled system with the oracle's iteration
-    count and a velocity of the same discretisation error below 1e-3."""
+    library's greedy colours, sqrt(mu) scaling and right-hand side with jump
+    data equal the oracle's (1e-13 / 1e-14 / 1e-13), ten V-cycle iterates
+    agree to max(1e-12, 1e-16 cond(A_bottom)), and FGMRES reaches 1e-11 on the
+    scaled system with the oracle's iteration count and a velocity of the same
+    discretisation error below 1e-3.  The iterate tolerance: the sqrt(mu)
+    scaling leaves the element blocks as well conditioned as at ratio 1
+    (cond(A_ii) <= 1.5e6 on both), but the bottom operator of the 1e6 case has
+    cond 1.8e8, and the bottom solve multiplies the rounding-level difference
+    of its right-hand side (the two sides sum in different orders) by it."""
     prob = EXTREME[name]()
     gpu = StokesMG(prob)
     orc = oracle_for(prob)
@@ -989,13 +994,16 @@ def test_multiphase_extreme_viscosity_ratios(name):
         rng = np.random.default_rng(21)
         bs = rng.uniform(-1, 1, prob.n_dofs)
         bs -= Z @ (Z.T @ bs)
+        lam = np.abs(np.linalg.eigvalsh(orc.levels[-1].A.toarray()))
+        lam = lam[lam > 1e-10 * lam.max()]
+        tol = max(1e-12, 1e-16 * lam.max() / lam.min())
         xd = torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda")
         xo = np.zeros(prob.n_dofs)
         for k in range(10):
             gpu.ctx.vcycle(xd, dev(bs))
             orc.vcycle(xo, bs)
             xg = xd.cpu().numpy()
-            assert rel(xg - Z @ (Z.T @ xg), xo - Z @ (Z.T @ xo)) <= 1e-12, k
+            assert rel(xg - Z @ (Z.T @ xg), xo - Z @ (Z.T @ xo)) <= tol, (k, tol)
         bsc = D * b
         x = torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda")
         gpu.ctx.set_solver(native.FGMRES, 40)
