@@ -45,6 +45,9 @@ def parse():
                          "unsteady viscous-stress problems (32^2..256^2, p 2/3) solved together")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batch workload")
     ap.add_argument("--batch-threads", type=int, default=16, help="host threads driving the batch")
+    ap.add_argument("--batch-persistent", type=int, default=0,
+                    help="1: solve the batch by iterative refinement in one persistent cooperative launch "
+                         "(stk_solve_batch_persistent) instead of host threads running each problem's solve")
     ap.add_argument("--re", type=float, default=100.0, help="effective Reynolds number (unsteady3d)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--p", type=int, default=3)
@@ -71,9 +74,10 @@ def parse():
     ap.add_argument("--learn-seeds", type=int, default=8)
     ap.add_argument("--learn-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default=None, choices=["gs", "resid", "solve"],
+    ap.add_argument("--profile", default=None, choices=["gs", "resid", "solve", "batch"],
                     help="run only a profiling target (for ncu): 8 finest-level colour sweeps, "
-                         "8 finest-level residuals, or one solve")
+                         "8 finest-level residuals, one solve, or one persistent batch solve of the first "
+                         "--batch problems of the serving mix with meshes of at most --n elements a side")
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -337,6 +341,17 @@ def run_profile(args):
     from paper_1911_05888_gb300 import native
     from paper_1911_05888_gb300.solver import StokesMG
     prec = {"fp64": native.FP64, "fp32": native.FP32, "bf16": native.BF16, "fp16": native.FP16}[args.precision]
+    if args.profile == "batch":
+        from paper_1911_05888_gb300 import problems as P
+        probs = [q for q in P.serving_mix(64, seed=0) if q.n[0] <= args.n][: args.batch]
+        gpus = [StokesMG(q, precision=native.FP32) for q in probs]
+        bs = [torch.from_numpy(g.rhs().ravel()).cuda() for g in gpus]
+        xs = [torch.zeros_like(b) for b in bs]
+        its, st, _ = native.solve_batch_persistent([g.ctx for g in gpus], xs, bs, rtol=1e-10, maxit=200)
+        torch.cuda.synchronize()
+        print("profile batch: %d problems (%s), iterations %s, status %s" % (
+            len(gpus), [q.n[0] for q in probs], its, st))
+        return
     prob = workload(args.n, args.p)
     mg = StokesMG(prob, precision=prec, nu=(args.nu, args.nu))
     # the library's default shapes (what the autotuner picks on this workload):
@@ -786,7 +801,7 @@ def run_batch(args):
         rng = np.random.default_rng(100 + i)
         return torch.from_numpy(np.concatenate([b] + [rng.uniform(-1, 1, b.size) for _ in range(nrhs - 1)])).cuda()
 
-    def measure(gpus, steps, warmup, threads=None):
+    def measure(gpus, steps, warmup, threads=None, persistent=False):
         threads = args.batch_threads if threads is None else threads
         bs = [rhs_of(g, i) for i, g in enumerate(gpus)]
         xs = [torch.zeros_like(b) for b in bs]
@@ -795,6 +810,8 @@ def run_batch(args):
         def step():
             for x in xs:
                 x.zero_()
+            if persistent and nrhs == 1:
+                return native.solve_batch_persistent(ctxs, xs, bs, rtol=1e-10, maxit=200)[0]
             return native.solve_batch(ctxs, xs, bs, nrhs=nrhs, rtol=1e-10, maxit=200, threads=threads)[0]
         for _ in range(warmup):
             step()
@@ -837,10 +854,11 @@ def run_batch(args):
     setup_s = time.perf_counter() - t0
     clocks = Clocks(0)
     clocks.start()
-    el, units, its, launches, e2e_s, nbytes, worst = measure(gpus, args.steps, args.warmup)
+    el, units, its, launches, e2e_s, nbytes, worst = measure(gpus, args.steps, args.warmup,
+                                                             persistent=bool(args.batch_persistent))
     clk = clocks.stop()
     # the same batch driven by one host thread: problems one after another
-    el_seq = measure(gpus, 1, 0, threads=1)[0]
+    el_seq = measure(gpus, 1, 0, threads=1)[0] if not args.batch_persistent else None
     dofs = sum(g.prob.n_dofs for g in gpus)
     for g in gpus:
         g.close()
@@ -862,12 +880,15 @@ def run_batch(args):
         "data": "synthetic (manufactured unsteady flows, seeded viscosities)",
         "config": {"workload": "batched-serving-mix-2d-unsteady-viscous-stress", "problems": len(probs),
                    "sizes": [q.n[0] for q in probs], "degrees": [q.p for q in probs], "dofs": dofs,
-                   "nu": [args.nu, args.nu], "outer": "fgmres(%d)" % args.restart, "rtol": 1e-10, "nrhs": nrhs,
+                   "nu": [args.nu, args.nu],
+                   "outer": ("iterative refinement, one persistent launch per batch solve"
+                             if args.batch_persistent and nrhs == 1 else "fgmres(%d)" % args.restart),
+                   "rtol": 1e-10, "nrhs": nrhs,
                    "host_threads": args.batch_threads, "cache": "inputs larger than L2"},
         "iters": its, "worst_rel_residual": worst, "setup_s": round(setup_s, 1),
         "e2e": {"value": units / e2e_s, "unit": "DOF-cycles/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_s / args.steps * 1e3},
-        "sequential_ms_per_step": el_seq * 1e3,
+        "sequential_ms_per_step": el_seq * 1e3 if el_seq is not None else None,
         "plain_fp64": plain, "gpu_launches": int(launches), "clocks": clk}))
 
 

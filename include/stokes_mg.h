@@ -177,6 +177,22 @@ int stk_set_cycle_shape(stk_ctx* ctx, int gamma, int growth, int max_sweeps);
  */
 int stk_set_persistent(stk_ctx* ctx, int max_elements, int ctas_per_sm);
 /*
+ * Element clustering (the Concluding Remarks' suggestion for p = 1): on = 1
+ * makes the block Gauss-Seidel smoother of level 0 use clusters of 2 x 2
+ * elements (the children of one cell of level 1) as its blocks: x_C <-
+ * A_CC^{-1}(b_C - sum_{D != C} A_CD x_D), clusters coloured like elements
+ * (checkerboard of the cluster grid for the standard form, 2^d parity
+ * colours otherwise).  Applies at the next stk_setup to 2D problems of degree
+ * 1 with one phase whose periodic axes have an even number of clusters
+ * (STK_INFO_CLUSTERS tells whether it took effect); cycles of one
+ * right-hand side only (stk_solve_multi keeps element blocks, and
+ * stk_solve_batch_persistent refuses such contexts).  The cluster blocks are
+ * 48 x 48 and run on the element kernels; vectors move between element and
+ * cluster layout at the cycle's start and end and around the transfers.
+ * Errors: STK_ERR_INVALID_ARG unless on is 0 or 1.
+ */
+int stk_set_clusters(stk_ctx* ctx, int on);
+/*
  * Self-test of the bounded grid barrier (a diagnostic, no solver state is
  * touched): a cooperative launch of the persistent cycle's grid passes four
  * barriers; with absent >= 0 that CTA returns at once and never arrives, so
@@ -219,14 +235,16 @@ int stk_get_sizes(stk_ctx* ctx, int* nlevels, int64_t* n_elements, int* nb, int*
  *                            2 equilibrated cuSOLVER syevd (device, above);
  *   STK_INFO_BOTTOM_UNKNOWNS unknowns of the bottom level;
  *   STK_INFO_COLOURS         colours of the level-0 smoother;
- *   STK_INFO_DEVICE_BYTES    device bytes the library holds for the context.
- * The first three need stk_setup (else STK_ERR_NOT_SETUP); an unknown key is
+ *   STK_INFO_DEVICE_BYTES    device bytes the library holds for the context;
+ *   STK_INFO_CLUSTERS        1 when level 0 smooths element clusters.
+ * All but STK_INFO_DEVICE_BYTES need stk_setup (else STK_ERR_NOT_SETUP); an unknown key is
  * STK_ERR_INVALID_ARG.
  */
 #define STK_INFO_BOTTOM_SOLVER 0
 #define STK_INFO_BOTTOM_UNKNOWNS 1
 #define STK_INFO_COLOURS 2
 #define STK_INFO_DEVICE_BYTES 3
+#define STK_INFO_CLUSTERS 4
 int stk_get_info(stk_ctx* ctx, int what, int64_t* value);
 
 /* Dense nb x nb block A_ij (row element i, column element j, natural

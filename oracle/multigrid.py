@@ -9,7 +9,9 @@ Section 3 (Multigrid design):
   * Algorithm 1: V(E_h, x_h, b_h) with nu1 pre- and nu2 post-smoothing sweeps,
     r_2h = (I_2h^h)^T (b_h - A_h x_h), coarse guess 0, x_h += I_2h^h x_2h.
   * Section 6's alternatives to the V-cycle: W-cycles (gamma coarse visits
-    per level) and variable V-cycles (smoothing counts growing per level).
+    per level) and variable V-cycles (smoothing counts growing per level);
+    the Concluding Remarks' element clustering (blocks of 2^d elements on the
+    finest level) as a smoother option.
   * Bottom solver (Section 3 footnote on the trivial kernel): symmetric
     eigendecomposition of the coarsest operator with near-zero eigenvalues
     snapped to zero (least-squares solution).
@@ -131,6 +133,80 @@ class SmootherLevel:
             x[sl] = self.inv[i] @ g
 
 
+def cluster_layout(mesh):
+    """Clusters of 2^d elements (the 2 x 2 (x 2) children of one cell of the
+    mesh with halved n): the cluster index of every element and its child
+    position ch = sum_k (i_k mod 2) 2^k, and the cluster grid."""
+    idx = mesh.idx
+    nc = [n // 2 for n in mesh.n]
+    cstride = [int(np.prod(nc[:k])) for k in range(mesh.d)]
+    cid = ((idx // 2) * np.asarray(cstride)).sum(axis=1)
+    child = ((idx % 2) * (2 ** np.arange(mesh.d))).sum(axis=1)
+    cidx = np.stack([(np.arange(int(np.prod(nc))) // cstride[k]) % nc[k] for k in range(mesh.d)], axis=1)
+    return cid, child, nc, cidx
+
+
+def clusters_apply(mesh, gamma):
+    """Element clustering (Concluding Remarks: larger smoother blocks for
+    p = 1) is used on a level when every axis has an even element count and
+    every periodic axis an even cluster count (so that the cluster colouring
+    closes around the wrap), on single-phase problems."""
+    if mesh.chi is not None:
+        return False
+    for k in range(mesh.d):
+        if mesh.n[k] % 2:
+            return False
+        if mesh.periodic(k) and (mesh.n[k] // 2) % 2:
+            return False
+    return True
+
+
+class ClusterSmootherLevel:
+    """Block Gauss-Seidel over clusters of 2^d elements: each block is every
+    unknown of the 2^d children of one coarse cell, x_C <- A_CC^{-1}(b_C -
+    sum_{D != C} A_CD x_D); clusters coloured like elements one level down
+    (checkerboard of the cluster index for the standard form, whose clusters
+    couple across faces only; 2^d parity colours otherwise), colours in
+    ascending order."""
+
+    def __init__(self, lev):
+        self.lev = lev
+        mesh = lev.mesh
+        nb = lev.nb
+        cid, child, nc, cidx = cluster_layout(mesh)
+        self.ncl = int(np.prod(nc))
+        self.rows = []
+        for C in range(self.ncl):
+            els = np.nonzero(cid == C)[0]
+            els = els[np.argsort(child[els])]
+            self.rows.append((els[:, None] * nb + np.arange(nb)[None, :]).ravel())
+        A = lev.A.tocsr()
+        self.blocks = [A[r][:, r].toarray() for r in self.rows]
+        self.inv = [np.linalg.inv(B) for B in self.blocks]
+        self.Arows = [A[r] for r in self.rows]
+        if lev.standard_form:
+            self.colour = cidx.sum(axis=1) % 2
+        else:
+            self.colour = (cidx % 2 * (2 ** np.arange(mesh.d))).sum(axis=1)
+        self.ncol = int(self.colour.max()) + 1
+
+    def colour_step(self, x, b, c):
+        """Update every cluster of colour c from the current x."""
+        for C in np.nonzero(self.colour == c)[0]:
+            r = self.rows[C]
+            g = b[r] - self.Arows[C] @ x + self.blocks[C] @ x[r]
+            x[r] = self.inv[C] @ g
+
+    def sweep(self, x, b):
+        for c in range(self.ncol):
+            self.colour_step(x, b, c)
+
+    def sweep_lexicographic(self, x, b):
+        for C in range(self.ncl):
+            r = self.rows[C]
+            x[r] = self.inv[C] @ (b[r] - self.Arows[C] @ x + self.blocks[C] @ x[r])
+
+
 def bottom_pseudo_inverse(A, theta=SNAP_THETA):
     """Least-squares inverse of the coarsest operator: eigendecomposition with
     |lambda| <= theta max|lambda| snapped to zero.  Returns (pinv, n_snapped)."""
@@ -146,7 +222,7 @@ class Multigrid:
     """The V-cycle hierarchy of a problem (oracle)."""
 
     def __init__(self, prob, storage=None, levels=None, injections=None, max_levels=None, shape=(1, 1, 64),
-                 two_colours=False):
+                 two_colours=False, clusters=False):
         self.prob = prob
         # cycle shape (Section 6): coarse visits per level (1 V, 2 W), growth
         # of the smoothing counts per coarser level, cap on the counts
@@ -159,6 +235,12 @@ class Multigrid:
         # two_colours: the checkerboard instead of the 2^d parity colours
         # (valid for face-coupled operators only: gamma = 0, single phase)
         self.sm = [SmootherLevel(l, storage, two_colours) for l in levels[:-1]]
+        # clusters: the finest level smooths 2^d-element clusters (FP64 blocks)
+        self.clusters = False
+        if clusters and storage is None and clusters_apply(levels[0].mesh, prob.gamma):
+            levels[0].standard_form = prob.gamma == 0
+            self.sm[0] = ClusterSmootherLevel(levels[0])
+            self.clusters = True
         self.bottom, self.kernel_dim_bottom = bottom_pseudo_inverse(levels[-1].A)
         self.nu1, self.nu2 = prob.nu1, prob.nu2
 

@@ -30,28 +30,33 @@ namespace stk {
 // back to direct loads when its records do not fit in shared memory.
 cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, const void* mat, const void* b,
                         void* x, void* r, cudaStream_t st) {
-  DevLevel& D = c.dev[l];
+  return run_element_on(c, c.pat, c.dev[l], prec, mode, pos0, npos, mat, b, x, r, st);
+}
+
+// The same on any level's records with its own pattern (the cluster level's).
+cudaError_t run_element_on(Ctx& c, const Pattern& pat, DevLevel& D, int prec, int mode, int pos0, int npos,
+                           const void* mat, const void* b, void* x, void* r, cudaStream_t st) {
   // FP16 records carry scales and run on the warp and wide kernels only.
   const bool scaled = prec == STK_FP16;
   const float* tsc = scaled ? D.csc : nullptr;
   const float* rsc = scaled ? (mode == MODE_GS ? D.isc : D.dsc) : nullptr;
   if (npos <= c.wide_max) {
-    cudaError_t e = launch_element_wide(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
+    cudaError_t e = launch_element_wide(pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
                                         x, r, st);
     if (e != cudaErrorInvalidValue || scaled) return e;
   }
   const int variant = c.variant_of[prec];
   if (variant == 2 || scaled) {
-    cudaError_t e = launch_element_warp(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
+    cudaError_t e = launch_element_warp(pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
                                         x, r, c.warp_ctas[prec], st);
     if (e != cudaErrorInvalidValue || scaled) return e;
   }
   if (variant == 1) {
-    cudaError_t e = launch_element_pipe(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
+    cudaError_t e = launch_element_pipe(pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r,
                                         c.dev_err, c.pipe_ctas[prec], c.pipe_stages[prec], st);
     if (e != cudaErrorInvalidValue) return e;
   }
-  return launch_element(c.pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r, st);
+  return launch_element(pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, b, x, r, st);
 }
 
 }  // namespace stk
@@ -110,6 +115,10 @@ void free_device(Ctx& c) {
   c.device_bytes = 0;
   free_persist(c);
   c.gbar = nullptr;
+  c.cluster_on = 0;
+  c.cdev = DevLevel();
+  c.chost = HostLevel();
+  for (int v = 0; v < 2; ++v) c.cvx[v] = c.cvb[v] = c.cvr[v] = c.ctmp[v] = nullptr;
   if (c.norm_host) cudaFreeHost(c.norm_host);
   c.norm_host = nullptr;
   if (c.khost) cudaFreeHost(c.khost);
@@ -167,11 +176,8 @@ int colour_of(const Ctx& c, const int* n, int64_t e) {
 
 // Pack the Stokes blocks of smoothing level l into the colour-major device
 // records of kernels.cu.
-void pack_level(Ctx& c, int l, cudaStream_t st) {
-  const HostLevel& H = c.host[l];
-  DevLevel& D = c.dev[l];
-  const Pattern& P = c.pat;
-  int s = c.s, nb = c.nb, ss = s * s;
+void pack_records(Ctx& c, const HostLevel& H, const Pattern& P, DevLevel& D, bool level0, cudaStream_t st) {
+  int s = P.s, nb = P.nb, ss = s * s;
   int64_t ne = H.ne;
   D.ne = (int)ne;
   for (int k = 0; k < 3; ++k) D.n[k] = H.n[k];
@@ -269,7 +275,7 @@ void pack_level(Ctx& c, int l, cudaStream_t st) {
   // With 16-bit smoother records the refined Krylov matvec still runs on FP32
   // couplings and diagonal blocks: its Arnoldi relation needs u * cond(A) < 1,
   // which 16-bit unit roundoffs (2^-8, 2^-11) do not give on these operators.
-  if (l == 0 && (c.precision == STK_BF16 || c.precision == STK_FP16)) {
+  if (level0 && (c.precision == STK_BF16 || c.precision == STK_FP16)) {
     void* src[2] = {D.cpl[0], D.dia[0]};
     size_t cnt[2] = {cpl_n, mat_n};
     void** dst[2] = {&D.cpl[STK_FP32], &D.dia[STK_FP32]};
@@ -279,7 +285,7 @@ void pack_level(Ctx& c, int l, cudaStream_t st) {
     }
   }
   // FP32 remainders for the FP64-accurate FGMRES matvec on the FP32 units
-  if (l == 0 && c.precision != STK_FP64) {
+  if (level0 && c.precision != STK_FP64) {
     D.cpl_lo = dalloc(c, cpl_n * 4);
     D.dia_lo = dalloc(c, mat_n * 4);
     ck(launch_fp32_remainder((int64_t)cpl_n, (const double*)D.cpl[0], D.cpl_lo, st), "remainder");
@@ -287,6 +293,9 @@ void pack_level(Ctx& c, int l, cudaStream_t st) {
   }
   (void)st;
 }
+
+void pack_level(Ctx& c, int l, cudaStream_t st) { pack_records(c, c.host[l], c.pat, c.dev[l], l == 0, st); }
+
 
 void alloc_vectors(Ctx& c) {
   int L = nlevels(c);
@@ -507,9 +516,15 @@ void enqueue_smooth(Ctx& c, int prec, int l, int sweeps, void* x, const void* b,
     }
 }
 
+void enqueue_cycle_clustered(Ctx& c, int prec, void* x, const void* b, cudaStream_t st);
+
 void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t st) {
   int vi = prec == STK_FP64 ? 0 : 1;
   int L = nlevels(c);
+  if (l == 0 && c.cluster_on) {
+    enqueue_cycle_clustered(c, prec, x, b, st);
+    return;
+  }
   if (l >= 1 && l == c.persist_level[prec] && c.persist_prog[prec] && x == c.dev[l].vx[vi] &&
       b == c.dev[l].vb[vi]) {
     // levels l .. L-1 in one cooperative launch (persist.cu)
@@ -659,6 +674,50 @@ void build_persist(Ctx& c) {
     c.persist_nphase[pr] = (int)prog.size();
     c.persist_level[pr] = l0;
   }
+}
+
+// Algorithm 1 on level 0 with 2 x 2 element clusters as the smoother's blocks
+// (Concluding Remarks): b and x move to the cluster layout, the cluster
+// records smooth and form the residual, which returns to the element layout
+// for the restriction; the prolongation adds into the element layout of x.
+void enqueue_cycle_clustered(Ctx& c, int prec, void* x, const void* b, cudaStream_t st) {
+  const int vi = prec == STK_FP64 ? 0 : 1;
+  DevLevel& D = c.dev[0];
+  DevLevel& Dc = c.dev[1];
+  DevLevel& K = c.cdev;
+  const int n0 = D.n[0], n1 = D.n[1], nvar = c.d + 1;
+  auto perm = [&](int to_cluster, const void* in, void* out) {
+    ck(launch_cluster_permute(vi == 0, n0, n1, c.s, nvar, to_cluster, in, out, st), "cluster layout");
+    c.launches++;
+  };
+  auto smooth = [&](int sweeps) {
+    for (int it = 0; it < sweeps; ++it)
+      for (int col = 0; col < K.ncolour; ++col) {
+        const int n = K.cstart[col + 1] - K.cstart[col];
+        if (n <= 0) continue;
+        ck(run_element_on(c, c.cpat, K, prec, MODE_GS, K.cstart[col], n, K.inv[prec], c.cvb[vi], c.cvx[vi], nullptr,
+                          st),
+           "cluster colour step");
+        c.launches++;
+      }
+  };
+  perm(1, b, c.cvb[vi]);
+  perm(1, x, c.cvx[vi]);
+  smooth(level_sweeps(c, c.nu1, 0));
+  ck(run_element_on(c, c.cpat, K, prec, MODE_RESID, 0, K.ne, K.dia[prec], c.cvb[vi], c.cvx[vi], c.cvr[vi], st),
+     "cluster residual");
+  c.launches++;
+  perm(0, c.cvr[vi], D.vr[vi]);
+  ck(launch_restrict(vi == 0, c.d, c.s, c.nb, Dc.n, D.n, Dc.ne, c.child_P[vi], D.vr[vi], Dc.vb[vi], st), "restrict");
+  ck(cudaMemsetAsync(Dc.vx[vi], 0, (size_t)Dc.ne * c.nb * (vi == 0 ? 8 : 4), st), "memset");
+  c.launches++;
+  for (int v = coarse_visits(c, 0); v > 0; --v) enqueue_cycle(c, prec, 1, Dc.vx[vi], Dc.vb[vi], st);
+  perm(0, c.cvx[vi], c.ctmp[vi]);
+  ck(launch_prolong(vi == 0, c.d, c.s, c.nb, D.n, Dc.n, Dc.ne, c.child_PT[vi], Dc.vx[vi], c.ctmp[vi], st), "prolong");
+  c.launches++;
+  perm(1, c.ctmp[vi], c.cvx[vi]);
+  smooth(level_sweeps(c, c.nu2, 0));
+  perm(0, c.cvx[vi], x);
 }
 
 void enqueue_residual64(Ctx& c, const double* x, const double* b, double* r, cudaStream_t st) {
@@ -1562,6 +1621,14 @@ int stk_set_colouring(stk_ctx* c, int mode) {
   });
 }
 
+int stk_set_clusters(stk_ctx* c, int on) {
+  return guard(c, [&]() -> int {
+    if (on != 0 && on != 1) return fail(c, STK_ERR_INVALID_ARG, "clusters: 0 or 1");
+    c->cluster_req = on;
+    return STK_OK;
+  });
+}
+
 int stk_set_persistent(stk_ctx* c, int max_elements, int ctas_per_sm) {
   return guard(c, [&]() -> int {
     if (max_elements < 0 || ctas_per_sm < 1 || ctas_per_sm > 8)
@@ -1640,6 +1707,35 @@ int stk_setup(stk_ctx* c, void* stream) {
       return fail(c, STK_ERR_SINGULAR_BLOCK, e.what());
     }
     alloc_vectors(*c);
+    // element clustering of level 0 (2D, p = 1, one phase, a hierarchy below
+    // it, every periodic axis with an even number of clusters)
+    c->cluster_on = 0;
+    if (c->cluster_req && c->d == 2 && c->p == 1 && c->chi.empty() && L >= 3) {
+      bool ok = true;
+      for (int k = 0; k < c->d; ++k)
+        if (c->host[0].n[k] % 2 || (c->bc[2 * k] == STK_BC_PERIODIC && (c->host[0].n[k] / 2) % 2)) ok = false;
+      if (ok) {
+        build_pattern(c->d, 3, c->gamma, false, c->cpat);
+        std::string err;
+        if (build_cluster_level(*c, c->host[0], c->pat, c->cpat, c->chost, err) != STK_OK) return fail(c, STK_ERR_INVALID_ARG, err);
+        try {
+          pack_records(*c, c->chost, c->cpat, c->cdev, false, st);
+        } catch (const std::runtime_error& e) {
+          free_device(*c);
+          return fail(c, STK_ERR_SINGULAR_BLOCK, e.what());
+        }
+        const int64_t n0 = level_ne(*c, 0) * c->nb;
+        for (int v = 0; v < 2; ++v) {
+          if (v == 1 && c->precision == STK_FP64) continue;
+          const size_t es = v == 0 ? 8 : 4;
+          c->cvx[v] = dalloc(*c, n0 * es);
+          c->cvb[v] = dalloc(*c, n0 * es);
+          c->cvr[v] = dalloc(*c, n0 * es);
+          c->ctmp[v] = dalloc(*c, n0 * es);
+        }
+        c->cluster_on = 1;
+      }
+    }
     setup_bottom(*c);
     c->dev_err = (int*)dalloc(*c, 16);
     ck(cudaMemset(c->dev_err, 0, 16), "memset");
@@ -1706,6 +1802,10 @@ int stk_get_info(stk_ctx* c, int what, int64_t* value) {
       case STK_INFO_COLOURS:
         if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
         *value = nlevels(*c) > 1 ? c->dev[0].ncolour : 0;
+        return STK_OK;
+      case STK_INFO_CLUSTERS:
+        if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+        *value = c->cluster_on;
         return STK_OK;
       case STK_INFO_DEVICE_BYTES:
         *value = c->device_bytes;
@@ -2802,6 +2902,9 @@ int stk_solve_batch_persistent(stk_ctx* const* ctx, int n, double* const* x, con
       if (c.precision != STK_FP32)
         return fail(c0, STK_ERR_INVALID_ARG, "the persistent batch runs FP32-record cycles (problem " +
                                                  std::to_string(i) + ")");
+      if (c.cluster_on)
+        return fail(c0, STK_ERR_INVALID_ARG, "the persistent batch smooths element by element (problem " +
+                                                 std::to_string(i) + " clusters its finest level)");
       const int sv = c.pat.s;
       if (sv != 4 && sv != 8 && sv != 9 && sv != 16 && sv != 27)
         return fail(c0, STK_ERR_INVALID_ARG, "degree not compiled into the persistent batch");

@@ -1248,6 +1248,41 @@ cudaError_t launch_to_bf16(int64_t n, void* y, const double* x, cudaStream_t st)
 }
 
 // ||x||_2^2 into out[0] (device); part holds 1024 partials.
+// ---- element <-> cluster layout (2D clusters of 2 x 2 elements) --------------
+// element layout [e][v][a] (e = i0 + n0 i1), cluster layout
+// [C][v][child][a] (C = i0/2 + (n0/2)(i1/2), child = (i0 mod 2) + 2 (i1 mod 2)).
+template <typename T>
+__global__ void cluster_permute_kernel(int n0, int n1, int s, int nvar, int to_cluster, const T* __restrict__ in,
+                                       T* __restrict__ out) {
+  const int64_t N = (int64_t)n0 * n1 * nvar * s;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / ((int64_t)nvar * s);
+    const int v = (int)((i / s) % nvar), a = (int)(i % s);
+    const int i0 = (int)(e % n0), i1 = (int)(e / n0);
+    const int64_t C = (i0 >> 1) + (int64_t)(n0 >> 1) * (i1 >> 1);
+    const int ch = (i0 & 1) + 2 * (i1 & 1);
+    const int64_t j = C * ((int64_t)nvar * 4 * s) + (int64_t)v * 4 * s + ch * s + a;
+    if (to_cluster)
+      out[j] = in[i];
+    else
+      out[i] = in[j];
+  }
+}
+
+cudaError_t launch_cluster_permute(int vec64, int n0, int n1, int s, int nvar, int to_cluster, const void* in,
+                                   void* out, cudaStream_t st) {
+  const int64_t N = (int64_t)n0 * n1 * nvar * s;
+  const int grid = (int)std::min<int64_t>((N + 255) / 256, (int64_t)num_sms() * 16);
+  if (N <= 0) return cudaSuccess;
+  if (vec64)
+    cluster_permute_kernel<double><<<grid, 256, 0, st>>>(n0, n1, s, nvar, to_cluster, (const double*)in,
+                                                         (double*)out);
+  else
+    cluster_permute_kernel<float><<<grid, 256, 0, st>>>(n0, n1, s, nvar, to_cluster, (const float*)in,
+                                                        (float*)out);
+  return cudaGetLastError();
+}
+
 // ---- FP64 FMA rate probe ----------------------------------------------------
 // Eight independent chains of dependent FMAs per thread (enough instruction-
 // level parallelism to cover the FP64 pipe latency with 8 warps per SM

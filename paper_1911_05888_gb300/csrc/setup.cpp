@@ -1635,3 +1635,115 @@ extern "C" int stk_host_pseudo_inverse(int n, const double* A, double theta, dou
     return STK_ERR_OOM;
   }
 }
+
+namespace stk {
+
+// Element clustering (Concluding Remarks: larger smoother blocks for p = 1):
+// the level-H operator re-blocked into clusters of 2^d elements, the children
+// of one cell of the halved mesh.  A cluster's unknowns are ordered
+// [variable][child][mode] (child = sum_k (i_k mod 2) 2^k), so a cluster is an
+// "element" of cp.s = 2^d ep.s modes per variable and the element kernels run
+// it unchanged.  Couplings inside a cluster join its diagonal block; the
+// others land in the task of cp whose (row variable, column variable, cluster
+// offset) they have.  Fails (STK_ERR_INVALID_ARG) if some coupling has no task.
+int build_cluster_level(const Ctx& c, const HostLevel& H, const Pattern& ep, const Pattern& cp, HostLevel& HC,
+                        std::string& err) {
+  const int d = c.d, s = ep.s, nb = ep.nb, nch = 1 << d;
+  const int S2 = cp.s, NB2 = cp.nb;
+  if (S2 != nch * s || NB2 != nch * nb) {
+    err = "cluster pattern does not match the element pattern";
+    return STK_ERR_INVALID_ARG;
+  }
+  HC = HostLevel();
+  int64_t ne2 = 1;
+  for (int k = 0; k < 3; ++k) {
+    HC.n[k] = k < d ? H.n[k] / 2 : 1;
+    HC.h[k] = k < d ? 2 * H.h[k] : 0;
+    ne2 *= HC.n[k];
+  }
+  HC.ne = (int)ne2;
+  HC.D.assign((size_t)ne2 * NB2 * NB2, 0.0);
+  HC.C.assign((size_t)ne2 * cp.T * S2 * S2, 0.0);
+  HC.nbr.assign((size_t)ne2 * cp.NO, -1);
+  auto cluster_id = [&](const int* ci) -> int64_t {
+    int64_t id = 0, stride = 1;
+    for (int k = 0; k < d; ++k) {
+      id += ci[k] * stride;
+      stride *= HC.n[k];
+    }
+    return id;
+  };
+  for (int64_t C = 0; C < ne2; ++C) {
+    int ci[3];
+    element_index(HC.n, d, C, ci);
+    for (int o = 0; o < cp.NO; ++o) {
+      int cj[3];
+      bool ok = true;
+      for (int k = 0; k < d; ++k) {
+        cj[k] = ci[k] + cp.off[o][k];
+        if (cj[k] < 0 || cj[k] >= HC.n[k]) {
+          if (c.bc[2 * k] == STK_BC_PERIODIC)
+            cj[k] = (cj[k] + HC.n[k]) % HC.n[k];
+          else
+            ok = false;
+        }
+      }
+      if (ok) HC.nbr[(size_t)C * cp.NO + o] = (int)cluster_id(cj);
+    }
+  }
+  auto floordiv2 = [](int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); };
+  for (int64_t e = 0; e < H.ne; ++e) {
+    int ie[3];
+    element_index(H.n, d, e, ie);
+    int ci[3] = {0, 0, 0}, ch = 0;
+    for (int k = 0; k < d; ++k) {
+      ci[k] = ie[k] / 2;
+      ch |= (ie[k] & 1) << k;
+    }
+    const int64_t C = cluster_id(ci);
+    double* DC = &HC.D[(size_t)C * NB2 * NB2];
+    const double* De = &H.D[(size_t)e * nb * nb];
+    for (int rv = 0; rv <= d; ++rv)
+      for (int cv = 0; cv <= d; ++cv)
+        for (int a = 0; a < s; ++a)
+          for (int b2 = 0; b2 < s; ++b2)
+            DC[(size_t)(rv * S2 + ch * s + a) * NB2 + cv * S2 + ch * s + b2] += De[(size_t)(rv * s + a) * nb + cv * s + b2];
+    for (int t = 0; t < ep.T; ++t) {
+      const int slot = ep.task_o[t];
+      const int64_t e2 = H.nbr[(size_t)e * ep.NO + slot];
+      if (e2 < 0) continue;
+      const int rv = ep.task_rv[t], cv = ep.task_cv[t];
+      int ie2[3], co[3] = {0, 0, 0}, ch2 = 0;
+      element_index(H.n, d, e2, ie2);
+      bool same = true;
+      for (int k = 0; k < d; ++k) {
+        co[k] = floordiv2(ie[k] + ep.off[slot][k]) - ie[k] / 2;   // geometric cluster offset
+        ch2 |= (ie2[k] & 1) << k;
+        if (co[k] != 0) same = false;
+      }
+      const double* blk = &H.C[((size_t)e * ep.T + t) * s * s];
+      if (same) {
+        for (int a = 0; a < s; ++a)
+          for (int b2 = 0; b2 < s; ++b2)
+            DC[(size_t)(rv * S2 + ch * s + a) * NB2 + cv * S2 + ch2 * s + b2] += blk[a * s + b2];
+        continue;
+      }
+      int o2 = -1;
+      for (int o = 0; o < cp.NO; ++o)
+        if (cp.off[o][0] == co[0] && cp.off[o][1] == co[1] && cp.off[o][2] == co[2]) o2 = o;
+      int t2 = -1;
+      for (int u = 0; u < cp.T && o2 >= 0; ++u)
+        if (cp.task_rv[u] == rv && cp.task_cv[u] == cv && cp.task_o[u] == o2) t2 = u;
+      if (t2 < 0) {
+        err = "a coupling between clusters has no task in the cluster pattern";
+        return STK_ERR_INVALID_ARG;
+      }
+      double* CC = &HC.C[((size_t)C * cp.T + t2) * S2 * S2];
+      for (int a = 0; a < s; ++a)
+        for (int b2 = 0; b2 < s; ++b2) CC[(size_t)(ch * s + a) * S2 + ch2 * s + b2] += blk[a * s + b2];
+    }
+  }
+  return STK_OK;
+}
+
+}  // namespace stk

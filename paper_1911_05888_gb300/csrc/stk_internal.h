@@ -232,6 +232,17 @@ struct Ctx {
   int persist_level[4] = {-1, -1, -1, -1};  // first level of the program, per storage precision
   CyclePhase* persist_prog[4] = {nullptr, nullptr, nullptr, nullptr};
   int persist_nphase[4] = {0, 0, 0, 0};
+  // element clustering of level 0 (2D, p = 1): requested, and in effect; the
+  // cluster level's pattern, host blocks, device records and vectors
+  // (cluster layout; ctmp in element layout)
+  int cluster_req = 0, cluster_on = 0;
+  Pattern cpat{};
+  HostLevel chost;
+  DevLevel cdev;
+  void* cvx[2] = {nullptr, nullptr};
+  void* cvb[2] = {nullptr, nullptr};
+  void* cvr[2] = {nullptr, nullptr};
+  void* ctmp[2] = {nullptr, nullptr};
   // several right-hand sides (interleaved; nr = 4 or 8 once allocated)
   int mr_nr = 0;
   double *mX = nullptr, *mB = nullptr, *mR = nullptr;   // level-0 FP64
@@ -293,6 +304,8 @@ int pseudo_inverse_jacobi(int n, std::vector<double>& A, std::vector<double>& pi
 void element_index(const int* n, int d, int64_t e, int* idx);
 void face_points(const Ctx& c, int kind, std::vector<double>& xyz, std::vector<double>* nrm);
 int assemble_rhs_host(const Ctx& c, const double* f_vol, const double* bdata, double* b);
+int build_cluster_level(const Ctx& c, const HostLevel& H, const Pattern& ep, const Pattern& cp, HostLevel& HC,
+                        std::string& err);
 
 
 // ---- kernels.cu / learn.cu launchers ------------------------------------------
@@ -374,6 +387,8 @@ cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int p
 void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages);
 
 cudaError_t launch_fp64_fma(int blocks, int iters, double* out, cudaStream_t st);
+cudaError_t launch_cluster_permute(int vec64, int n0, int n1, int s, int nvar, int to_cluster, const void* in,
+                                   void* out, cudaStream_t st);
 cudaError_t launch_coarse_cycle(const Pattern& pat, int storage, const CyclePhase* phases, int nphase,
                                 GridBarrierWords* gb, int* err, long long limit, int grid, cudaStream_t st);
 cudaError_t launch_batch_solve(const BatchProblem* probs, int nprob, const BatchStep* steps, int nsteps,
@@ -388,6 +403,8 @@ cudaError_t launch_barrier_selftest(GridBarrierWords* gb, int* err, long long li
 // level l of c, on the kernel variant the context's tuning picks for it.
 cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, const void* mat, const void* b,
                         void* x, void* r, cudaStream_t st);
+cudaError_t run_element_on(Ctx& c, const Pattern& pat, DevLevel& D, int prec, int mode, int pos0, int npos,
+                           const void* mat, const void* b, void* x, void* r, cudaStream_t st);
 
 }  // namespace stk
 

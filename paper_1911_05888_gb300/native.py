@@ -21,7 +21,7 @@ BC_PERIODIC, BC_DIRICHLET, BC_STRESS = 0, 1, 2
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 RICHARDSON, FGMRES, FGMRES_IR = 0, 1, 2
 PTS_VOLUME, PTS_INTERIOR_FACE, PTS_BOUNDARY_FACE = 0, 1, 2
-INFO_BOTTOM_SOLVER, INFO_BOTTOM_UNKNOWNS, INFO_COLOURS, INFO_DEVICE_BYTES = 0, 1, 2, 3
+INFO_BOTTOM_SOLVER, INFO_BOTTOM_UNKNOWNS, INFO_COLOURS, INFO_DEVICE_BYTES, INFO_CLUSTERS = 0, 1, 2, 3, 4
 BOTTOM_JACOBI, BOTTOM_HOST_QR, BOTTOM_CUSOLVER = 0, 1, 2
 COLOURS_AUTO, COLOURS_PARITY, COLOURS_CHECKERBOARD = 0, 1, 2
 
@@ -94,6 +94,7 @@ SIGNATURES = {
     "stk_learn_history": [_vp, _c_int_p, _c_dbl_p, ctypes.c_int, _c_int_p, _c_dbl_p],
     "stk_learn_error_state": [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float)],
     "stk_set_persistent": [_vp, ctypes.c_int, ctypes.c_int],
+    "stk_set_clusters": [_vp, ctypes.c_int],
     "stk_solve_batch_persistent": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), _c_dbl_p, _vp],
@@ -260,6 +261,11 @@ class Context:
         """gamma coarse visits per level (1 V-cycle, 2 W-cycle); smoothing
         counts nu * growth^level, at most max(nu, max_sweeps)."""
         self._check(self.lib.stk_set_cycle_shape(self.h, gamma, growth, max_sweeps), "stk_set_cycle_shape")
+
+    def set_clusters(self, on):
+        """Smooth level 0 with 2 x 2 element clusters (2D, p = 1); takes
+        effect at the next setup."""
+        self._check(self.lib.stk_set_clusters(self.h, 1 if on else 0), "stk_set_clusters")
 
     def set_persistent(self, max_elements, ctas_per_sm=1):
         """Run the levels of at most max_elements elements (below level 0) as

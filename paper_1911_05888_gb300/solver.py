@@ -10,7 +10,7 @@ from .problems import PERIODIC, DIRICHLET, STRESS
 
 class StokesMG:
     def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True, shape=None,
-                 colouring=native.COLOURS_AUTO):
+                 colouring=native.COLOURS_AUTO, clusters=False):
         self.prob = prob
         self.ctx = native.Context(device)
         d = prob.d
@@ -35,6 +35,7 @@ class StokesMG:
         if shape is not None:
             self.ctx.set_cycle_shape(*shape)
         self.ctx.set_colouring(colouring)
+        self.ctx.set_clusters(clusters)
         if setup:
             self.ctx.setup()
             self.nlevels, self.ne_levels, self.nb, self.n_snapped = self.ctx.sizes()
