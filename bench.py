@@ -62,6 +62,9 @@ def parse():
                     help="levels below level 0 with at most this many elements run as one persistent "
                          "cooperative launch per cycle (0: one launch per step)")
     ap.add_argument("--persistent-ctas", type=int, default=1, help="CTAs per SM of the persistent launch")
+    ap.add_argument("--bottom-max", type=int, default=0,
+                    help="stop the hierarchy at the first coarse level with at most this many unknowns "
+                         "(0: full depth)")
     ap.add_argument("--cycle-shape", default="1,1,64",
                     help="gamma,growth,max_sweeps: 1,1,64 = V-cycle, 2,1,64 = W-cycle, 1,2,N = variable V-cycle")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides solved together (1..8)")
@@ -111,6 +114,7 @@ def config(args, prob):
             "dofs": prob.n_dofs, "nu": [args.nu, args.nu if args.nu2 is None else args.nu2], "rtol": 1e-10,
             "outer": "%s(%d)" % (args.solver, args.restart) if args.solver != "richardson" else "richardson",
             "cycle_shape": shape_of(args), "persistent_coarse": [args.persistent, args.persistent_ctas],
+            "bottom_max_unknowns": args.bottom_max,
             "cache": "inputs larger than L2 (element blocks >= 3.6 GB per solve)",
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -463,9 +467,9 @@ def run_native(args):
 
     t0 = time.perf_counter()
     nu2 = args.nu if args.nu2 is None else args.nu2
-    mg = StokesMG(prob, precision=prec, device=local, nu=(args.nu, nu2))
+    mg = StokesMG(prob, precision=prec, device=local, nu=(args.nu, nu2), bottom_max=args.bottom_max)
     setup_s = time.perf_counter() - t0
-    mg64 = StokesMG(prob, precision=native.FP64, device=local, nu=(args.nu, args.nu)) \
+    mg64 = StokesMG(prob, precision=native.FP64, device=local, nu=(args.nu, args.nu), bottom_max=args.bottom_max) \
         if (prec != native.FP64 or nu2 != args.nu) else mg
     # launch shapes picked by the library's autotuner (outside the timed region)
     mg.ctx.set_cycle_shape(*shape_of(args))

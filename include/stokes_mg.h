@@ -193,6 +193,15 @@ int stk_set_persistent(stk_ctx* ctx, int max_elements, int ctas_per_sm);
  */
 int stk_set_clusters(stk_ctx* ctx, int on);
 /*
+ * Earlier bottom level (Section 3 leaves the depth of the hierarchy open;
+ * Algorithm 1 only needs an exact coarsest solve): the hierarchy stops at the
+ * first level below level 0 with at most max_unknowns unknowns, which is then
+ * solved by the dense eigen pseudo-inverse (cuSOLVER above 1200 unknowns).
+ * 0 (default): coarsen while every n_k is even and above 2.  Takes effect at
+ * the next stk_setup.  Errors: STK_ERR_INVALID_ARG outside 0..20000.
+ */
+int stk_set_bottom(stk_ctx* ctx, int64_t max_unknowns);
+/*
  * Self-test of the bounded grid barrier (a diagnostic, no solver state is
  * touched): a cooperative launch of the persistent cycle's grid passes four
  * barriers; with absent >= 0 that CTA returns at once and never arrives, so

@@ -1621,6 +1621,14 @@ int stk_set_colouring(stk_ctx* c, int mode) {
   });
 }
 
+int stk_set_bottom(stk_ctx* c, int64_t max_unknowns) {
+  return guard(c, [&]() -> int {
+    if (max_unknowns < 0 || max_unknowns > 20000) return fail(c, STK_ERR_INVALID_ARG, "bottom size out of 0..20000");
+    c->bottom_max = max_unknowns;
+    return STK_OK;
+  });
+}
+
 int stk_set_clusters(stk_ctx* c, int on) {
   return guard(c, [&]() -> int {
     if (on != 0 && on != 1) return fail(c, STK_ERR_INVALID_ARG, "clusters: 0 or 1");

@@ -1406,6 +1406,9 @@ int setup_host(Ctx& c) {
     bool stop = false;
     for (int k = 0; k < d; ++k)
       if (F.n[k] % 2 == 1 || F.n[k] <= 2) stop = true;
+    // an earlier bottom: this level is small enough for the dense eigen
+    // pseudo-inverse (and is not the finest level)
+    if (c.host.size() > 1 && c.bottom_max > 0 && (int64_t)F.ne * c.nb <= c.bottom_max) stop = true;
     if (stop) break;
     HostLevel Cl;
     Cl.ne = 1;

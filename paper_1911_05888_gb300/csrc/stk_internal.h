@@ -227,6 +227,10 @@ struct Ctx {
   // persistent coarse cycle: levels of at most persist_max elements (0: off)
   // run inside one cooperative launch of persist_ctas CTAs per SM
   int persist_max = 0, persist_ctas = 1;
+  // the hierarchy stops at the first level below level 0 with at most this
+  // many unknowns (0: coarsen until an axis is odd or 2, as Algorithm 1's
+  // hierarchy does)
+  int64_t bottom_max = 0;
   long long barrier_limit = 2000000000LL;   // clock ticks a grid-barrier wait may take (about 1 s)
   GridBarrierWords* gbar = nullptr;
   int persist_level[4] = {-1, -1, -1, -1};  // first level of the program, per storage precision

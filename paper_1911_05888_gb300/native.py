@@ -95,6 +95,7 @@ SIGNATURES = {
     "stk_learn_error_state": [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float)],
     "stk_set_persistent": [_vp, ctypes.c_int, ctypes.c_int],
     "stk_set_clusters": [_vp, ctypes.c_int],
+    "stk_set_bottom": [_vp, ctypes.c_int64],
     "stk_solve_batch_persistent": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), _c_dbl_p, _vp],
@@ -261,6 +262,11 @@ class Context:
         """gamma coarse visits per level (1 V-cycle, 2 W-cycle); smoothing
         counts nu * growth^level, at most max(nu, max_sweeps)."""
         self._check(self.lib.stk_set_cycle_shape(self.h, gamma, growth, max_sweeps), "stk_set_cycle_shape")
+
+    def set_bottom(self, max_unknowns):
+        """Stop the hierarchy at the first coarse level with at most
+        max_unknowns unknowns (0: full depth); takes effect at the next setup."""
+        self._check(self.lib.stk_set_bottom(self.h, int(max_unknowns)), "stk_set_bottom")
 
     def set_clusters(self, on):
         """Smooth level 0 with 2 x 2 element clusters (2D, p = 1); takes

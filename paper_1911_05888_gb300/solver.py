@@ -10,7 +10,7 @@ from .problems import PERIODIC, DIRICHLET, STRESS
 
 class StokesMG:
     def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True, shape=None,
-                 colouring=native.COLOURS_AUTO, clusters=False):
+                 colouring=native.COLOURS_AUTO, clusters=False, bottom_max=0):
         self.prob = prob
         self.ctx = native.Context(device)
         d = prob.d
@@ -36,6 +36,7 @@ class StokesMG:
             self.ctx.set_cycle_shape(*shape)
         self.ctx.set_colouring(colouring)
         self.ctx.set_clusters(clusters)
+        self.ctx.set_bottom(bottom_max)
         if setup:
             self.ctx.setup()
             self.nlevels, self.ne_levels, self.nb, self.n_snapped = self.ctx.sizes()

@@ -1017,3 +1017,34 @@ def test_multiphase_extreme_viscosity_ratios(name):
         np.testing.assert_allclose(eg, eo, rtol=1e-6)
     finally:
         gpu.close()
+
+
+@pytest.mark.parametrize("name,bottom,levels", [("stress16p3", 3072, 2), ("periodic16p2", 1728, 2),
+                                                ("dirichlet-rect", 648, 2)])
+def test_earlier_bottom_matches_oracle(name, bottom, levels):
+    """A hierarchy stopped early (stk_set_bottom): the bottom level is the
+    first coarse level with at most `bottom` unknowns, solved by the dense
+    pseudo-inverse (cuSOLVER above 1200 unknowns), and ten V-cycle iterates
+    equal the oracle's with the same number of levels to 1e-12."""
+    prob = CASES[name]()
+    gpu = StokesMG(prob, bottom_max=bottom)
+    orc = oracle_for(prob, max_levels=levels)
+    try:
+        assert gpu.nlevels == len(orc.levels) == levels
+        nbot = orc.levels[-1].ne * orc.levels[-1].nb
+        assert gpu.ctx.info(native.INFO_BOTTOM_UNKNOWNS) == nbot <= bottom
+        assert gpu.ctx.info(native.INFO_BOTTOM_SOLVER) == (native.BOTTOM_CUSOLVER if nbot > 1200 else
+                                                           native.BOTTOM_HOST_QR if nbot > 300 else native.BOTTOM_JACOBI)
+        assert gpu.n_snapped == orc.kernel_dim_bottom
+        Z = trivial_kernel(prob, orc)
+        b = np.random.default_rng(21).uniform(-1, 1, prob.n_dofs)
+        b -= Z @ (Z.T @ b)
+        xd = torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda")
+        xo = np.zeros(prob.n_dofs)
+        for k in range(10):
+            gpu.ctx.vcycle(xd, dev(b))
+            orc.vcycle(xo, b)
+            xg = xd.cpu().numpy()
+            assert rel(xg - Z @ (Z.T @ xg), xo - Z @ (Z.T @ xo)) <= 1e-12, k
+    finally:
+        gpu.close()
