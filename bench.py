@@ -439,6 +439,17 @@ def learned_arm(mg, args, stream, prec, objective=0):
         out["learned"].update({"accepted": int(acc), "rejected": int(rej), "kappa": kappa,
                                "decisions_last_solve": [int(v) for v in dec],
                                "ratios_last_solve": [round(float(v), 4) for v in ratio]})
+        if args.nu > 1:
+            # the correction in place of one post-smoothing sweep: V(nu, nu-1) + correction
+            mg.ctx.set_cycle(args.nu, args.nu - 1, prec)
+            mg.ctx.learn_enable(True)
+            out["learned_one_fewer_post_sweep"] = timed()
+            acc, rej = mg.ctx.learn_stats()
+            dec, ratio, kappa = mg.ctx.learn_history()
+            out["learned_one_fewer_post_sweep"].update({"accepted": int(acc), "rejected": int(rej), "kappa": kappa,
+                                                        "decisions_last_solve": [int(v) for v in dec]})
+            mg.ctx.learn_enable(False)
+            out["plain_one_fewer_post_sweep"] = timed()
     finally:
         if learn_ready:
             mg.ctx.learn_enable(False)

@@ -473,7 +473,9 @@ int stk_set_df_matvec(stk_ctx* ctx, int on);
  * norm, and the convergence test ||b - A x|| <= rtol ||b||), and step k of
  * all problems runs together -- a work list of (problem, step, element or
  * coarse element or chunk) units -- with a bounded grid barrier between
- * steps.  A problem that converged (or diverged: non-finite, or 1e6 times its
+ * steps; each unit is one warp's (an element on the warp-per-element body of
+ * the large launches, a coarse element, a bottom row, or a vector chunk).
+ * A problem that converged (or diverged: non-finite, or 1e6 times its
  * initial residual) stops taking part; the launch ends when none is left or
  * after maxit iterations.  Every context must be set up with FP32 cycles,
  * distinct, on one device, for a degree with 4, 8, 9, 16 or 27 scalar modes
@@ -482,8 +484,9 @@ int stk_set_df_matvec(stk_ctx* ctx, int on);
  * and b[i] are device arrays of the caller.  iters_out, status_out (n
  * entries) and hist (n x (maxit + 1): relative residual before the first and
  * after each iteration, zero beyond the last) may be NULL.  Every element of
- * every level runs on the one-CTA-per-element body, so results agree with
- * stk_solve's to rounding, not bit for bit.  The workspace (work list,
+ * every level runs on the warp-per-element body, so results agree with
+ * stk_solve's (whose coarse levels take the one-CTA-per-element body) to
+ * rounding, not bit for bit.  The workspace (work list,
  * partial sums) is allocated per call.  Errors: STK_ERR_INVALID_ARG,
  * STK_ERR_NOT_SETUP, STK_ERR_DIVERGED (status_out says which problem),
  * STK_ERR_TIMEOUT (a barrier wait reached its bound; messages in

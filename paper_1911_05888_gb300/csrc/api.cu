@@ -2985,7 +2985,7 @@ int stk_solve_batch_persistent(stk_ctx* const* ctx, int n, double* const* x, con
     std::vector<BatchStep> steps(nsteps);
     std::vector<BatchTask> tasks;
     auto units_of = [](const CyclePhase& ph) -> int64_t {
-      return ph.op == PHASE_BOTTOM ? (ph.n + 7) / 8 : ph.n;   // bottom: one row per warp, 8 warps per CTA
+      return ph.n;   // every unit is one warp's: element, coarse element, bottom row or vector chunk
     };
     for (size_t k = 0; k < nsteps; ++k) {
       steps[k].t0 = (int)tasks.size();

@@ -332,6 +332,145 @@ __device__ __forceinline__ void wide_element(const Pattern& pat, const WideGeom&
                                         false);
 }
 
+// ---- one warp per element (the bandwidth kernel of large launches) ------------
+constexpr int kWarps = 8;   // warps per CTA of element_warp_kernel
+
+template <typename TS>
+struct WarpGeom {
+  int NCG, CW, XS, words;  // column groups, columns per group, X slot stride, TA words per warp
+};
+
+template <typename TS>
+__host__ __device__ inline WarpGeom<TS> warp_geometry(const Pattern& pat) {
+  constexpr int V = StorageTraits<TS>::V;
+  WarpGeom<TS> g;
+  const int NRV = pat.NBP / V;
+  g.NCG = (32 / NRV) > 0 ? (32 / NRV) : 1;
+  g.CW = (pat.nb + g.NCG - 1) / g.NCG;
+  g.XS = pat.s + 1;
+  int w = pat.NG * g.XS + pat.TRP + 2 * pat.NBP + g.NCG * pat.NBP;
+  if (kScaledStorage<TS>) w += task_scale_stride(pat);
+  g.words = (w + 3) / 4 * 4;
+  return g;
+}
+
+// One element (position pos) of a colour step (MODE_GS) or residual
+// (MODE_RESID) by one warp: the gathered neighbour values and partial sums in
+// the warp's own shared-memory slice (wg.words accumulators), each lane
+// streaming V consecutive task-rows column by column with 16-byte evict-first
+// loads, then the dense block in column groups; only __syncwarp.  b, x and
+// rout carry no __restrict__ (the persistent batch writes them in earlier
+// steps of the same launch).
+template <typename TS, typename TX, int S>
+__device__ __forceinline__ void warp_element(const Pattern& pat, const WarpGeom<TS>& wg, int mode, int pos,
+                                             const int* __restrict__ perm, const int* __restrict__ nbr,
+                                             const TS* __restrict__ cpl, const TS* __restrict__ mat,
+                                             const float* __restrict__ tsc, const float* __restrict__ rsc,
+                                             const TX* b, TX* x, TX* rout, void* warp_smem) {
+  using Tr = StorageTraits<TS>;
+  using TA = typename Tr::Acc;
+  constexpr int V = Tr::V;
+  const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR;
+  const int NRV = NBP / V;
+  const int TP = task_scale_stride(pat);
+  const int lane = threadIdx.x & 31;
+  TA* base = reinterpret_cast<TA*>(warp_smem);
+  TA* Xs = base;
+  TA* part = Xs + pat.NG * wg.XS;
+  TA* g = part + TRP;
+  TA* xi = g + NBP;
+  TA* part2 = xi + NBP;
+  TA* tss = part2 + wg.NCG * NBP;   // task scales (FP16 records only)
+
+  const int e = perm[pos];
+  const int* nbe = nbr + (size_t)pos * pat.NO;
+  for (int i = lane; i < pat.NG * S; i += 32) {
+    const int gi = i / S, ci = i - gi * S;
+    const int j = nbe[pat.g_o[gi]];
+    Xs[gi * wg.XS + ci] = (j >= 0) ? (TA)x[(size_t)j * nb + pat.g_cv[gi] * S + ci] : (TA)0;
+  }
+  for (int i = lane; i < nb; i += 32) {
+    g[i] = (TA)b[(size_t)e * nb + i];
+    if (mode == MODE_RESID) xi[i] = (TA)x[(size_t)e * nb + i];
+  }
+  if constexpr (kScaledStorage<TS>)
+    for (int i = lane; i < pat.T; i += 32) tss[i] = tsc[(size_t)pos * TP + i];
+  __syncwarp();
+  const TS* rec = cpl + (size_t)pos * S * TRP;
+  for (int tv = lane; tv < TRP / V; tv += 32) {
+    const int tr0 = tv * V;
+    const TA* xp[V];
+    TA acc[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int tr = tr0 + j;
+      xp[j] = (tr < TR) ? Xs + pat.task_g[tr / S] * wg.XS : Xs;
+      acc[j] = 0;
+    }
+#pragma unroll
+    for (int ci = 0; ci < S; ++ci) {
+      TA w[V];
+      Tr::load(rec + (size_t)ci * TRP + tr0, w);
+#pragma unroll
+      for (int j = 0; j < V; ++j) acc[j] = fma(w[j], xp[j][ci], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) part[tr0 + j] = acc[j];
+  }
+  __syncwarp();
+  for (int r = lane; r < nb; r += 32) {
+    const int rv = r / S, rr = r - rv * S;
+    TA sum = 0;
+    if constexpr (kScaledStorage<TS>) {
+      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[t * S + rr] * tss[t];
+    } else {
+      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) sum += part[t * S + rr];
+    }
+    g[r] = g[r] - sum;
+  }
+  __syncwarp();
+  const TS* mrec = mat + (size_t)pos * nb * NBP;
+  const TA* vin = (mode == MODE_GS) ? g : xi;
+  // row scales of the FP16 dense block, fetched before its loads (nb <= 128)
+  float rs[4] = {1.f, 1.f, 1.f, 1.f};
+  if constexpr (kScaledStorage<TS>) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (lane + 32 * q < nb) rs[q] = rsc[(size_t)pos * NBP + lane + 32 * q];
+  }
+  for (int u = lane; u < NRV * wg.NCG; u += 32) {
+    const int rvv = u % NRV, cg = u / NRV;
+    const int c0 = cg * wg.CW, c1 = min(nb, c0 + wg.CW);
+    TA acc[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) acc[j] = 0;
+#pragma unroll 4
+    for (int ci = c0; ci < c1; ++ci) {
+      TA w[V];
+      Tr::load(mrec + (size_t)ci * NBP + rvv * V, w);
+      const TA v = vin[ci];
+#pragma unroll
+      for (int j = 0; j < V; ++j) acc[j] = fma(w[j], v, acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) part2[cg * NBP + rvv * V + j] = acc[j];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = lane + 32 * q;
+    if (r >= nb) break;
+    TA sum = 0;
+    for (int cg = 0; cg < wg.NCG; ++cg) sum += part2[cg * NBP + r];
+    if constexpr (kScaledStorage<TS>) sum *= rs[q];
+    if (mode == MODE_GS)
+      x[(size_t)e * nb + r] = (TX)sum;
+    else
+      rout[(size_t)e * nb + r] = (TX)(g[r] - sum);
+  }
+  __syncwarp();
+}
+
 // ---- restriction / prolongation of one coarse element -------------------------
 // P[ch][a][b]: fine coefficient a of coarse mode b for child ch (P_f of the
 // scalar injection; the (d+1) variables share it).  One CTA per coarse

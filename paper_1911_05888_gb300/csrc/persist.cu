@@ -187,26 +187,78 @@ cudaError_t launch_coarse_t(const Pattern& pat, const CyclePhase* phases, int np
 }
 
 // ---- batched outer iteration ----------------------------------------------------
-// One element unit of a batch step: the cycle's colour step or residual on the
-// FP32 records, or the outer FP64 residual on the FP64 records.
+// Every unit of a batch step is one warp's: an element (the warp-per-element
+// body of the bandwidth kernel), a coarse element of a transfer, a bottom
+// row, or a chunk of kBatchChunk vector entries.  Each warp owns a slice of
+// the CTA's shared memory.
 template <int S>
-__device__ __forceinline__ void batch_element(const Pattern& pat, int op, const CyclePhase& P, int pos,
-                                              unsigned char* smem) {
+__device__ __forceinline__ void batch_element(const Pattern& pat, int op, const CyclePhase& P, int pos, void* wsm) {
   if (op == PHASE_RESID64) {
-    const WideGeom wg = wide_geometry<double>(pat);
-    wide_element<double, double, S>(pat, wg, MODE_RESID, pos, P.perm, P.nbr, (const double*)P.cpl,
+    const WarpGeom<double> wg = warp_geometry<double>(pat);
+    warp_element<double, double, S>(pat, wg, MODE_RESID, pos, P.perm, P.nbr, (const double*)P.cpl,
                                     (const double*)P.mat, nullptr, nullptr, (const double*)P.b, (double*)P.x,
-                                    (double*)P.r, smem);
+                                    (double*)P.r, wsm);
   } else {
-    const WideGeom wg = wide_geometry<float>(pat);
-    wide_element<float, float, S>(pat, wg, op == PHASE_GS ? MODE_GS : MODE_RESID, pos, P.perm, P.nbr,
+    const WarpGeom<float> wg = warp_geometry<float>(pat);
+    warp_element<float, float, S>(pat, wg, op == PHASE_GS ? MODE_GS : MODE_RESID, pos, P.perm, P.nbr,
                                   (const float*)P.cpl, (const float*)P.mat, nullptr, nullptr, (const float*)P.b,
-                                  (float*)P.x, (float*)P.r, smem);
+                                  (float*)P.x, (float*)P.r, wsm);
   }
 }
 
+// r_c = I^T r on coarse element C by one warp (the sums of restrict_coarse,
+// in the same order)
+__device__ __forceinline__ void warp_restrict(int d, int s, int nb, int nc0, int nc1, int nf0, int nf1, int64_t C,
+                                              const float* __restrict__ P, const float* r, float* rc, float* rs,
+                                              int lane) {
+  const int nch = 1 << d;
+  const int I0 = (int)(C % nc0), I1 = (int)((C / nc0) % nc1), I2 = (int)(C / ((int64_t)nc0 * nc1));
+  __syncwarp();
+  for (int i = lane; i < nch * nb; i += 32) {
+    const int ch = i / nb, k = i - ch * nb;
+    const int f0 = 2 * I0 + (ch & 1), f1 = 2 * I1 + ((ch >> 1) & 1), f2 = 2 * I2 + ((ch >> 2) & 1);
+    const int64_t f = (d == 2) ? f0 + (int64_t)nf0 * f1 : f0 + (int64_t)nf0 * (f1 + (int64_t)nf1 * f2);
+    rs[i] = r[f * nb + k];
+  }
+  __syncwarp();
+  for (int o = lane; o < nb; o += 32) {
+    const int v = o / s, bm = o - v * s;
+    float acc = 0;
+    for (int ch = 0; ch < nch; ++ch) {
+      const float* pc = P + ch * s * s + bm;
+      const float* rr = rs + ch * nb + v * s;
+      for (int a = 0; a < s; ++a) acc += pc[a * s] * rr[a];
+    }
+    rc[C * nb + o] = acc;
+  }
+  __syncwarp();
+}
+
+// x += I x_c on the children of C by one warp (the sums of prolong_coarse)
+__device__ __forceinline__ void warp_prolong(int d, int s, int nb, int nf0, int nf1, int nc0, int nc1, int64_t C,
+                                             const float* __restrict__ PT, const float* xc, float* x, float* xs,
+                                             int lane) {
+  const int nch = 1 << d;
+  const int I0 = (int)(C % nc0), I1 = (int)((C / nc0) % nc1), I2 = (int)(C / ((int64_t)nc0 * nc1));
+  __syncwarp();
+  for (int i = lane; i < nb; i += 32) xs[i] = xc[C * nb + i];
+  __syncwarp();
+  for (int o = lane; o < nch * nb; o += 32) {
+    const int ch = o / nb, va = o - ch * nb;
+    const int v = va / s, am = va - v * s;
+    const int f0 = 2 * I0 + (ch & 1), f1 = 2 * I1 + ((ch >> 1) & 1), f2 = 2 * I2 + ((ch >> 2) & 1);
+    const int64_t f = (d == 2) ? f0 + (int64_t)nf0 * f1 : f0 + (int64_t)nf0 * (f1 + (int64_t)nf1 * f2);
+    const float* pc = PT + ch * s * s + am;
+    const float* xv = xs + v * s;
+    float acc = 0;
+    for (int bm = 0; bm < s; ++bm) acc += pc[bm * s] * xv[bm];
+    x[f * nb + va] += acc;
+  }
+  __syncwarp();
+}
+
 __device__ __forceinline__ void batch_unit(const BatchProblem& B, const CyclePhase& P, int64_t v, int it, double rtol,
-                                           unsigned char* smem_raw) {
+                                           void* wsm, int lane) {
   const Pattern& pat = B.pat;
   const int d = pat.d, s = pat.s, nb = pat.nb;
   switch (P.op) {
@@ -215,27 +267,26 @@ __device__ __forceinline__ void batch_unit(const BatchProblem& B, const CyclePha
     case PHASE_RESID64: {
       const int pos = P.pos0 + (int)v;
       switch (s) {
-        case 4: batch_element<4>(pat, P.op, P, pos, smem_raw); break;
-        case 8: batch_element<8>(pat, P.op, P, pos, smem_raw); break;
-        case 9: batch_element<9>(pat, P.op, P, pos, smem_raw); break;
-        case 16: batch_element<16>(pat, P.op, P, pos, smem_raw); break;
-        case 27: batch_element<27>(pat, P.op, P, pos, smem_raw); break;
+        case 4: batch_element<4>(pat, P.op, P, pos, wsm); break;
+        case 8: batch_element<8>(pat, P.op, P, pos, wsm); break;
+        case 9: batch_element<9>(pat, P.op, P, pos, wsm); break;
+        case 16: batch_element<16>(pat, P.op, P, pos, wsm); break;
+        case 27: batch_element<27>(pat, P.op, P, pos, wsm); break;
         default: break;
       }
       break;
     }
     case PHASE_RESTRICT:
-      restrict_coarse<float>(d, s, nb, P.dims[0], P.dims[1], P.dims[2], P.dims[3], v, (const float*)P.tr,
-                             (const float*)P.in, (float*)P.out, reinterpret_cast<float*>(smem_raw));
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) ((float*)P.xz)[v * nb + i] = 0.f;
+      warp_restrict(d, s, nb, P.dims[0], P.dims[1], P.dims[2], P.dims[3], v, (const float*)P.tr, (const float*)P.in,
+                    (float*)P.out, (float*)wsm, lane);
+      for (int i = lane; i < nb; i += 32) ((float*)P.xz)[v * nb + i] = 0.f;
       break;
     case PHASE_PROLONG:
-      prolong_coarse<float>(d, s, nb, P.dims[0], P.dims[1], P.dims[2], P.dims[3], v, (const float*)P.tr,
-                            (const float*)P.in, (float*)P.out, reinterpret_cast<float*>(smem_raw));
+      warp_prolong(d, s, nb, P.dims[0], P.dims[1], P.dims[2], P.dims[3], v, (const float*)P.tr, (const float*)P.in,
+                   (float*)P.out, (float*)wsm, lane);
       break;
-    case PHASE_BOTTOM: {
-      const int lane = threadIdx.x & 31;
-      const int64_t row = v * (blockDim.x / 32) + threadIdx.x / 32;
+    case PHASE_BOTTOM: {   // x = A_c^+ b, one row, FP64 accumulation (as bottom_kernel)
+      const int64_t row = v;
       if (row < P.n) {
         const double* pinv = (const double*)P.tr;
         const float* bb = (const float*)P.in;
@@ -249,7 +300,7 @@ __device__ __forceinline__ void batch_unit(const BatchProblem& B, const CyclePha
     case PHASE_CONVERT: {   // cycle right-hand side from the outer residual, zero initial guess
       const int64_t i0 = v * kBatchChunk, i1 = min(B.n0, i0 + kBatchChunk);
       const double* r = (const double*)P.in;
-      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      for (int64_t i = i0 + lane; i < i1; i += 32) {
         ((float*)P.out)[i] = (float)r[i];
         ((float*)P.xz)[i] = 0.f;
       }
@@ -258,28 +309,20 @@ __device__ __forceinline__ void batch_unit(const BatchProblem& B, const CyclePha
     case PHASE_AXPY: {      // x += c (the cycle's FP32 correction into the FP64 iterate)
       const int64_t i0 = v * kBatchChunk, i1 = min(B.n0, i0 + kBatchChunk);
       const float* c = (const float*)P.in;
-      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) ((double*)P.out)[i] += (double)c[i];
+      for (int64_t i = i0 + lane; i < i1; i += 32) ((double*)P.out)[i] += (double)c[i];
       break;
     }
     case PHASE_NORM: {      // partial sum of squares of one chunk, fixed reduction order
-      double* red = reinterpret_cast<double*>(smem_raw);
       const int64_t i0 = v * kBatchChunk, i1 = min(B.n0, i0 + kBatchChunk);
       const double* r = (const double*)P.in;
       double acc = 0.0;
-      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += r[i] * r[i];
-      __syncthreads();
-      red[threadIdx.x] = acc;
-      __syncthreads();
-      for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) B.part[v] = red[0];
-      __syncthreads();
+      for (int64_t i = i0 + lane; i < i1; i += 32) acc += r[i] * r[i];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) B.part[v] = acc;
       break;
     }
     case PHASE_CHECK: {     // ||r|| / ||b|| after this iteration; stop when converged or diverged
-      if (threadIdx.x == 0) {
+      if (lane == 0) {
         const int64_t nch = (B.n0 + kBatchChunk - 1) / kBatchChunk;
         double sum = 0.0;
         for (int64_t c = 0; c < nch; ++c) sum += *((volatile double*)&B.part[c]);
@@ -293,6 +336,7 @@ __device__ __forceinline__ void batch_unit(const BatchProblem& B, const CyclePha
           *((volatile int*)B.active) = 0;
         }
       }
+      __syncwarp();
       break;
     }
     default: break;
@@ -303,23 +347,26 @@ __device__ __forceinline__ void batch_unit(const BatchProblem& B, const CyclePha
 // launch: x <- x + V(0, b - A x) with the V-cycle in FP32 records, the
 // residual in FP64; the steps of one iteration run in order with a grid
 // barrier after each; a problem whose residual reached rtol stops taking part.
-__global__ void __launch_bounds__(kWideNT) batch_solve_kernel(const BatchProblem* __restrict__ probs, int nprob,
+__global__ void __launch_bounds__(kWideNT, 3) batch_solve_kernel(const BatchProblem* __restrict__ probs, int nprob,
                                                               const BatchStep* __restrict__ steps, int nsteps,
                                                               const BatchTask* __restrict__ tasks, int maxit,
-                                                              double rtol, GridBarrierWords* gb, int* err,
+                                                              double rtol, int slice, GridBarrierWords* gb, int* err,
                                                               long long limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_any;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  void* wsm = smem_raw + (size_t)warp * slice;
+  const int64_t gw = (int64_t)blockIdx.x * wpb + warp, nw = (int64_t)gridDim.x * wpb;
   for (int it = 0; it < maxit; ++it) {
     for (int k = 0; k < nsteps; ++k) {
       const BatchStep stp = steps[k];
       int t = stp.t0;
-      for (int64_t u = blockIdx.x; u < stp.units; u += gridDim.x) {
+      for (int64_t u = gw; u < stp.units; u += nw) {
         while (t + 1 < stp.t1 && tasks[t + 1].ustart <= u) ++t;
         const BatchProblem& B = probs[tasks[t].prob];
         if (*((volatile int*)B.active) == 0) continue;
         const CyclePhase P = tasks[t].ph;
-        batch_unit(B, P, u - tasks[t].ustart, it, rtol, smem_raw);
+        batch_unit(B, P, u - tasks[t].ustart, it, rtol, wsm, lane);
       }
       if (!grid_barrier(gb, err, limit)) return;
     }
@@ -335,18 +382,21 @@ __global__ void __launch_bounds__(kWideNT) batch_solve_kernel(const BatchProblem
 
 }  // namespace
 
+// Shared bytes of one warp's slice in the persistent batch.
 size_t batch_smem_bytes(const Pattern& pat) {
-  const WideGeom w32 = wide_geometry<float>(pat), w64 = wide_geometry<double>(pat);
-  size_t smem = std::max(wide_smem_bytes(w32), wide_smem_bytes(w64));
-  smem = std::max(smem, (size_t)(1 << pat.d) * pat.nb * sizeof(float));
-  smem = std::max(smem, (size_t)kWideNT * sizeof(double));
-  return smem;
+  const WarpGeom<float> w32 = warp_geometry<float>(pat);
+  const WarpGeom<double> w64 = warp_geometry<double>(pat);
+  size_t slice = std::max((size_t)w32.words * sizeof(float), (size_t)w64.words * sizeof(double));
+  slice = std::max(slice, (size_t)(1 << pat.d) * pat.nb * sizeof(float));
+  return (slice + 15) / 16 * 16;
 }
 
 cudaError_t launch_batch_solve(const BatchProblem* probs, int nprob, const BatchStep* steps, int nsteps,
                                const BatchTask* tasks, int maxit, double rtol, int smax, size_t smem,
                                GridBarrierWords* gb, int* err, long long limit, int grid, cudaStream_t st) {
   (void)smax;
+  const int slice = (int)smem;                 // per warp
+  smem = (size_t)slice * (kWideNT / 32);       // per CTA
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(batch_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -368,7 +418,8 @@ cudaError_t launch_batch_solve(const BatchProblem* probs, int nprob, const Batch
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, batch_solve_kernel, probs, nprob, steps, nsteps, tasks, maxit, rtol, gb, err, limit);
+  return cudaLaunchKernelEx(&cfg, batch_solve_kernel, probs, nprob, steps, nsteps, tasks, maxit, rtol, slice, gb, err,
+                            limit);
 }
 
 cudaError_t launch_coarse_cycle(const Pattern& pat, int storage, const CyclePhase* phases, int nphase,

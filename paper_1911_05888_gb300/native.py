@@ -607,7 +607,7 @@ def solve_batch(contexts, xs, bs, rtol=1e-10, maxit=200, nrhs=1, inner=3, thread
     return list(it), list(st)
 
 
-def solve_batch_persistent(contexts, xs, bs, rtol=1e-10, maxit=200, ctas_per_sm=1, stream=None):
+def solve_batch_persistent(contexts, xs, bs, rtol=1e-10, maxit=200, ctas_per_sm=3, stream=None):
     """stk_solve_batch_persistent: the whole batch (FP32-cycle contexts) by
     iterative refinement in one cooperative launch.  Returns (iterations,
     status codes, histories [n][maxit+1])."""

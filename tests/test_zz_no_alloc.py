@@ -6,7 +6,8 @@ cudaMalloc); its scratch is a fixed static device array.  This file is named so
 that pytest collects it last.  It checks, through the C ABI and on two calls in
 a row (the second with different inputs, so stale scratch would show), that the
 residual and its squared norm equal those of stk_residual within the 1e-12
-relative tolerance the other FP64 tests use.
+relative tolerance the other FP64 tests use, and that the residual is the
+oracle's b - A x to the same tolerance.
 """
 import numpy as np
 import pytest
@@ -20,8 +21,10 @@ pytestmark = pytest.mark.gpu
 
 
 def test_static_scratch_residual_matches_allocating_entry_point():
+    from oracle import multigrid
     prob = P.stress_variable_mu_2d(n=16, p=3)
     mg = StokesMG(prob)
+    A = multigrid.Multigrid(prob).A
     rng = np.random.default_rng(17)
     b = torch.from_numpy(rng.uniform(-1, 1, prob.n_dofs)).cuda()
     for call in range(2):
@@ -35,4 +38,6 @@ def test_static_scratch_residual_matches_allocating_entry_point():
         r_ref_h, r_h = r_ref.cpu().numpy(), r.cpu().numpy()
         assert np.linalg.norm(r_h - r_ref_h) <= 1e-12 * np.linalg.norm(r_ref_h)
         assert abs(np.sqrt(norm2.item()) - nrm_ref) <= 1e-12 * nrm_ref
+        r_orc = b.cpu().numpy() - A @ x.cpu().numpy()
+        assert np.linalg.norm(r_h - r_orc) <= 1e-12 * np.linalg.norm(r_orc)
     mg.close()
