@@ -872,6 +872,7 @@ def run_batch(args):
     el, units, its, launches, e2e_s, nbytes, worst = measure(gpus, args.steps, args.warmup,
                                                              persistent=bool(args.batch_persistent))
     clk = clocks.stop()
+    lib_bytes = sum(g.ctx.info(native.INFO_DEVICE_BYTES) for g in gpus)   # after the solves' work buffers
     # the same batch driven by one host thread: problems one after another
     el_seq = measure(gpus, 1, 0, threads=1)[0] if not args.batch_persistent else None
     dofs = sum(g.prob.n_dofs for g in gpus)
@@ -904,6 +905,9 @@ def run_batch(args):
         "e2e": {"value": units / e2e_s, "unit": "DOF-cycles/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_s / args.steps * 1e3},
         "sequential_ms_per_step": el_seq * 1e3 if el_seq is not None else None,
+        "device_gb": {"library_records_and_vectors": round(lib_bytes / 1e9, 1),
+                      "peak_allocated_by_torch": round(torch.cuda.max_memory_allocated() / 1e9, 1),
+                      "device_total": round(torch.cuda.get_device_properties(0).total_memory / 1e9, 1)},
         "plain_fp64": plain, "gpu_launches": int(launches), "clocks": clk}))
 
 

@@ -19,12 +19,15 @@ from oracle import multigrid  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
+# V(3,3), the paper's cycle: with V(1,1) plain iterative refinement does not
+# contract on the periodic p = 1 problem (the oracle's diverges as well, with or
+# without clusters), although GMRES preconditioned by the same cycle does.
 CASES = {
     "vs-dirichlet-stress-p1": lambda: P.generic(2, 16, 1, 1, [P.DIRICHLET] * 3 + [P.STRESS],
-                                                exact=P.paper_solution(2, 1)),
-    "std-periodic-p1": lambda: P.generic(2, 16, 1, 0, [P.PERIODIC] * 4, exact=P.paper_solution(2, 0)),
+                                                exact=P.paper_solution(2, 1), nu=(3, 3)),
+    "std-periodic-p1": lambda: P.generic(2, 16, 1, 0, [P.PERIODIC] * 4, exact=P.paper_solution(2, 0), nu=(3, 3)),
     "std-rect-p1": lambda: P.generic(2, (12, 8), 1, 0, [P.DIRICHLET, P.STRESS, P.DIRICHLET, P.DIRICHLET],
-                                     exact=P.paper_solution(2, 0)),
+                                     exact=P.paper_solution(2, 0), nu=(3, 3)),
 }
 
 
