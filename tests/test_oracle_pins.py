@@ -941,3 +941,78 @@ def test_earlier_bottom_keeps_the_contraction():
     rho_f, _ = full.gmres_rho(x0, maxit=100)
     rho_s, _ = short.gmres_rho(x0, maxit=100)
     assert rho_s <= rho_f * 1.05, (rho_s, rho_f)
+
+
+# ------------------------------------------ cut cells of an embedded circle ----
+
+def _cut_mesh(n=16, q=8):
+    from oracle import cutcell
+    return cutcell, cutcell.CutMesh(cutcell.Circle((0.5, 0.5), 0.25), n, q=q)
+
+
+def test_cut_cells_area_and_perimeter():
+    """Quadrature by dimension reduction: the inside pieces (and uncut inside
+    cells) integrate 1 to the disc's area pi r^2 and the interface rule to the
+    circumference 2 pi r, to 1e-13; the two pieces of every cut cell fill it."""
+    cutcell, m = _cut_mesh()
+    r = 0.25
+    area_in = sum(p["area"] for p in m.pieces if p["phase"] == 1)
+    perim = sum(w.sum() for (_, w, _) in m.interface.values())
+    assert abs(area_in - np.pi * r * r) <= 1e-13
+    assert abs(perim - 2 * np.pi * r) <= 1e-13
+    for (i, j) in m.interface:
+        a = m.pieces[m.piece_of[(i, j, 1)]]["area"] + m.pieces[m.piece_of[(i, j, 2)]]["area"]
+        assert abs(a - m.cell_area) <= 1e-15
+
+
+def test_cut_cells_polynomial_moments_of_the_disc():
+    """Second moments over the disc in closed form: int x^2 = pi r^2 (c_x^2 +
+    r^2/4), int x y = pi r^2 c_x c_y, summed over the inside pieces."""
+    cutcell, m = _cut_mesh(n=20, q=8)
+    c, r = np.array([0.5, 0.5]), 0.25
+    mx2 = sum((p["weights"] * p["points"][:, 0] ** 2).sum() for p in m.pieces if p["phase"] == 1)
+    mxy = sum((p["weights"] * p["points"][:, 0] * p["points"][:, 1]).sum() for p in m.pieces if p["phase"] == 1)
+    assert abs(mx2 - np.pi * r * r * (c[0] ** 2 + r * r / 4)) <= 1e-13
+    assert abs(mxy - np.pi * r * r * c[0] * c[1]) <= 1e-13
+
+
+def test_cut_cells_divergence_theorem_per_piece():
+    """Volume, face and interface rules agree with each other piece by piece:
+    int_P div F = int_{dP} F.n for F = (x^2 y, x y^3), with the piece's faces
+    (their same-phase parts, outward normals) and its arc (normal out of the
+    circle for the inside piece, into it for the outside piece)."""
+    cutcell, m = _cut_mesh(n=12, q=8)
+    F = lambda p: np.stack([p[:, 0] ** 2 * p[:, 1], p[:, 0] * p[:, 1] ** 3], axis=1)
+    divF = lambda p: 2 * p[:, 0] * p[:, 1] + 3 * p[:, 0] * p[:, 1] ** 2
+    for (i, j), (xif, wif, nif) in m.interface.items():
+        clo = m.lo + m.h * np.array([i, j])
+        for ph, sgn in ((1, 1.0), (2, -1.0)):
+            P = m.pieces[m.piece_of[(i, j, ph)]]
+            vol = (P["weights"] * divF(P["points"])).sum()
+            flux = sgn * (wif * (F(xif) * nif).sum(axis=1)).sum()
+            for axis in (0, 1):
+                for side in (0, 1):
+                    fixed = clo[axis] + side * m.h[axis]
+                    o = 1 - axis
+                    parts = cutcell.face_parts(m.circle, clo[o], clo[o] + m.h[o], axis, fixed, 8)
+                    pts, w = parts[ph]
+                    if len(w):
+                        flux += (2 * side - 1) * (w * F(pts)[:, axis]).sum()
+            assert abs(vol - flux) <= 1e-13, (i, j, ph, vol, flux)
+
+
+def test_cut_cells_merging():
+    """Pieces below a quarter of their cell join a same-phase piece across a
+    face of their cell that is not small itself; every element is then at
+    least a quarter of a cell; both phases keep elements on both sides."""
+    cutcell, m = _cut_mesh(n=32, q=6)
+    assert m.merged_into
+    for k, t in m.merged_into.items():
+        p, q_ = m.pieces[k], m.pieces[t]
+        assert p["area"] < 0.25 * m.cell_area <= q_["area"]
+        assert p["phase"] == q_["phase"]
+        (i, j), (ii, jj) = p["cell"], q_["cell"]
+        assert abs(i - ii) + abs(j - jj) == 1
+    reps = set(m.element)
+    assert all(m.element_area(rep) >= 0.25 * m.cell_area for rep in reps)
+    assert {m.pieces[r]["phase"] for r in reps} == {1, 2}
