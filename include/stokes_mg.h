@@ -344,6 +344,31 @@ int stk_prolong(stk_ctx* ctx, int level, const double* xc_dev, double* x_dev, vo
  */
 int stk_host_pseudo_inverse(int n, const double* A, double theta, double* pinv, int* snapped);
 
+/*
+ * Cut cells of an embedded circle (Section 5's circular interface; host only,
+ * no context or device needed): the n x n grid on [lo, hi] (2 entries each)
+ * cut by the circle of centre (cx, cy) and radius r.  Quadrature by dimension
+ * reduction with q Gauss points per sub-interval (height direction per cell
+ * along the larger normal component; chords found analytically); pieces below
+ * merge_fraction of their cell join the same-phase piece across the cell face
+ * they share most with (among neighbours not small themselves); the merged
+ * elements are coloured greedily (elements in the order of their
+ * representative piece, smallest colour not used by an element reachable
+ * through the coupling stencil {|o| <= 1} U {+-2 e_k} of any host cell).
+ * Pieces: every uncut cell, and the inside (phase 1) and outside (phase 2)
+ * parts of every cut cell, ordered by cell (x fastest), inside first.
+ * *npieces: in, the capacity of the output arrays; out, the number of pieces
+ * (call with capacity 0 to size them).  Outputs (may be NULL): cell [np][2],
+ * phase [np], area [np], element [np] (the representative piece of the
+ * element the piece belongs to), colour [np] (of its element),
+ * *interface_length (the interface rule's total weight).  The cut-cell LDG
+ * assembly and solves are not part of the library.  Errors:
+ * STK_ERR_INVALID_ARG (n outside 1..4096, r <= 0, q outside 1..32, empty box).
+ */
+int stk_cut_cells(int n, const double* lo, const double* hi, double cx, double cy, double r, int q,
+                  double merge_fraction, int64_t* npieces, int* cell, int* phase, double* area, int* element,
+                  int* colour, double* interface_length);
+
 /* Bottom solve x = A_c^+ b on the last level (FP64). */
 int stk_bottom_solve(stk_ctx* ctx, const double* b_dev, double* x_dev, void* stream);
 

@@ -244,3 +244,36 @@ class CutMesh:
 
     def element_area(self, rep):
         return sum(p["area"] for k, p in enumerate(self.pieces) if self.element[k] == rep)
+
+
+def greedy_colours(mesh):
+    """Colours of the merged elements (Section 3 asks only for a valid
+    multi-colouring).  Elements in the order of their representative piece
+    (cells lexicographic, x fastest; the inside piece first), each taking the
+    smallest colour not taken by an already coloured element that it may
+    couple with: some host cell of one lies at an offset of the coupling
+    stencil {|o_x|, |o_y| <= 1} or +-2 e_k of some host cell of the other (the
+    reach of the viscous-stress and interphase couplings, reading 18).
+    Returns (representatives in order, colour of each)."""
+    reps = sorted(set(mesh.element))
+    cells = {rep: set() for rep in reps}
+    for k, p in enumerate(mesh.pieces):
+        cells[mesh.element[k]].add(p["cell"])
+    stencil = [(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1)] + [(2, 0), (-2, 0), (0, 2), (0, -2)]
+    owner = {}
+    for rep in reps:
+        for c in cells[rep]:
+            owner.setdefault(c, []).append(rep)
+    colour = {}
+    for rep in reps:
+        used = set()
+        for (i, j) in cells[rep]:
+            for di, dj in stencil:
+                for other in owner.get((i + di, j + dj), []):
+                    if other != rep and other in colour:
+                        used.add(colour[other])
+        c = 0
+        while c in used:
+            c += 1
+        colour[rep] = c
+    return reps, np.array([colour[r] for r in reps], dtype=np.int64)

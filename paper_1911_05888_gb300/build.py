@@ -16,6 +16,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 SOURCES = [
     ("setup.cpp", ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-variable"]),
+    ("cutcell.cpp", ["g++", "-O3", "-std=c++17", "-fPIC", "-Wall"]),
     ("kernels.cu", ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                     "--expt-relaxed-constexpr"]),
     ("api.cu", ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]),

@@ -96,6 +96,9 @@ SIGNATURES = {
     "stk_set_persistent": [_vp, ctypes.c_int, ctypes.c_int],
     "stk_set_clusters": [_vp, ctypes.c_int],
     "stk_set_bottom": [_vp, ctypes.c_int64],
+    "stk_cut_cells": [ctypes.c_int, _c_dbl_p, _c_dbl_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                      ctypes.c_int, ctypes.c_double, _c_i64_p, _c_int_p, _c_int_p, _c_dbl_p, _c_int_p, _c_int_p,
+                      _c_dbl_p],
     "stk_solve_batch_persistent": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), _c_dbl_p, _vp],
@@ -627,6 +630,33 @@ def solve_batch_persistent(contexts, xs, bs, rtol=1e-10, maxit=200, ctas_per_sm=
         msg = lib.stk_last_error(contexts[0].h)
         raise StkError("stk_solve_batch_persistent: %s (%s)" % (msg.decode() if msg else "", ERRORS.get(rc, rc)))
     return list(it), list(st), hist
+
+
+def cut_cells(n, centre, radius, q=8, merge_fraction=0.25, lo=(0.0, 0.0), hi=(1.0, 1.0)):
+    """stk_cut_cells (host only): pieces of the n x n grid cut by a circle.
+    Returns dict of arrays cell [np, 2], phase, area, element, colour and the
+    interface length."""
+    lib = load()
+    lo_ = (ctypes.c_double * 2)(*lo)
+    hi_ = (ctypes.c_double * 2)(*hi)
+    npc = ctypes.c_int64(0)
+    rc = lib.stk_cut_cells(n, lo_, hi_, centre[0], centre[1], radius, q, merge_fraction, ctypes.byref(npc),
+                           None, None, None, None, None, None)
+    if rc != STK_OK:
+        raise StkError("stk_cut_cells: %s" % ERRORS.get(rc, rc))
+    m = npc.value
+    cell = np.zeros((m, 2), dtype=np.int32)
+    phase = np.zeros(m, dtype=np.int32)
+    area = np.zeros(m)
+    elem = np.zeros(m, dtype=np.int32)
+    col = np.zeros(m, dtype=np.int32)
+    ilen = ctypes.c_double()
+    rc = lib.stk_cut_cells(n, lo_, hi_, centre[0], centre[1], radius, q, merge_fraction, ctypes.byref(npc),
+                           cell.ctypes.data_as(_c_int_p), phase.ctypes.data_as(_c_int_p), area.ctypes.data_as(_c_dbl_p),
+                           elem.ctypes.data_as(_c_int_p), col.ctypes.data_as(_c_int_p), ctypes.byref(ilen))
+    if rc != STK_OK:
+        raise StkError("stk_cut_cells: %s" % ERRORS.get(rc, rc))
+    return dict(cell=cell, phase=phase, area=area, element=elem, colour=col, interface_length=ilen.value)
 
 
 def host_pseudo_inverse(A, theta=1e-10):
