@@ -21,7 +21,7 @@ namespace stk {
 // ---------------------------------------------------------------------------
 // Threads
 // ---------------------------------------------------------------------------
-static void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn) {
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn) {
   int nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 32u);
   if (n < 64 || nt == 1) {
     fn(0, n);
@@ -53,7 +53,7 @@ static void legendre(int p, double x, double* P, double* dP) {
   }
 }
 
-static void psi_eval(int p, double x, double* v, double* dv) {
+void psi_eval(int p, double x, double* v, double* dv) {
   double P[32], dP[32];
   legendre(p, x, P, dP);
   for (int l = 0; l <= p; ++l) {
