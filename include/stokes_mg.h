@@ -56,7 +56,7 @@ enum { STK_BC_PERIODIC = 0, STK_BC_DIRICHLET = 1, STK_BC_STRESS = 2 };
 enum { STK_FP64 = 0, STK_FP32 = 1, STK_BF16 = 2, STK_FP16 = 3 };
 
 /* Point sets at which the caller samples coefficients and data. */
-enum { STK_PTS_VOLUME = 0, STK_PTS_INTERIOR_FACE = 1, STK_PTS_BOUNDARY_FACE = 2 };
+enum { STK_PTS_VOLUME = 0, STK_PTS_INTERIOR_FACE = 1, STK_PTS_BOUNDARY_FACE = 2, STK_PTS_INTERFACE = 3 };
 
 typedef struct stk_ctx stk_ctx;
 
@@ -361,13 +361,58 @@ int stk_host_pseudo_inverse(int n, const double* A, double theta, double* pinv, 
  * (call with capacity 0 to size them).  Outputs (may be NULL): cell [np][2],
  * phase [np], area [np], element [np] (the representative piece of the
  * element the piece belongs to), colour [np] (of its element),
- * *interface_length (the interface rule's total weight).  The cut-cell LDG
- * assembly and solves are not part of the library.  Errors:
+ * *interface_length (the interface rule's total weight).  A context solves
+ * on these elements after stk_set_levelset_circle.  Errors:
  * STK_ERR_INVALID_ARG (n outside 1..4096, r <= 0, q outside 1..32, empty box).
  */
 int stk_cut_cells(int n, const double* lo, const double* hi, double cx, double cy, double r, int q,
                   double merge_fraction, int64_t* npieces, int* cell, int* phase, double* area, int* element,
                   int* colour, double* interface_length);
+
+/*
+ * Embedded circle (Section 5's curved interface; the multi-phase problems of
+ * Section 6): the 2D n x n mesh of stk_set_mesh (square cells, Dirichlet on
+ * every side) is cut by the circle of centre (cx, cy) and radius r into
+ * phase 1 (inside) and phase 2 (outside).  The cells' pieces carry the
+ * quadrature of stk_cut_cells with q = 2p + 2 points per sub-interval, pieces
+ * below a quarter of their cell are merged (stk_cut_cells with merge fraction
+ * 0.25), and each merged element takes the tensor Legendre basis Q_p on its
+ * bounding box (the union of its host cells), so element mass matrices are
+ * dense and vectors stay [element][nb] with elements in the order of their
+ * representative piece.  stk_setup then assembles Appendix A on these
+ * elements: intraphase lifts into the right element with the pressure
+ * penalty tau h / mu (eq. eop; eq. taupgeneral with densities), Dirichlet
+ * penalty c_bdry p mu / h, and on the circle the viscosity-upwinded fluxes of
+ * eq. (viscosityupwind) with the penalty 3 p min(mu-, mu+) / h.  The
+ * hierarchy agglomerates the elements of every level by the parent cell of
+ * their anchor cell and by phase until the grid is 2 x 2; a coarse element's
+ * basis lives on its members' union box, the injection onto a member f is the
+ * L2 projection M_f^{-1} int_f phi_f phi_c^T, and the coarse operators follow
+ * Algorithm 2 (Algorithm 3 with densities).  The smoother colours every level
+ * greedily (elements in order, smallest colour not used by an element within
+ * two face / interface steps; on coarse levels by an element holding coupled
+ * members).  Needs stk_set_phases(ctx, 2, NULL, mu_phase, scale) and takes
+ * p = 1..3, FP64 or FP32 blocks; clusters, the persistent launches, several
+ * right-hand sides, the learned smoother and the autotuner are Cartesian
+ * only.  r = 0 returns the context to the Cartesian mesh.  Call after
+ * stk_set_discretisation.  Errors: STK_ERR_INVALID_ARG (not 2D, bad circle).
+ */
+int stk_set_levelset_circle(stk_ctx* ctx, double cx, double cy, double r);
+/* Unsteady cut-cell problem (eq. timedep2): density rho_phase[2] > 0 per phase
+ * and delta > 0; delta = 0 returns to the steady problem (rho_phase unused). */
+int stk_set_phase_density(stk_ctx* ctx, const double* rho_phase, double delta);
+/* Phase (1 or 2) of every point of a point set of a cut-cell mesh (volume and
+ * boundary-face points: the phase of the piece they belong to; interface
+ * points: 1, the inside).  Cut-cell point sets: STK_PTS_VOLUME (the pieces'
+ * volume rules, pieces in order), STK_PTS_INTERIOR_FACE (empty),
+ * STK_PTS_BOUNDARY_FACE (box-face parts, cells in order, per cell the high x
+ * and high y faces then the low faces on the box's low sides), and
+ * STK_PTS_INTERFACE (the circle's rule, cut cells in order, normals out of
+ * the circle).  stk_assemble_rhs2 then takes f_vol [volume point][3] =
+ * (f_1, f_2, fdiv), bdata [boundary point][2] = g, idata [interface
+ * point][4] = (g_1, g_2, h_1, h_2) with g = u(1) - u(2) and
+ * h = sigma(1) n - sigma(2) n. */
+int stk_get_point_phases(stk_ctx* ctx, int kind, int* phase);
 
 /* Bottom solve x = A_c^+ b on the last level (FP64). */
 int stk_bottom_solve(stk_ctx* ctx, const double* b_dev, double* x_dev, void* stream);

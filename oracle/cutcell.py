@@ -65,6 +65,35 @@ def classify(circle, lo, hi):
     return 0
 
 
+def piece_box(circle, lo, hi, ph):
+    """Bounding box (lo, hi) of the phase-ph piece of the cut cell [lo, hi].
+    Along axis k the inside piece (cell and disk) spans the coordinates whose
+    line across the cell meets the disk: |x_k - c_k| < sqrt(r^2 - d^2), d the
+    distance from c to the cell's range on the other axis.  The outside piece
+    loses the coordinates whose whole line lies in the disk, |x_k - c_k| <
+    sqrt(r^2 - D^2) with D the largest distance to that range; its box is the
+    hull of what remains."""
+    lo, hi = np.asarray(lo, float), np.asarray(hi, float)
+    blo, bhi = lo.copy(), hi.copy()
+    c, r = circle.c, circle.r
+    for k in range(2):
+        o = 1 - k
+        if ph == 1:
+            d = max(0.0, lo[o] - c[o], c[o] - hi[o])
+            a = np.sqrt(max(r * r - d * d, 0.0))
+            blo[k] = max(lo[k], c[k] - a)
+            bhi[k] = min(hi[k], c[k] + a)
+        else:
+            D = max(abs(lo[o] - c[o]), abs(hi[o] - c[o]))
+            if r * r > D * D:
+                a = np.sqrt(r * r - D * D)
+                if c[k] - a <= lo[k] < c[k] + a:
+                    blo[k] = c[k] + a
+                if c[k] - a < hi[k] <= c[k] + a:
+                    bhi[k] = c[k] - a
+    return blo, bhi
+
+
 def cell_rules(circle, lo, hi, q):
     """Gauss rules of a cut cell [lo, hi]: (x_in, w_in), (x_out, w_out),
     (x_if, w_if, n_if).  Points [m, 2]."""
@@ -184,11 +213,11 @@ class CutMesh:
                 if k != 0:
                     ph = 1 if k < 0 else 2
                     px, pw = self._full_rule(clo, chi)
-                    self._add(i, j, ph, px, pw)
+                    self._add(i, j, ph, px, pw, (clo, chi))
                     continue
                 (xi, wi), (xo, wo), ifr = cell_rules(circle, clo, chi, q)
-                self._add(i, j, 1, xi, wi)
-                self._add(i, j, 2, xo, wo)
+                self._add(i, j, 1, xi, wi, piece_box(circle, clo, chi, 1))
+                self._add(i, j, 2, xo, wo, piece_box(circle, clo, chi, 2))
                 self.interface[(i, j)] = ifr
         self.cell_area = float(np.prod(self.h))
         self._merge(merge_fraction)
@@ -199,9 +228,10 @@ class CutMesh:
         X, Y = np.meshgrid(xs, ys, indexing="xy")
         return np.stack([X.ravel(), Y.ravel()], axis=1), np.outer(wy, wx).ravel()
 
-    def _add(self, i, j, ph, px, pw):
+    def _add(self, i, j, ph, px, pw, box):
         self.piece_of[(i, j, ph)] = len(self.pieces)
-        self.pieces.append(dict(cell=(i, j), phase=ph, area=float(pw.sum()), points=px, weights=pw))
+        self.pieces.append(dict(cell=(i, j), phase=ph, area=float(pw.sum()), points=px, weights=pw,
+                                box=(np.asarray(box[0], float), np.asarray(box[1], float))))
 
     def shared_face_length(self, i, j, di, dj, ph):
         """Length of the phase-ph part of the face between cell (i, j) and

@@ -4,8 +4,9 @@ Appendix A on the merged elements of cutcell.CutMesh, the same operators as
 ldg.py with every integral taken by the cut-cell quadrature:
 
   * element basis: the tensor Legendre basis Q_p of basis.py on the element's
-    bounding box (the union of its host cells), so that the element mass
-    matrix M_E = int_E phi_a phi_b is a dense block, not |E| I;
+    bounding box (the hull of its pieces' bounding boxes, cutcell.piece_box;
+    an uncut cell's box is the cell), so that the element mass matrix
+    M_E = int_E phi_a phi_b is a dense block, not |E| I;
   * G_k = M^{-1}(B_k + L_k): the broken derivative plus the lift of eq. (gsum)
     -- on an intraphase face (axis-aligned, normal +e_k from the left element
     to the right one) into the right (+) element's rows; on a Dirichlet face
@@ -35,8 +36,8 @@ from .ldg import _Acc
 
 
 class CutElements:
-    """The merged elements of a CutMesh: pieces, host cells, bounding box,
-    phase, and the basis on the box."""
+    """The merged elements of a CutMesh: pieces, host cells, bounding box
+    (hull of the pieces' boxes), phase, and the basis on the box."""
 
     def __init__(self, mesh, p):
         self.mesh, self.p, self.d = mesh, p, 2
@@ -52,9 +53,8 @@ class CutElements:
         self.box_lo = np.zeros((self.ne, 2))
         self.box_hi = np.zeros((self.ne, 2))
         for e in range(self.ne):
-            cells = np.array([mesh.pieces[k]["cell"] for k in self.pieces[e]])
-            self.box_lo[e] = mesh.lo + mesh.h * cells.min(axis=0)
-            self.box_hi[e] = mesh.lo + mesh.h * (cells.max(axis=0) + 1)
+            self.box_lo[e] = np.min([mesh.pieces[k]["box"][0] for k in self.pieces[e]], axis=0)
+            self.box_hi[e] = np.max([mesh.pieces[k]["box"][1] for k in self.pieces[e]], axis=0)
 
     def phi(self, e, x):
         """(Phi [m, s], [dPhi/dx, dPhi/dy]) of element e at points x [m, 2]."""
@@ -113,17 +113,26 @@ def faces(mesh, els, q):
     return intra, bdry, arcs
 
 
-def operators(mesh, p, mu_phase, tau, q=None):
+def operators(mesh, p, mu_phase, tau, q=None, rho_phase=None, delta=None, tau0=None):
     """The Appendix A operators on the cut-cell mesh (Dirichlet on the box),
-    as a dict like ldg.fine_operators (M, Mmu, G, Et, E, s, mesh with ne)."""
+    as a dict like ldg.fine_operators (M, Mmu, G, Et, E, s, mesh with ne).
+    With rho_phase and delta the unsteady problem (eq. timedep2): Mrho = rho M
+    per element, and on intraphase faces the pressure penalty of eq.
+    (taupgeneral), 1 / (h rho / (tau0 delta) + mu / (tau h)), with its two
+    limits tau h / mu (Emu) and tau0 delta / (h rho) (Erho) kept for
+    Algorithm 3."""
     q = 2 * p + 2 if q is None else q
+    unsteady = delta is not None
+    if unsteady:
+        tau0 = 0.5 * p if tau0 is None else tau0
     els = CutElements(mesh, p)
     s, ne = els.s, els.ne
     hk = mesh.h[0]
     mu = lambda e: mu_phase[els.phase[e] - 1]
-    Macc, Mmu_acc = _Acc(), _Acc()
+    rho = lambda e: rho_phase[els.phase[e] - 1]
+    Macc, Mmu_acc, Mrho_acc = _Acc(), _Acc(), _Acc()
     gacc = [_Acc(), _Acc()]
-    Et, E = _Acc(), _Acc()
+    Et, E, Emu, Erho = _Acc(), _Acc(), _Acc(), _Acc()
     for e in range(ne):
         M = np.zeros((s, s))
         B = [np.zeros((s, s)), np.zeros((s, s))]
@@ -136,6 +145,8 @@ def operators(mesh, p, mu_phase, tau, q=None):
                 B[a] += Phi.T @ (w[:, None] * D[a])     # rows: test, cols: trial derivative
         Macc.add([e], [e], M[None])
         Mmu_acc.add([e], [e], (mu(e) * M)[None])
+        if unsteady:
+            Mrho_acc.add([e], [e], (rho(e) * M)[None])
         for a in range(2):
             gacc[a].add([e], [e], B[a][None])
     intra, bdry, arcs = faces(mesh, els, q)
@@ -146,11 +157,18 @@ def operators(mesh, p, mu_phase, tau, q=None):
         # lift into the + (right) element: int (u^+ - u^-) v^+
         gacc[axis].add([eb], [eb], FF(Pb, Pb)[None])
         gacc[axis].add([eb], [ea], -FF(Pb, Pa)[None])
-        tp = tau * hk / mu(ea)
-        for r_, c_, sgn in ((ea, ea, 1), (eb, eb, 1), (ea, eb, -1), (eb, ea, -1)):
-            Pr = Pa if r_ == ea else Pb
-            Pc = Pa if c_ == ea else Pb
-            E.add([r_], [c_], (sgn * tp * FF(Pr, Pc))[None])
+        if unsteady:
+            tmu = tau * hk / mu(ea)
+            trho = tau0 * delta / (hk * rho(ea))
+            tgen = 1.0 / (hk * rho(ea) / (tau0 * delta) + mu(ea) / (tau * hk))
+            coefs = [(E, tgen), (Emu, tmu), (Erho, trho)]
+        else:
+            coefs = [(E, tau * hk / mu(ea))]
+        for acc, tp in coefs:
+            for r_, c_, sgn in ((ea, ea, 1), (eb, eb, 1), (ea, eb, -1), (eb, ea, -1)):
+                Pr = Pa if r_ == ea else Pb
+                Pc = Pa if c_ == ea else Pb
+                acc.add([r_], [c_], (sgn * tp * FF(Pr, Pc))[None])
     for e, axis, side, pts, w in bdry:
         P_, _ = els.phi(e, pts)
         FF = P_.T @ (w[:, None] * P_)
@@ -179,6 +197,8 @@ def operators(mesh, p, mu_phase, tau, q=None):
     G = [(Minv @ g.csr(ne, s)).tocsr() for g in gacc]
     ops = dict(mesh=types.SimpleNamespace(ne=ne), M=M, Mmu=Mmu_acc.csr(ne, s), G=G, Et=Et.csr(ne, s),
                E=E.csr(ne, s), s=s, els=els, faces=(intra, bdry, arcs), Minv=Minv, mu_phase=mu_phase, p=p, q=q)
+    if unsteady:
+        ops.update(Mrho=Mrho_acc.csr(ne, s), Emu=Emu.csr(ne, s), Erho=Erho.csr(ne, s), delta=delta)
     return ops
 
 

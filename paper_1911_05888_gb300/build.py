@@ -17,10 +17,12 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = [
     ("setup.cpp", ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-variable"]),
     ("cutcell.cpp", ["g++", "-O3", "-std=c++17", "-fPIC", "-Wall"]),
+    ("cutsetup.cpp", ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall"]),
     ("kernels.cu", ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                     "--expt-relaxed-constexpr"]),
     ("api.cu", ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]),
     ("noalloc.cu", ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]),
+    ("generic.cu", ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]),
     ("learn.cu", ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]),
     ("persist.cu", ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                     "--expt-relaxed-constexpr"]),

@@ -36,6 +36,9 @@ cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, c
 // The same on any level's records with its own pattern (the cluster level's).
 cudaError_t run_element_on(Ctx& c, const Pattern& pat, DevLevel& D, int prec, int mode, int pos0, int npos,
                            const void* mat, const void* b, void* x, void* r, cudaStream_t st) {
+  if (D.gen)   // general block-sparse level (cut-cell hierarchy)
+    return launch_gen_element(prec, mode, c.s, c.nb, D.nbp, pos0, npos, D.perm, D.tptr, D.tinfo, D.cpl[prec], mat,
+                              b, x, r, st);
   // FP16 records carry scales and run on the warp and wide kernels only.
   const bool scaled = prec == STK_FP16;
   const float* tsc = scaled ? D.csc : nullptr;
@@ -296,6 +299,99 @@ void pack_records(Ctx& c, const HostLevel& H, const Pattern& P, DevLevel& D, boo
 
 void pack_level(Ctx& c, int l, cudaStream_t st) { pack_records(c, c.host[l], c.pat, c.dev[l], l == 0, st); }
 
+// Device records of a general block-sparse level (cut-cell hierarchy): the
+// colour-major element order, every position's task range and task words,
+// the coupling records [task][s][s] row-major, A_ii^{-1} and A_ii
+// column-major [pos][nb][nb], and the injection to the next coarser level.
+void pack_generic(Ctx& c, int l, cudaStream_t st) {
+  const HostLevel& H = c.host[l];
+  DevLevel& D = c.dev[l];
+  const int s = c.s, nb = c.nb, ss = s * s, ne = H.ne;
+  D.gen = 1;
+  D.ne = ne;
+  D.nbp = nb;
+  for (int k = 0; k < 3; ++k) D.n[k] = H.n[k];
+  int ncol = 0;
+  for (int v : H.colour) ncol = std::max(ncol, v + 1);
+  if (ncol > 64) throw std::runtime_error("more than 64 colours");
+  D.ncolour = ncol;
+  std::vector<int> perm;
+  perm.reserve(ne);
+  D.cstart[0] = 0;
+  for (int col = 0; col < ncol; ++col) {
+    for (int e = 0; e < ne; ++e)
+      if (H.colour[e] == col) perm.push_back(e);
+    D.cstart[col + 1] = (int)perm.size();
+  }
+  std::vector<int> tptr(ne + 1, 0), tinfo;
+  std::vector<double> rec;
+  rec.reserve(H.C.size());
+  for (int pos = 0; pos < ne; ++pos) {
+    const int e = perm[pos];
+    for (int t = H.tptr[e]; t < H.tptr[e + 1]; ++t) {
+      tinfo.push_back(H.tnbr[t] * 16 + (H.tvar[t] / 4) * 4 + H.tvar[t] % 4);
+      rec.insert(rec.end(), H.C.begin() + (size_t)t * ss, H.C.begin() + (size_t)(t + 1) * ss);
+    }
+    tptr[pos + 1] = (int)tinfo.size();
+  }
+  if ((int64_t)ne * 16 >= (int64_t)1 << 31) throw std::runtime_error("too many elements for the task words");
+  D.perm = (int*)dalloc(c, (size_t)ne * sizeof(int));
+  D.tptr = (int*)dalloc(c, tptr.size() * sizeof(int));
+  D.tinfo = (int*)dalloc(c, std::max<size_t>(1, tinfo.size()) * sizeof(int));
+  ck(cudaMemcpy(D.perm, perm.data(), (size_t)ne * sizeof(int), cudaMemcpyHostToDevice), "copy perm");
+  ck(cudaMemcpy(D.tptr, tptr.data(), tptr.size() * sizeof(int), cudaMemcpyHostToDevice), "copy tptr");
+  if (!tinfo.empty())
+    ck(cudaMemcpy(D.tinfo, tinfo.data(), tinfo.size() * sizeof(int), cudaMemcpyHostToDevice), "copy tinfo");
+  D.cpl[0] = dalloc(c, std::max<size_t>(1, rec.size()) * sizeof(double));
+  if (!rec.empty())
+    ck(cudaMemcpy(D.cpl[0], rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice), "copy cpl");
+  std::vector<double> Dinv((size_t)ne * nb * nb);
+  std::string err;
+  if (invert_blocks(nb, ne, H.D.data(), Dinv.data(), err) != STK_OK) throw std::runtime_error(err);
+  const size_t mat_n = (size_t)ne * nb * nb;
+  std::vector<double> buf(mat_n);
+  auto pack_mat = [&](const std::vector<double>& M, void*& out) {
+    for (int pos = 0; pos < ne; ++pos) {
+      const double* m = &M[(size_t)perm[pos] * nb * nb];
+      double* o = &buf[(size_t)pos * nb * nb];
+      for (int r = 0; r < nb; ++r)
+        for (int cc = 0; cc < nb; ++cc) o[(size_t)cc * nb + r] = m[(size_t)r * nb + cc];
+    }
+    out = dalloc(c, mat_n * sizeof(double));
+    ck(cudaMemcpy(out, buf.data(), mat_n * sizeof(double), cudaMemcpyHostToDevice), "copy mat");
+  };
+  pack_mat(Dinv, D.inv[0]);
+  pack_mat(H.D, D.dia[0]);
+  if (c.precision == STK_FP32) {
+    void* src[3] = {D.cpl[0], D.inv[0], D.dia[0]};
+    size_t cnt[3] = {std::max<size_t>(1, rec.size()), mat_n, mat_n};
+    void** dst[3] = {&D.cpl[1], &D.inv[1], &D.dia[1]};
+    for (int i = 0; i < 3; ++i) {
+      *dst[i] = dalloc(c, cnt[i] * 4);
+      ck(launch_convert(0, 1, (int64_t)cnt[i], *dst[i], src[i], st), "convert fp32");
+    }
+  }
+  // injection to the next coarser level
+  if (!H.parent.empty()) {
+    const int nc = c.host[l + 1].ne;
+    std::vector<int> cptr(nc + 1, 0), clist(ne);
+    for (int f = 0; f < ne; ++f) cptr[H.parent[f] + 1]++;
+    for (int k = 0; k < nc; ++k) cptr[k + 1] += cptr[k];
+    std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+    for (int f = 0; f < ne; ++f) clist[fill[H.parent[f]]++] = f;
+    D.gparent = (int*)dalloc(c, (size_t)ne * sizeof(int));
+    D.gcptr = (int*)dalloc(c, cptr.size() * sizeof(int));
+    D.gclist = (int*)dalloc(c, clist.size() * sizeof(int));
+    ck(cudaMemcpy(D.gparent, H.parent.data(), (size_t)ne * sizeof(int), cudaMemcpyHostToDevice), "copy parent");
+    ck(cudaMemcpy(D.gcptr, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice), "copy cptr");
+    ck(cudaMemcpy(D.gclist, clist.data(), clist.size() * sizeof(int), cudaMemcpyHostToDevice), "copy clist");
+    D.gI[0] = dalloc(c, H.Ib.size() * sizeof(double));
+    ck(cudaMemcpy(D.gI[0], H.Ib.data(), H.Ib.size() * sizeof(double), cudaMemcpyHostToDevice), "copy injection");
+    D.gI[1] = dalloc(c, H.Ib.size() * sizeof(float));
+    ck(launch_convert(0, 1, (int64_t)H.Ib.size(), D.gI[1], D.gI[0], st), "convert injection");
+  }
+}
+
 
 void alloc_vectors(Ctx& c) {
   int L = nlevels(c);
@@ -444,6 +540,17 @@ void setup_bottom(Ctx& c) {
     for (int r = 0; r < nb; ++r)
       for (int cc = 0; cc < nb; ++cc)
         A[(size_t)(a * nb + r) * n + a * nb + cc] += H.D[(size_t)a * nb * nb + r * nb + cc];
+    if (c.cut) {
+      // general block-sparse level: the element's coupling tasks
+      for (int t = H.tptr[a]; t < H.tptr[a + 1]; ++t) {
+        const int64_t bb = H.tnbr[t];
+        const int rv = H.tvar[t] / 4, cv = H.tvar[t] % 4;
+        for (int i = 0; i < s; ++i)
+          for (int j = 0; j < s; ++j)
+            A[(size_t)(a * nb + rv * s + i) * n + bb * nb + cv * s + j] += H.C[(size_t)t * ss + i * s + j];
+      }
+      continue;
+    }
     for (int t = 0; t < P.T; ++t) {
       int64_t bb = H.nbr[(size_t)a * P.NO + P.task_o[t]];
       if (bb < 0) continue;
@@ -544,12 +651,14 @@ void enqueue_cycle(Ctx& c, int prec, int l, void* x, const void* b, cudaStream_t
   DevLevel& Dc = c.dev[l + 1];
   enqueue_smooth(c, prec, l, level_sweeps(c, c.nu1, l), x, b, st);
   ck(run_element(c, l, prec, MODE_RESID, 0, D.ne, D.dia[prec], b, x, D.vr[vi], st), "residual launch");
-  ck(launch_restrict(vi == 0, c.d, c.s, c.nb, Dc.n, D.n, Dc.ne, c.child_P[vi], D.vr[vi], Dc.vb[vi], st),
+  ck(D.gen ? launch_gen_restrict(vi == 0, Dc.ne, c.s, c.nb, D.gcptr, D.gclist, D.gI[vi], D.vr[vi], Dc.vb[vi], st)
+           : launch_restrict(vi == 0, c.d, c.s, c.nb, Dc.n, D.n, Dc.ne, c.child_P[vi], D.vr[vi], Dc.vb[vi], st),
      "restrict launch");
   ck(cudaMemsetAsync(Dc.vx[vi], 0, (size_t)Dc.ne * c.nb * (vi == 0 ? 8 : 4), st), "memset");
   c.launches += 2;  // residual + restriction
   for (int v = coarse_visits(c, l); v > 0; --v) enqueue_cycle(c, prec, l + 1, Dc.vx[vi], Dc.vb[vi], st);
-  ck(launch_prolong(vi == 0, c.d, c.s, c.nb, D.n, Dc.n, Dc.ne, c.child_PT[vi], Dc.vx[vi], x, st),
+  ck(D.gen ? launch_gen_prolong(vi == 0, D.ne, c.s, c.nb, D.gparent, D.gI[vi], Dc.vx[vi], x, st)
+           : launch_prolong(vi == 0, c.d, c.s, c.nb, D.n, Dc.n, Dc.ne, c.child_PT[vi], Dc.vx[vi], x, st),
      "prolong launch");
   c.launches++;
   enqueue_smooth(c, prec, l, level_sweeps(c, c.nu2, l), x, b, st);
@@ -654,7 +763,7 @@ void free_persist(Ctx& c) {
 // persist_max elements below level 0; none when persist_max is 0.
 void build_persist(Ctx& c) {
   free_persist(c);
-  if (!c.ready || c.persist_max <= 0) return;
+  if (!c.ready || c.persist_max <= 0 || c.cut) return;
   const int L = nlevels(c);
   int l0 = -1;
   for (int l = 1; l < L; ++l)
@@ -1521,15 +1630,34 @@ int stk_set_penalty(stk_ctx* c, double tau, double tau0, double c_bdry, double c
 
 int stk_num_points(stk_ctx* c, int kind, int64_t* count) {
   return guard(c, [&]() -> int {
-    if (c->p < 0 || !count || kind < 0 || kind > 2) return fail(c, STK_ERR_INVALID_ARG, "bad call");
-    *count = count_points(*c, kind);
+    if (c->p < 0 || !count || kind < 0 || kind > (c->cut ? 3 : 2)) return fail(c, STK_ERR_INVALID_ARG, "bad call");
+    *count = c->cut ? cut_count_points(*c, kind) : count_points(*c, kind);
+    return STK_OK;
+  });
+}
+
+int stk_get_point_phases(stk_ctx* c, int kind, int* phase) {
+  return guard(c, [&]() -> int {
+    if (c->p < 0 || !phase || kind < 0 || kind > (c->cut ? 3 : 2)) return fail(c, STK_ERR_INVALID_ARG, "bad call");
+    if (!c->cut) return fail(c, STK_ERR_INVALID_ARG, "point phases belong to cut-cell meshes");
+    std::vector<double> pts;
+    std::vector<int> ph;
+    cut_points(*c, kind, pts, nullptr, &ph);
+    std::copy(ph.begin(), ph.end(), phase);
     return STK_OK;
   });
 }
 
 int stk_get_points(stk_ctx* c, int kind, double* xyz, double* normals) {
   return guard(c, [&]() -> int {
-    if (c->p < 0 || !xyz || kind < 0 || kind > 2) return fail(c, STK_ERR_INVALID_ARG, "bad call");
+    if (c->p < 0 || !xyz || kind < 0 || kind > (c->cut ? 3 : 2)) return fail(c, STK_ERR_INVALID_ARG, "bad call");
+    if (c->cut) {
+      std::vector<double> pts, nrm;
+      cut_points(*c, kind, pts, normals ? &nrm : nullptr, nullptr);
+      std::copy(pts.begin(), pts.end(), xyz);
+      if (normals) std::copy(nrm.begin(), nrm.end(), normals);
+      return STK_OK;
+    }
     std::vector<double> pts, nrm;
     face_points(*c, kind, pts, normals ? &nrm : nullptr);
     std::copy(pts.begin(), pts.end(), xyz);
@@ -1690,9 +1818,54 @@ int stk_set_cycle_shape(stk_ctx* c, int gamma, int growth, int max_sweeps) {
   });
 }
 
+// stk_setup for a cut-cell mesh of the embedded circle: the general
+// block-sparse hierarchy of cutsetup.cpp on the device.
+int setup_cut_device(stk_ctx* c, cudaStream_t st) {
+  const double hx = (c->hi[0] - c->lo[0]) / c->n[0], hy = (c->hi[1] - c->lo[1]) / c->n[1];
+  if (c->d != 2 || c->n[0] != c->n[1] || c->n[0] < 4 || std::fabs(hx - hy) > 1e-12 * hx)
+    return fail(c, STK_ERR_INVALID_ARG, "the embedded circle needs a 2D n x n mesh of square cells, n >= 4");
+  for (int i = 0; i < 4; ++i)
+    if (c->bc[i] != STK_BC_DIRICHLET) return fail(c, STK_ERR_INVALID_ARG, "cut-cell meshes take Dirichlet sides only");
+  if (c->p > 3) return fail(c, STK_ERR_INVALID_ARG, "cut-cell meshes take p = 1..3");
+  if (c->mu_phase.size() != 2) return fail(c, STK_ERR_INVALID_ARG, "set the two phase viscosities (stk_set_phases)");
+  if (c->cut_delta > 0 && c->rho_phase.size() != 2)
+    return fail(c, STK_ERR_INVALID_ARG, "set the two phase densities (stk_set_phase_density)");
+  if (c->precision != STK_FP64 && c->precision != STK_FP32)
+    return fail(c, STK_ERR_INVALID_ARG, "cut-cell levels store FP64 or FP32 blocks");
+  if (c->c_intra != 0.0) return fail(c, STK_ERR_INVALID_ARG, "cut-cell meshes take no interior velocity penalty");
+  std::string err;
+  int rc = setup_cut(*c, err);
+  if (rc != STK_OK) return fail(c, rc, err);
+  const int L = nlevels(*c);
+  if (L < 2) return fail(c, STK_ERR_INVALID_ARG, "mesh too small for a hierarchy");
+  c->dev.assign(L, DevLevel());
+  try {
+    for (int l = 0; l < L - 1; ++l) pack_generic(*c, l, st);
+  } catch (const std::runtime_error& e) {
+    free_device(*c);
+    return fail(c, STK_ERR_SINGULAR_BLOCK, e.what());
+  }
+  alloc_vectors(*c);
+  c->cluster_on = 0;
+  setup_bottom(*c);
+  c->dev_err = (int*)dalloc(*c, 16);
+  ck(cudaMemset(c->dev_err, 0, 16), "memset");
+  c->gbar = (GridBarrierWords*)dalloc(*c, 64);
+  ck(cudaMemset(c->gbar, 0, 64), "memset");
+  ck(cudaStreamSynchronize(st), "setup sync");
+  ck(cudaDeviceSynchronize(), "setup sync");
+  c->ready = true;
+  return STK_OK;
+}
+
 int stk_setup(stk_ctx* c, void* stream) {
   return guard(c, [&]() -> int {
     if (c->p < 0) return fail(c, STK_ERR_INVALID_ARG, "set mesh and discretisation first");
+    if (c->cut) {
+      ck(cudaSetDevice(c->device), "cudaSetDevice");
+      free_device(*c);
+      return setup_cut_device(c, (cudaStream_t)stream);
+    }
     if (c->mu_vol.empty()) return fail(c, STK_ERR_INVALID_ARG, "set the viscosity first");
     if (c->colouring == STK_COLOURS_CHECKERBOARD && (c->gamma != 0 || !c->chi.empty()))
       return fail(c, STK_ERR_INVALID_ARG,
@@ -1833,6 +2006,15 @@ int stk_get_block(stk_ctx* c, int level, int64_t i, int64_t j, double* out) {
     int nb = c->nb, s = c->s, ss = s * s;
     std::fill(out, out + (size_t)nb * nb, 0.0);
     if (i == j) std::copy(&H.D[(size_t)i * nb * nb], &H.D[(size_t)(i + 1) * nb * nb], out);
+    if (c->cut) {
+      for (int t = H.tptr[i]; t < H.tptr[i + 1]; ++t) {
+        if (H.tnbr[t] != j) continue;
+        const int rv = H.tvar[t] / 4, cv = H.tvar[t] % 4;
+        for (int a = 0; a < s; ++a)
+          for (int b = 0; b < s; ++b) out[(size_t)(rv * s + a) * nb + cv * s + b] += H.C[(size_t)t * ss + a * s + b];
+      }
+      return STK_OK;
+    }
     for (int t = 0; t < c->pat.T; ++t) {
       if (H.nbr[(size_t)i * c->pat.NO + c->pat.task_o[t]] != j) continue;
       int rv = c->pat.task_rv[t], cv = c->pat.task_cv[t];
@@ -1848,6 +2030,7 @@ int stk_assemble_rhs(stk_ctx* c, const double* f_vol, const double* bdata, doubl
   return guard(c, [&]() -> int {
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
     if (!f_vol || !b) return fail(c, STK_ERR_INVALID_ARG, "null argument");
+    if (c->cut) return fail(c, STK_ERR_INVALID_ARG, "cut-cell meshes take stk_assemble_rhs2 (interface data)");
     if (count_points(*c, 2) > 0 && !bdata) return fail(c, STK_ERR_INVALID_ARG, "null boundary data");
     return assemble_rhs_host(*c, f_vol, bdata, b);
   });
@@ -1935,7 +2118,8 @@ int stk_restrict(stk_ctx* c, int level, const double* r, double* rc, void* strea
     if (level < 0 || level >= nlevels(*c) - 1 || !r || !rc) return fail(c, STK_ERR_INVALID_ARG, "bad args");
     DevLevel& D = c->dev[level];
     DevLevel& Dc = c->dev[level + 1];
-    ck(launch_restrict(1, c->d, c->s, c->nb, Dc.n, D.n, Dc.ne, c->child_P[0], r, rc, (cudaStream_t)stream),
+    ck(D.gen ? launch_gen_restrict(1, Dc.ne, c->s, c->nb, D.gcptr, D.gclist, D.gI[0], r, rc, (cudaStream_t)stream)
+             : launch_restrict(1, c->d, c->s, c->nb, Dc.n, D.n, Dc.ne, c->child_P[0], r, rc, (cudaStream_t)stream),
        "restrict");
     c->launches++;
     return STK_OK;
@@ -1948,7 +2132,8 @@ int stk_prolong(stk_ctx* c, int level, const double* xc, double* x, void* stream
     if (level < 0 || level >= nlevels(*c) - 1 || !xc || !x) return fail(c, STK_ERR_INVALID_ARG, "bad args");
     DevLevel& D = c->dev[level];
     DevLevel& Dc = c->dev[level + 1];
-    ck(launch_prolong(1, c->d, c->s, c->nb, D.n, Dc.n, Dc.ne, c->child_PT[0], xc, x, (cudaStream_t)stream),
+    ck(D.gen ? launch_gen_prolong(1, D.ne, c->s, c->nb, D.gparent, D.gI[0], xc, x, (cudaStream_t)stream)
+             : launch_prolong(1, c->d, c->s, c->nb, D.n, Dc.n, Dc.ne, c->child_PT[0], xc, x, (cudaStream_t)stream),
        "prolong");
     c->launches++;
     return STK_OK;
@@ -2133,6 +2318,7 @@ int stk_set_wide_launch(stk_ctx* c, int max_positions) {
 int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
   return guard(c, [&]() -> int {
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (c->cut) return fail(c, STK_ERR_INVALID_ARG, "not available on cut-cell meshes");
     cudaStream_t st = (cudaStream_t)stream;
     const int L = nlevels(*c);
     for (int l = 0; l < L - 1; ++l)
@@ -2359,6 +2545,7 @@ int stk_solve_multi(stk_ctx* c, double* X, const double* B, int nrhs, double rto
                     int* iters_out, double* hist, void* stream) {
   return guard(c, [&]() -> int {
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (c->cut) return fail(c, STK_ERR_INVALID_ARG, "not available on cut-cell meshes");
     if (!X || !B || nrhs < 1 || nrhs > 8 || maxit < 0 || inner < 1 || inner > 16 || !(rtol > 0))
       return fail(c, STK_ERR_INVALID_ARG, "bad multi-rhs arguments (1 <= nrhs <= 8, 1 <= inner <= 16)");
     if (c->precision == STK_FP16)
@@ -2467,6 +2654,7 @@ static void init_uniform(std::vector<float>& w, uint64_t seed, float a) {
 int stk_learn_setup(stk_ctx* c, int hidden, uint64_t seed) {
   return guard(c, [&]() -> int {
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+    if (c->cut) return fail(c, STK_ERR_INVALID_ARG, "not available on cut-cell meshes");
     if (c->precision == STK_FP64) return fail(c, STK_ERR_INVALID_ARG, "the learned smoother runs in FP32/BF16 cycles");
     if (hidden < 8 || hidden > 512) return fail(c, STK_ERR_INVALID_ARG, "hidden width must be in 8..512");
     const int nb = c->nb, ne = c->dev[0].ne;
@@ -2781,6 +2969,50 @@ int stk_learn_weights(stk_ctx* c, float* host, int64_t count, int direction) {
   });
 }
 
+int stk_set_levelset_circle(stk_ctx* c, double cx, double cy, double r) {
+  return guard(c, [&]() -> int {
+    if (c->d != 2) return fail(c, STK_ERR_INVALID_ARG, "set a 2D mesh first");
+    if (!std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(r) || r < 0)
+      return fail(c, STK_ERR_INVALID_ARG, "bad circle");
+    free_device(*c);
+    c->cutg.reset();
+    c->cuts.reset();
+    if (r == 0) {
+      c->cut = 0;
+      c->mu_phase.clear();
+      c->rho_phase.clear();
+      c->cut_delta = 0.0;
+      return STK_OK;
+    }
+    c->cut = 1;
+    c->cut_c[0] = cx;
+    c->cut_c[1] = cy;
+    c->cut_r = r;
+    c->chi.clear();
+    return STK_OK;
+  });
+}
+
+int stk_set_phase_density(stk_ctx* c, const double* rho_phase, double delta) {
+  return guard(c, [&]() -> int {
+    if (!c->cut) return fail(c, STK_ERR_INVALID_ARG, "phase densities belong to cut-cell meshes");
+    if (!(delta >= 0) || !std::isfinite(delta)) return fail(c, STK_ERR_INVALID_ARG, "delta must be >= 0");
+    free_device(*c);
+    if (delta == 0) {
+      c->rho_phase.clear();
+      c->cut_delta = 0.0;
+      return STK_OK;
+    }
+    if (!rho_phase) return fail(c, STK_ERR_INVALID_ARG, "null densities");
+    for (int i = 0; i < 2; ++i)
+      if (!(rho_phase[i] > 0) || !std::isfinite(rho_phase[i]))
+        return fail(c, STK_ERR_INVALID_ARG, "phase density must be finite and positive");
+    c->rho_phase.assign(rho_phase, rho_phase + 2);
+    c->cut_delta = delta;
+    return STK_OK;
+  });
+}
+
 int stk_set_phases(stk_ctx* c, int nphase, const int* chi, const double* mu_phase, int scale) {
   return guard(c, [&]() -> int {
     if (c->p < 0) return fail(c, STK_ERR_INVALID_ARG, "set mesh and discretisation first");
@@ -2789,6 +3021,17 @@ int stk_set_phases(stk_ctx* c, int nphase, const int* chi, const double* mu_phas
       c->chi.clear();
       c->mu_phase.clear();
       c->scale_mu = 0;
+      return STK_OK;
+    }
+    if (c->cut) {
+      // embedded circle: phase 1 inside, 2 outside; no element phase array
+      if (nphase != 2 || !mu_phase) return fail(c, STK_ERR_INVALID_ARG, "the embedded circle has two phases");
+      for (int i = 0; i < 2; ++i)
+        if (!(mu_phase[i] > 0) || !std::isfinite(mu_phase[i]))
+          return fail(c, STK_ERR_INVALID_ARG, "phase viscosity must be finite and positive");
+      c->chi.clear();
+      c->mu_phase.assign(mu_phase, mu_phase + 2);
+      c->scale_mu = scale ? 1 : 0;
       return STK_OK;
     }
     if (nphase < 1 || nphase > 64 || !chi || !mu_phase) return fail(c, STK_ERR_INVALID_ARG, "bad phase arguments");
@@ -2809,6 +3052,7 @@ int stk_set_phases(stk_ctx* c, int nphase, const int* chi, const double* mu_phas
 int stk_get_interface(stk_ctx* c, int* chi_minus, int* chi_plus, double* normals) {
   return guard(c, [&]() -> int {
     if (c->p < 0) return fail(c, STK_ERR_INVALID_ARG, "set mesh and discretisation first");
+    if (c->cut) return fail(c, STK_ERR_INVALID_ARG, "cut-cell meshes: interface points are kind STK_PTS_INTERFACE");
     std::vector<int> cm, cp;
     std::vector<double> nr;
     interface_info(*c, cm, cp, nr);
@@ -2823,6 +3067,12 @@ int stk_assemble_rhs2(stk_ctx* c, const double* f_vol, const double* bdata, cons
   return guard(c, [&]() -> int {
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
     if (!f_vol || !b) return fail(c, STK_ERR_INVALID_ARG, "null argument");
+    if (c->cut) {
+      if (!bdata || !idata) return fail(c, STK_ERR_INVALID_ARG, "null boundary or interface data");
+      std::string err;
+      const int rc = cut_assemble_rhs(*c, f_vol, bdata, idata, b, err);
+      return rc == STK_OK ? rc : fail(c, rc, err);
+    }
     if (count_points(*c, 2) > 0 && !bdata) return fail(c, STK_ERR_INVALID_ARG, "null boundary data");
     return assemble_rhs_host2(*c, f_vol, bdata, idata, b);
   });
@@ -2907,6 +3157,7 @@ int stk_solve_batch_persistent(stk_ctx* const* ctx, int n, double* const* x, con
       Ctx& c = *ctx[i];
       if (!c.ready) return fail(c0, STK_ERR_NOT_SETUP, "problem " + std::to_string(i) + " is not set up");
       if (c.device != c0->device) return fail(c0, STK_ERR_INVALID_ARG, "problems on different devices");
+      if (c.cut) return fail(c0, STK_ERR_INVALID_ARG, "the persistent batch takes Cartesian problems");
       if (c.precision != STK_FP32)
         return fail(c0, STK_ERR_INVALID_ARG, "the persistent batch runs FP32-record cycles (problem " +
                                                  std::to_string(i) + ")");

@@ -52,9 +52,19 @@ int classify(const Circ& C, const double* lo, const double* hi) {
   return 0;
 }
 
-// Areas of the two pieces of a cut cell and the length of its interface arc.
-void cut_cell(const Circ& C, const double* lo, const double* hi, const std::vector<double>& gx,
-              const std::vector<double>& gw, double& a_in, double& a_out, double& arc) {
+// Gauss rule of q points on [a, b], appended to (t, w).
+void gauss_on(double a, double b, const std::vector<double>& gx, const std::vector<double>& gw,
+              std::vector<double>& t, std::vector<double>& w) {
+  for (size_t k = 0; k < gx.size(); ++k) {
+    t.push_back(0.5 * (a + b) + 0.5 * (b - a) * gx[k]);
+    w.push_back(0.5 * (b - a) * gw[k]);
+  }
+}
+
+// Volume rules of the inside and outside pieces of a cut cell and its
+// interface rule (points, weights, normals out of the circle).
+void cut_cell_rules(const Circ& C, const double* lo, const double* hi, const std::vector<double>& gx,
+                    const std::vector<double>& gw, CutPiece& in, CutPiece& out, CutArc& arc) {
   const double cx = 0.5 * (lo[0] + hi[0]) - C.c[0], cy = 0.5 * (lo[1] + hi[1]) - C.c[1];
   const int h_ax = std::fabs(cy) > std::fabs(cx) ? 1 : 0, t_ax = 1 - h_ax;
   const double c_t = C.c[t_ax], c_h = C.c[h_ax], r = C.r;
@@ -72,19 +82,26 @@ void cut_cell(const Circ& C, const double* lo, const double* hi, const std::vect
     const double t = c_t + s * r;
     if (t0 < t && t < t1) brk.insert(t);
   }
-  const int q = (int)gx.size();
-  auto interval = [&](double a, double b) {
-    double sum = 0.0;   // length via the same Gauss weights as the oracle
-    for (int k = 0; k < q; ++k) sum += 0.5 * (b - a) * gw[k];
-    return sum;
+  auto put = [&](CutPiece& P, double t, double wt, double a, double b) {
+    std::vector<double> hs, wh;
+    gauss_on(a, b, gx, gw, hs, wh);
+    for (size_t k = 0; k < hs.size(); ++k) {
+      double x[2];
+      x[t_ax] = t;
+      x[h_ax] = hs[k];
+      P.x.push_back(x[0]);
+      P.x.push_back(x[1]);
+      P.w.push_back(wt * wh[k]);
+    }
   };
-  a_in = a_out = arc = 0.0;
   std::vector<double> bs(brk.begin(), brk.end());
   for (size_t m = 0; m + 1 < bs.size(); ++m) {
     const double a = bs[m], b = bs[m + 1];
     if (b - a <= 0) continue;
-    for (int k = 0; k < q; ++k) {
-      const double t = 0.5 * (a + b) + 0.5 * (b - a) * gx[k], wt = 0.5 * (b - a) * gw[k];
+    std::vector<double> ts, wts;
+    gauss_on(a, b, gx, gw, ts, wts);
+    for (size_t k = 0; k < ts.size(); ++k) {
+      const double t = ts[k], wt = wts[k];
       const double disc = r * r - (t - c_t) * (t - c_t);
       double lo_in = 0.0, hi_in = 0.0, w = 0.0;
       if (disc > 0) {
@@ -93,27 +110,72 @@ void cut_cell(const Circ& C, const double* lo, const double* hi, const std::vect
         hi_in = std::min(h1, c_h + w);
       }
       if (hi_in > lo_in) {
-        a_in += wt * interval(lo_in, hi_in);
-        if (lo_in > h0) a_out += wt * interval(h0, lo_in);
-        if (h1 > hi_in) a_out += wt * interval(hi_in, h1);
+        put(in, t, wt, lo_in, hi_in);
+        if (lo_in > h0) put(out, t, wt, h0, lo_in);
+        if (h1 > hi_in) put(out, t, wt, hi_in, h1);
       } else {
-        a_out += wt * interval(h0, h1);
+        put(out, t, wt, h0, h1);
       }
       if (disc > 0)
         for (double s : {-1.0, 1.0}) {
           const double hv = c_h + s * w;
           if (h0 <= hv && hv <= h1) {
             const double dh = -s * (t - c_t) / w;
-            arc += wt * std::sqrt(1.0 + dh * dh);
+            double x[2];
+            x[t_ax] = t;
+            x[h_ax] = hv;
+            const double vx = x[0] - C.c[0], vy = x[1] - C.c[1], nv = std::sqrt(vx * vx + vy * vy);
+            arc.x.push_back(x[0]);
+            arc.x.push_back(x[1]);
+            arc.w.push_back(wt * std::sqrt(1.0 + dh * dh));
+            arc.nrm.push_back(vx / nv);
+            arc.nrm.push_back(vy / nv);
           }
         }
     }
   }
 }
 
-// Length of the phase-ph part of the face {x_axis = fixed, other in [a, b]}.
-double face_part_length(const Circ& C, double a, double b, int axis, double fixed, int ph,
-                        const std::vector<double>& gw) {
+// Bounding box of the phase-ph piece of the cut cell [lo, hi]: along axis k
+// the inside piece spans the coordinates whose line across the cell meets
+// the disk, |x_k - c_k| < sqrt(r^2 - d^2) with d the distance from c to the
+// cell's range on the other axis; the outside piece loses the coordinates
+// whose whole line lies in the disk, |x_k - c_k| < sqrt(r^2 - D^2) with D the
+// largest distance to that range, and keeps the hull of the rest.
+void piece_box(const Circ& C, const double* lo, const double* hi, int ph, double* blo, double* bhi) {
+  for (int k = 0; k < 2; ++k) {
+    const int o = 1 - k;
+    blo[k] = lo[k];
+    bhi[k] = hi[k];
+    if (ph == 1) {
+      const double d = std::max(0.0, std::max(lo[o] - C.c[o], C.c[o] - hi[o]));
+      const double a = std::sqrt(std::max(C.r * C.r - d * d, 0.0));
+      blo[k] = std::max(lo[k], C.c[k] - a);
+      bhi[k] = std::min(hi[k], C.c[k] + a);
+    } else {
+      const double D = std::max(std::fabs(lo[o] - C.c[o]), std::fabs(hi[o] - C.c[o]));
+      if (C.r * C.r > D * D) {
+        const double a = std::sqrt(C.r * C.r - D * D);
+        if (C.c[k] - a <= lo[k] && lo[k] < C.c[k] + a) blo[k] = C.c[k] + a;
+        if (C.c[k] - a < hi[k] && hi[k] <= C.c[k] + a) bhi[k] = C.c[k] - a;
+      }
+    }
+  }
+}
+
+double sum_of(const std::vector<double>& w) {
+  double a = 0.0;
+  for (double v : w) a += v;
+  return a;
+}
+
+}  // namespace
+
+void cut_face_parts(const CutGeometry& G, double a, double b, int axis, double fixed, std::vector<double>* x,
+                    std::vector<double>* w) {
+  const Circ C{{G.c[0], G.c[1]}, G.r};
+  std::vector<double> gx, gw;
+  gauss_rule(G.q, gx, gw);
   const int o = 1 - axis;
   std::set<double> cuts = {a, b};
   const double disc = C.r * C.r - (fixed - C.c[axis]) * (fixed - C.c[axis]);
@@ -122,22 +184,127 @@ double face_part_length(const Circ& C, double a, double b, int axis, double fixe
       const double v = C.c[o] + s * std::sqrt(disc);
       if (a < v && v < b) cuts.insert(v);
     }
+  for (int ph = 0; ph < 2; ++ph) {
+    x[ph].clear();
+    w[ph].clear();
+  }
   std::vector<double> cs(cuts.begin(), cuts.end());
-  double len = 0.0;
   for (size_t m = 0; m + 1 < cs.size(); ++m) {
     const double u = cs[m], v = cs[m + 1];
     if (v <= u) continue;
     double mid[2];
     mid[axis] = fixed;
     mid[o] = 0.5 * (u + v);
-    const int p = C.phi(mid[0], mid[1]) < 0 ? 1 : 2;
-    if (p != ph) continue;
-    for (double w : gw) len += 0.5 * (v - u) * w;
+    const int ph = C.phi(mid[0], mid[1]) < 0 ? 0 : 1;
+    std::vector<double> ts, ws;
+    gauss_on(u, v, gx, gw, ts, ws);
+    for (size_t k = 0; k < ts.size(); ++k) {
+      double p[2];
+      p[axis] = fixed;
+      p[o] = ts[k];
+      x[ph].push_back(p[0]);
+      x[ph].push_back(p[1]);
+      w[ph].push_back(ws[k]);
+    }
   }
-  return len;
 }
 
-}  // namespace
+void build_cut_geometry(CutGeometry& G, int n, const double* lo, const double* hi, double cx, double cy, double r,
+                        int q, double frac) {
+  G = CutGeometry();
+  G.n = n;
+  G.q = q;
+  G.frac = frac;
+  G.c[0] = cx;
+  G.c[1] = cy;
+  G.r = r;
+  for (int k = 0; k < 2; ++k) {
+    G.lo[k] = lo[k];
+    G.hi[k] = hi[k];
+    G.h[k] = (hi[k] - lo[k]) / n;
+  }
+  const Circ C{{cx, cy}, r};
+  std::vector<double> gx, gw;
+  gauss_rule(q, gx, gw);
+  auto add = [&](CutPiece&& P) {
+    P.area = sum_of(P.w);
+    G.piece_of[((int64_t)P.j * n + P.i) * 4 + P.ph] = (int)G.pieces.size();
+    G.pieces.push_back(std::move(P));
+  };
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      const double clo[2] = {lo[0] + G.h[0] * i, lo[1] + G.h[1] * j};
+      const double chi[2] = {clo[0] + G.h[0], clo[1] + G.h[1]};
+      const int k = classify(C, clo, chi);
+      if (k != 0) {
+        // the full cell: tensor Gauss rule, x fastest
+        CutPiece P;
+        P.i = i;
+        P.j = j;
+        P.ph = k < 0 ? 1 : 2;
+        for (int a = 0; a < 2; ++a) {
+          P.blo[a] = clo[a];
+          P.bhi[a] = chi[a];
+        }
+        std::vector<double> xs, wx, ys, wy;
+        gauss_on(clo[0], chi[0], gx, gw, xs, wx);
+        gauss_on(clo[1], chi[1], gx, gw, ys, wy);
+        for (int v = 0; v < q; ++v)
+          for (int u = 0; u < q; ++u) {
+            P.x.push_back(xs[u]);
+            P.x.push_back(ys[v]);
+            P.w.push_back(wy[v] * wx[u]);
+          }
+        add(std::move(P));
+        continue;
+      }
+      CutPiece in, out;
+      CutArc arc;
+      in.i = out.i = arc.i = i;
+      in.j = out.j = arc.j = j;
+      in.ph = 1;
+      out.ph = 2;
+      cut_cell_rules(C, clo, chi, gx, gw, in, out, arc);
+      piece_box(C, clo, chi, 1, in.blo, in.bhi);
+      piece_box(C, clo, chi, 2, out.blo, out.bhi);
+      add(std::move(in));
+      add(std::move(out));
+      G.arcs.push_back(std::move(arc));
+    }
+  // merging: a small piece joins the same-phase piece across the cell face
+  // with the longest same-phase part, among neighbours not small themselves
+  const int np = (int)G.pieces.size();
+  const double cell_area = G.h[0] * G.h[1];
+  G.element.resize(np);
+  for (int k = 0; k < np; ++k) G.element[k] = k;
+  std::vector<char> small(np);
+  for (int k = 0; k < np; ++k) small[k] = G.pieces[k].area < frac * cell_area;
+  for (int k = 0; k < np; ++k) {
+    if (!small[k]) continue;
+    const CutPiece& p = G.pieces[k];
+    int best = -1;
+    double best_len = -1.0;
+    const int dd[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    for (auto& dv : dd) {
+      const int ii = p.i + dv[0], jj = p.j + dv[1];
+      if (ii < 0 || ii >= n || jj < 0 || jj >= n) continue;
+      const int nb = G.find(ii, jj, p.ph);
+      if (nb < 0 || small[nb]) continue;
+      const double clo[2] = {lo[0] + G.h[0] * p.i, lo[1] + G.h[1] * p.j};
+      std::vector<double> fx[2], fw[2];
+      if (dv[0] != 0)
+        cut_face_parts(G, clo[1], clo[1] + G.h[1], 0, clo[0] + (dv[0] > 0 ? G.h[0] : 0.0), fx, fw);
+      else
+        cut_face_parts(G, clo[0], clo[0] + G.h[0], 1, clo[1] + (dv[1] > 0 ? G.h[1] : 0.0), fx, fw);
+      const double L = sum_of(fw[p.ph - 1]);
+      if (L > best_len) {
+        best = nb;
+        best_len = L;
+      }
+    }
+    if (best >= 0) G.element[k] = best;
+  }
+}
 
 }  // namespace stk
 
@@ -149,69 +316,18 @@ extern "C" int stk_cut_cells(int n, const double* lo, const double* hi, double c
   if (n < 1 || n > 4096 || !lo || !hi || !(r > 0) || q < 1 || q > 32 || !(merge_fraction >= 0) || !npieces)
     return STK_ERR_INVALID_ARG;
   if (!(hi[0] > lo[0]) || !(hi[1] > lo[1])) return STK_ERR_INVALID_ARG;
-  const Circ C{{cx, cy}, r};
-  std::vector<double> gx, gw;
-  gauss_rule(q, gx, gw);
-  const double hx = (hi[0] - lo[0]) / n, hy = (hi[1] - lo[1]) / n, cell_area = hx * hy;
+  CutGeometry G;
+  build_cut_geometry(G, n, lo, hi, cx, cy, r, q, merge_fraction);
   struct Piece {
     int i, j, ph;
     double area;
   };
   std::vector<Piece> pieces;
-  std::map<int64_t, int> piece_of;   // (cell, phase) -> piece
+  for (const CutPiece& P : G.pieces) pieces.push_back({P.i, P.j, P.ph, P.area});
   double arc_total = 0.0;
-  auto key = [n](int i, int j, int ph) { return ((int64_t)j * n + i) * 4 + ph; };
-  for (int j = 0; j < n; ++j)
-    for (int i = 0; i < n; ++i) {
-      const double clo[2] = {lo[0] + hx * i, lo[1] + hy * j}, chi[2] = {clo[0] + hx, clo[1] + hy};
-      const int k = classify(C, clo, chi);
-      if (k != 0) {
-        // the full cell: the tensor rule's weights sum to the cell's area
-        double a = 0.0;
-        for (int u = 0; u < q; ++u)
-          for (int v = 0; v < q; ++v) a += 0.5 * hx * gw[v] * 0.5 * hy * gw[u];
-        piece_of[key(i, j, k < 0 ? 1 : 2)] = (int)pieces.size();
-        pieces.push_back({i, j, k < 0 ? 1 : 2, a});
-        continue;
-      }
-      double a_in, a_out, arc;
-      cut_cell(C, clo, chi, gx, gw, a_in, a_out, arc);
-      arc_total += arc;
-      piece_of[key(i, j, 1)] = (int)pieces.size();
-      pieces.push_back({i, j, 1, a_in});
-      piece_of[key(i, j, 2)] = (int)pieces.size();
-      pieces.push_back({i, j, 2, a_out});
-    }
+  for (const CutArc& A : G.arcs) arc_total += sum_of(A.w);
   const int np = (int)pieces.size();
-  // merging
-  std::vector<int> elem(np);
-  for (int k = 0; k < np; ++k) elem[k] = k;
-  std::vector<char> small(np);
-  for (int k = 0; k < np; ++k) small[k] = pieces[k].area < merge_fraction * cell_area;
-  for (int k = 0; k < np; ++k) {
-    if (!small[k]) continue;
-    const Piece& p = pieces[k];
-    int best = -1;
-    double best_len = -1.0;
-    const int dd[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
-    for (auto& dv : dd) {
-      const int ii = p.i + dv[0], jj = p.j + dv[1];
-      if (ii < 0 || ii >= n || jj < 0 || jj >= n) continue;
-      auto it = piece_of.find(key(ii, jj, p.ph));
-      if (it == piece_of.end() || small[it->second]) continue;
-      const double clo[2] = {lo[0] + hx * p.i, lo[1] + hy * p.j};
-      double L;
-      if (dv[0] != 0)
-        L = face_part_length(C, clo[1], clo[1] + hy, 0, clo[0] + (dv[0] > 0 ? hx : 0.0), p.ph, gw);
-      else
-        L = face_part_length(C, clo[0], clo[0] + hx, 1, clo[1] + (dv[1] > 0 ? hy : 0.0), p.ph, gw);
-      if (L > best_len) {
-        best = it->second;
-        best_len = L;
-      }
-    }
-    if (best >= 0) elem[k] = best;
-  }
+  const std::vector<int>& elem = G.element;
   // greedy colours of the elements (representatives in increasing order)
   std::vector<int> reps;
   for (int k = 0; k < np; ++k)

@@ -1,0 +1,230 @@
+// Kernels of general block-sparse levels (the cut-cell hierarchy): the
+// coloured block Gauss-Seidel step and the residual of Section 3 with
+// per-element coupling lists of any length, and the transfers of Algorithm 1
+// through per-element injection blocks.
+//
+// Element kernel: one warp per element position of the launch.  Task t of the
+// element is one s x s sub-block C_t (row variable rv, column variable cv,
+// neighbour j), stored row-major, 16 rows x 16 columns for p = 3.  Lane pair
+// (2r, 2r+1) owns row r: each lane multiplies half the row with the matching
+// half of x_j (16-byte loads of records and vector), the pair sums with one
+// shuffle and adds the result into the running sum of row r of variable rv.
+// A task's record is one contiguous 1 KB (FP32) read by the whole warp.  The
+// dense A_ii^{-1} (colour step) or A_ii (residual) is stored column-major so
+// that lanes read consecutive rows of one column.
+#include <cuda_runtime.h>
+
+#include "stk_internal.h"
+#include "../../include/stokes_mg.h"
+
+namespace stk {
+
+namespace {
+
+constexpr int kGenWarps = 4;    // warps (elements) per CTA
+constexpr int kGenMaxNb = 64;   // largest block (2D, p = 3: 3 x 16)
+
+template <typename T, typename V, int N>
+__device__ __forceinline__ V dot_n(const T* __restrict__ a, const V* b) {
+  V acc = V(0);
+#pragma unroll
+  for (int k = 0; k < N; ++k) acc += (V)a[k] * b[k];
+  return acc;
+}
+
+// Half a row of a 16-column block: 8 entries from 16-byte aligned addresses.
+__device__ __forceinline__ void load8(const float* p, float* v) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void load8(const double* p, double* v) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p) + k);
+    v[2 * k] = a.x;
+    v[2 * k + 1] = a.y;
+  }
+}
+// The iterate is written by other launches (and, for the element's own block,
+// by this one), so it is read through plain loads.
+__device__ __forceinline__ void load8v(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void load8v(const double* p, double* v) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = *(reinterpret_cast<const double2*>(p) + k);
+    v[2 * k] = a.x;
+    v[2 * k + 1] = a.y;
+  }
+}
+
+template <typename T, typename V, int S, int MODE>
+__global__ void __launch_bounds__(kGenWarps * 32, 8)
+    gen_element_kernel(int pos0, int npos, int nb, int nbp, const int* __restrict__ perm,
+                       const int* __restrict__ tptr, const int* __restrict__ tinfo, const T* __restrict__ cpl,
+                       const T* __restrict__ mat, const V* b, V* x, V* r) {
+  constexpr int H = (S + 1) / 2;   // columns of the first half-row
+  __shared__ V sg[kGenWarps][kGenMaxNb];
+  __shared__ V sx[kGenWarps][kGenMaxNb];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pos = pos0 + blockIdx.x * kGenWarps + w;
+  if (pos >= pos0 + npos) return;   // whole warp
+  const int e = perm[pos];
+  const int row = lane >> 1, half = lane & 1;
+  const bool active = row < S;
+  const int c0 = half ? H : 0;
+  V acc0 = V(0), acc1 = V(0), acc2 = V(0);
+  const int t0 = tptr[pos], t1 = tptr[pos + 1];
+  for (int t = t0; t < t1; ++t) {
+    const int info = __ldg(tinfo + t);
+    const int j = info >> 4, rv = (info >> 2) & 3, cv = info & 3;
+    V part = V(0);
+    if (active) {
+      const T* rec = cpl + (size_t)t * S * S + row * S + c0;
+      const V* xj = x + (size_t)j * nb + cv * S + c0;
+      if (S == 16) {
+        T a[8];
+        V v[8];
+        load8(rec, a);
+        load8v(xj, v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) part += (V)a[k] * v[k];
+      } else if (half) {
+        part = dot_n<T, V, S - H>(rec, xj);
+      } else {
+        part = dot_n<T, V, H>(rec, xj);
+      }
+    }
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    if (rv == 0) acc0 += part;
+    else if (rv == 1) acc1 += part;
+    else acc2 += part;
+  }
+  if (active && !half) {
+    const V* be = b + (size_t)e * nb;
+    sg[w][row] = be[row] - acc0;
+    sg[w][S + row] = be[S + row] - acc1;
+    sg[w][2 * S + row] = be[2 * S + row] - acc2;
+  }
+  if (MODE == MODE_RESID)
+    for (int o = lane; o < nb; o += 32) sx[w][o] = x[(size_t)e * nb + o];
+  __syncwarp();
+  const T* m = mat + (size_t)pos * nb * nbp;
+  for (int o = lane; o < nb; o += 32) {
+    V y = V(0);
+    if (MODE == MODE_GS) {
+      for (int k = 0; k < nb; ++k) y += (V)__ldg(m + (size_t)k * nbp + o) * sg[w][k];
+      x[(size_t)e * nb + o] = y;
+    } else {
+      for (int k = 0; k < nb; ++k) y += (V)__ldg(m + (size_t)k * nbp + o) * sx[w][k];
+      r[(size_t)e * nb + o] = sg[w][o] - y;
+    }
+  }
+}
+
+// r_c(c) = sum over children f of I_f^T r(f), per variable; one thread per
+// coarse unknown.
+template <typename V, typename T>
+__global__ void gen_restrict_kernel(int nc, int s, int nb, const int* __restrict__ cptr,
+                                    const int* __restrict__ clist, const T* __restrict__ I, const V* __restrict__ r,
+                                    V* __restrict__ rc) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nc * nb) return;
+  const int c = (int)(idx / nb), row = (int)(idx % nb), v = row / s, a = row % s;
+  V sum = V(0);
+  for (int k = cptr[c]; k < cptr[c + 1]; ++k) {
+    const int f = clist[k];
+    const T* If = I + (size_t)f * s * s;
+    const V* rf = r + (size_t)f * nb + v * s;
+    for (int bb = 0; bb < s; ++bb) sum += (V)If[bb * s + a] * rf[bb];
+  }
+  rc[idx] = sum;
+}
+
+// x(f) += I_f x_c(parent(f)), per variable; one thread per fine unknown.
+template <typename V, typename T>
+__global__ void gen_prolong_kernel(int nf, int s, int nb, const int* __restrict__ parent, const T* __restrict__ I,
+                                   const V* __restrict__ xc, V* __restrict__ x) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nf * nb) return;
+  const int f = (int)(idx / nb), row = (int)(idx % nb), v = row / s, a = row % s;
+  const T* If = I + (size_t)f * s * s + (size_t)a * s;
+  const V* xp = xc + (size_t)parent[f] * nb + v * s;
+  V sum = V(0);
+  for (int bb = 0; bb < s; ++bb) sum += (V)If[bb] * xp[bb];
+  x[idx] += sum;
+}
+
+template <typename T, typename V, int S>
+cudaError_t gen_launch(int mode, int nb, int nbp, int pos0, int npos, const int* perm, const int* tptr,
+                       const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                       cudaStream_t st) {
+  const int blocks = (npos + kGenWarps - 1) / kGenWarps;
+  if (mode == MODE_GS)
+    gen_element_kernel<T, V, S, MODE_GS><<<blocks, kGenWarps * 32, 0, st>>>(
+        pos0, npos, nb, nbp, perm, tptr, tinfo, (const T*)cpl, (const T*)mat, (const V*)b, (V*)x, (V*)r);
+  else
+    gen_element_kernel<T, V, S, MODE_RESID><<<blocks, kGenWarps * 32, 0, st>>>(
+        pos0, npos, nb, nbp, perm, tptr, tinfo, (const T*)cpl, (const T*)mat, (const V*)b, (V*)x, (V*)r);
+  return cudaGetLastError();
+}
+
+template <typename T, typename V>
+cudaError_t gen_dispatch(int mode, int s, int nb, int nbp, int pos0, int npos, const int* perm, const int* tptr,
+                         const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                         cudaStream_t st) {
+  switch (s) {
+    case 4: return gen_launch<T, V, 4>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    case 9: return gen_launch<T, V, 9>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    case 16: return gen_launch<T, V, 16>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gen_element(int storage, int mode, int s, int nb, int nbp, int pos0, int npos, const int* perm,
+                               const int* tptr, const int* tinfo, const void* cpl, const void* mat, const void* b,
+                               void* x, void* r, cudaStream_t st) {
+  if (npos <= 0) return cudaSuccess;
+  if (nb != 3 * s || nb > kGenMaxNb) return cudaErrorInvalidValue;
+  // the 16-column kernels read the iterate with 16-byte loads
+  if (s == 16 && (((uintptr_t)x | (uintptr_t)b) & 15)) return cudaErrorMisalignedAddress;
+  if (storage == STK_FP64)
+    return gen_dispatch<double, double>(mode, s, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+  if (storage == STK_FP32)
+    return gen_dispatch<float, float>(mode, s, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gen_restrict(int vec64, int nc, int s, int nb, const int* cptr, const int* clist, const void* I,
+                                const void* r, void* rc, cudaStream_t st) {
+  const int64_t n = (int64_t)nc * nb;
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)((n + 255) / 256);
+  if (vec64)
+    gen_restrict_kernel<double, double><<<blocks, 256, 0, st>>>(nc, s, nb, cptr, clist, (const double*)I,
+                                                                (const double*)r, (double*)rc);
+  else
+    gen_restrict_kernel<float, float><<<blocks, 256, 0, st>>>(nc, s, nb, cptr, clist, (const float*)I,
+                                                              (const float*)r, (float*)rc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_prolong(int vec64, int nf, int s, int nb, const int* parent, const void* I, const void* xc,
+                               void* x, cudaStream_t st) {
+  const int64_t n = (int64_t)nf * nb;
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)((n + 255) / 256);
+  if (vec64)
+    gen_prolong_kernel<double, double><<<blocks, 256, 0, st>>>(nf, s, nb, parent, (const double*)I,
+                                                               (const double*)xc, (double*)x);
+  else
+    gen_prolong_kernel<float, float><<<blocks, 256, 0, st>>>(nf, s, nb, parent, (const float*)I,
+                                                             (const float*)xc, (float*)x);
+  return cudaGetLastError();
+}
+
+}  // namespace stk

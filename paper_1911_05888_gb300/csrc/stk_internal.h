@@ -2,7 +2,10 @@
 #pragma once
 
 #include <atomic>
+#include <functional>
 #include <cstdint>
+#include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -109,6 +112,16 @@ struct HostLevel {
   std::vector<double> D;                // [ne][nb*nb] diagonal blocks (row-major)
   std::vector<double> C;                // [ne][T][s*s] coupling task blocks (row-major)
   std::vector<int> nbr;                 // [ne][NO] neighbour element (-1 absent)
+  // General block-sparse levels (cut-cell meshes): the coupling tasks of
+  // element e are [tptr[e], tptr[e+1]), task t the s x s sub-block C[t] (rows
+  // of variable tvar[t] / 4 of e, columns of variable tvar[t] % 4 of tnbr[t]);
+  // the smoother colour of every element; and the injection to the next
+  // coarser level (fine element e = Ib[e] times its parent's coefficients,
+  // per variable).
+  std::vector<int> tptr, tnbr, tvar;
+  std::vector<int> colour;
+  std::vector<int> parent;
+  std::vector<double> Ib;               // [ne][s*s] row-major
 };
 
 // Device data of one level.
@@ -140,7 +153,51 @@ struct DevLevel {
   void* mb[2] = {nullptr, nullptr};
   void* mr[2] = {nullptr, nullptr};
   int n[3] = {1, 1, 1};
+  // general block-sparse level (cut-cell meshes): task range of every
+  // position, task word nbr * 16 + rv * 4 + cv, records cpl[prec] [task][s][s]
+  // row-major; transfer to the next coarser level: injection blocks (FP64,
+  // FP32) [fine element][s][s], parent of every fine element, children of
+  // every coarse element (cptr [nc+1], clist)
+  int gen = 0;
+  int* tptr = nullptr;
+  int* tinfo = nullptr;
+  int nbp = 0;                          // padded row count of the column-major dense blocks
+  void* gI[2] = {nullptr, nullptr};
+  int* gparent = nullptr;
+  int* gcptr = nullptr;
+  int* gclist = nullptr;
 };
+
+// Cut cells of an embedded circle (cutcell.cpp): pieces with their volume
+// rules, interface arcs of the cut cells, and the merging of small pieces.
+struct CutPiece {
+  int i = 0, j = 0, ph = 0;             // host cell, phase (1 inside, 2 outside)
+  double area = 0;
+  double blo[2] = {0, 0}, bhi[2] = {0, 0};   // bounding box of the piece
+  std::vector<double> x, w;             // points [m][2], weights [m]
+};
+struct CutArc {
+  int i = 0, j = 0;
+  std::vector<double> x, w, nrm;        // points [m][2], weights, normals [m][2] (out of the circle)
+};
+struct CutGeometry {
+  int n = 0, q = 0;
+  double lo[2] = {0, 0}, hi[2] = {1, 1}, h[2] = {1, 1}, c[2] = {0, 0}, r = 0, frac = 0.25;
+  std::vector<CutPiece> pieces;         // cells in order (x fastest), inside piece first
+  std::map<int64_t, int> piece_of;      // ((j n + i) 4 + ph) -> piece
+  std::vector<CutArc> arcs;             // one per cut cell, cells in order
+  std::vector<int> element;             // piece -> representative piece of its element
+  int find(int i, int j, int ph) const {
+    auto it = piece_of.find(((int64_t)j * n + i) * 4 + ph);
+    return it == piece_of.end() ? -1 : it->second;
+  }
+};
+void build_cut_geometry(CutGeometry& G, int n, const double* lo, const double* hi, double cx, double cy, double r,
+                        int q, double frac);
+// Gauss rules of the phase-1 and phase-2 parts of the face segment
+// {x_axis = fixed, other coordinate in [a, b]}: points [m][2] and weights.
+void cut_face_parts(const CutGeometry& G, double a, double b, int axis, double fixed, std::vector<double>* x,
+                    std::vector<double>* w);
 
 struct Ctx {
   int device = 0;
@@ -285,6 +342,15 @@ struct Ctx {
   int64_t mgraph_kernels = 0;
   std::vector<void*> allocations;
   int64_t device_bytes = 0;   // bytes the library allocated for this context
+  // embedded circle (cut-cell mesh of the box): centre, radius, merge
+  // fraction; density per phase and delta of an unsteady cut-cell problem;
+  // the geometry (built on demand for the current mesh and degree)
+  int cut = 0;
+  double cut_c[2] = {0, 0}, cut_r = 0, cut_frac = 0.25;
+  std::vector<double> rho_phase;
+  double cut_delta = 0.0;
+  std::shared_ptr<CutGeometry> cutg;
+  std::shared_ptr<struct CutState> cuts;   // elements, faces and finest operators after setup
 };
 
 // ---- setup.cpp --------------------------------------------------------------
@@ -310,6 +376,16 @@ void face_points(const Ctx& c, int kind, std::vector<double>& xyz, std::vector<d
 int assemble_rhs_host(const Ctx& c, const double* f_vol, const double* bdata, double* b);
 int build_cluster_level(const Ctx& c, const HostLevel& H, const Pattern& ep, const Pattern& cp, HostLevel& HC,
                         std::string& err);
+void psi_eval(int p, double x, double* v, double* dv);
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn);
+
+// ---- cutsetup.cpp -------------------------------------------------------------
+const CutGeometry& cut_geometry(Ctx& c);    // (re)built for the current mesh and degree
+int setup_cut(Ctx& c, std::string& err);     // levels of the cut-cell hierarchy (general block-sparse)
+int64_t cut_count_points(Ctx& c, int kind);
+void cut_points(Ctx& c, int kind, std::vector<double>& xyz, std::vector<double>* nrm, std::vector<int>* phase);
+int cut_assemble_rhs(Ctx& c, const double* f_vol, const double* bdata, const double* idata, double* b,
+                     std::string& err);
 
 
 // ---- kernels.cu / learn.cu launchers ------------------------------------------
@@ -399,6 +475,13 @@ cudaError_t launch_batch_solve(const BatchProblem* probs, int nprob, const Batch
                                const BatchTask* tasks, int maxit, double rtol, int smax, size_t smem,
                                GridBarrierWords* gb, int* err, long long limit, int grid, cudaStream_t st);
 size_t batch_smem_bytes(const Pattern& pat);
+cudaError_t launch_gen_element(int storage, int mode, int s, int nb, int nbp, int pos0, int npos, const int* perm,
+                               const int* tptr, const int* tinfo, const void* cpl, const void* mat, const void* b,
+                               void* x, void* r, cudaStream_t st);
+cudaError_t launch_gen_restrict(int vec64, int nc, int s, int nb, const int* cptr, const int* clist, const void* I,
+                                const void* r, void* rc, cudaStream_t st);
+cudaError_t launch_gen_prolong(int vec64, int nf, int s, int nb, const int* parent, const void* I, const void* xc,
+                               void* x, cudaStream_t st);
 cudaError_t launch_barrier_selftest(GridBarrierWords* gb, int* err, long long limit, int rounds, int absent, int grid,
                                     unsigned int* passed, cudaStream_t st);
 

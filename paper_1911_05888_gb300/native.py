@@ -20,7 +20,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "TIMEOUT", -5:
 BC_PERIODIC, BC_DIRICHLET, BC_STRESS = 0, 1, 2
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 RICHARDSON, FGMRES, FGMRES_IR = 0, 1, 2
-PTS_VOLUME, PTS_INTERIOR_FACE, PTS_BOUNDARY_FACE = 0, 1, 2
+PTS_VOLUME, PTS_INTERIOR_FACE, PTS_BOUNDARY_FACE, PTS_INTERFACE = 0, 1, 2, 3
 INFO_BOTTOM_SOLVER, INFO_BOTTOM_UNKNOWNS, INFO_COLOURS, INFO_DEVICE_BYTES, INFO_CLUSTERS = 0, 1, 2, 3, 4
 BOTTOM_JACOBI, BOTTOM_HOST_QR, BOTTOM_CUSOLVER = 0, 1, 2
 COLOURS_AUTO, COLOURS_PARITY, COLOURS_CHECKERBOARD = 0, 1, 2
@@ -103,6 +103,9 @@ SIGNATURES = {
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), _c_dbl_p, _vp],
     "stk_barrier_selftest": [_vp, ctypes.c_int, ctypes.c_int64, _c_i64_p],
+    "stk_set_levelset_circle": [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+    "stk_set_phase_density": [_vp, _c_dbl_p, ctypes.c_double],
+    "stk_get_point_phases": [_vp, ctypes.c_int, _c_int_p],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
 
@@ -299,6 +302,8 @@ class Context:
     def setup(self, stream=None):
         self._check(self.lib.stk_setup(self.h, _stream(stream)), "stk_setup")
         nl, ne, nb, _ = self.sizes()
+        if getattr(self, "cut", False):
+            self.ne = int(ne[0])   # merged cut-cell elements
         self._level_n = [int(v) * nb for v in ne]   # unknowns per level, for the vector checks
         self._nb = nb
 
@@ -337,7 +342,8 @@ class Context:
         if bdata is not None:
             self._expect("bdata", bdata, self.num_points(PTS_BOUNDARY_FACE), d)
         if idata is not None:
-            self._expect("idata", idata, self.num_points(PTS_INTERIOR_FACE), 2 * d)
+            kind = PTS_INTERFACE if getattr(self, "cut", False) else PTS_INTERIOR_FACE
+            self._expect("idata", idata, self.num_points(kind), 2 * d)
 
     def assemble_rhs(self, f_vol, bdata, ne, nb):
         self._check_rhs_data(f_vol, bdata, ne)
@@ -540,6 +546,34 @@ class Context:
             raise ValueError("set_phases: phase indices must lie in 1..%d" % len(mu))
         self._check(self.lib.stk_set_phases(self.h, len(mu), chi.ctypes.data_as(_c_int_p),
                                             mu.ctypes.data_as(_c_dbl_p), 1 if scale else 0), "stk_set_phases")
+
+    def set_levelset_circle(self, centre, radius):
+        """Embedded circle (cut-cell mesh); radius 0 returns to the Cartesian mesh."""
+        self._check(self.lib.stk_set_levelset_circle(self.h, float(centre[0]), float(centre[1]), float(radius)),
+                    "stk_set_levelset_circle")
+        self.cut = radius > 0
+
+    def set_cut_phases(self, mu_phase, scale=True):
+        """Viscosities of the circle's inside (phase 1) and outside (phase 2)."""
+        mu = np.ascontiguousarray(mu_phase, dtype=np.float64)
+        self._expect("mu_phase", mu, 2)
+        self._check(self.lib.stk_set_phases(self.h, 2, None, mu.ctypes.data_as(_c_dbl_p), 1 if scale else 0),
+                    "stk_set_phases")
+
+    def set_phase_density(self, rho_phase, delta):
+        if delta == 0:
+            self._check(self.lib.stk_set_phase_density(self.h, None, 0.0), "stk_set_phase_density")
+            return
+        rho = np.ascontiguousarray(rho_phase, dtype=np.float64)
+        self._expect("rho_phase", rho, 2)
+        self._check(self.lib.stk_set_phase_density(self.h, rho.ctypes.data_as(_c_dbl_p), float(delta)),
+                    "stk_set_phase_density")
+
+    def get_point_phases(self, kind):
+        out = np.zeros(self.num_points(kind), dtype=np.int32)
+        self._check(self.lib.stk_get_point_phases(self.h, kind, out.ctypes.data_as(_c_int_p)),
+                    "stk_get_point_phases")
+        return out
 
     def get_interface(self, npts, d):
         cm = np.zeros(npts, dtype=np.int32)
