@@ -19,10 +19,12 @@
   that level's element mean viscosity.
 * The levels halve the grid until it is 2 x 2 cells; the last is the bottom.
 * Smoother colouring: deterministic greedy over the structural coupling graph
-  (element pairs that some block of the operator joins structurally: on the
-  finest level the pairs within two face / interface steps, on a coarse level
-  the groups that contain structurally coupled members), elements in index
-  order, each the smallest colour unused by an already coloured neighbour.
+  (element pairs that some block of the operator joins structurally), elements
+  in index order, each the smallest colour unused by an already coloured
+  neighbour.  The field operators G_k, E, E~ of a level couple elements one
+  face / interface step apart (on a coarse level: groups with members one
+  step apart), and the Stokes operator's G^T M G reaches two such steps, so
+  the graph is the square of the level's one-step graph.
 """
 import types
 
@@ -80,8 +82,8 @@ def build(mesh, p, mu_phase, tau, gamma, nmin=2, rho_phase=None, delta=None, tau
     anchor = np.array([mesh.pieces[els.reps[e]]["cell"] for e in range(ne)])
     box_lo, box_hi = els.box_lo.copy(), els.box_hi.copy()
     phase = els.phase.copy()
-    G1 = _face_graph(ne, ops)
-    structure = ((G1 @ G1) != 0).astype(np.float64)       # blocks of G^T M G reach two face steps
+    G1 = _face_graph(ne, ops)                            # one face / interface step
+    structure = ((G1 @ G1) != 0).astype(np.float64)       # blocks of G^T M G reach two steps
     levels, injections = [], []
     n = mesh.n
 
@@ -149,7 +151,8 @@ def build(mesh, p, mu_phase, tau, gamma, nmin=2, rho_phase=None, delta=None, tau
         I = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(ne * s, nc * s))
         ops = coarsen(ops, I, types.SimpleNamespace(ne=nc), unsteady)
         Pm = sp.csr_matrix((np.ones(ne), (np.arange(ne), parent)), shape=(ne, nc))
-        structure = ((Pm.T @ structure @ Pm) != 0).astype(np.float64)
+        G1 = ((Pm.T @ G1 @ Pm) != 0).astype(np.float64)
+        structure = ((G1 @ G1) != 0).astype(np.float64)
         lev = make_level(ops, nc, c_lo, c_hi, c_phase, structure)
         Ifull = sp.block_diag([I] * nvar, format="csr")
         injections.append((levels[-1].P @ Ifull @ lev.P.T).tocsr())

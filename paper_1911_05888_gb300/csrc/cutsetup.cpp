@@ -27,9 +27,11 @@
 //    f re-expands the coarse polynomial in the member's basis (the L2
 //    projection over the member's box, exact for Q_p).
 //  * Colouring: greedy, elements in index order, each the smallest colour not
-//    used by an already coloured element it is structurally coupled with: on
-//    the finest level the pairs within two face / interface steps, on a
-//    coarse level the groups that hold coupled members.
+//    used by an already coloured element it is structurally coupled with:
+//    the level's field operators couple elements one face / interface step
+//    apart (on a coarse level, groups with members one step apart) and
+//    G^T M G reaches two steps, so the graph is the square of the one-step
+//    graph.
 #include <algorithm>
 #include <array>
 #include <atomic>
@@ -632,9 +634,13 @@ int setup_cut(Ctx& c, std::string& err) {
     G1[F.ea].insert(F.eb);
     G1[F.eb].insert(F.ea);
   }
-  std::vector<std::set<int>> structure(ne0);
-  for (int e = 0; e < ne0; ++e)
-    for (int m : G1[e]) structure[e].insert(G1[m].begin(), G1[m].end());
+  auto square = [](const std::vector<std::set<int>>& g) {
+    std::vector<std::set<int>> out(g.size());
+    for (size_t e = 0; e < g.size(); ++e)
+      for (int m : g[e]) out[e].insert(g[m].begin(), g[m].end());
+    return out;
+  };
+  std::vector<std::set<int>> structure = square(G1);
   // level state for the coarsening: anchors, boxes, phases, level-0 pieces
   int ne = ne0;
   std::vector<int> anchor(2 * ne), phase = S->phase;
@@ -720,10 +726,11 @@ int setup_cut(Ctx& c, std::string& err) {
     Lf.parent = parent;
     Lf.Ib = Ib;
     ops = coarsen(ops, parent, Ib, children);
-    std::vector<std::set<int>> cs(nc);
+    std::vector<std::set<int>> g1(nc);
     for (int e = 0; e < ne; ++e)
-      for (int j : structure[e]) cs[parent[e]].insert(parent[j]);
-    structure.swap(cs);
+      for (int j : G1[e]) g1[parent[e]].insert(parent[j]);
+    G1.swap(g1);
+    structure = square(G1);
     ne = nc;
     anchor.swap(c_anchor);
     phase.swap(c_phase);

@@ -282,6 +282,52 @@ class MultiPhaseManufactured:
         return g, h
 
 
+@dataclasses.dataclass
+class CutProblem:
+    """Two-phase Stokes problem on the unit square cut by an embedded circle
+    (Section 5's curved interface; the bubble configurations of Section 6):
+    phase 1 inside the circle, phase 2 outside, Dirichlet data on the box,
+    velocity and stress jumps on the circle from the per-phase manufactured
+    solution of Appendix C (MultiPhaseManufactured).  With rho_phase and delta
+    the unsteady problem of eq. (timedep1); its forcing adds rho/delta u."""
+    n: int = 128
+    p: int = 3
+    gamma: int = 1
+    mu_phase: Sequence[float] = (1e-3, 1.0)
+    rho_phase: Optional[Sequence[float]] = None
+    delta: Optional[float] = None
+    centre: Sequence[float] = (0.5, 0.5)
+    radius: float = 0.25
+    nu1: int = 3
+    nu2: int = 3
+    tau: Optional[float] = None
+    tau0: Optional[float] = None
+    scale_mu: bool = True
+
+    def __post_init__(self):
+        if self.tau is None:
+            self.tau = TABLE1_TAU[(self.gamma, 2, self.p)]
+        if self.tau0 is None:
+            self.tau0 = 0.5 * self.p
+        c, r = np.asarray(self.centre, dtype=np.float64), float(self.radius)
+        self.phase = lambda x: np.where(np.sqrt(((np.asarray(x) - c) ** 2).sum(-1)) < r, 1, 2)
+        self.exact = MultiPhaseManufactured(2, self.gamma, list(self.mu_phase), self.phase)
+        self.d = 2
+
+    @property
+    def unsteady(self):
+        return self.delta is not None and self.delta > 0
+
+    def forcing(self, x, chi):
+        """(f_1, f_2, fdiv) at points x of phase chi, with rho/delta u for the
+        unsteady problem."""
+        f = self.exact.f(x, chi=chi)
+        if self.unsteady:
+            rho = np.asarray(self.rho_phase, dtype=np.float64)[np.asarray(chi) - 1]
+            f = f + (rho / self.delta)[:, None] * self.exact.u(x, chi=chi)
+        return np.concatenate([f, self.exact.fdiv(x, chi=chi)[:, None]], axis=1)
+
+
 def square_interface(d=2, n=16, p=2, mu_inner=1e-3, mu_outer=1.0, nu=(3, 3), tau=None, scale_mu=True,
                      bc=None):
     """Multi-phase test of Section 5.6: phase 1 = (1/4, 3/4)^d with viscosity

@@ -86,3 +86,53 @@ class StokesMG:
 
     def close(self):
         self.ctx.close()
+
+
+class CutStokesMG:
+    """The same for a problems.CutProblem: the embedded circle's cut-cell mesh
+    (stk_set_levelset_circle), phase viscosities and densities, data sampled
+    at the library's cut-cell points."""
+
+    def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True):
+        self.prob = prob
+        self.ctx = native.Context(device)
+        self.ctx.set_mesh(2, (prob.n, prob.n), (0.0, 0.0), (1.0, 1.0), [DIRICHLET] * 4)
+        self.ctx.set_discretisation(prob.p, prob.gamma)
+        self.ctx.set_penalty(prob.tau, prob.tau0)
+        self.ctx.set_levelset_circle(prob.centre, prob.radius)
+        self.ctx.set_cut_phases(prob.mu_phase, scale=prob.scale_mu)
+        if prob.unsteady:
+            self.ctx.set_phase_density(prob.rho_phase, prob.delta)
+        nu1, nu2 = (prob.nu1, prob.nu2) if nu is None else nu
+        self.ctx.set_cycle(nu1, nu2, precision)
+        if setup:
+            self.ctx.setup()
+            self.nlevels, self.ne_levels, self.nb, self.n_snapped = self.ctx.sizes()
+            self.ne = int(self.ne_levels[0])
+
+    def points(self, kind):
+        x, n = self.ctx.get_points(kind, 2)
+        return x, n, self.ctx.get_point_phases(kind)
+
+    def rhs(self):
+        """b of the manufactured two-phase problem (host array [ne][nb], unscaled)."""
+        prob, ex = self.prob, self.prob.exact
+        xv, _, cv = self.points(native.PTS_VOLUME)
+        xb, _, cb = self.points(native.PTS_BOUNDARY_FACE)
+        xi, ni, _ = self.points(native.PTS_INTERFACE)
+        f_vol = prob.forcing(xv, cv)
+        bdata = ex.u(xb, chi=cb)
+        idata = np.zeros((len(xi), 4))
+        if len(xi):
+            one, two = np.ones(len(xi), dtype=int), np.full(len(xi), 2)
+            idata[:, :2] = ex.u(xi, chi=one) - ex.u(xi, chi=two)
+            # sigma n with the per-point normal: sigma e_0 n_0 + sigma e_1 n_1
+            for k, ek in enumerate((np.array([1.0, 0.0]), np.array([0.0, 1.0]))):
+                idata[:, 2:] += (ex.stress(xi, ek, chi=one) - ex.stress(xi, ek, chi=two)) * ni[:, k:k + 1]
+        return self.ctx.assemble_rhs2(f_vol, bdata, idata, self.ne, self.nb)
+
+    def scaling(self):
+        return self.ctx.get_scaling(self.ne, self.nb)
+
+    def close(self):
+        self.ctx.close()
