@@ -245,7 +245,10 @@ int stk_get_sizes(stk_ctx* ctx, int* nlevels, int64_t* n_elements, int* nb, int*
  *   STK_INFO_BOTTOM_UNKNOWNS unknowns of the bottom level;
  *   STK_INFO_COLOURS         colours of the level-0 smoother;
  *   STK_INFO_DEVICE_BYTES    device bytes the library holds for the context;
- *   STK_INFO_CLUSTERS        1 when level 0 smooths element clusters.
+ *   STK_INFO_CLUSTERS        1 when level 0 smooths element clusters;
+ *   STK_INFO_COUPLING_BLOCKS s x s coupling sub-blocks level 0 stores (the
+ *                            records a colour sweep streams besides the
+ *                            dense A_ii^{-1}).
  * All but STK_INFO_DEVICE_BYTES need stk_setup (else STK_ERR_NOT_SETUP); an unknown key is
  * STK_ERR_INVALID_ARG.
  */
@@ -254,6 +257,7 @@ int stk_get_sizes(stk_ctx* ctx, int* nlevels, int64_t* n_elements, int* nb, int*
 #define STK_INFO_COLOURS 2
 #define STK_INFO_DEVICE_BYTES 3
 #define STK_INFO_CLUSTERS 4
+#define STK_INFO_COUPLING_BLOCKS 5
 int stk_get_info(stk_ctx* ctx, int what, int64_t* value);
 
 /* Dense nb x nb block A_ij (row element i, column element j, natural

@@ -1991,6 +1991,10 @@ int stk_get_info(stk_ctx* c, int what, int64_t* value) {
       case STK_INFO_DEVICE_BYTES:
         *value = c->device_bytes;
         return STK_OK;
+      case STK_INFO_COUPLING_BLOCKS:
+        if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
+        *value = c->cut ? (int64_t)c->host[0].tnbr.size() : (int64_t)c->host[0].ne * c->pat.T;
+        return STK_OK;
       default:
         return fail(c, STK_ERR_INVALID_ARG, "unknown info key");
     }

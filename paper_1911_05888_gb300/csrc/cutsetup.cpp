@@ -486,16 +486,14 @@ void stokes_blocks(const Ctx& c, const Ops& O, HostLevel& L) {
   }
   // rows in parallel: per element row, a map neighbour -> 3 x 3 sub-blocks
   std::vector<std::vector<int>> nbrs(ne);
-  std::vector<std::vector<std::vector<double>>> blocks(ne);   // per neighbour: [9][ss] (empty = absent)
-  std::vector<std::vector<unsigned>> present(ne);
+  std::vector<std::vector<std::array<Blk, 9>>> blocks(ne);   // per neighbour: 3 x 3 sub-blocks (empty = absent)
   parallel_for(ne, [&](int64_t e0, int64_t e1) {
     for (int64_t e = e0; e < e1; ++e) {
-      std::map<int, std::pair<unsigned, std::vector<double>>> row;
+      std::map<int, std::array<Blk, 9>> row;
       auto sub = [&](int f, int rv, int cv) -> double* {
-        auto& ent = row[f];
-        if (ent.second.empty()) ent.second.assign((size_t)9 * ss, 0.0);
-        ent.first |= 1u << (rv * 3 + cv);
-        return &ent.second[(size_t)(rv * 3 + cv) * ss];
+        Blk& b = row[f][rv * 3 + cv];
+        if (b.empty()) b.assign(ss, 0.0);
+        return b.data();
       };
       // velocity-velocity: gamma G_j^T Mmu G_i (rv = i, cv = j) plus, on the
       // diagonal variable blocks, sum_k G_k^T Mmu G_k + E~ (+ Mrho / delta)
@@ -541,45 +539,62 @@ void stokes_blocks(const Ctx& c, const Ops& O, HostLevel& L) {
       add_all(O.E, -1.0, 2, 2);
       for (auto& kv : row) {
         nbrs[e].push_back(kv.first);
-        present[e].push_back(kv.second.first);
-        blocks[e].push_back(std::move(kv.second.second));
+        blocks[e].push_back(std::move(kv.second));
       }
     }
   });
-  // element-major assembly, scaling, tasks
+  // element-major assembly, scaling, tasks: scale and count in parallel,
+  // then place every element's tasks at its prefix offset
   L.D.assign((size_t)ne * nb * nb, 0.0);
-  L.tptr.assign(ne + 1, 0);
-  L.tnbr.clear();
-  L.tvar.clear();
-  L.C.clear();
-  for (int e = 0; e < ne; ++e) {
-    for (size_t k = 0; k < nbrs[e].size(); ++k) {
-      const int f = nbrs[e][k];
-      std::vector<double>& B = blocks[e][k];
-      for (int rv = 0; rv < 3; ++rv)
-        for (int cv = 0; cv < 3; ++cv) {
-          if (!(present[e][k] & (1u << (rv * 3 + cv)))) continue;
-          double* blk = &B[(size_t)(rv * 3 + cv) * ss];
+  std::vector<int> count(ne, 0);
+  parallel_for(ne, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e)
+      for (size_t k = 0; k < nbrs[e].size(); ++k) {
+        const int f = nbrs[e][k];
+        for (int v = 0; v < 9; ++v) {
+          Blk& B = blocks[e][k][v];
+          if (B.empty()) continue;
+          const int rv = v / 3, cv = v % 3;
           if (!L.Dscale.empty())
             for (int a = 0; a < s; ++a)
-              for (int b = 0; b < s; ++b)
-                blk[a * s + b] *= L.Dscale[(size_t)e * nb + rv * s + a] * L.Dscale[(size_t)f * nb + cv * s + b];
+              for (int bb = 0; bb < s; ++bb)
+                B[a * s + bb] *= L.Dscale[(size_t)e * nb + rv * s + a] * L.Dscale[(size_t)f * nb + cv * s + bb];
           if (f == e) {
             for (int a = 0; a < s; ++a)
-              for (int b = 0; b < s; ++b) L.D[((size_t)e * nb + rv * s + a) * nb + cv * s + b] = blk[a * s + b];
+              for (int bb = 0; bb < s; ++bb) L.D[((size_t)e * nb + rv * s + a) * nb + cv * s + bb] = B[a * s + bb];
+            Blk().swap(B);
             continue;
           }
           bool nz = false;
-          for (int q = 0; q < ss && !nz; ++q) nz = blk[q] != 0.0;
-          if (!nz) continue;
-          L.tnbr.push_back(f);
-          L.tvar.push_back(rv * 4 + cv);
-          L.C.insert(L.C.end(), blk, blk + ss);
+          for (int q = 0; q < ss && !nz; ++q) nz = B[q] != 0.0;
+          if (nz)
+            ++count[e];
+          else
+            Blk().swap(B);
         }
-      std::vector<double>().swap(B);
+      }
+  });
+  L.tptr.assign(ne + 1, 0);
+  for (int e = 0; e < ne; ++e) L.tptr[e + 1] = L.tptr[e] + count[e];
+  const size_t nt = (size_t)L.tptr[ne];
+  L.tnbr.assign(nt, 0);
+  L.tvar.assign(nt, 0);
+  L.C.assign(nt * ss, 0.0);
+  parallel_for(ne, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) {
+      size_t t = (size_t)L.tptr[e];
+      for (size_t k = 0; k < nbrs[e].size(); ++k)
+        for (int v = 0; v < 9; ++v) {
+          Blk& B = blocks[e][k][v];
+          if (B.empty()) continue;
+          L.tnbr[t] = nbrs[e][k];
+          L.tvar[t] = (v / 3) * 4 + v % 3;
+          std::copy(B.begin(), B.end(), L.C.begin() + t * ss);
+          ++t;
+          Blk().swap(B);
+        }
     }
-    L.tptr[e + 1] = (int)L.tnbr.size();
-  }
+  });
 }
 
 std::vector<int> greedy(const std::vector<std::set<int>>& S) {

@@ -77,7 +77,43 @@ __global__ void __launch_bounds__(kGenWarps * 32, 8)
   const int c0 = half ? H : 0;
   V acc0 = V(0), acc1 = V(0), acc2 = V(0);
   const int t0 = tptr[pos], t1 = tptr[pos + 1];
-  for (int t = t0; t < t1; ++t) {
+  auto add = [&](int rv, V part) {
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    if (rv == 0) acc0 += part;
+    else if (rv == 1) acc1 += part;
+    else acc2 += part;
+  };
+  int t = t0;
+  if (S == 16) {
+    // U tasks per round (4 with FP32 records, 2 with FP64 ones, the most the
+    // 64 registers hold without spilling): their words, records and x
+    // segments are all requested before the first product, so a warp keeps
+    // U 1 KB (2 KB) record reads in flight
+    constexpr int U = sizeof(T) == 4 ? 4 : 2;
+    for (; t + U <= t1; t += U) {
+      int info[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) info[u] = __ldg(tinfo + t + u);
+      T a[U][8];
+      V v[U][8];
+      if (active) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          load8(cpl + (size_t)(t + u) * S * S + row * S + c0, a[u]);
+          load8v(x + (size_t)(info[u] >> 4) * nb + (info[u] & 3) * S + c0, v[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        V part = V(0);
+        if (active)
+#pragma unroll
+          for (int k = 0; k < 8; ++k) part += (V)a[u][k] * v[u][k];
+        add((info[u] >> 2) & 3, part);
+      }
+    }
+  }
+  for (; t < t1; ++t) {
     const int info = __ldg(tinfo + t);
     const int j = info >> 4, rv = (info >> 2) & 3, cv = info & 3;
     V part = V(0);
@@ -97,10 +133,7 @@ __global__ void __launch_bounds__(kGenWarps * 32, 8)
         part = dot_n<T, V, H>(rec, xj);
       }
     }
-    part += __shfl_xor_sync(0xffffffffu, part, 1);
-    if (rv == 0) acc0 += part;
-    else if (rv == 1) acc1 += part;
-    else acc2 += part;
+    add(rv, part);
   }
   if (active && !half) {
     const V* be = b + (size_t)e * nb;

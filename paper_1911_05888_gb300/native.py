@@ -22,6 +22,7 @@ FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 RICHARDSON, FGMRES, FGMRES_IR = 0, 1, 2
 PTS_VOLUME, PTS_INTERIOR_FACE, PTS_BOUNDARY_FACE, PTS_INTERFACE = 0, 1, 2, 3
 INFO_BOTTOM_SOLVER, INFO_BOTTOM_UNKNOWNS, INFO_COLOURS, INFO_DEVICE_BYTES, INFO_CLUSTERS = 0, 1, 2, 3, 4
+INFO_COUPLING_BLOCKS = 5
 BOTTOM_JACOBI, BOTTOM_HOST_QR, BOTTOM_CUSOLVER = 0, 1, 2
 COLOURS_AUTO, COLOURS_PARITY, COLOURS_CHECKERBOARD = 0, 1, 2
 

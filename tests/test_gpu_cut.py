@@ -29,15 +29,20 @@ from oracle import cutcell, cutldg, cuthier, multigrid  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 # name -> (problem, block tolerance of the finest level, of coarse levels,
-#          V-cycle iterate tolerance)
+#          V-cycle iterate tolerance, residual tolerance); the residual of a
+#          random x multiplies the block differences by the operator's largest
+#          entries, which the unsteady mass term rho / (delta mu) raises
 CASES = {
-    "c8p2-mu10": (lambda: P.CutProblem(n=8, p=2, mu_phase=(1.0, 10.0)), 1e-13, 1e-12, 1e-10),
-    "c16p2-mu1e-3": (lambda: P.CutProblem(n=16, p=2, mu_phase=(1e-3, 1.0)), 1e-13, 1e-12, 1e-10),
+    "c8p2-mu10": (lambda: P.CutProblem(n=8, p=2, mu_phase=(1.0, 10.0)), 1e-13, 1e-12, 1e-10, 1e-11),
+    "c16p2-mu1e-3": (lambda: P.CutProblem(n=16, p=2, mu_phase=(1e-3, 1.0)), 1e-13, 1e-12, 1e-10, 1e-11),
     "c16p3-mu1e3-rho1e3": (lambda: P.CutProblem(n=16, p=3, mu_phase=(1e3, 1.0), rho_phase=(1e3, 1.0), delta=0.01),
-                           1e-11, 1e-9, 1e-7),
-    "c12p1-standard": (lambda: P.CutProblem(n=12, p=1, gamma=0, mu_phase=(1.0, 10.0)), 1e-13, 1e-12, 1e-10),
+                           1e-11, 1e-9, 1e-7, 1e-9),
+    # the paper's bubble fluids at ratio 1e3 (light bubble: rho = mu = 1e-3 inside), delta = 0.1 h
+    "c16p3-bubble": (lambda: P.CutProblem(n=16, p=3, mu_phase=(1e-3, 1.0), rho_phase=(1e-3, 1.0), delta=0.1 / 16),
+                     1e-11, 1e-9, 1e-7, 1e-8),
+    "c12p1-standard": (lambda: P.CutProblem(n=12, p=1, gamma=0, mu_phase=(1.0, 10.0)), 1e-13, 1e-12, 1e-10, 1e-11),
     "c20p2-offcentre": (lambda: P.CutProblem(n=20, p=2, mu_phase=(1.0, 1e-3), centre=(0.47, 0.53)),
-                        1e-13, 1e-12, 1e-10),
+                        1e-13, 1e-12, 1e-10, 1e-11),
 }
 
 _cache = {}
@@ -121,7 +126,7 @@ def test_cut_points_match_oracle(name):
 @pytest.mark.parametrize("name", list(CASES))
 def test_cut_hierarchy_blocks_and_colours(name):
     prob, gpu, mesh, levels, inj, orc = get(name)
-    _, tol0, tolc, _ = CASES[name]
+    _, tol0, tolc, _, _ = CASES[name]
     assert gpu.nlevels == len(levels)
     assert [int(v) for v in gpu.ne_levels] == [lev.ne for lev in levels]
     assert gpu.n_snapped == orc.kernel_dim_bottom
@@ -152,7 +157,7 @@ def test_cut_colour_step_and_residual(name):
     so that one step's difference is measured at a time) and the FP64
     residual: the GPU against the oracle's smoother step on its own blocks."""
     prob, gpu, mesh, levels, inj, orc = get(name)
-    _, tol0, _, _ = CASES[name]
+    _, tol0, _, _, tolr = CASES[name]
     rng = np.random.default_rng(11)
     lev = levels[0]
     n = lev.ne * lev.nb
@@ -172,8 +177,8 @@ def test_cut_colour_step_and_residual(name):
     nrm = gpu.ctx.residual(xd, bd, r, want_norm=True)
     ro = orc.residual(0, xo, b)
     print(name, "colour step %.1e residual %.1e" % (worst, maxrel(r.cpu().numpy(), ro)))
-    assert maxrel(r.cpu().numpy(), ro) <= 100 * tol0
-    assert abs(nrm - np.linalg.norm(ro)) <= 100 * tol0 * np.linalg.norm(ro)
+    assert maxrel(r.cpu().numpy(), ro) <= tolr
+    assert abs(nrm - np.linalg.norm(ro)) <= tolr * np.linalg.norm(ro)
     assert worst <= 1e4 * tol0
 
 
@@ -199,9 +204,10 @@ def test_cut_transfers_and_bottom(name):
     gpu.ctx.bottom_solve(dev(bb), xb)
     xo = orc.bottom_solve(bb)
     # the two pseudo-inverses agree to rounding times the condition number of
-    # the bottom operator on its range (the snapped direction excluded)
+    # the bottom operator on its range (the snapped direction excluded), with
+    # a factor 10 for the rounding constant of the two eigensolvers
     lam = np.sort(np.abs(np.linalg.eigvalsh(lev.A.toarray())))[orc.kernel_dim_bottom:]
-    tol = max(1e-12, 1e-16 * lam[-1] / lam[0])
+    tol = 10 * max(1e-13, 1e-16 * lam[-1] / lam[0])
     print(name, "bottom %.1e (tolerance %.1e)" % (maxrel(xb.cpu().numpy(), xo), tol))
     assert maxrel(xb.cpu().numpy(), xo) <= tol
 
@@ -260,17 +266,20 @@ def test_cut_rhs_matches_oracle(name):
 @pytest.mark.parametrize("name,precision", [("c16p2-mu1e-3", native.FP64), ("c16p2-mu1e-3", native.FP32),
                                             ("c16p3-mu1e3-rho1e3", native.FP64),
                                             ("c16p3-mu1e3-rho1e3", native.FP32),
+                                            ("c16p3-bubble", native.FP32),
                                             ("c12p1-standard", native.FP32)])
 def test_cut_solve_solves_the_oracle_system(name, precision):
     """FGMRES with the V-cycle (FP64 or FP32 blocks) solves the scaled system
     D A D x~ = D b of the manufactured problem to 1e-10, and its solution
     solves the oracle's own system (oracle operator, oracle right-hand side)
-    to 1e-9: what the two implementations must agree on.  A solution-level
-    comparison would only hold to cond(A) times the residual, and along the
-    constant pressure, a kernel only up to the curved pieces' quadrature
-    error, not even that; the velocity is compared at cond-independent
-    accuracy instead through the manufactured solution (L2 error below 1e-2
-    of its norm at these resolutions)."""
+    to 1e-9: what the two implementations must agree on.  Its velocity field
+    equals the one of the oracle's direct solution (L2 over the pieces' rules,
+    1e-7 of its norm); the pressure is not compared, since the constant
+    pressure is a kernel direction only up to the curved pieces' quadrature
+    error and the solution's component along it is not determined to more
+    than cond(A) times the residual."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
     prob, gpu, mesh, levels, inj, orc = get(name, precision)
     gpu.ctx.set_solver(native.FGMRES, 30)
     b = gpu.rhs().ravel()
@@ -287,19 +296,26 @@ def test_cut_solve_solves_the_oracle_system(name, precision):
     bo -= z * (z @ bo)
     xg = xd.cpu().numpy()
     res = np.linalg.norm(bo - lev.A @ xg) / np.linalg.norm(bo)
-    # velocity error against the manufactured solution, on the pieces' rules
+    A = lev.A
+    Aa = sp.bmat([[A, sp.csr_matrix(z[:, None])], [sp.csr_matrix(z[None, :]), None]], format="csc")
+    xo = spla.spsolve(Aa, np.concatenate([bo, [0.0]]))[:-1]
+    # velocity fields of the two solutions, on the pieces' rules
     els = lev.ops["els"]
-    x = (D * xg).reshape(lev.ne, lev.nb)
-    err = nrm = 0.0
+    xgu = (lev.D * xg).reshape(lev.ne, lev.nb)
+    xou = (lev.D * xo).reshape(lev.ne, lev.nb)
+    diff = nrm = 0.0
     for e in range(lev.ne):
         for k in els.pieces[e]:
             pc = mesh.pieces[k]
             Phi, _ = els.phi(e, pc["points"])
-            ue = prob.exact.u(pc["points"], chi=np.full(len(pc["weights"]), els.phase[e]))
             for i in range(2):
-                err += (pc["weights"] * (Phi @ x[e, i * lev.s:(i + 1) * lev.s] - ue[:, i]) ** 2).sum()
-                nrm += (pc["weights"] * ue[:, i] ** 2).sum()
+                ug = Phi @ xgu[e, i * lev.s:(i + 1) * lev.s]
+                uo = Phi @ xou[e, i * lev.s:(i + 1) * lev.s]
+                diff += (pc["weights"] * (ug - uo) ** 2).sum()
+                nrm += (pc["weights"] * uo ** 2).sum()
     print(name, precision, "iterations", it, "oracle-system residual %.1e" % res,
-          "velocity error %.1e" % np.sqrt(err / nrm))
+          "velocity difference %.1e" % np.sqrt(diff / nrm))
     assert res <= 1e-9
-    assert np.sqrt(err / nrm) <= 1e-2
+    # p = 1 standard form: cond(A) ~ 1e7 on velocity modes, so a 1e-10 residual
+    # leaves the velocity determined to ~1e-3 only
+    assert np.sqrt(diff / nrm) <= (1e-2 if prob.p == 1 else 1e-7)
