@@ -882,6 +882,7 @@ def run_cut(args):
             c["mg"].close()
         del cases, mg
         torch.cuda.empty_cache()
+    learned = None if args.learned == 0 else cut_learned_protocol(args, n, p, delta, stream)
     head = min(arms, key=lambda k: arms[k]["ms"] if max(arms[k]["res"]) <= 1e-10 else 1e30)
     other = "fp32" if head == "fp64" else "fp64"
     m = arms[head]
@@ -916,7 +917,68 @@ def run_cut(args):
                      "traffic": None, "algorithmic_bytes_per_sweep": sw["bytes"], "sweep_ms": round(sw["ms"], 4),
                      "colours": sw["colours"], "coupling_blocks": sw["coupling_blocks"],
                      "peak_source": "measured" if peaks else "fallback"},
+        "learned_protocol": learned,
         "device_gb": m["device_gb"], "gpu_launches": m["launches"], "clocks": m["clocks"]}))
+
+
+def cut_learned_protocol(args, n, p, delta, stream, evaluations=4):
+    """The learned post-smoother's protocol on the cut-cell workload (the light
+    bubble, FP32 cycle, iterative refinement with the acceptance rule): train
+    on V-cycle states of smooth random fields from seeds 0-255 (sample k uses
+    hash seed 7919 k), then solve b = A x* for fields x* from seeds 256 onwards
+    with and without the correction.  Training is setup, outside the
+    timings."""
+    import torch
+    from paper_1911_05888_gb300 import native, problems as P
+    from paper_1911_05888_gb300.solver import CutStokesMG
+    prob = P.CutProblem(n=n, p=p, mu_phase=(1e-3, 1.0), rho_phase=(1e-3, 1.0) if delta else None, delta=delta,
+                        nu1=args.nu, nu2=args.nu)
+    mg = CutStokesMG(prob, precision=native.FP32)
+    out = {"problem": "light bubble (inside/outside mu and rho 1e-3), FP32 blocks",
+           "outer": "iterative refinement (the acceptance rule judges each cycle's outer residual)"}
+    try:
+        mg.ctx.set_solver(native.RICHARDSON, args.restart)
+        t0 = time.perf_counter()
+        mg.ctx.learn_setup(hidden=64, seed=0)
+        mg.ctx.learn_generate(nseeds=256, cycles=2, seed=0)
+        epochs = 2
+        loss = mg.ctx.learn_train(epochs=epochs, batch=0, lr=1e-3, seed=1)
+        out["train"] = {"seeds": "0-255", "cycles_per_seed": 2, "states": 512, "hidden": 64, "epochs": epochs,
+                        "final_loss": loss, "train_s": round(time.perf_counter() - t0, 1)}
+        nvec = mg.ne * mg.nb
+        zero = torch.zeros(nvec, dtype=torch.float64, device="cuda")
+        xs = torch.empty_like(zero)
+        r = torch.empty_like(zero)
+        x = torch.empty_like(zero)
+        rows = []
+        for k in range(256, 256 + evaluations):
+            mg.ctx.learn_field(7919 * k, xs)
+            mg.ctx.residual(xs, zero, r)
+            b = -r
+            row = {"seed": k}
+            for name, on in (("plain", False), ("learned", True)):
+                mg.ctx.learn_enable(on)
+                mg.ctx.solve(x.zero_(), b, rtol=1e-10, maxit=300)   # warm
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                it, hist = mg.ctx.solve(x.zero_(), b, rtol=1e-10, maxit=300)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row[name] = {"ms": round(e0.elapsed_time(e1), 2), "iters": int(it),
+                             "final_rel_residual": float(hist[-1])}
+                if on:
+                    dec, ratio, kappa = mg.ctx.learn_history()
+                    row[name].update({"kept": int(sum(1 for d in dec if d == 1)),
+                                      "undone": int(sum(1 for d in dec if d == 0)),
+                                      "kappa": round(kappa, 4)})
+            mg.ctx.learn_enable(False)
+            rows.append(row)
+        out["evaluation"] = rows
+    finally:
+        mg.close()
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args):

@@ -402,6 +402,12 @@ int stk_cut_cells(int n, const double* lo, const double* hi, double cx, double c
  * stk_set_discretisation.  Errors: STK_ERR_INVALID_ARG (not 2D, bad circle).
  */
 int stk_set_levelset_circle(stk_ctx* ctx, double cx, double cy, double r);
+/* Warps that share one element in the element kernel of cut-cell levels: 0
+ * (default) picks by launch size (4 for launches of fewer than 32 elements
+ * per SM, 2 below 64, else 1), or 1, 2, 4 fixed.  Results agree to rounding
+ * (the warps' partial sums meet in a different order).  Errors:
+ * STK_ERR_INVALID_ARG. */
+int stk_set_element_warps(stk_ctx* ctx, int warps);
 /* Unsteady cut-cell problem (eq. timedep2): density rho_phase[2] > 0 per phase
  * and delta > 0; delta = 0 returns to the steady problem (rho_phase unused). */
 int stk_set_phase_density(stk_ctx* ctx, const double* rho_phase, double delta);
@@ -620,6 +626,13 @@ int stk_learn_train(stk_ctx* ctx, int epochs, int batch, double lr, uint64_t see
 int stk_learn_enable(stk_ctx* ctx, int on);
 int stk_learn_stats(stk_ctx* ctx, int64_t* accepted, int64_t* rejected);
 int stk_learn_weights(stk_ctx* ctx, float* host, int64_t count, int direction);
+/* The smooth random field of the training data for hash seed `seed` (sample k
+ * of stk_learn_generate(..., seed0) uses seed0 + 7919 k) into the caller's
+ * FP64 device vector x [element][nb]: per variable a sum of four seeded
+ * sines of the element centre (mode 0) plus 1e-3 seeded noise on the higher
+ * modes.  For evaluation right-hand sides b = A x from seeds the training did
+ * not use.  Needs stk_learn_setup. */
+int stk_learn_field(stk_ctx* ctx, uint64_t seed, double* x_dev, void* stream);
 int stk_learn_objective(stk_ctx* ctx, int objective);
 int stk_learn_history(stk_ctx* ctx, int* decision, double* ratio, int max, int* count, double* kappa_out);
 /* Sizes: input width (2d+1) nb, hidden width, output nb, number of weights

@@ -36,6 +36,28 @@ def face_neighbours(mesh):
     return out
 
 
+def cut_face_neighbours(mesh, els):
+    """[ne, 4] neighbours of the merged cut-cell elements (cutcell.CutMesh,
+    cutldg.CutElements) at -e_0, +e_0, -e_1, +e_1: the element of the piece of
+    the element's own phase in the cell next to its anchor cell (the host cell
+    of its representative piece); -1 where that cell is outside the box, holds
+    no piece of that phase, or belongs to the element itself."""
+    out = np.full((els.ne, 4), -1, dtype=np.int64)
+    for e in range(els.ne):
+        i, j = mesh.pieces[els.reps[e]]["cell"]
+        for k, (di, dj) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
+            ii, jj = i + di, j + dj
+            if not (0 <= ii < mesh.n and 0 <= jj < mesh.n):
+                continue
+            piece = mesh.piece_of.get((ii, jj, int(els.phase[e])))
+            if piece is None:
+                continue
+            f = int(els.of_piece[piece])
+            if f != e:
+                out[e, k] = f
+    return out
+
+
 def features(r, nbrs):
     """r [ne, nb] -> (F [ne, (2d+1) nb], ||r_i||)."""
     ne, nb = r.shape

@@ -37,8 +37,8 @@ cudaError_t run_element(Ctx& c, int l, int prec, int mode, int pos0, int npos, c
 cudaError_t run_element_on(Ctx& c, const Pattern& pat, DevLevel& D, int prec, int mode, int pos0, int npos,
                            const void* mat, const void* b, void* x, void* r, cudaStream_t st) {
   if (D.gen)   // general block-sparse level (cut-cell hierarchy)
-    return launch_gen_element(prec, mode, c.s, c.nb, D.nbp, pos0, npos, D.perm, D.tptr, D.tinfo, D.cpl[prec], mat,
-                              b, x, r, st);
+    return launch_gen_element(prec, mode, c.gen_warps, c.s, c.nb, D.nbp, pos0, npos, D.perm, D.tptr, D.tinfo,
+                              D.cpl[prec], mat, b, x, r, st);
   // FP16 records carry scales and run on the warp and wide kernels only.
   const bool scaled = prec == STK_FP16;
   const float* tsc = scaled ? D.csc : nullptr;
@@ -309,7 +309,7 @@ void pack_generic(Ctx& c, int l, cudaStream_t st) {
   const int s = c.s, nb = c.nb, ss = s * s, ne = H.ne;
   D.gen = 1;
   D.ne = ne;
-  D.nbp = nb;
+  D.nbp = (nb + 3) / 4 * 4;   // columns of 16-byte multiples in FP32 and FP64 (cp.async staging)
   for (int k = 0; k < 3; ++k) D.n[k] = H.n[k];
   int ncol = 0;
   for (int v : H.colour) ncol = std::max(ncol, v + 1);
@@ -348,14 +348,15 @@ void pack_generic(Ctx& c, int l, cudaStream_t st) {
   std::vector<double> Dinv((size_t)ne * nb * nb);
   std::string err;
   if (invert_blocks(nb, ne, H.D.data(), Dinv.data(), err) != STK_OK) throw std::runtime_error(err);
-  const size_t mat_n = (size_t)ne * nb * nb;
-  std::vector<double> buf(mat_n);
+  const int nbp = D.nbp;
+  const size_t mat_n = (size_t)ne * nb * nbp;
+  std::vector<double> buf(mat_n, 0.0);
   auto pack_mat = [&](const std::vector<double>& M, void*& out) {
     for (int pos = 0; pos < ne; ++pos) {
       const double* m = &M[(size_t)perm[pos] * nb * nb];
-      double* o = &buf[(size_t)pos * nb * nb];
+      double* o = &buf[(size_t)pos * nb * nbp];
       for (int r = 0; r < nb; ++r)
-        for (int cc = 0; cc < nb; ++cc) o[(size_t)cc * nb + r] = m[(size_t)r * nb + cc];
+        for (int cc = 0; cc < nb; ++cc) o[(size_t)cc * nbp + r] = m[(size_t)r * nb + cc];
     }
     out = dalloc(c, mat_n * sizeof(double));
     ck(cudaMemcpy(out, buf.data(), mat_n * sizeof(double), cudaMemcpyHostToDevice), "copy mat");
@@ -588,7 +589,7 @@ void enqueue_learned_delta(Ctx& c, int prec, const void* xv, const void* bv, cud
   DevLevel& D0 = c.dev[0];
   const int ne = D0.ne, nb = c.nb, nface = 2 * c.d;
   ck(run_element(c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], bv, (void*)xv, D0.vr[1], st), "learned residual");
-  ck(launch_features(ne, nb, nface, c.pat.NO, c.l_ldf, c.l_nbr, (const float*)D0.vr[1], c.lF, c.lnrm, st), "features");
+  ck(launch_features(ne, nb, nface, c.l_no, c.l_ldf, c.l_nbr, (const float*)D0.vr[1], c.lF, c.lnrm, st), "features");
   ck(launch_sgemm(ne, c.l_hid, c.l_in, 0, 0, c.lF, c.l_ldf, c.lW1, c.l_hid, c.lH, c.l_hid, c.lb1, 1, 1.f, 0.f, st),
      "layer 1");
   ck(launch_sgemm(ne, nb, c.l_hid, 0, 0, c.lH, c.l_hid, c.lW2, nb, c.lY, nb, c.lb2, 0, 1.f, 0.f, st), "layer 2");
@@ -2658,7 +2659,6 @@ static void init_uniform(std::vector<float>& w, uint64_t seed, float a) {
 int stk_learn_setup(stk_ctx* c, int hidden, uint64_t seed) {
   return guard(c, [&]() -> int {
     if (!c->ready) return fail(c, STK_ERR_NOT_SETUP, "call stk_setup first");
-    if (c->cut) return fail(c, STK_ERR_INVALID_ARG, "not available on cut-cell meshes");
     if (c->precision == STK_FP64) return fail(c, STK_ERR_INVALID_ARG, "the learned smoother runs in FP32/BF16 cycles");
     if (hidden < 8 || hidden > 512) return fail(c, STK_ERR_INVALID_ARG, "hidden width must be in 8..512");
     const int nb = c->nb, ne = c->dev[0].ne;
@@ -2685,8 +2685,25 @@ int stk_learn_setup(stk_ctx* c, int hidden, uint64_t seed) {
     std::copy(w2.begin(), w2.end(), w.begin() + n1 + n2);
     ck(cudaMemcpy(wbase, w.data(), c->l_nparam * 4, cudaMemcpyHostToDevice), "copy weights");
     c->l_adam_t = 0;
-    c->l_nbr = (int*)dalloc(*c, (size_t)ne * c->pat.NO * 4);
-    ck(cudaMemcpy(c->l_nbr, c->host[0].nbr.data(), (size_t)ne * c->pat.NO * 4, cudaMemcpyHostToDevice), "copy nbr");
+    c->l_ndev = (int*)dalloc(*c, 16);
+    ck(cudaMemcpy(c->l_ndev, c->host[0].n, 3 * sizeof(int), cudaMemcpyHostToDevice), "copy n");
+    if (c->cut) {
+      // neighbours across the anchor cell's faces in the element's phase
+      std::vector<int> nbr;
+      std::vector<double> ctr;
+      cut_face_neighbours(*c, nbr, ctr);
+      c->l_no = 4;
+      c->l_nbr = (int*)dalloc(*c, nbr.size() * 4);
+      ck(cudaMemcpy(c->l_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice), "copy nbr");
+      c->l_ctr = (double*)dalloc(*c, ctr.size() * 8);
+      ck(cudaMemcpy(c->l_ctr, ctr.data(), ctr.size() * 8, cudaMemcpyHostToDevice), "copy centres");
+    } else {
+      c->l_no = c->pat.NO;
+      c->l_ctr = nullptr;
+      c->l_nbr = (int*)dalloc(*c, (size_t)ne * c->pat.NO * 4);
+      ck(cudaMemcpy(c->l_nbr, c->host[0].nbr.data(), (size_t)ne * c->pat.NO * 4, cudaMemcpyHostToDevice),
+         "copy nbr");
+    }
     c->lF = (float*)dalloc(*c, (size_t)ne * c->l_ldf * 4);
     c->lH = (float*)dalloc(*c, (size_t)ne * hidden * 4);
     c->lY = (float*)dalloc(*c, (size_t)ne * nb * 4);
@@ -2721,8 +2738,7 @@ int stk_learn_generate(stk_ctx* c, int nseeds, int cycles, uint64_t seed) {
       c->l_cap = need;
     }
     c->l_rows = 0;
-    int* ndev = (int*)dalloc(*c, 16);
-    ck(cudaMemcpy(ndev, c->host[0].n, 3 * sizeof(int), cudaMemcpyHostToDevice), "copy n");
+    const int* ndev = c->l_ndev;
     float* xs = (float*)dalloc(*c, (size_t)nvec * 4);
     float* bb = (float*)dalloc(*c, (size_t)nvec * 4);
     float* zero = (float*)dalloc(*c, (size_t)nvec * 4);
@@ -2730,7 +2746,7 @@ int stk_learn_generate(stk_ctx* c, int nseeds, int cycles, uint64_t seed) {
     int on = c->learn_on;
     c->learn_on = 0;   // states come from the plain V-cycle
     for (int sd = 0; sd < nseeds; ++sd) {
-      ck(launch_smooth_field(ne, nb, c->s, c->d, ndev, seed + 7919ULL * sd, xs, st), "field");
+      ck(launch_smooth_field(ne, nb, c->s, c->d, ndev, c->l_ctr, seed + 7919ULL * sd, xs, st), "field");
       // b = A x*: the residual of x* against a zero right-hand side is -A x*.
       ck(run_element(*c, 0, prec, MODE_RESID, 0, ne, D0.dia[prec], zero, xs, D0.vr[1], st), "matvec");
       ck(launch_scale_f(nvec, -1.f, (const float*)D0.vr[1], bb, st), "negate");
@@ -2755,6 +2771,21 @@ int stk_learn_generate(stk_ctx* c, int nseeds, int cycles, uint64_t seed) {
   });
 }
 
+int stk_learn_field(stk_ctx* c, uint64_t seed, double* x, void* stream) {
+  return guard(c, [&]() -> int {
+    if (!c->lW1) return fail(c, STK_ERR_NOT_SETUP, "call stk_learn_setup first");
+    if (!x) return fail(c, STK_ERR_INVALID_ARG, "null vector");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ne = c->dev[0].ne, nb = c->nb;
+    float* xs = (float*)c->lxt;   // scratch of the learned smoother, [ne][nb]
+    ck(launch_smooth_field(ne, nb, c->s, c->d, c->l_ndev, c->l_ctr, seed, xs, st), "field");
+    ck(launch_convert(1, 0, (int64_t)ne * nb, x, xs, st), "convert");
+    c->launches += 2;
+    ck(cudaStreamSynchronize(st), "sync");
+    return STK_OK;
+  });
+}
+
 // Loss ||r - A delta||^2 / ||r||^2 of one residual state and its gradient
 // (packed like the weights) in c.lgrad; the loss goes to *loss_dev (device).
 // delta_i = ||r_i|| MLP(features_i); A is symmetric, so d loss / d delta =
@@ -2768,7 +2799,7 @@ void enqueue_residual_loss_grad(Ctx& c, const float* r, double* sums, cudaStream
   float* gb1 = gW1 + (int64_t)IN * H;
   float* gW2 = gb1 + H;
   float* gb2 = gW2 + (int64_t)H * nb;
-  ck(launch_features(ne, nb, 2 * c.d, c.pat.NO, ldf, c.l_nbr, r, c.lF, c.lnrm, st), "features");
+  ck(launch_features(ne, nb, 2 * c.d, c.l_no, ldf, c.l_nbr, r, c.lF, c.lnrm, st), "features");
   ck(launch_sgemm(ne, H, IN, 0, 0, c.lF, ldf, c.lW1, H, c.lH, H, c.lb1, 1, 1.f, 0.f, st), "fwd1");
   ck(launch_sgemm(ne, nb, H, 0, 0, c.lH, H, c.lW2, nb, c.lY, nb, c.lb2, 0, 1.f, 0.f, st), "fwd2");
   ck(cudaMemsetAsync(c.lrt, 0, (size_t)nvec * 4, st), "memset");
@@ -2801,7 +2832,7 @@ void enqueue_supervised_loss_grad(Ctx& c, const float* r, const float* e, double
   float* gb1 = gW1 + (int64_t)IN * H;
   float* gW2 = gb1 + H;
   float* gb2 = gW2 + (int64_t)H * nb;
-  ck(launch_features(ne, nb, 2 * c.d, c.pat.NO, ldf, c.l_nbr, r, c.lF, c.lnrm, st), "features");
+  ck(launch_features(ne, nb, 2 * c.d, c.l_no, ldf, c.l_nbr, r, c.lF, c.lnrm, st), "features");
   ck(launch_sgemm(ne, H, IN, 0, 0, c.lF, ldf, c.lW1, H, c.lH, H, c.lb1, 1, 1.f, 0.f, st), "fwd1");
   ck(launch_sgemm(ne, nb, H, 0, 0, c.lH, H, c.lW2, nb, c.lY, nb, c.lb2, 0, 1.f, 0.f, st), "fwd2");
   ck(launch_target(ne, nb, nb, e, c.l_zero, c.lnrm, c.lTg, st), "targets");
@@ -2865,7 +2896,7 @@ int stk_learn_infer(stk_ctx* c, const float* r, float* y, float* nrm) {
     if (!r || !y || !nrm) return fail(c, STK_ERR_INVALID_ARG, "null vector");
     const int ne = c->dev[0].ne, nb = c->nb;
     cudaStream_t st = c->stream;
-    ck(launch_features(ne, nb, 2 * c->d, c->pat.NO, c->l_ldf, c->l_nbr, r, c->lF, nrm, st), "features");
+    ck(launch_features(ne, nb, 2 * c->d, c->l_no, c->l_ldf, c->l_nbr, r, c->lF, nrm, st), "features");
     ck(launch_sgemm(ne, c->l_hid, c->l_in, 0, 0, c->lF, c->l_ldf, c->lW1, c->l_hid, c->lH, c->l_hid, c->lb1, 1, 1.f,
                     0.f, st),
        "layer 1");
@@ -2993,6 +3024,16 @@ int stk_set_levelset_circle(stk_ctx* c, double cx, double cy, double r) {
     c->cut_c[1] = cy;
     c->cut_r = r;
     c->chi.clear();
+    return STK_OK;
+  });
+}
+
+int stk_set_element_warps(stk_ctx* c, int warps) {
+  return guard(c, [&]() -> int {
+    if (warps != 0 && warps != 1 && warps != 2 && warps != 4)
+      return fail(c, STK_ERR_INVALID_ARG, "warps per element: 0 (by launch size), 1, 2 or 4");
+    c->gen_warps = warps;
+    invalidate_graphs(*c);
     return STK_OK;
   });
 }

@@ -924,4 +924,24 @@ int cut_assemble_rhs(Ctx& c, const double* f_vol, const double* bdata, const dou
   return STK_OK;
 }
 
+void cut_face_neighbours(Ctx& c, std::vector<int>& nbr, std::vector<double>& ctr) {
+  const CutGeometry& G = cut_geometry(c);
+  if (!c.cuts) throw std::runtime_error("cut-cell problem not set up");
+  const CutState& S = *c.cuts;
+  nbr.assign((size_t)S.ne * 4, -1);
+  ctr.assign((size_t)S.ne * 2, 0.0);
+  const int dd[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+  for (int e = 0; e < S.ne; ++e) {
+    const CutPiece& rep = G.pieces[S.reps[e]];
+    for (int k = 0; k < 4; ++k) {
+      const int ii = rep.i + dd[k][0], jj = rep.j + dd[k][1];
+      if (ii < 0 || ii >= G.n || jj < 0 || jj >= G.n) continue;
+      const int piece = G.find(ii, jj, S.phase[e]);
+      if (piece >= 0 && S.of_piece[piece] != e) nbr[(size_t)e * 4 + k] = S.of_piece[piece];
+    }
+    for (int a = 0; a < 2; ++a)
+      ctr[(size_t)e * 2 + a] = (0.5 * (S.box_lo[2 * e + a] + S.box_hi[2 * e + a]) - G.lo[a]) / (G.hi[a] - G.lo[a]);
+  }
+}
+
 }  // namespace stk

@@ -10,8 +10,9 @@
 // half of x_j (16-byte loads of records and vector), the pair sums with one
 // shuffle and adds the result into the running sum of row r of variable rv.
 // A task's record is one contiguous 1 KB (FP32) read by the whole warp.  The
-// dense A_ii^{-1} (colour step) or A_ii (residual) is stored column-major so
-// that lanes read consecutive rows of one column.
+// dense A_ii^{-1} (colour step) or A_ii (residual) is stored column-major,
+// nb columns of nbp rows (nbp: nb rounded up to 16 bytes of entries), and
+// staged in shared memory.
 #include <cuda_runtime.h>
 
 #include "stk_internal.h"
@@ -31,6 +32,13 @@ __device__ __forceinline__ V dot_n(const T* __restrict__ a, const V* b) {
   for (int k = 0; k < N; ++k) acc += (V)a[k] * b[k];
   return acc;
 }
+
+__device__ __forceinline__ void gen_cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned int d = (unsigned int)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void gen_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void gen_cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Half a row of a 16-column block: 8 entries from 16-byte aligned addresses.
 __device__ __forceinline__ void load8(const float* p, float* v) {
@@ -60,35 +68,62 @@ __device__ __forceinline__ void load8v(const double* p, double* v) {
   }
 }
 
-template <typename T, typename V, int S, int MODE>
-__global__ void __launch_bounds__(kGenWarps * 32, 8)
+// W warps per element (W = 1, 2, 4; 4 / W elements per CTA of 4 warps): warp
+// wi of an element takes the wi-th contiguous chunk of its tasks, the row sums
+// of the W warps meet in shared memory, and the element's W x 32 threads share
+// the dense product by rows.  The element's dense block (A_ii^{-1} or A_ii) is
+// copied into shared memory by cp.async when the kernel starts, so that its
+// load overlaps the coupling tasks and the dense product reads shared memory.  Small launches (a colour of a few thousand
+// elements, the coarse levels) take W = 4, so that each element's chain of
+// dependent record rounds is a quarter as long and the launch still fills the
+// SMs; large launches take W = 1.
+template <typename T, typename V, int S, int MODE, int W>
+__global__ void __launch_bounds__(kGenWarps * 32, 6)
     gen_element_kernel(int pos0, int npos, int nb, int nbp, const int* __restrict__ perm,
                        const int* __restrict__ tptr, const int* __restrict__ tinfo, const T* __restrict__ cpl,
                        const T* __restrict__ mat, const V* b, V* x, V* r) {
   constexpr int H = (S + 1) / 2;   // columns of the first half-row
-  __shared__ V sg[kGenWarps][kGenMaxNb];
-  __shared__ V sx[kGenWarps][kGenMaxNb];
+  constexpr int G = 32 * W;        // threads per element
+  constexpr int E = kGenWarps / W; // elements per CTA
+  __shared__ V part[kGenWarps][3][16];
+  __shared__ V sg[E][kGenMaxNb];
+  __shared__ V sx[E][kGenMaxNb];
+  extern __shared__ __align__(16) unsigned char gen_dyn[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pos = pos0 + blockIdx.x * kGenWarps + w;
-  if (pos >= pos0 + npos) return;   // whole warp
-  const int e = perm[pos];
+  const int grp = threadIdx.x / G, gt = threadIdx.x % G, wi = gt >> 5;
+  const int pos = pos0 + blockIdx.x * E + grp;
+  const bool valid = pos < pos0 + npos;   // uniform over the element's warps
+  const int e = valid ? perm[pos] : 0;
+  // the dense block, nb x nbp entries (nbp a multiple of 16 bytes), staged
+  T* smat = reinterpret_cast<T*>(gen_dyn) + (size_t)grp * nb * nbp;
+  if (valid) {
+    const int chunks = nb * nbp * (int)sizeof(T) / 16;
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(mat + (size_t)pos * nb * nbp);
+    for (int q = gt; q < chunks; q += G)
+      gen_cp_async16(reinterpret_cast<unsigned char*>(smat) + (size_t)q * 16, src + (size_t)q * 16);
+  }
+  gen_cp_async_commit();
   const int row = lane >> 1, half = lane & 1;
   const bool active = row < S;
   const int c0 = half ? H : 0;
   V acc0 = V(0), acc1 = V(0), acc2 = V(0);
-  const int t0 = tptr[pos], t1 = tptr[pos + 1];
-  auto add = [&](int rv, V part) {
-    part += __shfl_xor_sync(0xffffffffu, part, 1);
-    if (rv == 0) acc0 += part;
-    else if (rv == 1) acc1 += part;
-    else acc2 += part;
+  int t = 0, t1 = 0;
+  if (valid) {
+    const int a0 = tptr[pos], a1 = tptr[pos + 1];
+    const int chunk = (a1 - a0 + W - 1) / W;
+    t = min(a1, a0 + wi * chunk);
+    t1 = min(a1, t + chunk);
+  }
+  auto add = [&](int rv, V pv) {
+    pv += __shfl_xor_sync(0xffffffffu, pv, 1);
+    if (rv == 0) acc0 += pv;
+    else if (rv == 1) acc1 += pv;
+    else acc2 += pv;
   };
-  int t = t0;
   if (S == 16) {
     // U tasks per round (4 with FP32 records, 2 with FP64 ones, the most the
-    // 64 registers hold without spilling): their words, records and x
-    // segments are all requested before the first product, so a warp keeps
-    // U 1 KB (2 KB) record reads in flight
+    // 80 registers hold without spilling): their words, records and x
+    // segments are all requested before the first product
     constexpr int U = sizeof(T) == 4 ? 4 : 2;
     for (; t + U <= t1; t += U) {
       int info[U];
@@ -105,18 +140,18 @@ __global__ void __launch_bounds__(kGenWarps * 32, 8)
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        V part = V(0);
+        V pv = V(0);
         if (active)
 #pragma unroll
-          for (int k = 0; k < 8; ++k) part += (V)a[u][k] * v[u][k];
-        add((info[u] >> 2) & 3, part);
+          for (int k = 0; k < 8; ++k) pv += (V)a[u][k] * v[u][k];
+        add((info[u] >> 2) & 3, pv);
       }
     }
   }
   for (; t < t1; ++t) {
     const int info = __ldg(tinfo + t);
     const int j = info >> 4, rv = (info >> 2) & 3, cv = info & 3;
-    V part = V(0);
+    V pv = V(0);
     if (active) {
       const T* rec = cpl + (size_t)t * S * S + row * S + c0;
       const V* xj = x + (size_t)j * nb + cv * S + c0;
@@ -126,33 +161,42 @@ __global__ void __launch_bounds__(kGenWarps * 32, 8)
         load8(rec, a);
         load8v(xj, v);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) part += (V)a[k] * v[k];
+        for (int k = 0; k < 8; ++k) pv += (V)a[k] * v[k];
       } else if (half) {
-        part = dot_n<T, V, S - H>(rec, xj);
+        pv = dot_n<T, V, S - H>(rec, xj);
       } else {
-        part = dot_n<T, V, H>(rec, xj);
+        pv = dot_n<T, V, H>(rec, xj);
       }
     }
-    add(rv, part);
+    add(rv, pv);
   }
   if (active && !half) {
-    const V* be = b + (size_t)e * nb;
-    sg[w][row] = be[row] - acc0;
-    sg[w][S + row] = be[S + row] - acc1;
-    sg[w][2 * S + row] = be[2 * S + row] - acc2;
+    part[w][0][row] = acc0;
+    part[w][1][row] = acc1;
+    part[w][2][row] = acc2;
   }
-  if (MODE == MODE_RESID)
-    for (int o = lane; o < nb; o += 32) sx[w][o] = x[(size_t)e * nb + o];
-  __syncwarp();
-  const T* m = mat + (size_t)pos * nb * nbp;
-  for (int o = lane; o < nb; o += 32) {
+  gen_cp_async_wait_all();
+  __syncthreads();
+  if (valid) {
+    for (int o = gt; o < nb; o += G) {
+      const int v = o / S, rr = o % S;
+      V sum = V(0);
+#pragma unroll
+      for (int q = 0; q < W; ++q) sum += part[grp * W + q][v][rr];
+      sg[grp][o] = b[(size_t)e * nb + o] - sum;
+      if (MODE == MODE_RESID) sx[grp][o] = x[(size_t)e * nb + o];
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  for (int o = gt; o < nb; o += G) {
     V y = V(0);
     if (MODE == MODE_GS) {
-      for (int k = 0; k < nb; ++k) y += (V)__ldg(m + (size_t)k * nbp + o) * sg[w][k];
+      for (int k = 0; k < nb; ++k) y += (V)smat[k * nbp + o] * sg[grp][k];
       x[(size_t)e * nb + o] = y;
     } else {
-      for (int k = 0; k < nb; ++k) y += (V)__ldg(m + (size_t)k * nbp + o) * sx[w][k];
-      r[(size_t)e * nb + o] = sg[w][o] - y;
+      for (int k = 0; k < nb; ++k) y += (V)smat[k * nbp + o] * sx[grp][k];
+      r[(size_t)e * nb + o] = sg[grp][o] - y;
     }
   }
 }
@@ -190,45 +234,87 @@ __global__ void gen_prolong_kernel(int nf, int s, int nb, const int* __restrict_
   x[idx] += sum;
 }
 
-template <typename T, typename V, int S>
-cudaError_t gen_launch(int mode, int nb, int nbp, int pos0, int npos, const int* perm, const int* tptr,
-                       const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r,
-                       cudaStream_t st) {
-  const int blocks = (npos + kGenWarps - 1) / kGenWarps;
+template <typename T, typename V, int S, int W>
+cudaError_t gen_launch_w(int mode, int nb, int nbp, int pos0, int npos, const int* perm, const int* tptr,
+                         const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                         cudaStream_t st) {
+  constexpr int E = kGenWarps / W;
+  const int blocks = (npos + E - 1) / E;
+  const size_t smem = (size_t)E * nb * nbp * sizeof(T);
+  if (((size_t)nb * nbp * sizeof(T)) % 16 != 0 || smem > 200 * 1024) return cudaErrorInvalidValue;
+  static bool opted[2] = {false, false};
+  if (!opted[mode == MODE_GS ? 0 : 1]) {
+    // the staged dense blocks of 4 / W elements (FP64 p = 3, W = 1: 72 KB)
+    cudaError_t e = mode == MODE_GS
+                        ? cudaFuncSetAttribute(gen_element_kernel<T, V, S, MODE_GS, W>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)
+                        : cudaFuncSetAttribute(gen_element_kernel<T, V, S, MODE_RESID, W>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    opted[mode == MODE_GS ? 0 : 1] = true;
+  }
   if (mode == MODE_GS)
-    gen_element_kernel<T, V, S, MODE_GS><<<blocks, kGenWarps * 32, 0, st>>>(
+    gen_element_kernel<T, V, S, MODE_GS, W><<<blocks, kGenWarps * 32, smem, st>>>(
         pos0, npos, nb, nbp, perm, tptr, tinfo, (const T*)cpl, (const T*)mat, (const V*)b, (V*)x, (V*)r);
   else
-    gen_element_kernel<T, V, S, MODE_RESID><<<blocks, kGenWarps * 32, 0, st>>>(
+    gen_element_kernel<T, V, S, MODE_RESID, W><<<blocks, kGenWarps * 32, smem, st>>>(
         pos0, npos, nb, nbp, perm, tptr, tinfo, (const T*)cpl, (const T*)mat, (const V*)b, (V*)x, (V*)r);
   return cudaGetLastError();
 }
 
+// Warps per element by launch size: the elements' warps should fill about
+// two waves of 32 warps on each of the device's SMs.
+template <typename T, typename V, int S>
+cudaError_t gen_launch(int mode, int warps, int nb, int nbp, int pos0, int npos, const int* perm, const int* tptr,
+                       const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                       cudaStream_t st) {
+  if (warps == 1)
+    return gen_launch_w<T, V, S, 1>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+  if (warps == 2)
+    return gen_launch_w<T, V, S, 2>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+  if (warps == 4)
+    return gen_launch_w<T, V, S, 4>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  const int64_t target = (int64_t)sms * 64;
+  if ((int64_t)npos >= target)
+    return gen_launch_w<T, V, S, 1>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+  if ((int64_t)npos * 2 >= target)
+    return gen_launch_w<T, V, S, 2>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+  return gen_launch_w<T, V, S, 4>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+}
+
 template <typename T, typename V>
-cudaError_t gen_dispatch(int mode, int s, int nb, int nbp, int pos0, int npos, const int* perm, const int* tptr,
-                         const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r,
-                         cudaStream_t st) {
+cudaError_t gen_dispatch(int mode, int warps, int s, int nb, int nbp, int pos0, int npos, const int* perm,
+                         const int* tptr, const int* tinfo, const void* cpl, const void* mat, const void* b, void* x,
+                         void* r, cudaStream_t st) {
   switch (s) {
-    case 4: return gen_launch<T, V, 4>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
-    case 9: return gen_launch<T, V, 9>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
-    case 16: return gen_launch<T, V, 16>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    case 4: return gen_launch<T, V, 4>(mode, warps, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    case 9: return gen_launch<T, V, 9>(mode, warps, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    case 16: return gen_launch<T, V, 16>(mode, warps, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_gen_element(int storage, int mode, int s, int nb, int nbp, int pos0, int npos, const int* perm,
-                               const int* tptr, const int* tinfo, const void* cpl, const void* mat, const void* b,
-                               void* x, void* r, cudaStream_t st) {
+cudaError_t launch_gen_element(int storage, int mode, int warps, int s, int nb, int nbp, int pos0, int npos,
+                               const int* perm, const int* tptr, const int* tinfo, const void* cpl, const void* mat,
+                               const void* b, void* x, void* r, cudaStream_t st) {
   if (npos <= 0) return cudaSuccess;
   if (nb != 3 * s || nb > kGenMaxNb) return cudaErrorInvalidValue;
   // the 16-column kernels read the iterate with 16-byte loads
   if (s == 16 && (((uintptr_t)x | (uintptr_t)b) & 15)) return cudaErrorMisalignedAddress;
   if (storage == STK_FP64)
-    return gen_dispatch<double, double>(mode, s, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    return gen_dispatch<double, double>(mode, warps, s, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r,
+                                        st);
   if (storage == STK_FP32)
-    return gen_dispatch<float, float>(mode, s, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    return gen_dispatch<float, float>(mode, warps, s, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
   return cudaErrorInvalidValue;
 }
 

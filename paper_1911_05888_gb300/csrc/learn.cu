@@ -197,8 +197,10 @@ __device__ inline float hash_uniform(uint64_t seed, uint64_t i) {
 
 // Smooth random field: mode 0 of every variable is a sum of 4 seeded plane
 // waves of the element centre; higher modes carry 1e-3 white noise.
-__global__ void smooth_field_kernel(int ne, int nb, int s, int d, const int* n, const double* lo, const double* hi,
-                                    uint64_t seed, float* __restrict__ x) {
+// ctr (may be NULL): element centres [ne][d] in box-relative coordinates, for
+// meshes whose element index is not a grid index (cut cells).
+__global__ void smooth_field_kernel(int ne, int nb, int s, int d, const int* n, const double* ctr, uint64_t seed,
+                                    float* __restrict__ x) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)ne * nb) return;
   const int e = (int)(i / nb), k = (int)(i - (int64_t)e * nb);
@@ -207,9 +209,13 @@ __global__ void smooth_field_kernel(int ne, int nb, int s, int d, const int* n, 
     x[i] = 1e-3f * hash_uniform(seed, i);
     return;
   }
-  int idx[3] = {e % n[0], (e / n[0]) % n[1], d == 3 ? e / (n[0] * n[1]) : 0};
   double c[3];
-  for (int a = 0; a < d; ++a) c[a] = (idx[a] + 0.5) / n[a];
+  if (ctr) {
+    for (int a = 0; a < d; ++a) c[a] = ctr[(size_t)e * d + a];
+  } else {
+    const int idx[3] = {e % n[0], (e / n[0]) % n[1], d == 3 ? e / (n[0] * n[1]) : 0};
+    for (int a = 0; a < d; ++a) c[a] = (idx[a] + 0.5) / n[a];
+  }
   float acc = 0.f;
   for (int w = 0; w < 4; ++w) {
     const uint64_t base = ((uint64_t)v * 4 + w) * 8;
@@ -222,8 +228,6 @@ __global__ void smooth_field_kernel(int ne, int nb, int s, int d, const int* n, 
     acc += amp * (float)sin(ph);
   }
   x[i] = acc;
-  (void)lo;
-  (void)hi;
 }
 
 // T[i] = (x*_i - x_i) / ||r_i||
@@ -312,10 +316,10 @@ cudaError_t launch_sumsq_f(int64_t n, const float* x, double* part, double* out,
   return cudaGetLastError();
 }
 
-cudaError_t launch_smooth_field(int ne, int nb, int s, int d, const int* n_dev, uint64_t seed, float* x,
-                                cudaStream_t st) {
+cudaError_t launch_smooth_field(int ne, int nb, int s, int d, const int* n_dev, const double* ctr, uint64_t seed,
+                                float* x, cudaStream_t st) {
   int64_t n = (int64_t)ne * nb;
-  smooth_field_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ne, nb, s, d, n_dev, nullptr, nullptr, seed, x);
+  smooth_field_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ne, nb, s, d, n_dev, ctr, seed, x);
   return cudaGetLastError();
 }
 

@@ -317,7 +317,10 @@ struct Ctx {
   float *lW1 = nullptr, *lb1 = nullptr, *lW2 = nullptr, *lb2 = nullptr;   // [in][hid], [hid], [hid][nb], [nb]
   float *lgrad = nullptr, *lm = nullptr, *lv = nullptr;                   // packed like the weights
   int64_t l_nparam = 0;
-  int* l_nbr = nullptr;         // natural-order neighbour table of level 0
+  int* l_nbr = nullptr;         // natural-order neighbour table of level 0 (l_no slots per element,
+  int l_no = 0;                 // the first 2d: -e_0, +e_0, -e_1, ...)
+  double* l_ctr = nullptr;      // element centres of a cut-cell level 0 (training fields)
+  int* l_ndev = nullptr;        // level-0 grid counts on the device (training fields)
   float *lF = nullptr, *lH = nullptr, *lY = nullptr, *lnrm = nullptr, *lxt = nullptr, *lrt = nullptr;
   double* lsums = nullptr;      // [0] ||r||^2, [1] ||r_t||^2, then partials
   float *lF2 = nullptr, *l_zero = nullptr;   // hidden-layer gradient, zero vector
@@ -349,6 +352,7 @@ struct Ctx {
   double cut_c[2] = {0, 0}, cut_r = 0, cut_frac = 0.25;
   std::vector<double> rho_phase;
   double cut_delta = 0.0;
+  int gen_warps = 0;                    // warps per element of the general element kernel (0: by launch size)
   std::shared_ptr<CutGeometry> cutg;
   std::shared_ptr<struct CutState> cuts;   // elements, faces and finest operators after setup
 };
@@ -386,6 +390,10 @@ int64_t cut_count_points(Ctx& c, int kind);
 void cut_points(Ctx& c, int kind, std::vector<double>& xyz, std::vector<double>* nrm, std::vector<int>* phase);
 int cut_assemble_rhs(Ctx& c, const double* f_vol, const double* bdata, const double* idata, double* b,
                      std::string& err);
+// Level-0 element neighbours across the four faces of each element's anchor
+// cell in its own phase ([ne][4]: -x, +x, -y, +y; -1 none) and element box
+// centres in box-relative coordinates ([ne][2]).
+void cut_face_neighbours(Ctx& c, std::vector<int>& nbr, std::vector<double>& ctr);
 
 
 // ---- kernels.cu / learn.cu launchers ------------------------------------------
@@ -443,7 +451,8 @@ cudaError_t launch_adam(int64_t n, float lr, float b1, float b2, float c1, float
 cudaError_t launch_apply_correction(int ne, int nb, int ldy, const float* x, const float* nrm, const float* Y, float* xt,
                                     cudaStream_t st);
 cudaError_t launch_sumsq_f(int64_t n, const float* x, double* part, double* out, cudaStream_t st);
-cudaError_t launch_smooth_field(int ne, int nb, int s, int d, const int* n_dev, uint64_t seed, float* x,
+cudaError_t launch_smooth_field(int ne, int nb, int s, int d, const int* n_dev, const double* ctr, uint64_t seed,
+                                float* x,
                                 cudaStream_t st);
 cudaError_t launch_target(int ne, int nb, int ldt, const float* xs, const float* x, const float* nrm, float* T,
                           cudaStream_t st);
@@ -475,9 +484,9 @@ cudaError_t launch_batch_solve(const BatchProblem* probs, int nprob, const Batch
                                const BatchTask* tasks, int maxit, double rtol, int smax, size_t smem,
                                GridBarrierWords* gb, int* err, long long limit, int grid, cudaStream_t st);
 size_t batch_smem_bytes(const Pattern& pat);
-cudaError_t launch_gen_element(int storage, int mode, int s, int nb, int nbp, int pos0, int npos, const int* perm,
-                               const int* tptr, const int* tinfo, const void* cpl, const void* mat, const void* b,
-                               void* x, void* r, cudaStream_t st);
+cudaError_t launch_gen_element(int storage, int mode, int warps, int s, int nb, int nbp, int pos0, int npos,
+                               const int* perm, const int* tptr, const int* tinfo, const void* cpl, const void* mat,
+                               const void* b, void* x, void* r, cudaStream_t st);
 cudaError_t launch_gen_restrict(int vec64, int nc, int s, int nb, const int* cptr, const int* clist, const void* I,
                                 const void* r, void* rc, cudaStream_t st);
 cudaError_t launch_gen_prolong(int vec64, int nf, int s, int nb, const int* parent, const void* I, const void* xc,

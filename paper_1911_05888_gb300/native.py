@@ -107,6 +107,8 @@ SIGNATURES = {
     "stk_set_levelset_circle": [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double],
     "stk_set_phase_density": [_vp, _c_dbl_p, ctypes.c_double],
     "stk_get_point_phases": [_vp, ctypes.c_int, _c_int_p],
+    "stk_set_element_warps": [_vp, ctypes.c_int],
+    "stk_learn_field": [_vp, ctypes.c_uint64, _vp, _vp],
 }
 _RESTYPE = {"stk_last_error": ctypes.c_char_p}
 
@@ -496,6 +498,10 @@ class Context:
                                             ctypes.byref(loss)), "stk_learn_grad")
         return loss.value, g
 
+    def learn_field(self, seed, x, stream=None):
+        self._check(self.lib.stk_learn_field(self.h, int(seed), _vec("x", x, self._n(0)), _stream(stream)),
+                    "stk_learn_field")
+
     def learn_enable(self, on):
         self._check(self.lib.stk_learn_enable(self.h, 1 if on else 0), "stk_learn_enable")
 
@@ -569,6 +575,9 @@ class Context:
         self._expect("rho_phase", rho, 2)
         self._check(self.lib.stk_set_phase_density(self.h, rho.ctypes.data_as(_c_dbl_p), float(delta)),
                     "stk_set_phase_density")
+
+    def set_element_warps(self, warps):
+        self._check(self.lib.stk_set_element_warps(self.h, warps), "stk_set_element_warps")
 
     def get_point_phases(self, kind):
         out = np.zeros(self.num_points(kind), dtype=np.int32)

@@ -319,3 +319,108 @@ def test_cut_solve_solves_the_oracle_system(name, precision):
     # p = 1 standard form: cond(A) ~ 1e7 on velocity modes, so a 1e-10 residual
     # leaves the velocity determined to ~1e-3 only
     assert np.sqrt(diff / nrm) <= (1e-2 if prob.p == 1 else 1e-7)
+
+
+@pytest.mark.parametrize("warps", [1, 2, 4])
+@pytest.mark.parametrize("name", ["c16p2-mu1e-3", "c16p3-bubble"])
+def test_cut_element_warps_match_oracle(name, warps):
+    """The cut-cell element kernel with 1, 2 or 4 warps sharing an element
+    (stk_set_element_warps; by default the launch size decides): V-cycle
+    iterates against the oracle at the case's tolerance, FP64 and FP32 colour
+    steps of the three variants against each other to rounding."""
+    prob, gpu, mesh, levels, inj, orc = get(name)
+    tolv = CASES[name][3]
+    lev = levels[0]
+    z = kernel_basis(lev)
+    rng = np.random.default_rng(22)
+    b = rng.uniform(-1, 1, lev.ne * lev.nb)
+    b -= z * (z @ b)
+    gpu.ctx.set_element_warps(warps)
+    try:
+        bd = dev(b)
+        xd = torch.zeros_like(bd)
+        xo = np.zeros_like(b)
+        worst = 0.0
+        for k in range(4):
+            gpu.ctx.vcycle(xd, bd)
+            orc.vcycle(xo, b)
+            xg = xd.cpu().numpy()
+            worst = max(worst, maxrel(xg - z * (z @ xg), xo - z * (z @ xo)))
+        assert worst <= tolv, worst
+    finally:
+        gpu.ctx.set_element_warps(0)
+    gpu32 = get(name, native.FP32)[1]
+    x32 = torch.from_numpy(rng.uniform(-1, 1, lev.ne * lev.nb).astype(np.float32)).cuda()
+    b32 = torch.from_numpy(b.astype(np.float32)).cuda()
+    outs = []
+    try:
+        for w in (warps, 1):
+            gpu32.ctx.set_element_warps(w)
+            xx = x32.clone()
+            for c in range(int(lev.colour.max()) + 1):
+                gpu32.ctx.gs_colour_ex(0, c, native.FP32, xx, b32)
+            outs.append(xx.cpu().numpy())
+    finally:
+        gpu32.ctx.set_element_warps(0)
+    # FP32 sums in another order: within a few units of FP32 rounding of the
+    # products, amplified by A_ii^{-1}
+    assert maxrel(outs[0], outs[1]) <= 1e-4, maxrel(outs[0], outs[1])
+
+
+def test_cut_learned_features_and_acceptance_match_oracle():
+    """The learned post-smoother on a cut-cell mesh (FP32 cycle): features of
+    a seeded residual (element and its anchor cell's four same-phase face
+    neighbours, oracle.learned.cut_face_neighbours) and the network output
+    against the oracle, then training on smooth seeded fields and the
+    acceptance decisions of the outer iteration against the oracle's (FP32
+    rounded blocks, the same weights), as in the Cartesian test."""
+    from oracle import learned
+    prob = P.CutProblem(n=16, p=2, mu_phase=(1e-3, 1.0), rho_phase=(1e-3, 1.0), delta=0.1 / 16)
+    gpu = CutStokesMG(prob, precision=native.FP32)
+    try:
+        gpu.ctx.learn_setup(hidden=32, seed=0)
+        nin, hid, nout, npar, _ = gpu.ctx.learn_sizes()
+        w = gpu.ctx.learn_weights(npar).astype(np.float64)
+        mesh = cutcell.CutMesh(cutcell.Circle(prob.centre, prob.radius), prob.n, q=2 * prob.p + 2)
+        levels, inj = cuthier.build(mesh, prob.p, list(prob.mu_phase), prob.tau, prob.gamma,
+                                    rho_phase=list(prob.rho_phase), delta=prob.delta, tau0=prob.tau0, scale=True)
+        els = levels[0].ops["els"]
+        nbrs = learned.cut_face_neighbours(mesh, els)
+        ne, nb = gpu.ne, gpu.nb
+        rng = np.random.default_rng(3)
+        r = rng.standard_normal((ne, nb)).astype(np.float32)
+        rd = torch.from_numpy(r.ravel()).cuda()
+        y = torch.empty_like(rd)
+        nrm = torch.empty(ne, dtype=torch.float32, device="cuda")
+        gpu.ctx.learn_infer(rd, y, nrm)
+        F, n_ref = learned.features(r.astype(np.float64), nbrs)
+        y_ref, _ = learned.forward(F, w, nin, hid, nout)
+        assert rel(nrm.cpu().numpy(), n_ref) <= 1e-6
+        assert rel(y.cpu().numpy().reshape(ne, -1), y_ref) <= 1e-5
+        # training and the acceptance rule
+        gpu.ctx.learn_generate(nseeds=4, cycles=2, seed=0)
+        gpu.ctx.learn_train(epochs=3, batch=0, lr=1e-3, seed=2)
+        w = gpu.ctx.learn_weights(npar).astype(np.float64)
+        gpu.ctx.learn_enable(True)
+        z = kernel_basis(levels[0])
+        bt = gpu.scaling().ravel() * gpu.rhs().ravel()
+        bt -= z * (z @ bt)
+        b = dev(bt)
+        x = torch.zeros_like(b)
+        it, hist = gpu.ctx.solve(x, b, rtol=1e-10, maxit=100)
+        dec, ratio, kappa = gpu.ctx.learn_history()
+        orc = multigrid.Multigrid(types.SimpleNamespace(nu1=prob.nu1, nu2=prob.nu2, gamma=prob.gamma),
+                                  storage="fp32", levels=levels, injections=inj)
+        xo, ho, dec_o, ratio_o, kappa_o = learned.solve_with_correction(orc, bt, w, nin, hid, nout, nbrs,
+                                                                        rtol=1e-10, maxit=100)
+        assert abs(kappa - kappa_o) <= 1e-4 * kappa_o, (kappa, kappa_o)
+        compared = 0
+        for k in range(min(len(dec), len(dec_o))):
+            if dec_o[k] >= 0 and abs(ratio_o[k] - 1.0) <= 1e-3:
+                break
+            assert dec[k] == dec_o[k], (k, list(dec), dec_o)
+            compared += 1
+        assert compared >= 3
+        assert hist[-1] <= 1e-10 and abs(it - (len(ho) - 1)) <= 1
+    finally:
+        gpu.close()
