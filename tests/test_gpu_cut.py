@@ -321,13 +321,13 @@ def test_cut_solve_solves_the_oracle_system(name, precision):
     assert np.sqrt(diff / nrm) <= (1e-2 if prob.p == 1 else 1e-7)
 
 
-@pytest.mark.parametrize("warps", [1, 2, 4])
+@pytest.mark.parametrize("warps", [0, 1, 2, 4])
 @pytest.mark.parametrize("name", ["c16p2-mu1e-3", "c16p3-bubble"])
 def test_cut_element_warps_match_oracle(name, warps):
-    """The cut-cell element kernel with 1, 2 or 4 warps sharing an element
-    (stk_set_element_warps; by default the launch size decides): V-cycle
-    iterates against the oracle at the case's tolerance, FP64 and FP32 colour
-    steps of the three variants against each other to rounding."""
+    """The cut-cell element kernel with 1, 2 or 4 warps sharing an element,
+    or by launch size (0, the default; stk_set_element_warps): V-cycle
+    iterates against the oracle at the case's tolerance, FP32 colour steps of
+    each variant against the one-warp variant to rounding."""
     prob, gpu, mesh, levels, inj, orc = get(name)
     tolv = CASES[name][3]
     lev = levels[0]
