@@ -791,6 +791,10 @@ def run_cut(args):
     n = args.n if args.n != 256 else 128
     p = args.p
     delta = 0.1 / n if args.delta < 0 else (args.delta if args.delta > 0 else None)
+    # the hierarchy stops at the first level of at most 4000 unknowns (the 8 x 8
+    # level at 128^2, about 3,800): the two coarsest agglomerated levels hold
+    # elements with cond(A_ii) up to 1e12, on which an FP32 smoother fails
+    bottom = args.bottom_max if args.bottom_max > 0 else 4000
     stream = torch.cuda.current_stream()
     precs = {"fp64": native.FP64, "fp32": native.FP32}
     if args.profile == "gs":
@@ -799,7 +803,7 @@ def run_cut(args):
         prec = precs.get(args.precision, native.FP32)
         prob = P.CutProblem(n=n, p=p, mu_phase=(1.0, 1e-3), rho_phase=(1.0, 1e-3) if delta else None,
                             delta=delta, nu1=args.nu, nu2=args.nu)
-        mg = CutStokesMG(prob, precision=prec)
+        mg = CutStokesMG(prob, precision=prec, bottom_max=bottom)
         vt = torch.float64 if prec == native.FP64 else torch.float32
         vx = torch.zeros(mg.ne * mg.nb, dtype=vt, device="cuda")
         vb = torch.ones(mg.ne * mg.nb, dtype=vt, device="cuda")
@@ -816,7 +820,7 @@ def run_cut(args):
         prec = precs.get(args.precision, native.FP64)
         prob = P.CutProblem(n=n, p=p, mu_phase=(1.0, 1e-3), rho_phase=(1.0, 1e-3) if delta else None,
                             delta=delta, nu1=args.nu, nu2=args.nu)
-        mg = CutStokesMG(prob, precision=prec)
+        mg = CutStokesMG(prob, precision=prec, bottom_max=bottom)
         mg.ctx.set_solver(native.FGMRES, args.restart)
         D = mg.scaling().ravel()
         z = np.zeros((mg.ne, mg.nb))
@@ -840,7 +844,7 @@ def run_cut(args):
             prob = P.CutProblem(n=n, p=p, mu_phase=mu, rho_phase=mu if delta else None, delta=delta,
                                 nu1=args.nu, nu2=args.nu)
             t0 = time.perf_counter()
-            mg = CutStokesMG(prob, precision=precision)
+            mg = CutStokesMG(prob, precision=precision, bottom_max=bottom)
             setup_s = time.perf_counter() - t0
             mg.ctx.set_solver({"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR,
                                "richardson": native.RICHARDSON}[args.solver], args.restart)
@@ -905,7 +909,7 @@ def run_cut(args):
         torch.cuda.empty_cache()
     learned = None
     if args.learned:
-        learned = [cut_learned_protocol(args, nn, p, 0.1 / nn if args.delta < 0 else delta, stream)
+        learned = [cut_learned_protocol(args, nn, p, 0.1 / nn if args.delta < 0 else delta, stream, bottom)
                    for nn in sorted({64, n})]
     head = min(arms, key=lambda k: arms[k]["ms"] if max(arms[k]["res"]) <= 1e-10 else 1e30)
     other = "fp32" if head == "fp64" else "fp64"
@@ -930,6 +934,7 @@ def run_cut(args):
                    "rho_ratios_inside_outside": [1e-3, 1e3] if delta else None,
                    "phases": "heavy rho = mu = 1, light rho = mu = 1e-3",
                    "delta": delta, "nu": [args.nu, args.nu], "outer": "%s(%d)" % (args.solver, args.restart),
+                   "bottom_max_unknowns": bottom,
                    "rtol": 1e-10, "cache": "inputs larger than L2 (level-0 records %.2f GB)" % (sw["bytes"] / 1e9)},
         "iters_per_solve": m["its"], "final_rel_residual": m["res"], "setup_s": m["setup_s"],
         "dof_cycles_per_s": m["dofs"] * sum(m["its"]) / (m["ms"] / 1e3),
@@ -945,7 +950,7 @@ def run_cut(args):
         "device_gb": m["device_gb"], "gpu_launches": m["launches"], "clocks": m["clocks"]}))
 
 
-def cut_learned_protocol(args, n, p, delta, stream, evaluations=4):
+def cut_learned_protocol(args, n, p, delta, stream, bottom, evaluations=4):
     """The learned post-smoother's protocol on the cut-cell workload (the light
     bubble, FP32 cycle, iterative refinement with the acceptance rule): train
     on V-cycle states of smooth random fields from seeds 0-255 (sample k uses
@@ -957,7 +962,7 @@ def cut_learned_protocol(args, n, p, delta, stream, evaluations=4):
     from paper_1911_05888_gb300.solver import CutStokesMG
     prob = P.CutProblem(n=n, p=p, mu_phase=(1e-3, 1.0), rho_phase=(1e-3, 1.0) if delta else None, delta=delta,
                         nu1=args.nu, nu2=args.nu)
-    mg = CutStokesMG(prob, precision=native.FP32)
+    mg = CutStokesMG(prob, precision=native.FP32, bottom_max=bottom)
     out = {"problem": "light bubble (inside/outside mu and rho 1e-3), FP32 blocks", "n": n,
            "outer": "iterative refinement (the acceptance rule judges each cycle's outer residual)"}
     try:

@@ -197,8 +197,9 @@ int stk_set_clusters(stk_ctx* ctx, int on);
  * Algorithm 1 only needs an exact coarsest solve): the hierarchy stops at the
  * first level below level 0 with at most max_unknowns unknowns, which is then
  * solved by the dense eigen pseudo-inverse (cuSOLVER above 1200 unknowns).
- * 0 (default): coarsen while every n_k is even and above 2.  Takes effect at
- * the next stk_setup.  Errors: STK_ERR_INVALID_ARG outside 0..20000.
+ * 0 (default): coarsen while every n_k is even and above 2 (cut-cell
+ * meshes: until the grid is 2 x 2).  Takes effect at the next stk_setup.
+ * Errors: STK_ERR_INVALID_ARG outside 0..20000.
  */
 int stk_set_bottom(stk_ctx* ctx, int64_t max_unknowns);
 /*

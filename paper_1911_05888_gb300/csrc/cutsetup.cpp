@@ -673,6 +673,9 @@ int setup_cut(Ctx& c, std::string& err) {
     L.colour = greedy(structure);
     c.host.push_back(std::move(L));
     if (n <= 2) break;
+    // an earlier bottom: this level (not level 0) is small enough for the
+    // dense pseudo-inverse (stk_set_bottom)
+    if (c.host.size() > 1 && c.bottom_max > 0 && (int64_t)ne * 3 * s <= c.bottom_max) break;
     n /= 2;
     // same-phase agglomeration by the parent of the anchor cell
     std::map<std::array<int, 3>, int> keys;

@@ -93,7 +93,7 @@ class CutStokesMG:
     (stk_set_levelset_circle), phase viscosities and densities, data sampled
     at the library's cut-cell points."""
 
-    def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True):
+    def __init__(self, prob, precision=native.FP64, device=0, nu=None, setup=True, bottom_max=0):
         self.prob = prob
         self.ctx = native.Context(device)
         self.ctx.set_mesh(2, (prob.n, prob.n), (0.0, 0.0), (1.0, 1.0), [DIRICHLET] * 4)
@@ -105,6 +105,7 @@ class CutStokesMG:
             self.ctx.set_phase_density(prob.rho_phase, prob.delta)
         nu1, nu2 = (prob.nu1, prob.nu2) if nu is None else nu
         self.ctx.set_cycle(nu1, nu2, precision)
+        self.ctx.set_bottom(bottom_max)
         if setup:
             self.ctx.setup()
             self.nlevels, self.ne_levels, self.nb, self.n_snapped = self.ctx.sizes()

@@ -424,3 +424,40 @@ def test_cut_learned_features_and_acceptance_match_oracle():
         assert hist[-1] <= 1e-10 and abs(it - (len(ho) - 1)) <= 1
     finally:
         gpu.close()
+
+
+def test_cut_earlier_bottom_matches_oracle():
+    """stk_set_bottom on a cut hierarchy: the 16^2 mesh stops at its 8 x 8
+    level (76 elements, 2052 unknowns: the equilibrated cuSOLVER bottom), and
+    V-cycle iterates equal those of the oracle's hierarchy cut at the same
+    level (cuthier.build with nmin = 8)."""
+    prob = P.CutProblem(n=16, p=2, mu_phase=(1e-3, 1.0))
+    gpu = CutStokesMG(prob, bottom_max=2100)
+    try:
+        mesh = cutcell.CutMesh(cutcell.Circle(prob.centre, prob.radius), prob.n, q=2 * prob.p + 2)
+        levels, inj = cuthier.build(mesh, prob.p, list(prob.mu_phase), prob.tau, prob.gamma, nmin=8, scale=True)
+        assert gpu.nlevels == len(levels) == 2
+        assert gpu.ctx.info(native.INFO_BOTTOM_SOLVER) == native.BOTTOM_CUSOLVER
+        orc = multigrid.Multigrid(types.SimpleNamespace(nu1=prob.nu1, nu2=prob.nu2, gamma=prob.gamma),
+                                  levels=levels, injections=inj)
+        assert gpu.n_snapped == orc.kernel_dim_bottom
+        lev = levels[0]
+        z = kernel_basis(lev)
+        rng = np.random.default_rng(23)
+        b = rng.uniform(-1, 1, lev.ne * lev.nb)
+        b -= z * (z @ b)
+        bd = dev(b)
+        xd = torch.zeros_like(bd)
+        xo = np.zeros_like(b)
+        worst = 0.0
+        for k in range(4):
+            gpu.ctx.vcycle(xd, bd)
+            orc.vcycle(xo, b)
+            xg = xd.cpu().numpy()
+            worst = max(worst, maxrel(xg - z * (z @ xg), xo - z * (z @ xo)))
+        # the 2052-unknown bottom operator's condition number times rounding
+        Ad = levels[-1].A.toarray()
+        lam = np.sort(np.abs(np.linalg.eigvalsh(0.5 * (Ad + Ad.T))))[orc.kernel_dim_bottom:]
+        assert worst <= max(1e-10, 1e-15 * lam[-1] / lam[0]), worst
+    finally:
+        gpu.close()
