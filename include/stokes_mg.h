@@ -404,10 +404,10 @@ int stk_cut_cells(int n, const double* lo, const double* hi, double cx, double c
  */
 int stk_set_levelset_circle(stk_ctx* ctx, double cx, double cy, double r);
 /* Warps that share one element in the element kernel of cut-cell levels: 0
- * (default) picks by launch size (4 for launches of fewer than 32 elements
- * per SM, 2 below 64, else 1), or 1, 2, 4 fixed.  Results agree to rounding
- * (the warps' partial sums meet in a different order).  Errors:
- * STK_ERR_INVALID_ARG. */
+ * (default) picks by launch size (4 for launches of fewer than 8 elements per
+ * SM with FP32 records or 32 with FP64 records, else 2), or 1, 2, 4 fixed.
+ * Results agree to rounding (the warps' partial sums meet in a different
+ * order).  Errors: STK_ERR_INVALID_ARG. */
 int stk_set_element_warps(stk_ctx* ctx, int warps);
 /* Unsteady cut-cell problem (eq. timedep2): density rho_phase[2] > 0 per phase
  * and delta > 0; delta = 0 returns to the steady problem (rho_phase unused). */

@@ -262,8 +262,11 @@ cudaError_t gen_launch_w(int mode, int nb, int nbp, int pos0, int npos, const in
   return cudaGetLastError();
 }
 
-// Warps per element by launch size: the elements' warps should fill about
-// two waves of 32 warps on each of the device's SMs.
+// Warps per element by launch size and record width (measured on the 128^2
+// p = 3 cut mesh): launches of fewer than 8 (FP32) or 32 (FP64) elements per
+// SM take four warps per element, larger ones two; one warp per element was
+// never faster (FP64 residual of 16,468 elements: 0.406 ms with one warp,
+// 0.336 with two; FP32 colour sweep 0.182 / 0.167 ms).
 template <typename T, typename V, int S>
 cudaError_t gen_launch(int mode, int warps, int nb, int nbp, int pos0, int npos, const int* perm, const int* tptr,
                        const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r,
@@ -281,10 +284,8 @@ cudaError_t gen_launch(int mode, int warps, int nb, int nbp, int pos0, int npos,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 152;
   }
-  const int64_t target = (int64_t)sms * 64;
-  if ((int64_t)npos >= target)
-    return gen_launch_w<T, V, S, 1>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
-  if ((int64_t)npos * 2 >= target)
+  const int64_t four_below = (int64_t)sms * (sizeof(T) == 4 ? 8 : 32);
+  if ((int64_t)npos >= four_below)
     return gen_launch_w<T, V, S, 2>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
   return gen_launch_w<T, V, S, 4>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
 }
