@@ -3,9 +3,9 @@
 // per-element coupling lists of any length, and the transfers of Algorithm 1
 // through per-element injection blocks.
 //
-// Element kernel: one warp per element position of the launch.  Task t of the
-// element is one s x s sub-block C_t (row variable rv, column variable cv,
-// neighbour j), stored row-major, 16 rows x 16 columns for p = 3.  Lane pair
+// Element kernel: W warps per element position of the launch (W by launch
+// size).  Task t of the element is one s x s sub-block C_t (row variable rv,
+// column variable cv, neighbour j), stored row-major, 16 x 16 for p = 3.  Lane pair
 // (2r, 2r+1) owns row r: each lane multiplies half the row with the matching
 // half of x_j (16-byte loads of records and vector), the pair sums with one
 // shuffle and adds the result into the running sum of row r of variable rv.
@@ -73,10 +73,9 @@ __device__ __forceinline__ void load8v(const double* p, double* v) {
 // of the W warps meet in shared memory, and the element's W x 32 threads share
 // the dense product by rows.  The element's dense block (A_ii^{-1} or A_ii) is
 // copied into shared memory by cp.async when the kernel starts, so that its
-// load overlaps the coupling tasks and the dense product reads shared memory.  Small launches (a colour of a few thousand
-// elements, the coarse levels) take W = 4, so that each element's chain of
-// dependent record rounds is a quarter as long and the launch still fills the
-// SMs; large launches take W = 1.
+// load overlaps the coupling tasks and the dense product reads shared memory.
+// Small launches (the coarse levels) take W = 4, so that each element's chain
+// of dependent record rounds is a quarter as long; larger ones W = 2.
 template <typename T, typename V, int S, int MODE, int W>
 __global__ void __launch_bounds__(kGenWarps * 32, 6)
     gen_element_kernel(int pos0, int npos, int nb, int nbp, const int* __restrict__ perm,
