@@ -195,10 +195,13 @@ def face_parts(circle, a, b, fixed_axis, fixed, q):
 class CutMesh:
     """The pieces of an n x n grid on [lo, hi]^2 cut by a circle: one piece per
     uncut cell, two per cut cell; each piece with its phase, area and volume
-    rule; and the merged elements."""
+    rule; and the merged elements.  inside_only keeps the phase-1 pieces only:
+    the disc as a curved domain (Section 5's curved-geometry problems), whose
+    boundary is the circle."""
 
-    def __init__(self, circle, n, lo=(0.0, 0.0), hi=(1.0, 1.0), q=8, merge_fraction=0.25):
+    def __init__(self, circle, n, lo=(0.0, 0.0), hi=(1.0, 1.0), q=8, merge_fraction=0.25, inside_only=False):
         self.circle, self.n, self.q = circle, int(n), q
+        self.inside_only = bool(inside_only)
         self.lo, self.hi = np.asarray(lo, float), np.asarray(hi, float)
         self.h = (self.hi - self.lo) / self.n
         self.pieces = []           # dicts: cell (i, j), phase, area, rule (points, weights)
@@ -229,6 +232,8 @@ class CutMesh:
         return np.stack([X.ravel(), Y.ravel()], axis=1), np.outer(wy, wx).ravel()
 
     def _add(self, i, j, ph, px, pw, box):
+        if self.inside_only and ph != 1:
+            return
         self.piece_of[(i, j, ph)] = len(self.pieces)
         self.pieces.append(dict(cell=(i, j), phase=ph, area=float(pw.sum()), points=px, weights=pw,
                                 box=(np.asarray(box[0], float), np.asarray(box[1], float))))

@@ -72,9 +72,10 @@ class CutElements:
 
 def faces(mesh, els, q):
     """Intraphase faces (left element, right element, axis, points, weights),
-    Dirichlet boundary faces (element, axis, side, points, weights) and
-    interface arcs (inside element, outside element, points, weights,
-    normals), each from the cut-cell rules."""
+    Dirichlet boundary faces (element, axis, side, points, weights, outward
+    normals; axis -1 and side 0 for the circle when it bounds the domain, the
+    inside_only mesh) and interface arcs (inside element, outside element,
+    points, weights, normals), each from the cut-cell rules."""
     intra, bdry, arcs = [], [], []
     n = mesh.n
     for j in range(n):
@@ -97,24 +98,38 @@ def faces(mesh, els, q):
                         if ea != eb:
                             intra.append((ea, eb, axis, pts, w))
                     else:
-                        bdry.append((els.of_piece[mesh.piece_of[(i, j, ph)]], axis, 1, pts, w))
+                        a = mesh.piece_of.get((i, j, ph))
+                        if a is not None:
+                            bdry.append((els.of_piece[a], axis, 1, pts, w, _side_normals(axis, 1, len(w))))
                 # low boundary sides of the box
                 if (axis == 0 and i == 0) or (axis == 1 and j == 0):
                     parts = cutcell.face_parts(mesh.circle, clo[o], clo[o] + mesh.h[o], axis, clo[axis], q)
                     for ph, (pts, w) in parts.items():
-                        if len(w):
-                            bdry.append((els.of_piece[mesh.piece_of[(i, j, ph)]], axis, -1, pts, w))
+                        a = mesh.piece_of.get((i, j, ph))
+                        if len(w) and a is not None:
+                            bdry.append((els.of_piece[a], axis, -1, pts, w, _side_normals(axis, -1, len(w))))
             if (i, j) in mesh.interface:
                 xif, wif, nif = mesh.interface[(i, j)]
                 if len(wif):
                     ein = els.of_piece[mesh.piece_of[(i, j, 1)]]
-                    eout = els.of_piece[mesh.piece_of[(i, j, 2)]]
-                    arcs.append((ein, eout, xif, wif, nif))
+                    out = mesh.piece_of.get((i, j, 2))
+                    if out is None:
+                        # the circle bounds the domain: a Dirichlet face of the inside element
+                        bdry.append((ein, -1, 0, xif, wif, nif))
+                    else:
+                        arcs.append((ein, els.of_piece[out], xif, wif, nif))
     return intra, bdry, arcs
 
 
+def _side_normals(axis, side, m):
+    nrm = np.zeros((m, 2))
+    nrm[:, axis] = side
+    return nrm
+
+
 def operators(mesh, p, mu_phase, tau, q=None, rho_phase=None, delta=None, tau0=None):
-    """The Appendix A operators on the cut-cell mesh (Dirichlet on the box),
+    """The Appendix A operators on the cut-cell mesh (Dirichlet on the box, and
+    on the circle when the mesh keeps the inside only),
     as a dict like ldg.fine_operators (M, Mmu, G, Et, E, s, mesh with ne).
     With rho_phase and delta the unsteady problem (eq. timedep2): Mrho = rho M
     per element, and on intraphase faces the pressure penalty of eq.
@@ -169,10 +184,15 @@ def operators(mesh, p, mu_phase, tau, q=None, rho_phase=None, delta=None, tau0=N
                 Pr = Pa if r_ == ea else Pb
                 Pc = Pa if c_ == ea else Pb
                 acc.add([r_], [c_], (sgn * tp * FF(Pr, Pc))[None])
-    for e, axis, side, pts, w in bdry:
+    for e, axis, side, pts, w, nrm in bdry:
         P_, _ = els.phi(e, pts)
         FF = P_.T @ (w[:, None] * P_)
-        gacc[axis].add([e], [e], (-side * FF)[None])
+        if axis >= 0:
+            gacc[axis].add([e], [e], (-side * FF)[None])
+        else:
+            # curved Dirichlet boundary: -int u v n_k with the outward normal
+            for k in range(2):
+                gacc[k].add([e], [e], (-(P_.T @ ((w * nrm[:, k])[:, None] * P_)))[None])
         Et.add([e], [e], (10.0 * p * mu(e) / hk * FF)[None])
     for em, ep, pts, w, nrm in arcs:
         Pm, _ = els.phi(em, pts)
@@ -225,14 +245,18 @@ def rhs(ops, exact, gamma):
                 bu[i][e] += Phi.T @ (w * f[:, i])
             bp[e] += Phi.T @ (w * fd)
     intra, bdry, arcs = ops["faces"]
-    for e, axis, side, pts, w in bdry:
+    for e, axis, side, pts, w, nrm in bdry:
         P_, _ = els.phi(e, pts)
         g = exact.u(pts, chi=np.full(len(w), els.phase[e]))
         tau_d = 10.0 * p * mu(e) / hk
         for i in range(2):
             integ = P_.T @ (w * g[:, i])
             bu[i][e] += tau_d * integ
-            jg[i][axis][e] += side * integ
+            if axis >= 0:
+                jg[i][axis][e] += side * integ
+            else:
+                for k in range(2):
+                    jg[i][k][e] += P_.T @ (w * nrm[:, k] * g[:, i])
     for em, ep, pts, w, nrm in arcs:
         Pm, _ = els.phi(em, pts)
         Pp, _ = els.phi(ep, pts)

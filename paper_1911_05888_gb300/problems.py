@@ -289,7 +289,9 @@ class CutProblem:
     phase 1 inside the circle, phase 2 outside, Dirichlet data on the box,
     velocity and stress jumps on the circle from the per-phase manufactured
     solution of Appendix C (MultiPhaseManufactured).  With rho_phase and delta
-    the unsteady problem of eq. (timedep1); its forcing adds rho/delta u."""
+    the unsteady problem of eq. (timedep1); its forcing adds rho/delta u.
+    With inside_only and one viscosity, the disc alone (Section 5's curved
+    domain) with Dirichlet data from the same solution on the circle."""
     n: int = 128
     p: int = 3
     gamma: int = 1
@@ -303,6 +305,7 @@ class CutProblem:
     tau: Optional[float] = None
     tau0: Optional[float] = None
     scale_mu: bool = True
+    inside_only: bool = False   # the disc alone (one phase, Dirichlet data on the circle)
 
     def __post_init__(self):
         if self.tau is None:
