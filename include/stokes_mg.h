@@ -396,7 +396,11 @@ int stk_cut_cells(int n, const double* lo, const double* hi, double cx, double c
  * Algorithm 2 (Algorithm 3 with densities).  The smoother colours every level
  * greedily (elements in order, smallest colour not used by an element within
  * two face / interface steps; on coarse levels by an element holding coupled
- * members).  Needs stk_set_phases(ctx, 2, NULL, mu_phase, scale) and takes
+ * members).  Needs stk_set_phases(ctx, 2, NULL, mu_phase, scale), or
+ * stk_set_phases(ctx, 1, NULL, &mu, scale) for the disc alone (Section 5's
+ * curved domain: the outside pieces are dropped and the circle carries
+ * Dirichlet data, lifted with its outward normal and penalised like the
+ * box's sides; its sample points join STK_PTS_BOUNDARY_FACE), and takes
  * p = 1..3, FP64 or FP32 blocks; clusters, the persistent launches, several
  * right-hand sides, the learned smoother and the autotuner are Cartesian
  * only.  r = 0 returns the context to the Cartesian mesh.  Call after
@@ -409,8 +413,10 @@ int stk_set_levelset_circle(stk_ctx* ctx, double cx, double cy, double r);
  * Results agree to rounding (the warps' partial sums meet in a different
  * order).  Errors: STK_ERR_INVALID_ARG. */
 int stk_set_element_warps(stk_ctx* ctx, int warps);
-/* Unsteady cut-cell problem (eq. timedep2): density rho_phase[2] > 0 per phase
- * and delta > 0; delta = 0 returns to the steady problem (rho_phase unused). */
+/* Unsteady cut-cell problem (eq. timedep2): density rho_phase > 0 per phase
+ * of stk_set_phases (2 values, 1 for the disc) and delta > 0; delta = 0
+ * returns to the steady problem (rho_phase unused).  Call after
+ * stk_set_phases. */
 int stk_set_phase_density(stk_ctx* ctx, const double* rho_phase, double delta);
 /* Phase (1 or 2) of every point of a point set of a cut-cell mesh (volume and
  * boundary-face points: the phase of the piece they belong to; interface

@@ -1828,9 +1828,10 @@ int setup_cut_device(stk_ctx* c, cudaStream_t st) {
   for (int i = 0; i < 4; ++i)
     if (c->bc[i] != STK_BC_DIRICHLET) return fail(c, STK_ERR_INVALID_ARG, "cut-cell meshes take Dirichlet sides only");
   if (c->p > 3) return fail(c, STK_ERR_INVALID_ARG, "cut-cell meshes take p = 1..3");
-  if (c->mu_phase.size() != 2) return fail(c, STK_ERR_INVALID_ARG, "set the two phase viscosities (stk_set_phases)");
-  if (c->cut_delta > 0 && c->rho_phase.size() != 2)
-    return fail(c, STK_ERR_INVALID_ARG, "set the two phase densities (stk_set_phase_density)");
+  const size_t nph = c->cut_inside ? 1 : 2;
+  if (c->mu_phase.size() != nph) return fail(c, STK_ERR_INVALID_ARG, "set the phase viscosities (stk_set_phases)");
+  if (c->cut_delta > 0 && c->rho_phase.size() != nph)
+    return fail(c, STK_ERR_INVALID_ARG, "set the phase densities (stk_set_phase_density)");
   if (c->precision != STK_FP64 && c->precision != STK_FP32)
     return fail(c, STK_ERR_INVALID_ARG, "cut-cell levels store FP64 or FP32 blocks");
   if (c->c_intra != 0.0) return fail(c, STK_ERR_INVALID_ARG, "cut-cell meshes take no interior velocity penalty");
@@ -3014,6 +3015,7 @@ int stk_set_levelset_circle(stk_ctx* c, double cx, double cy, double r) {
     c->cuts.reset();
     if (r == 0) {
       c->cut = 0;
+      c->cut_inside = 0;
       c->mu_phase.clear();
       c->rho_phase.clear();
       c->cut_delta = 0.0;
@@ -3049,10 +3051,11 @@ int stk_set_phase_density(stk_ctx* c, const double* rho_phase, double delta) {
       return STK_OK;
     }
     if (!rho_phase) return fail(c, STK_ERR_INVALID_ARG, "null densities");
-    for (int i = 0; i < 2; ++i)
+    const int np = c->cut_inside ? 1 : 2;   // one per phase of stk_set_phases
+    for (int i = 0; i < np; ++i)
       if (!(rho_phase[i] > 0) || !std::isfinite(rho_phase[i]))
         return fail(c, STK_ERR_INVALID_ARG, "phase density must be finite and positive");
-    c->rho_phase.assign(rho_phase, rho_phase + 2);
+    c->rho_phase.assign(rho_phase, rho_phase + np);
     c->cut_delta = delta;
     return STK_OK;
   });
@@ -3069,13 +3072,20 @@ int stk_set_phases(stk_ctx* c, int nphase, const int* chi, const double* mu_phas
       return STK_OK;
     }
     if (c->cut) {
-      // embedded circle: phase 1 inside, 2 outside; no element phase array
-      if (nphase != 2 || !mu_phase) return fail(c, STK_ERR_INVALID_ARG, "the embedded circle has two phases");
-      for (int i = 0; i < 2; ++i)
+      // embedded circle: phase 1 inside, 2 outside (nphase = 2), or the disc
+      // alone with Dirichlet data on the circle (nphase = 1); no element phase array
+      if ((nphase != 1 && nphase != 2) || !mu_phase)
+        return fail(c, STK_ERR_INVALID_ARG, "the embedded circle takes two phases, or one (the disc alone)");
+      for (int i = 0; i < nphase; ++i)
         if (!(mu_phase[i] > 0) || !std::isfinite(mu_phase[i]))
           return fail(c, STK_ERR_INVALID_ARG, "phase viscosity must be finite and positive");
       c->chi.clear();
-      c->mu_phase.assign(mu_phase, mu_phase + 2);
+      c->mu_phase.assign(mu_phase, mu_phase + nphase);
+      c->cut_inside = nphase == 1 ? 1 : 0;
+      c->rho_phase.clear();
+      c->cut_delta = 0.0;
+      c->cutg.reset();
+      c->cuts.reset();
       c->scale_mu = scale ? 1 : 0;
       return STK_OK;
     }

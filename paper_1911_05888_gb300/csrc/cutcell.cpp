@@ -210,8 +210,9 @@ void cut_face_parts(const CutGeometry& G, double a, double b, int axis, double f
 }
 
 void build_cut_geometry(CutGeometry& G, int n, const double* lo, const double* hi, double cx, double cy, double r,
-                        int q, double frac) {
+                        int q, double frac, bool inside_only) {
   G = CutGeometry();
+  G.inside_only = inside_only;
   G.n = n;
   G.q = q;
   G.frac = frac;
@@ -227,6 +228,7 @@ void build_cut_geometry(CutGeometry& G, int n, const double* lo, const double* h
   std::vector<double> gx, gw;
   gauss_rule(q, gx, gw);
   auto add = [&](CutPiece&& P) {
+    if (inside_only && P.ph != 1) return;
     P.area = sum_of(P.w);
     G.piece_of[((int64_t)P.j * n + P.i) * 4 + P.ph] = (int)G.pieces.size();
     G.pieces.push_back(std::move(P));

@@ -276,7 +276,15 @@ void elements_of(const CutGeometry& G, int p, CutState& S) {
   }
 }
 
-// Intraphase faces, Dirichlet box faces and interface arcs, cells in order.
+std::vector<double> side_normals(int axis, int side, size_t m) {
+  std::vector<double> nrm(2 * m, 0.0);
+  for (size_t k = 0; k < m; ++k) nrm[2 * k + axis] = side;
+  return nrm;
+}
+
+// Intraphase faces, Dirichlet faces (box sides with their outward normals, and
+// the circle with its outward normal when it bounds the domain: axis -1) and
+// interface arcs, cells in order.
 void faces_of(const CutGeometry& G, CutState& S) {
   const int n = G.n;
   S.intra.clear();
@@ -300,8 +308,11 @@ void faces_of(const CutGeometry& G, CutState& S) {
             if (ea != eb) S.intra.push_back({ea, eb, axis, 0, px[ph - 1], pw[ph - 1], {}});
           } else {
             const int a = G.find(i, j, ph);
-            if (a < 0) throw std::runtime_error("boundary face part without a piece");
-            S.bdry.push_back({S.of_piece[a], -1, axis, 1, px[ph - 1], pw[ph - 1], {}});
+            if (a < 0) {
+              if (G.inside_only) continue;
+              throw std::runtime_error("boundary face part without a piece");
+            }
+            S.bdry.push_back({S.of_piece[a], -1, axis, 1, px[ph - 1], pw[ph - 1], side_normals(axis, 1, pw[ph - 1].size())});
           }
         }
         if ((axis == 0 && i == 0) || (axis == 1 && j == 0)) {
@@ -309,15 +320,25 @@ void faces_of(const CutGeometry& G, CutState& S) {
           for (int ph = 1; ph <= 2; ++ph) {
             if (pw[ph - 1].empty()) continue;
             const int a = G.find(i, j, ph);
-            if (a < 0) throw std::runtime_error("boundary face part without a piece");
-            S.bdry.push_back({S.of_piece[a], -1, axis, -1, px[ph - 1], pw[ph - 1], {}});
+            if (a < 0) {
+              if (G.inside_only) continue;
+              throw std::runtime_error("boundary face part without a piece");
+            }
+            S.bdry.push_back({S.of_piece[a], -1, axis, -1, px[ph - 1], pw[ph - 1],
+                              side_normals(axis, -1, pw[ph - 1].size())});
           }
         }
       }
       if (arc_i < G.arcs.size() && G.arcs[arc_i].i == i && G.arcs[arc_i].j == j) {
         const CutArc& A = G.arcs[arc_i++];
-        if (!A.w.empty())
-          S.arcs.push_back({S.of_piece[G.find(i, j, 1)], S.of_piece[G.find(i, j, 2)], -1, 0, A.x, A.w, A.nrm});
+        if (!A.w.empty()) {
+          const int in = S.of_piece[G.find(i, j, 1)];
+          const int out = G.find(i, j, 2);
+          if (out < 0)   // the circle bounds the domain: a Dirichlet face of the inside element
+            S.bdry.push_back({in, -1, -1, 0, A.x, A.w, A.nrm});
+          else
+            S.arcs.push_back({in, S.of_piece[out], -1, 0, A.x, A.w, A.nrm});
+        }
       }
     }
 }
@@ -407,7 +428,16 @@ void fine_operators(const Ctx& c, const CutGeometry& G, CutState& S) {
   for (const Face& F : S.bdry) {
     std::vector<double> P;
     phi(F.ea, F.x, P, nullptr);
-    add(g[F.axis], F.ea, F.ea, -(double)F.side, P, P, F.w);
+    if (F.axis >= 0) {
+      add(g[F.axis], F.ea, F.ea, -(double)F.side, P, P, F.w);
+    } else {
+      // curved Dirichlet boundary: -int u v n_k with the outward normal
+      for (int k = 0; k < 2; ++k) {
+        std::vector<double> wn(F.w.size());
+        for (size_t q = 0; q < F.w.size(); ++q) wn[q] = F.w[q] * F.nrm[2 * q + k];
+        add(g[k], F.ea, F.ea, -1.0, P, P, wn);
+      }
+    }
     add(O.Et, F.ea, F.ea, c.c_bdry * p * mu(F.ea) / hk, P, P, F.w);
   }
   for (const Face& F : S.arcs) {
@@ -613,7 +643,8 @@ std::vector<int> greedy(const std::vector<std::set<int>>& S) {
 
 bool same_geometry(const CutGeometry& G, const Ctx& c) {
   return G.n == c.n[0] && G.q == c.q && G.lo[0] == c.lo[0] && G.lo[1] == c.lo[1] && G.hi[0] == c.hi[0] &&
-         G.hi[1] == c.hi[1] && G.c[0] == c.cut_c[0] && G.c[1] == c.cut_c[1] && G.r == c.cut_r && G.frac == c.cut_frac;
+         G.hi[1] == c.hi[1] && G.c[0] == c.cut_c[0] && G.c[1] == c.cut_c[1] && G.r == c.cut_r && G.frac == c.cut_frac &&
+         G.inside_only == (c.cut_inside != 0);
 }
 
 }  // namespace
@@ -621,7 +652,7 @@ bool same_geometry(const CutGeometry& G, const Ctx& c) {
 const CutGeometry& cut_geometry(Ctx& c) {
   if (!c.cutg || !same_geometry(*c.cutg, c)) {
     auto G = std::make_shared<CutGeometry>();
-    build_cut_geometry(*G, c.n[0], c.lo, c.hi, c.cut_c[0], c.cut_c[1], c.cut_r, c.q, c.cut_frac);
+    build_cut_geometry(*G, c.n[0], c.lo, c.hi, c.cut_c[0], c.cut_c[1], c.cut_r, c.q, c.cut_frac, c.cut_inside != 0);
     c.cutg = G;
     c.cuts.reset();
   }
@@ -789,15 +820,7 @@ void cut_points(Ctx& c, int kind, std::vector<double>& xyz, std::vector<double>*
   for (const Face& F : list) {
     xyz.insert(xyz.end(), F.x.begin(), F.x.end());
     const size_t m = F.w.size();
-    if (nrm) {
-      if (kind == STK_PTS_BOUNDARY_FACE)
-        for (size_t k = 0; k < m; ++k) {
-          nrm->push_back(F.axis == 0 ? (double)F.side : 0.0);
-          nrm->push_back(F.axis == 1 ? (double)F.side : 0.0);
-        }
-      else
-        nrm->insert(nrm->end(), F.nrm.begin(), F.nrm.end());
-    }
+    if (nrm) nrm->insert(nrm->end(), F.nrm.begin(), F.nrm.end());
     if (phase) phase->insert(phase->end(), m, kind == STK_PTS_BOUNDARY_FACE ? S->phase[F.ea] : 1);
   }
 }
@@ -860,7 +883,15 @@ int cut_assemble_rhs(Ctx& c, const double* f_vol, const double* bdata, const dou
     const double tau_d = c.c_bdry * p * mu(F.ea) / hk;
     for (int i = 0; i < 2; ++i) {
       acc(bu[i], F.ea, Phi, F.w, g + i, 2, tau_d);
-      acc(jg[i][F.axis], F.ea, Phi, F.w, g + i, 2, (double)F.side);
+      if (F.axis >= 0) {
+        acc(jg[i][F.axis], F.ea, Phi, F.w, g + i, 2, (double)F.side);
+      } else {
+        for (int k = 0; k < 2; ++k) {
+          std::vector<double> ng(F.w.size());
+          for (size_t q = 0; q < F.w.size(); ++q) ng[q] = F.nrm[2 * q + k] * g[q * 2 + i];
+          acc(jg[i][k], F.ea, Phi, F.w, ng.data(), 1, 1.0);
+        }
+      }
     }
     off += F.w.size();
   }

@@ -183,6 +183,7 @@ struct CutArc {
 struct CutGeometry {
   int n = 0, q = 0;
   double lo[2] = {0, 0}, hi[2] = {1, 1}, h[2] = {1, 1}, c[2] = {0, 0}, r = 0, frac = 0.25;
+  bool inside_only = false;             // the disc alone: phase-2 pieces dropped, the circle a boundary
   std::vector<CutPiece> pieces;         // cells in order (x fastest), inside piece first
   std::map<int64_t, int> piece_of;      // ((j n + i) 4 + ph) -> piece
   std::vector<CutArc> arcs;             // one per cut cell, cells in order
@@ -193,7 +194,7 @@ struct CutGeometry {
   }
 };
 void build_cut_geometry(CutGeometry& G, int n, const double* lo, const double* hi, double cx, double cy, double r,
-                        int q, double frac);
+                        int q, double frac, bool inside_only = false);
 // Gauss rules of the phase-1 and phase-2 parts of the face segment
 // {x_axis = fixed, other coordinate in [a, b]}: points [m][2] and weights.
 void cut_face_parts(const CutGeometry& G, double a, double b, int axis, double fixed, std::vector<double>* x,
@@ -350,6 +351,7 @@ struct Ctx {
   // the geometry (built on demand for the current mesh and degree)
   int cut = 0;
   double cut_c[2] = {0, 0}, cut_r = 0, cut_frac = 0.25;
+  int cut_inside = 0;           // one phase: the disc inside the circle, Dirichlet on the circle
   std::vector<double> rho_phase;
   double cut_delta = 0.0;
   int gen_warps = 0;                    // warps per element of the general element kernel (0: by launch size)

@@ -561,18 +561,21 @@ class Context:
         self.cut = radius > 0
 
     def set_cut_phases(self, mu_phase, scale=True):
-        """Viscosities of the circle's inside (phase 1) and outside (phase 2)."""
-        mu = np.ascontiguousarray(mu_phase, dtype=np.float64)
-        self._expect("mu_phase", mu, 2)
-        self._check(self.lib.stk_set_phases(self.h, 2, None, mu.ctypes.data_as(_c_dbl_p), 1 if scale else 0),
-                    "stk_set_phases")
+        """Viscosities of the circle's inside (phase 1) and outside (phase 2),
+        or one viscosity: the disc alone, Dirichlet data on the circle."""
+        mu = np.ascontiguousarray(mu_phase, dtype=np.float64).ravel()
+        if mu.size not in (1, 2):
+            raise ValueError("mu_phase: 1 or 2 values, got %d" % mu.size)
+        self._check(self.lib.stk_set_phases(self.h, int(mu.size), None, mu.ctypes.data_as(_c_dbl_p),
+                                            1 if scale else 0), "stk_set_phases")
+        self._cut_phases = int(mu.size)
 
     def set_phase_density(self, rho_phase, delta):
         if delta == 0:
             self._check(self.lib.stk_set_phase_density(self.h, None, 0.0), "stk_set_phase_density")
             return
         rho = np.ascontiguousarray(rho_phase, dtype=np.float64)
-        self._expect("rho_phase", rho, 2)
+        self._expect("rho_phase", rho, getattr(self, "_cut_phases", 2))
         self._check(self.lib.stk_set_phase_density(self.h, rho.ctypes.data_as(_c_dbl_p), float(delta)),
                     "stk_set_phase_density")
 

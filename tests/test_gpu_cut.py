@@ -43,6 +43,11 @@ CASES = {
     "c12p1-standard": (lambda: P.CutProblem(n=12, p=1, gamma=0, mu_phase=(1.0, 10.0)), 1e-13, 1e-12, 1e-10, 1e-11),
     "c20p2-offcentre": (lambda: P.CutProblem(n=20, p=2, mu_phase=(1.0, 1e-3), centre=(0.47, 0.53)),
                         1e-13, 1e-12, 1e-10, 1e-11),
+    # Section 5's curved domain: the disc of radius 0.45 alone, Dirichlet data on the circle
+    "disc16p2-standard": (lambda: P.CutProblem(n=16, p=2, gamma=0, mu_phase=(1.0,), radius=0.45, inside_only=True),
+                          1e-13, 1e-12, 1e-10, 1e-11),
+    "disc16p3-stress": (lambda: P.CutProblem(n=16, p=3, gamma=1, mu_phase=(1.0,), radius=0.45, inside_only=True),
+                        1e-11, 1e-9, 1e-7, 1e-9),
 }
 
 _cache = {}
@@ -56,7 +61,8 @@ def get(name, precision=native.FP64):
         if (name, native.FP64) in _cache:
             mesh, levels, inj, orc = _cache[(name, native.FP64)][2:]
         else:
-            mesh = cutcell.CutMesh(cutcell.Circle(prob.centre, prob.radius), prob.n, q=2 * prob.p + 2)
+            mesh = cutcell.CutMesh(cutcell.Circle(prob.centre, prob.radius), prob.n, q=2 * prob.p + 2,
+                                   inside_only=prob.inside_only)
             kw = dict(scale=prob.scale_mu)
             if prob.unsteady:
                 kw.update(rho_phase=list(prob.rho_phase), delta=prob.delta, tau0=prob.tau0)
@@ -118,6 +124,9 @@ def test_cut_points_match_oracle(name):
     els = levels[0].ops["els"]
     assert np.array_equal(cb, np.concatenate([[els.phase[f[0]]] * len(f[4]) for f in bdry]))
     xi, ni, _ = gpu.points(native.PTS_INTERFACE)
+    if not arcs:   # the disc alone: the circle's points are boundary-face points
+        assert len(xi) == 0 and prob.inside_only
+        return
     oi = np.concatenate([a[2] for a in arcs])
     assert xi.shape == oi.shape and np.abs(xi - oi).max() <= 1e-15
     assert np.abs(ni - np.concatenate([a[4] for a in arcs])).max() <= 1e-15
@@ -267,7 +276,9 @@ def test_cut_rhs_matches_oracle(name):
                                             ("c16p3-mu1e3-rho1e3", native.FP64),
                                             ("c16p3-mu1e3-rho1e3", native.FP32),
                                             ("c16p3-bubble", native.FP32),
-                                            ("c12p1-standard", native.FP32)])
+                                            ("c12p1-standard", native.FP32),
+                                            ("disc16p2-standard", native.FP64),
+                                            ("disc16p3-stress", native.FP32)])
 def test_cut_solve_solves_the_oracle_system(name, precision):
     """FGMRES with the V-cycle (FP64 or FP32 blocks) solves the scaled system
     D A D x~ = D b of the manufactured problem to 1e-10, and its solution
