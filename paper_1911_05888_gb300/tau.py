@@ -11,7 +11,10 @@ the minimum (Table 2).  Every rho is computed by the library's
 reads the results.
 
 Command line: ``python -m paper_1911_05888_gb300.tau --cases 0,2,2 1,2,3
---n 128`` prints one JSON line per (form, d, p) case.
+--n 128`` prints one JSON line per (form, d, p) case.  ``--disc 32 64 128
+--disc-p 2 3`` instead prints rho on Section 5's curved domain (the disc of
+radius 0.45 on an n x n background grid, standard form, mu = 1, Dirichlet data
+on the circle) with Table 1's tau.
 """
 import argparse
 import json
@@ -37,6 +40,21 @@ def rho_of(prob, tau, precision=native.FP64, seed=1, reduction=1e-8, maxit=100, 
     finally:
         mg.ctx.close()
     return r, n
+
+
+def disc_rho(n, p, precision=native.FP64, seed=1, reduction=1e-8, maxit=100):
+    """(rho, iterations, elements) of eq. (rho) on the disc of radius 0.45 cut
+    from an n x n grid (standard form, mu = 1, Table 1's tau)."""
+    import torch
+    from .solver import CutStokesMG
+    prob = P.CutProblem(n=n, p=p, gamma=0, mu_phase=(1.0,), radius=0.45, inside_only=True)
+    mg = CutStokesMG(prob, precision=precision)
+    try:
+        x0 = torch.from_numpy(P.random_vector(mg.ne, mg.nb, seed=seed).ravel()).cuda()
+        r, it, _, _ = mg.ctx.gmres_rho(x0, reduction, maxit)
+    finally:
+        mg.close()
+    return r, it, mg.ne
 
 
 def parabolic_min(t, r):
@@ -98,7 +116,18 @@ def main(argv=None):
     ap.add_argument("--n3", type=int, default=32, help="elements per axis (3D)")
     ap.add_argument("--per-octave", type=int, default=4)
     ap.add_argument("--octaves", type=int, default=2)
+    ap.add_argument("--disc", type=int, nargs="*", default=None, help="background grid sizes of the disc")
+    ap.add_argument("--disc-p", type=int, nargs="+", default=[2, 3])
     args = ap.parse_args(argv)
+    if args.disc:
+        for p in args.disc_p:
+            for n in args.disc:
+                t0 = time.perf_counter()
+                r, it, ne = disc_rho(n, p)
+                print(json.dumps({"domain": "disc r = 0.45, standard form, mu = 1, Dirichlet", "p": p, "n": n,
+                                  "elements": ne, "tau": P.TABLE1_TAU[(0, 2, p)], "rho": round(r, 4),
+                                  "iterations": it, "seconds": round(time.perf_counter() - t0, 1)}), flush=True)
+        return
     for case in args.cases:
         form, d, p = (int(v) for v in case.split(","))
         n = args.n if d == 2 else args.n3
