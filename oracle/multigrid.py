@@ -27,7 +27,11 @@ Low-precision storage (not in the paper; emulated here as the library stores
 it): every block of the smoother -- A_ii^{-1}, A_ii and the couplings -- is
 rounded once from FP64, and a cycle with rounded blocks also forms its
 in-cycle residual b - A x from those rounded blocks (the outer residual stays
-FP64).  Vectors and sums stay FP64 in the emulation.
+FP64).  precondition() keeps vectors and sums in FP64; precondition_fp32()
+runs the same cycle on float32 vectors with float32 products and sums (the
+library's FP32 cycle: FP32 vectors on every level, the injection rounded to
+FP32, the bottom pseudo-inverse applied in FP64 to the float32 right-hand side
+and rounded back).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -113,9 +117,22 @@ class SmootherLevel:
         self.rows = [(e[:, None] * self.nb + np.arange(self.nb)[None, :]).ravel() for e in self.elems]
         self.Aoff_rows = [self.Aoff[r, :].tocsr() for r in self.rows]
 
+    def f32(self):
+        """float32 copies of the blocks (for a float32 cycle)."""
+        if not hasattr(self, "_f32"):
+            self._f32 = (self.inv.astype(np.float32), self.diag.astype(np.float32),
+                         [m.astype(np.float32) for m in self.Aoff_rows], self.Aoff.astype(np.float32))
+        return self._f32
+
     def colour_step(self, x, b, c):
-        """Update every element of colour c from the current x (one data-parallel step)."""
+        """Update every element of colour c from the current x (one data-parallel step).
+        float32 vectors take float32 products and sums."""
         r = self.rows[c]
+        if x.dtype == np.float32:
+            inv, _, rows, _ = self.f32()
+            g = (b[r] - rows[c] @ x).reshape(-1, self.nb)
+            x[r] = np.einsum("eij,ej->ei", inv[self.elems[c]], g).ravel()
+            return
         g = (b[r] - self.Aoff_rows[c] @ x).reshape(-1, self.nb)
         x[r] = np.einsum("eij,ej->ei", self.inv[self.elems[c]], g).ravel()
 
@@ -276,18 +293,32 @@ class Multigrid:
     def cycle_residual(self, l, x, b):
         """Residual inside the V-cycle: from the smoother's stored blocks
         (rounded ones for a low-precision cycle; = residual() in FP64)."""
+        if x.dtype == np.float32:
+            sm = self.sm[l]
+            _, diag, _, Aoff = sm.f32()
+            y = np.einsum("eij,ej->ei", diag, x.reshape(-1, sm.nb)).ravel()
+            return b - (y + Aoff @ x)
         if self.storage is None:
             return self.residual(l, x, b)
         sm = self.sm[l]
         y = np.einsum("eij,ej->ei", sm.diag, x.reshape(-1, sm.nb)).ravel()
         return b - (y + sm.Aoff @ x)
 
+    def _I32(self, l):
+        if not hasattr(self, "_i32"):
+            self._i32 = [m.astype(np.float32) for m in self.I]
+        return self._i32[l]
+
     def restrict(self, l, r):
         """r_2h = (I_2h^h)^T r_h, the coarse right-hand side of Algorithm 1."""
+        if r.dtype == np.float32:
+            return self._I32(l).T @ r
         return self.I[l].T @ r
 
     def prolong(self, l, xc):
         """I_2h^h x_2h (injection)."""
+        if xc.dtype == np.float32:
+            return self._I32(l) @ xc
         return self.I[l] @ xc
 
     def sweeps(self, nu, l):
@@ -306,7 +337,10 @@ class Multigrid:
         nu1 = self.nu1 if nu1 is None else nu1
         nu2 = self.nu2 if nu2 is None else nu2
         if l == len(self.levels) - 1:
-            x[:] = self.bottom_solve(b)
+            if x.dtype == np.float32:
+                x[:] = (self.bottom @ b.astype(np.float64)).astype(np.float32)
+            else:
+                x[:] = self.bottom_solve(b)
             return x
         sm = self.sm[l]
         for _ in range(self.sweeps(nu1, l)):
@@ -325,6 +359,13 @@ class Multigrid:
         """The linear operator V: one V-cycle from a zero initial guess."""
         c = np.zeros_like(r)
         return self.vcycle(c, r, **kw)
+
+    def precondition_fp32(self, r, **kw):
+        """V on float32 vectors with float32 products and sums (the library's
+        FP32 cycle): r rounded to float32, the result returned in FP64."""
+        r32 = r.astype(np.float32)
+        c = np.zeros_like(r32)
+        return self.vcycle(c, r32, **kw).astype(np.float64)
 
     def solve(self, b, x0=None, rtol=1e-10, maxit=100, **kw):
         """Outer iteration x <- x + V(0, b - A x) (iterative refinement)."""

@@ -14,7 +14,8 @@ Command line: ``python -m paper_1911_05888_gb300.tau --cases 0,2,2 1,2,3
 --n 128`` prints one JSON line per (form, d, p) case.  ``--disc 32 64 128
 --disc-p 2 3`` instead prints rho on Section 5's curved domain (the disc of
 radius 0.45 on an n x n background grid, standard form, mu = 1, Dirichlet data
-on the circle) with Table 1's tau.
+on the circle) with Table 1's tau; ``--bubble 32 64 128`` the same for the
+water / gas bubble of Section 6.
 """
 import argparse
 import json
@@ -49,6 +50,27 @@ def disc_rho(n, p, precision=native.FP64, seed=1, reduction=1e-8, maxit=100):
     from .solver import CutStokesMG
     prob = P.CutProblem(n=n, p=p, gamma=0, mu_phase=(1.0,), radius=0.45, inside_only=True)
     mg = CutStokesMG(prob, precision=precision)
+    try:
+        x0 = torch.from_numpy(P.random_vector(mg.ne, mg.nb, seed=seed).ravel()).cuda()
+        r, it, _, _ = mg.ctx.gmres_rho(x0, reduction, maxit)
+    finally:
+        mg.close()
+    return r, it, mg.ne
+
+
+def bubble_rho(n, p, water_inside, precision=native.FP64, seed=1, reduction=1e-8, maxit=100, bottom_max=0):
+    """(rho, iterations, elements) of eq. (rho) for the paper's time-dependent
+    two-phase bubble (Section 6): the circle of radius 0.3 in the unit
+    square, water (rho = 1, mu = 1) and gas (rho = 1e-3, mu = 2e-4), delta =
+    0.1 h, viscous-stress form, Dirichlet box, sqrt(mu) scaling; water inside
+    (water_inside) or gas inside."""
+    import torch
+    from .solver import CutStokesMG
+    water, gas = (1.0, 1.0), (1e-3, 2e-4)   # (rho, mu)
+    inside, outside = (water, gas) if water_inside else (gas, water)
+    prob = P.CutProblem(n=n, p=p, gamma=1, mu_phase=(inside[1], outside[1]), rho_phase=(inside[0], outside[0]),
+                        delta=0.1 / n, radius=0.3)
+    mg = CutStokesMG(prob, precision=precision, bottom_max=bottom_max)
     try:
         x0 = torch.from_numpy(P.random_vector(mg.ne, mg.nb, seed=seed).ravel()).cuda()
         r, it, _, _ = mg.ctx.gmres_rho(x0, reduction, maxit)
@@ -118,7 +140,20 @@ def main(argv=None):
     ap.add_argument("--octaves", type=int, default=2)
     ap.add_argument("--disc", type=int, nargs="*", default=None, help="background grid sizes of the disc")
     ap.add_argument("--disc-p", type=int, nargs="+", default=[2, 3])
+    ap.add_argument("--bubble", type=int, nargs="*", default=None,
+                    help="background grid sizes of the water / gas bubble (Section 6)")
     args = ap.parse_args(argv)
+    if args.bubble:
+        for water_inside in (True, False):
+            for p in args.disc_p:
+                for n in args.bubble:
+                    t0 = time.perf_counter()
+                    r, it, ne = bubble_rho(n, p, water_inside)
+                    print(json.dumps({"problem": "water bubble in gas" if water_inside else "gas bubble in water",
+                                      "radius": 0.3, "delta": "0.1 h", "p": p, "n": n, "elements": ne,
+                                      "tau": P.TABLE1_TAU[(1, 2, p)], "rho": round(r, 4), "iterations": it,
+                                      "seconds": round(time.perf_counter() - t0, 1)}), flush=True)
+        return
     if args.disc:
         for p in args.disc_p:
             for n in args.disc:

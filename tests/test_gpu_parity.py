@@ -273,6 +273,28 @@ def test_low_precision_cycle_close_to_oracle_emulation(name, precision):
         assert rel(x.cpu().numpy(), orc32.precondition(b)) > 10 * rel(x.cpu().numpy(), xo)
 
 
+@pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "dirichlet-rect", "3d-mixed-p1", "square-1e-3"])
+def test_fp32_cycle_matches_float32_emulation(name):
+    """One FP32 cycle (FP32-rounded blocks, FP32 vectors, FP32 sums) against
+    the oracle's float32 emulation of the same cycle (precondition_fp32): the
+    two differ only in the order of FP32 sums, 1e-5 relative (the emulation
+    with FP64 vectors is ~1e-6 away from either, so a kernel that accumulated
+    in a wider type, or in a wrong order of magnitude, would show)."""
+    prob, gpu64, _ = get(name)
+    _, gpu, _ = get(name, native.FP32)
+    orc = oracle_for(prob, storage="fp32")
+    b = gpu64.rhs().ravel()
+    bd = dev(b)
+    x = torch.zeros_like(bd)
+    gpu.ctx.set_solver(native.RICHARDSON, 30)   # one outer step from zero is x = V(b)
+    gpu.ctx.solve(x, bd, rtol=1e-30, maxit=1)
+    xg = x.cpu().numpy()
+    x32 = orc.precondition_fp32(b)
+    print(name, "fp32 emulation %.1e (entry-wise %.1e), fp64-vector emulation %.1e"
+          % (rel(xg, x32), maxrel(xg, x32), rel(xg, orc.precondition(b))))
+    assert rel(xg, x32) <= 1e-5 and maxrel(xg, x32) <= 1e-4
+
+
 @pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-mixed-p1"])
 def test_fp16_colour_step_warp_and_wide_kernels(name):
     """FP16 colour steps of both kernels (one warp per element; one CTA per
