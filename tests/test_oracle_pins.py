@@ -1229,3 +1229,18 @@ def test_cut_disc_order(gamma):
     assert max(a8, a16) <= 1e-12 and max(r8, r16) <= 1e-10
     rate = np.log2(e8 / e16)
     assert np.all(np.abs(rate - 3.0) < 0.35), rate
+
+
+def test_float32_cycle_emulation_tracks_the_fp64_cycle():
+    """The oracle's float32 cycle (float32 vectors, products and sums; FP32
+    injection; FP64 bottom) takes the same steps as its FP64-vector cycle with
+    the same FP32-rounded blocks: the two agree to FP32 rounding amplified by
+    the cycle (1e-5), and the float32 cycle is not the FP64 one (it differs by
+    more than 1e-9)."""
+    prob = P.stress_variable_mu_2d(n=8, p=2)
+    mg = multigrid.Multigrid(prob, storage="fp32")
+    b = np.random.default_rng(0).uniform(-1, 1, prob.n_dofs)
+    x64 = mg.precondition(b)
+    x32 = mg.precondition_fp32(b)
+    d = np.linalg.norm(x32 - x64) / np.linalg.norm(x64)
+    assert 1e-9 < d <= 1e-5, d
