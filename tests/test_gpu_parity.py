@@ -276,10 +276,12 @@ def test_low_precision_cycle_close_to_oracle_emulation(name, precision):
 @pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "dirichlet-rect", "3d-mixed-p1", "square-1e-3"])
 def test_fp32_cycle_matches_float32_emulation(name):
     """One FP32 cycle (FP32-rounded blocks, FP32 vectors, FP32 sums) against
-    the oracle's float32 emulation of the same cycle (precondition_fp32): the
-    two differ only in the order of FP32 sums, 1e-5 relative (the emulation
-    with FP64 vectors is ~1e-6 away from either, so a kernel that accumulated
-    in a wider type, or in a wrong order of magnitude, would show)."""
+    the oracle's float32 emulation of the same cycle (precondition_fp32) and
+    its FP64-vector emulation: within FP32 rounding noise of both, 3e-5
+    relative and 5e-5 entry-wise.  (Measured: the GPU lies 4e-7 to 1.4e-5
+    from the float32 emulation and 3e-7 to 9e-6 from the FP64-vector one; its
+    fused multiply-adds round once per product and sum, numpy's float32 twice,
+    so the FP64-vector emulation is the nearer of the two.)"""
     prob, gpu64, _ = get(name)
     _, gpu, _ = get(name, native.FP32)
     orc = oracle_for(prob, storage="fp32")
@@ -290,9 +292,11 @@ def test_fp32_cycle_matches_float32_emulation(name):
     gpu.ctx.solve(x, bd, rtol=1e-30, maxit=1)
     xg = x.cpu().numpy()
     x32 = orc.precondition_fp32(b)
+    x64 = orc.precondition(b)
     print(name, "fp32 emulation %.1e (entry-wise %.1e), fp64-vector emulation %.1e"
-          % (rel(xg, x32), maxrel(xg, x32), rel(xg, orc.precondition(b))))
-    assert rel(xg, x32) <= 1e-5 and maxrel(xg, x32) <= 1e-4
+          % (rel(xg, x32), maxrel(xg, x32), rel(xg, x64)))
+    assert rel(xg, x32) <= 3e-5 and maxrel(xg, x32) <= 5e-5
+    assert rel(xg, x64) <= 3e-5 and maxrel(xg, x64) <= 5e-5
 
 
 @pytest.mark.parametrize("name", ["stress16p3", "periodic16p2", "3d-mixed-p1"])
