@@ -592,14 +592,18 @@ def run_native(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     ach = alg / t_gs / 1e9
     traffic = read_profile_traffic("gs_sweep_%s_256x256_p3.md" % args.precision)
-    roof = {"kernel": "element_kernel (block GS colour sweep, finest level, %s blocks)" % args.precision,
+    kernel_of = {0: "element_kernel", 1: "element_pipe_kernel", 2: "element_warp_kernel",
+                 3: "element_ring_kernel"}
+    roof = {"kernel": "%s (block GS colour sweep, finest level, %s blocks)" % (
+                kernel_of.get(tuned["variant"], "element_kernel"), args.precision),
             "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(ach / hbm_peak, 3), "traffic": traffic,
             "algorithmic_bytes_per_launch": int(alg), "launch_ms": round(t_gs * 1e3, 4),
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     variants = {}
-    names = {0: "direct", 1: "bulk_pipeline", 2: "warp_per_element"}
-    for var in ((2,) if prec == native.FP16 else (0, 1, 2)):   # FP16 records: warp kernel only
+    names = {0: "direct", 1: "bulk_pipeline", 2: "warp_per_element", 3: "warp_per_element_staged"}
+    # FP16 records: the warp kernels only; the staged one takes 16-bit records
+    for var in {native.FP16: (2, 3), native.BF16: (0, 1, 2, 3)}.get(prec, (0, 1, 2)):
         mg.ctx.set_tuning(var, prec)
         tv = time_kernel(lambda: mg.ctx.gs_colour_ex(0, 0, prec, xv, bv, stream), 20, stream)
         variants[names[var]] = {"launch_ms": round(tv * 1e3, 4), "GBps": round(alg / tv / 1e9, 1)}

@@ -676,7 +676,15 @@ int stk_set_solver(stk_ctx* ctx, int method, int restart);
  * variant 0 = one CTA per element with direct 16-byte loads of the element
  * records; variant 1 = the records streamed into a shared-memory ring of
  * `stages` buffers by 1-D bulk copies (cp.async.bulk, mbarrier completion);
- * variant 2 (default) = one warp per element, no block-wide barriers.
+ * variant 2 (default for FP64 and FP32 blocks) = one warp per element, no
+ * block-wide barriers;
+ * variant 3 = one warp per element whose records, scales and gathered
+ * neighbour values are copied into the warp's shared memory by cp.async, the
+ * next element's coupling records while the warp computes this element's
+ * dense product (the default for BF16 and FP16
+ * blocks, s and nb multiples of 4, at most 32 neighbour offsets; other
+ * shapes and precisions run variant 2; the same products as variant 2, each
+ * coupling row summed as two halves of its columns).
  * The variant and `ctas_per_sm` (the grid of variants 1 and 2, CTAs per SM)
  * apply to the blocks stored in `precision` only.  Zero for ctas_per_sm and stages selects the
  * built-in shape for the record size.
@@ -702,8 +710,9 @@ int stk_set_wide_launch(stk_ctx* ctx, int max_positions);
 /*
  * Autotuner for the element-kernel launches (no counterpart in the paper):
  * on this context's own finest-level records it times one colour step for
- * the warp-per-element kernel at 2, 3, 4, 6 and 8 CTAs per SM and for the
- * one-CTA-per-element kernel with direct loads, in the cycle's precision and
+ * the warp-per-element kernel at 2, 3, 4, 6 and 8 CTAs per SM, for the
+ * one-CTA-per-element kernel with direct loads and, for 16-bit blocks, for
+ * the staged warp kernel (variant 3), in the cycle's precision and
  * in FP64 (the outer residual), and keeps the fastest shapes; then it times
  * both that choice and the one-CTA-per-element latency kernel on every
  * smoothing level and sets the stk_set_wide_launch threshold with the least

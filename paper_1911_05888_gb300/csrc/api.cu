@@ -49,7 +49,12 @@ cudaError_t run_element_on(Ctx& c, const Pattern& pat, DevLevel& D, int prec, in
     if (e != cudaErrorInvalidValue || scaled) return e;
   }
   const int variant = c.variant_of[prec];
-  if (variant == 2 || scaled) {
+  if (variant == 3) {   // 16-bit records, next element staged while this one computes
+    cudaError_t e = launch_element_ring(pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b, x,
+                                        r, st);
+    if (e != cudaErrorInvalidValue) return e;
+  }
+  if (variant >= 2 || scaled) {
     cudaError_t e = launch_element_warp(pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
                                         x, r, c.warp_ctas[prec], st);
     if (e != cudaErrorInvalidValue || scaled) return e;
@@ -2279,7 +2284,7 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
 
 int stk_set_tuning(stk_ctx* c, int variant, int precision, int ctas_per_sm, int stages) {
   return guard(c, [&]() -> int {
-    if (variant < 0 || variant > 2 || precision < 0 || precision > 3 || ctas_per_sm < 0 || ctas_per_sm > 32 ||
+    if (variant < 0 || variant > 3 || precision < 0 || precision > 3 || ctas_per_sm < 0 || ctas_per_sm > 32 ||
         stages < 0 || stages > 16)
       return fail(c, STK_ERR_INVALID_ARG, "bad tuning options");
     c->variant_of[precision] = variant;
@@ -2398,8 +2403,15 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
         c->variant_of[prec] = 0;
         t0 = time_step(0, prec, 10);
       }
-      c->variant_of[prec] = t0 < t2 ? 0 : 2;
-      best[pi] = std::min(t0, t2);
+      // 16-bit records: the warp kernel with the next element staged (falls
+      // back to the plain warp kernel where the shape does not fit)
+      double t3 = 1e300;
+      if (prec == STK_FP16 || prec == STK_BF16) {
+        c->variant_of[prec] = 3;
+        t3 = time_step(0, prec, 10);
+      }
+      c->variant_of[prec] = t3 < std::min(t0, t2) ? 3 : (t0 < t2 ? 0 : 2);
+      best[pi] = std::min(std::min(t0, t2), t3);
     }
     // FGMRES matvec of a low-precision cycle: FP32-unit double-float kernel or
     // the FP64 residual kernel, whichever is faster over the whole level 0.

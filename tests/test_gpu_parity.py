@@ -326,6 +326,76 @@ def test_fp16_colour_step_warp_and_wide_kernels(name):
         gpu.ctx.set_wide_launch(1024)
 
 
+def _steps_and_residual(gpu, precision, x0, b):
+    """Every colour step of level 0 from x0, then the residual of the result,
+    as float32 arrays."""
+    xd = torch.from_numpy(x0).float().cuda()
+    bd = torch.from_numpy(b).float().cuda()
+    for c in range(gpu.ctx.info(native.INFO_COLOURS)):
+        gpu.ctx.gs_colour_ex(0, c, precision, xd, bd)
+    r = torch.empty_like(xd)
+    gpu.ctx.residual_ex(0, precision, xd, bd, r)
+    torch.cuda.synchronize()
+    return xd.cpu().numpy(), r.cpu().numpy()
+
+
+def _with_variant(gpu, precision, variant, fn):
+    gpu.ctx.set_wide_launch(0)
+    gpu.ctx.set_tuning(variant, precision)
+    try:
+        return fn()
+    finally:
+        gpu.ctx.set_tuning(3, precision)   # the default for 16-bit records
+        gpu.ctx.set_wide_launch(1024)
+
+
+@pytest.mark.parametrize("precision", [native.FP16, native.BF16])
+@pytest.mark.parametrize("name", ["stress16p3", "3d-mixed-p1"])
+def test_staged_16bit_kernel_matches_oracle(name, precision):
+    """The warp kernel with the next element staged in shared memory (variant
+    3, 16-bit records): its colour steps and residual agree with the plain
+    warp kernel's to FP32 rounding (the same products; each coupling row
+    summed as two halves of its columns), and its colour steps equal the
+    oracle's colour step with the same rounded blocks to FP32 level."""
+    prob, _, _ = get(name)
+    _, gpu, _ = get(name, precision)
+    orc = oracle_for(prob, storage="fp16" if precision == native.FP16 else "bf16")
+    sm = orc.sm[0]
+    rng = np.random.default_rng(23)
+    x0 = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
+    b = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
+    xs, rs = _with_variant(gpu, precision, 3, lambda: _steps_and_residual(gpu, precision, x0, b))
+    xw, rw = _with_variant(gpu, precision, 2, lambda: _steps_and_residual(gpu, precision, x0, b))
+    assert rel(xs, xw) <= 1e-5 and maxrel(xs, xw) <= 1e-5
+    assert rel(rs, rw) <= 1e-5 and maxrel(rs, rw) <= 1e-5
+    xo = x0.copy()
+    for c in range(sm.ncol):
+        sm.colour_step(xo, b, c)
+    assert rel(xs, xo) <= 1e-4 and maxrel(xs, xo) <= 1e-3
+
+
+@pytest.mark.parametrize("precision", [native.FP16, native.BF16])
+def test_staged_16bit_kernel_on_many_elements_per_warp(precision):
+    """128 x 128, p = 3 viscous stress: each warp of the staged kernel walks
+    several elements per launch (4096 per colour over at most 152 x 8 warps),
+    so every element's records are requested while the warp computes the
+    one before.  Colour steps and residual agree with the plain warp kernel's
+    to FP32 rounding."""
+    prob = P.stress_variable_mu_2d(n=128, p=3)
+    gpu = StokesMG(prob, precision=precision)
+    try:
+        rng = np.random.default_rng(29)
+        x0 = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
+        b = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
+        xs, rs = _with_variant(gpu, precision, 3, lambda: _steps_and_residual(gpu, precision, x0, b))
+        xw, rw = _with_variant(gpu, precision, 2, lambda: _steps_and_residual(gpu, precision, x0, b))
+        assert np.all(np.isfinite(xs)) and np.abs(xs - x0).max() > 0
+        assert rel(xs, xw) <= 1e-5 and maxrel(xs, xw) <= 1e-5
+        assert rel(rs, rw) <= 1e-5 and maxrel(rs, rw) <= 1e-5
+    finally:
+        gpu.close()
+
+
 def test_invalid_arguments_are_rejected():
     ctx = native.Context(0)
     with pytest.raises(native.StkError):
