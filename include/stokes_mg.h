@@ -678,15 +678,16 @@ int stk_set_solver(stk_ctx* ctx, int method, int restart);
  * `stages` buffers by 1-D bulk copies (cp.async.bulk, mbarrier completion);
  * variant 2 (default for FP64 and FP32 blocks) = one warp per element, no
  * block-wide barriers;
- * variant 3 = one warp per element whose records, scales and gathered
- * neighbour values are copied into the warp's shared memory by cp.async, the
- * next element's coupling records while the warp computes this element's
+ * variant 3 = one or two warps per element whose records, scales and
+ * gathered neighbour values are copied into their shared memory by cp.async,
+ * the next element's coupling records while they compute this element's
  * dense product (the default for BF16 and FP16
  * blocks, s and nb multiples of 4, at most 32 neighbour offsets; other
  * shapes and precisions run variant 2; the same products as variant 2, each
  * coupling row summed as two halves of its columns).
- * The variant and `ctas_per_sm` (the grid of variants 1 and 2, CTAs per SM)
- * apply to the blocks stored in `precision` only.  Zero for ctas_per_sm and stages selects the
+ * The variant and `ctas_per_sm` (the grid of variants 1 and 2, CTAs per SM;
+ * for variant 3 the warps per element, 1 or 2, default 2) apply to the
+ * blocks stored in `precision` only.  Zero for ctas_per_sm and stages selects the
  * built-in shape for the record size.
  * Shapes whose ring does not fit in shared memory fall back to variant 0.
  * If a bulk copy never completes, the kernel's bounded wait (about one
@@ -712,7 +713,8 @@ int stk_set_wide_launch(stk_ctx* ctx, int max_positions);
  * on this context's own finest-level records it times one colour step for
  * the warp-per-element kernel at 2, 3, 4, 6 and 8 CTAs per SM, for the
  * one-CTA-per-element kernel with direct loads and, for 16-bit blocks, for
- * the staged warp kernel (variant 3), in the cycle's precision and
+ * the staged kernel (variant 3) with one and two warps per element, in the
+ * cycle's precision and
  * in FP64 (the outer residual), and keeps the fastest shapes; then it times
  * both that choice and the one-CTA-per-element latency kernel on every
  * smoothing level and sets the stk_set_wide_launch threshold with the least
@@ -724,7 +726,8 @@ int stk_set_wide_launch(stk_ctx* ctx, int max_positions);
  * (the FP64 outer residual may take another kernel than the cycle); under a
  * low-precision cycle it also times the two FGMRES matvecs (stk_set_df_matvec)
  * over level 0 and keeps the faster.  choice (may be NULL, 6 ints) receives
- * {variant and CTAs per SM in the cycle precision, variant and CTAs per SM in
+ * {variant and CTAs per SM (variant 3: warps per element) in the cycle
+ * precision, variant and CTAs per SM in
  * FP64, latency-kernel limit, FP32-unit matvec on/off};
  * best_ms (may be NULL, 2 doubles) the fastest finest-level colour step in
  * the cycle precision and in FP64.  Results are unchanged up to the

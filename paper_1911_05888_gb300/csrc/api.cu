@@ -50,8 +50,8 @@ cudaError_t run_element_on(Ctx& c, const Pattern& pat, DevLevel& D, int prec, in
   }
   const int variant = c.variant_of[prec];
   if (variant == 3) {   // 16-bit records, next element staged while this one computes
-    cudaError_t e = launch_element_ring(pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b, x,
-                                        r, st);
+    cudaError_t e = launch_element_ring(pat, prec, c.ring_warps[prec], mode, pos0, npos, D.perm, D.nbr, D.cpl[prec],
+                                        mat, tsc, rsc, b, x, r, st);
     if (e != cudaErrorInvalidValue) return e;
   }
   if (variant >= 2 || scaled) {
@@ -2289,6 +2289,10 @@ int stk_set_tuning(stk_ctx* c, int variant, int precision, int ctas_per_sm, int 
       return fail(c, STK_ERR_INVALID_ARG, "bad tuning options");
     c->variant_of[precision] = variant;
     if (variant == 2 && ctas_per_sm > 0) c->warp_ctas[precision] = ctas_per_sm;
+    if (variant == 3) {
+      if (ctas_per_sm > 2) return fail(c, STK_ERR_INVALID_ARG, "variant 3 takes 1 or 2 warps per element");
+      c->ring_warps[precision] = ctas_per_sm > 0 ? ctas_per_sm : 2;
+    }
     if (variant == 1 && ctas_per_sm > 0 && stages > 0) {
       c->pipe_ctas[precision] = ctas_per_sm;
       c->pipe_stages[precision] = stages;
@@ -2408,7 +2412,16 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
       double t3 = 1e300;
       if (prec == STK_FP16 || prec == STK_BF16) {
         c->variant_of[prec] = 3;
-        t3 = time_step(0, prec, 10);
+        int bw = 2;
+        for (int w : {1, 2}) {
+          c->ring_warps[prec] = w;
+          const double t = time_step(0, prec, 10);
+          if (t < t3) {
+            t3 = t;
+            bw = w;
+          }
+        }
+        c->ring_warps[prec] = bw;
       }
       c->variant_of[prec] = t3 < std::min(t0, t2) ? 3 : (t0 < t2 ? 0 : 2);
       best[pi] = std::min(std::min(t0, t2), t3);
@@ -2492,7 +2505,7 @@ int stk_autotune(stk_ctx* c, int* choice, double* best_ms, void* stream) {
     c->cycle_graph_prec = -1;
     if (choice) {
       choice[0] = c->variant_of[c->precision];
-      choice[1] = c->warp_ctas[c->precision];
+      choice[1] = c->variant_of[c->precision] == 3 ? c->ring_warps[c->precision] : c->warp_ctas[c->precision];
       choice[2] = c->variant_of[STK_FP64];
       choice[3] = c->warp_ctas[STK_FP64];
       choice[4] = c->wide_max;

@@ -396,8 +396,8 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
 // For 16-bit records (FP16 with scales, BF16; FP32 vectors).  A 16-bit record
 // carries half the bytes of an FP32 one per dependent load round, so the
 // warp kernel above, whose warp walks one element through its gather, record
-// and dense-block rounds, leaves HBM half idle.  Here each warp owns one
-// shared-memory stage of an element, filled by cp.async in two groups:
+// and dense-block rounds, leaves HBM half idle.  Here each element slot owns
+// one shared-memory stage of an element, filled by cp.async in two groups:
 //   G1: the coupling records, their task scales, the S-value segments of x
 //       the gathers address (zeros where the neighbour is absent) and b_e;
 //   G2: the dense block A_ii^{-1} or A_ii, its row scales and, for
@@ -405,9 +405,9 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
 // As soon as the coupling rows and their row sums of element k are done, G1
 // of element k + stride is issued into the same space, so the bulk of the
 // next element's bytes flies while the warp does element k's dense product;
-// G2 follows when element k is written.  One stage per warp (rather than two
-// alternating ones) leaves room for about twice as many warps, hence as many
-// elements in flight per SM.  Element and neighbour indices are loaded one
+// G2 follows when element k is written.  One stage per element slot (rather
+// than two alternating ones) leaves room for about twice as many slots,
+// hence as many elements in flight per SM; one or two warps work on a slot.  Element and neighbour indices are loaded one
 // element further ahead, so issuing a group never waits on a load.  In a
 // colour step the gathered segments belong to other colours, which no warp
 // of the launch writes, so a segment fetched early holds the value the step
@@ -415,28 +415,30 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
 // (items of (half, lane-column) fill the warp's lanes evenly), so each
 // coupling row sum is the sum of two partial sums: the association differs
 // from element_warp_kernel's in that one step.
-constexpr int kRingMaxWarps = 16;
+constexpr int kRingMaxWarps = 20;   // 640 threads: 102 registers a thread
 
 struct RingGeom {
-  int warps;                                     // warps per CTA (0: shape not supported)
+  int P;                                         // warps per element
+  int slots;                                     // elements (stages) per CTA (0: shape not supported)
   int XR;                                        // slot stride of a gathered segment (S + 4 values)
   int NCG, CW;                                   // dense column groups, columns per group
   uint32_t o_tsc, o_xg, o_b, o_mat, o_rsc, o_xi; // byte offsets inside the stage
   uint32_t o_work;                               // byte offset of the work arrays
-  uint32_t warp_bytes;                           // shared bytes per warp
+  uint32_t slot_bytes;                           // shared bytes per stage and its work arrays
 };
 
 template <typename TS>
-static RingGeom ring_geometry(const Pattern& pat) {
+static RingGeom ring_geometry(const Pattern& pat, int P) {
   constexpr int V = StorageTraits<TS>::V;
   auto up = [](size_t v) { return (uint32_t)((v + 15) / 16 * 16); };
   RingGeom g{};
+  g.P = P;
   const int S = pat.s;
   // 16-byte copies need S and nb in whole float4s; lanes hold the neighbour
-  // indices (NO <= 32); the final row loop covers 4 x 32 rows
+  // indices (NO <= 32); the final row loop covers 128 rows
   if (S % 4 || pat.nb % 4 || pat.NO > 32 || pat.nb > 128) return g;
   const int NRV = pat.NBP / V;
-  g.NCG = (32 / NRV) > 0 ? (32 / NRV) : 1;
+  g.NCG = (32 * P / NRV) > 0 ? (32 * P / NRV) : 1;
   g.CW = (pat.nb + g.NCG - 1) / g.NCG;
   g.XR = S + 4;
   size_t o = up((size_t)S * pat.TRP * sizeof(TS));   // coupling records at 0
@@ -456,15 +458,15 @@ static RingGeom ring_geometry(const Pattern& pat) {
   // part (two halves of TRP partial sums; the dense product's column-group
   // partials reuse it once the row sums have read it), then g
   const size_t work = (std::max<size_t>(2 * (size_t)pat.TRP, (size_t)g.NCG * pat.NBP) + pat.NBP) * sizeof(float);
-  g.warp_bytes = up(g.o_work + work);
-  const int w = (int)std::min<size_t>(kRingMaxWarps, (size_t)(226 * 1024) / g.warp_bytes);
-  g.warps = w >= 2 ? w : 0;
+  g.slot_bytes = up(g.o_work + work);
+  const int w = (int)std::min<size_t>(kRingMaxWarps / P, (size_t)(226 * 1024) / g.slot_bytes);
+  g.slots = w >= 2 ? w : 0;
   return g;
 }
 
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-template <typename TS, int S>
+template <typename TS, int S, int P>
 __global__ void __launch_bounds__(32 * kRingMaxWarps)
     element_ring_kernel(const __grid_constant__ Pattern pat, const __grid_constant__ RingGeom rg, int mode,
                         int pos0, int npos, const int* __restrict__ perm, const int* __restrict__ nbr,
@@ -473,12 +475,20 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
   using Tr = StorageTraits<TS>;
   constexpr int V = Tr::V;
   constexpr int QS = S / 4;   // float4 chunks per gathered segment
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int G = 32 * P;   // threads per element
+  const int lane = threadIdx.x & 31, t = threadIdx.x % G, slot = threadIdx.x / G;
   const int nb = pat.nb, NBP = pat.NBP, TRP = pat.TRP, TR = pat.TR, NO = pat.NO;
   const int NRV = NBP / V;
   const int TP = task_scale_stride(pat);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* st = smem_raw + (size_t)wid * rg.warp_bytes;
+  unsigned char* st = smem_raw + (size_t)slot * rg.slot_bytes;
+  // the element's threads meet: one warp, or a named barrier of the P warps
+  auto sync = [&]() {
+    if constexpr (P == 1)
+      __syncwarp();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(G) : "memory");
+  };
   const TS* rec = reinterpret_cast<const TS*>(st);
   const float* tss = reinterpret_cast<const float*>(st + rg.o_tsc);
   float* xg = reinterpret_cast<float*>(st + rg.o_xg);
@@ -490,9 +500,9 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
   float* part2 = part;   // after the row sums
   float* g = part + max(2 * TRP, rg.NCG * NBP);
   const int end = pos0 + npos;
-  const int stride = gridDim.x * rg.warps;
-  int pos = pos0 + blockIdx.x * rg.warps + wid;
-  if (pos >= end) return;   // uniform over the warp
+  const int stride = gridDim.x * rg.slots;
+  int pos = pos0 + blockIdx.x * rg.slots + slot;
+  if (pos >= end) return;   // uniform over the element's warps
 
   // element id and this lane's neighbour index (lane o holds offset o) of position p
   auto load_idx = [&](int p, int& e, int& nj) {
@@ -508,12 +518,12 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
     const unsigned char* src = reinterpret_cast<const unsigned char*>(cpl + (size_t)p * S * TRP);
     const int nc = S * TRP * (int)sizeof(TS) / 16;
 #pragma unroll 4
-    for (int q = lane; q < nc; q += 32) cp_async16(st + (size_t)q * 16, src + (size_t)q * 16);
+    for (int q = t; q < nc; q += G) cp_async16(st + (size_t)q * 16, src + (size_t)q * 16);
     if constexpr (kScaledStorage<TS>)
-      for (int q = lane; q < TP / 4; q += 32) cp_async16(st + rg.o_tsc + q * 16, tsc + (size_t)p * TP + q * 4);
+      for (int q = t; q < TP / 4; q += G) cp_async16(st + rg.o_tsc + q * 16, tsc + (size_t)p * TP + q * 4);
     const int nq = pat.NG * QS;
-    for (int q0 = 0; q0 < nq; q0 += 32) {   // uniform trip count: every lane takes part in the shuffle
-      const int q = q0 + lane;
+    for (int q0 = 0; q0 < nq; q0 += G) {   // uniform trip count: every lane takes part in the shuffle
+      const int q = q0 + t;
       const int gi = q < nq ? q / QS : 0;
       const int j = __shfl_sync(0xffffffffu, nj, pat.g_o[gi]);
       if (q < nq) {
@@ -525,18 +535,18 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
           *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    for (int q = lane; q < nb / 4; q += 32) cp_async16(st + rg.o_b + q * 16, b + (size_t)e * nb + q * 4);
+    for (int q = t; q < nb / 4; q += G) cp_async16(st + rg.o_b + q * 16, b + (size_t)e * nb + q * 4);
   };
   // G2 of position p
   auto issue_g2 = [&](int p, int e) {
     const unsigned char* src = reinterpret_cast<const unsigned char*>(mat + (size_t)p * nb * NBP);
     const int nm = nb * NBP * (int)sizeof(TS) / 16;
 #pragma unroll 4
-    for (int q = lane; q < nm; q += 32) cp_async16(st + rg.o_mat + (size_t)q * 16, src + (size_t)q * 16);
+    for (int q = t; q < nm; q += G) cp_async16(st + rg.o_mat + (size_t)q * 16, src + (size_t)q * 16);
     if constexpr (kScaledStorage<TS>)
-      for (int q = lane; q < NBP / 4; q += 32) cp_async16(st + rg.o_rsc + q * 16, rsc + (size_t)p * NBP + q * 4);
+      for (int q = t; q < NBP / 4; q += G) cp_async16(st + rg.o_rsc + q * 16, rsc + (size_t)p * NBP + q * 4);
     if (mode == MODE_RESID)
-      for (int q = lane; q < nb / 4; q += 32) cp_async16(st + rg.o_xi + q * 16, x + (size_t)e * nb + q * 4);
+      for (int q = t; q < nb / 4; q += G) cp_async16(st + rg.o_xi + q * 16, x + (size_t)e * nb + q * 4);
   };
 
   int e_cur, nj_cur, e_nxt, nj_nxt;
@@ -550,7 +560,7 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
     const int e = e_cur;
     const int pn = pos + stride;   // this warp's next position; e_nxt / nj_nxt are its indices
     cp_async_wait_one();   // this lane's G1 of pos has landed (its G2 may still fly)
-    __syncwarp();          // ... and every lane's
+    sync();          // ... and every lane's
     if constexpr (S % V == 0) {
       // The V rows of a lane-column lie in one task (one x value per column).
       // Work item it = (half h, lane-column tv): the columns of half h, so
@@ -558,7 +568,7 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
       // halves' partial sums meet in the row sums.
       constexpr int SH = S / 2;
       const int NTV = TRP / V;
-      for (int it = lane; it < 2 * NTV; it += 32) {
+      for (int it = t; it < 2 * NTV; it += G) {
         const int h = it >= NTV ? 1 : 0;
         const int tv = it - h * NTV, tr0 = tv * V;
         const float* xp = ((tr0 < TR) ? xg + pat.task_g[tr0 / S] * rg.XR : xg) + h * SH;
@@ -584,7 +594,7 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
         for (int j = 0; j < V / 2; j += 2) dst[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
       }
     } else {
-      for (int tv = lane; tv < TRP / V; tv += 32) {
+      for (int tv = t; tv < TRP / V; tv += G) {
         const int tr0 = tv * V;
         float acc[V];
         const float* xp[V];
@@ -606,8 +616,8 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
         for (int j = 0; j < V; j += 4) dst[j / 4] = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
       }
     }
-    __syncwarp();
-    for (int r = lane; r < nb; r += 32) {
+    sync();
+    for (int r = t; r < nb; r += G) {
       const int rv = r / S, rr = r - rv * S;
       float sum = 0.f;
       for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) {
@@ -618,13 +628,13 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
       }
       g[r] = bs[r] - sum;
     }
-    __syncwarp();   // G1's space is consumed: refill it with the next element's
+    sync();   // G1's space is consumed: refill it with the next element's
     if (pn < end) issue_g1(pn, e_nxt, nj_nxt);
     cp_async_commit();
     cp_async_wait_one();   // G2 of pos has landed (G1 of pn may still fly)
-    __syncwarp();
+    sync();
     const float* vin = (mode == MODE_GS) ? g : xis;
-    for (int u = lane; u < NRV * rg.NCG; u += 32) {
+    for (int u = t; u < NRV * rg.NCG; u += G) {
       const int rvv = u % NRV, cg = u / NRV;
       const int c0 = cg * rg.CW, c1 = min(nb, c0 + rg.CW);
       float2 acc[V / 2];
@@ -642,10 +652,10 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
 #pragma unroll
       for (int j = 0; j < V / 2; j += 2) dst[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
     }
-    __syncwarp();
+    sync();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = lane + 32 * q;
+    for (int q = 0; q < 128 / G; ++q) {
+      const int r = t + G * q;
       if (r >= nb) break;
       float sum = 0.f;
       for (int cg = 0; cg < rg.NCG; ++cg) sum += part2[cg * NBP + r];
@@ -655,7 +665,7 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
       else
         rout[(size_t)e * nb + r] = g[r] - sum;
     }
-    __syncwarp();   // G2's space and the work arrays are consumed
+    sync();   // G2's space and the work arrays are consumed
     if (pn < end) issue_g2(pn, e_nxt);
     cp_async_commit();
     e_cur = e_nxt;
@@ -1143,54 +1153,70 @@ cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int p
   }
 }
 
-template <typename TS, int S>
+template <typename TS, int S, int P>
 static cudaError_t launch_ring_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
                                  const void* cpl, const void* mat, const float* tsc, const float* rsc, const void* b,
                                  void* x, void* r, cudaStream_t st) {
   if (npos <= 0) return cudaSuccess;
-  const RingGeom rg = ring_geometry<TS>(pat);
-  if (!rg.warps) return cudaErrorInvalidValue;
+  const RingGeom rg = ring_geometry<TS>(pat, P);
+  if (!rg.slots) return cudaErrorInvalidValue;
   if (kScaledStorage<TS> && (!tsc || !rsc)) return cudaErrorInvalidValue;
   // every cp.async source is a 16-byte chunk of one of these arrays
   auto a16 = [](const void* p) { return p == nullptr || ((uintptr_t)p & 15) == 0; };
   if (!a16(cpl) || !a16(mat) || !a16(tsc) || !a16(rsc) || !a16(b) || !a16(x) || !a16(r))
     return cudaErrorInvalidValue;
-  const size_t smem = (size_t)rg.warps * rg.warp_bytes;
+  const size_t smem = (size_t)rg.slots * rg.slot_bytes;
   const int per_sm = std::max<int>(1, (int)((228 * 1024) / (smem + 1024)));
-  const int grid = std::min((npos + rg.warps - 1) / rg.warps, num_sms() * per_sm);
-  element_ring_kernel<TS, S><<<grid, 32 * rg.warps, smem, st>>>(pat, rg, mode, pos0, npos, perm, nbr, (const TS*)cpl,
-                                                               (const TS*)mat, tsc, rsc, (const float*)b, (float*)x,
-                                                               (float*)r);
+  const int grid = std::min((npos + rg.slots - 1) / rg.slots, num_sms() * per_sm);
+  element_ring_kernel<TS, S, P><<<grid, 32 * P * rg.slots, smem, st>>>(pat, rg, mode, pos0, npos, perm, nbr,
+                                                                      (const TS*)cpl, (const TS*)mat, tsc, rsc,
+                                                                      (const float*)b, (float*)x, (float*)r);
   return cudaGetLastError();
 }
 
-template <typename TS>
-static cudaError_t launch_ring_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
+template <typename TS, int P>
+static cudaError_t launch_ring_p(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
                                  const void* cpl, const void* mat, const float* tsc, const float* rsc, const void* b,
                                  void* x, void* r, cudaStream_t st) {
   switch (pat.s) {
-    case 4: return launch_ring_s<TS, 4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
-    case 8: return launch_ring_s<TS, 8>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
-    case 16: return launch_ring_s<TS, 16>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 4: return launch_ring_s<TS, 4, P>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 8: return launch_ring_s<TS, 8, P>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 16: return launch_ring_s<TS, 16, P>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename TS>
-static void prepare_ring_t() {
-  cudaFuncSetAttribute(element_ring_kernel<TS, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
-  cudaFuncSetAttribute(element_ring_kernel<TS, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
-  cudaFuncSetAttribute(element_ring_kernel<TS, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+static cudaError_t launch_ring_t(const Pattern& pat, int warps, int mode, int pos0, int npos, const int* perm,
+                                 const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
+                                 const void* b, void* x, void* r, cudaStream_t st) {
+  if (warps == 1) return launch_ring_p<TS, 1>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+  return launch_ring_p<TS, 2>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
 }
 
-// 16-bit records only (storage 2 = BF16, 3 = scaled FP16); cudaErrorInvalidValue
-// for other storages and for shapes the staged kernel does not take.
-cudaError_t launch_element_ring(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
-                                const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
-                                const void* b, void* x, void* r, cudaStream_t st) {
+template <typename TS, int P>
+static void prepare_ring_p() {
+  cudaFuncSetAttribute(element_ring_kernel<TS, 4, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_ring_kernel<TS, 8, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaFuncSetAttribute(element_ring_kernel<TS, 16, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+}
+
+template <typename TS>
+static void prepare_ring_t() {
+  prepare_ring_p<TS, 1>();
+  prepare_ring_p<TS, 2>();
+}
+
+// 16-bit records only (storage 2 = BF16, 3 = scaled FP16), warps = 1 or 2
+// per element; cudaErrorInvalidValue for other storages and for shapes the
+// staged kernel does not take.
+cudaError_t launch_element_ring(const Pattern& pat, int storage, int warps, int mode, int pos0, int npos,
+                                const int* perm, const int* nbr, const void* cpl, const void* mat, const float* tsc,
+                                const float* rsc, const void* b, void* x, void* r, cudaStream_t st) {
   switch (storage) {
-    case 2: return launch_ring_t<__nv_bfloat16>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
-    case 3: return launch_ring_t<__half>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 2:
+      return launch_ring_t<__nv_bfloat16>(pat, warps, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 3: return launch_ring_t<__half>(pat, warps, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
     default: return cudaErrorInvalidValue;
   }
 }

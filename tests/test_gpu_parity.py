@@ -339,9 +339,9 @@ def _steps_and_residual(gpu, precision, x0, b):
     return xd.cpu().numpy(), r.cpu().numpy()
 
 
-def _with_variant(gpu, precision, variant, fn):
+def _with_variant(gpu, precision, variant, fn, shape=0):
     gpu.ctx.set_wide_launch(0)
-    gpu.ctx.set_tuning(variant, precision)
+    gpu.ctx.set_tuning(variant, precision, shape)
     try:
         return fn()
     finally:
@@ -349,9 +349,10 @@ def _with_variant(gpu, precision, variant, fn):
         gpu.ctx.set_wide_launch(1024)
 
 
+@pytest.mark.parametrize("warps", [1, 2])
 @pytest.mark.parametrize("precision", [native.FP16, native.BF16])
 @pytest.mark.parametrize("name", ["stress16p3", "3d-mixed-p1"])
-def test_staged_16bit_kernel_matches_oracle(name, precision):
+def test_staged_16bit_kernel_matches_oracle(name, precision, warps):
     """The warp kernel with the next element staged in shared memory (variant
     3, 16-bit records): its colour steps and residual agree with the plain
     warp kernel's to FP32 rounding (the same products; each coupling row
@@ -364,7 +365,7 @@ def test_staged_16bit_kernel_matches_oracle(name, precision):
     rng = np.random.default_rng(23)
     x0 = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
     b = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
-    xs, rs = _with_variant(gpu, precision, 3, lambda: _steps_and_residual(gpu, precision, x0, b))
+    xs, rs = _with_variant(gpu, precision, 3, lambda: _steps_and_residual(gpu, precision, x0, b), warps)
     xw, rw = _with_variant(gpu, precision, 2, lambda: _steps_and_residual(gpu, precision, x0, b))
     assert rel(xs, xw) <= 1e-5 and maxrel(xs, xw) <= 1e-5
     assert rel(rs, rw) <= 1e-5 and maxrel(rs, rw) <= 1e-5
@@ -374,10 +375,11 @@ def test_staged_16bit_kernel_matches_oracle(name, precision):
     assert rel(xs, xo) <= 1e-4 and maxrel(xs, xo) <= 1e-3
 
 
+@pytest.mark.parametrize("warps", [1, 2])
 @pytest.mark.parametrize("precision", [native.FP16, native.BF16])
-def test_staged_16bit_kernel_on_many_elements_per_warp(precision):
-    """128 x 128, p = 3 viscous stress: each warp of the staged kernel walks
-    several elements per launch (4096 per colour over at most 152 x 8 warps),
+def test_staged_16bit_kernel_on_many_elements_per_warp(precision, warps):
+    """128 x 128, p = 3 viscous stress: each element slot of the staged kernel
+    walks several elements per launch (4096 per colour over 152 x 10 slots),
     so every element's records are requested while the warp computes the
     one before.  Colour steps and residual agree with the plain warp kernel's
     to FP32 rounding."""
@@ -387,7 +389,7 @@ def test_staged_16bit_kernel_on_many_elements_per_warp(precision):
         rng = np.random.default_rng(29)
         x0 = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
         b = rng.uniform(-1, 1, prob.n_dofs).astype(np.float32).astype(np.float64)
-        xs, rs = _with_variant(gpu, precision, 3, lambda: _steps_and_residual(gpu, precision, x0, b))
+        xs, rs = _with_variant(gpu, precision, 3, lambda: _steps_and_residual(gpu, precision, x0, b), warps)
         xw, rw = _with_variant(gpu, precision, 2, lambda: _steps_and_residual(gpu, precision, x0, b))
         assert np.all(np.isfinite(xs)) and np.abs(xs - x0).max() > 0
         assert rel(xs, xw) <= 1e-5 and maxrel(xs, xw) <= 1e-5
