@@ -404,18 +404,21 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
 //       residuals, x_e.
 // As soon as the coupling rows and their row sums of element k are done, G1
 // of element k + stride is issued into the same space, so the bulk of the
-// next element's bytes flies while the warp does element k's dense product;
+// next element's bytes flies while the slot does element k's dense product;
 // G2 follows when element k is written.  One stage per element slot (rather
-// than two alternating ones) leaves room for about twice as many slots,
-// hence as many elements in flight per SM; one or two warps work on a slot.  Element and neighbour indices are loaded one
-// element further ahead, so issuing a group never waits on a load.  In a
+// than two alternating ones), whose consumed records also take the coupling
+// and dense partial sums, leaves room for about twice as many slots (12 of
+// 18.5 KB per SM for FP16, p = 3), hence as many elements in flight per SM;
+// one or two warps work on a slot.  Element and neighbour indices are loaded
+// one element further ahead, so issuing a group never waits on a load.  In a
 // colour step the gathered segments belong to other colours, which no warp
 // of the launch writes, so a segment fetched early holds the value the step
 // must read.  The coupling rows are split into two halves of the columns
-// (items of (half, lane-column) fill the warp's lanes evenly), so each
-// coupling row sum is the sum of two partial sums: the association differs
-// from element_warp_kernel's in that one step.
-constexpr int kRingMaxWarps = 20;   // 640 threads: 102 registers a thread
+// (items of (half, lane-column) fill the threads evenly), so each coupling
+// row sum is the sum of two partial sums: the association differs from
+// element_warp_kernel's in that one step.
+constexpr int kRingMaxWarps = 24;   // 768 threads: 85 registers a thread
+constexpr int kRingItems = 128;     // coupling work items of an element (4 / P per thread)
 
 struct RingGeom {
   int P;                                         // warps per element
@@ -455,10 +458,16 @@ static RingGeom ring_geometry(const Pattern& pat, int P) {
   g.o_xi = (uint32_t)o;
   o += up((size_t)pat.NBP * sizeof(float));
   g.o_work = (uint32_t)o;
-  // part (two halves of TRP partial sums; the dense product's column-group
-  // partials reuse it once the row sums have read it), then g
-  const size_t work = (std::max<size_t>(2 * (size_t)pat.TRP, (size_t)g.NCG * pat.NBP) + pat.NBP) * sizeof(float);
-  g.slot_bytes = up(g.o_work + work);
+  // Work arrays: g alone.  The coupling partial sums (up to two halves of
+  // TRP values) overwrite the consumed coupling records and the dense
+  // product's column-group partials the consumed dense block; each thread
+  // keeps its coupling items (at most kRingItems per element) in registers.
+  const int ntv = pat.TRP / V, nit = (S % V == 0) ? 2 * ntv : ntv;
+  if ((size_t)((S % V == 0) ? 2 : 1) * pat.TRP * sizeof(float) > (size_t)S * pat.TRP * sizeof(TS) ||
+      (size_t)g.NCG * pat.NBP * sizeof(float) > (size_t)pat.nb * pat.NBP * sizeof(TS) ||
+      nit > kRingItems)
+    return g;
+  g.slot_bytes = up(g.o_work + (size_t)pat.NBP * sizeof(float));
   const int w = (int)std::min<size_t>(kRingMaxWarps / P, (size_t)(226 * 1024) / g.slot_bytes);
   g.slots = w >= 2 ? w : 0;
   return g;
@@ -496,9 +505,7 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
   const TS* mrec = reinterpret_cast<const TS*>(st + rg.o_mat);
   const float* rss = reinterpret_cast<const float*>(st + rg.o_rsc);
   const float* xis = reinterpret_cast<const float*>(st + rg.o_xi);
-  float* part = reinterpret_cast<float*>(st + rg.o_work);
-  float* part2 = part;   // after the row sums
-  float* g = part + max(2 * TRP, rg.NCG * NBP);
+  float* g = reinterpret_cast<float*>(st + rg.o_work);
   const int end = pos0 + npos;
   const int stride = gridDim.x * rg.slots;
   int pos = pos0 + blockIdx.x * rg.slots + slot;
@@ -558,72 +565,85 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
   cp_async_commit();
   for (; pos < end; pos += stride) {
     const int e = e_cur;
-    const int pn = pos + stride;   // this warp's next position; e_nxt / nj_nxt are its indices
-    cp_async_wait_one();   // this lane's G1 of pos has landed (its G2 may still fly)
-    sync();          // ... and every lane's
-    if constexpr (S % V == 0) {
-      // The V rows of a lane-column lie in one task (one x value per column).
-      // Work item it = (half h, lane-column tv): the columns of half h, so
-      // that the 2 x TRP / V items fill the warp's lanes evenly; the two
-      // halves' partial sums meet in the row sums.
-      constexpr int SH = S / 2;
-      const int NTV = TRP / V;
-      for (int it = t; it < 2 * NTV; it += G) {
-        const int h = it >= NTV ? 1 : 0;
+    const int pn = pos + stride;   // this element slot's next position; e_nxt / nj_nxt are its indices
+    cp_async_wait_one();   // this thread's G1 of pos has landed (its G2 may still fly)
+    sync();                // ... and every thread's
+    // Coupling rows.  Work item it = (half h, lane-column tv) when the V rows
+    // of a lane-column lie in one task (one x value per column; the columns
+    // of half h, so that the 2 x TRP / V items fill the threads evenly and
+    // the two halves' partial sums meet in the row sums), else it = tv over
+    // all columns.  The partial sums stay in registers until every thread has
+    // read its records, then overwrite the consumed records.
+    constexpr bool kHalves = S % V == 0;
+    constexpr int SH = kHalves ? S / 2 : S;
+    const int NTV = TRP / V;
+    const int nit = kHalves ? 2 * NTV : NTV;
+    constexpr int MI = kRingItems / G;   // items per thread
+    float2 acc[MI][V / 2];
+    int dst_off[MI];
+#pragma unroll
+    for (int i = 0; i < MI; ++i) {
+      const int it = t + i * G;
+      dst_off[i] = -1;
+      if (it < nit) {
+        const int h = (kHalves && it >= NTV) ? 1 : 0;
         const int tv = it - h * NTV, tr0 = tv * V;
-        const float* xp = ((tr0 < TR) ? xg + pat.task_g[tr0 / S] * rg.XR : xg) + h * SH;
         const TS* rp = rec + (size_t)h * SH * TRP + tr0;
-        float2 acc[V / 2];   // row pairs: packed FP32 FMAs, each lane of a pair rounded as fmaf
 #pragma unroll
-        for (int j = 0; j < V / 2; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < V / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
+        if constexpr (kHalves) {
+          const float* xp = ((tr0 < TR) ? xg + pat.task_g[tr0 / S] * rg.XR : xg) + h * SH;
 #pragma unroll
-        for (int c4 = 0; c4 < SH; c4 += 4) {
-          const float4 xv4 = *reinterpret_cast<const float4*>(xp + c4);
-          const float xv[4] = {xv4.x, xv4.y, xv4.z, xv4.w};
+          for (int c4 = 0; c4 < SH; c4 += 4) {
+            const float4 xv4 = *reinterpret_cast<const float4*>(xp + c4);
+            const float xv[4] = {xv4.x, xv4.y, xv4.z, xv4.w};
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 4; ++k) {
+              float w[V];
+              Tr::load_shared(rp + (size_t)(c4 + k) * TRP, w);
+              const float2 x2 = make_float2(xv[k], xv[k]);
+#pragma unroll
+              for (int j = 0; j < V / 2; ++j)
+                acc[i][j] = __ffma2_rn(make_float2(w[2 * j], w[2 * j + 1]), x2, acc[i][j]);
+            }
+          }
+        } else {
+          const float* xp[V];
+#pragma unroll
+          for (int j = 0; j < V; ++j) {
+            const int tr = tr0 + j;
+            xp[j] = (tr < TR) ? xg + pat.task_g[tr / S] * rg.XR : xg;
+          }
+#pragma unroll
+          for (int ci = 0; ci < S; ++ci) {
             float w[V];
-            Tr::load_shared(rp + (size_t)(c4 + k) * TRP, w);
-            const float2 x2 = make_float2(xv[k], xv[k]);
+            Tr::load_shared(rp + (size_t)ci * TRP, w);
 #pragma unroll
-            for (int j = 0; j < V / 2; ++j) acc[j] = __ffma2_rn(make_float2(w[2 * j], w[2 * j + 1]), x2, acc[j]);
+            for (int j = 0; j < V / 2; ++j)
+              acc[i][j] = __ffma2_rn(make_float2(w[2 * j], w[2 * j + 1]), make_float2(xp[2 * j][ci], xp[2 * j + 1][ci]),
+                                     acc[i][j]);
           }
         }
-        float4* dst = reinterpret_cast<float4*>(part + h * TRP + tr0);
-#pragma unroll
-        for (int j = 0; j < V / 2; j += 2) dst[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
-      }
-    } else {
-      for (int tv = t; tv < TRP / V; tv += G) {
-        const int tr0 = tv * V;
-        float acc[V];
-        const float* xp[V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-          const int tr = tr0 + j;
-          xp[j] = (tr < TR) ? xg + pat.task_g[tr / S] * rg.XR : xg;
-          acc[j] = 0.f;
-        }
-#pragma unroll
-        for (int ci = 0; ci < S; ++ci) {
-          float w[V];
-          Tr::load_shared(rec + (size_t)ci * TRP + tr0, w);
-#pragma unroll
-          for (int j = 0; j < V; ++j) acc[j] = fmaf(w[j], xp[j][ci], acc[j]);
-        }
-        float4* dst = reinterpret_cast<float4*>(part + tr0);
-#pragma unroll
-        for (int j = 0; j < V; j += 4) dst[j / 4] = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+        dst_off[i] = h * TRP + tr0;
       }
     }
+    sync();   // the coupling records are consumed: their space takes the partial sums
+    float* part = reinterpret_cast<float*>(st);
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+      if (dst_off[i] >= 0) {
+        float4* d4 = reinterpret_cast<float4*>(part + dst_off[i]);
+#pragma unroll
+        for (int j = 0; j < V / 2; j += 2) d4[j / 2] = make_float4(acc[i][j].x, acc[i][j].y, acc[i][j + 1].x, acc[i][j + 1].y);
+      }
     sync();
     for (int r = t; r < nb; r += G) {
       const int rv = r / S, rr = r - rv * S;
       float sum = 0.f;
-      for (int t = pat.rv_t0[rv]; t < pat.rv_t1[rv]; ++t) {
-        float pt = part[t * S + rr];
-        if constexpr (S % V == 0) pt += part[TRP + t * S + rr];
-        if constexpr (kScaledStorage<TS>) pt *= tss[t];
+      for (int tk = pat.rv_t0[rv]; tk < pat.rv_t1[rv]; ++tk) {
+        float pt = part[tk * S + rr];
+        if constexpr (kHalves) pt += part[TRP + tk * S + rr];
+        if constexpr (kScaledStorage<TS>) pt *= tss[tk];
         sum += pt;
       }
       g[r] = bs[r] - sum;
@@ -633,24 +653,31 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
     cp_async_commit();
     cp_async_wait_one();   // G2 of pos has landed (G1 of pn may still fly)
     sync();
+    // Dense product in column groups: one item per thread (NCG = G / NRV);
+    // the group partials overwrite the consumed dense block.
     const float* vin = (mode == MODE_GS) ? g : xis;
-    for (int u = t; u < NRV * rg.NCG; u += G) {
-      const int rvv = u % NRV, cg = u / NRV;
-      const int c0 = cg * rg.CW, c1 = min(nb, c0 + rg.CW);
-      float2 acc[V / 2];
+    float2 dacc[V / 2];
+    const int u = t, rvv = u % NRV, cg = u / NRV;
+    const bool dact = u < NRV * rg.NCG;
 #pragma unroll
-      for (int j = 0; j < V / 2; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < V / 2; ++j) dacc[j] = make_float2(0.f, 0.f);
+    if (dact) {
+      const int c0 = cg * rg.CW, c1 = min(nb, c0 + rg.CW);
 #pragma unroll 4
       for (int ci = c0; ci < c1; ++ci) {
         float w[V];
         Tr::load_shared(mrec + (size_t)ci * NBP + rvv * V, w);
         const float2 v2 = make_float2(vin[ci], vin[ci]);
 #pragma unroll
-        for (int j = 0; j < V / 2; ++j) acc[j] = __ffma2_rn(make_float2(w[2 * j], w[2 * j + 1]), v2, acc[j]);
+        for (int j = 0; j < V / 2; ++j) dacc[j] = __ffma2_rn(make_float2(w[2 * j], w[2 * j + 1]), v2, dacc[j]);
       }
-      float4* dst = reinterpret_cast<float4*>(part2 + cg * NBP + rvv * V);
+    }
+    sync();   // every thread has read its part of the dense block
+    float* part2 = reinterpret_cast<float*>(st + rg.o_mat);
+    if (dact) {
+      float4* d4 = reinterpret_cast<float4*>(part2 + cg * NBP + rvv * V);
 #pragma unroll
-      for (int j = 0; j < V / 2; j += 2) dst[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
+      for (int j = 0; j < V / 2; j += 2) d4[j / 2] = make_float4(dacc[j].x, dacc[j].y, dacc[j + 1].x, dacc[j + 1].y);
     }
     sync();
 #pragma unroll
@@ -658,14 +685,14 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
       const int r = t + G * q;
       if (r >= nb) break;
       float sum = 0.f;
-      for (int cg = 0; cg < rg.NCG; ++cg) sum += part2[cg * NBP + r];
+      for (int c = 0; c < rg.NCG; ++c) sum += part2[c * NBP + r];
       if constexpr (kScaledStorage<TS>) sum *= rss[r];
       if (mode == MODE_GS)
         x[(size_t)e * nb + r] = sum;
       else
         rout[(size_t)e * nb + r] = g[r] - sum;
     }
-    sync();   // G2's space and the work arrays are consumed
+    sync();   // G2's space is consumed
     if (pn < end) issue_g2(pn, e_nxt);
     cp_async_commit();
     e_cur = e_nxt;
