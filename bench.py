@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--learn-seeds", type=int, default=8)
     ap.add_argument("--learn-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--wide-max", type=int, default=-1,
+                    help="--profile runs: element-kernel launches of at most this many elements take the "
+                         "one-CTA-per-element kernel (-1: the library's default)")
     ap.add_argument("--profile", default=None, choices=["gs", "resid", "solve", "batch"],
                     help="run only a profiling target (for ncu): 8 finest-level colour sweeps, "
                          "8 finest-level residuals, one solve, or one persistent batch solve of the first "
@@ -373,6 +376,8 @@ def run_profile(args):
     # timing runs inside a profiler would mislead the autotuner
     mg.ctx.set_solver({"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR,
                        "richardson": native.RICHARDSON}[args.solver], args.restart)
+    if args.wide_max >= 0:
+        mg.ctx.set_wide_launch(args.wide_max)
     torch.cuda.synchronize()
     vdt = torch.float64 if prec == native.FP64 else torch.float32
     if args.profile in ("gs", "resid"):
