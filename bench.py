@@ -574,6 +574,14 @@ def run_native(args):
         if a != head:
             arms[a][0].close()
     el, iters, launches, hist = arm_runs[head]
+    overlap = None
+    if prec in (native.FP16, native.BF16):
+        # the staged kernel's programmatic dependent launch, off for comparison
+        mg.ctx.set_launch_overlap(0)
+        el_off = timed(mg.ctx, args.steps, 1)[0]
+        mg.ctx.set_launch_overlap(1)
+        overlap = {"on_ms_per_solve": round(el / args.steps * 1e3, 3),
+                   "off_ms_per_solve": round(el_off / args.steps * 1e3, 3)}
     cycles = sum(iters)
     el, units = aggregate(dist, el, prob.n_dofs * max(1, args.nrhs) * cycles, "cuda")
     value = units / el
@@ -693,7 +701,7 @@ def run_native(args):
         "gs_variants": variants, "autotune": {"cycle": tuned, "fp64": tuned64,
                                               "best_colour_step_ms": [round(v, 4) for v in tuned_ms]},
         "mixed_learned": mixed_learned,
-        "precision_arms": precision_arms, "headline_precision": head,
+        "precision_arms": precision_arms, "headline_precision": head, "launch_overlap": overlap,
         "clocks": clk,
     }
     if want_cpu:

@@ -51,7 +51,7 @@ cudaError_t run_element_on(Ctx& c, const Pattern& pat, DevLevel& D, int prec, in
   const int variant = c.variant_of[prec];
   if (variant == 3) {   // 16-bit records, next element staged while this one computes
     cudaError_t e = launch_element_ring(pat, prec, c.ring_warps[prec], mode, pos0, npos, D.perm, D.nbr, D.cpl[prec],
-                                        mat, tsc, rsc, b, x, r, st);
+                                        mat, tsc, rsc, b, x, r, c.launch_overlap, st);
     if (e != cudaErrorInvalidValue) return e;
   }
   if (variant >= 2 || scaled) {
@@ -2278,6 +2278,20 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
       }
     }
     if (iters_out) *iters_out = it;
+    return STK_OK;
+  });
+}
+
+int stk_set_launch_overlap(stk_ctx* c, int on) {
+  return guard(c, [&]() -> int {
+    if (on != 0 && on != 1) return fail(c, STK_ERR_INVALID_ARG, "launch overlap is 0 or 1");
+    c->launch_overlap = on;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_x = c->graph_b = nullptr;
+    if (c->cycle_graph) cudaGraphExecDestroy(c->cycle_graph);
+    c->cycle_graph = nullptr;
+    c->cycle_graph_prec = -1;
     return STK_OK;
   });
 }

@@ -475,6 +475,14 @@ static RingGeom ring_geometry(const Pattern& pat, int P) {
 
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel lets the next launch on its stream
+// start (griddepcontrol.launch_dependents; a no-op when that launch does not
+// ask for it), and a kernel launched with programmatic serialisation waits
+// for the previous one to complete, its writes visible, before it touches
+// what that kernel may write (griddepcontrol.wait; a no-op otherwise).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename TS, int S, int P>
 __global__ void __launch_bounds__(32 * kRingMaxWarps)
     element_ring_kernel(const __grid_constant__ Pattern pat, const __grid_constant__ RingGeom rg, int mode,
@@ -520,14 +528,18 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
       if (lane < NO) nj = nbr[(size_t)p * NO + lane];
     }
   };
-  // G1 of position p (element e, neighbour indices nj held by the lanes)
-  auto issue_g1 = [&](int p, int e, int nj) {
+  // G1 of position p (element e, neighbour indices nj held by the lanes):
+  // the records and scales, which no launch writes ...
+  auto issue_g1_records = [&](int p) {
     const unsigned char* src = reinterpret_cast<const unsigned char*>(cpl + (size_t)p * S * TRP);
     const int nc = S * TRP * (int)sizeof(TS) / 16;
 #pragma unroll 4
     for (int q = t; q < nc; q += G) cp_async16(st + (size_t)q * 16, src + (size_t)q * 16);
     if constexpr (kScaledStorage<TS>)
       for (int q = t; q < TP / 4; q += G) cp_async16(st + rg.o_tsc + q * 16, tsc + (size_t)p * TP + q * 4);
+  };
+  // ... and the vector segments, which earlier launches write
+  auto issue_g1_vectors = [&](int e, int nj) {
     const int nq = pat.NG * QS;
     for (int q0 = 0; q0 < nq; q0 += G) {   // uniform trip count: every lane takes part in the shuffle
       const int q = q0 + t;
@@ -544,24 +556,41 @@ __global__ void __launch_bounds__(32 * kRingMaxWarps)
     }
     for (int q = t; q < nb / 4; q += G) cp_async16(st + rg.o_b + q * 16, b + (size_t)e * nb + q * 4);
   };
-  // G2 of position p
-  auto issue_g2 = [&](int p, int e) {
+  auto issue_g1 = [&](int p, int e, int nj) {
+    issue_g1_records(p);
+    issue_g1_vectors(e, nj);
+  };
+  // G2 of position p: the dense block and its scales, and x_e (residuals)
+  auto issue_g2_records = [&](int p) {
     const unsigned char* src = reinterpret_cast<const unsigned char*>(mat + (size_t)p * nb * NBP);
     const int nm = nb * NBP * (int)sizeof(TS) / 16;
 #pragma unroll 4
     for (int q = t; q < nm; q += G) cp_async16(st + rg.o_mat + (size_t)q * 16, src + (size_t)q * 16);
     if constexpr (kScaledStorage<TS>)
       for (int q = t; q < NBP / 4; q += G) cp_async16(st + rg.o_rsc + q * 16, rsc + (size_t)p * NBP + q * 4);
+  };
+  auto issue_g2_vectors = [&](int e) {
     if (mode == MODE_RESID)
       for (int q = t; q < nb / 4; q += G) cp_async16(st + rg.o_xi + q * 16, x + (size_t)e * nb + q * 4);
   };
+  auto issue_g2 = [&](int p, int e) {
+    issue_g2_records(p);
+    issue_g2_vectors(e);
+  };
 
+  // The first element: its records (and the indices) are requested before the
+  // wait for the previous launch, its vector segments after it; the first
+  // commit group then holds both records and G1's vectors.
+  pdl_trigger();
   int e_cur, nj_cur, e_nxt, nj_nxt;
   load_idx(pos, e_cur, nj_cur);
   load_idx(pos + stride, e_nxt, nj_nxt);
-  issue_g1(pos, e_cur, nj_cur);
+  issue_g1_records(pos);
+  issue_g2_records(pos);
+  pdl_wait();
+  issue_g1_vectors(e_cur, nj_cur);
   cp_async_commit();
-  issue_g2(pos, e_cur);
+  issue_g2_vectors(e_cur);
   cp_async_commit();
   for (; pos < end; pos += stride) {
     const int e = e_cur;
@@ -942,6 +971,7 @@ static size_t element_smem(const Pattern& pat) {
 template <typename TX>
 __global__ void restrict_kernel(int d, int s, int nb, int nc0, int nc1, int nf0, int nf1, int64_t nec,
                                 const TX* __restrict__ P, const TX* __restrict__ r, TX* __restrict__ rc) {
+  pdl_trigger();   // the next (staged) launch may start
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TX* rs = reinterpret_cast<TX*>(smem_raw);
   for (int64_t C = blockIdx.x; C < nec; C += gridDim.x)
@@ -952,6 +982,7 @@ __global__ void restrict_kernel(int d, int s, int nb, int nc0, int nc1, int nf0,
 template <typename TX>
 __global__ void prolong_kernel(int d, int s, int nb, int nf0, int nf1, int nc0, int nc1, int64_t nec,
                                const TX* __restrict__ PT, const TX* __restrict__ xc, TX* __restrict__ x) {
+  pdl_trigger();   // the next (staged) launch may start
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TX* xs = reinterpret_cast<TX*>(smem_raw);
   for (int64_t C = blockIdx.x; C < nec; C += gridDim.x)
@@ -962,6 +993,7 @@ __global__ void prolong_kernel(int d, int s, int nb, int nf0, int nf1, int nc0, 
 template <typename TX>
 __global__ void bottom_kernel(int64_t n, const double* __restrict__ pinv, const TX* __restrict__ b,
                               TX* __restrict__ x) {
+  pdl_trigger();   // the next (staged) launch may start
   int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -1183,7 +1215,7 @@ cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int p
 template <typename TS, int S, int P>
 static cudaError_t launch_ring_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
                                  const void* cpl, const void* mat, const float* tsc, const float* rsc, const void* b,
-                                 void* x, void* r, cudaStream_t st) {
+                                 void* x, void* r, int overlap, cudaStream_t st) {
   if (npos <= 0) return cudaSuccess;
   const RingGeom rg = ring_geometry<TS>(pat, P);
   if (!rg.slots) return cudaErrorInvalidValue;
@@ -1195,20 +1227,28 @@ static cudaError_t launch_ring_s(const Pattern& pat, int mode, int pos0, int npo
   const size_t smem = (size_t)rg.slots * rg.slot_bytes;
   const int per_sm = std::max<int>(1, (int)((228 * 1024) / (smem + 1024)));
   const int grid = std::min((npos + rg.slots - 1) / rg.slots, num_sms() * per_sm);
-  element_ring_kernel<TS, S, P><<<grid, 32 * P * rg.slots, smem, st>>>(pat, rg, mode, pos0, npos, perm, nbr,
-                                                                      (const TS*)cpl, (const TS*)mat, tsc, rsc,
-                                                                      (const float*)b, (float*)x, (float*)r);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)(32 * P * rg.slots));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, element_ring_kernel<TS, S, P>, pat, rg, mode, pos0, npos, perm, nbr,
+                            (const TS*)cpl, (const TS*)mat, tsc, rsc, (const float*)b, (float*)x, (float*)r);
 }
 
 template <typename TS, int P>
 static cudaError_t launch_ring_p(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
                                  const void* cpl, const void* mat, const float* tsc, const float* rsc, const void* b,
-                                 void* x, void* r, cudaStream_t st) {
+                                 void* x, void* r, int ov, cudaStream_t st) {
   switch (pat.s) {
-    case 4: return launch_ring_s<TS, 4, P>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
-    case 8: return launch_ring_s<TS, 8, P>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
-    case 16: return launch_ring_s<TS, 16, P>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 4: return launch_ring_s<TS, 4, P>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ov, st);
+    case 8: return launch_ring_s<TS, 8, P>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ov, st);
+    case 16: return launch_ring_s<TS, 16, P>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ov, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1216,9 +1256,9 @@ static cudaError_t launch_ring_p(const Pattern& pat, int mode, int pos0, int npo
 template <typename TS>
 static cudaError_t launch_ring_t(const Pattern& pat, int warps, int mode, int pos0, int npos, const int* perm,
                                  const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
-                                 const void* b, void* x, void* r, cudaStream_t st) {
-  if (warps == 1) return launch_ring_p<TS, 1>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
-  return launch_ring_p<TS, 2>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+                                 const void* b, void* x, void* r, int ov, cudaStream_t st) {
+  if (warps == 1) return launch_ring_p<TS, 1>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ov, st);
+  return launch_ring_p<TS, 2>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ov, st);
 }
 
 template <typename TS, int P>
@@ -1235,15 +1275,19 @@ static void prepare_ring_t() {
 }
 
 // 16-bit records only (storage 2 = BF16, 3 = scaled FP16), warps = 1 or 2
-// per element; cudaErrorInvalidValue for other storages and for shapes the
-// staged kernel does not take.
+// per element; overlap = launch with programmatic serialisation (the kernel
+// starts while the previous launch on the stream finishes, and fetches its
+// first element's records before waiting for it).  cudaErrorInvalidValue for
+// other storages and for shapes the staged kernel does not take.
 cudaError_t launch_element_ring(const Pattern& pat, int storage, int warps, int mode, int pos0, int npos,
                                 const int* perm, const int* nbr, const void* cpl, const void* mat, const float* tsc,
-                                const float* rsc, const void* b, void* x, void* r, cudaStream_t st) {
+                                const float* rsc, const void* b, void* x, void* r, int overlap, cudaStream_t st) {
   switch (storage) {
     case 2:
-      return launch_ring_t<__nv_bfloat16>(pat, warps, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
-    case 3: return launch_ring_t<__half>(pat, warps, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+      return launch_ring_t<__nv_bfloat16>(pat, warps, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r,
+                                          overlap, st);
+    case 3:
+      return launch_ring_t<__half>(pat, warps, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, overlap, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -278,6 +278,7 @@ struct Ctx {
   // with the pipeline shape per storage precision (CTAs per SM, ring depth)
   int variant_of[4] = {2, 2, 3, 3};   // per storage precision (3: 16-bit records staged)
   int ring_warps[4] = {2, 2, 2, 2};   // warps per element of variant 3
+  int launch_overlap = 1;             // staged launches with programmatic serialisation
   int pipe_ctas[4] = {0, 0, 0, 0}, pipe_stages[4] = {0, 0, 0, 0};
   int warp_ctas[4] = {4, 4, 4, 4};   // CTAs (of 8 warps) per SM for the warp-per-element kernel
   // launches of at most this many elements use one CTA per element (latency variant), whatever the variant
@@ -478,7 +479,7 @@ cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int p
                                 const void* b, void* x, void* r, int ctas, cudaStream_t st);
 cudaError_t launch_element_ring(const Pattern& pat, int storage, int warps, int mode, int pos0, int npos,
                                 const int* perm, const int* nbr, const void* cpl, const void* mat, const float* tsc,
-                                const float* rsc, const void* b, void* x, void* r, cudaStream_t st);
+                                const float* rsc, const void* b, void* x, void* r, int overlap, cudaStream_t st);
 void pipe_default_shape(const Pattern& pat, int storage, int* ctas, int* stages);
 
 cudaError_t launch_fp64_fma(int blocks, int iters, double* out, cudaStream_t st);

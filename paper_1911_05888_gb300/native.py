@@ -78,6 +78,7 @@ SIGNATURES = {
     "stk_set_wide_launch": [_vp, ctypes.c_int],
     "stk_set_mrhs_tensor": [_vp, ctypes.c_int],
     "stk_set_df_matvec": [_vp, ctypes.c_int],
+    "stk_set_launch_overlap": [_vp, ctypes.c_int],
     "stk_autotune": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _vp],
     "stk_solve_batch": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
                         ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -523,6 +524,9 @@ class Context:
 
     def set_tuning(self, variant, precision, ctas_per_sm=0, stages=0):
         self._check(self.lib.stk_set_tuning(self.h, variant, precision, ctas_per_sm, stages), "stk_set_tuning")
+
+    def set_launch_overlap(self, on):
+        self._check(self.lib.stk_set_launch_overlap(self.h, 1 if on else 0), "stk_set_launch_overlap")
 
     def set_df_matvec(self, on):
         self._check(self.lib.stk_set_df_matvec(self.h, 1 if on else 0), "stk_set_df_matvec")

@@ -398,6 +398,31 @@ def test_staged_16bit_kernel_on_many_elements_per_warp(precision, warps):
         gpu.close()
 
 
+@pytest.mark.parametrize("precision", [native.FP16, native.BF16])
+def test_staged_kernel_launch_overlap_is_bit_identical(precision):
+    """Programmatic dependent launch of the staged kernel
+    (stk_set_launch_overlap): whole solves (V-cycles replayed from CUDA
+    graphs, transfers, bottom solve, every smoothing level on the staged
+    kernel) give the same iterate bit for bit with the overlap on and off."""
+    prob = P.stress_variable_mu_2d(n=64, p=3)
+    gpu = StokesMG(prob, precision=precision)
+    try:
+        gpu.ctx.set_wide_launch(0)
+        gpu.ctx.set_solver(native.FGMRES, 30)
+        b = torch.from_numpy(gpu.rhs().ravel()).cuda()
+        out = []
+        for on in (1, 0, 1):
+            gpu.ctx.set_launch_overlap(on)
+            x = torch.zeros_like(b)
+            it, hist = gpu.ctx.solve(x, b, rtol=1e-10, maxit=100)
+            out.append((it, x.cpu().numpy(), hist[-1]))
+        assert out[0][0] == out[1][0] == out[2][0]
+        assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][1], out[2][1])
+        assert out[0][2] <= 1e-10
+    finally:
+        gpu.close()
+
+
 def test_invalid_arguments_are_rejected():
     ctx = native.Context(0)
     with pytest.raises(native.StkError):
