@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--learn-seeds", type=int, default=8)
     ap.add_argument("--learn-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
+                    help="programmatic dependent launch of the element kernels (stk_set_launch_overlap)")
     ap.add_argument("--wide-max", type=int, default=-1,
                     help="--profile runs: element-kernel launches of at most this many elements take the "
                          "one-CTA-per-element kernel (-1: the library's default)")
@@ -372,6 +374,7 @@ def run_profile(args):
         return
     prob = workload(args.n, args.p)
     mg = StokesMG(prob, precision=prec, nu=(args.nu, args.nu))
+    mg.ctx.set_launch_overlap(args.overlap)
     # the library's default shapes (what the autotuner picks on this workload):
     # timing runs inside a profiler would mislead the autotuner
     mg.ctx.set_solver({"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR,
@@ -502,6 +505,7 @@ def run_native(args):
         t0 = time.perf_counter()
         m = StokesMG(prob, precision=precs[pname], device=local, nu=(args.nu, nu2), bottom_max=args.bottom_max)
         m.ctx.set_cycle_shape(*shape_of(args))
+        m.ctx.set_launch_overlap(args.overlap)
         tn = m.ctx.autotune()
         m.ctx.set_persistent(args.persistent, args.persistent_ctas)
         m.ctx.set_solver(method, args.restart)
@@ -514,6 +518,7 @@ def run_native(args):
     mg64 = StokesMG(prob, precision=native.FP64, device=local, nu=(args.nu, args.nu), bottom_max=args.bottom_max) \
         if (prec != native.FP64 or nu2 != args.nu or len(arm_names) > 1) else mg
     mg64.ctx.set_cycle_shape(*shape_of(args))
+    mg64.ctx.set_launch_overlap(args.overlap)
     tuned64 = mg64.ctx.autotune()[0] if mg64 is not mg else tuned
     mg64.ctx.set_persistent(args.persistent, args.persistent_ctas)
     mg64.ctx.set_solver(native.FGMRES if method == native.FGMRES_IR else method, args.restart)
@@ -575,8 +580,8 @@ def run_native(args):
             arms[a][0].close()
     el, iters, launches, hist = arm_runs[head]
     overlap = None
-    if prec in (native.FP16, native.BF16):
-        # the staged kernel's programmatic dependent launch, off for comparison
+    if args.overlap:
+        # the element kernels' programmatic dependent launch, off for comparison
         mg.ctx.set_launch_overlap(0)
         el_off = timed(mg.ctx, args.steps, 1)[0]
         mg.ctx.set_launch_overlap(1)
@@ -781,6 +786,7 @@ def run_unsteady(args):
     t0 = time.perf_counter()
     mg = StokesMG(prob, precision=prec, nu=(args.nu, args.nu))
     setup_s = time.perf_counter() - t0
+    mg.ctx.set_launch_overlap(args.overlap)
     mg.ctx.autotune()
     mg.ctx.set_solver({"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR,
                        "richardson": native.RICHARDSON}[args.solver], args.restart)
@@ -861,6 +867,7 @@ def run_cut(args):
         prob = P.CutProblem(n=n, p=p, mu_phase=(1.0, 1e-3), rho_phase=(1.0, 1e-3) if delta else None,
                             delta=delta, nu1=args.nu, nu2=args.nu)
         mg = CutStokesMG(prob, precision=prec, bottom_max=bottom)
+        mg.ctx.set_launch_overlap(args.overlap)
         vt = torch.float64 if prec == native.FP64 else torch.float32
         vx = torch.zeros(mg.ne * mg.nb, dtype=vt, device="cuda")
         vb = torch.ones(mg.ne * mg.nb, dtype=vt, device="cuda")
@@ -878,6 +885,7 @@ def run_cut(args):
         prob = P.CutProblem(n=n, p=p, mu_phase=(1.0, 1e-3), rho_phase=(1.0, 1e-3) if delta else None,
                             delta=delta, nu1=args.nu, nu2=args.nu)
         mg = CutStokesMG(prob, precision=prec, bottom_max=bottom)
+        mg.ctx.set_launch_overlap(args.overlap)
         mg.ctx.set_solver(native.FGMRES, args.restart)
         D = mg.scaling().ravel()
         z = np.zeros((mg.ne, mg.nb))
@@ -902,6 +910,7 @@ def run_cut(args):
                                 nu1=args.nu, nu2=args.nu)
             t0 = time.perf_counter()
             mg = CutStokesMG(prob, precision=precision, bottom_max=bottom)
+            mg.ctx.set_launch_overlap(args.overlap)
             setup_s = time.perf_counter() - t0
             mg.ctx.set_solver({"fgmres": native.FGMRES, "fgmres-ir": native.FGMRES_IR,
                                "richardson": native.RICHARDSON}[args.solver], args.restart)
@@ -1020,6 +1029,7 @@ def cut_learned_protocol(args, n, p, delta, stream, bottom, evaluations=4):
     prob = P.CutProblem(n=n, p=p, mu_phase=(1e-3, 1.0), rho_phase=(1e-3, 1.0) if delta else None, delta=delta,
                         nu1=args.nu, nu2=args.nu)
     mg = CutStokesMG(prob, precision=native.FP32, bottom_max=bottom)
+    mg.ctx.set_launch_overlap(args.overlap)
     out = {"problem": "light bubble (inside/outside mu and rho 1e-3), FP32 blocks", "n": n,
            "outer": "iterative refinement (the acceptance rule judges each cycle's outer residual)"}
     try:

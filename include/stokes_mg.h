@@ -696,14 +696,17 @@ int stk_set_solver(stk_ctx* ctx, int method, int restart);
 int stk_set_tuning(stk_ctx* ctx, int variant, int precision, int ctas_per_sm, int stages);
 
 /*
- * Launch overlap for the variant-3 kernel (not in the paper): on = 1 (the
- * default) launches it with programmatic stream serialisation, so that its
- * CTAs start while the previous kernel on the stream (a colour step, a
- * transfer or the bottom solve, each of which lets its dependents start at
- * once) is still running; they request their first element's records and
- * neighbour indices, which no launch writes, then wait for the previous
- * kernel to complete and its writes to be visible before they read any
- * vector.  Results are unchanged bit for bit; on = 0 launches it plainly.
+ * Launch overlap for the element kernels (not in the paper): on = 1 (the
+ * default) launches the colour steps and residuals of the warp (variant 2),
+ * staged (variant 3), one-CTA-per-element (coarse levels) and cut-cell
+ * kernels with programmatic stream serialisation, so that their CTAs start
+ * while the previous kernel on the stream (a colour step, a transfer or the
+ * bottom solve, each of which lets its dependents start at once) is still
+ * running.  The staged, one-CTA-per-element and cut-cell kernels first
+ * request what no launch writes (their first element's records, the dense
+ * blocks, neighbour indices); every kernel then waits for the previous one
+ * to complete and its writes to be visible before it reads or writes any
+ * vector.  Results are unchanged bit for bit; on = 0 launches them plainly.
  * Errors: STK_ERR_INVALID_ARG unless on is 0 or 1.
  */
 int stk_set_launch_overlap(stk_ctx* ctx, int on);

@@ -38,14 +38,14 @@ cudaError_t run_element_on(Ctx& c, const Pattern& pat, DevLevel& D, int prec, in
                            const void* mat, const void* b, void* x, void* r, cudaStream_t st) {
   if (D.gen)   // general block-sparse level (cut-cell hierarchy)
     return launch_gen_element(prec, mode, c.gen_warps, c.s, c.nb, D.nbp, pos0, npos, D.perm, D.tptr, D.tinfo,
-                              D.cpl[prec], mat, b, x, r, st);
+                              D.cpl[prec], mat, b, x, r, st, c.launch_overlap);
   // FP16 records carry scales and run on the warp and wide kernels only.
   const bool scaled = prec == STK_FP16;
   const float* tsc = scaled ? D.csc : nullptr;
   const float* rsc = scaled ? (mode == MODE_GS ? D.isc : D.dsc) : nullptr;
   if (npos <= c.wide_max) {
     cudaError_t e = launch_element_wide(pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
-                                        x, r, st);
+                                        x, r, st, c.launch_overlap);
     if (e != cudaErrorInvalidValue || scaled) return e;
   }
   const int variant = c.variant_of[prec];
@@ -56,7 +56,7 @@ cudaError_t run_element_on(Ctx& c, const Pattern& pat, DevLevel& D, int prec, in
   }
   if (variant >= 2 || scaled) {
     cudaError_t e = launch_element_warp(pat, prec, mode, pos0, npos, D.perm, D.nbr, D.cpl[prec], mat, tsc, rsc, b,
-                                        x, r, c.warp_ctas[prec], st);
+                                        x, r, c.warp_ctas[prec], st, c.launch_overlap);
     if (e != cudaErrorInvalidValue || scaled) return e;
   }
   if (variant == 1) {

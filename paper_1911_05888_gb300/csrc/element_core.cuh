@@ -146,6 +146,13 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Programmatic dependent launch: a kernel lets the next launch on its stream
+// start (griddepcontrol.launch_dependents; a no-op when that launch does not
+// ask for it), and a kernel launched with programmatic serialisation waits
+// for the previous one to complete, its writes visible, before it touches
+// what that kernel may write (griddepcontrol.wait; a no-op otherwise).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <typename TS>

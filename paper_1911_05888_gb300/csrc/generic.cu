@@ -15,6 +15,7 @@
 // staged in shared memory.
 #include <cuda_runtime.h>
 
+#include "element_core.cuh"
 #include "stk_internal.h"
 #include "../../include/stokes_mg.h"
 
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(kGenWarps * 32, 6)
   const int grp = threadIdx.x / G, gt = threadIdx.x % G, wi = gt >> 5;
   const int pos = pos0 + blockIdx.x * E + grp;
   const bool valid = pos < pos0 + npos;   // uniform over the element's warps
+  pdl_trigger();   // the next launch may start
   const int e = valid ? perm[pos] : 0;
   // the dense block, nb x nbp entries (nbp a multiple of 16 bytes), staged
   T* smat = reinterpret_cast<T*>(gen_dyn) + (size_t)grp * nb * nbp;
@@ -113,6 +115,9 @@ __global__ void __launch_bounds__(kGenWarps * 32, 6)
     t = min(a1, a0 + wi * chunk);
     t1 = min(a1, t + chunk);
   }
+  // Everything above reads what no launch writes (indices, the dense block);
+  // the iterate and right-hand side wait for the previous launch.
+  pdl_wait();
   auto add = [&](int rv, V pv) {
     pv += __shfl_xor_sync(0xffffffffu, pv, 1);
     if (rv == 0) acc0 += pv;
@@ -206,6 +211,7 @@ template <typename V, typename T>
 __global__ void gen_restrict_kernel(int nc, int s, int nb, const int* __restrict__ cptr,
                                     const int* __restrict__ clist, const T* __restrict__ I, const V* __restrict__ r,
                                     V* __restrict__ rc) {
+  pdl_trigger();   // the next launch may start
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nc * nb) return;
   const int c = (int)(idx / nb), row = (int)(idx % nb), v = row / s, a = row % s;
@@ -223,6 +229,7 @@ __global__ void gen_restrict_kernel(int nc, int s, int nb, const int* __restrict
 template <typename V, typename T>
 __global__ void gen_prolong_kernel(int nf, int s, int nb, const int* __restrict__ parent, const T* __restrict__ I,
                                    const V* __restrict__ xc, V* __restrict__ x) {
+  pdl_trigger();   // the next launch may start
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nf * nb) return;
   const int f = (int)(idx / nb), row = (int)(idx % nb), v = row / s, a = row % s;
@@ -236,7 +243,7 @@ __global__ void gen_prolong_kernel(int nf, int s, int nb, const int* __restrict_
 template <typename T, typename V, int S, int W>
 cudaError_t gen_launch_w(int mode, int nb, int nbp, int pos0, int npos, const int* perm, const int* tptr,
                          const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r,
-                         cudaStream_t st) {
+                         int ov, cudaStream_t st) {
   constexpr int E = kGenWarps / W;
   const int blocks = (npos + E - 1) / E;
   const size_t smem = (size_t)E * nb * nbp * sizeof(T);
@@ -252,13 +259,23 @@ cudaError_t gen_launch_w(int mode, int nb, int nbp, int pos0, int npos, const in
     if (e != cudaSuccess) return e;
     opted[mode == MODE_GS ? 0 : 1] = true;
   }
+  // ov: programmatic serialisation (the kernel starts during the previous
+  // launch, stages its dense blocks, then waits for it before any vector)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kGenWarps * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = ov ? 1 : 0;
   if (mode == MODE_GS)
-    gen_element_kernel<T, V, S, MODE_GS, W><<<blocks, kGenWarps * 32, smem, st>>>(
-        pos0, npos, nb, nbp, perm, tptr, tinfo, (const T*)cpl, (const T*)mat, (const V*)b, (V*)x, (V*)r);
-  else
-    gen_element_kernel<T, V, S, MODE_RESID, W><<<blocks, kGenWarps * 32, smem, st>>>(
-        pos0, npos, nb, nbp, perm, tptr, tinfo, (const T*)cpl, (const T*)mat, (const V*)b, (V*)x, (V*)r);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, gen_element_kernel<T, V, S, MODE_GS, W>, pos0, npos, nb, nbp, perm, tptr, tinfo,
+                              (const T*)cpl, (const T*)mat, (const V*)b, (V*)x, (V*)r);
+  return cudaLaunchKernelEx(&cfg, gen_element_kernel<T, V, S, MODE_RESID, W>, pos0, npos, nb, nbp, perm, tptr, tinfo,
+                            (const T*)cpl, (const T*)mat, (const V*)b, (V*)x, (V*)r);
 }
 
 // Warps per element by launch size and record width (measured on the 128^2
@@ -268,14 +285,14 @@ cudaError_t gen_launch_w(int mode, int nb, int nbp, int pos0, int npos, const in
 // 0.336 with two; FP32 colour sweep 0.182 / 0.167 ms).
 template <typename T, typename V, int S>
 cudaError_t gen_launch(int mode, int warps, int nb, int nbp, int pos0, int npos, const int* perm, const int* tptr,
-                       const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r,
+                       const int* tinfo, const void* cpl, const void* mat, const void* b, void* x, void* r, int ov,
                        cudaStream_t st) {
   if (warps == 1)
-    return gen_launch_w<T, V, S, 1>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    return gen_launch_w<T, V, S, 1>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, ov, st);
   if (warps == 2)
-    return gen_launch_w<T, V, S, 2>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    return gen_launch_w<T, V, S, 2>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, ov, st);
   if (warps == 4)
-    return gen_launch_w<T, V, S, 4>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    return gen_launch_w<T, V, S, 4>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, ov, st);
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -285,18 +302,18 @@ cudaError_t gen_launch(int mode, int warps, int nb, int nbp, int pos0, int npos,
   }
   const int64_t four_below = (int64_t)sms * (sizeof(T) == 4 ? 8 : 32);
   if ((int64_t)npos >= four_below)
-    return gen_launch_w<T, V, S, 2>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
-  return gen_launch_w<T, V, S, 4>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    return gen_launch_w<T, V, S, 2>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, ov, st);
+  return gen_launch_w<T, V, S, 4>(mode, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, ov, st);
 }
 
 template <typename T, typename V>
 cudaError_t gen_dispatch(int mode, int warps, int s, int nb, int nbp, int pos0, int npos, const int* perm,
                          const int* tptr, const int* tinfo, const void* cpl, const void* mat, const void* b, void* x,
-                         void* r, cudaStream_t st) {
+                         void* r, int ov, cudaStream_t st) {
   switch (s) {
-    case 4: return gen_launch<T, V, 4>(mode, warps, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
-    case 9: return gen_launch<T, V, 9>(mode, warps, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
-    case 16: return gen_launch<T, V, 16>(mode, warps, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    case 4: return gen_launch<T, V, 4>(mode, warps, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, ov, st);
+    case 9: return gen_launch<T, V, 9>(mode, warps, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, ov, st);
+    case 16: return gen_launch<T, V, 16>(mode, warps, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, ov, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -305,16 +322,17 @@ cudaError_t gen_dispatch(int mode, int warps, int s, int nb, int nbp, int pos0, 
 
 cudaError_t launch_gen_element(int storage, int mode, int warps, int s, int nb, int nbp, int pos0, int npos,
                                const int* perm, const int* tptr, const int* tinfo, const void* cpl, const void* mat,
-                               const void* b, void* x, void* r, cudaStream_t st) {
+                               const void* b, void* x, void* r, cudaStream_t st, int ov) {
   if (npos <= 0) return cudaSuccess;
   if (nb != 3 * s || nb > kGenMaxNb) return cudaErrorInvalidValue;
   // the 16-column kernels read the iterate with 16-byte loads
   if (s == 16 && (((uintptr_t)x | (uintptr_t)b) & 15)) return cudaErrorMisalignedAddress;
   if (storage == STK_FP64)
     return gen_dispatch<double, double>(mode, warps, s, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r,
-                                        st);
+                                        ov, st);
   if (storage == STK_FP32)
-    return gen_dispatch<float, float>(mode, warps, s, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, st);
+    return gen_dispatch<float, float>(mode, warps, s, nb, nbp, pos0, npos, perm, tptr, tinfo, cpl, mat, b, x, r, ov,
+                                      st);
   return cudaErrorInvalidValue;
 }
 

@@ -388,6 +388,8 @@ __global__ void __launch_bounds__(32 * kWarps) element_warp_kernel(const __grid_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TA* base = reinterpret_cast<TA*>(smem_raw) + (size_t)wid * wg.words;
   const int nwarps = gridDim.x * kWarps;
+  pdl_trigger();   // the next launch may start; this one waits for the previous
+  pdl_wait();
   for (int pos = pos0 + blockIdx.x * kWarps + wid; pos < pos0 + npos; pos += nwarps)
     warp_element<TS, TX, S>(pat, wg, mode, pos, perm, nbr, cpl, mat, tsc, rsc, b, x, rout, base);
 }
@@ -474,14 +476,6 @@ static RingGeom ring_geometry(const Pattern& pat, int P) {
 }
 
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// Programmatic dependent launch: a kernel lets the next launch on its stream
-// start (griddepcontrol.launch_dependents; a no-op when that launch does not
-// ask for it), and a kernel launched with programmatic serialisation waits
-// for the previous one to complete, its writes visible, before it touches
-// what that kernel may write (griddepcontrol.wait; a no-op otherwise).
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename TS, int S, int P>
 __global__ void __launch_bounds__(32 * kRingMaxWarps)
@@ -951,8 +945,19 @@ __global__ void __launch_bounds__(kWideNT) element_wide_kernel(const __grid_cons
                                                                const float* __restrict__ rsc,
                                                                const TX* __restrict__ b, TX* x, TX* rout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int pos = pos0 + blockIdx.x; pos < pos0 + npos; pos += gridDim.x)
-    wide_element<TS, TX, S>(pat, wg, mode, pos, perm, nbr, cpl, mat, tsc, rsc, b, x, rout, smem_raw);
+  // the first element's records (which no launch writes) are copied while the
+  // previous launch finishes; vectors wait for it
+  pdl_trigger();
+  bool staged = false;
+  if (wg.prefetch && pos0 + (int)blockIdx.x < pos0 + npos) {
+    wide_stage<TS>(pat, wg, pos0 + (int)blockIdx.x, cpl, mat, smem_raw);
+    staged = true;
+  }
+  pdl_wait();
+  for (int pos = pos0 + blockIdx.x; pos < pos0 + npos; pos += gridDim.x) {
+    wide_element<TS, TX, S>(pat, wg, mode, pos, perm, nbr, cpl, mat, tsc, rsc, b, x, rout, smem_raw, staged);
+    staged = false;
+  }
 }
 
 template <typename TS>
@@ -1143,10 +1148,28 @@ static void prepare_pipe_t() {
   prepare_pipe_s<TS, TX, 27>();
 }
 
+// A launch with programmatic stream serialisation when ov is set (the kernel
+// waits for its predecessor with griddepcontrol.wait before touching vectors).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_ov(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                             int ov, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = ov ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <typename TS, typename TX, int S>
 static cudaError_t launch_warp_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
                                  const int* nbr, const void* cpl, const void* mat, const float* tsc,
-                                 const float* rsc, const void* b, void* x, void* r, int ctas, cudaStream_t st) {
+                                 const float* rsc, const void* b, void* x, void* r, int ctas, cudaStream_t st, int ov) {
   if (npos <= 0) return cudaSuccess;
   if (pat.nb > 128) return cudaErrorInvalidValue;   // the final row loop covers 4 x 32 rows
   WarpGeom<TS> wg = warp_geometry<TS>(pat);
@@ -1154,10 +1177,8 @@ static cudaError_t launch_warp_s(const Pattern& pat, int mode, int pos0, int npo
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
   int grid = std::min((npos + kWarps - 1) / kWarps, num_sms() * std::max(1, ctas));
   if (kScaledStorage<TS> && (!tsc || !rsc)) return cudaErrorInvalidValue;
-  element_warp_kernel<TS, TX, S><<<grid, 32 * kWarps, smem, st>>>(pat, mode, pos0, npos, perm, nbr,
-                                                                   (const TS*)cpl, (const TS*)mat, tsc, rsc,
-                                                                   (const TX*)b, (TX*)x, (TX*)r);
-  return cudaGetLastError();
+  return launch_ov(element_warp_kernel<TS, TX, S>, (unsigned)grid, 32 * kWarps, smem, st, ov, pat, mode, pos0, npos,
+                   perm, nbr, (const TS*)cpl, (const TS*)mat, tsc, rsc, (const TX*)b, (TX*)x, (TX*)r);
 }
 
 template <typename TS, typename TX, int S>
@@ -1168,10 +1189,10 @@ static void prepare_warp_s() {
 template <typename TS, typename TX>
 static cudaError_t launch_warp_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
                                  const void* cpl, const void* mat, const float* tsc, const float* rsc, const void* b,
-                                 void* x, void* r, int ctas, cudaStream_t st) {
+                                 void* x, void* r, int ctas, cudaStream_t st, int ov) {
 #define STK_WARP_CASE(SV) \
   case SV:                \
-    return launch_warp_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st);
+    return launch_warp_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st, ov);
   switch (pat.s) {
     STK_WARP_CASE(4)
     STK_WARP_CASE(8)
@@ -1197,17 +1218,17 @@ static void prepare_warp_t() {
 // tsc / rsc: the FP16 records' task and row scales (ignored for the other storages).
 cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
                                 const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
-                                const void* b, void* x, void* r, int ctas, cudaStream_t st) {
+                                const void* b, void* x, void* r, int ctas, cudaStream_t st, int ov) {
   switch (storage) {
     case 0:
-      return launch_warp_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st);
+      return launch_warp_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st, ov);
     case 1:
-      return launch_warp_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st);
+      return launch_warp_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st, ov);
     case 2:
       return launch_warp_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas,
-                                                  st);
+                                                  st, ov);
     case 3:
-      return launch_warp_t<__half, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st);
+      return launch_warp_t<__half, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ctas, st, ov);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1295,17 +1316,15 @@ cudaError_t launch_element_ring(const Pattern& pat, int storage, int warps, int 
 template <typename TS, typename TX, int S>
 static cudaError_t launch_wide_s(const Pattern& pat, int mode, int pos0, int npos, const int* perm,
                                  const int* nbr, const void* cpl, const void* mat, const float* tsc,
-                                 const float* rsc, const void* b, void* x, void* r, cudaStream_t st) {
+                                 const float* rsc, const void* b, void* x, void* r, cudaStream_t st, int ov) {
   if (npos <= 0) return cudaSuccess;
   const WideGeom wg = wide_geometry<TS>(pat);
   size_t smem = wide_smem_bytes(wg);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
   int grid = std::min(npos, num_sms() * (2048 / kWideNT));
   if (kScaledStorage<TS> && (!tsc || !rsc)) return cudaErrorInvalidValue;
-  element_wide_kernel<TS, TX, S><<<grid, kWideNT, smem, st>>>(pat, wg, mode, pos0, npos, perm, nbr,
-                                                             (const TS*)cpl, (const TS*)mat, tsc, rsc,
-                                                             (const TX*)b, (TX*)x, (TX*)r);
-  return cudaGetLastError();
+  return launch_ov(element_wide_kernel<TS, TX, S>, (unsigned)grid, kWideNT, smem, st, ov, pat, wg, mode, pos0, npos,
+                   perm, nbr, (const TS*)cpl, (const TS*)mat, tsc, rsc, (const TX*)b, (TX*)x, (TX*)r);
 }
 
 template <typename TS, typename TX, int S>
@@ -1316,9 +1335,9 @@ static void prepare_wide_s() {
 template <typename TS, typename TX>
 static cudaError_t launch_wide_t(const Pattern& pat, int mode, int pos0, int npos, const int* perm, const int* nbr,
                                  const void* cpl, const void* mat, const float* tsc, const float* rsc, const void* b,
-                                 void* x, void* r, cudaStream_t st) {
+                                 void* x, void* r, cudaStream_t st, int ov) {
 #define STK_WIDE_CASE(SV) \
-  case SV: return launch_wide_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+  case SV: return launch_wide_s<TS, TX, SV>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st, ov);
   switch (pat.s) {
     STK_WIDE_CASE(4)
     STK_WIDE_CASE(8)
@@ -1345,13 +1364,13 @@ static void prepare_wide_t() {
 // geometry does not fit in shared memory.
 cudaError_t launch_element_wide(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
                                 const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
-                                const void* b, void* x, void* r, cudaStream_t st) {
+                                const void* b, void* x, void* r, cudaStream_t st, int ov) {
   switch (storage) {
-    case 0: return launch_wide_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
-    case 1: return launch_wide_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+    case 0: return launch_wide_t<double, double>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st, ov);
+    case 1: return launch_wide_t<float, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st, ov);
     case 2:
-      return launch_wide_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
-    case 3: return launch_wide_t<__half, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st);
+      return launch_wide_t<__nv_bfloat16, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st, ov);
+    case 3: return launch_wide_t<__half, float>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, st, ov);
     default: return cudaErrorInvalidValue;
   }
 }

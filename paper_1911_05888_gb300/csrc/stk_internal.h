@@ -464,7 +464,7 @@ cudaError_t launch_scale_f(int64_t n, float a, const float* x, float* y, cudaStr
 cudaError_t launch_scale_by_norm(int64_t n, const double* sums, float* g, cudaStream_t st);
 cudaError_t launch_element_wide(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
                                 const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
-                                const void* b, void* x, void* r, cudaStream_t st);
+                                const void* b, void* x, void* r, cudaStream_t st, int overlap = 0);
 cudaError_t launch_element_df(const Pattern& pat, int pos0, int npos, const int* perm, const int* nbr,
                               const void* cpl_hi, const void* cpl_lo, const void* dia_hi, const void* dia_lo,
                               const float* z, double* w, int ctas, cudaStream_t st);
@@ -476,7 +476,7 @@ cudaError_t launch_to_fp16_rows(int64_t npos, int nb, int NBP, void* dst, float*
                                 cudaStream_t st);
 cudaError_t launch_element_warp(const Pattern& pat, int storage, int mode, int pos0, int npos, const int* perm,
                                 const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
-                                const void* b, void* x, void* r, int ctas, cudaStream_t st);
+                                const void* b, void* x, void* r, int ctas, cudaStream_t st, int overlap = 0);
 cudaError_t launch_element_ring(const Pattern& pat, int storage, int warps, int mode, int pos0, int npos,
                                 const int* perm, const int* nbr, const void* cpl, const void* mat, const float* tsc,
                                 const float* rsc, const void* b, void* x, void* r, int overlap, cudaStream_t st);
@@ -493,7 +493,7 @@ cudaError_t launch_batch_solve(const BatchProblem* probs, int nprob, const Batch
 size_t batch_smem_bytes(const Pattern& pat);
 cudaError_t launch_gen_element(int storage, int mode, int warps, int s, int nb, int nbp, int pos0, int npos,
                                const int* perm, const int* tptr, const int* tinfo, const void* cpl, const void* mat,
-                               const void* b, void* x, void* r, cudaStream_t st);
+                               const void* b, void* x, void* r, cudaStream_t st, int overlap = 0);
 cudaError_t launch_gen_restrict(int vec64, int nc, int s, int nb, const int* cptr, const int* clist, const void* I,
                                 const void* r, void* rc, cudaStream_t st);
 cudaError_t launch_gen_prolong(int vec64, int nf, int s, int nb, const int* parent, const void* I, const void* xc,

@@ -478,3 +478,29 @@ def test_cut_earlier_bottom_matches_oracle():
         assert worst <= max(1e-10, 1e-15 * lam[-1] / lam[0]), worst
     finally:
         gpu.close()
+
+
+@pytest.mark.parametrize("precision", [native.FP64, native.FP32])
+def test_cut_launch_overlap_is_bit_identical(precision):
+    """Programmatic dependent launch of the cut-cell element kernel: whole
+    solves give the same iterate bit for bit with the overlap on and off."""
+    prob, gpu, mesh, levels, inj, orc = get("c16p3-bubble", precision)
+    D = gpu.scaling().ravel()
+    z = kernel_basis(levels[0])
+    bt = D * gpu.rhs().ravel()
+    bt -= z * (z @ bt)   # the consistent right-hand side of the scaled system
+    b = dev(bt)
+    gpu.ctx.set_solver(native.FGMRES, 30)
+    out = []
+    try:
+        for on in (1, 0, 1):
+            gpu.ctx.set_launch_overlap(on)
+            x = torch.zeros_like(b)
+            it, hist = gpu.ctx.solve(x, b, rtol=1e-10, maxit=200)
+            out.append((it, x.cpu().numpy(), hist[-1]))
+    finally:
+        gpu.ctx.set_launch_overlap(1)
+        gpu.ctx.set_solver(native.RICHARDSON, 30)
+    assert out[0][0] == out[1][0] == out[2][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][1], out[2][1])
+    assert out[0][2] <= 1e-10

@@ -398,16 +398,19 @@ def test_staged_16bit_kernel_on_many_elements_per_warp(precision, warps):
         gpu.close()
 
 
-@pytest.mark.parametrize("precision", [native.FP16, native.BF16])
-def test_staged_kernel_launch_overlap_is_bit_identical(precision):
-    """Programmatic dependent launch of the staged kernel
+@pytest.mark.parametrize("wide", [0, 1024])
+@pytest.mark.parametrize("precision", [native.FP16, native.BF16, native.FP32, native.FP64])
+def test_launch_overlap_is_bit_identical(precision, wide):
+    """Programmatic dependent launch of the element kernels
     (stk_set_launch_overlap): whole solves (V-cycles replayed from CUDA
-    graphs, transfers, bottom solve, every smoothing level on the staged
-    kernel) give the same iterate bit for bit with the overlap on and off."""
+    graphs, transfers, bottom solve; the staged kernel for 16-bit records,
+    the warp kernel otherwise, and with wide = 1024 the one-CTA-per-element
+    kernel on the coarse levels) give the same iterate bit for bit with the
+    overlap on and off."""
     prob = P.stress_variable_mu_2d(n=64, p=3)
     gpu = StokesMG(prob, precision=precision)
     try:
-        gpu.ctx.set_wide_launch(0)
+        gpu.ctx.set_wide_launch(wide)
         gpu.ctx.set_solver(native.FGMRES, 30)
         b = torch.from_numpy(gpu.rhs().ravel()).cuda()
         out = []
