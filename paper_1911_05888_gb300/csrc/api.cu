@@ -1367,6 +1367,7 @@ double host_norm(Ctx& c, const double* v, cudaStream_t st) {
 }
 
 // Returns the iteration count; rel holds the final true relative residual.
+// On entry c.r64 holds b - A x and rel its norm over bnorm (stk_solve).
 int fgmres(Ctx& c, double* x, const double* b, double rtol, int maxit, double* hist, double bnorm,
            double& rel, cudaStream_t st) {
   ensure_krylov(c, c.restart);
@@ -1374,9 +1375,7 @@ int fgmres(Ctx& c, double* x, const double* b, double rtol, int maxit, double* h
   int64_t n0 = level_ne(c, 0) * c.nb;
   const int m = c.restart;
   std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), h(m + 1), h2(m + 1), y(m);
-  enqueue_residual64(c, x, b, c.r64, st);
-  double beta = host_norm(c, c.r64, st);
-  rel = beta / bnorm;
+  double beta = rel * bnorm;
   double rel0 = rel;
   int it = 0;
   while (rel > rtol && it < maxit) {
@@ -2170,15 +2169,26 @@ int stk_solve(stk_ctx* c, double* x, const double* b, double rtol, int maxit, in
     ck(cudaStreamSynchronize(user), "sync caller stream");
     cudaStream_t st = c->stream;
     ck(cudaMemsetAsync(c->dev_err, 0, sizeof(int), st), "clear error word");
-    // ||b||
+    // ||b||, and ||x|| to recognise a zero first guess
     enqueue_norm(*c, b, st);
     ck(cudaStreamSynchronize(st), "sync");
-    double bnorm = std::sqrt(c->norm_host[0]);
-    if (bnorm == 0.0) bnorm = 1.0;
-    enqueue_residual64(*c, x, b, c->r64, st);
-    enqueue_norm(*c, c->r64, st);
+    const double bnorm_true = std::sqrt(c->norm_host[0]);
+    double bnorm = bnorm_true == 0.0 ? 1.0 : bnorm_true;
+    enqueue_norm(*c, x, st);
     ck(cudaStreamSynchronize(st), "sync");
-    double rel = std::sqrt(c->norm_host[0]) / bnorm, rel0 = rel;
+    double rnorm;
+    if (c->norm_host[0] == 0.0) {
+      // x = 0: b - A x is b itself, exactly (no pass over the FP64 records)
+      ck(cudaMemcpyAsync(c->r64, b, (size_t)level_ne(*c, 0) * c->nb * sizeof(double), cudaMemcpyDeviceToDevice, st),
+         "r = b");
+      rnorm = bnorm_true;
+    } else {
+      enqueue_residual64(*c, x, b, c->r64, st);
+      enqueue_norm(*c, c->r64, st);
+      ck(cudaStreamSynchronize(st), "sync");
+      rnorm = std::sqrt(c->norm_host[0]);
+    }
+    double rel = rnorm / bnorm, rel0 = rel;
     if (hist) hist[0] = rel;
     int it = 0;
     const bool learned = c->learn_on && c->lW1 && c->precision != STK_FP64;
