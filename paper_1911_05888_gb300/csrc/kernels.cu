@@ -1432,7 +1432,9 @@ cudaError_t launch_element(const Pattern& pat, int storage, int mode, int pos0, 
 // P: [child][s][s] in the vector precision; PT its per-child transpose.
 cudaError_t launch_restrict(int vec64, int d, int s, int nb, const int* nc, const int* nf, int64_t nec,
                             const void* P, const void* r, void* rc, cudaStream_t st) {
-  int grid = (int)std::min<int64_t>(nec, (int64_t)num_sms() * 8);
+  // 16 CTAs of 128 threads per SM: each CTA walks its coarse elements one
+  // after another, so the finest-level transfer is a chain per CTA
+  int grid = (int)std::min<int64_t>(nec, (int64_t)num_sms() * 16);
   size_t es = vec64 ? 8 : 4;
   size_t smem = (size_t)(1 << d) * nb * es;
   if (vec64)
@@ -1446,7 +1448,7 @@ cudaError_t launch_restrict(int vec64, int d, int s, int nb, const int* nc, cons
 
 cudaError_t launch_prolong(int vec64, int d, int s, int nb, const int* nf, const int* nc, int64_t nec,
                            const void* PT, const void* xc, void* x, cudaStream_t st) {
-  int grid = (int)std::min<int64_t>(nec, (int64_t)num_sms() * 8);
+  int grid = (int)std::min<int64_t>(nec, (int64_t)num_sms() * 16);
   size_t es = vec64 ? 8 : 4;
   size_t smem = (size_t)nb * es;
   if (vec64)
