@@ -686,7 +686,8 @@ int stk_set_solver(stk_ctx* ctx, int method, int restart);
  * shapes and precisions run variant 2; the same products as variant 2, each
  * coupling row summed as two halves of its columns).
  * The variant and `ctas_per_sm` (the grid of variants 1 and 2, CTAs per SM;
- * for variant 3 the warps per element, 1 or 2, default 2) apply to the
+ * for variant 3 the warps per element: 1, 4, or 2 (the default: four on
+ * launches of at most six elements per SM)) apply to the
  * blocks stored in `precision` only.  Zero for ctas_per_sm and stages selects the
  * built-in shape for the record size.
  * Shapes whose ring does not fit in shared memory fall back to variant 0.

@@ -2314,7 +2314,8 @@ int stk_set_tuning(stk_ctx* c, int variant, int precision, int ctas_per_sm, int 
     c->variant_of[precision] = variant;
     if (variant == 2 && ctas_per_sm > 0) c->warp_ctas[precision] = ctas_per_sm;
     if (variant == 3) {
-      if (ctas_per_sm > 2) return fail(c, STK_ERR_INVALID_ARG, "variant 3 takes 1 or 2 warps per element");
+      if (ctas_per_sm == 3 || ctas_per_sm > 4)
+        return fail(c, STK_ERR_INVALID_ARG, "variant 3 takes 1, 2 or 4 warps per element");
       c->ring_warps[precision] = ctas_per_sm > 0 ? ctas_per_sm : 2;
     }
     if (variant == 1 && ctas_per_sm > 0 && stages > 0) {

@@ -1278,7 +1278,12 @@ template <typename TS>
 static cudaError_t launch_ring_t(const Pattern& pat, int warps, int mode, int pos0, int npos, const int* perm,
                                  const int* nbr, const void* cpl, const void* mat, const float* tsc, const float* rsc,
                                  const void* b, void* x, void* r, int ov, cudaStream_t st) {
+  // warps = 2 (the default) takes four warps per element for launches of at
+  // most one element per four-warp slot (the coarse levels: each slot then
+  // walks a single element, whose compute four warps halve)
   if (warps == 1) return launch_ring_p<TS, 1>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ov, st);
+  if (warps == 4 || (warps == 2 && npos <= num_sms() * (kRingMaxWarps / 4)))
+    return launch_ring_p<TS, 4>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ov, st);
   return launch_ring_p<TS, 2>(pat, mode, pos0, npos, perm, nbr, cpl, mat, tsc, rsc, b, x, r, ov, st);
 }
 
@@ -1293,10 +1298,11 @@ template <typename TS>
 static void prepare_ring_t() {
   prepare_ring_p<TS, 1>();
   prepare_ring_p<TS, 2>();
+  prepare_ring_p<TS, 4>();
 }
 
-// 16-bit records only (storage 2 = BF16, 3 = scaled FP16), warps = 1 or 2
-// per element; overlap = launch with programmatic serialisation (the kernel
+// 16-bit records only (storage 2 = BF16, 3 = scaled FP16), warps = 1, 2 or
+// 4 per element (2: four for small launches); overlap = launch with programmatic serialisation (the kernel
 // starts while the previous launch on the stream finishes, and fetches its
 // first element's records before waiting for it).  cudaErrorInvalidValue for
 // other storages and for shapes the staged kernel does not take.

@@ -349,7 +349,7 @@ def _with_variant(gpu, precision, variant, fn, shape=0):
         gpu.ctx.set_wide_launch(1024)
 
 
-@pytest.mark.parametrize("warps", [1, 2])
+@pytest.mark.parametrize("warps", [1, 2, 4])
 @pytest.mark.parametrize("precision", [native.FP16, native.BF16])
 @pytest.mark.parametrize("name", ["stress16p3", "3d-mixed-p1"])
 def test_staged_16bit_kernel_matches_oracle(name, precision, warps):
@@ -375,7 +375,7 @@ def test_staged_16bit_kernel_matches_oracle(name, precision, warps):
     assert rel(xs, xo) <= 1e-4 and maxrel(xs, xo) <= 1e-3
 
 
-@pytest.mark.parametrize("warps", [1, 2])
+@pytest.mark.parametrize("warps", [1, 2, 4])
 @pytest.mark.parametrize("precision", [native.FP16, native.BF16])
 def test_staged_16bit_kernel_on_many_elements_per_warp(precision, warps):
     """128 x 128, p = 3 viscous stress: each element slot of the staged kernel
