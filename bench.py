@@ -569,6 +569,10 @@ def run_native(args):
     clk = clocks.stop()
     ok = [a for a in arm_names if final_residual(arm_runs[a][3]) <= 1e-10] or arm_names
     head = min(ok, key=lambda a: arm_runs[a][0])
+    if dist:   # every rank reports the arm rank 0 chose
+        hi = torch.tensor([arm_names.index(head)], dtype=torch.int64, device="cuda")
+        dist.broadcast(hi, 0)
+        head = arm_names[int(hi.item())]
     precision_arms = {a: {"ms_per_solve": round(arm_runs[a][0] / args.steps * 1e3, 3), "iters": arm_runs[a][1][0],
                           "final_rel_residual": final_residual(arm_runs[a][3]),
                           "autotune": arms[a][1][0]} for a in arm_names}
