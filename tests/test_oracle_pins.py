@@ -1244,3 +1244,103 @@ def test_float32_cycle_emulation_tracks_the_fp64_cycle():
     x32 = mg.precondition_fp32(b)
     d = np.linalg.norm(x32 - x64) / np.linalg.norm(x64)
     assert 1e-9 < d <= 1e-5, d
+
+
+# ---- Chebyshev-accelerated block Gauss-Seidel (Concluding Remarks; oracle/chebyshev.py)
+
+def _gs_pair(prob):
+    mg = multigrid.Multigrid(prob, two_colours=prob.gamma == 0 and prob.phase is None)
+    sm = mg.sm[0]
+    A = mg.levels[0].A
+
+    def minv(r):
+        z = np.zeros_like(r)
+        sm.sweep(z, r)
+        return z
+    return mg, sm, A, minv
+
+
+def test_chebyshev_degree_one_is_a_gauss_seidel_sweep():
+    """One step with theta = 1 is x + M^{-1}(b - A x): one coloured block
+    Gauss-Seidel sweep, whatever delta^2."""
+    from oracle import chebyshev
+    mg, sm, A, minv = _gs_pair(P.stress_variable_mu_2d(n=4, p=2))
+    rng = np.random.default_rng(41)
+    x0, b = rng.uniform(-1, 1, A.shape[0]), rng.uniform(-1, 1, A.shape[0])
+    ref = x0.copy()
+    sm.sweep(ref, b)
+    for d2 in (-0.3, 0.0, 0.2):
+        x = chebyshev.chebyshev_iteration(lambda v: A @ v, minv, x0.copy(), b, 1, 1.0, d2)
+        assert np.abs(x - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_chebyshev_error_is_the_scaled_chebyshev_polynomial():
+    """Textbook property on a symmetric positive definite diagonal operator
+    with spectrum in [a, b] and M = I: after k steps with theta = (a + b) / 2,
+    delta = (b - a) / 2 each eigencomponent of the error is multiplied by
+    T_k((theta - lambda) / delta) / T_k(theta / delta)."""
+    from numpy.polynomial import chebyshev as C
+    from oracle import chebyshev
+    lam = np.linspace(0.2, 3.0, 40)
+    a, b_ = lam.min(), lam.max()
+    theta, delta = 0.5 * (a + b_), 0.5 * (b_ - a)
+    xs = np.random.default_rng(43).uniform(-1, 1, lam.size)
+    rhs = lam * xs
+    for k in (1, 2, 3, 5, 8):
+        x = chebyshev.chebyshev_iteration(lambda v: lam * v, lambda r: r, np.zeros_like(xs), rhs, k, theta,
+                                          delta ** 2)
+        Tk = np.zeros(k + 1)
+        Tk[k] = 1.0
+        factor = C.chebval((theta - lam) / delta, Tk) / C.chebval(theta / delta, Tk)
+        assert np.abs((xs - x) - factor * xs).max() <= 1e-12
+
+
+def test_chebyshev_real_recurrence_matches_complex_form():
+    """With imaginary foci (delta^2 < 0) Saad's recurrence in complex
+    arithmetic produces real iterates, equal to the real recurrence in
+    delta^2: pins the rewriting q_k = rho_k / delta."""
+    from oracle import chebyshev
+    mg, sm, A, minv = _gs_pair(P.periodic_standard_2d(n=4, p=1))
+    rng = np.random.default_rng(47)
+    x0, b = rng.uniform(-1, 1, A.shape[0]), rng.uniform(-1, 1, A.shape[0])
+    for theta, d2 in ((0.9, -0.2), (1.1, -0.05), (0.8, 0.1)):
+        xr = chebyshev.chebyshev_iteration(lambda v: A @ v, minv, x0.copy(), b, 4, theta, d2)
+        delta = np.sqrt(complex(d2))
+        xc = chebyshev.chebyshev_complex(lambda v: A @ v, minv, x0.copy(), b, 4, theta, delta)
+        scale = np.abs(xr).max()
+        assert np.abs(xc.imag).max() <= 1e-12 * scale
+        assert np.abs(xc.real - xr).max() <= 1e-12 * scale
+
+
+def test_chebyshev_cycle_with_theta_one_and_zero_delta_is_the_plain_cycle():
+    """theta = 1, delta^2 = 0 makes every step x + M^{-1}(b - A x): the
+    Chebyshev V-cycle is Algorithm 1's V-cycle."""
+    from oracle import chebyshev
+    prob = P.stress_variable_mu_2d(n=8, p=2)
+    mg = multigrid.Multigrid(prob)
+    mc = chebyshev.ChebyshevMultigrid(prob, params=[(1.0, 0.0)] * len(mg.sm))
+    r = np.random.default_rng(53).uniform(-1, 1, prob.n_dofs)
+    xp, xc = mg.precondition(r), mc.precondition(r)
+    assert np.abs(xp - xc).max() <= 1e-12 * np.abs(xp).max()
+
+
+def test_chebyshev_does_not_beat_plain_sweeps_at_equal_passes():
+    """Measured comparison behind the decision not to put the Chebyshev
+    smoother on the GPU.  A Chebyshev phase of degree k costs k sweeps and
+    k - 1 residuals, i.e. k + (k - 1) passes over the blocks when a residual
+    pass is counted like a sweep; degree 2 costs the three passes of plain
+    V(3,3)'s phase.  The best (theta, delta^2) of a grid over theta in
+    [0.7, 1.1] and delta^2 in [-0.3, 0.2] (found on these 8 x 8, p = 2
+    problems: (0.85, 0) viscous stress, (0.9, -0.1) periodic standard form)
+    gives a V(2,2)-Chebyshev rho above plain V(3,3)'s."""
+    from oracle import chebyshev
+    for prob, best in ((P.stress_variable_mu_2d(n=8, p=2), (0.85, 0.0)),
+                       (P.periodic_standard_2d(n=8, p=2), (0.9, -0.1))):
+        two = prob.gamma == 0 and prob.phase is None
+        x0 = np.random.default_rng(0).uniform(-1, 1, prob.n_dofs)
+        plain = multigrid.Multigrid(prob.with_(nu1=3, nu2=3), two_colours=two).gmres_rho(x0)[0]
+        p2 = prob.with_(nu1=2, nu2=2)
+        mg2 = multigrid.Multigrid(p2, two_colours=two)
+        cheb = chebyshev.ChebyshevMultigrid(p2, params=[best] * len(mg2.sm), two_colours=two).gmres_rho(x0,
+                                                                                                     maxit=60)[0]
+        assert cheb > plain, (cheb, plain)
