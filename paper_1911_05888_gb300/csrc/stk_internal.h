@@ -278,7 +278,7 @@ struct Ctx {
   // with the pipeline shape per storage precision (CTAs per SM, ring depth)
   int variant_of[4] = {2, 2, 3, 3};   // per storage precision (3: 16-bit records staged)
   int ring_warps[4] = {2, 2, 2, 2};   // warps per element of variant 3
-  int launch_overlap = 1;             // staged launches with programmatic serialisation
+  int launch_overlap = 1;             // element-kernel launches with programmatic serialisation
   int pipe_ctas[4] = {0, 0, 0, 0}, pipe_stages[4] = {0, 0, 0, 0};
   int warp_ctas[4] = {4, 4, 4, 4};   // CTAs (of 8 warps) per SM for the warp-per-element kernel
   // launches of at most this many elements use one CTA per element (latency variant), whatever the variant
