@@ -91,3 +91,23 @@ def test_cpu_child_single_outer_iteration():
     assert p.returncode == 0, p.stderr
     rec = json.loads(p.stdout.strip().splitlines()[-1])
     assert rec["cycles"] == 1 and rec["setup_s"] >= 0
+
+
+@pytest.mark.parametrize("argv,arms,precision", [
+    ([], "fp32,fp16", "fp32"),
+    (["--precision", "bf16"], "bf16", "bf16"),
+    (["--arms", "fp16"], "fp16", "fp32"),
+    (["--workload", "unsteady3d"], "fp32", "fp16"),
+    (["--workload", "batch"], "fp32", "fp16"),
+    (["--workload", "cut"], "fp32", "fp32"),
+    (["--workload", "cut", "--precision", "fp64"], "fp64", "fp64"),
+])
+def test_precision_defaults(monkeypatch, argv, arms, precision):
+    """The default run times the FP32 and the scaled-FP16 cycle of the 256^2
+    workload; the unsteady and batch workloads default to FP16 blocks, the
+    cut-cell one to FP32; an explicit --precision is the only arm."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+    args = bench.parse()
+    assert args.arms == arms and args.precision == precision
