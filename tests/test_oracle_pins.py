@@ -1344,3 +1344,98 @@ def test_chebyshev_does_not_beat_plain_sweeps_at_equal_passes():
         cheb = chebyshev.ChebyshevMultigrid(p2, params=[best] * len(mg2.sm), two_colours=two).gmres_rho(x0,
                                                                                                      maxit=60)[0]
         assert cheb > plain, (cheb, plain)
+
+
+# ---- 3D cut cells of an embedded sphere (Section 5's sphere; oracle/cutcell3d.py)
+
+def _sphere_grid(S, n, q):
+    from oracle import cutcell3d as C3
+    h = 1.0 / n
+    out = []
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                lo = np.array([i, j, k]) * h
+                hi = lo + h
+                cl = C3.classify(S, lo, hi)
+                if cl == 0:
+                    out.append((lo, hi, 0, C3.cell_rules(S, lo, hi, q)))
+                else:
+                    out.append((lo, hi, cl, C3._box_rule(lo, hi, q)))
+    return out
+
+
+def test_sphere_cut_cells_volume_area_and_moment():
+    """Ball volume 4/3 pi r^3, sphere area 4 pi r^2 and the second moment
+    int_ball |x - c|^2 = 4 pi r^5 / 5, summed over the cut and uncut cells of
+    a 10^3 grid (q = 6); the inside and outside rules together give the box."""
+    from oracle import cutcell3d as C3
+    S = C3.Sphere((0.51, 0.47, 0.53), 0.3)
+    r = S.r
+    vin = vtot = area = m2 = 0.0
+    for lo, hi, cl, rules in _sphere_grid(S, 10, 6):
+        if cl == 0:
+            (xi, wi), (xo, wo), (xs, ws, ns) = rules
+            vin += wi.sum()
+            vtot += wi.sum() + wo.sum()
+            area += ws.sum()
+            m2 += (wi * ((xi - S.c) ** 2).sum(1)).sum()
+        else:
+            x, w = rules
+            vtot += w.sum()
+            if cl < 0:
+                vin += w.sum()
+                m2 += (w * ((x - S.c) ** 2).sum(1)).sum()
+    assert abs(vin - 4.0 / 3.0 * np.pi * r ** 3) <= 1e-10
+    assert abs(area - 4.0 * np.pi * r ** 2) <= 1e-8
+    assert abs(m2 - 4.0 * np.pi * r ** 5 / 5.0) <= 1e-11
+    assert abs(vtot - 1.0) <= 1e-13
+
+
+def test_sphere_cut_cells_divergence_theorem_per_piece():
+    """For a cubic vector field F, on the inside and the outside piece of every
+    cut cell: int div F dV equals the flux through the piece's boundary (the
+    sphere patch with its normal, pointing out of the ball, and the piece's
+    parts of the six cell faces), to 1e-9 of the cell's scale."""
+    from oracle import cutcell3d as C3
+    S = C3.Sphere((0.49, 0.52, 0.5), 0.27)
+    rng = np.random.default_rng(61)
+    A = rng.uniform(-1, 1, (3, 4, 3))   # F_a = sum_m A[a, m, b] x_b^m
+
+    def F(x):
+        return np.stack([sum(A[a, m, b] * x[:, b] ** m for m in range(4) for b in range(3)) for a in range(3)], 1)
+
+    def divF(x):
+        return sum(sum(m * A[a, m, a] * x[:, a] ** (m - 1) for m in range(1, 4)) for a in range(3))
+    q = 6
+    checked = 0
+    for lo, hi, cl, rules in _sphere_grid(S, 8, q):
+        if cl != 0:
+            continue
+        (xi, wi), (xo, wo), (xs, ws, ns) = rules
+        flux_s = (ws * (F(xs) * ns).sum(1)).sum()
+        for ph, (x, w), sgn in ((1, (xi, wi), 1.0), (2, (xo, wo), -1.0)):
+            flux = sgn * flux_s
+            for axis in range(3):
+                for value, out in ((lo[axis], -1.0), (hi[axis], 1.0)):
+                    fx, fw = C3.face_parts(S, lo, hi, axis, value, q)[ph]
+                    if len(fw):
+                        flux += out * (fw * F(fx)[:, axis]).sum()
+            vol = (w * divF(x)).sum()
+            assert abs(vol - flux) <= 1e-9 * (hi[0] - lo[0]) ** 2, (lo, ph, vol, flux)
+        checked += 1
+    assert checked > 50
+
+
+def test_sphere_inside_one_cell_is_handled_by_subdivision():
+    """A sphere wholly inside one cell: every height direction has the
+    silhouette crossing the cell's tangential rectangle, so the cell is split
+    until one does not; the rules still give the ball's volume and the
+    sphere's area."""
+    from oracle import cutcell3d as C3
+    S = C3.Sphere((0.4, 0.55, 0.45), 0.2)
+    (xi, wi), (xo, wo), (xs, ws, ns) = C3.cell_rules(S, np.zeros(3), np.ones(3), 8)
+    assert abs(wi.sum() - 4.0 / 3.0 * np.pi * 0.2 ** 3) <= 1e-11
+    assert abs(ws.sum() - 4.0 * np.pi * 0.2 ** 2) <= 1e-9
+    assert abs(wi.sum() + wo.sum() - 1.0) <= 1e-13
+    assert np.abs(np.linalg.norm(xs - S.c, axis=1) - 0.2).max() <= 1e-14
