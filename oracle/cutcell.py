@@ -51,6 +51,29 @@ def _gauss_on(a, b, q):
     return 0.5 * (a + b) + 0.5 * (b - a) * x, 0.5 * (b - a) * w
 
 
+def graded_cuts(a, b, sing, levels=40):
+    """Cut points of [a, b]: its ends, plus halvings toward an end that one of
+    the branch points sing (the circle's extreme points, where the chord's
+    half-width and the arc's ds / dt have square-root singularities) lies
+    beyond or at, closer than b - a: a + L / 2^j (or b - L / 2^j), j = 1, 2, ...
+    until the step is no longer than the distance (at most `levels` halvings).
+    Each piece then sees the singularity at a relative distance of order one,
+    so its Gauss rule converges exponentially."""
+    L = b - a
+    cuts = {a, b}
+    for end, inward in ((a, 1.0), (b, -1.0)):
+        d = min((abs(e - end) for e in sing if (e - end) * inward <= 0.0), default=np.inf)
+        if d >= L:
+            continue
+        step = L
+        for _ in range(levels):
+            step *= 0.5
+            cuts.add(end + inward * step)
+            if step <= d:
+                break
+    return sorted(cuts)
+
+
 def classify(circle, lo, hi):
     """-1 inside, +1 outside, 0 cut, for the cell [lo, hi] (2D)."""
     lo, hi = np.asarray(lo, float), np.asarray(hi, float)
@@ -125,9 +148,12 @@ def cell_rules(circle, lo, hi, q):
         p[:, h_ax] = hvals
         lst.append(p)
 
+    pieces = []
     for a, b in zip(brk[:-1], brk[1:]):
-        if b - a <= 0:
-            continue
+        if b - a > 0:
+            cuts = graded_cuts(a, b, (c_t - r, c_t + r))
+            pieces += [(u, v) for u, v in zip(cuts[:-1], cuts[1:]) if v > u]
+    for a, b in pieces:
         ts, wts = _gauss_on(a, b, q)
         for t, wt in zip(ts, wts):
             disc = r * r - (t - c_t) ** 2

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <limits>
 #include <set>
 #include <string>
 #include <vector>
@@ -95,9 +96,37 @@ void cut_cell_rules(const Circ& C, const double* lo, const double* hi, const std
     }
   };
   std::vector<double> bs(brk.begin(), brk.end());
+  // Each interval graded by halving toward an end that one of the circle's
+  // extreme points (square-root branch points of the chord's half-width and
+  // of the arc's ds / dt) lies beyond or at, closer than the interval's length
+  // (at most 40 halvings): the Gauss rules of the pieces then converge
+  // exponentially.
+  const double sing[2] = {c_t - r, c_t + r};
+  std::vector<std::pair<double, double>> pieces;
   for (size_t m = 0; m + 1 < bs.size(); ++m) {
     const double a = bs[m], b = bs[m + 1];
     if (b - a <= 0) continue;
+    const double L = b - a;
+    std::set<double> cuts = {a, b};
+    const double ends[2] = {a, b}, inward[2] = {1.0, -1.0};
+    for (int side = 0; side < 2; ++side) {
+      double d = std::numeric_limits<double>::infinity();
+      for (double e : sing)
+        if ((e - ends[side]) * inward[side] <= 0.0) d = std::min(d, std::fabs(e - ends[side]));
+      if (d >= L) continue;
+      double step = L;
+      for (int lev = 0; lev < 40; ++lev) {
+        step *= 0.5;
+        cuts.insert(ends[side] + inward[side] * step);
+        if (step <= d) break;
+      }
+    }
+    std::vector<double> cv(cuts.begin(), cuts.end());
+    for (size_t j = 0; j + 1 < cv.size(); ++j)
+      if (cv[j + 1] > cv[j]) pieces.emplace_back(cv[j], cv[j + 1]);
+  }
+  for (const auto& pc : pieces) {
+    const double a = pc.first, b = pc.second;
     std::vector<double> ts, wts;
     gauss_on(a, b, gx, gw, ts, wts);
     for (size_t k = 0; k < ts.size(); ++k) {
