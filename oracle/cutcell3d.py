@@ -297,3 +297,101 @@ def face_parts(sphere, lo, hi, axis, value, q):
         p[:, axis] = value
         return p
     return {1: (lift(xi), wi), 2: (lift(xo), wo)}
+
+
+class CutMesh3D:
+    """The pieces of an n^3 grid on [lo, hi]^3 cut by a sphere: one piece per
+    uncut cell, two per cut cell (phase 1 inside, 2 outside), each with its
+    volume and rule; and the merged elements, by the same reading as the 2D
+    mesh: a piece below merge_fraction of its cell's volume joins the
+    same-phase piece across the cell face whose same-phase part has the
+    largest area, among neighbours that are not small themselves."""
+
+    def __init__(self, sphere, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), q=6, merge_fraction=0.25):
+        self.sphere, self.n, self.q = sphere, int(n), q
+        self.lo, self.hi = np.asarray(lo, float), np.asarray(hi, float)
+        self.h = (self.hi - self.lo) / self.n
+        self.cell_volume = float(np.prod(self.h))
+        self.pieces = []
+        self.piece_of = {}
+        self.interface = {}
+        for kk in range(self.n):
+            for j in range(self.n):
+                for i in range(self.n):
+                    clo = self.lo + self.h * np.array([i, j, kk])
+                    chi = clo + self.h
+                    cl = classify(sphere, clo, chi)
+                    if cl != 0:
+                        self._add((i, j, kk), 1 if cl < 0 else 2, *_box_rule(clo, chi, q))
+                        continue
+                    (xi, wi), (xo, wo), ifr = cell_rules(sphere, clo, chi, q)
+                    self._add((i, j, kk), 1, xi, wi)
+                    self._add((i, j, kk), 2, xo, wo)
+                    self.interface[(i, j, kk)] = ifr
+        self._merge(merge_fraction)
+
+    def _add(self, cell, ph, px, pw):
+        self.piece_of[cell + (ph,)] = len(self.pieces)
+        self.pieces.append(dict(cell=cell, phase=ph, volume=float(pw.sum()), points=px, weights=pw))
+
+    def shared_face_area(self, cell, axis, sign, ph):
+        """Area of the phase-ph part of the face of `cell` toward its neighbour
+        at +-e_axis (sign +1 or -1)."""
+        clo = self.lo + self.h * np.array(cell)
+        chi = clo + self.h
+        value = chi[axis] if sign > 0 else clo[axis]
+        return float(face_parts(self.sphere, clo, chi, axis, value, self.q)[ph][1].sum())
+
+    def _merge(self, frac):
+        """element[p]: the element (a representative piece) of every piece.
+        A small piece joins the same-phase face neighbour whose shared
+        same-phase face part is largest, non-small neighbours first; if all of
+        them are small (a sliver near an edge or corner of the cell, where the
+        sphere enters it only slightly, a case the 2D mesh does not have) it
+        joins the largest-sharing small one, and the joins are followed
+        transitively.  The representative of an element is its non-small
+        piece, else its first piece."""
+        npc = len(self.pieces)
+        parent = list(range(npc))
+
+        def find(a):
+            while parent[a] != a:
+                parent[a] = parent[parent[a]]
+                a = parent[a]
+            return a
+        small = [p["volume"] < frac * self.cell_volume for p in self.pieces]
+        self.merged_into = {}
+        for k, p in enumerate(self.pieces):
+            if not small[k]:
+                continue
+            cand = []
+            for axis in range(3):
+                for sign in (-1, 1):
+                    nc = list(p["cell"])
+                    nc[axis] += sign
+                    if not 0 <= nc[axis] < self.n:
+                        continue
+                    nb = self.piece_of.get(tuple(nc) + (p["phase"],))
+                    if nb is None:
+                        continue
+                    A = self.shared_face_area(p["cell"], axis, sign, p["phase"])
+                    if A > 0:
+                        cand.append((not small[nb], A, -nb, nb))
+            if cand:
+                best = max(cand)[3]
+                self.merged_into[k] = best
+                ra, rb = find(k), find(best)
+                if ra != rb:
+                    parent[ra] = rb
+        groups = {}
+        for k in range(npc):
+            groups.setdefault(find(k), []).append(k)
+        self.element = [0] * npc
+        for members in groups.values():
+            big = [k for k in members if not small[k]]
+            rep = big[0] if big else members[0]
+            for k in members:
+                self.element[k] = rep
+
+    def element_volume(self, rep):
+        return sum(p["volume"] for k, p in enumerate(self.pieces) if self.element[k] == rep)

@@ -1459,3 +1459,28 @@ def test_cut_cell_rules_converge_on_coarse_cells():
     dy = 0.52 - 0.5
     half = rho * rho * np.arccos(dy / rho) - dy * np.sqrt(rho * rho - dy * dy)   # segment y <= 0.5
     assert abs(w.sum() - 0.5 * half) <= 1e-13
+
+
+def test_sphere_cut_mesh_merging():
+    """The 3D cut mesh of a sphere (8^3 cells): the pieces keep the ball's
+    volume and the box's; after merging every element holds at least a
+    quarter of a cell, has one phase, and every join links face neighbours
+    that share a positive same-phase face area."""
+    from oracle import cutcell3d as C3
+    S = C3.Sphere((0.48, 0.53, 0.5), 0.29)
+    m = C3.CutMesh3D(S, 8, q=6)
+    vin = sum(p["volume"] for p in m.pieces if p["phase"] == 1)
+    assert abs(vin - 4.0 / 3.0 * np.pi * S.r ** 3) <= 1e-10
+    assert abs(sum(p["volume"] for p in m.pieces) - 1.0) <= 1e-12
+    assert len(m.merged_into) > 0
+    groups = {}
+    for k, rep in enumerate(m.element):
+        groups.setdefault(rep, []).append(k)
+    for rep, members in groups.items():
+        assert sum(m.pieces[k]["volume"] for k in members) >= 0.25 * m.cell_volume
+        assert len({m.pieces[k]["phase"] for k in members}) == 1
+    for k, tgt in m.merged_into.items():
+        a, b = np.array(m.pieces[k]["cell"]), np.array(m.pieces[tgt]["cell"])
+        assert np.abs(a - b).sum() == 1 and m.pieces[k]["phase"] == m.pieces[tgt]["phase"]
+        axis = int(np.nonzero(b - a)[0][0])
+        assert m.shared_face_area(tuple(a), axis, int((b - a)[axis]), m.pieces[k]["phase"]) > 0
